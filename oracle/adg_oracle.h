@@ -1,0 +1,88 @@
+/* Plain FP64 CPU oracle of the asynchronous discontinuous Galerkin (ADG) scheme
+ * for the 1D reacting Euler equations (arXiv 2501.01747).
+ *
+ * TEST INFRASTRUCTURE ONLY. This library exists to check the CUDA path: only the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg may load it.
+ * It shares no code with the CUDA library (no headers, helpers or tables).
+ *
+ * Conventions (the oracle's own; the C-ABI of the CUDA library is separate):
+ *   state w: modal Legendre coefficients, layout [nv][n_elem][p+1], nv = ns + 2,
+ *   variable 0 = rho*u, 1 = rho*E, 2+i = rho*Y_i. Density is the sum of the
+ *   partial densities.
+ */
+#ifndef ADG_ORACLE_H
+#define ADG_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int ns, nr;
+  const double *W, *cp, *hf, *s0;  /* [ns] kg/mol, J/mol/K, J/mol, J/mol/K */
+  const signed char *nu_f, *nu_r;  /* [nr][ns] */
+  const double *A, *b, *Ea;        /* [nr] SI, -, J/mol */
+} or_mech;
+
+typedef struct {
+  int n_elem, p, n_pe;
+  double x0, length, dt;
+  int bc_left, bc_right; /* 0 periodic, 1 reflecting, 2 outflow */
+  int flux;              /* 0 local Lax-Friedrichs, 1 HLLC */
+  int limiter;           /* 0 none, 1 WENO (AT-WENO at delayed PE faces) */
+  int at_order;          /* >= 1 */
+  int delay_mode;        /* 0 synchronous, 1 CAA, 2 SAA */
+  int max_delay;
+  const double *delay_probs; /* [max_delay+1] (SAA) */
+  uint64_t seed;
+  double tvb_M;
+} or_cfg;
+
+typedef struct or_ctx or_ctx;
+
+/* quadrature and basis */
+void or_legendre(int n, double x, double *P, double *dP);
+int or_gauss(int q, double *x, double *w);
+/* AT coefficients c_m(k), m = 0..order-1 (Eq. 7-8) */
+void or_at_coeffs(int order, int k, double *c);
+int or_delay(const or_cfg *cfg, int64_t step, int face);
+uint64_t or_splitmix64(uint64_t x);
+
+/* thermo and kinetics */
+int or_temperature(const or_mech *m, const double *r, double rhoe, double Tguess,
+                   double *T);
+void or_state(const or_mech *m, const double *w, double *rho, double *u, double *T,
+              double *P, double *a);
+void or_cons_from_prim(const or_mech *m, double T, double P, double u, const double *Y,
+                       double *w);
+void or_rates(const or_mech *m, double T, int j, double *kf, double *Kc);
+void or_wdot(const or_mech *m, double T, const double *conc, double *wdot);
+void or_phys_flux(const or_mech *m, const double *w, double *f);
+void or_num_flux(const or_mech *m, int kind, const double *wl, const double *wr,
+                 double *f);
+void or_eigen(const or_mech *m, const double *wbar, double *R, double *L, double *lam);
+
+/* DG tables for degree p (shift: neighbour polynomial continued into the cell) */
+void or_beta_matrix(int p, double *B);
+void or_shift_matrix(int p, int dir, double *S);
+
+/* full scheme */
+or_ctx *or_create(const or_cfg *cfg, const or_mech *m);
+void or_destroy(or_ctx *c);
+int or_set_primitive(or_ctx *c, const double *prim);
+int or_set_state(or_ctx *c, const double *w);
+int or_get_state(const or_ctx *c, double *w);
+int or_step(or_ctx *c, int n_steps);
+int64_t or_steps_done(const or_ctx *c);
+/* troubled-cell flags: stages of the last step [3][n_elem] and per-element count */
+int or_get_flags(const or_ctx *c, uint8_t *last, int32_t *count);
+int or_get_temperature(const or_ctx *c, double *T);
+/* one synchronous right-hand side L(w) (Eq. 5), no delays */
+int or_rhs_sync(const or_cfg *cfg, const or_mech *m, const double *w, double *rhs);
+int or_reactor0d(const or_mech *m, double *r, double rhoe, double dt, int n_steps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
