@@ -1,0 +1,171 @@
+/* adg.h — C ABI of the GB300 library for the asynchronous discontinuous Galerkin
+ * (ADG) right-hand side of the 1D multicomponent reacting Euler equations
+ * (arXiv 2501.01747), with PE boundaries emulated on one GPU.
+ *
+ * The operation every call serves is one explicit time step of the semi-discrete
+ * DG system, Eq. (5) of Sec. 3.1:
+ *     dw_i/dt = (2i+1)/dx [ int f(w) P_i' - fhat_{e+1} + (-1)^i fhat_e ] + proj_i(s),
+ * advanced with three SSP-RK3 stages, where fhat is the local Lax-Friedrichs or
+ * HLLC flux (Sec. 3.1), replaced at PE faces by the asynchrony-tolerant flux of
+ * Eq. (7) at a common delayed level (Sec. 3.2), and every stage is followed by the
+ * troubled-cell indicator and (AT-)WENO limiter of Sec. 3.3 (Eq. 9-11). Delays are
+ * CAA (Sec. 4.1) or SAA (Sec. 4.2) draws, one per PE face per step.
+ *
+ * Conventions for every function:
+ *  - return 0 (ADG_OK) on success, a negative ADG_ERR_* code otherwise;
+ *    adg_error_string() names it. No function aborts the process.
+ *  - state arrays are FP64 modal Legendre coefficients in the layout
+ *    [nv][n_elem][p+1], nv = n_species + 2, variable 0 = rho*u, 1 = rho*E,
+ *    2+i = rho*Y_i (the density is the sum of the partial densities).
+ *  - pointers named *_host are host memory owned by the caller and only read or
+ *    written during the call; pointers named *_dev are device memory owned by the
+ *    caller. The context owns every buffer it allocated.
+ *  - all work is enqueued on the CUDA stream passed to adg_step (0 = legacy
+ *    default stream); the get/set functions synchronise that stream.
+ */
+#ifndef ADG_H
+#define ADG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADG_OK 0
+#define ADG_ERR_ARG -1          /* invalid argument or configuration */
+#define ADG_ERR_CUDA -2         /* a CUDA runtime call failed */
+#define ADG_ERR_NOMEM -3        /* device allocation failed or workspace too small */
+#define ADG_ERR_NONPHYSICAL -4  /* density, temperature or state not finite/positive */
+#define ADG_ERR_HISTORY -5      /* a delayed level is missing from the history ring */
+#define ADG_ERR_NOLIB -6        /* no CUDA device is available */
+
+#define ADG_BC_PERIODIC 0
+#define ADG_BC_REFLECT 1
+#define ADG_BC_OUTFLOW 2
+#define ADG_FLUX_LF 0
+#define ADG_FLUX_HLLC 1
+#define ADG_LIM_NONE 0
+#define ADG_LIM_WENO 1
+#define ADG_SYNC 0
+#define ADG_CAA 1
+#define ADG_SAA 2
+#define ADG_FP64 0
+#define ADG_MIXED 1
+
+#define ADG_MAX_P 4        /* polynomial degree 1..4 */
+#define ADG_MAX_SPECIES 60
+#define ADG_MAX_DELAY 7
+#define ADG_MAX_AT_ORDER 6
+
+/* Mechanism (Sec. 2, Eq. 1-2: source W_i omega_i). Constant-c_p species;
+ * reversible reactions with k_f = A T^b exp(-E_a/(R T)) and k_r = k_f / K_c. */
+typedef struct {
+  int n_species, n_reactions;
+  const double *W;                  /* [n_species] kg/mol */
+  const double *cp;                 /* [n_species] J/mol/K */
+  const double *h_f;                /* [n_species] J/mol at 298.15 K */
+  const double *s0;                 /* [n_species] J/mol/K at 298.15 K, 1 atm */
+  const signed char *nu_f, *nu_r;   /* [n_reactions][n_species] >= 0 */
+  const double *A, *b, *Ea;         /* [n_reactions] SI, -, J/mol */
+} adg_mechanism;
+
+/* One instance (one 1D domain [x0, x0+length] cut into n_pe PEs). */
+typedef struct {
+  int n_elem, p, n_pe;
+  double x0, length, dt;
+  int bc_left, bc_right;   /* ADG_BC_*; periodic must be on both sides */
+  int flux;                /* ADG_FLUX_* */
+  int limiter;             /* ADG_LIM_* (AT-WENO at delayed PE faces) */
+  int at_order;            /* 1..ADG_MAX_AT_ORDER; p+1 keeps the design order */
+  int delay_mode;          /* ADG_SYNC | ADG_CAA | ADG_SAA */
+  int max_delay;           /* 0..ADG_MAX_DELAY */
+  const double *delay_probs; /* host [max_delay+1], SAA only (may be NULL otherwise) */
+  uint64_t seed;           /* SAA delay seed */
+  double tvb_M;            /* TVB constant of the indicator (0 = TVD) */
+} adg_config;
+
+typedef struct adg_ctx adg_ctx;
+
+/* Bytes of device memory adg_create needs for these instances (ring buffers,
+ * state and stage buffers, flags, tables). Sec. 3.2 (history of delayed levels). */
+int adg_workspace_bytes(const adg_mechanism *mech, const adg_config *cfgs, int n_instances,
+                        size_t *bytes);
+
+/* Create a context. workspace_dev: NULL lets the library cudaMalloc what it needs;
+ * otherwise a caller-owned device buffer of at least adg_workspace_bytes bytes,
+ * 256-byte aligned, that must outlive the context. The mechanism and configs are
+ * copied. Errors: ADG_ERR_ARG (unsupported p, species count, delay, order, or a
+ * reaction with more than 4 species on one side), ADG_ERR_NOMEM, ADG_ERR_CUDA. */
+int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n_instances,
+               void *workspace_dev, size_t workspace_bytes, adg_ctx **out);
+void adg_destroy(adg_ctx *ctx);
+
+/* Initial condition from primitive values at the p+1 Gauss-Legendre points of
+ * every element: prim_host layout [n_species+3][n_elem][p+1] with rows T (K),
+ * P (Pa), u (m/s), Y_1..Y_ns. L2-projects the conserved variables onto the modal
+ * basis (Sec. 3.1) on the device, and resets the step counter and history. */
+int adg_set_primitive(adg_ctx *ctx, int instance, const double *prim_host);
+
+/* Copy a modal state in (host or device memory) and reset counter and history. */
+int adg_set_state(adg_ctx *ctx, int instance, const double *w_host);
+int adg_set_state_device(adg_ctx *ctx, int instance, const double *w_dev, void *stream);
+
+/* Overwrite the current state of a running instance from host memory,
+ * asynchronously on `stream`, keeping the step counter and the history ring (a
+ * restart of a continuing run). w_host should be pinned for a true async copy
+ * and must stay valid until the stream reaches the copy. */
+int adg_write_state(adg_ctx *ctx, int instance, const double *w_host, void *stream);
+
+/* Read the current state into host memory asynchronously on `stream` (no
+ * synchronisation; the data is valid once the stream has passed the copy). */
+int adg_read_state(adg_ctx *ctx, int instance, double *w_host, void *stream);
+
+/* Copy the current modal state out (synchronises the context's last stream). */
+int adg_get_state(adg_ctx *ctx, int instance, double *w_host);
+int adg_get_state_device(adg_ctx *ctx, int instance, double *w_dev, void *stream);
+
+/* Advance every instance by n_steps SSP-RK3 steps on `stream` (a cudaStream_t;
+ * NULL = default stream). Asynchronous: returns after enqueueing. Errors found
+ * on the device are reported by adg_status. */
+int adg_step(adg_ctx *ctx, int n_steps, void *stream);
+
+/* Synchronise and report the first device-side error since the last reset
+ * (ADG_ERR_NONPHYSICAL or ADG_ERR_HISTORY), with the instance, element, step and
+ * stage where it happened (any pointer may be NULL); clears it. */
+int adg_status(adg_ctx *ctx, int *instance, int *element, int64_t *step, int *stage);
+
+/* Troubled-cell flags of the three stages of the last step ([3][n_elem] bytes)
+ * and per-element counts of flagged stages since the last set ([n_elem] int32). */
+int adg_get_flags(adg_ctx *ctx, int instance, uint8_t *last_host, int32_t *count_host);
+
+/* Temperature at the Gauss points of the current state, [n_elem][p+1]. */
+int adg_get_temperature(adg_ctx *ctx, int instance, double *T_host);
+
+int64_t adg_steps_done(const adg_ctx *ctx, int instance);
+
+/* Delays the context draws (Sec. 4.1 CAA: k = n mod (max_delay+1); Sec. 4.2 SAA:
+ * SplitMix64 of seed ^ (step << 32 + face), top 53 bits, matched to the bins of
+ * the cumulative probabilities), for steps [step0, step0+n_steps) and every PE
+ * face: out_host [n_steps][n_pe_faces] bytes. n_pe_faces = n_pe (periodic) or
+ * n_pe - 1 (bounded), 0 when n_pe == 1. */
+int adg_delay_table(const adg_config *cfg, int64_t step0, int n_steps, uint8_t *out_host);
+
+/* Per-kernel timing with CUDA events recorded around every launch on the
+ * launching stream (on = 1 starts a new measurement). adg_kernel_times
+ * synchronises and returns, per kernel kind (0: stage RHS/update kernel,
+ * 1: limiter kernel), the summed milliseconds and launch counts since
+ * enabling; ms and launches point to arrays of 2. */
+int adg_enable_kernel_timing(adg_ctx *ctx, int on);
+int adg_kernel_times(adg_ctx *ctx, double *ms, int64_t *launches);
+
+/* Number of kernel launches one adg_step(ctx, 1, ...) enqueues. */
+int adg_launches_per_step(const adg_ctx *ctx);
+
+const char *adg_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,319 @@
+"""Python binding of the CUDA library (include/adg.h): argument marshalling only.
+
+Every step of the method runs in the CUDA kernels of ``csrc/``; this module builds
+the shared library, converts numpy inputs to the C structs, hands PyTorch-owned
+device memory and the current PyTorch stream to the library, and raises on error
+codes. There is no CPU fallback: without the built library or a GPU every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "libadg.so")
+SOURCES = ["adg_kernels.cu", "adg_api.cu"]
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", ARCH]
+
+ADG_OK = 0
+ERRORS = {-1: "ADG_ERR_ARG", -2: "ADG_ERR_CUDA", -3: "ADG_ERR_NOMEM",
+          -4: "ADG_ERR_NONPHYSICAL", -5: "ADG_ERR_HISTORY", -6: "ADG_ERR_NOLIB"}
+
+
+class AdgError(RuntimeError):
+    def __init__(self, code, what=""):
+        msg = "%s (%d)" % (ERRORS.get(code, "unknown"), code)
+        try:
+            msg += ": " + lib().adg_error_string(code).decode()
+        except Exception:  # pragma: no cover
+            pass
+        super().__init__((what + ": " if what else "") + msg)
+        self.code = code
+
+
+def _nvcc():
+    cand = [os.environ.get("NVCC", ""), "/usr/local/cuda/bin/nvcc", "nvcc"]
+    for c in cand:
+        if c and (os.path.isabs(c) and os.path.exists(c) or not os.path.isabs(c)):
+            return c
+    return "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile csrc/*.cu for sm_103a into _build/libadg.so (objects in parallel)."""
+    os.makedirs(BUILD, exist_ok=True)
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    deps.append(os.path.join(os.path.dirname(HERE), "include", "adg.h"))
+    newest = max(os.path.getmtime(d) for d in deps)
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
+        return LIB
+    nvcc = _nvcc()
+    objs = []
+
+    def compile_one(src):
+        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        cmd = [nvcc, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.check_call(cmd)
+        return obj
+
+    with ThreadPoolExecutor(len(SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = LIB + ".tmp%d" % os.getpid()
+    subprocess.check_call([nvcc, ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class Mechanism_(C.Structure):
+    _fields_ = [("n_species", C.c_int), ("n_reactions", C.c_int),
+                ("W", C.POINTER(C.c_double)), ("cp", C.POINTER(C.c_double)),
+                ("h_f", C.POINTER(C.c_double)), ("s0", C.POINTER(C.c_double)),
+                ("nu_f", C.POINTER(C.c_byte)), ("nu_r", C.POINTER(C.c_byte)),
+                ("A", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)),
+                ("Ea", C.POINTER(C.c_double))]
+
+
+class Config_(C.Structure):
+    _fields_ = [("n_elem", C.c_int), ("p", C.c_int), ("n_pe", C.c_int),
+                ("x0", C.c_double), ("length", C.c_double), ("dt", C.c_double),
+                ("bc_left", C.c_int), ("bc_right", C.c_int), ("flux", C.c_int),
+                ("limiter", C.c_int), ("at_order", C.c_int), ("delay_mode", C.c_int),
+                ("max_delay", C.c_int), ("delay_probs", C.POINTER(C.c_double)),
+                ("seed", C.c_uint64), ("tvb_M", C.c_double)]
+
+
+_lib = None
+EXPORTS = ["adg_workspace_bytes", "adg_create", "adg_destroy", "adg_set_primitive",
+           "adg_set_state", "adg_set_state_device", "adg_get_state", "adg_get_state_device",
+           "adg_step", "adg_status", "adg_get_flags", "adg_get_temperature", "adg_steps_done",
+           "adg_delay_table", "adg_launches_per_step", "adg_error_string",
+           "adg_write_state", "adg_read_state", "adg_enable_kernel_timing",
+           "adg_kernel_times"]
+
+
+def lib(path: str | None = None):
+    """Load the library (building it first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or build()
+    L = C.CDLL(path)
+    vp, d = C.c_void_p, C.POINTER(C.c_double)
+    L.adg_workspace_bytes.argtypes = [C.POINTER(Mechanism_), C.POINTER(Config_), C.c_int,
+                                      C.POINTER(C.c_size_t)]
+    L.adg_create.argtypes = [C.POINTER(Mechanism_), C.POINTER(Config_), C.c_int, vp,
+                             C.c_size_t, C.POINTER(vp)]
+    L.adg_destroy.argtypes = [vp]
+    L.adg_destroy.restype = None
+    L.adg_set_primitive.argtypes = [vp, C.c_int, d]
+    L.adg_set_state.argtypes = [vp, C.c_int, d]
+    L.adg_set_state_device.argtypes = [vp, C.c_int, vp, vp]
+    L.adg_get_state.argtypes = [vp, C.c_int, d]
+    L.adg_get_state_device.argtypes = [vp, C.c_int, vp, vp]
+    L.adg_step.argtypes = [vp, C.c_int, vp]
+    L.adg_status.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                             C.POINTER(C.c_int64), C.POINTER(C.c_int)]
+    L.adg_get_flags.argtypes = [vp, C.c_int, C.POINTER(C.c_uint8), C.POINTER(C.c_int32)]
+    L.adg_get_temperature.argtypes = [vp, C.c_int, d]
+    L.adg_steps_done.argtypes = [vp, C.c_int]
+    L.adg_steps_done.restype = C.c_int64
+    L.adg_delay_table.argtypes = [C.POINTER(Config_), C.c_int64, C.c_int, C.POINTER(C.c_uint8)]
+    L.adg_launches_per_step.argtypes = [vp]
+    L.adg_write_state.argtypes = [vp, C.c_int, d, vp]
+    L.adg_read_state.argtypes = [vp, C.c_int, d, vp]
+    L.adg_enable_kernel_timing.argtypes = [vp, C.c_int]
+    L.adg_kernel_times.argtypes = [vp, d, C.POINTER(C.c_int64)]
+    L.adg_error_string.restype = C.c_char_p
+    L.adg_error_string.argtypes = [C.c_int]
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(rc, what=""):
+    if rc != ADG_OK:
+        raise AdgError(rc, what)
+
+
+class _MechArgs:
+    def __init__(self, mech):
+        self.keep = [np.ascontiguousarray(x, dtype=np.float64) for x in
+                     (mech.W, mech.cp, mech.h_f, mech.s0, mech.A, mech.b, mech.Ea)]
+        self.nu_f = np.ascontiguousarray(mech.nu_f, dtype=np.int8)
+        self.nu_r = np.ascontiguousarray(mech.nu_r, dtype=np.int8)
+        W, cp, hf, s0, A, b, Ea = self.keep
+        self.s = Mechanism_(W.shape[0], A.shape[0], _dp(W), _dp(cp), _dp(hf), _dp(s0),
+                            self.nu_f.ctypes.data_as(C.POINTER(C.c_byte)),
+                            self.nu_r.ctypes.data_as(C.POINTER(C.c_byte)),
+                            _dp(A), _dp(b), _dp(Ea))
+
+
+def config_struct(wl):
+    probs = np.ascontiguousarray(np.array(wl.delay_probs or [1.0], dtype=np.float64))
+    c = Config_(wl.n_elem, wl.p, wl.n_pe, wl.x0, wl.length, wl.dt, wl.bc_left, wl.bc_right,
+                wl.flux, wl.limiter, wl.at_order, wl.delay_mode, wl.max_delay, _dp(probs),
+                wl.seed & ((1 << 64) - 1), wl.tvb_M)
+    return c, probs
+
+
+def delay_table(wl, step0, n_steps):
+    """Delays [n_steps][n_pe_faces] as the library draws them."""
+    cfg, probs = config_struct(wl)
+    npf = 0 if wl.n_pe <= 1 else (wl.n_pe if wl.bc_left == 0 else wl.n_pe - 1)
+    out = np.zeros((n_steps, max(npf, 0)), dtype=np.uint8)
+    _check(lib().adg_delay_table(C.byref(cfg), int(step0), int(n_steps),
+                                 out.ctypes.data_as(C.POINTER(C.c_uint8))), "adg_delay_table")
+    return out
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class ADG:
+    """A context of one or more instances sharing one mechanism.
+
+    Device memory is one PyTorch uint8 tensor handed to ``adg_create`` (the
+    library carves its buffers out of it); kernels run on PyTorch's current CUDA
+    stream unless a stream is given."""
+
+    def __init__(self, mech, workloads, device=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise AdgError(-6, "ADG needs a CUDA device")
+        self.L = lib()
+        self.workloads = list(workloads)
+        self._m = _MechArgs(mech)
+        self.ns = int(self._m.keep[0].shape[0])
+        self.nv = self.ns + 2
+        cfgs = [config_struct(w) for w in self.workloads]
+        self._probs = [c[1] for c in cfgs]
+        arr = (Config_ * len(cfgs))(*[c[0] for c in cfgs])
+        self._cfgs = arr
+        nbytes = C.c_size_t(0)
+        _check(self.L.adg_workspace_bytes(C.byref(self._m.s), arr, len(cfgs), C.byref(nbytes)),
+               "adg_workspace_bytes")
+        self.device = torch.device(device or "cuda")
+        self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8,
+                                     device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        h = C.c_void_p(0)
+        _check(self.L.adg_create(C.byref(self._m.s), arr, len(cfgs), C.c_void_p(aligned),
+                                 C.c_size_t(int(nbytes.value)), C.byref(h)), "adg_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.adg_destroy(self.h)
+            self.h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _k(self, k):
+        if not (0 <= int(k) < len(self.workloads)):
+            raise AdgError(-1, "instance %r out of range" % (k,))
+        return int(k)
+
+    def shape(self, k=0):
+        wl = self.workloads[self._k(k)]
+        return (self.nv, wl.n_elem, wl.p + 1)
+
+    def _stream(self, stream):
+        if stream is None:
+            return C.c_void_p(_torch().cuda.current_stream(self.device).cuda_stream)
+        if hasattr(stream, "cuda_stream"):
+            return C.c_void_p(stream.cuda_stream)
+        return C.c_void_p(int(stream))
+
+    def set_primitive(self, prim, k=0):
+        prim = np.ascontiguousarray(prim, dtype=np.float64)
+        _check(self.L.adg_set_primitive(self.h, k, _dp(prim)), "adg_set_primitive")
+
+    def set_state(self, w, k=0):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        _check(self.L.adg_set_state(self.h, k, _dp(w)), "adg_set_state")
+
+    def set_state_device(self, w_dev, k=0, stream=None):
+        _check(self.L.adg_set_state_device(self.h, k, C.c_void_p(w_dev.data_ptr()),
+                                           self._stream(stream)), "adg_set_state_device")
+
+    def get_state(self, k=0, out=None):
+        w = out if out is not None else np.zeros(self.shape(k))
+        _check(self.L.adg_get_state(self.h, k, _dp(w)), "adg_get_state")
+        return w
+
+    def get_state_device(self, w_dev, k=0, stream=None):
+        _check(self.L.adg_get_state_device(self.h, k, C.c_void_p(w_dev.data_ptr()),
+                                           self._stream(stream)), "adg_get_state_device")
+
+    def step(self, n=1, stream=None):
+        _check(self.L.adg_step(self.h, int(n), self._stream(stream)), "adg_step")
+
+    def status(self):
+        inst, el, st, sg = C.c_int(-1), C.c_int(-1), C.c_int64(-1), C.c_int(-1)
+        rc = self.L.adg_status(self.h, C.byref(inst), C.byref(el), C.byref(st), C.byref(sg))
+        return rc, (inst.value, el.value, st.value, sg.value)
+
+    def check(self):
+        rc, where = self.status()
+        if rc != ADG_OK:
+            raise AdgError(rc, "device error at instance/element/step/stage %s" % (where,))
+
+    def flags(self, k=0):
+        n = self.workloads[self._k(k)].n_elem
+        last = np.zeros((3, n), dtype=np.uint8)
+        cnt = np.zeros(n, dtype=np.int32)
+        _check(self.L.adg_get_flags(self.h, k, last.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                    cnt.ctypes.data_as(C.POINTER(C.c_int32))), "adg_get_flags")
+        return last, cnt
+
+    def temperature(self, k=0):
+        wl = self.workloads[self._k(k)]
+        T = np.zeros((wl.n_elem, wl.p + 1))
+        _check(self.L.adg_get_temperature(self.h, k, _dp(T)), "adg_get_temperature")
+        return T
+
+    def steps_done(self, k=0):
+        return int(self.L.adg_steps_done(self.h, k))
+
+    def write_state(self, w_host, k=0, stream=None):
+        """Async H2D overwrite of the running state (history kept)."""
+        _check(self.L.adg_write_state(self.h, k, _dp(w_host), self._stream(stream)),
+               "adg_write_state")
+
+    def read_state(self, w_host, k=0, stream=None):
+        """Async D2H read of the state (valid after the stream passes it)."""
+        _check(self.L.adg_read_state(self.h, k, _dp(w_host), self._stream(stream)),
+               "adg_read_state")
+
+    def enable_kernel_timing(self, on=True):
+        _check(self.L.adg_enable_kernel_timing(self.h, 1 if on else 0), "timing")
+
+    def kernel_times(self):
+        ms = np.zeros(2)
+        n = np.zeros(2, dtype=np.int64)
+        _check(self.L.adg_kernel_times(self.h, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64))),
+               "adg_kernel_times")
+        return ms, n
+
+    def launches_per_step(self):
+        return int(self.L.adg_launches_per_step(self.h))

@@ -1,0 +1,654 @@
+// Host runtime of the ADG library: context, device memory, tables, C ABI.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "adg_internal.cuh"
+#include "adg_math.cuh"
+
+
+using namespace adg;
+
+// ---------------------------------------------------------------------------
+// Basis tables of the modal Legendre DG method (Sec. 3.1) and of the WENO
+// limiter (Sec. 3.3), computed on the host in FP64.
+
+static void legendre_all(int n, double x, double *P) {
+  P[0] = 1.0;
+  if (n >= 1) P[1] = x;
+  for (int j = 1; j < n; ++j) P[j + 1] = ((2 * j + 1) * x * P[j] - j * P[j - 1]) / (j + 1);
+}
+
+// s-th derivatives of P_0..P_n at x by differentiating the three-term recurrence:
+// (j+1) P_{j+1}^(s) = (2j+1) (x P_j^(s) + s P_j^(s-1)) - j P_{j-1}^(s).
+static void legendre_deriv(int n, int s, double x, double *D) {
+  double prev[MAXQ + 1], cur[MAXQ + 1];
+  legendre_all(n, x, prev);
+  for (int d = 1; d <= s; ++d) {
+    cur[0] = 0.0;
+    if (n >= 1) cur[1] = (d == 1) ? 1.0 : 0.0;
+    for (int j = 1; j < n; ++j)
+      cur[j + 1] = ((2 * j + 1) * (x * cur[j] + d * prev[j]) - j * cur[j - 1]) / (j + 1);
+    for (int j = 0; j <= n; ++j) prev[j] = cur[j];
+  }
+  for (int j = 0; j <= n; ++j) D[j] = prev[j];
+}
+
+static void gauss_points(int Q, double *x, double *w) {
+  double P[MAXQ + 2], D[MAXQ + 2];
+  for (int i = 0; i < Q; ++i) {
+    double t = -cos(M_PI * (2 * i + 1) / (2.0 * Q));
+    for (int it = 0; it < 200; ++it) {
+      legendre_all(Q, t, P);
+      legendre_deriv(Q, 1, t, D);
+      double d = P[Q] / D[Q];
+      t -= d;
+      if (fabs(d) <= 1e-17) break;
+    }
+    legendre_deriv(Q, 1, t, D);
+    x[i] = t;
+    w[i] = 2.0 / ((1.0 - t * t) * D[Q] * D[Q]);
+  }
+}
+
+static void make_basis(int p, Basis *B) {
+  int Q = p + 1;
+  memset(B, 0, sizeof(Basis));
+  gauss_points(Q, B->x, B->w);
+  for (int q = 0; q < Q; ++q) {
+    double P[MAXQ + 1], D[MAXQ + 1];
+    legendre_all(p, B->x[q], P);
+    legendre_deriv(p, 1, B->x[q], D);
+    for (int j = 0; j < Q; ++j) {
+      B->P[q][j] = P[j];
+      B->dP[q][j] = D[j];
+    }
+  }
+  // beta = sum_s 2^(2s-1) int (d^s v/dxi^s)^2: Gauss rule with Q points is exact
+  for (int s = 1; s <= p; ++s) {
+    for (int q = 0; q < Q; ++q) {
+      double D[MAXQ + 1];
+      legendre_deriv(p, s, B->x[q], D);
+      for (int i = 0; i < Q; ++i)
+        for (int j = 0; j < Q; ++j) B->B[i][j] += ldexp(1.0, 2 * s - 1) * B->w[q] * D[i] * D[j];
+    }
+  }
+  // neighbour polynomials continued into the cell: left uses xi' = xi + 2
+  for (int q = 0; q < Q; ++q) {
+    double Pl[MAXQ + 1], Pr[MAXQ + 1], P[MAXQ + 1];
+    legendre_all(p, B->x[q] + 2.0, Pl);
+    legendre_all(p, B->x[q] - 2.0, Pr);
+    legendre_all(p, B->x[q], P);
+    for (int i = 0; i < Q; ++i)
+      for (int j = 0; j < Q; ++j) {
+        B->Sl[i][j] += 0.5 * (2 * i + 1) * B->w[q] * Pl[j] * P[i];
+        B->Sr[i][j] += 0.5 * (2 * i + 1) * B->w[q] * Pr[j] * P[i];
+      }
+  }
+}
+
+// AT weights (Eq. 7-8): extrapolation to t_n from levels t_n - (k+m) dt.
+static void at_weights(int order, int k, double *c) {
+  for (int m = 0; m < order; ++m) {
+    double v = 1.0;
+    for (int j = 0; j < order; ++j)
+      if (j != m) v *= (double)(k + j) / (double)(j - m);
+    c[m] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+
+struct InstHost {
+  Inst d;         // device view
+  int64_t n;      // steps done
+  int TE;
+  double *prim;   // staging for projection / temperature
+};
+
+struct adg_ctx {
+  std::vector<cudaEvent_t> ev;   // timing events, pairs per launch
+  std::vector<int> ev_kind;
+  size_t ev_used;
+  bool timing;
+  int n_inst;
+  int ns, nr;
+  Mech mech;
+  std::vector<InstHost> inst;
+  void *mem;
+  bool owns_mem;
+  size_t bytes;
+  int *err_all;   // device error words [n_inst][4]
+  cudaStream_t last_stream;
+};
+
+namespace {
+
+struct Carver {
+  char *base;
+  size_t off, cap;
+  bool dry;
+  void *take(size_t n) {
+    off = (off + 255) & ~(size_t)255;
+    void *p = dry ? nullptr : base + off;
+    off += n;
+    return p;
+  }
+};
+
+int check_args(const adg_mechanism *m, const adg_config *cfgs, int n) {
+  if (!m || !cfgs || n < 1) return ADG_ERR_ARG;
+  if (m->n_species < 1 || m->n_species > ADG_MAX_SPECIES || m->n_reactions < 0) return ADG_ERR_ARG;
+  if (!m->W || !m->cp || !m->h_f || !m->s0) return ADG_ERR_ARG;
+  if (m->n_reactions > 0 && (!m->nu_f || !m->nu_r || !m->A || !m->b || !m->Ea)) return ADG_ERR_ARG;
+  for (int i = 0; i < m->n_species; ++i)
+    if (!(m->W[i] > 0.0) || !(m->cp[i] > RU)) return ADG_ERR_ARG;
+  for (int j = 0; j < m->n_reactions; ++j) {
+    int nf = 0, nr = 0, nx = 0;
+    for (int i = 0; i < m->n_species; ++i) {
+      int a = m->nu_f[j * m->n_species + i], b = m->nu_r[j * m->n_species + i];
+      if (a < 0 || b < 0 || a > 2 || b > 2) return ADG_ERR_ARG;
+      nf += a > 0;
+      nr += b > 0;
+      nx += (b - a) != 0;
+    }
+    if (nf > SIDE || nr > SIDE || nx > NET) return ADG_ERR_ARG;
+    if (!(m->A[j] > 0.0)) return ADG_ERR_ARG;
+  }
+  for (int k = 0; k < n; ++k) {
+    const adg_config &c = cfgs[k];
+    if (c.p < 1 || c.p > ADG_MAX_P || c.n_elem < 1 || c.n_pe < 1 || c.n_pe > c.n_elem)
+      return ADG_ERR_ARG;
+    if (!(c.length > 0.0) || !(c.dt > 0.0)) return ADG_ERR_ARG;
+    if (c.at_order < 1 || c.at_order > ADG_MAX_AT_ORDER) return ADG_ERR_ARG;
+    if (c.max_delay < 0 || c.max_delay > ADG_MAX_DELAY) return ADG_ERR_ARG;
+    if (c.delay_mode < ADG_SYNC || c.delay_mode > ADG_SAA) return ADG_ERR_ARG;
+    if (c.delay_mode == ADG_SAA && !c.delay_probs) return ADG_ERR_ARG;
+    if (c.flux != ADG_FLUX_LF && c.flux != ADG_FLUX_HLLC) return ADG_ERR_ARG;
+    if (c.limiter != ADG_LIM_NONE && c.limiter != ADG_LIM_WENO) return ADG_ERR_ARG;
+    bool lp = c.bc_left == ADG_BC_PERIODIC, rp = c.bc_right == ADG_BC_PERIODIC;
+    if (lp != rp) return ADG_ERR_ARG;
+    if (c.bc_left < 0 || c.bc_left > 2 || c.bc_right < 0 || c.bc_right > 2) return ADG_ERR_ARG;
+    if ((int64_t)c.n_elem * (c.p + 1) * (m->n_species + 3) > (int64_t)1 << 31) return ADG_ERR_ARG;
+  }
+  return ADG_OK;
+}
+
+int n_pe_faces(const adg_config &c) {
+  if (c.n_pe <= 1) return 0;
+  return c.bc_left == ADG_BC_PERIODIC ? c.n_pe : c.n_pe - 1;
+}
+
+// Lay out every buffer; with dry = true only measures.
+size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
+  int ns = ctx->ns, nr = ctx->nr, nv = ns + 2;
+  int nrr = nr > 0 ? nr : 1;
+  Mech &M = ctx->mech;
+  M.sp = (const double *)cv.take(sizeof(double) * SP_NFIELDS * ns);
+  M.rx = (const Rxn *)cv.take(sizeof(Rxn) * nrr);
+  ctx->err_all = (int *)cv.take(sizeof(int) * 4 * ctx->n_inst);
+  for (int k = 0; k < ctx->n_inst; ++k) {
+    const adg_config &c = cfgs[k];
+    InstHost &h = ctx->inst[k];
+    Inst &I = h.d;
+    int N = c.n_elem, Q = c.p + 1, npf = n_pe_faces(c);
+    size_t st = (size_t)nv * N * Q;
+    I.wn = (double *)cv.take(sizeof(double) * st);
+    I.wa = (double *)cv.take(sizeof(double) * st);
+    I.wpre = (double *)cv.take(sizeof(double) * st);
+    size_t rs = (size_t)(c.max_delay + c.at_order) * 3 * (npf > 0 ? npf : 1) * 2 * nv * Q;
+    I.ring_in = (double *)cv.take(sizeof(double) * rs);
+    I.ring_pre = (double *)cv.take(sizeof(double) * rs);
+    I.flags = (uint8_t *)cv.take((size_t)3 * N);
+    I.count = (int32_t *)cv.take(sizeof(int32_t) * N);
+    I.pf_of_left = (const int *)cv.take(sizeof(int) * N);
+    I.pf_of_right = (const int *)cv.take(sizeof(int) * N);
+    I.pf_elem = (const int *)cv.take(sizeof(int) * 2 * (npf > 0 ? npf : 1));
+    h.prim = (double *)cv.take(sizeof(double) * (size_t)(ns + 3) * N * Q);
+    I.err = ctx->err_all ? ctx->err_all + 4 * k : nullptr;
+  }
+  return cv.off;
+}
+
+thread_local char g_last_error[256];
+
+}  // namespace
+
+extern "C" {
+
+const char *adg_error_string(int code) {
+  switch (code) {
+    case ADG_OK: return "ok";
+    case ADG_ERR_ARG: return "invalid argument";
+    case ADG_ERR_CUDA: return g_last_error[0] ? g_last_error : "CUDA error";
+    case ADG_ERR_NOMEM: return "out of device memory or workspace too small";
+    case ADG_ERR_NONPHYSICAL: return "non-physical state (density or temperature)";
+    case ADG_ERR_HISTORY: return "delayed level missing from the history ring";
+    case ADG_ERR_NOLIB: return "no CUDA device";
+  }
+  return "unknown error";
+}
+
+static int cuda_fail(cudaError_t e) {
+  snprintf(g_last_error, sizeof(g_last_error), "CUDA error: %s", cudaGetErrorString(e));
+  return ADG_ERR_CUDA;
+}
+
+#define CK(x)                              \
+  do {                                     \
+    cudaError_t e_ = (x);                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+int adg_workspace_bytes(const adg_mechanism *mech, const adg_config *cfgs, int n, size_t *bytes) {
+  int rc = check_args(mech, cfgs, n);
+  if (rc) return rc;
+  if (!bytes) return ADG_ERR_ARG;
+  adg_ctx tmp;
+  tmp.n_inst = n;
+  tmp.ns = mech->n_species;
+  tmp.nr = mech->n_reactions;
+  tmp.inst.resize(n);
+  tmp.err_all = nullptr;
+  Carver cv{nullptr, 0, 0, true};
+  *bytes = layout(&tmp, cfgs, cv) + 256;
+  return ADG_OK;
+}
+
+int adg_delay_table(const adg_config *c, int64_t step0, int n_steps, uint8_t *out) {
+  if (!c || !out || n_steps < 0 || c->max_delay < 0 || c->max_delay > ADG_MAX_DELAY)
+    return ADG_ERR_ARG;
+  if (c->delay_mode == ADG_SAA && !c->delay_probs) return ADG_ERR_ARG;
+  double cum[MAXD + 1];
+  double acc = 0.0;
+  for (int k = 0; k <= c->max_delay; ++k) {
+    acc += (c->delay_mode == ADG_SAA) ? c->delay_probs[k] : 0.0;
+    cum[k] = acc;
+  }
+  int npf = n_pe_faces(*c);
+  for (int s = 0; s < n_steps; ++s)
+    for (int f = 0; f < npf; ++f)
+      out[(size_t)s * npf + f] =
+          (uint8_t)draw_delay(c->delay_mode, c->max_delay, c->seed, cum, step0 + s, f);
+  return ADG_OK;
+}
+
+int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *workspace,
+               size_t ws_bytes, adg_ctx **out) {
+  if (!out) return ADG_ERR_ARG;
+  *out = nullptr;
+  int rc = check_args(mech, cfgs, n);
+  if (rc) return rc;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return ADG_ERR_NOLIB;
+  adg_ctx *ctx = new (std::nothrow) adg_ctx();
+  if (!ctx) return ADG_ERR_NOMEM;
+  ctx->n_inst = n;
+  ctx->ns = mech->n_species;
+  ctx->nr = mech->n_reactions;
+  ctx->inst.resize(n);
+  ctx->last_stream = 0;
+  ctx->err_all = nullptr;
+  ctx->ev_used = 0;
+  ctx->timing = false;
+  Carver dry{nullptr, 0, 0, true};
+  size_t need = layout(ctx, cfgs, dry) + 256;
+  if (workspace) {
+    if (ws_bytes < need || ((uintptr_t)workspace & 255)) {
+      delete ctx;
+      return ADG_ERR_NOMEM;
+    }
+    ctx->mem = workspace;
+    ctx->owns_mem = false;
+  } else {
+    if (cudaMalloc(&ctx->mem, need) != cudaSuccess) {
+      cudaGetLastError();
+      delete ctx;
+      return ADG_ERR_NOMEM;
+    }
+    ctx->owns_mem = true;
+  }
+  ctx->bytes = need;
+  Carver cv{(char *)ctx->mem, 0, need, false};
+  layout(ctx, cfgs, cv);
+  int ns = ctx->ns, nr = ctx->nr, nv = ns + 2;
+  Mech &M = ctx->mech;
+  M.ns = ns;
+  M.nr = nr;
+  // mechanism tables: species fields and packed reactions
+  std::vector<double> sp(SP_NFIELDS * ns);
+  for (int i = 0; i < ns; ++i) {
+    double W = mech->W[i], cp = mech->cp[i], hf = mech->h_f[i], s0 = mech->s0[i];
+    sp[SP_W * ns + i] = W;
+    sp[SP_INVW * ns + i] = 1.0 / W;
+    sp[SP_QW * ns + i] = (hf - cp * TREF) / W;
+    sp[SP_CVW * ns + i] = (cp - RU) / W;
+    sp[SP_RW * ns + i] = RU / W;
+    sp[SP_CPW * ns + i] = cp / W;
+    sp[SP_G0 * ns + i] = (hf - cp * TREF) / RU;
+    sp[SP_G1 * ns + i] = cp / RU * (1.0 + log(TREF)) - s0 / RU;
+    sp[SP_CPR * ns + i] = cp / RU;
+  }
+  int rc2 = ADG_OK;
+  if (cudaMemcpy((void *)M.sp, sp.data(), sizeof(double) * sp.size(), cudaMemcpyHostToDevice))
+    rc2 = ADG_ERR_CUDA;
+  std::vector<Rxn> rx(nr > 0 ? nr : 1);
+  memset(rx.data(), 0, sizeof(Rxn) * rx.size());
+  for (int j = 0; j < nr; ++j) {
+    Rxn &R = rx[j];
+    R.lnA = log(mech->A[j]);
+    R.b = mech->b[j];
+    R.EaR = mech->Ea[j] / RU;
+    int a = 0, b = 0, x = 0, dnu = 0;
+    for (int i = 0; i < ns; ++i) {
+      int f = mech->nu_f[j * ns + i], r = mech->nu_r[j * ns + i];
+      if (f > 0) { R.rs[a] = (uint8_t)i; R.rn[a] = (uint8_t)f; ++a; }
+      if (r > 0) { R.ps[b] = (uint8_t)i; R.pn[b] = (uint8_t)r; ++b; }
+      if (r - f != 0) { R.xs[x] = (uint8_t)i; R.xn[x] = (int8_t)(r - f); ++x; dnu += r - f; }
+    }
+    R.dnu = (double)dnu;
+  }
+  if (nr > 0 &&
+      cudaMemcpy((void *)M.rx, rx.data(), sizeof(Rxn) * nr, cudaMemcpyHostToDevice))
+    rc2 = ADG_ERR_CUDA;
+  // exp table: 2^(j/32) and the split of ln2/32, in extended precision
+  {
+    ExpTable et;
+    for (int j = 0; j < 32; ++j) et.t[j] = (double)exp2l((long double)j / 32.0L);
+    long double l = logl(2.0L) / 32.0L;
+    int ex;
+    long double mant = frexpl(l, &ex);
+    long double hi = ldexpl(floorl(ldexpl(mant, 32)), ex - 32);
+    et.l_hi = (double)hi;
+    et.l_lo = (double)(l - hi);
+    if (upload_exp_table(&et) != cudaSuccess) rc2 = ADG_ERR_CUDA;
+  }
+  if (cudaMemset(ctx->err_all, 0, sizeof(int) * 4 * n)) rc2 = ADG_ERR_CUDA;
+  // basis tables
+  Basis tables[ADG_MAX_P];
+  for (int p = 1; p <= ADG_MAX_P; ++p) make_basis(p, &tables[p - 1]);
+  if (upload_basis(tables) != cudaSuccess) rc2 = ADG_ERR_CUDA;
+  // instances
+  for (int k = 0; k < n && rc2 == ADG_OK; ++k) {
+    const adg_config &c = cfgs[k];
+    InstHost &h = ctx->inst[k];
+    Inst &I = h.d;
+    int N = c.n_elem, Q = c.p + 1, npf = n_pe_faces(c);
+    I.n_elem = N;
+    I.p = c.p;
+    I.nv = nv;
+    I.npf = npf;
+    I.depth = c.max_delay + c.at_order;
+    I.at_order = c.at_order;
+    I.bc_left = c.bc_left;
+    I.bc_right = c.bc_right;
+    I.flux = c.flux;
+    I.limiter = c.limiter;
+    I.delay_mode = c.delay_mode;
+    I.max_delay = c.max_delay;
+    I.dx = c.length / N;
+    I.dt = c.dt;
+    I.tvb = c.tvb_M * I.dx * I.dx;
+    I.seed = c.seed;
+    I.instance = k;
+    double acc = 0.0;
+    for (int d = 0; d <= MAXD; ++d) {
+      if (d <= c.max_delay) acc += (c.delay_mode == ADG_SAA) ? c.delay_probs[d] : 0.0;
+      I.cum[d] = acc;
+    }
+    for (int d = 0; d <= MAXD; ++d) {
+      double w[MAXO];
+      for (int m = 0; m < MAXO; ++m) w[m] = 0.0;
+      if (d <= c.max_delay) at_weights(c.at_order, d, w);
+      for (int m = 0; m < MAXO; ++m) I.at[d][m] = w[m];
+    }
+    // PE partition (Sec. 4): PE q owns elements [q N / P, (q+1) N / P)
+    std::vector<int> pl(N, -1), pr(N, -1), pe(2 * (npf > 0 ? npf : 1), -1);
+    int P = c.n_pe;
+    for (int f = 0; f < npf; ++f) {
+      int right = (int)(((int64_t)((f + 1) % P) * N) / P);
+      int left = (right == 0) ? N - 1 : right - 1;
+      pr[left] = f;
+      pl[right] = f;
+      pe[2 * f] = left;
+      pe[2 * f + 1] = right;
+    }
+    if (cudaMemcpy((void *)I.pf_of_left, pl.data(), sizeof(int) * N, cudaMemcpyHostToDevice) ||
+        cudaMemcpy((void *)I.pf_of_right, pr.data(), sizeof(int) * N, cudaMemcpyHostToDevice) ||
+        cudaMemcpy((void *)I.pf_elem, pe.data(), sizeof(int) * pe.size(), cudaMemcpyHostToDevice) ||
+        cudaMemset(I.flags, 0, (size_t)3 * N) || cudaMemset(I.count, 0, sizeof(int32_t) * N) ||
+        cudaMemset(I.wn, 0, sizeof(double) * (size_t)nv * N * Q))
+      rc2 = ADG_ERR_CUDA;
+    h.n = 0;
+    h.TE = stage_tile(Q, nv, ns, nr);
+    // smaller tiles when the instance would not fill two CTAs per SM
+    int target = (N + 2 * 152 - 1) / (2 * 152);
+    if (target < h.TE) h.TE = target < 4 ? 4 : target;
+  }
+  if (rc2 != ADG_OK) {
+    if (ctx->owns_mem) cudaFree(ctx->mem);
+    delete ctx;
+    return rc2;
+  }
+  *out = ctx;
+  return ADG_OK;
+}
+
+void adg_destroy(adg_ctx *ctx) {
+  if (!ctx) return;
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  if (ctx->owns_mem) cudaFree(ctx->mem);
+  delete ctx;
+}
+
+static int inst_ok(adg_ctx *ctx, int k) {
+  return ctx && k >= 0 && k < ctx->n_inst;
+}
+
+static void reset_history(adg_ctx *ctx, int k) {
+  InstHost &h = ctx->inst[k];
+  h.n = 0;
+  cudaMemset(h.d.count, 0, sizeof(int32_t) * h.d.n_elem);
+  cudaMemset(h.d.flags, 0, (size_t)3 * h.d.n_elem);
+}
+
+int adg_set_primitive(adg_ctx *ctx, int k, const double *prim) {
+  if (!inst_ok(ctx, k) || !prim) return ADG_ERR_ARG;
+  InstHost &h = ctx->inst[k];
+  size_t n = (size_t)(ctx->ns + 3) * h.d.n_elem * (h.d.p + 1);
+  CK(cudaMemcpy(h.prim, prim, sizeof(double) * n, cudaMemcpyHostToDevice));
+  CK(launch_project(ctx->mech, h.d, h.prim, h.d.wn, 0));
+  CK(cudaDeviceSynchronize());
+  reset_history(ctx, k);
+  return ADG_OK;
+}
+
+int adg_set_state(adg_ctx *ctx, int k, const double *w) {
+  if (!inst_ok(ctx, k) || !w) return ADG_ERR_ARG;
+  InstHost &h = ctx->inst[k];
+  size_t n = (size_t)h.d.nv * h.d.n_elem * (h.d.p + 1);
+  CK(cudaMemcpyAsync(h.d.wn, w, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->last_stream));
+  CK(cudaStreamSynchronize(ctx->last_stream));
+  reset_history(ctx, k);
+  return ADG_OK;
+}
+
+int adg_set_state_device(adg_ctx *ctx, int k, const double *w, void *stream) {
+  if (!inst_ok(ctx, k) || !w) return ADG_ERR_ARG;
+  InstHost &h = ctx->inst[k];
+  size_t n = (size_t)h.d.nv * h.d.n_elem * (h.d.p + 1);
+  CK(cudaMemcpyAsync(h.d.wn, w, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                     (cudaStream_t)stream));
+  h.n = 0;
+  CK(cudaMemsetAsync(h.d.count, 0, sizeof(int32_t) * h.d.n_elem, (cudaStream_t)stream));
+  ctx->last_stream = (cudaStream_t)stream;
+  return ADG_OK;
+}
+
+int adg_get_state(adg_ctx *ctx, int k, double *w) {
+  if (!inst_ok(ctx, k) || !w) return ADG_ERR_ARG;
+  InstHost &h = ctx->inst[k];
+  size_t n = (size_t)h.d.nv * h.d.n_elem * (h.d.p + 1);
+  CK(cudaMemcpyAsync(w, h.d.wn, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->last_stream));
+  CK(cudaStreamSynchronize(ctx->last_stream));
+  return ADG_OK;
+}
+
+int adg_get_state_device(adg_ctx *ctx, int k, double *w, void *stream) {
+  if (!inst_ok(ctx, k) || !w) return ADG_ERR_ARG;
+  InstHost &h = ctx->inst[k];
+  size_t n = (size_t)h.d.nv * h.d.n_elem * (h.d.p + 1);
+  CK(cudaMemcpyAsync(w, h.d.wn, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                     (cudaStream_t)stream));
+  return ADG_OK;
+}
+
+// Event pair around one launch when timing is on.
+static cudaError_t timed_begin(adg_ctx *ctx, int kind, cudaStream_t st) {
+  if (!ctx->timing) return cudaSuccess;
+  if (ctx->ev_used + 2 > ctx->ev.size()) {
+    for (int t = 0; t < 256; ++t) {
+      cudaEvent_t e;
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      ctx->ev.push_back(e);
+      ctx->ev_kind.push_back(0);
+    }
+  }
+  ctx->ev_kind[ctx->ev_used] = kind;
+  return cudaEventRecord(ctx->ev[ctx->ev_used], st);
+}
+
+static cudaError_t timed_end(adg_ctx *ctx, cudaStream_t st) {
+  if (!ctx->timing) return cudaSuccess;
+  cudaError_t r = cudaEventRecord(ctx->ev[ctx->ev_used + 1], st);
+  ctx->ev_used += 2;
+  return r;
+}
+
+int adg_step(adg_ctx *ctx, int n_steps, void *stream) {
+  if (!ctx || n_steps < 0) return ADG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  for (int it = 0; it < n_steps; ++it) {
+    for (int k = 0; k < ctx->n_inst; ++k) {
+      InstHost &h = ctx->inst[k];
+      Inst &I = h.d;
+      for (int s = 0; s < 3; ++s) {
+        StageArgs A;
+        A.win = (s == 0) ? I.wn : I.wa;
+        A.w0 = I.wn;
+        A.wout = I.wpre;
+        A.s = s;
+        A.n = h.n;
+        A.TE = h.TE;
+        CK(timed_begin(ctx, 0, st));
+        CK(launch_stage(ctx->mech, I, A, st));
+        CK(timed_end(ctx, st));
+        LimArgs L;
+        L.wpre = I.wpre;
+        L.wout = (s == 2) ? I.wn : I.wa;
+        L.s = s;
+        L.n = h.n;
+        CK(timed_begin(ctx, 1, st));
+        CK(launch_limiter(ctx->mech, I, L, st));
+        CK(timed_end(ctx, st));
+      }
+      h.n += 1;
+    }
+  }
+  return ADG_OK;
+}
+
+int adg_launches_per_step(const adg_ctx *ctx) { return ctx ? 6 * ctx->n_inst : 0; }
+
+int adg_enable_kernel_timing(adg_ctx *ctx, int on) {
+  if (!ctx) return ADG_ERR_ARG;
+  ctx->timing = on != 0;
+  ctx->ev_used = 0;
+  return ADG_OK;
+}
+
+int adg_kernel_times(adg_ctx *ctx, double *ms, int64_t *launches) {
+  if (!ctx || !ms || !launches) return ADG_ERR_ARG;
+  ms[0] = ms[1] = 0.0;
+  launches[0] = launches[1] = 0;
+  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+    CK(cudaEventSynchronize(ctx->ev[i + 1]));
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]));
+    int k = ctx->ev_kind[i];
+    ms[k] += t;
+    launches[k] += 1;
+  }
+  return ADG_OK;
+}
+
+int adg_write_state(adg_ctx *ctx, int k, const double *w, void *stream) {
+  if (!inst_ok(ctx, k) || !w) return ADG_ERR_ARG;
+  InstHost &h = ctx->inst[k];
+  size_t n = (size_t)h.d.nv * h.d.n_elem * (h.d.p + 1);
+  CK(cudaMemcpyAsync(h.d.wn, w, sizeof(double) * n, cudaMemcpyHostToDevice,
+                     (cudaStream_t)stream));
+  ctx->last_stream = (cudaStream_t)stream;
+  return ADG_OK;
+}
+
+int adg_read_state(adg_ctx *ctx, int k, double *w, void *stream) {
+  if (!inst_ok(ctx, k) || !w) return ADG_ERR_ARG;
+  InstHost &h = ctx->inst[k];
+  size_t n = (size_t)h.d.nv * h.d.n_elem * (h.d.p + 1);
+  CK(cudaMemcpyAsync(w, h.d.wn, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                     (cudaStream_t)stream));
+  ctx->last_stream = (cudaStream_t)stream;
+  return ADG_OK;
+}
+
+int64_t adg_steps_done(const adg_ctx *ctx, int k) {
+  if (!ctx || k < 0 || k >= ctx->n_inst) return -1;
+  return ctx->inst[k].n;
+}
+
+int adg_status(adg_ctx *ctx, int *instance, int *element, int64_t *step, int *stage) {
+  if (!ctx) return ADG_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->last_stream));
+  std::vector<int> h(4 * ctx->n_inst);
+  CK(cudaMemcpy(h.data(), ctx->err_all, sizeof(int) * h.size(), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < ctx->n_inst; ++k) {
+    if (h[4 * k] != 0) {
+      if (instance) *instance = k;
+      if (element) *element = h[4 * k + 1];
+      if (stage) *stage = h[4 * k + 2];
+      if (step) *step = h[4 * k + 3];
+      int code = h[4 * k];
+      CK(cudaMemset(ctx->err_all, 0, sizeof(int) * h.size()));
+      return code;
+    }
+  }
+  return ADG_OK;
+}
+
+int adg_get_flags(adg_ctx *ctx, int k, uint8_t *last, int32_t *count) {
+  if (!inst_ok(ctx, k)) return ADG_ERR_ARG;
+  InstHost &h = ctx->inst[k];
+  CK(cudaStreamSynchronize(ctx->last_stream));
+  if (last) CK(cudaMemcpy(last, h.d.flags, (size_t)3 * h.d.n_elem, cudaMemcpyDeviceToHost));
+  if (count)
+    CK(cudaMemcpy(count, h.d.count, sizeof(int32_t) * h.d.n_elem, cudaMemcpyDeviceToHost));
+  return ADG_OK;
+}
+
+int adg_get_temperature(adg_ctx *ctx, int k, double *T) {
+  if (!inst_ok(ctx, k) || !T) return ADG_ERR_ARG;
+  InstHost &h = ctx->inst[k];
+  CK(cudaStreamSynchronize(ctx->last_stream));
+  CK(launch_temperature(ctx->mech, h.d, h.d.wn, h.prim, 0));
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(T, h.prim, sizeof(double) * h.d.n_elem * (h.d.p + 1), cudaMemcpyDeviceToHost));
+  return ADG_OK;
+}
+
+}  // extern "C"

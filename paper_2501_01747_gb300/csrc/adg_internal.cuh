@@ -1,0 +1,231 @@
+// Device-side data structures and physics of the ADG hot path.
+//
+// Layout in HBM (per instance): modal state [nv][n_elem][p+1] FP64, SoA by
+// variable, so that a tile of consecutive elements of one variable is one
+// contiguous span; history ring [depth][3 stages][PE faces][2 sides][nv][p+1].
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/adg.h"
+
+namespace adg {
+
+constexpr double RU = 8.314462618;   // J/mol/K
+constexpr double TREF = 298.15;      // K
+constexpr double PATM = 101325.0;    // Pa
+constexpr int MAXQ = ADG_MAX_P + 1;
+constexpr int MAXO = ADG_MAX_AT_ORDER;
+constexpr int MAXD = ADG_MAX_DELAY;
+constexpr int SIDE = 4;              // species slots per reaction side
+constexpr int NET = 8;               // species slots of the net stoichiometry
+
+// Species data (structure of arrays, field f of species i at sp[f * ns + i]).
+enum SpeciesField {
+  SP_W = 0,     // kg/mol
+  SP_INVW,      // 1/W
+  SP_QW,        // (h_f - c_p T_ref)/W   : e_i(T) = qW_i + cvW_i T
+  SP_CVW,       // (c_p - R)/W
+  SP_RW,        // R/W
+  SP_CPW,       // c_p/W
+  SP_G0,        // (h_f - c_p T_ref)/R   : g_i/(R T) = G0/T + G1 - cpR ln T
+  SP_G1,        // c_p/R (1 + ln T_ref) - s0/R
+  SP_CPR,       // c_p/R
+  SP_NFIELDS
+};
+
+// One reversible reaction, 64 bytes: ln k_f = lnA + b ln T - EaR / T and
+// ln k_r = ln k_f + sum_i nu_i g_i/(R T) + dnu ln(R T / P_atm).
+struct alignas(16) Rxn {
+  double lnA, b, EaR, dnu;
+  uint8_t rs[4], rn[4];   // reactants: species, coefficient (rn = 0 ends)
+  uint8_t ps[4], pn[4];   // products
+  uint8_t xs[8];          // species with nonzero net coefficient, ascending
+  int8_t xn[8];           // net coefficient (0 ends)
+};
+
+struct Mech {
+  int ns, nr;
+  const double *sp;   // [SP_NFIELDS][ns]
+  const Rxn *rx;      // [nr]
+};
+
+// Per-instance description, passed by value to the kernels.
+struct Inst {
+  int n_elem, p, nv, npf, depth, at_order;
+  int bc_left, bc_right, flux, limiter, delay_mode, max_delay;
+  double dx, dt, tvb;
+  uint64_t seed;
+  double cum[MAXD + 1];                 // cumulative SAA probabilities
+  double at[MAXD + 1][MAXO];            // AT weights c_m(k)
+  double *wn, *wa, *wpre;               // [nv][N][Q]
+  double *ring_in, *ring_pre;           // history ring
+  uint8_t *flags;                       // [3][N]
+  int32_t *count;                       // [N]
+  const int *pf_of_left;                // per element: PE face on its left face or -1
+  const int *pf_of_right;               // per element: PE face on its right face or -1
+  const int *pf_elem;                   // per PE face: [left element, right element]
+  int *err;                             // [4] code, element, stage, step (low bits)
+  int instance;
+};
+
+__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Delay of PE face f at step n (Sec. 4.1 CAA, Sec. 4.2 SAA).
+__host__ __device__ inline int draw_delay(int mode, int max_delay, uint64_t seed,
+                                          const double *cum, int64_t n, int f) {
+  if (mode == ADG_SYNC) return 0;
+  if (mode == ADG_CAA) return (int)(n % (int64_t)(max_delay + 1));
+  uint64_t key = seed ^ (((uint64_t)n << 32) + (uint64_t)(uint32_t)f);
+  double r = (double)(splitmix64(key) >> 11) * (1.0 / 9007199254740992.0);
+  for (int k = 0; k <= max_delay; ++k)
+    if (r < cum[k]) return k;
+  return max_delay;
+}
+
+// Delay in force: synchronous until the ring holds levels n-k-(o-1).
+__device__ inline int effective_delay(const Inst &I, int64_t n, int f) {
+  int k = draw_delay(I.delay_mode, I.max_delay, I.seed, I.cum, n, f);
+  return (n >= (int64_t)k + I.at_order - 1) ? k : 0;
+}
+
+__device__ inline size_t ring_block(const Inst &I, int64_t level, int s, int pf, int side) {
+  int slot = (int)(level % I.depth);
+  return ((((size_t)slot * 3 + s) * I.npf + pf) * 2 + side) * (size_t)I.nv * (I.p + 1);
+}
+
+__device__ inline void report_error(const Inst &I, int code, int elem, int stage, int64_t n) {
+  if (atomicCAS(I.err, 0, code) == 0) {
+    I.err[1] = elem;
+    I.err[2] = stage;
+    I.err[3] = (int)n;
+  }
+}
+
+// Thermodynamic state of a conserved vector w (stride `st` between variables).
+struct Thermo {
+  double rho, u, T, P, a, gm1;
+};
+
+// T from the internal energy: e(T) is linear for constant c_p, so the Newton
+// iteration on e(T) = e reaches its root in one step from any guess; that step
+// is this closed form. sp: species fields (shared or global memory).
+__device__ inline Thermo thermo_of(const double *sp, int ns, const double *w, int st) {
+  Thermo t;
+  double rho = 0.0, qsum = 0.0, cv = 0.0, Rm = 0.0, cpm = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    double r = w[(2 + i) * st];
+    rho += r;
+    qsum += r * sp[SP_QW * ns + i];
+    cv += r * sp[SP_CVW * ns + i];
+    Rm += r * sp[SP_RW * ns + i];
+    cpm += r * sp[SP_CPW * ns + i];
+  }
+  double m = w[0], E = w[st];
+  t.rho = rho;
+  t.u = m / rho;
+  double rhoe = E - 0.5 * m * m / rho;
+  t.T = (rhoe - qsum) / cv;
+  t.P = t.T * Rm;
+  t.gm1 = cpm / cv - 1.0;
+  t.a = sqrt(cpm / cv * t.P / rho);
+  return t;
+}
+
+// Physical flux component v of w (Eq. 2).
+__device__ inline double phys_flux(const double *w, int st, int v, const Thermo &t) {
+  if (v == 0) return w[0] * t.u + t.P;
+  if (v == 1) return t.u * (w[st] + t.P);
+  return t.u * w[v * st];
+}
+
+// Numerical flux (Sec. 3.1): local Lax-Friedrichs or HLLC (Toro 1994, wave
+// speeds S_L = min(u_L - a_L, u_R - a_R), S_R = max(u_L + a_L, u_R + a_R)).
+// out[v] for v = 0..nv-1; wl, wr with unit stride.
+__device__ inline void num_flux(const double *sp, int ns, int kind, const double *wl,
+                                const double *wr, double *out, double coef, bool accumulate) {
+  const int nv = ns + 2;
+  Thermo L = thermo_of(sp, ns, wl, 1), R = thermo_of(sp, ns, wr, 1);
+  if (kind == ADG_FLUX_LF) {
+    double lam = fmax(fabs(L.u) + L.a, fabs(R.u) + R.a);
+    for (int v = 0; v < nv; ++v) {
+      double f = 0.5 * (phys_flux(wl, 1, v, L) + phys_flux(wr, 1, v, R) - lam * (wr[v] - wl[v]));
+      out[v] = accumulate ? out[v] + coef * f : f;
+    }
+    return;
+  }
+  double SL = fmin(L.u - L.a, R.u - R.a);
+  double SR = fmax(L.u + L.a, R.u + R.a);
+  double SM = (R.P - L.P + L.rho * L.u * (SL - L.u) - R.rho * R.u * (SR - R.u)) /
+              (L.rho * (SL - L.u) - R.rho * (SR - R.u));
+  for (int v = 0; v < nv; ++v) {
+    double f;
+    if (0.0 <= SL) {
+      f = phys_flux(wl, 1, v, L);
+    } else if (0.0 <= SM) {
+      double c = L.rho * (SL - L.u) / (SL - SM);
+      double us;
+      if (v == 0) us = c * SM;
+      else if (v == 1) us = c * (wl[1] / L.rho + (SM - L.u) * (SM + L.P / (L.rho * (SL - L.u))));
+      else us = c * (wl[v] / L.rho);
+      f = phys_flux(wl, 1, v, L) + SL * (us - wl[v]);
+    } else if (0.0 <= SR) {
+      double c = R.rho * (SR - R.u) / (SR - SM);
+      double us;
+      if (v == 0) us = c * SM;
+      else if (v == 1) us = c * (wr[1] / R.rho + (SM - R.u) * (SM + R.P / (R.rho * (SR - R.u))));
+      else us = c * (wr[v] / R.rho);
+      f = phys_flux(wr, 1, v, R) + SR * (us - wr[v]);
+    } else {
+      f = phys_flux(wr, 1, v, R);
+    }
+    out[v] = accumulate ? out[v] + coef * f : f;
+  }
+}
+
+// Gauss-Legendre tables (points, weights, P_j and P_j' at the points) per Q.
+struct Basis {
+  double x[MAXQ], w[MAXQ];
+  double P[MAXQ][MAXQ];   // P[q][j]
+  double dP[MAXQ][MAXQ];  // dP[q][j]
+  double B[MAXQ][MAXQ];   // smoothness-indicator quadratic form
+  double Sl[MAXQ][MAXQ];  // left neighbour continued into the cell
+  double Sr[MAXQ][MAXQ];  // right neighbour continued into the cell
+};
+
+// Arguments of one stage of the RHS/update kernel.
+struct StageArgs {
+  const double *win;   // stage input W^(s)
+  const double *w0;    // w^n
+  double *wout;        // pre-limit stage output
+  int s;               // stage 0..2
+  int64_t n;           // step level
+  int TE;              // elements per tile
+};
+
+// Arguments of the limiter kernel of one stage.
+struct LimArgs {
+  const double *wpre;  // pre-limit stage output (read)
+  double *wout;        // limited stage output (written)
+  int s;
+  int64_t n;
+};
+
+struct ExpTable;
+cudaError_t upload_basis(const Basis *tables);
+cudaError_t upload_exp_table(const ExpTable *t);
+int stage_tile(int Q, int nv, int ns, int nr);
+size_t stage_smem(int TE, int Q, int nv, int ns, int nr);
+cudaError_t launch_stage(const Mech &M, const Inst &I, const StageArgs &A, cudaStream_t st);
+cudaError_t launch_limiter(const Mech &M, const Inst &I, const LimArgs &A, cudaStream_t st);
+cudaError_t launch_project(const Mech &M, const Inst &I, const double *prim, double *w,
+                           cudaStream_t st);
+cudaError_t launch_temperature(const Mech &M, const Inst &I, const double *w, double *T,
+                               cudaStream_t st);
+
+}  // namespace adg

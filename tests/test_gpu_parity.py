@@ -1,0 +1,248 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar (FP64 path): relative L-infinity error <= 1e-10 on every conserved variable,
+the error of variable v being max|w_gpu - w_oracle| / scale_v over all elements
+and modes, with the physical scale of each variable: max|rho E| for the energy,
+max rho (|u| + a) for the momentum, max|rho Y_i| for a partial density, floored
+at 1e-5 of the largest density. Relative to its own maximum, the momentum of a
+gas at rest or a species at a mass fraction of 1e-12 moves by 1e-6 when the
+oracle's own input moves by 1e-15; in these scales the oracle moves by less than
+1e-11 (tests/test_oracle_conditioning.py), ten times below the bar.
+Troubled-cell flags must be identical (per stage of the last step and counted
+over the whole run)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2501_01747_gb300 import adg
+from paper_2501_01747_gb300 import inputs as I
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def scales(w, mech):
+    return H.parity_scales(w, mech)
+
+
+def rel_err(a, b, mech=None):
+    mech = mech if mech is not None else CURRENT_MECH[0]
+    return H.parity_error(a, b, mech)
+
+
+CURRENT_MECH = [None]
+
+
+def run_both(wl, mech, prim, n_steps, chunks=1):
+    CURRENT_MECH[0] = mech
+    g = adg.ADG(mech, [wl])
+    g.set_primitive(prim)
+    o = O.Oracle(wl, mech)
+    o.set_primitive(prim)
+    per = n_steps // chunks
+    for _ in range(chunks):
+        g.step(per)
+        o.step(per)
+    g.check()
+    return g, o
+
+
+def assert_parity(g, o, tol=TOL, flags=True):
+    w, ref = g.get_state(), o.state()
+    err = rel_err(w, ref)
+    assert np.all(np.isfinite(w))
+    assert err.max() <= tol, err
+    if flags:
+        gl, gc = g.flags()
+        ol, oc = o.flags()
+        assert np.array_equal(gc, oc), np.flatnonzero(gc != oc)[:10]
+        assert np.array_equal(gl, ol)
+    return err
+
+
+def W():
+    return I.load_workloads()
+
+
+def test_ignition_5sp_full_run():
+    """The 5-species ignition workload as configured: 200 x p3, 4 PEs, SAA delays
+    (set 1), AT order 4, WENO, 500 steps."""
+    wl = W()["ignition-5sp-200x3"]
+    mech = wl.mechanism()
+    prim = wl.primitive(mech)
+    g, o = run_both(wl, mech, prim, 500, chunks=5)
+    assert g.steps_done() == 500
+    assert_parity(g, o)
+    T = g.temperature()
+    assert np.abs(T - o.temperature()).max() <= 1e-9 * T.max()
+
+
+@pytest.mark.parametrize("mode", [I.DELAY_SYNC, I.DELAY_CAA, I.DELAY_SAA])
+@pytest.mark.parametrize("flux", [I.FLUX_LF, I.FLUX_HLLC])
+def test_delay_modes_and_fluxes(mode, flux):
+    wl = W()["ignition-5sp-200x3"]
+    wl.delay_mode, wl.flux = mode, flux
+    mech = wl.mechanism()
+    g, o = run_both(wl, mech, wl.primitive(mech), 120)
+    assert_parity(g, o)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_every_degree_ragged_mesh_shock(p):
+    """Prime element count (ragged last tile), reflecting wall and outflow, HLLC,
+    WENO on a shock, SAA delays with AT order p+1, the 9-species mechanism."""
+    base = W()["detonation-9sp-16384x3"]
+    wl = I.scaled(base, 97, 7)
+    wl.p = p
+    wl.at_order = p + 1
+    wl.dt = base.dt * 0.05
+    mech = wl.mechanism()
+    g, o = run_both(wl, mech, wl.primitive(mech), 60)
+    assert_parity(g, o)
+    assert o.flags()[1].sum() > 0
+
+
+def test_one_element_per_pe_and_single_pe():
+    wl = W()["ignition-5sp-200x3"]
+    mech = wl.mechanism()
+    for n_pe, steps in [(1, 60), (200, 40)]:
+        w = I.scaled(wl, 200, n_pe)
+        w.dt = wl.dt * 0.25
+        g, o = run_both(w, mech, w.primitive(mech), steps)
+        assert_parity(g, o)
+
+
+def test_no_limiter_and_tvb():
+    wl = W()["ignition-5sp-200x3"]
+    mech = wl.mechanism()
+    wl.limiter = I.LIM_NONE
+    g, o = run_both(wl, mech, wl.primitive(mech), 80)
+    assert_parity(g, o)
+    assert g.flags()[1].sum() == 0
+    wl2 = W()["ignition-5sp-200x3"]
+    wl2.tvb_M = 50.0
+    g, o = run_both(wl2, mech, wl2.primitive(mech), 80)
+    assert_parity(g, o)
+
+
+def test_ignition_9sp_full_size():
+    """4096 x p4, 21 reactions, 64 PEs, delays up to 4 with AT order 5."""
+    wl = W()["ignition-9sp-4096x4"]
+    mech = wl.mechanism()
+    g, o = run_both(wl, mech, wl.primitive(mech), 12)
+    assert_parity(g, o)
+
+
+def test_detonation_9sp_full_size():
+    """16384 x p3, HLLC, WENO, reflecting/outflow, 256 PEs, delays up to 3."""
+    wl = W()["detonation-9sp-16384x3"]
+    mech = wl.mechanism()
+    g, o = run_both(wl, mech, wl.primitive(mech), 8)
+    assert_parity(g, o)
+
+
+def test_detonation_53sp_full_size_sampled():
+    """65536 x p3 with 53 species / 325 reactions: one full-size GPU step, checked
+    on sampled elements. After one step an element depends only on the 6
+    neighbours on each side (a face flux and a limiter stencil per stage), and the
+    first step is synchronous, so the oracle runs 13-element windows around the
+    samples and their centres must match."""
+    wl = W()["detonation-53sp-65536x3"]
+    mech = wl.mechanism()
+    prim = wl.primitive(mech)
+    g = adg.ADG(mech, [wl])
+    g.set_primitive(prim)
+    g.step(1)
+    g.check()
+    w = g.get_state()
+    rng = np.random.default_rng(0)
+    dx = wl.length / wl.n_elem
+    samples = sorted(set([6, 3276, 3277, 3280, wl.n_elem - 7] +
+                         list(rng.integers(6, wl.n_elem - 7, size=6))))
+    for e in samples:
+        win = I.scaled(wl, 13, 1)
+        win.x0 = wl.x0 + (e - 6) * dx
+        win.bc_left = win.bc_right = I.BC_OUTFLOW
+        o = O.Oracle(win, mech)
+        o.set_primitive(prim[:, e - 6:e + 7])
+        o.step(1)
+        ref = o.state()[:, 6:7]
+        got = w[:, e:e + 1]
+        scale = scales(w, mech)
+        err = (np.abs(got - ref) / np.maximum(scale, 1e-300)[:, None, None]).max()
+        assert err <= TOL, (e, err)
+
+
+def test_ensemble_of_instances_in_one_context():
+    """Several instances of different degree and size stepping together."""
+    ens = I.ensemble_workloads()
+    mech = ens[0].mechanism()
+    pick = []
+    for p in (2, 3, 4):
+        k = next(i for i, w in enumerate(ens) if w.p == p)
+        pick.append(I.scaled(ens[k], 67 + 10 * p, 3))
+    g = adg.ADG(mech, pick)
+    oracles = []
+    for k, wl in enumerate(pick):
+        prim = wl.primitive(mech)
+        g.set_primitive(prim, k)
+        o = O.Oracle(wl, mech)
+        o.set_primitive(prim)
+        oracles.append(o)
+    g.step(30)
+    g.check()
+    for k, o in enumerate(oracles):
+        o.step(30)
+        err = rel_err(g.get_state(k), o.state(), mech)
+        assert err.max() <= TOL, (k, err)
+        assert np.array_equal(g.flags(k)[1], o.flags()[1])
+
+
+def test_state_roundtrip_zero_steps_and_determinism():
+    wl = W()["ignition-5sp-200x3"]
+    mech = wl.mechanism()
+    prim = wl.primitive(mech)
+    g = adg.ADG(mech, [wl])
+    g.set_primitive(prim)
+    w0 = g.get_state()
+    g.step(0)
+    assert np.array_equal(g.get_state(), w0)
+    g.set_state(w0)
+    assert np.array_equal(g.get_state(), w0)
+    g.step(30)
+    a = g.get_state()
+    g.set_state(w0)
+    g.step(30)
+    assert np.array_equal(g.get_state(), a)
+
+
+def test_nonphysical_state_is_reported():
+    """A state with negative density (made on the host) is reported by
+    adg_status as ADG_ERR_NONPHYSICAL; the context stays usable."""
+    wl = W()["ignition-5sp-200x3"]
+    mech = wl.mechanism()
+    g = adg.ADG(mech, [wl])
+    g.set_primitive(wl.primitive(mech))
+    w = g.get_state()
+    bad = w.copy()
+    bad[2:, 17, 0] *= -1.0
+    g.set_state(bad)
+    g.step(1)
+    rc, where = g.status()
+    assert rc == -4
+    assert where[0] == 0
+    g.set_state(w)
+    g.step(2)
+    g.check()
+
+
+def test_invalid_arguments_raise():
+    wl = W()["ignition-5sp-200x3"]
+    mech = wl.mechanism()
+    g = adg.ADG(mech, [wl])
+    with pytest.raises(adg.AdgError):
+        g.get_state(k=3)
+    with pytest.raises(adg.AdgError):
+        g.step(-1)
