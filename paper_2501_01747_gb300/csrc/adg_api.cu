@@ -90,6 +90,19 @@ static void make_basis(int p, Basis *B) {
   }
 }
 
+// All constant tables: the DG/WENO basis for p = 1..ADG_MAX_P, and for the
+// table-driven exp the values 2^(j/32) and the split of ln2/32 (extended precision).
+void adg::make_tables(Basis *tables, ExpTable *et) {
+  for (int p = 1; p <= ADG_MAX_P; ++p) make_basis(p, &tables[p - 1]);
+  for (int j = 0; j < 32; ++j) et->t[j] = (double)exp2l((long double)j / 32.0L);
+  long double l = logl(2.0L) / 32.0L;
+  int ex;
+  long double mant = frexpl(l, &ex);
+  long double hi = ldexpl(floorl(ldexpl(mant, 32)), ex - 32);
+  et->l_hi = (double)hi;
+  et->l_lo = (double)(l - hi);
+}
+
 // AT weights (Eq. 7-8): extrapolation to t_n from levels t_n - (k+m) dt.
 static void at_weights(int order, int k, double *c) {
   for (int m = 0; m < order; ++m) {
@@ -354,23 +367,15 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
   if (nr > 0 &&
       cudaMemcpy((void *)M.rx, rx.data(), sizeof(Rxn) * nr, cudaMemcpyHostToDevice))
     rc2 = ADG_ERR_CUDA;
-  // exp table: 2^(j/32) and the split of ln2/32, in extended precision
-  {
-    ExpTable et;
-    for (int j = 0; j < 32; ++j) et.t[j] = (double)exp2l((long double)j / 32.0L);
-    long double l = logl(2.0L) / 32.0L;
-    int ex;
-    long double mant = frexpl(l, &ex);
-    long double hi = ldexpl(floorl(ldexpl(mant, 32)), ex - 32);
-    et.l_hi = (double)hi;
-    et.l_lo = (double)(l - hi);
-    if (upload_exp_table(&et) != cudaSuccess) rc2 = ADG_ERR_CUDA;
-  }
   if (cudaMemset(ctx->err_all, 0, sizeof(int) * 4 * n)) rc2 = ADG_ERR_CUDA;
-  // basis tables
-  Basis tables[ADG_MAX_P];
-  for (int p = 1; p <= ADG_MAX_P; ++p) make_basis(p, &tables[p - 1]);
-  if (upload_basis(tables) != cudaSuccess) rc2 = ADG_ERR_CUDA;
+  // basis tables and the exp table in constant memory
+  {
+    Basis tables[ADG_MAX_P];
+    ExpTable et;
+    make_tables(tables, &et);
+    if (upload_basis(tables) != cudaSuccess || upload_exp_table(&et) != cudaSuccess)
+      rc2 = ADG_ERR_CUDA;
+  }
   // instances
   for (int k = 0; k < n && rc2 == ADG_OK; ++k) {
     const adg_config &c = cfgs[k];

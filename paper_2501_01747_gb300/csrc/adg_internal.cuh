@@ -217,6 +217,7 @@ struct LimArgs {
 };
 
 struct ExpTable;
+void make_tables(Basis *tables, ExpTable *et);
 cudaError_t upload_basis(const Basis *tables);
 cudaError_t upload_exp_table(const ExpTable *t);
 int stage_tile(int Q, int nv, int ns, int nr);
