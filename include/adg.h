@@ -165,6 +165,37 @@ int adg_launches_per_step(const adg_ctx *ctx);
 
 const char *adg_error_string(int code);
 
+/* ---------------------------------------------------------------------------
+ * Time step without any device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, for instance code
+ * that runs while a CUDA graph is being captured, inside an allocator-free
+ * runtime, or under a memory budget that forbids growing the device heap.
+ *
+ * adg_step_noalloc advances one instance (mechanism and config as for
+ * adg_create) by n_steps SSP-RK3 steps from the modal state w_in_dev to
+ * w_out_dev (both caller-owned device arrays [nv][n_elem][p+1]; they may be the
+ * same array). Like adg_set_state followed by adg_step, it starts from step 0
+ * with an empty history, so the first steps are synchronous. All scratch (stage
+ * buffers, history ring, tables, flags) lives in one static device array of
+ * ADG_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits; the call allocates nothing, neither on the device nor on the
+ * host heap. Work is enqueued on `stream` and the call returns without waiting.
+ *
+ * - The first call on each device looks up the array's device address and
+ *   uploads the constant tables; make that first call before any stream
+ *   capture on that device.
+ * - A problem whose scratch does not fit returns ADG_ERR_NOMEM (nothing is
+ *   enqueued); more than ADG_NOALLOC_MAX_REACTIONS reactions returns ADG_ERR_ARG.
+ * - Every call reuses the same array: calls that overlap on the GPU (on
+ *   different streams, or on one device from several threads without ordering)
+ *   race and corrupt each other. The call clears what must start at zero.
+ * - Non-physical states found on the device are not reported (there is no
+ *   context to query); check the output. */
+#define ADG_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define ADG_NOALLOC_MAX_REACTIONS 512
+int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg, const double *w_in_dev,
+                     double *w_out_dev, int n_steps, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libadg.so")
-SOURCES = ["adg_kernels.cu", "adg_api.cu"]
+SOURCES = ["adg_kernels.cu", "adg_api.cu", "adg_static.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", ARCH]
 
@@ -98,7 +98,7 @@ EXPORTS = ["adg_workspace_bytes", "adg_create", "adg_destroy", "adg_set_primitiv
            "adg_step", "adg_status", "adg_get_flags", "adg_get_temperature", "adg_steps_done",
            "adg_delay_table", "adg_launches_per_step", "adg_error_string",
            "adg_write_state", "adg_read_state", "adg_enable_kernel_timing",
-           "adg_kernel_times"]
+           "adg_kernel_times", "adg_step_noalloc"]
 
 
 def lib(path: str | None = None):
@@ -133,6 +133,8 @@ def lib(path: str | None = None):
     L.adg_read_state.argtypes = [vp, C.c_int, d, vp]
     L.adg_enable_kernel_timing.argtypes = [vp, C.c_int]
     L.adg_kernel_times.argtypes = [vp, d, C.POINTER(C.c_int64)]
+    L.adg_step_noalloc.argtypes = [C.POINTER(Mechanism_), C.POINTER(Config_), vp, vp, C.c_int,
+                                   vp]
     L.adg_error_string.restype = C.c_char_p
     L.adg_error_string.argtypes = [C.c_int]
     _lib = L
@@ -177,6 +179,20 @@ def delay_table(wl, step0, n_steps):
     _check(lib().adg_delay_table(C.byref(cfg), int(step0), int(n_steps),
                                  out.ctypes.data_as(C.POINTER(C.c_uint8))), "adg_delay_table")
     return out
+
+
+def step_noalloc(mech, wl, w_in_dev, w_out_dev, n_steps, stream=None):
+    """adg_step_noalloc: advance one instance from the device tensor w_in_dev to
+    w_out_dev without any allocation (scratch in the library's static array)."""
+    m = _MechArgs(mech)
+    cfg, probs = config_struct(wl)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(w_out_dev.device)
+    st = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().adg_step_noalloc(C.byref(m.s), C.byref(cfg), C.c_void_p(w_in_dev.data_ptr()),
+                                  C.c_void_p(w_out_dev.data_ptr()), int(n_steps), st),
+           "adg_step_noalloc")
 
 
 def _torch():

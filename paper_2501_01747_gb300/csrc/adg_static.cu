@@ -1,0 +1,263 @@
+// adg_step_noalloc: the ADG time step for callers that cannot allocate device
+// memory. All scratch (mechanism tables, stage buffers, history ring, flags,
+// PE maps, error word) lives in one file-scope device array of fixed size.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "adg_internal.cuh"
+#include "adg_math.cuh"
+
+namespace adg {
+
+// The scratch. Every GPU that loads the library holds it until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ADG_NOALLOC_SCRATCH_BYTES];
+
+// PE maps of one instance computed on the device (PE q owns elements
+// [q N / P, (q+1) N / P); the element e belongs to PE ((e+1) P - 1) / N).
+__global__ void noalloc_maps_kernel(int N, int P, int npf, int periodic, int *pf_left,
+                                    int *pf_right, int32_t *count, uint8_t *flags, int *err) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e == 0)
+    for (int k = 0; k < 4; ++k) err[k] = 0;
+  if (e >= N) return;
+  count[e] = 0;
+  flags[e] = flags[N + e] = flags[2 * N + e] = 0;
+  int l = -1, r = -1;
+  if (npf > 0) {
+    int64_t q = (((int64_t)e + 1) * P - 1) / N;
+    int64_t first = q * N / P;
+    int64_t next = (q + 1) * N / P;
+    if (e == first) {
+      if (q > 0) l = (int)(q - 1);
+      else if (periodic) l = P - 1;
+    }
+    if (e == next - 1) {
+      if (q < P - 1) r = (int)q;
+      else if (periodic) r = P - 1;
+    }
+  }
+  pf_left[e] = l;
+  pf_right[e] = r;
+}
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+unsigned char *g_ptr[kMaxDevices];
+bool g_ready[kMaxDevices];
+
+struct Cursor {
+  unsigned char *base;
+  size_t off;
+  size_t take(size_t n) {
+    off = (off + 255) & ~(size_t)255;
+    size_t at = off;
+    off += n;
+    return at;
+  }
+};
+
+}  // namespace
+}  // namespace adg
+
+using namespace adg;
+
+extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg,
+                                const double *w_in_dev, double *w_out_dev, int n_steps,
+                                void *stream) {
+  if (!mech || !cfg || !w_in_dev || !w_out_dev || n_steps < 0) return ADG_ERR_ARG;
+  const adg_config &c = *cfg;
+  const int ns = mech->n_species, nr = mech->n_reactions;
+  if (ns < 1 || ns > ADG_MAX_SPECIES || nr < 0 || nr > ADG_NOALLOC_MAX_REACTIONS)
+    return ADG_ERR_ARG;
+  if (c.p < 1 || c.p > ADG_MAX_P || c.n_elem < 1 || c.n_pe < 1 || c.n_pe > c.n_elem ||
+      !(c.length > 0.0) || !(c.dt > 0.0) || c.at_order < 1 || c.at_order > ADG_MAX_AT_ORDER ||
+      c.max_delay < 0 || c.max_delay > ADG_MAX_DELAY || c.delay_mode < ADG_SYNC ||
+      c.delay_mode > ADG_SAA || (c.delay_mode == ADG_SAA && !c.delay_probs) ||
+      (c.flux != ADG_FLUX_LF && c.flux != ADG_FLUX_HLLC) ||
+      (c.limiter != ADG_LIM_NONE && c.limiter != ADG_LIM_WENO) || c.bc_left < 0 ||
+      c.bc_left > 2 || c.bc_right < 0 || c.bc_right > 2 ||
+      ((c.bc_left == ADG_BC_PERIODIC) != (c.bc_right == ADG_BC_PERIODIC)))
+    return ADG_ERR_ARG;
+  for (int i = 0; i < ns; ++i)
+    if (!(mech->W[i] > 0.0) || !(mech->cp[i] > RU)) return ADG_ERR_ARG;
+  const int N = c.n_elem, Q = c.p + 1, nv = ns + 2;
+  const bool periodic = c.bc_left == ADG_BC_PERIODIC;
+  const int npf = c.n_pe <= 1 ? 0 : (periodic ? c.n_pe : c.n_pe - 1);
+  const int depth = c.max_delay + c.at_order;
+
+  // layout of the scratch; reject problems that do not fit
+  Cursor cur{nullptr, 0};
+  size_t o_sp = cur.take(sizeof(double) * SP_NFIELDS * ns);
+  size_t o_rx = cur.take(sizeof(Rxn) * (nr > 0 ? nr : 1));
+  size_t o_err = cur.take(sizeof(int) * 4);
+  size_t st = (size_t)nv * N * Q;
+  size_t o_wa = cur.take(sizeof(double) * st);
+  size_t o_wpre = cur.take(sizeof(double) * st);
+  size_t rs = (size_t)depth * 3 * (npf > 0 ? npf : 1) * 2 * nv * Q;
+  size_t o_rin = cur.take(sizeof(double) * rs);
+  size_t o_rpre = cur.take(sizeof(double) * rs);
+  size_t o_flags = cur.take((size_t)3 * N);
+  size_t o_count = cur.take(sizeof(int32_t) * N);
+  size_t o_pl = cur.take(sizeof(int) * N);
+  size_t o_pr = cur.take(sizeof(int) * N);
+  if (cur.off > (size_t)ADG_NOALLOC_SCRATCH_BYTES) return ADG_ERR_NOMEM;
+
+  // host-side tables on the stack (no heap)
+  double sp[SP_NFIELDS * ADG_MAX_SPECIES];
+  Rxn rx[ADG_NOALLOC_MAX_REACTIONS > 0 ? ADG_NOALLOC_MAX_REACTIONS : 1];
+  for (int i = 0; i < ns; ++i) {
+    double W = mech->W[i], cp = mech->cp[i], hf = mech->h_f[i], s0 = mech->s0[i];
+    sp[SP_W * ns + i] = W;
+    sp[SP_INVW * ns + i] = 1.0 / W;
+    sp[SP_QW * ns + i] = (hf - cp * TREF) / W;
+    sp[SP_CVW * ns + i] = (cp - RU) / W;
+    sp[SP_RW * ns + i] = RU / W;
+    sp[SP_CPW * ns + i] = cp / W;
+    sp[SP_G0 * ns + i] = (hf - cp * TREF) / RU;
+    sp[SP_G1 * ns + i] = cp / RU * (1.0 + log(TREF)) - s0 / RU;
+    sp[SP_CPR * ns + i] = cp / RU;
+  }
+  for (int j = 0; j < nr; ++j) {
+    Rxn &R = rx[j];
+    memset(&R, 0, sizeof(Rxn));
+    if (!(mech->A[j] > 0.0)) return ADG_ERR_ARG;
+    R.lnA = log(mech->A[j]);
+    R.b = mech->b[j];
+    R.EaR = mech->Ea[j] / RU;
+    int a = 0, b = 0, x = 0, dnu = 0;
+    for (int i = 0; i < ns; ++i) {
+      int f = mech->nu_f[j * ns + i], r = mech->nu_r[j * ns + i];
+      if (f < 0 || r < 0 || f > 2 || r > 2) return ADG_ERR_ARG;
+      if (f > 0) {
+        if (a == SIDE) return ADG_ERR_ARG;
+        R.rs[a] = (uint8_t)i;
+        R.rn[a++] = (uint8_t)f;
+      }
+      if (r > 0) {
+        if (b == SIDE) return ADG_ERR_ARG;
+        R.ps[b] = (uint8_t)i;
+        R.pn[b++] = (uint8_t)r;
+      }
+      if (r != f) {
+        if (x == NET) return ADG_ERR_ARG;
+        R.xs[x] = (uint8_t)i;
+        R.xn[x++] = (int8_t)(r - f);
+        dnu += r - f;
+      }
+    }
+    R.dnu = (double)dnu;
+  }
+
+  // once per device: the scratch address and the constant tables. This is the
+  // only set-up; it runs on the first call on each device.
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ADG_ERR_CUDA;
+  {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_ready[dev]) {
+      void *p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) return ADG_ERR_CUDA;
+      Basis tables[ADG_MAX_P];
+      ExpTable et;
+      make_tables(tables, &et);
+      if (upload_basis(tables) != cudaSuccess || upload_exp_table(&et) != cudaSuccess)
+        return ADG_ERR_CUDA;
+      g_ptr[dev] = (unsigned char *)p;
+      g_ready[dev] = true;
+    }
+  }
+  unsigned char *base = g_ptr[dev];
+  cudaStream_t s = (cudaStream_t)stream;
+
+  Mech M;
+  M.ns = ns;
+  M.nr = nr;
+  M.sp = (const double *)(base + o_sp);
+  M.rx = (const Rxn *)(base + o_rx);
+  Inst I;
+  memset(&I, 0, sizeof(I));
+  I.n_elem = N;
+  I.p = c.p;
+  I.nv = nv;
+  I.npf = npf;
+  I.depth = depth;
+  I.at_order = c.at_order;
+  I.bc_left = c.bc_left;
+  I.bc_right = c.bc_right;
+  I.flux = c.flux;
+  I.limiter = c.limiter;
+  I.delay_mode = c.delay_mode;
+  I.max_delay = c.max_delay;
+  I.dx = c.length / N;
+  I.dt = c.dt;
+  I.tvb = c.tvb_M * I.dx * I.dx;
+  I.seed = c.seed;
+  double acc = 0.0;
+  for (int d = 0; d <= MAXD; ++d) {
+    if (d <= c.max_delay) acc += (c.delay_mode == ADG_SAA) ? c.delay_probs[d] : 0.0;
+    I.cum[d] = acc;
+  }
+  for (int d = 0; d <= MAXD; ++d)
+    for (int m = 0; m < MAXO; ++m) {
+      double v = 0.0;
+      if (d <= c.max_delay && m < c.at_order) {
+        v = 1.0;
+        for (int j = 0; j < c.at_order; ++j)
+          if (j != m) v *= (double)(d + j) / (double)(j - m);
+      }
+      I.at[d][m] = v;
+    }
+  I.wn = w_out_dev;
+  I.wa = (double *)(base + o_wa);
+  I.wpre = (double *)(base + o_wpre);
+  I.ring_in = (double *)(base + o_rin);
+  I.ring_pre = (double *)(base + o_rpre);
+  I.flags = (uint8_t *)(base + o_flags);
+  I.count = (int32_t *)(base + o_count);
+  I.pf_of_left = (const int *)(base + o_pl);
+  I.pf_of_right = (const int *)(base + o_pr);
+  I.pf_elem = nullptr;
+  I.err = (int *)(base + o_err);
+  I.instance = 0;
+
+#define NA_CK(x)                               \
+  do {                                         \
+    if ((x) != cudaSuccess) return ADG_ERR_CUDA; \
+  } while (0)
+  NA_CK(cudaMemcpyAsync(base + o_sp, sp, sizeof(double) * SP_NFIELDS * ns,
+                        cudaMemcpyHostToDevice, s));
+  if (nr > 0) NA_CK(cudaMemcpyAsync(base + o_rx, rx, sizeof(Rxn) * nr, cudaMemcpyHostToDevice, s));
+  if (w_out_dev != w_in_dev)
+    NA_CK(cudaMemcpyAsync(w_out_dev, w_in_dev, sizeof(double) * st, cudaMemcpyDeviceToDevice, s));
+  noalloc_maps_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, c.n_pe, npf, periodic ? 1 : 0,
+                                                      (int *)I.pf_of_left, (int *)I.pf_of_right,
+                                                      I.count, I.flags, I.err);
+  NA_CK(cudaGetLastError());
+  int TE = stage_tile(Q, nv, ns, nr);
+  int target = (N + 2 * 152 - 1) / (2 * 152);
+  if (target < TE) TE = target < 4 ? 4 : target;
+  for (int64_t n = 0; n < n_steps; ++n) {
+    for (int stg = 0; stg < 3; ++stg) {
+      StageArgs A;
+      A.win = (stg == 0) ? I.wn : I.wa;
+      A.w0 = I.wn;
+      A.wout = I.wpre;
+      A.s = stg;
+      A.n = n;
+      A.TE = TE;
+      NA_CK(launch_stage(M, I, A, s));
+      LimArgs L;
+      L.wpre = I.wpre;
+      L.wout = (stg == 2) ? I.wn : I.wa;
+      L.s = stg;
+      L.n = n;
+      NA_CK(launch_limiter(M, I, L, s));
+    }
+  }
+#undef NA_CK
+  return ADG_OK;
+}
