@@ -307,7 +307,7 @@ def main(argv=None):
     return 0
 
 
-KERNEL_REV = "fp64-v2"
+KERNEL_REV = "fp64-v4"
 
 if __name__ == "__main__":
     sys.exit(main())

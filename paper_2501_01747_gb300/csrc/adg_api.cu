@@ -76,6 +76,11 @@ static void make_basis(int p, Basis *B) {
         for (int j = 0; j < Q; ++j) B->B[i][j] += ldexp(1.0, 2 * s - 1) * B->w[q] * D[i] * D[j];
     }
   }
+  for (int q = 0; q < Q; ++q)
+    for (int i = 0; i < Q; ++i) {
+      B->WdP[q][i] = B->w[q] * B->dP[q][i];
+      B->WPh[q][i] = B->w[q] * B->P[q][i] * 0.5 * (2 * i + 1);
+    }
   // neighbour polynomials continued into the cell: left uses xi' = xi + 2
   for (int q = 0; q < Q; ++q) {
     double Pl[MAXQ + 1], Pr[MAXQ + 1], P[MAXQ + 1];
@@ -211,6 +216,7 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
     size_t st = (size_t)nv * N * Q;
     I.wn = (double *)cv.take(sizeof(double) * st);
     I.wa = (double *)cv.take(sizeof(double) * st);
+    I.wb = (double *)cv.take(sizeof(double) * st);
     I.wpre = (double *)cv.take(sizeof(double) * st);
     size_t rs = (size_t)(c.max_delay + c.at_order) * 3 * (npf > 0 ? npf : 1) * 2 * nv * Q;
     I.ring_in = (double *)cv.take(sizeof(double) * rs);
@@ -360,8 +366,9 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
       int f = mech->nu_f[j * ns + i], r = mech->nu_r[j * ns + i];
       if (f > 0) { R.rs[a] = (uint8_t)i; R.rn[a] = (uint8_t)f; ++a; }
       if (r > 0) { R.ps[b] = (uint8_t)i; R.pn[b] = (uint8_t)r; ++b; }
-      if (r - f != 0) { R.xs[x] = (uint8_t)i; R.xn[x] = (int8_t)(r - f); ++x; dnu += r - f; }
+      if (r - f != 0) { R.xs[x] = (uint8_t)i; R.xc[x] = (double)(r - f); ++x; dnu += r - f; }
     }
+    R.nx = (uint8_t)x;
     R.dnu = (double)dnu;
   }
   if (nr > 0 &&
@@ -542,25 +549,31 @@ int adg_step(adg_ctx *ctx, int n_steps, void *stream) {
     for (int k = 0; k < ctx->n_inst; ++k) {
       InstHost &h = ctx->inst[k];
       Inst &I = h.d;
+      // stage inputs w^n -> wa -> wb -> w^n: a stage never writes the buffer
+      // whose halo other CTAs read in the same launch
+      double *bufs[4] = {I.wn, I.wa, I.wb, I.wn};
       for (int s = 0; s < 3; ++s) {
         StageArgs A;
-        A.win = (s == 0) ? I.wn : I.wa;
+        A.win = bufs[s];
         A.w0 = I.wn;
         A.wout = I.wpre;
+        A.wnext = bufs[s + 1];
         A.s = s;
         A.n = h.n;
         A.TE = h.TE;
         CK(timed_begin(ctx, 0, st));
         CK(launch_stage(ctx->mech, I, A, st));
         CK(timed_end(ctx, st));
-        LimArgs L;
-        L.wpre = I.wpre;
-        L.wout = (s == 2) ? I.wn : I.wa;
-        L.s = s;
-        L.n = h.n;
-        CK(timed_begin(ctx, 1, st));
-        CK(launch_limiter(ctx->mech, I, L, st));
-        CK(timed_end(ctx, st));
+        if (I.limiter != ADG_LIM_NONE) {
+          LimArgs L;
+          L.wpre = I.wpre;
+          L.wout = bufs[s + 1];
+          L.s = s;
+          L.n = h.n;
+          CK(timed_begin(ctx, 1, st));
+          CK(launch_limiter(ctx->mech, I, L, st));
+          CK(timed_end(ctx, st));
+        }
       }
       h.n += 1;
     }
@@ -568,7 +581,12 @@ int adg_step(adg_ctx *ctx, int n_steps, void *stream) {
   return ADG_OK;
 }
 
-int adg_launches_per_step(const adg_ctx *ctx) { return ctx ? 6 * ctx->n_inst : 0; }
+int adg_launches_per_step(const adg_ctx *ctx) {
+  if (!ctx) return 0;
+  int n = 0;
+  for (const InstHost &h : ctx->inst) n += (h.d.limiter != ADG_LIM_NONE) ? 6 : 3;
+  return n;
+}
 
 int adg_enable_kernel_timing(adg_ctx *ctx, int on) {
   if (!ctx) return ADG_ERR_ARG;

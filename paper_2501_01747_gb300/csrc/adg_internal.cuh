@@ -34,15 +34,18 @@ enum SpeciesField {
   SP_NFIELDS
 };
 
-// One reversible reaction, 64 bytes: ln k_f = lnA + b ln T - EaR / T and
+// One reversible reaction, 128 bytes: ln k_f = lnA + b ln T - EaR / T and
 // ln k_r = ln k_f + sum_i nu_i g_i/(R T) + dnu ln(R T / P_atm).
 struct alignas(16) Rxn {
   double lnA, b, EaR, dnu;
+  double xc[8];           // net coefficient nu_i of species xs[t]
+  uint8_t xs[8];          // species with nonzero net coefficient, ascending
   uint8_t rs[4], rn[4];   // reactants: species, coefficient (rn = 0 ends)
   uint8_t ps[4], pn[4];   // products
-  uint8_t xs[8];          // species with nonzero net coefficient, ascending
-  int8_t xn[8];           // net coefficient (0 ends)
+  uint8_t nx;             // number of entries of xs/xc
+  uint8_t pad[7];
 };
+static_assert(sizeof(Rxn) == 128, "reaction record is 128 bytes");
 
 struct Mech {
   int ns, nr;
@@ -58,7 +61,7 @@ struct Inst {
   uint64_t seed;
   double cum[MAXD + 1];                 // cumulative SAA probabilities
   double at[MAXD + 1][MAXO];            // AT weights c_m(k)
-  double *wn, *wa, *wpre;               // [nv][N][Q]
+  double *wn, *wa, *wb, *wpre;          // [nv][N][Q]: w^n, stage 1 and 2 inputs, pre-limit
   double *ring_in, *ring_pre;           // history ring
   uint8_t *flags;                       // [3][N]
   int32_t *count;                       // [N]
@@ -121,19 +124,21 @@ __device__ inline Thermo thermo_of(const double *sp, int ns, const double *w, in
   for (int i = 0; i < ns; ++i) {
     double r = w[(2 + i) * st];
     rho += r;
-    qsum += r * sp[SP_QW * ns + i];
-    cv += r * sp[SP_CVW * ns + i];
-    Rm += r * sp[SP_RW * ns + i];
-    cpm += r * sp[SP_CPW * ns + i];
+    qsum = fma(r, sp[SP_QW * ns + i], qsum);
+    cv = fma(r, sp[SP_CVW * ns + i], cv);
+    Rm = fma(r, sp[SP_RW * ns + i], Rm);
+    cpm = fma(r, sp[SP_CPW * ns + i], cpm);
   }
+  const double irho = 1.0 / rho, icv = 1.0 / cv;
   double m = w[0], E = w[st];
   t.rho = rho;
-  t.u = m / rho;
-  double rhoe = E - 0.5 * m * m / rho;
-  t.T = (rhoe - qsum) / cv;
+  t.u = m * irho;
+  double rhoe = E - 0.5 * m * t.u;
+  t.T = (rhoe - qsum) * icv;
   t.P = t.T * Rm;
-  t.gm1 = cpm / cv - 1.0;
-  t.a = sqrt(cpm / cv * t.P / rho);
+  double gam = cpm * icv;
+  t.gm1 = gam - 1.0;
+  t.a = sqrt(gam * t.P * irho);
   return t;
 }
 
@@ -196,13 +201,16 @@ struct Basis {
   double B[MAXQ][MAXQ];   // smoothness-indicator quadratic form
   double Sl[MAXQ][MAXQ];  // left neighbour continued into the cell
   double Sr[MAXQ][MAXQ];  // right neighbour continued into the cell
+  double WdP[MAXQ][MAXQ]; // w_q P_i'(x_q)            (volume integral)
+  double WPh[MAXQ][MAXQ]; // w_q P_i(x_q) (2i+1)/2     (source projection)
 };
 
 // Arguments of one stage of the RHS/update kernel.
 struct StageArgs {
   const double *win;   // stage input W^(s)
   const double *w0;    // w^n
-  double *wout;        // pre-limit stage output
+  double *wout;        // pre-limit stage output (limiter input)
+  double *wnext;       // next-stage buffer: pre-limit output, limited in place later
   int s;               // stage 0..2
   int64_t n;           // step level
   int TE;              // elements per tile

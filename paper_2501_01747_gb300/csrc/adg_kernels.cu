@@ -8,9 +8,12 @@
 //                      fluxes of the tile (AT flux at delayed PE faces), assembles
 //                      Eq. (5) and the SSP-RK3 combination, writes the pre-limit
 //                      stage output and the history ring of PE-boundary elements.
-//   limiter_kernel<Q>: one thread per element: troubled-cell indicator in the
+//   limiter_kernel<Q>: 16 or 32 lanes per element: troubled-cell indicator in the
 //                      characteristic fields of the cell average and, on troubled
-//                      cells, the (AT-)WENO reconstruction of Eq. (9)-(11).
+//                      cells, the (AT-)WENO reconstruction of Eq. (9)-(11). The
+//                      stage kernel writes the pre-limit output twice (limiter
+//                      input and next-stage buffer) so that the limiter only
+//                      rewrites troubled cells.
 #include <cstdio>
 
 #include "adg_internal.cuh"
@@ -98,20 +101,20 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, Inst I, StageArgs A)
     const double lnT = log(th.T), invT = 1.0 / th.T;
     double *cq = sconc + t, *gq = sg + t, *wd = swd + t;
     for (int i = 0; i < ns; ++i) {
-      cq[(size_t)i * TQ] = fmax(wq[(size_t)(2 + i) * TQ], 0.0) * sIW[i];
-      gq[(size_t)i * TQ] = fma(sG0[i], invT, sG1[i]) - sCR[i] * lnT;
+      double r = wq[(size_t)(2 + i) * TQ];
+      // clip at zero by the sign bit (no FP64 instruction)
+      r = (__double2hiint(r) < 0) ? 0.0 : r;
+      cq[(size_t)i * TQ] = r * sIW[i];
+      gq[(size_t)i * TQ] = fma(-sCR[i], lnT, fma(sG0[i], invT, sG1[i]));
       wd[(size_t)i * TQ] = 0.0;
     }
     const double lr = lnT + LN_R_PATM;
     for (int j = 0; j < nr; ++j) {
       const Rxn &R = srx[j];
-      double lkf = fma(R.b, lnT, R.lnA) - R.EaR * invT;
+      double lkf = fma(-R.EaR, invT, fma(R.b, lnT, R.lnA));
       double dg = R.dnu * lr;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (R.xn[k] == 0) break;
-        dg = fma((double)R.xn[k], gq[(size_t)R.xs[k] * TQ], dg);
-      }
+      const int nx = R.nx;
+      for (int k = 0; k < nx; ++k) dg = fma(R.xc[k], gq[(size_t)R.xs[k] * TQ], dg);
       double fwd = fexp(lkf, *stab), rev = fexp(lkf + dg, *stab);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -128,11 +131,8 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, Inst I, StageArgs A)
         if (R.pn[k] > 1) rev *= c;
       }
       double qj = fwd - rev;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (R.xn[k] == 0) break;
-        wd[(size_t)R.xs[k] * TQ] = fma((double)R.xn[k], qj, wd[(size_t)R.xs[k] * TQ]);
-      }
+      for (int k = 0; k < nx; ++k)
+        wd[(size_t)R.xs[k] * TQ] = fma(R.xc[k], qj, wd[(size_t)R.xs[k] * TQ]);
     }
     double f0 = phys_flux(wq, TQ, 0, th), f1 = phys_flux(wq, TQ, 1, th);
     for (int v = 2; v < nv; ++v) wq[(size_t)v * TQ] = th.u * wq[(size_t)v * TQ];
@@ -190,31 +190,39 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, Inst I, StageArgs A)
 
   // 4. assembly of Eq. (5) and the SSP-RK3 combination; history ring writes
   const int slot_ok = (I.npf > 0);
+  const double inv_dx = 1.0 / I.dx;
   for (int item = tid; item < nv * te; item += nth) {
     int v = item / te, e = item - v * te, ge = e0 + e, le = e + 1;
     const double *wi = sw + ((size_t)v * (TE + 2) + le) * Q;
     const double *fq = snode + (size_t)v * TQ + e * Q;
     const double *sq = (v >= 2) ? swd + (size_t)(v - 2) * TQ + e * Q : nullptr;
     const double Wv = (v >= 2) ? sW[v - 2] : 0.0;
+    const double fr = sfh[(size_t)(e + 1) * nv + v], fl = sfh[(size_t)e * nv + v];
+    double fqr[Q], sqr[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      fqr[q] = fq[q];
+      sqr[q] = (v >= 2) ? sq[q] : 0.0;
+    }
     double out[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       double V = 0.0, S = 0.0;
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        V += B.w[q] * fq[q] * B.dP[q][i];
-        if (v >= 2) S += B.w[q] * (Wv * sq[q]) * B.P[q][i];
+        V = fma(B.WdP[q][i], fqr[q], V);
+        S = fma(B.WPh[q][i], sqr[q], S);
       }
-      double sgn = (i & 1) ? -1.0 : 1.0;
-      double surf = V - sfh[(size_t)(e + 1) * nv + v] + sgn * sfh[(size_t)e * nv + v];
-      double r = (2.0 * i + 1.0) / I.dx * surf + 0.5 * (2.0 * i + 1.0) * S;
+      double surf = (i & 1) ? (V - fr - fl) : (V - fr + fl);
+      double r = fma((2.0 * i + 1.0) * inv_dx, surf, Wv * S);
       size_t gi = ((size_t)v * N + ge) * Q + i;
       double o;
-      if (A.s == 0) o = A.w0[gi] + I.dt * r;
-      else if (A.s == 1) o = 0.75 * A.w0[gi] + 0.25 * (wi[i] + I.dt * r);
-      else o = (1.0 / 3.0) * A.w0[gi] + (2.0 / 3.0) * (wi[i] + I.dt * r);
+      if (A.s == 0) o = fma(I.dt, r, A.w0[gi]);
+      else if (A.s == 1) o = fma(0.25, fma(I.dt, r, wi[i]), 0.75 * A.w0[gi]);
+      else o = fma(2.0 / 3.0, fma(I.dt, r, wi[i]), (1.0 / 3.0) * A.w0[gi]);
       out[i] = o;
       A.wout[gi] = o;
+      A.wnext[gi] = o;
     }
     if (slot_ok) {
       int pr = I.pf_of_right[ge], pl = I.pf_of_left[ge];
@@ -236,208 +244,228 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, Inst I, StageArgs A)
   }
 }
 
-// Access to a neighbour block for the limiter: the pre-limit field, the AT
-// extrapolation of the neighbour's pre-limit history (Eq. 11), or a boundary ghost.
-struct Nb {
-  const double *direct;     // pointer to variable 0, mode 0 of the element; stride N*Q per var
-  size_t vstride;
-  const double *lev[MAXO];  // ring blocks (stride Q per var)
-  double c[MAXO];
-  int nlev;
-  int ghost;                // 0 none, 1 mirror (reflecting wall)
-  __device__ inline double get(int v, int j, int Q) const {
-    if (nlev > 0) {
-      double acc = 0.0;
-      for (int m = 0; m < nlev; ++m) acc += c[m] * lev[m][v * Q + j];
-      return acc;
-    }
-    double x = direct[v * vstride + j];
-    if (ghost == 1) {
-      double sg = (j & 1) ? -1.0 : 1.0;
-      if (v == 0) sg = -sg;
-      x *= sg;
-    }
-    return x;
-  }
-};
-
 __device__ inline double minmod3(double a, double b, double c) {
   if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
   if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
   return 0.0;
 }
 
-// Eigen-structure of the frozen Jacobian at the cell average (Sec. 3.3):
-// right vectors r_-/+ = (u -/+ a, H -/+ u a, Y), species r_k = (u, u^2 - phi_k/g, e_k),
-// left vectors l_-/+ = (gradP -/+ a (1, 0, -u..-u)) / (2 a^2), l_k = e_k - Y_k gradP / a^2,
-// gradP = (-u g, g, phi_1..phi_ns), g = gamma - 1,
-// phi_k = g (u^2/2 - e_k) + R_u T / W_k.
-template <int Q>
-__global__ void __launch_bounds__(128) limiter_kernel(Mech M, Inst I, LimArgs A) {
+// Shared memory (doubles) per element of the limiter: the element and its two
+// neighbours, the limited characteristic modes, gradP.w, the partial-density
+// sums and momenta of the three blocks, the per-species phi_k, two mode sums.
+__host__ __device__ inline int limiter_elem_doubles(int nv, int ns, int Q) {
+  return 3 * nv * Q + nv * Q + 3 * 3 * Q + ns + 2 * Q;
+}
+constexpr int LIM_WARPS = 8;
+
+// Troubled-cell indicator and (AT-)WENO limiter (Sec. 3.3, Eq. 9-11), a group of
+// G lanes per element (G = 16 when nv <= 16, else 32).
+// Eigen-structure of the frozen Jacobian at the cell average: right vectors
+// r_-/+ = (u -/+ a, H -/+ u a, Y), species r_k = (u, u^2 - phi_k/g, e_k); left
+// vectors l_-/+ = (gradP -/+ a (1, 0, -u..-u)) / (2 a^2), l_k = e_k - Y_k gradP/a^2,
+// gradP = (-u g, g, phi_1..phi_ns), g = gamma - 1, phi_k = g (u^2/2 - e_k) + R T / W_k.
+// Every characteristic value is written in one branch-free form,
+// v = A gradP.w + B (rho u)_w + C (sum rho Y)_w + D (rho Y_k)_w,
+// with (A, B, C, D) = (1/2a^2, -/+ a/2a^2, +/- a u/2a^2, 0) for the acoustic fields
+// and (-Y_k/a^2, 0, 0, 1) for species k, so that all lanes run the same FP64 code.
+// The stage kernel has already written the pre-limit values into the output;
+// only troubled cells are rewritten here.
+template <int Q, int G>
+__global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, Inst I, LimArgs A) {
+  extern __shared__ __align__(16) double lsm[];
   const Basis &B = c_basis[Q - 2];
   const int N = I.n_elem, nv = I.nv, ns = M.ns;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gl = lane % G, gw = lane / G;
+  constexpr int EPW = 32 / G;
+  const int slot = warp * EPW + gw;
+  const int e = blockIdx.x * (LIM_WARPS * EPW) + slot;
+  const bool valid = e < N;
+  const unsigned FULL = 0xffffffffu;
+  const unsigned gmask = (G == 32) ? FULL : (0xffffu << (16 * gw));
   const size_t VS = (size_t)N * Q;
-  const double *own = A.wpre + (size_t)e * Q;
+  const int NB = nv * Q;
+  double *blk = lsm + (size_t)slot * limiter_elem_doubles(nv, ns, Q);  // [3][nv][Q]
+  double *vlim = blk + 3 * NB;                                          // [nv][Q]
+  double *gpv = vlim + NB;                                              // [3][Q]
+  double *rsv = gpv + 3 * Q;                                            // [3][Q]
+  double *mmv = rsv + 3 * Q;                                            // [3][Q]
+  double *phi = mmv + 3 * Q;                                            // [ns]
+  double *sums = phi + ns;                                              // [2][Q]
   const bool periodic = (I.bc_left == ADG_BC_PERIODIC);
-  // neighbours
-  Nb nb[2];
-  for (int d = 0; d < 2; ++d) {
-    Nb &x = nb[d];
-    x.nlev = 0;
-    x.ghost = 0;
-    x.vstride = VS;
-    int pf = d == 0 ? I.pf_of_left[e] : I.pf_of_right[e];
-    int k = (pf >= 0) ? effective_delay(I, A.n, pf) : 0;
-    if (k > 0) {
-      int side = d == 0 ? 0 : 1;
-      x.nlev = I.at_order;
-      for (int m = 0; m < I.at_order; ++m) {
-        x.lev[m] = I.ring_pre + ring_block(I, A.n - k - m, A.s, pf, side);
-        x.c[m] = I.at[k][m];
-      }
-      x.direct = nullptr;
-      continue;
-    }
-    int nbe = d == 0 ? e - 1 : e + 1;
-    if (nbe < 0 || nbe >= N) {
-      if (periodic) {
-        nbe = (nbe + N) % N;
-      } else {
-        nbe = e;
-        int bc = d == 0 ? I.bc_left : I.bc_right;
-        x.ghost = (bc == ADG_BC_REFLECT) ? 1 : 0;
-      }
-    }
-    x.direct = A.wpre + (size_t)nbe * Q;
-  }
 
-  // cell average and eigen-quantities
-  double wbar[2];
-  wbar[0] = own[0];
-  wbar[1] = own[VS];
-  double rho = 0.0, qsum = 0.0, cv = 0.0, Rm = 0.0, cpm = 0.0;
+  // 1. the element (block 0) and its neighbours (1 left, 2 right): the pre-limit
+  //    field, the AT extrapolation of the neighbour's pre-limit history across a
+  //    delayed PE face (Eq. 11), or a boundary ghost
+  if (valid) {
+    for (int d = 0; d < 3; ++d) {
+      double *dst = blk + d * NB;
+      int src = e, ghost = 0, k = 0, pf = -1;
+      if (d > 0) {
+        pf = d == 1 ? I.pf_of_left[e] : I.pf_of_right[e];
+        k = (pf >= 0) ? effective_delay(I, A.n, pf) : 0;
+        src = d == 1 ? e - 1 : e + 1;
+        if (src < 0 || src >= N) {
+          if (periodic) {
+            src = (src + N) % N;
+          } else {
+            src = e;
+            ghost = ((d == 1 ? I.bc_left : I.bc_right) == ADG_BC_REFLECT) ? 1 : 0;
+          }
+        }
+      }
+      if (k > 0) {
+        int side = d == 1 ? 0 : 1;
+        for (int t = gl; t < NB; t += G) {
+          double acc = 0.0;
+          for (int m = 0; m < I.at_order; ++m)
+            acc += I.at[k][m] * I.ring_pre[ring_block(I, A.n - k - m, A.s, pf, side) + t];
+          dst[t] = acc;
+        }
+      } else {
+        for (int t = gl; t < NB; t += G) {
+          int v = t / Q, j = t - v * Q;
+          double x = A.wpre[(size_t)v * VS + (size_t)src * Q + j];
+          if (ghost && (((j & 1) != 0) != (v == 0))) x = -x;
+          dst[t] = x;
+        }
+      }
+    }
+  }
+  __syncwarp();
+
+  // 2. cell average: thermo and eigen-quantities (species sums split over lanes)
   const double *qW = M.sp + SP_QW * ns, *cvW = M.sp + SP_CVW * ns;
   const double *RW = M.sp + SP_RW * ns, *cpW = M.sp + SP_CPW * ns;
-  for (int i = 0; i < ns; ++i) {
-    double r = own[(2 + i) * VS];
-    rho += r;
-    qsum += r * qW[i];
-    cv += r * cvW[i];
-    Rm += r * RW[i];
-    cpm += r * cpW[i];
+  double rho = 0.0, qsum = 0.0, cv = 0.0, Rm = 0.0, cpm = 0.0;
+  if (valid)
+    for (int i = gl; i < ns; i += G) {
+      double r = blk[(2 + i) * Q];
+      rho += r;
+      qsum = fma(r, qW[i], qsum);
+      cv = fma(r, cvW[i], cv);
+      Rm = fma(r, RW[i], Rm);
+      cpm = fma(r, cpW[i], cpm);
+    }
+  for (int o = G / 2; o > 0; o >>= 1) {
+    rho += __shfl_xor_sync(FULL, rho, o, G);
+    qsum += __shfl_xor_sync(FULL, qsum, o, G);
+    cv += __shfl_xor_sync(FULL, cv, o, G);
+    Rm += __shfl_xor_sync(FULL, Rm, o, G);
+    cpm += __shfl_xor_sync(FULL, cpm, o, G);
   }
-  const double u = wbar[0] / rho;
-  const double T = (wbar[1] - 0.5 * wbar[0] * wbar[0] / rho - qsum) / cv;
+  if (!valid) {
+    rho = 1.0;
+    cv = 1.0;
+    cpm = 2.0;
+    Rm = 1.0;
+  }
+  const double irho = 1.0 / rho, icv = 1.0 / cv;
+  const double m0 = valid ? blk[0] : 0.0, E0 = valid ? blk[Q] : 1.0;
+  const double u = m0 * irho;
+  const double T = (E0 - 0.5 * m0 * u - qsum) * icv;
   const double P = T * Rm;
-  const double g = cpm / cv - 1.0;
-  const double a = sqrt(cpm / cv * P / rho);
-  const double H = (wbar[1] + P) / rho;
+  const double gam = cpm * icv, g = gam - 1.0;
+  const double a = sqrt(gam * P * irho);
+  const double H = (E0 + P) * irho;
   const double ia2 = 1.0 / (a * a);
-  if (!(rho > 0.0) || !(T > 0.0) || !isfinite(T)) {
+  if (valid && gl == 0 && (!(rho > 0.0) || !(T > 0.0) || !isfinite(T)))
     report_error(I, ADG_ERR_NONPHYSICAL, e, A.s, A.n);
+  if (valid) {
+    for (int i = gl; i < ns; i += G)
+      phi[i] = fma(g, fma(-cvW[i], T, 0.5 * u * u - qW[i]), T * RW[i]);
   }
-  // gradP . w, sum of partial densities and momentum, for every mode of the three
-  // blocks (0 own, 1 left, 2 right)
-  double gp[3][Q], rs[3][Q], mm[3][Q];
-  for (int b = 0; b < 3; ++b)
-    for (int j = 0; j < Q; ++j) {
-      double m_, E_;
-      if (b == 0) {
-        m_ = own[j];
-        E_ = own[VS + j];
-      } else {
-        m_ = nb[b - 1].get(0, j, Q);
-        E_ = nb[b - 1].get(1, j, Q);
-      }
-      double acc = -u * g * m_ + g * E_, sr = 0.0;
+  __syncwarp();
+  if (valid)
+    for (int t = gl; t < 3 * Q; t += G) {
+      int b = t / Q, j = t - b * Q;
+      const double *x = blk + b * NB;
+      double acc = g * fma(-u, x[j], x[Q + j]), sr = 0.0;
       for (int i = 0; i < ns; ++i) {
-        double r = (b == 0) ? own[(2 + i) * VS + j] : nb[b - 1].get(2 + i, j, Q);
-        double phi = g * (0.5 * u * u - (qW[i] + cvW[i] * T)) + T * RW[i];
-        acc += phi * r;
+        double r = x[(2 + i) * Q + j];
+        acc = fma(phi[i], r, acc);
         sr += r;
       }
-      gp[b][j] = acc;
-      rs[b][j] = sr;
-      mm[b][j] = m_;
+      gpv[t] = acc;
+      rsv[t] = sr;
+      mmv[t] = x[j];
     }
-  // per-variable magnitudes of the noise floor
-  const double sig0 = rho * a + fabs(wbar[0]), sig1 = fabs(wbar[1]), sigr = rho;
-  const double tvb = I.tvb;
-  const double tau = 1e-10;
-  // field values of a block-mode combination: v_k = l_k . w
-  auto acoustic = [&](int b, int j, double sgn) {
-    return (gp[b][j] + sgn * a * (mm[b][j] - u * rs[b][j])) * 0.5 * ia2;
+  __syncwarp();
+
+  // coefficients of field k and its value for block b, mode j
+  const double ha2 = 0.5 * ia2;
+  auto coef = [&](int k, double &cA, double &cB, double &cC, double &cD, int &ri) {
+    bool ac = (k == 0) || (k == nv - 1);
+    double sgn = (k == 0) ? -1.0 : 1.0;
+    ri = ac ? 0 : k - 1;
+    double Yk = ac ? 0.0 : blk[(2 + ri) * Q] * irho;
+    cA = ac ? ha2 : -Yk * ia2;
+    cB = ac ? sgn * a * ha2 : 0.0;
+    cC = ac ? -sgn * a * u * ha2 : 0.0;
+    cD = ac ? 0.0 : 1.0;
   };
-  // gradP magnitudes for the floor of the acoustic and species fields
-  double sum_abs_grad = fabs(u * g) * sig0 + fabs(g) * sig1;
-  bool troubled = false;
-  // acoustic fields
-  for (int f = 0; f < 2 && !troubled; ++f) {
-    double sgn = f == 0 ? -1.0 : 1.0;
-    double vb = acoustic(0, 0, sgn), vp = 0.0, vm = 0.0;
-    for (int j = 0; j < Q; ++j) {
-      double x = acoustic(0, j, sgn);
-      vp += x;
-      vm += (j & 1) ? -x : x;
+  auto val = [&](double cA, double cB, double cC, double cD, int ri, int b, int j) {
+    return fma(cA, gpv[b * Q + j],
+               fma(cB, mmv[b * Q + j], fma(cC, rsv[b * Q + j], cD * blk[b * NB + (2 + ri) * Q + j])));
+  };
+
+  // 3. indicator: the lanes of a group test the fields
+  const double sig0 = fma(rho, a, fabs(m0)), sig1 = fabs(E0), sigr = rho;
+  const double tvb = I.tvb, tau = 1e-10;
+  bool mine = false;
+  if (valid)
+    for (int k = gl; k < nv; k += G) {
+      double cA, cB, cC, cD;
+      int ri;
+      coef(k, cA, cB, cC, cD, ri);
+      double vb = val(cA, cB, cC, cD, ri, 0, 0), vp = vb, vm = vb;
+#pragma unroll
+      for (int j = 1; j < Q; ++j) {
+        double x = val(cA, cB, cC, cD, ri, 0, j);
+        vp += x;
+        vm += (j & 1) ? -x : x;
+      }
+      double vL = val(cA, cB, cC, cD, ri, 1, 0), vR = val(cA, cB, cC, cD, ri, 2, 0);
+      double scale = fabs(fma(cA, -u * g, cB)) * sig0 + fabs(cA * g) * sig1;
+      for (int i = 0; i < ns; ++i) {
+        double l = fma(cA, phi[i], cC) + ((i == ri) ? cD : 0.0);
+        scale = fma(fabs(l), sigr, scale);
+      }
+      double ut = vp - vb, utt = vb - vm, dp = vR - vb, dm = vb - vL;
+      double fl = tau * scale;
+      if (fabs(ut) > fl && fabs(ut) > tvb && minmod3(ut, dp, dm) != ut) mine = true;
+      if (fabs(utt) > fl && fabs(utt) > tvb && minmod3(utt, dp, dm) != utt) mine = true;
     }
-    double vL = acoustic(1, 0, sgn), vR = acoustic(2, 0, sgn);
-    double scale = (fabs(-u * g + sgn * a) * sig0 + fabs(g) * sig1) * 0.5 * ia2;
-    for (int i = 0; i < ns; ++i) {
-      double phi = g * (0.5 * u * u - (qW[i] + cvW[i] * T)) + T * RW[i];
-      scale += fabs(phi - sgn * a * u) * sigr * 0.5 * ia2;
-    }
-    double ut = vp - vb, utt = vb - vm, dp = vR - vb, dm = vb - vL;
-    double fl = tau * scale;
-    if (fabs(ut) > fl && fabs(ut) > tvb && minmod3(ut, dp, dm) != ut) troubled = true;
-    if (fabs(utt) > fl && fabs(utt) > tvb && minmod3(utt, dp, dm) != utt) troubled = true;
+  unsigned bal = __ballot_sync(FULL, mine) & gmask;
+  const bool troubled = valid && bal != 0u && I.limiter != ADG_LIM_NONE;
+  if (valid && gl == 0) {
+    I.flags[(size_t)A.s * N + e] = troubled ? 1 : 0;
+    if (troubled) I.count[e] += 1;
   }
-  // species fields
-  for (int k = 0; k < ns && !troubled; ++k) {
-    double Yk = own[(2 + k) * VS] / rho;
-    auto fieldv = [&](int b, int j) {
-      double r = (b == 0) ? own[(2 + k) * VS + j] : nb[b - 1].get(2 + k, j, Q);
-      return r - Yk * gp[b][j] * ia2;
-    };
-    double vb = fieldv(0, 0), vp = 0.0, vm = 0.0;
-    for (int j = 0; j < Q; ++j) {
-      double x = fieldv(0, j);
-      vp += x;
-      vm += (j & 1) ? -x : x;
-    }
-    double vL = fieldv(1, 0), vR = fieldv(2, 0);
-    double scale = fabs(Yk) * ia2 * sum_abs_grad;
-    for (int i = 0; i < ns; ++i) {
-      double phi = g * (0.5 * u * u - (qW[i] + cvW[i] * T)) + T * RW[i];
-      double l = (i == k ? 1.0 : 0.0) - Yk * phi * ia2;
-      scale += fabs(l) * sigr;
-    }
-    double ut = vp - vb, utt = vb - vm, dp = vR - vb, dm = vb - vL;
-    double fl = tau * scale;
-    if (fabs(ut) > fl && fabs(ut) > tvb && minmod3(ut, dp, dm) != ut) troubled = true;
-    if (fabs(utt) > fl && fabs(utt) > tvb && minmod3(utt, dp, dm) != utt) troubled = true;
-  }
-  if (I.limiter == ADG_LIM_NONE) troubled = false;
-  I.flags[(size_t)A.s * N + e] = troubled ? 1 : 0;
-  if (troubled) I.count[e] += 1;
-  double *out = A.wout + (size_t)e * Q;
-  if (!troubled) {
-    for (int v = 0; v < nv; ++v)
-      for (int j = 0; j < Q; ++j) out[v * VS + j] = own[v * VS + j];
-    return;
-  }
-  // WENO (Eq. 9-10) in the characteristic fields, reconstructed with R
-  const double gam[3] = {0.001, 0.998, 0.001};
+  if (!troubled) return;
+
+  // 4. WENO (Eq. 9-10) per characteristic field, the group's lanes over fields
+  const double gmw[3] = {0.001, 0.998, 0.001};
   const double eps = 1e-6;
-  auto weno_field = [&](double *vo, double *vl0, double *vr0, double *vlim) {
-    // continue the neighbours into this cell, replace their mean by the own mean
-    double vl[Q], vr[Q];
+  for (int k = gl; k < nv; k += G) {
+    double cA, cB, cC, cD;
+    int ri;
+    coef(k, cA, cB, cC, cD, ri);
+    double vo[Q], vl0[Q], vr0[Q], vl[Q], vr[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      vo[j] = val(cA, cB, cC, cD, ri, 0, j);
+      vl0[j] = val(cA, cB, cC, cD, ri, 1, j);
+      vr0[j] = val(cA, cB, cC, cD, ri, 2, j);
+    }
+    // neighbours continued into this cell, their mean replaced by the own mean
+#pragma unroll
     for (int i = 0; i < Q; ++i) {
       double al = 0.0, ar = 0.0;
+#pragma unroll
       for (int j = 0; j < Q; ++j) {
-        al += B.Sl[i][j] * vl0[j];
-        ar += B.Sr[i][j] * vr0[j];
+        al = fma(B.Sl[i][j], vl0[j], al);
+        ar = fma(B.Sr[i][j], vr0[j], ar);
       }
       vl[i] = al;
       vr[i] = ar;
@@ -445,65 +473,49 @@ __global__ void __launch_bounds__(128) limiter_kernel(Mech M, Inst I, LimArgs A)
     vl[0] = vo[0];
     vr[0] = vo[0];
     double be[3] = {0.0, 0.0, 0.0};
-    for (int i = 0; i < Q; ++i)
-      for (int j = 0; j < Q; ++j) {
-        be[0] += vl[i] * B.B[i][j] * vl[j];
-        be[1] += vo[i] * B.B[i][j] * vo[j];
-        be[2] += vr[i] * B.B[i][j] * vr[j];
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+#pragma unroll
+      for (int j = 1; j < Q; ++j) {
+        be[0] = fma(vl[i] * B.B[i][j], vl[j], be[0]);
+        be[1] = fma(vo[i] * B.B[i][j], vo[j], be[1]);
+        be[2] = fma(vr[i] * B.B[i][j], vr[j], be[2]);
       }
     double wt[3], sw = 0.0;
     for (int t = 0; t < 3; ++t) {
-      wt[t] = gam[t] / ((eps + be[t]) * (eps + be[t]));
+      double d = eps + be[t];
+      wt[t] = gmw[t] / (d * d);
       sw += wt[t];
     }
-    for (int t = 0; t < 3; ++t) wt[t] /= sw;
-    vlim[0] = vo[0];
-    for (int i = 1; i < Q; ++i) vlim[i] = wt[0] * vl[i] + wt[1] * vo[i] + wt[2] * vr[i];
-  };
-  double lm[Q], lp[Q];
-  {
-    double vo[Q], vl[Q], vr[Q];
-    for (int j = 0; j < Q; ++j) {
-      vo[j] = acoustic(0, j, -1.0);
-      vl[j] = acoustic(1, j, -1.0);
-      vr[j] = acoustic(2, j, -1.0);
-    }
-    weno_field(vo, vl, vr, lm);
-    for (int j = 0; j < Q; ++j) {
-      vo[j] = acoustic(0, j, 1.0);
-      vl[j] = acoustic(1, j, 1.0);
-      vr[j] = acoustic(2, j, 1.0);
-    }
-    weno_field(vo, vl, vr, lp);
+    double isw = 1.0 / sw;
+    vlim[k * Q] = vo[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+      vlim[k * Q + i] = (wt[0] * vl[i] + wt[1] * vo[i] + wt[2] * vr[i]) * isw;
   }
-  double sm_[Q], se_[Q];
-  for (int i = 0; i < Q; ++i) {
-    sm_[i] = 0.0;
-    se_[i] = 0.0;
-  }
-  for (int k = 0; k < ns; ++k) {
-    double Yk = own[(2 + k) * VS] / rho;
-    double ek = qW[k] + cvW[k] * T;
-    double phik = g * (0.5 * u * u - ek) + T * RW[k];
-    double vo[Q], vl[Q], vr[Q], lim[Q];
-    for (int j = 0; j < Q; ++j) {
-      vo[j] = own[(2 + k) * VS + j] - Yk * gp[0][j] * ia2;
-      vl[j] = nb[0].get(2 + k, j, Q) - Yk * gp[1][j] * ia2;
-      vr[j] = nb[1].get(2 + k, j, Q) - Yk * gp[2][j] * ia2;
+  __syncwarp(gmask);
+  // 5. back to conserved variables with R (modes >= 1; the cell average is kept)
+  for (int i = gl; i < Q; i += G) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = 1; k < nv - 1; ++k) {
+      double x = vlim[k * Q + i];
+      s1 += x;
+      s2 = fma(x, u * u - phi[k - 1] / g, s2);
     }
-    weno_field(vo, vl, vr, lim);
-    out[(2 + k) * VS] = own[(2 + k) * VS];
-    for (int i = 1; i < Q; ++i) {
-      out[(2 + k) * VS + i] = (lm[i] + lp[i]) * Yk + lim[i];
-      sm_[i] += lim[i];
-      se_[i] += lim[i] * (u * u - phik / g);
-    }
+    sums[i] = s1;
+    sums[Q + i] = s2;
   }
-  out[0] = own[0];
-  out[VS] = own[VS];
-  for (int i = 1; i < Q; ++i) {
-    out[i] = lm[i] * (u - a) + lp[i] * (u + a) + u * sm_[i];
-    out[VS + i] = lm[i] * (H - u * a) + lp[i] * (H + u * a) + se_[i];
+  __syncwarp(gmask);
+  double *out = A.wout + (size_t)e * Q;
+  for (int t = gl; t < NB; t += G) {
+    int v = t / Q, i = t - v * Q;
+    if (i == 0) continue;
+    double lm = vlim[i], lp = vlim[(nv - 1) * Q + i];
+    double o;
+    if (v == 0) o = lm * (u - a) + lp * (u + a) + u * sums[i];
+    else if (v == 1) o = lm * (H - u * a) + lp * (H + u * a) + sums[Q + i];
+    else o = (lm + lp) * (blk[v * Q] * irho) + vlim[(v - 1) * Q + i];
+    out[(size_t)v * VS + i] = o;
   }
 }
 
@@ -605,16 +617,39 @@ cudaError_t launch_stage(const Mech &M, const Inst &I, const StageArgs &A, cudaS
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_limiter(const Mech &M, const Inst &I, const LimArgs &A, cudaStream_t st) {
-  int nblk = (I.n_elem + 127) / 128;
-  switch (I.p + 1) {
-    case 2: limiter_kernel<2><<<nblk, 128, 0, st>>>(M, I, A); break;
-    case 3: limiter_kernel<3><<<nblk, 128, 0, st>>>(M, I, A); break;
-    case 4: limiter_kernel<4><<<nblk, 128, 0, st>>>(M, I, A); break;
-    case 5: limiter_kernel<5><<<nblk, 128, 0, st>>>(M, I, A); break;
-    default: return cudaErrorInvalidValue;
+template <int Q, int G>
+static cudaError_t launch_limiter_qg(const Mech &M, const Inst &I, const LimArgs &A,
+                                     cudaStream_t st) {
+  constexpr int EPW = 32 / G;
+  size_t smem = (size_t)LIM_WARPS * EPW * limiter_elem_doubles(I.nv, M.ns, Q) * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(limiter_kernel<Q, G>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
   }
+  int per = LIM_WARPS * EPW;
+  int nblk = (I.n_elem + per - 1) / per;
+  limiter_kernel<Q, G><<<nblk, 32 * LIM_WARPS, smem, st>>>(M, I, A);
   return cudaGetLastError();
+}
+
+template <int Q>
+static cudaError_t launch_limiter_q(const Mech &M, const Inst &I, const LimArgs &A,
+                                    cudaStream_t st) {
+  if (I.nv <= 16) return launch_limiter_qg<Q, 16>(M, I, A, st);
+  return launch_limiter_qg<Q, 32>(M, I, A, st);
+}
+
+cudaError_t launch_limiter(const Mech &M, const Inst &I, const LimArgs &A, cudaStream_t st) {
+  switch (I.p + 1) {
+    case 2: return launch_limiter_q<2>(M, I, A, st);
+    case 3: return launch_limiter_q<3>(M, I, A, st);
+    case 4: return launch_limiter_q<4>(M, I, A, st);
+    case 5: return launch_limiter_q<5>(M, I, A, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_project(const Mech &M, const Inst &I, const double *prim, double *w,

@@ -29,7 +29,9 @@ struct ExpTable {
 // exp(x) with the table in shared memory (tab). Falls back to the library exp
 // outside |x| <= 700, where the exponent-field scaling could leave the range.
 __device__ __forceinline__ double fexp(double x, const ExpTable &tab) {
-  if (!(fabs(x) <= EXP_MAX_ARG)) return exp(x);
+  // |x| <= 700 tested on the high word (0x4085E000 is that of 700.0), off the FP64 pipe;
+  // NaN and infinities take the library path too
+  if ((__double2hiint(x) & 0x7fffffff) > 0x4085E000) return exp(x);
   double t = fma(x, EXP_INV_L, EXP_SHIFTER);
   double nd = t - EXP_SHIFTER;
   int n = (int)(__double2loint(t));          // the low mantissa bits hold N

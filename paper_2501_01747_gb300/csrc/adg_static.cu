@@ -95,6 +95,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   size_t o_err = cur.take(sizeof(int) * 4);
   size_t st = (size_t)nv * N * Q;
   size_t o_wa = cur.take(sizeof(double) * st);
+  size_t o_wb = cur.take(sizeof(double) * st);
   size_t o_wpre = cur.take(sizeof(double) * st);
   size_t rs = (size_t)depth * 3 * (npf > 0 ? npf : 1) * 2 * nv * Q;
   size_t o_rin = cur.take(sizeof(double) * rs);
@@ -144,10 +145,11 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
       if (r != f) {
         if (x == NET) return ADG_ERR_ARG;
         R.xs[x] = (uint8_t)i;
-        R.xn[x++] = (int8_t)(r - f);
+        R.xc[x++] = (double)(r - f);
         dnu += r - f;
       }
     }
+    R.nx = (uint8_t)x;
     R.dnu = (double)dnu;
   }
 
@@ -213,6 +215,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
     }
   I.wn = w_out_dev;
   I.wa = (double *)(base + o_wa);
+  I.wb = (double *)(base + o_wb);
   I.wpre = (double *)(base + o_wpre);
   I.ring_in = (double *)(base + o_rin);
   I.ring_pre = (double *)(base + o_rpre);
@@ -240,22 +243,26 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   int TE = stage_tile(Q, nv, ns, nr);
   int target = (N + 2 * 152 - 1) / (2 * 152);
   if (target < TE) TE = target < 4 ? 4 : target;
+  double *bufs[4] = {I.wn, I.wa, I.wb, I.wn};
   for (int64_t n = 0; n < n_steps; ++n) {
     for (int stg = 0; stg < 3; ++stg) {
       StageArgs A;
-      A.win = (stg == 0) ? I.wn : I.wa;
+      A.win = bufs[stg];
       A.w0 = I.wn;
       A.wout = I.wpre;
+      A.wnext = bufs[stg + 1];
       A.s = stg;
       A.n = n;
       A.TE = TE;
       NA_CK(launch_stage(M, I, A, s));
-      LimArgs L;
-      L.wpre = I.wpre;
-      L.wout = (stg == 2) ? I.wn : I.wa;
-      L.s = stg;
-      L.n = n;
-      NA_CK(launch_limiter(M, I, L, s));
+      if (I.limiter != ADG_LIM_NONE) {
+        LimArgs L;
+        L.wpre = I.wpre;
+        L.wout = bufs[stg + 1];
+        L.s = stg;
+        L.n = n;
+        NA_CK(launch_limiter(M, I, L, s));
+      }
     }
   }
 #undef NA_CK
