@@ -152,13 +152,26 @@ int64_t adg_steps_done(const adg_ctx *ctx, int instance);
  * n_pe - 1 (bounded), 0 when n_pe == 1. */
 int adg_delay_table(const adg_config *cfg, int64_t step0, int n_steps, uint8_t *out_host);
 
-/* Per-kernel timing with CUDA events recorded around every launch on the
- * launching stream (on = 1 starts a new measurement). adg_kernel_times
- * synchronises and returns, per kernel kind (0: stage RHS/update kernel,
- * 1: limiter kernel), the summed milliseconds and launch counts since
- * enabling; ms and launches point to arrays of 2. */
+/* Per-kernel timing (on = 1 starts a new measurement). While it is on, adg_step
+ * runs a variant of the step graph with a CUDA event pair around every kernel,
+ * waits for each step, and adds the kernels' times up; adg_step is then
+ * synchronous. adg_kernel_times returns, per kind (0: stage RHS/update kernel,
+ * 1: limiter kernel, 2: whole step from the graph's first to its last node),
+ * the summed milliseconds and counts since enabling; ms and launches point to
+ * arrays of 3. Without timing, adg_step replays a captured CUDA graph of the
+ * step and returns at once. */
 int adg_enable_kernel_timing(adg_ctx *ctx, int on);
 int adg_kernel_times(adg_ctx *ctx, double *ms, int64_t *launches);
+
+/* Autotuner of the launch configuration (elements per stage tile and chemistry
+ * chunks per Gauss point, per group of instances of equal degree): times the
+ * stage kernel for every candidate that fits in shared memory on `stream`,
+ * keeps the fastest and drops the captured step graphs. The trajectory is not
+ * changed (the trial launches only rewrite buffers the next step rewrites).
+ * Synchronous. adg_get_tuning fills tuning[4 * g + {0,1,2,3}] with the degree,
+ * tile elements, chunks and tile count of group g (at most ADG_MAX_P groups). */
+int adg_autotune(adg_ctx *ctx, void *stream);
+int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning);
 
 /* Number of kernel launches one adg_step(ctx, 1, ...) enqueues. */
 int adg_launches_per_step(const adg_ctx *ctx);

@@ -98,7 +98,7 @@ EXPORTS = ["adg_workspace_bytes", "adg_create", "adg_destroy", "adg_set_primitiv
            "adg_step", "adg_status", "adg_get_flags", "adg_get_temperature", "adg_steps_done",
            "adg_delay_table", "adg_launches_per_step", "adg_error_string",
            "adg_write_state", "adg_read_state", "adg_enable_kernel_timing",
-           "adg_kernel_times", "adg_step_noalloc"]
+           "adg_kernel_times", "adg_step_noalloc", "adg_autotune", "adg_get_tuning"]
 
 
 def lib(path: str | None = None):
@@ -135,6 +135,8 @@ def lib(path: str | None = None):
     L.adg_kernel_times.argtypes = [vp, d, C.POINTER(C.c_int64)]
     L.adg_step_noalloc.argtypes = [C.POINTER(Mechanism_), C.POINTER(Config_), vp, vp, C.c_int,
                                    vp]
+    L.adg_autotune.argtypes = [vp, vp]
+    L.adg_get_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.adg_error_string.restype = C.c_char_p
     L.adg_error_string.argtypes = [C.c_int]
     _lib = L
@@ -325,11 +327,24 @@ class ADG:
         _check(self.L.adg_enable_kernel_timing(self.h, 1 if on else 0), "timing")
 
     def kernel_times(self):
-        ms = np.zeros(2)
-        n = np.zeros(2, dtype=np.int64)
+        """(ms, counts) per kind: stage kernel, limiter kernel, whole step."""
+        ms = np.zeros(3)
+        n = np.zeros(3, dtype=np.int64)
         _check(self.L.adg_kernel_times(self.h, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64))),
                "adg_kernel_times")
         return ms, n
+
+    def autotune(self, stream=None):
+        """Pick elements per tile and chemistry chunks by timing the stage kernel."""
+        _check(self.L.adg_autotune(self.h, self._stream(stream)), "adg_autotune")
+        return self.tuning()
+
+    def tuning(self):
+        n = C.c_int(0)
+        t = (C.c_int * 16)()
+        _check(self.L.adg_get_tuning(self.h, C.byref(n), t), "adg_get_tuning")
+        return [{"p": t[4 * g], "elements_per_tile": t[4 * g + 1], "chem_chunks": t[4 * g + 2],
+                 "tiles": t[4 * g + 3]} for g in range(n.value)]
 
     def launches_per_step(self):
         return int(self.L.adg_launches_per_step(self.h))

@@ -121,29 +121,56 @@ static void at_weights(int order, int k, double *c) {
 // ---------------------------------------------------------------------------
 
 struct InstHost {
-  Inst d;         // device view
-  int64_t n;      // steps done
-  int TE;
+  Inst d;         // device view (a copy lives in the device instance table)
+  int64_t n;      // steps done (host mirror of the device counter)
   double *prim;   // staging for projection / temperature
 };
 
+// Instances of one polynomial degree share the stage and limiter launches.
+struct Group {
+  int Q = 0;
+  int TE = 0;                   // elements per stage tile
+  int R = 1;                    // chemistry chunks per Gauss point
+  int O = 1;                    // largest AT order of the group
+  int n_tiles = 0, n_blocks = 0;
+  int2 *d_tiles = nullptr;      // (instance, first element) per stage CTA
+  int2 *d_blocks = nullptr;     // (instance, first element) per limiter CTA
+  bool any_limiter = false;
+};
+
 struct adg_ctx {
-  std::vector<cudaEvent_t> ev;   // timing events, pairs per launch
-  std::vector<int> ev_kind;
-  size_t ev_used;
-  bool timing;
+  std::vector<cudaEvent_t> ev;   // timing events: a pair around every kernel of one step
+  std::vector<int> ev_kind;      // kernel kind of each pair
+  size_t ev_used;                // events recorded while capturing the timing graph
+  bool timing;                   // steps run the timing graph and accumulate kernel times
+  bool capturing_timed;          // enqueue_step is recording event pairs
+  double kms[3];
+  int64_t kcount[3];
+  cudaEvent_t span[2];           // first and last node of the timing graph
+  cudaGraph_t tgraph;            // the step with event pairs
+  cudaGraphExec_t texec;
   int n_inst;
   int ns, nr;
   Mech mech;
   std::vector<InstHost> inst;
+  Group groups[ADG_MAX_P];
+  int n_groups;
+  Inst *d_insts;                 // device instance table
+  int64_t *d_steps;              // device step counters [n_inst]
   void *mem;
   bool owns_mem;
   size_t bytes;
   int *err_all;   // device error words [n_inst][4]
   cudaStream_t last_stream;
+  cudaStream_t cap_stream;       // private stream for graph capture
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  bool graph_ok;
 };
 
 namespace {
+
+constexpr int kMinTile = 2;   // smallest stage tile (elements) the autotuner tries
 
 struct Carver {
   char *base;
@@ -208,6 +235,45 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
   M.sp = (const double *)cv.take(sizeof(double) * SP_NFIELDS * ns);
   M.rx = (const Rxn *)cv.take(sizeof(Rxn) * nrr);
   ctx->err_all = (int *)cv.take(sizeof(int) * 4 * ctx->n_inst);
+  ctx->d_insts = (Inst *)cv.take(sizeof(Inst) * ctx->n_inst);
+  ctx->d_steps = (int64_t *)cv.take(sizeof(int64_t) * ctx->n_inst);
+  // groups of equal degree: tile sizes and tables
+  ctx->n_groups = 0;
+  const int epb = limiter_elems_per_block(nv);
+  for (int Q = 2; Q <= ADG_MAX_P + 1; ++Q) {
+    int64_t total = 0, tiles = 0, blocks = 0;
+    bool lim = false, any = false;
+    int O = 1;
+    for (int k = 0; k < ctx->n_inst; ++k)
+      if (cfgs[k].p + 1 == Q) {
+        any = true;
+        total += cfgs[k].n_elem;
+        lim = lim || cfgs[k].limiter != ADG_LIM_NONE;
+        if (cfgs[k].at_order > O) O = cfgs[k].at_order;
+      }
+    if (!any) continue;
+    Group &G = ctx->groups[ctx->n_groups++];
+    G.Q = Q;
+    G.O = O;
+    G.TE = stage_tile(Q, nv, ns, nr, 8, O);
+    // smaller tiles when the group would not fill two CTAs per SM
+    int64_t target = (total + 2 * 152 - 1) / (2 * 152);
+    if (target < G.TE) G.TE = target < 4 ? 4 : (int)target;
+    G.R = stage_chunks(G.TE, Q, nr);
+    int64_t max_tiles = 0;
+    for (int k = 0; k < ctx->n_inst; ++k)
+      if (cfgs[k].p + 1 == Q) {
+        tiles += (cfgs[k].n_elem + G.TE - 1) / G.TE;
+        max_tiles += (cfgs[k].n_elem + kMinTile - 1) / kMinTile;
+        blocks += (cfgs[k].n_elem + epb - 1) / epb;
+      }
+    G.n_tiles = (int)tiles;
+    G.n_blocks = (int)blocks;
+    G.any_limiter = lim;
+    // room for the tile table of the smallest tile the autotuner may pick
+    G.d_tiles = (int2 *)cv.take(sizeof(int2) * max_tiles);
+    G.d_blocks = (int2 *)cv.take(sizeof(int2) * blocks);
+  }
   for (int k = 0; k < ctx->n_inst; ++k) {
     const adg_config &c = cfgs[k];
     InstHost &h = ctx->inst[k];
@@ -218,9 +284,9 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
     I.wa = (double *)cv.take(sizeof(double) * st);
     I.wb = (double *)cv.take(sizeof(double) * st);
     I.wpre = (double *)cv.take(sizeof(double) * st);
-    size_t rs = (size_t)(c.max_delay + c.at_order) * 3 * (npf > 0 ? npf : 1) * 2 * nv * Q;
+    size_t rs = (size_t)(c.max_delay + c.at_order) * 3 * (npf > 0 ? npf : 1) * 2 * nv;
     I.ring_in = (double *)cv.take(sizeof(double) * rs);
-    I.ring_pre = (double *)cv.take(sizeof(double) * rs);
+    I.ring_pre = (double *)cv.take(sizeof(double) * rs * Q);
     I.flags = (uint8_t *)cv.take((size_t)3 * N);
     I.count = (int32_t *)cv.take(sizeof(int32_t) * N);
     I.pf_of_left = (const int *)cv.take(sizeof(int) * N);
@@ -235,6 +301,18 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
 thread_local char g_last_error[256];
 
 }  // namespace
+
+// Stage tile table of a group for its current tile size.
+static cudaError_t upload_tiles(adg_ctx *ctx, Group &G) {
+  std::vector<int2> tl;
+  for (int k = 0; k < ctx->n_inst; ++k) {
+    const Inst &I = ctx->inst[k].d;
+    if (I.p + 1 != G.Q) continue;
+    for (int e = 0; e < I.n_elem; e += G.TE) tl.push_back(make_int2(k, e));
+  }
+  G.n_tiles = (int)tl.size();
+  return cudaMemcpy(G.d_tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
+}
 
 extern "C" {
 
@@ -313,6 +391,16 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
   ctx->err_all = nullptr;
   ctx->ev_used = 0;
   ctx->timing = false;
+  ctx->capturing_timed = false;
+  ctx->kms[0] = ctx->kms[1] = ctx->kms[2] = 0.0;
+  ctx->kcount[0] = ctx->kcount[1] = ctx->kcount[2] = 0;
+  ctx->span[0] = ctx->span[1] = nullptr;
+  ctx->tgraph = nullptr;
+  ctx->texec = nullptr;
+  ctx->cap_stream = nullptr;
+  ctx->graph = nullptr;
+  ctx->exec = nullptr;
+  ctx->graph_ok = false;
   Carver dry{nullptr, 0, 0, true};
   size_t need = layout(ctx, cfgs, dry) + 256;
   if (workspace) {
@@ -435,12 +523,32 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
         cudaMemset(I.wn, 0, sizeof(double) * (size_t)nv * N * Q))
       rc2 = ADG_ERR_CUDA;
     h.n = 0;
-    h.TE = stage_tile(Q, nv, ns, nr);
-    // smaller tiles when the instance would not fill two CTAs per SM
-    int target = (N + 2 * 152 - 1) / (2 * 152);
-    if (target < h.TE) h.TE = target < 4 ? 4 : target;
+    I.step = ctx->d_steps + k;
+  }
+  if (rc2 == ADG_OK) {
+    std::vector<Inst> hi(n);
+    for (int k = 0; k < n; ++k) hi[k] = ctx->inst[k].d;
+    if (cudaMemcpy(ctx->d_insts, hi.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice) ||
+        cudaMemset(ctx->d_steps, 0, sizeof(int64_t) * n))
+      rc2 = ADG_ERR_CUDA;
+    const int epb = limiter_elems_per_block(nv);
+    for (int gi = 0; gi < ctx->n_groups && rc2 == ADG_OK; ++gi) {
+      Group &G = ctx->groups[gi];
+      std::vector<int2> bl;
+      for (int k = 0; k < n; ++k) {
+        if (cfgs[k].p + 1 != G.Q) continue;
+        for (int e = 0; e < cfgs[k].n_elem; e += epb) bl.push_back(make_int2(k, e));
+      }
+      if (upload_tiles(ctx, G) != cudaSuccess ||
+          cudaMemcpy(G.d_blocks, bl.data(), sizeof(int2) * bl.size(), cudaMemcpyHostToDevice))
+        rc2 = ADG_ERR_CUDA;
+    }
+    if (prepare_kernels(nv, ns, nr) != cudaSuccess) rc2 = ADG_ERR_CUDA;
+    if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      rc2 = ADG_ERR_CUDA;
   }
   if (rc2 != ADG_OK) {
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->owns_mem) cudaFree(ctx->mem);
     delete ctx;
     return rc2;
@@ -452,6 +560,13 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
 void adg_destroy(adg_ctx *ctx) {
   if (!ctx) return;
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+  if (ctx->texec) cudaGraphExecDestroy(ctx->texec);
+  for (cudaEvent_t e : ctx->span)
+    if (e) cudaEventDestroy(e);
+  if (ctx->tgraph) cudaGraphDestroy(ctx->tgraph);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->owns_mem) cudaFree(ctx->mem);
   delete ctx;
 }
@@ -460,11 +575,15 @@ static int inst_ok(adg_ctx *ctx, int k) {
   return ctx && k >= 0 && k < ctx->n_inst;
 }
 
-static void reset_history(adg_ctx *ctx, int k) {
+// Step counter to 0 (the history ring is then never read before it is written
+// again) and flags cleared.
+static cudaError_t reset_history(adg_ctx *ctx, int k, cudaStream_t st) {
   InstHost &h = ctx->inst[k];
   h.n = 0;
-  cudaMemset(h.d.count, 0, sizeof(int32_t) * h.d.n_elem);
-  cudaMemset(h.d.flags, 0, (size_t)3 * h.d.n_elem);
+  cudaError_t e = cudaMemsetAsync(ctx->d_steps + k, 0, sizeof(int64_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h.d.count, 0, sizeof(int32_t) * h.d.n_elem, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h.d.flags, 0, (size_t)3 * h.d.n_elem, st);
+  return e;
 }
 
 int adg_set_primitive(adg_ctx *ctx, int k, const double *prim) {
@@ -473,8 +592,8 @@ int adg_set_primitive(adg_ctx *ctx, int k, const double *prim) {
   size_t n = (size_t)(ctx->ns + 3) * h.d.n_elem * (h.d.p + 1);
   CK(cudaMemcpy(h.prim, prim, sizeof(double) * n, cudaMemcpyHostToDevice));
   CK(launch_project(ctx->mech, h.d, h.prim, h.d.wn, 0));
+  CK(reset_history(ctx, k, 0));
   CK(cudaDeviceSynchronize());
-  reset_history(ctx, k);
   return ADG_OK;
 }
 
@@ -483,8 +602,8 @@ int adg_set_state(adg_ctx *ctx, int k, const double *w) {
   InstHost &h = ctx->inst[k];
   size_t n = (size_t)h.d.nv * h.d.n_elem * (h.d.p + 1);
   CK(cudaMemcpyAsync(h.d.wn, w, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->last_stream));
+  CK(reset_history(ctx, k, ctx->last_stream));
   CK(cudaStreamSynchronize(ctx->last_stream));
-  reset_history(ctx, k);
   return ADG_OK;
 }
 
@@ -494,8 +613,7 @@ int adg_set_state_device(adg_ctx *ctx, int k, const double *w, void *stream) {
   size_t n = (size_t)h.d.nv * h.d.n_elem * (h.d.p + 1);
   CK(cudaMemcpyAsync(h.d.wn, w, sizeof(double) * n, cudaMemcpyDeviceToDevice,
                      (cudaStream_t)stream));
-  h.n = 0;
-  CK(cudaMemsetAsync(h.d.count, 0, sizeof(int32_t) * h.d.n_elem, (cudaStream_t)stream));
+  CK(reset_history(ctx, k, (cudaStream_t)stream));
   ctx->last_stream = (cudaStream_t)stream;
   return ADG_OK;
 }
@@ -518,94 +636,247 @@ int adg_get_state_device(adg_ctx *ctx, int k, double *w, void *stream) {
   return ADG_OK;
 }
 
-// Event pair around one launch when timing is on.
+// Event pair around one launch while the timing graph is captured.
 static cudaError_t timed_begin(adg_ctx *ctx, int kind, cudaStream_t st) {
-  if (!ctx->timing) return cudaSuccess;
-  if (ctx->ev_used + 2 > ctx->ev.size()) {
-    for (int t = 0; t < 256; ++t) {
-      cudaEvent_t e;
-      cudaError_t r = cudaEventCreate(&e);
-      if (r != cudaSuccess) return r;
-      ctx->ev.push_back(e);
-      ctx->ev_kind.push_back(0);
-    }
+  if (!ctx->capturing_timed) return cudaSuccess;
+  while (ctx->ev_used + 2 > ctx->ev.size()) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    ctx->ev.push_back(e);
+    ctx->ev_kind.push_back(0);
   }
   ctx->ev_kind[ctx->ev_used] = kind;
-  return cudaEventRecord(ctx->ev[ctx->ev_used], st);
+  // external record: an event node of the graph, readable after each replay
+  return cudaEventRecordWithFlags(ctx->ev[ctx->ev_used], st, cudaEventRecordExternal);
 }
 
 static cudaError_t timed_end(adg_ctx *ctx, cudaStream_t st) {
-  if (!ctx->timing) return cudaSuccess;
-  cudaError_t r = cudaEventRecord(ctx->ev[ctx->ev_used + 1], st);
+  if (!ctx->capturing_timed) return cudaSuccess;
+  cudaError_t r = cudaEventRecordWithFlags(ctx->ev[ctx->ev_used + 1], st, cudaEventRecordExternal);
   ctx->ev_used += 2;
   return r;
+}
+
+// One SSP-RK3 step of every instance: per stage, the stage kernel and the
+// limiter of every degree group, then the step counters advance.
+static int enqueue_step(adg_ctx *ctx, cudaStream_t st) {
+  for (int s = 0; s < 3; ++s) {
+    for (int gi = 0; gi < ctx->n_groups; ++gi) {
+      const Group &G = ctx->groups[gi];
+      StageArgs A;
+      A.insts = ctx->d_insts;
+      A.tiles = G.d_tiles;
+      A.s = s;
+      A.TE = G.TE;
+      A.R = G.R;
+      A.O = G.O;
+      CK(timed_begin(ctx, 0, st));
+      CK(launch_stage(ctx->mech, A, G.Q, G.n_tiles, st));
+      CK(timed_end(ctx, st));
+    }
+    for (int gi = 0; gi < ctx->n_groups; ++gi) {
+      const Group &G = ctx->groups[gi];
+      if (!G.any_limiter) continue;
+      LimArgs L;
+      L.insts = ctx->d_insts;
+      L.blocks = G.d_blocks;
+      L.s = s;
+      CK(timed_begin(ctx, 1, st));
+      CK(launch_limiter(ctx->mech, L, G.Q, ctx->ns + 2, G.n_blocks, st));
+      CK(timed_end(ctx, st));
+    }
+  }
+  CK(launch_advance(ctx->d_steps, ctx->n_inst, st));
+  return ADG_OK;
+}
+
+// The step as a CUDA graph, captured once on the context's private stream;
+// the timing variant records an event pair around every kernel.
+static int capture(adg_ctx *ctx, bool timed, cudaGraph_t *graph, cudaGraphExec_t *exec) {
+  ctx->capturing_timed = timed;
+  ctx->ev_used = 0;
+  if (timed && !ctx->span[0]) {
+    CK(cudaEventCreate(&ctx->span[0]));
+    CK(cudaEventCreate(&ctx->span[1]));
+  }
+  CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = ADG_OK;
+  if (timed && cudaEventRecordWithFlags(ctx->span[0], ctx->cap_stream,
+                                        cudaEventRecordExternal) != cudaSuccess)
+    rc = ADG_ERR_CUDA;
+  if (rc == ADG_OK) rc = enqueue_step(ctx, ctx->cap_stream);
+  if (rc == ADG_OK && timed &&
+      cudaEventRecordWithFlags(ctx->span[1], ctx->cap_stream, cudaEventRecordExternal) !=
+          cudaSuccess)
+    rc = ADG_ERR_CUDA;
+  // the capture always ends, so that the private stream is usable again
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  ctx->capturing_timed = false;
+  if (rc != ADG_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return rc != ADG_OK ? rc : cuda_fail(e);
+  }
+  e = cudaGraphInstantiate(exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e);
+  }
+  *graph = g;
+  return ADG_OK;
+}
+
+static int ensure_graph(adg_ctx *ctx) {
+  if (ctx->graph_ok) return ADG_OK;
+  int rc = capture(ctx, false, &ctx->graph, &ctx->exec);
+  if (rc == ADG_OK) ctx->graph_ok = true;
+  return rc;
 }
 
 int adg_step(adg_ctx *ctx, int n_steps, void *stream) {
   if (!ctx || n_steps < 0) return ADG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = st;
-  for (int it = 0; it < n_steps; ++it) {
-    for (int k = 0; k < ctx->n_inst; ++k) {
-      InstHost &h = ctx->inst[k];
-      Inst &I = h.d;
-      // stage inputs w^n -> wa -> wb -> w^n: a stage never writes the buffer
-      // whose halo other CTAs read in the same launch
-      double *bufs[4] = {I.wn, I.wa, I.wb, I.wn};
-      for (int s = 0; s < 3; ++s) {
+  if (n_steps == 0) return ADG_OK;
+  if (ctx->timing) {
+    // the timing graph, one step at a time: wait for it and add up its kernels
+    if (!ctx->texec) {
+      int rc = capture(ctx, true, &ctx->tgraph, &ctx->texec);
+      if (rc != ADG_OK) return rc;
+    }
+    for (int it = 0; it < n_steps; ++it) {
+      CK(cudaGraphLaunch(ctx->texec, st));
+      CK(cudaStreamSynchronize(st));
+      for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]));
+        ctx->kms[ctx->ev_kind[i]] += t;
+        ctx->kcount[ctx->ev_kind[i]] += 1;
+      }
+      float t = 0.0f;
+      CK(cudaEventElapsedTime(&t, ctx->span[0], ctx->span[1]));
+      ctx->kms[2] += t;
+      ctx->kcount[2] += 1;
+    }
+  } else {
+    int rc = ensure_graph(ctx);
+    if (rc != ADG_OK) return rc;
+    for (int it = 0; it < n_steps; ++it) CK(cudaGraphLaunch(ctx->exec, st));
+  }
+  for (InstHost &h : ctx->inst) h.n += n_steps;
+  return ADG_OK;
+}
+
+// Drop the captured graphs (after the launch configuration changed).
+static void drop_graphs(adg_ctx *ctx) {
+  if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  if (ctx->texec) cudaGraphExecDestroy(ctx->texec);
+  if (ctx->tgraph) cudaGraphDestroy(ctx->tgraph);
+  ctx->exec = ctx->texec = nullptr;
+  ctx->graph = ctx->tgraph = nullptr;
+  ctx->graph_ok = false;
+}
+
+int adg_autotune(adg_ctx *ctx, void *stream) {
+  if (!ctx) return ADG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaStreamSynchronize(ctx->last_stream));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int nv = ctx->ns + 2, ns = ctx->ns, nr = ctx->nr;
+  static const int kTE[] = {2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 32, 40, 48, 64, 96, 128};
+  static const int kR[] = {1, 2, 3, 4, 6, 8};
+  int rc = ADG_OK;
+  for (int gi = 0; gi < ctx->n_groups && rc == ADG_OK; ++gi) {
+    Group &G = ctx->groups[gi];
+    int bestTE = G.TE, bestR = G.R;
+    float best = 1e30f;
+    for (int te : kTE) {
+      if (te < kMinTile || te * G.Q > 256) continue;
+      for (int R : kR) {
+        if (R > (nr > 0 ? nr : 1)) continue;
+        if (stage_smem(te, G.Q, nv, ns, nr, R, G.O) > 200 * 1024) continue;
+        G.TE = te;
+        G.R = R;
+        if (upload_tiles(ctx, G) != cudaSuccess) {
+          rc = ADG_ERR_CUDA;
+          break;
+        }
         StageArgs A;
-        A.win = bufs[s];
-        A.w0 = I.wn;
-        A.wout = I.wpre;
-        A.wnext = bufs[s + 1];
-        A.s = s;
-        A.n = h.n;
-        A.TE = h.TE;
-        CK(timed_begin(ctx, 0, st));
-        CK(launch_stage(ctx->mech, I, A, st));
-        CK(timed_end(ctx, st));
-        if (I.limiter != ADG_LIM_NONE) {
-          LimArgs L;
-          L.wpre = I.wpre;
-          L.wout = bufs[s + 1];
-          L.s = s;
-          L.n = h.n;
-          CK(timed_begin(ctx, 1, st));
-          CK(launch_limiter(ctx->mech, I, L, st));
-          CK(timed_end(ctx, st));
+        A.insts = ctx->d_insts;
+        A.tiles = G.d_tiles;
+        A.s = 0;
+        A.TE = te;
+        A.R = R;
+        A.O = G.O;
+        // stage 0 alone rewrites only buffers that the next step rewrites again
+        // (stage buffers, the ring slot of the current level), so the
+        // trajectory is unchanged
+        bool ok = true;
+        for (int w = 0; w < 2 && ok; ++w) ok = launch_stage(ctx->mech, A, G.Q, G.n_tiles, st) == cudaSuccess;
+        ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
+        for (int w = 0; w < 5 && ok; ++w) ok = launch_stage(ctx->mech, A, G.Q, G.n_tiles, st) == cudaSuccess;
+        ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = 0.0f;
+        if (!ok || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          rc = ADG_ERR_CUDA;
+          break;
+        }
+        if (ms < best) {
+          best = ms;
+          bestTE = te;
+          bestR = R;
         }
       }
-      h.n += 1;
+      if (rc != ADG_OK) break;
     }
+    G.TE = bestTE;
+    G.R = bestR;
+    if (upload_tiles(ctx, G) != cudaSuccess) rc = ADG_ERR_CUDA;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  drop_graphs(ctx);
+  if (rc == ADG_ERR_CUDA) return cuda_fail(cudaGetLastError());
+  return rc;
+}
+
+int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning) {
+  if (!ctx || !n_groups || !tuning) return ADG_ERR_ARG;
+  *n_groups = ctx->n_groups;
+  for (int gi = 0; gi < ctx->n_groups; ++gi) {
+    const Group &G = ctx->groups[gi];
+    tuning[4 * gi + 0] = G.Q - 1;
+    tuning[4 * gi + 1] = G.TE;
+    tuning[4 * gi + 2] = G.R;
+    tuning[4 * gi + 3] = G.n_tiles;
   }
   return ADG_OK;
 }
 
 int adg_launches_per_step(const adg_ctx *ctx) {
   if (!ctx) return 0;
-  int n = 0;
-  for (const InstHost &h : ctx->inst) n += (h.d.limiter != ADG_LIM_NONE) ? 6 : 3;
+  int n = 1;
+  for (int gi = 0; gi < ctx->n_groups; ++gi) n += ctx->groups[gi].any_limiter ? 6 : 3;
   return n;
 }
 
 int adg_enable_kernel_timing(adg_ctx *ctx, int on) {
   if (!ctx) return ADG_ERR_ARG;
   ctx->timing = on != 0;
-  ctx->ev_used = 0;
+  ctx->kms[0] = ctx->kms[1] = ctx->kms[2] = 0.0;
+  ctx->kcount[0] = ctx->kcount[1] = ctx->kcount[2] = 0;
   return ADG_OK;
 }
 
 int adg_kernel_times(adg_ctx *ctx, double *ms, int64_t *launches) {
   if (!ctx || !ms || !launches) return ADG_ERR_ARG;
-  ms[0] = ms[1] = 0.0;
-  launches[0] = launches[1] = 0;
-  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
-    CK(cudaEventSynchronize(ctx->ev[i + 1]));
-    float t = 0.0f;
-    CK(cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]));
-    int k = ctx->ev_kind[i];
-    ms[k] += t;
-    launches[k] += 1;
+  for (int k = 0; k < 3; ++k) {
+    ms[k] = ctx->kms[k];
+    launches[k] = ctx->kcount[k];
   }
   return ADG_OK;
 }

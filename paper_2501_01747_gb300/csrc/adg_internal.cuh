@@ -62,13 +62,15 @@ struct Inst {
   double cum[MAXD + 1];                 // cumulative SAA probabilities
   double at[MAXD + 1][MAXO];            // AT weights c_m(k)
   double *wn, *wa, *wb, *wpre;          // [nv][N][Q]: w^n, stage 1 and 2 inputs, pre-limit
-  double *ring_in, *ring_pre;           // history ring
+  double *ring_in;   // history of the stage inputs' face traces [depth][3][npf][2][nv]
+  double *ring_pre;  // history of the pre-limit outputs [depth][3][npf][2][nv][p+1]
   uint8_t *flags;                       // [3][N]
   int32_t *count;                       // [N]
   const int *pf_of_left;                // per element: PE face on its left face or -1
   const int *pf_of_right;               // per element: PE face on its right face or -1
   const int *pf_elem;                   // per PE face: [left element, right element]
   int *err;                             // [4] code, element, stage, step (low bits)
+  int64_t *step;                        // step counter of this instance (device)
   int instance;
 };
 
@@ -100,6 +102,12 @@ __device__ inline int effective_delay(const Inst &I, int64_t n, int f) {
 __device__ inline size_t ring_block(const Inst &I, int64_t level, int s, int pf, int side) {
   int slot = (int)(level % I.depth);
   return ((((size_t)slot * 3 + s) * I.npf + pf) * 2 + side) * (size_t)I.nv * (I.p + 1);
+}
+
+// Offset of the face-trace record (nv values) of one side of a PE face.
+__device__ inline size_t ring_trace(const Inst &I, int64_t level, int s, int pf, int side) {
+  int slot = (int)(level % I.depth);
+  return ((((size_t)slot * 3 + s) * I.npf + pf) * 2 + side) * (size_t)I.nv;
 }
 
 __device__ inline void report_error(const Inst &I, int code, int elem, int stage, int64_t n) {
@@ -205,33 +213,41 @@ struct Basis {
   double WPh[MAXQ][MAXQ]; // w_q P_i(x_q) (2i+1)/2     (source projection)
 };
 
-// Arguments of one stage of the RHS/update kernel.
+// Arguments of one stage-kernel launch. A launch covers every instance of one
+// polynomial degree: CTA b works on elements [tiles[b].y, tiles[b].y + TE) of
+// instance tiles[b].x. Stage s reads w^n (wn) and its input (wn, wa, wb for
+// s = 0, 1, 2), writes the pre-limit output to wpre and to the next stage's
+// buffer (wa, wb, wn), and reads the step level from the instance's counter.
 struct StageArgs {
-  const double *win;   // stage input W^(s)
-  const double *w0;    // w^n
-  double *wout;        // pre-limit stage output (limiter input)
-  double *wnext;       // next-stage buffer: pre-limit output, limited in place later
-  int s;               // stage 0..2
-  int64_t n;           // step level
-  int TE;              // elements per tile
+  const Inst *insts;
+  const int2 *tiles;
+  int s;
+  int TE;     // elements per tile
+  int R;      // chemistry chunks per Gauss point
+  int O;      // AT levels provided for (largest AT order of the group)
 };
 
-// Arguments of the limiter kernel of one stage.
+// Arguments of one limiter launch: CTA b limits the elements of instance
+// blocks[b].x starting at blocks[b].y (LIM_WARPS warps, 32/G elements a warp).
 struct LimArgs {
-  const double *wpre;  // pre-limit stage output (read)
-  double *wout;        // limited stage output (written)
+  const Inst *insts;
+  const int2 *blocks;
   int s;
-  int64_t n;
 };
 
 struct ExpTable;
 void make_tables(Basis *tables, ExpTable *et);
 cudaError_t upload_basis(const Basis *tables);
 cudaError_t upload_exp_table(const ExpTable *t);
-int stage_tile(int Q, int nv, int ns, int nr);
-size_t stage_smem(int TE, int Q, int nv, int ns, int nr);
-cudaError_t launch_stage(const Mech &M, const Inst &I, const StageArgs &A, cudaStream_t st);
-cudaError_t launch_limiter(const Mech &M, const Inst &I, const LimArgs &A, cudaStream_t st);
+int stage_tile(int Q, int nv, int ns, int nr, int R, int O);
+int stage_chunks(int TE, int Q, int nr);
+size_t stage_smem(int TE, int Q, int nv, int ns, int nr, int R, int O);
+cudaError_t prepare_kernels(int nv, int ns, int nr);
+cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, int n_tiles, cudaStream_t st);
+cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, int nv, int n_blocks,
+                           cudaStream_t st);
+cudaError_t launch_advance(int64_t *steps, int n, cudaStream_t st);
+int limiter_elems_per_block(int nv);
 cudaError_t launch_project(const Mech &M, const Inst &I, const double *prim, double *w,
                            cudaStream_t st);
 cudaError_t launch_temperature(const Mech &M, const Inst &I, const double *w, double *T,

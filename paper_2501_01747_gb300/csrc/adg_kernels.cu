@@ -25,37 +25,64 @@ __constant__ Basis c_basis[ADG_MAX_P];   // index p-1
 
 __constant__ ExpTable c_exp;
 
-// Shared-memory footprint (bytes) of a stage tile of TE elements.
-__host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int nv, int ns, int nr) {
+// Shared-memory footprint (bytes) of a stage tile of TE elements, R chemistry
+// chunks per Gauss point and up to O AT levels per face.
+__host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int nv, int ns, int nr, int R,
+                                                   int O) {
+  size_t TQ = (size_t)TE * Q, F = TE + 1;
   size_t n = (size_t)SP_NFIELDS * ns      // species fields
              + 34                         // exp table and ln2/32 split
-             + (size_t)nv * (TE + 2) * Q  // modal tile with halo    [v][le][j]
-             + (size_t)nv * TE * Q        // nodal state, then flux  [v][t]
-             + (size_t)ns * TE * Q * 3    // conc, g/RT, rates        [i][t]
-             + (size_t)(TE + 1) * nv      // face fluxes             [f][v]
-             + (size_t)(TE + 1) * 2 * nv; // face traces             [f][2][v]
+             + (size_t)nv * (TE + 2) * Q  // modal tile with halo        [v][le][j]
+             + (size_t)nv * TQ            // nodal state, then flux      [v][t]
+             + (size_t)ns * TQ * 2        // concentrations, g/RT        [i][t]
+             + (size_t)R * ns * TQ        // production rates per chunk  [c][i][t]
+             + 2 * TQ                     // ln T, 1/T                   [t]
+             + F * nv                     // face fluxes                 [f][v]
+             + (size_t)O * F * nv         // level fluxes                [m][f][v]
+             + (size_t)O * F * 2 * nv     // traces per (level, face)    [m][f][2][v]
+             + F;                         // delay of each face (as int)
   return n * sizeof(double) + (size_t)nr * sizeof(Rxn);
 }
 
+// Copy an instance description into shared memory (by 8-byte words).
+__device__ inline void load_inst(Inst &dst, const Inst *src) {
+  const unsigned long long *a = reinterpret_cast<const unsigned long long *>(src);
+  unsigned long long *b = reinterpret_cast<unsigned long long *>(&dst);
+  for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 8); k += blockDim.x) b[k] = a[k];
+}
+
 template <int Q>
-__global__ void __launch_bounds__(256) stage_kernel(Mech M, Inst I, StageArgs A) {
+__global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
   extern __shared__ __align__(16) double sm[];
+  __shared__ Inst sI;
+  const int2 tile = A.tiles[blockIdx.x];
+  load_inst(sI, A.insts + tile.x);
+  __syncthreads();
+  const Inst &I = sI;
   const Basis &B = c_basis[Q - 2];
   const int nv = I.nv, ns = M.ns, nr = M.nr, N = I.n_elem, TE = A.TE;
   const int TQ = TE * Q;
-  const int e0 = blockIdx.x * TE;
+  const int e0 = tile.y;
   const int te = min(TE, N - e0);
+  const int64_t nstep = *I.step;
+  const double *A_win = (A.s == 0) ? I.wn : (A.s == 1) ? I.wa : I.wb;
+  double *A_wnext = (A.s == 0) ? I.wa : (A.s == 1) ? I.wb : I.wn;
   const bool periodic = (I.bc_left == ADG_BC_PERIODIC);
   Rxn *srx = reinterpret_cast<Rxn *>(sm);
   double *ssp = reinterpret_cast<double *>(srx + nr);       // [F][ns]
   ExpTable *stab = reinterpret_cast<ExpTable *>(ssp + SP_NFIELDS * ns);
+  const int R = A.R, O = A.O, NF = TE + 1;
   double *sw = reinterpret_cast<double *>(stab + 1);        // [v][TE+2][Q]
   double *snode = sw + (size_t)nv * (TE + 2) * Q;           // [v][TQ]
   double *sconc = snode + (size_t)nv * TQ;                  // [i][TQ]
   double *sg = sconc + (size_t)ns * TQ;                     // [i][TQ]
-  double *swd = sg + (size_t)ns * TQ;                       // [i][TQ]
-  double *sfh = swd + (size_t)ns * TQ;                      // [TE+1][nv]
-  double *str = sfh + (size_t)(TE + 1) * nv;                // [TE+1][2][nv]
+  double *swd = sg + (size_t)ns * TQ;                       // [R][i][TQ]
+  double *slnT = swd + (size_t)R * ns * TQ;                 // [TQ]
+  double *sinvT = slnT + TQ;                                // [TQ]
+  double *sfh = sinvT + TQ;                                 // [NF][nv]
+  double *sflx = sfh + (size_t)NF * nv;                     // [O][NF][nv]
+  double *str = sflx + (size_t)O * NF * nv;                 // [O][NF][2][nv]
+  int *sk = reinterpret_cast<int *>(str + (size_t)O * NF * 2 * nv);  // [NF]
   const int tid = threadIdx.x, nth = blockDim.x;
 
   // 0. mechanism, species fields and exp table into shared memory
@@ -76,15 +103,16 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, Inst I, StageArgs A)
     int e = e0 - 1 + le;
     if (e < 0) e = periodic ? e + N : 0;
     if (e >= N) e = periodic ? e - N : N - 1;
-    sw[((size_t)v * (TE + 2) + le) * Q + j] = A.win[((size_t)v * N + e) * Q + j];
+    sw[((size_t)v * (TE + 2) + le) * Q + j] = A_win[((size_t)v * N + e) * Q + j];
   }
   __syncthreads();
 
-  // 2. Gauss points: conserved state, thermo, chemistry, flux
+  // 2a. Gauss points: conserved state, thermo, concentrations, g_i/(R T), flux
   const double *sW = ssp + SP_W * ns, *sIW = ssp + SP_INVW * ns;
   const double *sG0 = ssp + SP_G0 * ns, *sG1 = ssp + SP_G1 * ns, *sCR = ssp + SP_CPR * ns;
   const double LN_R_PATM = log(RU / PATM);
-  for (int t = tid; t < te * Q; t += nth) {
+  const int teq = te * Q;
+  for (int t = tid; t < teq; t += nth) {
     int e = t / Q, q = t - e * Q, le = e + 1;
     double *wq = snode + t;   // stride TQ between variables
     for (int v = 0; v < nv; ++v) {
@@ -95,79 +123,92 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, Inst I, StageArgs A)
     }
     Thermo th = thermo_of(ssp, ns, wq, TQ);
     if (!(th.rho > 0.0) || !(th.T > 0.0) || !isfinite(th.T) || !isfinite(wq[0]))
-      report_error(I, ADG_ERR_NONPHYSICAL, e0 + e, A.s, A.n);
-    // chemistry: law of mass action on non-negative concentrations, reversible
-    // rates from the species' Gibbs energies (2 exponentials per reaction)
+      report_error(I, ADG_ERR_NONPHYSICAL, e0 + e, A.s, nstep);
     const double lnT = log(th.T), invT = 1.0 / th.T;
-    double *cq = sconc + t, *gq = sg + t, *wd = swd + t;
+    slnT[t] = lnT;
+    sinvT[t] = invT;
+    double *cq = sconc + t, *gq = sg + t;
     for (int i = 0; i < ns; ++i) {
       double r = wq[(size_t)(2 + i) * TQ];
-      // clip at zero by the sign bit (no FP64 instruction)
+      // law of mass action on non-negative concentrations: clip at zero by the
+      // sign bit (no FP64 instruction)
       r = (__double2hiint(r) < 0) ? 0.0 : r;
       cq[(size_t)i * TQ] = r * sIW[i];
       gq[(size_t)i * TQ] = fma(-sCR[i], lnT, fma(sG0[i], invT, sG1[i]));
-      wd[(size_t)i * TQ] = 0.0;
-    }
-    const double lr = lnT + LN_R_PATM;
-    for (int j = 0; j < nr; ++j) {
-      const Rxn &R = srx[j];
-      double lkf = fma(-R.EaR, invT, fma(R.b, lnT, R.lnA));
-      double dg = R.dnu * lr;
-      const int nx = R.nx;
-      for (int k = 0; k < nx; ++k) dg = fma(R.xc[k], gq[(size_t)R.xs[k] * TQ], dg);
-      double fwd = fexp(lkf, *stab), rev = fexp(lkf + dg, *stab);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (R.rn[k] == 0) break;
-        double c = cq[(size_t)R.rs[k] * TQ];
-        fwd *= c;
-        if (R.rn[k] > 1) fwd *= c;
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (R.pn[k] == 0) break;
-        double c = cq[(size_t)R.ps[k] * TQ];
-        rev *= c;
-        if (R.pn[k] > 1) rev *= c;
-      }
-      double qj = fwd - rev;
-      for (int k = 0; k < nx; ++k)
-        wd[(size_t)R.xs[k] * TQ] = fma(R.xc[k], qj, wd[(size_t)R.xs[k] * TQ]);
     }
     double f0 = phys_flux(wq, TQ, 0, th), f1 = phys_flux(wq, TQ, 1, th);
     for (int v = 2; v < nv; ++v) wq[(size_t)v * TQ] = th.u * wq[(size_t)v * TQ];
     wq[0] = f0;
     wq[TQ] = f1;
   }
+  __syncthreads();
 
-  // 3. face fluxes of the tile: local face f sits between local elements f and f+1
-  for (int f = tid; f <= te; f += nth) {
-    int g = e0 + f;  // global face index
-    double *fh = sfh + (size_t)f * nv;
-    double *wl = str + (size_t)f * 2 * nv, *wr = wl + nv;
-    int pf = (g < N) ? I.pf_of_left[g] : I.pf_of_right[N - 1];
-    int k = (pf >= 0) ? effective_delay(I, A.n, pf) : 0;
-    if (k > 0) {
-      // AT flux (Eq. 7): both sides at the common delayed levels n-k-m
-      for (int mm = 0; mm < I.at_order; ++mm) {
-        int64_t lv = A.n - k - mm;
-        const double *bl = I.ring_in + ring_block(I, lv, A.s, pf, 0);
-        const double *br = I.ring_in + ring_block(I, lv, A.s, pf, 1);
-        for (int v = 0; v < nv; ++v) {
-          double a = 0.0, b = 0.0;
-          for (int j = 0; j < Q; ++j) {
-            a += bl[v * Q + j];
-            b += ((j & 1) ? -1.0 : 1.0) * br[v * Q + j];
-          }
-          wl[v] = a;
-          wr[v] = b;
-        }
-        num_flux(ssp, ns, I.flux, wl, wr, fh, I.at[k][mm], mm > 0);
-        if (mm == 0)
-          for (int v = 0; v < nv; ++v) fh[v] *= I.at[k][0];
+  // 2b. chemistry, the reactions of every Gauss point split into R chunks:
+  // reversible rates from the species' Gibbs energies, two exponentials each
+  for (int item = tid; item < R * teq; item += nth) {
+    int c = item / teq, t = item - c * teq;
+    const double lnT = slnT[t], invT = sinvT[t];
+    const double *cq = sconc + t, *gq = sg + t;
+    double *wd = swd + (size_t)c * ns * TQ + t;
+    for (int i = 0; i < ns; ++i) wd[(size_t)i * TQ] = 0.0;
+    const double lr = lnT + LN_R_PATM;
+    const int j0 = c * nr / R, j1 = (c + 1) * nr / R;
+    for (int j = j0; j < j1; ++j) {
+      const Rxn &Rx = srx[j];
+      double lkf = fma(-Rx.EaR, invT, fma(Rx.b, lnT, Rx.lnA));
+      double dg = Rx.dnu * lr;
+      const int nx = Rx.nx;
+      for (int k = 0; k < nx; ++k) dg = fma(Rx.xc[k], gq[(size_t)Rx.xs[k] * TQ], dg);
+      double fwd = fexp(lkf, *stab), rev = fexp(lkf + dg, *stab);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (Rx.rn[k] == 0) break;
+        double cc = cq[(size_t)Rx.rs[k] * TQ];
+        fwd *= cc;
+        if (Rx.rn[k] > 1) fwd *= cc;
       }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (Rx.pn[k] == 0) break;
+        double cc = cq[(size_t)Rx.ps[k] * TQ];
+        rev *= cc;
+        if (Rx.pn[k] > 1) rev *= cc;
+      }
+      double qj = fwd - rev;
+      for (int k = 0; k < nx; ++k)
+        wd[(size_t)Rx.xs[k] * TQ] = fma(Rx.xc[k], qj, wd[(size_t)Rx.xs[k] * TQ]);
+    }
+  }
+  __syncthreads();
+
+  // 2c. sum of the chunks' rates into chunk 0
+  if (R > 1)
+    for (int item = tid; item < ns * teq; item += nth) {
+      int i = item / teq, t = item - i * teq;
+      double acc = swd[(size_t)i * TQ + t];
+      for (int c = 1; c < R; ++c) acc += swd[((size_t)c * ns + i) * TQ + t];
+      swd[(size_t)i * TQ + t] = acc;
+    }
+  // 3a. face fluxes of the tile (local face f between local elements f and f+1),
+  // one thread per (level, face): the plain flux, or one delayed level of the AT
+  // flux (Eq. 7) with both sides at the common level n-k-m
+  for (int job = tid; job < O * (te + 1); job += nth) {
+    int m = job / (te + 1), f = job - m * (te + 1);
+    int g = e0 + f;  // global face index
+    int pf = (g < N) ? I.pf_of_left[g] : I.pf_of_right[N - 1];
+    int k = (pf >= 0) ? effective_delay(I, nstep, pf) : 0;
+    if (m == 0) sk[f] = k;
+    double *fl = sflx + ((size_t)m * NF + f) * nv;
+    double *wl = str + ((size_t)m * NF + f) * 2 * nv, *wr = wl + nv;
+    if (k > 0) {
+      if (m >= I.at_order) continue;
+      int64_t lv = nstep - k - m;
+      const double *bl = I.ring_in + ring_trace(I, lv, A.s, pf, 0);
+      const double *br = I.ring_in + ring_trace(I, lv, A.s, pf, 1);
+      num_flux(ssp, ns, I.flux, bl, br, fl, 1.0, false);
       continue;
     }
+    if (m > 0) continue;
     for (int v = 0; v < nv; ++v) {
       double a = 0.0, b = 0.0;
       for (int j = 0; j < Q; ++j) {
@@ -184,7 +225,20 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, Inst I, StageArgs A)
       for (int v = 0; v < nv; ++v) wr[v] = wl[v];
       if (I.bc_right == ADG_BC_REFLECT) wr[0] = -wl[0];
     }
-    num_flux(ssp, ns, I.flux, wl, wr, fh, 1.0, false);
+    num_flux(ssp, ns, I.flux, wl, wr, fl, 1.0, false);
+  }
+  __syncthreads();
+  // 3b. the AT sum over levels, m = 0..o-1 in order
+  for (int item = tid; item < (te + 1) * nv; item += nth) {
+    int f = item / nv, v = item - f * nv;
+    int k = sk[f];
+    double acc = sflx[(size_t)f * nv + v];
+    if (k > 0) {
+      acc *= I.at[k][0];
+      for (int m = 1; m < I.at_order; ++m)
+        acc = fma(I.at[k][m], sflx[((size_t)m * NF + f) * nv + v], acc);
+    }
+    sfh[(size_t)f * nv + v] = acc;
   }
   __syncthreads();
 
@@ -217,28 +271,34 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, Inst I, StageArgs A)
       double r = fma((2.0 * i + 1.0) * inv_dx, surf, Wv * S);
       size_t gi = ((size_t)v * N + ge) * Q + i;
       double o;
-      if (A.s == 0) o = fma(I.dt, r, A.w0[gi]);
-      else if (A.s == 1) o = fma(0.25, fma(I.dt, r, wi[i]), 0.75 * A.w0[gi]);
-      else o = fma(2.0 / 3.0, fma(I.dt, r, wi[i]), (1.0 / 3.0) * A.w0[gi]);
+      if (A.s == 0) o = fma(I.dt, r, I.wn[gi]);
+      else if (A.s == 1) o = fma(0.25, fma(I.dt, r, wi[i]), 0.75 * I.wn[gi]);
+      else o = fma(2.0 / 3.0, fma(I.dt, r, wi[i]), (1.0 / 3.0) * I.wn[gi]);
       out[i] = o;
-      A.wout[gi] = o;
-      A.wnext[gi] = o;
+      I.wpre[gi] = o;
+      A_wnext[gi] = o;
     }
     if (slot_ok) {
       int pr = I.pf_of_right[ge], pl = I.pf_of_left[ge];
       if (pr >= 0) {
-        size_t b = ring_block(I, A.n, A.s, pr, 0) + (size_t)v * Q;
+        // left element of the PE face: its trace at xi = +1
+        size_t b = ring_block(I, nstep, A.s, pr, 0) + (size_t)v * Q;
+        double tr = 0.0;
         for (int i = 0; i < Q; ++i) {
-          I.ring_in[b + i] = wi[i];
+          tr += wi[i];
           I.ring_pre[b + i] = out[i];
         }
+        I.ring_in[ring_trace(I, nstep, A.s, pr, 0) + v] = tr;
       }
       if (pl >= 0) {
-        size_t b = ring_block(I, A.n, A.s, pl, 1) + (size_t)v * Q;
+        // right element of the PE face: its trace at xi = -1
+        size_t b = ring_block(I, nstep, A.s, pl, 1) + (size_t)v * Q;
+        double tr = 0.0;
         for (int i = 0; i < Q; ++i) {
-          I.ring_in[b + i] = wi[i];
+          tr += ((i & 1) ? -1.0 : 1.0) * wi[i];
           I.ring_pre[b + i] = out[i];
         }
+        I.ring_in[ring_trace(I, nstep, A.s, pl, 1) + v] = tr;
       }
     }
   }
@@ -254,7 +314,7 @@ __device__ inline double minmod3(double a, double b, double c) {
 // neighbours, the limited characteristic modes, gradP.w, the partial-density
 // sums and momenta of the three blocks, the per-species phi_k, two mode sums.
 __host__ __device__ inline int limiter_elem_doubles(int nv, int ns, int Q) {
-  return 3 * nv * Q + nv * Q + 3 * 3 * Q + ns + 2 * Q;
+  return 3 * nv * Q + nv * Q + 3 * 3 * Q + ns + 2 * Q + 8;
 }
 constexpr int LIM_WARPS = 8;
 
@@ -271,16 +331,25 @@ constexpr int LIM_WARPS = 8;
 // The stage kernel has already written the pre-limit values into the output;
 // only troubled cells are rewritten here.
 template <int Q, int G>
-__global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, Inst I, LimArgs A) {
+__global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs A) {
   extern __shared__ __align__(16) double lsm[];
+  __shared__ Inst sI;
+  const int2 blkid = A.blocks[blockIdx.x];
+  load_inst(sI, A.insts + blkid.x);
+  __syncthreads();
+  const Inst &I = sI;
+  if (I.limiter == ADG_LIM_NONE) return;
   const Basis &B = c_basis[Q - 2];
   const int N = I.n_elem, nv = I.nv, ns = M.ns;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gl = lane % G, gw = lane / G;
   constexpr int EPW = 32 / G;
   const int slot = warp * EPW + gw;
-  const int e = blockIdx.x * (LIM_WARPS * EPW) + slot;
+  const int e = blkid.y + slot;
   const bool valid = e < N;
+  const int64_t nstep = *I.step;
+  double *A_wout = (A.s == 0) ? I.wa : (A.s == 1) ? I.wb : I.wn;
+  const double *A_wpre = I.wpre;
   const unsigned FULL = 0xffffffffu;
   const unsigned gmask = (G == 32) ? FULL : (0xffffu << (16 * gw));
   const size_t VS = (size_t)N * Q;
@@ -292,6 +361,7 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, Inst I,
   double *mmv = rsv + 3 * Q;                                            // [3][Q]
   double *phi = mmv + 3 * Q;                                            // [ns]
   double *sums = phi + ns;                                              // [2][Q]
+  double *ssum = sums + 2 * Q;   // mode sums of block 0: gp, mm, rs (plain, alternating)
   const bool periodic = (I.bc_left == ADG_BC_PERIODIC);
 
   // 1. the element (block 0) and its neighbours (1 left, 2 right): the pre-limit
@@ -303,7 +373,7 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, Inst I,
       int src = e, ghost = 0, k = 0, pf = -1;
       if (d > 0) {
         pf = d == 1 ? I.pf_of_left[e] : I.pf_of_right[e];
-        k = (pf >= 0) ? effective_delay(I, A.n, pf) : 0;
+        k = (pf >= 0) ? effective_delay(I, nstep, pf) : 0;
         src = d == 1 ? e - 1 : e + 1;
         if (src < 0 || src >= N) {
           if (periodic) {
@@ -319,13 +389,13 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, Inst I,
         for (int t = gl; t < NB; t += G) {
           double acc = 0.0;
           for (int m = 0; m < I.at_order; ++m)
-            acc += I.at[k][m] * I.ring_pre[ring_block(I, A.n - k - m, A.s, pf, side) + t];
+            acc += I.at[k][m] * I.ring_pre[ring_block(I, nstep - k - m, A.s, pf, side) + t];
           dst[t] = acc;
         }
       } else {
         for (int t = gl; t < NB; t += G) {
           int v = t / Q, j = t - v * Q;
-          double x = A.wpre[(size_t)v * VS + (size_t)src * Q + j];
+          double x = A_wpre[(size_t)v * VS + (size_t)src * Q + j];
           if (ghost && (((j & 1) != 0) != (v == 0))) x = -x;
           dst[t] = x;
         }
@@ -370,10 +440,22 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, Inst I,
   const double H = (E0 + P) * irho;
   const double ia2 = 1.0 / (a * a);
   if (valid && gl == 0 && (!(rho > 0.0) || !(T > 0.0) || !isfinite(T)))
-    report_error(I, ADG_ERR_NONPHYSICAL, e, A.s, A.n);
+    report_error(I, ADG_ERR_NONPHYSICAL, e, A.s, nstep);
+  // phi_k, and the sums of |phi_i|, |phi_i - a u|, |phi_i + a u| for the noise floor
+  double sphi = 0.0, sphm = 0.0, sphp = 0.0;
   if (valid) {
-    for (int i = gl; i < ns; i += G)
-      phi[i] = fma(g, fma(-cvW[i], T, 0.5 * u * u - qW[i]), T * RW[i]);
+    for (int i = gl; i < ns; i += G) {
+      double ph = fma(g, fma(-cvW[i], T, 0.5 * u * u - qW[i]), T * RW[i]);
+      phi[i] = ph;
+      sphi += fabs(ph);
+      sphm += fabs(ph - a * u);
+      sphp += fabs(ph + a * u);
+    }
+  }
+  for (int o = G / 2; o > 0; o >>= 1) {
+    sphi += __shfl_xor_sync(FULL, sphi, o, G);
+    sphm += __shfl_xor_sync(FULL, sphm, o, G);
+    sphp += __shfl_xor_sync(FULL, sphp, o, G);
   }
   __syncwarp();
   if (valid)
@@ -390,6 +472,13 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, Inst I,
       rsv[t] = sr;
       mmv[t] = x[j];
     }
+  __syncwarp();
+  if (valid && gl < 6) {
+    const double *src = (gl % 3 == 0) ? gpv : (gl % 3 == 1) ? mmv : rsv;
+    double acc = 0.0;
+    for (int j = 0; j < Q; ++j) acc += (gl >= 3 && (j & 1)) ? -src[j] : src[j];
+    ssum[gl] = acc;
+  }
   __syncwarp();
 
   // coefficients of field k and its value for block b, mode j
@@ -418,19 +507,24 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, Inst I,
       double cA, cB, cC, cD;
       int ri;
       coef(k, cA, cB, cC, cD, ri);
-      double vb = val(cA, cB, cC, cD, ri, 0, 0), vp = vb, vm = vb;
+      // the face values v(+1), v(-1) from the mode sums (linear in the modes)
+      const double *rk = blk + (2 + ri) * Q;
+      double rsum = 0.0, ralt = 0.0;
 #pragma unroll
-      for (int j = 1; j < Q; ++j) {
-        double x = val(cA, cB, cC, cD, ri, 0, j);
-        vp += x;
-        vm += (j & 1) ? -x : x;
+      for (int j = 0; j < Q; ++j) {
+        rsum += rk[j];
+        ralt += (j & 1) ? -rk[j] : rk[j];
       }
+      double vb = val(cA, cB, cC, cD, ri, 0, 0);
+      double vp = fma(cA, ssum[0], fma(cB, ssum[1], fma(cC, ssum[2], cD * rsum)));
+      double vm = fma(cA, ssum[3], fma(cB, ssum[4], fma(cC, ssum[5], cD * ralt)));
       double vL = val(cA, cB, cC, cD, ri, 1, 0), vR = val(cA, cB, cC, cD, ri, 2, 0);
-      double scale = fabs(fma(cA, -u * g, cB)) * sig0 + fabs(cA * g) * sig1;
-      for (int i = 0; i < ns; ++i) {
-        double l = fma(cA, phi[i], cC) + ((i == ri) ? cD : 0.0);
-        scale = fma(fabs(l), sigr, scale);
-      }
+      // sum_v |L_kv| sigma_v in closed form: for species k, |1 + A phi_k| plus
+      // |A| (sum |phi| - |phi_k|); for the acoustic fields A sum |phi_i -/+ a u|
+      bool ac = (k == 0) || (k == nv - 1);
+      double sr = ac ? cA * (k == 0 ? sphp : sphm)
+                     : fabs(fma(cA, phi[ri], 1.0)) + fabs(cA) * (sphi - fabs(phi[ri]));
+      double scale = fma(fabs(fma(cA, -u * g, cB)), sig0, fma(fabs(cA * g), sig1, sr * sigr));
       double ut = vp - vb, utt = vb - vm, dp = vR - vb, dm = vb - vL;
       double fl = tau * scale;
       if (fabs(ut) > fl && fabs(ut) > tvb && minmod3(ut, dp, dm) != ut) mine = true;
@@ -506,7 +600,7 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, Inst I,
     sums[Q + i] = s2;
   }
   __syncwarp(gmask);
-  double *out = A.wout + (size_t)e * Q;
+  double *out = A_wout + (size_t)e * Q;
   for (int t = gl; t < NB; t += G) {
     int v = t / Q, i = t - v * Q;
     if (i == 0) continue;
@@ -574,15 +668,32 @@ cudaError_t upload_basis(const Basis *tables) {
   return cudaMemcpyToSymbol(c_basis, tables, sizeof(Basis) * ADG_MAX_P);
 }
 
-int stage_tile(int Q, int nv, int ns, int nr) {
+int stage_tile(int Q, int nv, int ns, int nr, int R, int O) {
   // elements per tile: up to 256 Gauss-point threads, at most ~96 KB of tile
   int TE = 256 / Q;
-  while (TE > 2 && stage_smem_bytes(TE, Q, nv, ns, nr) > 96 * 1024) TE /= 2;
+  while (TE > 2 && stage_smem_bytes(TE, Q, nv, ns, nr, R, O) > 96 * 1024) TE /= 2;
   return TE;
 }
 
-size_t stage_smem(int TE, int Q, int nv, int ns, int nr) {
-  return stage_smem_bytes(TE, Q, nv, ns, nr);
+int stage_chunks(int TE, int Q, int nr) {
+  // chemistry chunks per Gauss point that best fill the CTA's threads
+  int TQ = TE * Q, nth = ((TQ + 31) / 32) * 32;
+  int best = 1;
+  double best_fill = 0.0;
+  for (int R = 1; R <= 8 && R <= (nr > 0 ? nr : 1); ++R) {
+    int items = TQ * R;
+    int rounds = (items + nth - 1) / nth;
+    double fill = (double)items / (rounds * nth);
+    if (fill > best_fill + 0.02) {
+      best_fill = fill;
+      best = R;
+    }
+  }
+  return best;
+}
+
+size_t stage_smem(int TE, int Q, int nv, int ns, int nr, int R, int O) {
+  return stage_smem_bytes(TE, Q, nv, ns, nr, R, O);
 }
 
 cudaError_t upload_exp_table(const ExpTable *t) {
@@ -590,66 +701,86 @@ cudaError_t upload_exp_table(const ExpTable *t) {
 }
 
 template <int Q>
-static cudaError_t launch_stage_q(const Mech &M, const Inst &I, const StageArgs &A,
+static cudaError_t launch_stage_q(const Mech &M, const StageArgs &A, int n_tiles,
                                   cudaStream_t st) {
-  size_t smem = stage_smem_bytes(A.TE, Q, I.nv, M.ns, M.nr);
-  static bool attr_set[4] = {false, false, false, false};
-  if (!attr_set[Q - 2]) {
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<Q>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set[Q - 2] = true;
-  }
-  int nblk = (I.n_elem + A.TE - 1) / A.TE;
-  int nth = A.TE * Q;
-  nth = ((nth + 31) / 32) * 32;
-  stage_kernel<Q><<<nblk, nth, smem, st>>>(M, I, A);
+  int nv = M.ns + 2;
+  size_t smem = stage_smem_bytes(A.TE, Q, nv, M.ns, M.nr, A.R, A.O);
+  int nth = ((A.TE * Q + 31) / 32) * 32;
+  stage_kernel<Q><<<n_tiles, nth, smem, st>>>(M, A);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stage(const Mech &M, const Inst &I, const StageArgs &A, cudaStream_t st) {
-  switch (I.p + 1) {
-    case 2: return launch_stage_q<2>(M, I, A, st);
-    case 3: return launch_stage_q<3>(M, I, A, st);
-    case 4: return launch_stage_q<4>(M, I, A, st);
-    case 5: return launch_stage_q<5>(M, I, A, st);
+cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, int n_tiles, cudaStream_t st) {
+  switch (Q) {
+    case 2: return launch_stage_q<2>(M, A, n_tiles, st);
+    case 3: return launch_stage_q<3>(M, A, n_tiles, st);
+    case 4: return launch_stage_q<4>(M, A, n_tiles, st);
+    case 5: return launch_stage_q<5>(M, A, n_tiles, st);
   }
   return cudaErrorInvalidValue;
 }
+
+int limiter_elems_per_block(int nv) { return LIM_WARPS * (nv <= 16 ? 2 : 1); }
 
 template <int Q, int G>
-static cudaError_t launch_limiter_qg(const Mech &M, const Inst &I, const LimArgs &A,
+static cudaError_t launch_limiter_qg(const Mech &M, const LimArgs &A, int nv, int n_blocks,
                                      cudaStream_t st) {
   constexpr int EPW = 32 / G;
-  size_t smem = (size_t)LIM_WARPS * EPW * limiter_elem_doubles(I.nv, M.ns, Q) * sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(limiter_kernel<Q, G>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  int per = LIM_WARPS * EPW;
-  int nblk = (I.n_elem + per - 1) / per;
-  limiter_kernel<Q, G><<<nblk, 32 * LIM_WARPS, smem, st>>>(M, I, A);
+  size_t smem = (size_t)LIM_WARPS * EPW * limiter_elem_doubles(nv, M.ns, Q) * sizeof(double);
+  limiter_kernel<Q, G><<<n_blocks, 32 * LIM_WARPS, smem, st>>>(M, A);
   return cudaGetLastError();
 }
 
-template <int Q>
-static cudaError_t launch_limiter_q(const Mech &M, const Inst &I, const LimArgs &A,
-                                    cudaStream_t st) {
-  if (I.nv <= 16) return launch_limiter_qg<Q, 16>(M, I, A, st);
-  return launch_limiter_qg<Q, 32>(M, I, A, st);
-}
-
-cudaError_t launch_limiter(const Mech &M, const Inst &I, const LimArgs &A, cudaStream_t st) {
-  switch (I.p + 1) {
-    case 2: return launch_limiter_q<2>(M, I, A, st);
-    case 3: return launch_limiter_q<3>(M, I, A, st);
-    case 4: return launch_limiter_q<4>(M, I, A, st);
-    case 5: return launch_limiter_q<5>(M, I, A, st);
+cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, int nv, int n_blocks,
+                           cudaStream_t st) {
+  bool g16 = nv <= 16;
+  switch (Q) {
+    case 2: return g16 ? launch_limiter_qg<2, 16>(M, A, nv, n_blocks, st)
+                       : launch_limiter_qg<2, 32>(M, A, nv, n_blocks, st);
+    case 3: return g16 ? launch_limiter_qg<3, 16>(M, A, nv, n_blocks, st)
+                       : launch_limiter_qg<3, 32>(M, A, nv, n_blocks, st);
+    case 4: return g16 ? launch_limiter_qg<4, 16>(M, A, nv, n_blocks, st)
+                       : launch_limiter_qg<4, 32>(M, A, nv, n_blocks, st);
+    case 5: return g16 ? launch_limiter_qg<5, 16>(M, A, nv, n_blocks, st)
+                       : launch_limiter_qg<5, 32>(M, A, nv, n_blocks, st);
   }
   return cudaErrorInvalidValue;
+}
+
+// Raise the dynamic shared-memory limit of every kernel instance (before any
+// launch or stream capture).
+cudaError_t prepare_kernels(int nv, int ns, int nr) {
+  (void)nv;
+  (void)ns;
+  (void)nr;
+  const int lim = 200 * 1024;
+  cudaError_t e = cudaSuccess;
+#define SET(fn) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+  SET(stage_kernel<2>);
+  SET(stage_kernel<3>);
+  SET(stage_kernel<4>);
+  SET(stage_kernel<5>);
+  SET((limiter_kernel<2, 16>));
+  SET((limiter_kernel<3, 16>));
+  SET((limiter_kernel<4, 16>));
+  SET((limiter_kernel<5, 16>));
+  SET((limiter_kernel<2, 32>));
+  SET((limiter_kernel<3, 32>));
+  SET((limiter_kernel<4, 32>));
+  SET((limiter_kernel<5, 32>));
+#undef SET
+  return e;
+}
+
+__global__ void advance_kernel(int64_t *steps, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) steps[i] += 1;
+}
+
+cudaError_t launch_advance(int64_t *steps, int n, cudaStream_t st) {
+  advance_kernel<<<(n + 127) / 128, 128, 0, st>>>(steps, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_project(const Mech &M, const Inst &I, const double *prim, double *w,

@@ -16,11 +16,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[ADG_NOALLOC_SCR
 // PE maps of one instance computed on the device (PE q owns elements
 // [q N / P, (q+1) N / P); the element e belongs to PE ((e+1) P - 1) / N).
 __global__ void noalloc_maps_kernel(int N, int P, int npf, int periodic, int *pf_left,
-                                    int *pf_right, int32_t *count, uint8_t *flags, int *err) {
+                                    int *pf_right, int32_t *count, uint8_t *flags, int *err,
+                                    int64_t *step, int TE, int2 *tiles, int EPB, int2 *blocks) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e == 0)
+  if (e == 0) {
     for (int k = 0; k < 4; ++k) err[k] = 0;
+    *step = 0;
+  }
   if (e >= N) return;
+  if (e % TE == 0) tiles[e / TE] = make_int2(0, e);
+  if (e % EPB == 0) blocks[e / EPB] = make_int2(0, e);
   count[e] = 0;
   flags[e] = flags[N + e] = flags[2 * N + e] = 0;
   int l = -1, r = -1;
@@ -97,13 +102,23 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   size_t o_wa = cur.take(sizeof(double) * st);
   size_t o_wb = cur.take(sizeof(double) * st);
   size_t o_wpre = cur.take(sizeof(double) * st);
-  size_t rs = (size_t)depth * 3 * (npf > 0 ? npf : 1) * 2 * nv * Q;
+  size_t rs = (size_t)depth * 3 * (npf > 0 ? npf : 1) * 2 * nv;
   size_t o_rin = cur.take(sizeof(double) * rs);
-  size_t o_rpre = cur.take(sizeof(double) * rs);
+  size_t o_rpre = cur.take(sizeof(double) * rs * Q);
   size_t o_flags = cur.take((size_t)3 * N);
   size_t o_count = cur.take(sizeof(int32_t) * N);
   size_t o_pl = cur.take(sizeof(int) * N);
   size_t o_pr = cur.take(sizeof(int) * N);
+  int TE = stage_tile(Q, nv, ns, nr, 8, c.at_order);
+  int target = (N + 2 * 152 - 1) / (2 * 152);
+  if (target < TE) TE = target < 4 ? 4 : target;
+  const int RC = stage_chunks(TE, Q, nr);
+  const int EPB = limiter_elems_per_block(nv);
+  const int n_tiles = (N + TE - 1) / TE, n_blocks = (N + EPB - 1) / EPB;
+  size_t o_inst = cur.take(sizeof(Inst));
+  size_t o_step = cur.take(sizeof(int64_t));
+  size_t o_tiles = cur.take(sizeof(int2) * n_tiles);
+  size_t o_blocks = cur.take(sizeof(int2) * n_blocks);
   if (cur.off > (size_t)ADG_NOALLOC_SCRATCH_BYTES) return ADG_ERR_NOMEM;
 
   // host-side tables on the stack (no heap)
@@ -166,7 +181,8 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
       Basis tables[ADG_MAX_P];
       ExpTable et;
       make_tables(tables, &et);
-      if (upload_basis(tables) != cudaSuccess || upload_exp_table(&et) != cudaSuccess)
+      if (upload_basis(tables) != cudaSuccess || upload_exp_table(&et) != cudaSuccess ||
+          prepare_kernels(nv, ns, nr) != cudaSuccess)
         return ADG_ERR_CUDA;
       g_ptr[dev] = (unsigned char *)p;
       g_ready[dev] = true;
@@ -225,6 +241,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   I.pf_of_right = (const int *)(base + o_pr);
   I.pf_elem = nullptr;
   I.err = (int *)(base + o_err);
+  I.step = (int64_t *)(base + o_step);
   I.instance = 0;
 
 #define NA_CK(x)                               \
@@ -236,34 +253,30 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   if (nr > 0) NA_CK(cudaMemcpyAsync(base + o_rx, rx, sizeof(Rxn) * nr, cudaMemcpyHostToDevice, s));
   if (w_out_dev != w_in_dev)
     NA_CK(cudaMemcpyAsync(w_out_dev, w_in_dev, sizeof(double) * st, cudaMemcpyDeviceToDevice, s));
-  noalloc_maps_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, c.n_pe, npf, periodic ? 1 : 0,
-                                                      (int *)I.pf_of_left, (int *)I.pf_of_right,
-                                                      I.count, I.flags, I.err);
+  NA_CK(cudaMemcpyAsync(base + o_inst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
+  noalloc_maps_kernel<<<(N + 127) / 128, 128, 0, s>>>(
+      N, c.n_pe, npf, periodic ? 1 : 0, (int *)I.pf_of_left, (int *)I.pf_of_right, I.count,
+      I.flags, I.err, I.step, TE, (int2 *)(base + o_tiles), EPB, (int2 *)(base + o_blocks));
   NA_CK(cudaGetLastError());
-  int TE = stage_tile(Q, nv, ns, nr);
-  int target = (N + 2 * 152 - 1) / (2 * 152);
-  if (target < TE) TE = target < 4 ? 4 : target;
-  double *bufs[4] = {I.wn, I.wa, I.wb, I.wn};
   for (int64_t n = 0; n < n_steps; ++n) {
     for (int stg = 0; stg < 3; ++stg) {
       StageArgs A;
-      A.win = bufs[stg];
-      A.w0 = I.wn;
-      A.wout = I.wpre;
-      A.wnext = bufs[stg + 1];
+      A.insts = (const Inst *)(base + o_inst);
+      A.tiles = (const int2 *)(base + o_tiles);
       A.s = stg;
-      A.n = n;
       A.TE = TE;
-      NA_CK(launch_stage(M, I, A, s));
+      A.R = RC;
+      A.O = c.at_order;
+      NA_CK(launch_stage(M, A, Q, n_tiles, s));
       if (I.limiter != ADG_LIM_NONE) {
         LimArgs L;
-        L.wpre = I.wpre;
-        L.wout = bufs[stg + 1];
+        L.insts = (const Inst *)(base + o_inst);
+        L.blocks = (const int2 *)(base + o_blocks);
         L.s = stg;
-        L.n = n;
-        NA_CK(launch_limiter(M, I, L, s));
+        NA_CK(launch_limiter(M, L, Q, nv, n_blocks, s));
       }
     }
+    NA_CK(launch_advance(I.step, 1, s));
   }
 #undef NA_CK
   return ADG_OK;

@@ -246,3 +246,46 @@ def test_invalid_arguments_raise():
         g.get_state(k=3)
     with pytest.raises(adg.AdgError):
         g.step(-1)
+
+
+def test_graph_replay_and_timed_steps_agree():
+    """adg_step replays a captured CUDA graph; with kernel timing on it runs a
+    graph with event pairs and waits per step. Both give the same state bit for
+    bit, and the timing counts every kernel."""
+    wl = W()["ignition-5sp-200x3"]
+    mech = wl.mechanism()
+    g = adg.ADG(mech, [wl])
+    g.set_primitive(wl.primitive(mech))
+    w0 = g.get_state()
+    g.step(12)
+    a = g.get_state()
+    g.set_state(w0)
+    g.enable_kernel_timing(True)
+    g.step(12)
+    ms, n = g.kernel_times()
+    g.enable_kernel_timing(False)
+    assert np.array_equal(g.get_state(), a)
+    assert n[0] == 36 and n[1] == 36 and n[2] == 12
+    assert ms[2] >= ms[0] + ms[1] > 0
+    assert g.launches_per_step() == 7
+
+
+def test_autotune_keeps_the_trajectory():
+    """The autotuner times candidate launch configurations of the stage kernel
+    and keeps the fastest; the result still matches the oracle."""
+    wl = W()["ignition-9sp-4096x4"]
+    wl = I.scaled(wl, 1024, 16)
+    mech = wl.mechanism()
+    CURRENT_MECH[0] = mech
+    prim = wl.primitive(mech)
+    g = adg.ADG(mech, [wl])
+    g.set_primitive(prim)
+    g.step(8)
+    tun = g.autotune()
+    assert tun and tun[0]["elements_per_tile"] >= 2 and tun[0]["chem_chunks"] >= 1
+    g.step(8)
+    g.check()
+    o = O.Oracle(wl, mech)
+    o.set_primitive(prim)
+    o.step(16)
+    assert_parity(g, o)
