@@ -51,6 +51,12 @@ extern "C" {
 #define ADG_SYNC 0
 #define ADG_CAA 1
 #define ADG_SAA 2
+/* Arithmetic of the RK-stage right-hand side (Sec. 5, mixed-precision runs).
+ * ADG_FP64: every step in double precision.
+ * ADG_MIXED: the numerical flux, the DG volume/surface/source assembly and the
+ * troubled-cell indicator and WENO reconstruction in float; the state, the
+ * Gauss-point temperature, the Arrhenius and equilibrium exponentials, the AT
+ * level sums and the RK accumulation in double. The state arrays stay double. */
 #define ADG_FP64 0
 #define ADG_MIXED 1
 
@@ -84,6 +90,7 @@ typedef struct {
   const double *delay_probs; /* host [max_delay+1], SAA only (may be NULL otherwise) */
   uint64_t seed;           /* SAA delay seed */
   double tvb_M;            /* TVB constant of the indicator (0 = TVD) */
+  int precision;           /* ADG_FP64 | ADG_MIXED */
 } adg_config;
 
 typedef struct adg_ctx adg_ctx;
@@ -164,12 +171,14 @@ int adg_enable_kernel_timing(adg_ctx *ctx, int on);
 int adg_kernel_times(adg_ctx *ctx, double *ms, int64_t *launches);
 
 /* Autotuner of the launch configuration (elements per stage tile and chemistry
- * chunks per Gauss point, per group of instances of equal degree): times the
+ * chunks per Gauss point, per group of instances): times the
  * stage kernel for every candidate that fits in shared memory on `stream`,
  * keeps the fastest and drops the captured step graphs. The trajectory is not
  * changed (the trial launches only rewrite buffers the next step rewrites).
- * Synchronous. adg_get_tuning fills tuning[4 * g + {0,1,2,3}] with the degree,
- * tile elements, chunks and tile count of group g (at most ADG_MAX_P groups). */
+ * Synchronous. Instances are grouped by degree and precision. adg_get_tuning
+ * fills tuning[5 * g + {0,1,2,3,4}] with the degree, precision, tile elements,
+ * chunks and tile count of group g (at most ADG_MAX_GROUPS groups). */
+#define ADG_MAX_GROUPS (2 * ADG_MAX_P)
 int adg_autotune(adg_ctx *ctx, void *stream);
 int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning);
 

@@ -809,10 +809,12 @@ static int neighbour(or_ctx *c, const double *arr, int e, int dir, int s, double
  * characteristic field of L(wbar_e), the face deviations v(+1)-vbar and
  * vbar-v(-1) are passed through the TVB-modified minmod with the neighbours'
  * average differences; the cell is troubled if any deviation is modified.
- * Deviations below 1e-10 of the field's magnitude sum_v |L_kv| sigma_v count as
+ * Deviations below 1e-5 of the field's magnitude sum_v |L_kv| sigma_v count as
  * zero, with sigma = (rho a + |rho u|, |rho E|, rho, .., rho) of the cell
- * average, so that rounding noise on flat data, and species present only at
- * round-off level, never flag a cell.
+ * average, so that rounding noise on flat data, species present only at
+ * round-off level, and the rounding of a run in single precision (about 1e-6
+ * of that magnitude after the characteristic transform) never flag a cell: the
+ * same cells are troubled whatever the precision of the arithmetic.
  * Limiter: v_lim = w_-1 vt_{e-1} + w_0 v_e + w_1 vt_{e+1} with vt = the neighbour
  * polynomial on Omega_e with its mean there replaced by the mean of v_e; linear
  * weights (0.001, 0.998, 0.001), eps = 1e-6; w_lim = R v_lim on modes >= 1, the
@@ -821,7 +823,7 @@ static int limit_stage(or_ctx *c, int s, uint8_t *flags) {
   int nv = c->nv, q = c->np1, ne = c->ne;
   const double gam[3] = {0.001, 0.998, 0.001};
   const double eps = 1e-6;
-  const double tau = 1e-10;
+  const double tau = 1e-5;
   double R[MAXV * MAXV], L[MAXV * MAXV], lam[MAXV];
   double own[MAXV * MAXQ], nbl[MAXV * MAXQ], nbr[MAXV * MAXQ];
   double shl[MAXV * MAXQ], shr[MAXV * MAXQ];

@@ -89,7 +89,7 @@ class Config_(C.Structure):
                 ("bc_left", C.c_int), ("bc_right", C.c_int), ("flux", C.c_int),
                 ("limiter", C.c_int), ("at_order", C.c_int), ("delay_mode", C.c_int),
                 ("max_delay", C.c_int), ("delay_probs", C.POINTER(C.c_double)),
-                ("seed", C.c_uint64), ("tvb_M", C.c_double)]
+                ("seed", C.c_uint64), ("tvb_M", C.c_double), ("precision", C.c_int)]
 
 
 _lib = None
@@ -165,11 +165,25 @@ class _MechArgs:
                             _dp(A), _dp(b), _dp(Ea))
 
 
-def config_struct(wl):
+FP64, MIXED = 0, 1
+PRECISIONS = {"fp64": FP64, "mixed": MIXED}
+
+
+def _precision(x):
+    if isinstance(x, str):
+        if x not in PRECISIONS:
+            raise AdgError(-1, "precision must be one of %s" % sorted(PRECISIONS))
+        return PRECISIONS[x]
+    if int(x) not in (FP64, MIXED):
+        raise AdgError(-1, "precision must be ADG_FP64 or ADG_MIXED")
+    return int(x)
+
+
+def config_struct(wl, precision=FP64):
     probs = np.ascontiguousarray(np.array(wl.delay_probs or [1.0], dtype=np.float64))
     c = Config_(wl.n_elem, wl.p, wl.n_pe, wl.x0, wl.length, wl.dt, wl.bc_left, wl.bc_right,
                 wl.flux, wl.limiter, wl.at_order, wl.delay_mode, wl.max_delay, _dp(probs),
-                wl.seed & ((1 << 64) - 1), wl.tvb_M)
+                wl.seed & ((1 << 64) - 1), wl.tvb_M, _precision(precision))
     return c, probs
 
 
@@ -183,11 +197,11 @@ def delay_table(wl, step0, n_steps):
     return out
 
 
-def step_noalloc(mech, wl, w_in_dev, w_out_dev, n_steps, stream=None):
+def step_noalloc(mech, wl, w_in_dev, w_out_dev, n_steps, stream=None, precision="fp64"):
     """adg_step_noalloc: advance one instance from the device tensor w_in_dev to
     w_out_dev without any allocation (scratch in the library's static array)."""
     m = _MechArgs(mech)
-    cfg, probs = config_struct(wl)
+    cfg, probs = config_struct(wl, precision)
     if stream is None:
         import torch
         stream = torch.cuda.current_stream(w_out_dev.device)
@@ -207,9 +221,10 @@ class ADG:
 
     Device memory is one PyTorch uint8 tensor handed to ``adg_create`` (the
     library carves its buffers out of it); kernels run on PyTorch's current CUDA
-    stream unless a stream is given."""
+    stream unless a stream is given. ``precision`` is "fp64" or "mixed" for all
+    instances, or a list with one entry per instance."""
 
-    def __init__(self, mech, workloads, device=None):
+    def __init__(self, mech, workloads, device=None, precision="fp64"):
         torch = _torch()
         if not torch.cuda.is_available():
             raise AdgError(-6, "ADG needs a CUDA device")
@@ -218,7 +233,12 @@ class ADG:
         self._m = _MechArgs(mech)
         self.ns = int(self._m.keep[0].shape[0])
         self.nv = self.ns + 2
-        cfgs = [config_struct(w) for w in self.workloads]
+        prec = precision if isinstance(precision, (list, tuple)) else \
+            [precision] * len(self.workloads)
+        if len(prec) != len(self.workloads):
+            raise AdgError(-1, "one precision per instance")
+        self.precision = [_precision(x) for x in prec]
+        cfgs = [config_struct(w, x) for w, x in zip(self.workloads, self.precision)]
         self._probs = [c[1] for c in cfgs]
         arr = (Config_ * len(cfgs))(*[c[0] for c in cfgs])
         self._cfgs = arr
@@ -341,10 +361,11 @@ class ADG:
 
     def tuning(self):
         n = C.c_int(0)
-        t = (C.c_int * 16)()
+        t = (C.c_int * 40)()
         _check(self.L.adg_get_tuning(self.h, C.byref(n), t), "adg_get_tuning")
-        return [{"p": t[4 * g], "elements_per_tile": t[4 * g + 1], "chem_chunks": t[4 * g + 2],
-                 "tiles": t[4 * g + 3]} for g in range(n.value)]
+        return [{"p": t[5 * g], "precision": "mixed" if t[5 * g + 1] == MIXED else "fp64",
+                 "elements_per_tile": t[5 * g + 2], "chem_chunks": t[5 * g + 3],
+                 "tiles": t[5 * g + 4]} for g in range(n.value)]
 
     def launches_per_step(self):
         return int(self.L.adg_launches_per_step(self.h))

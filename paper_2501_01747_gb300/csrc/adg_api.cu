@@ -126,9 +126,11 @@ struct InstHost {
   double *prim;   // staging for projection / temperature
 };
 
-// Instances of one polynomial degree share the stage and limiter launches.
+// Instances of one polynomial degree and precision share the stage and limiter
+// launches.
 struct Group {
   int Q = 0;
+  bool mixed = false;
   int TE = 0;                   // elements per stage tile
   int R = 1;                    // chemistry chunks per Gauss point
   int O = 1;                    // largest AT order of the group
@@ -153,7 +155,7 @@ struct adg_ctx {
   int ns, nr;
   Mech mech;
   std::vector<InstHost> inst;
-  Group groups[ADG_MAX_P];
+  Group groups[ADG_MAX_GROUPS];
   int n_groups;
   Inst *d_insts;                 // device instance table
   int64_t *d_steps;              // device step counters [n_inst]
@@ -217,6 +219,7 @@ int check_args(const adg_mechanism *m, const adg_config *cfgs, int n) {
     bool lp = c.bc_left == ADG_BC_PERIODIC, rp = c.bc_right == ADG_BC_PERIODIC;
     if (lp != rp) return ADG_ERR_ARG;
     if (c.bc_left < 0 || c.bc_left > 2 || c.bc_right < 0 || c.bc_right > 2) return ADG_ERR_ARG;
+    if (c.precision != ADG_FP64 && c.precision != ADG_MIXED) return ADG_ERR_ARG;
     if ((int64_t)c.n_elem * (c.p + 1) * (m->n_species + 3) > (int64_t)1 << 31) return ADG_ERR_ARG;
   }
   return ADG_OK;
@@ -237,15 +240,17 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
   ctx->err_all = (int *)cv.take(sizeof(int) * 4 * ctx->n_inst);
   ctx->d_insts = (Inst *)cv.take(sizeof(Inst) * ctx->n_inst);
   ctx->d_steps = (int64_t *)cv.take(sizeof(int64_t) * ctx->n_inst);
-  // groups of equal degree: tile sizes and tables
+  // groups of equal degree and precision: tile sizes and tables
   ctx->n_groups = 0;
   const int epb = limiter_elems_per_block(nv);
-  for (int Q = 2; Q <= ADG_MAX_P + 1; ++Q) {
+  for (int gk = 0; gk < ADG_MAX_GROUPS; ++gk) {
+    const int Q = 2 + gk / 2, prec = gk % 2;
+    auto member = [&](int k) { return cfgs[k].p + 1 == Q && cfgs[k].precision == prec; };
     int64_t total = 0, tiles = 0, blocks = 0;
     bool lim = false, any = false;
     int O = 1;
     for (int k = 0; k < ctx->n_inst; ++k)
-      if (cfgs[k].p + 1 == Q) {
+      if (member(k)) {
         any = true;
         total += cfgs[k].n_elem;
         lim = lim || cfgs[k].limiter != ADG_LIM_NONE;
@@ -254,15 +259,16 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
     if (!any) continue;
     Group &G = ctx->groups[ctx->n_groups++];
     G.Q = Q;
+    G.mixed = prec == ADG_MIXED;
     G.O = O;
-    G.TE = stage_tile(Q, nv, ns, nr, 8, O);
+    G.TE = stage_tile(Q, nv, ns, nr, 8, O, G.mixed);
     // smaller tiles when the group would not fill two CTAs per SM
     int64_t target = (total + 2 * 152 - 1) / (2 * 152);
     if (target < G.TE) G.TE = target < 4 ? 4 : (int)target;
     G.R = stage_chunks(G.TE, Q, nr);
     int64_t max_tiles = 0;
     for (int k = 0; k < ctx->n_inst; ++k)
-      if (cfgs[k].p + 1 == Q) {
+      if (member(k)) {
         tiles += (cfgs[k].n_elem + G.TE - 1) / G.TE;
         max_tiles += (cfgs[k].n_elem + kMinTile - 1) / kMinTile;
         blocks += (cfgs[k].n_elem + epb - 1) / epb;
@@ -307,7 +313,7 @@ static cudaError_t upload_tiles(adg_ctx *ctx, Group &G) {
   std::vector<int2> tl;
   for (int k = 0; k < ctx->n_inst; ++k) {
     const Inst &I = ctx->inst[k].d;
-    if (I.p + 1 != G.Q) continue;
+    if (I.p + 1 != G.Q || (I.mixed != 0) != G.mixed) continue;
     for (int e = 0; e < I.n_elem; e += G.TE) tl.push_back(make_int2(k, e));
   }
   G.n_tiles = (int)tl.size();
@@ -492,6 +498,7 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
     I.dx = c.length / N;
     I.dt = c.dt;
     I.tvb = c.tvb_M * I.dx * I.dx;
+    I.mixed = c.precision == ADG_MIXED;
     I.seed = c.seed;
     I.instance = k;
     double acc = 0.0;
@@ -536,7 +543,7 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
       Group &G = ctx->groups[gi];
       std::vector<int2> bl;
       for (int k = 0; k < n; ++k) {
-        if (cfgs[k].p + 1 != G.Q) continue;
+        if (cfgs[k].p + 1 != G.Q || (cfgs[k].precision == ADG_MIXED) != G.mixed) continue;
         for (int e = 0; e < cfgs[k].n_elem; e += epb) bl.push_back(make_int2(k, e));
       }
       if (upload_tiles(ctx, G) != cudaSuccess ||
@@ -672,7 +679,7 @@ static int enqueue_step(adg_ctx *ctx, cudaStream_t st) {
       A.R = G.R;
       A.O = G.O;
       CK(timed_begin(ctx, 0, st));
-      CK(launch_stage(ctx->mech, A, G.Q, G.n_tiles, st));
+      CK(launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st));
       CK(timed_end(ctx, st));
     }
     for (int gi = 0; gi < ctx->n_groups; ++gi) {
@@ -683,7 +690,7 @@ static int enqueue_step(adg_ctx *ctx, cudaStream_t st) {
       L.blocks = G.d_blocks;
       L.s = s;
       CK(timed_begin(ctx, 1, st));
-      CK(launch_limiter(ctx->mech, L, G.Q, ctx->ns + 2, G.n_blocks, st));
+      CK(launch_limiter(ctx->mech, L, G.Q, G.mixed, ctx->ns + 2, G.n_blocks, st));
       CK(timed_end(ctx, st));
     }
   }
@@ -798,7 +805,7 @@ int adg_autotune(adg_ctx *ctx, void *stream) {
       if (te < kMinTile || te * G.Q > 256) continue;
       for (int R : kR) {
         if (R > (nr > 0 ? nr : 1)) continue;
-        if (stage_smem(te, G.Q, nv, ns, nr, R, G.O) > 200 * 1024) continue;
+        if (stage_smem(te, G.Q, nv, ns, nr, R, G.O, G.mixed) > 200 * 1024) continue;
         G.TE = te;
         G.R = R;
         if (upload_tiles(ctx, G) != cudaSuccess) {
@@ -816,9 +823,9 @@ int adg_autotune(adg_ctx *ctx, void *stream) {
         // (stage buffers, the ring slot of the current level), so the
         // trajectory is unchanged
         bool ok = true;
-        for (int w = 0; w < 2 && ok; ++w) ok = launch_stage(ctx->mech, A, G.Q, G.n_tiles, st) == cudaSuccess;
+        for (int w = 0; w < 2 && ok; ++w) ok = launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
         ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
-        for (int w = 0; w < 5 && ok; ++w) ok = launch_stage(ctx->mech, A, G.Q, G.n_tiles, st) == cudaSuccess;
+        for (int w = 0; w < 5 && ok; ++w) ok = launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
         ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
         float ms = 0.0f;
         if (!ok || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
@@ -849,10 +856,11 @@ int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning) {
   *n_groups = ctx->n_groups;
   for (int gi = 0; gi < ctx->n_groups; ++gi) {
     const Group &G = ctx->groups[gi];
-    tuning[4 * gi + 0] = G.Q - 1;
-    tuning[4 * gi + 1] = G.TE;
-    tuning[4 * gi + 2] = G.R;
-    tuning[4 * gi + 3] = G.n_tiles;
+    tuning[5 * gi + 0] = G.Q - 1;
+    tuning[5 * gi + 1] = G.mixed ? ADG_MIXED : ADG_FP64;
+    tuning[5 * gi + 2] = G.TE;
+    tuning[5 * gi + 3] = G.R;
+    tuning[5 * gi + 4] = G.n_tiles;
   }
   return ADG_OK;
 }

@@ -72,6 +72,7 @@ struct Inst {
   int *err;                             // [4] code, element, stage, step (low bits)
   int64_t *step;                        // step counter of this instance (device)
   int instance;
+  int mixed;                            // ADG_MIXED: FP32 flux, DG operator, limiter
 };
 
 __host__ __device__ inline uint64_t splitmix64(uint64_t x) {
@@ -118,86 +119,99 @@ __device__ inline void report_error(const Inst &I, int code, int elem, int stage
   }
 }
 
-// Thermodynamic state of a conserved vector w (stride `st` between variables).
-struct Thermo {
-  double rho, u, T, P, a, gm1;
+// Thermodynamic state of a conserved vector w (stride `st` between variables),
+// in the arithmetic type R (double, or float for the mixed-precision flux).
+template <typename R>
+struct ThermoT {
+  R rho, u, T, P, a, gm1;
 };
+using Thermo = ThermoT<double>;
 
 // T from the internal energy: e(T) is linear for constant c_p, so the Newton
 // iteration on e(T) = e reaches its root in one step from any guess; that step
 // is this closed form. sp: species fields (shared or global memory).
-__device__ inline Thermo thermo_of(const double *sp, int ns, const double *w, int st) {
-  Thermo t;
-  double rho = 0.0, qsum = 0.0, cv = 0.0, Rm = 0.0, cpm = 0.0;
+template <typename R>
+__device__ inline ThermoT<R> thermo_t(const R *sp, int ns, const R *w, int st) {
+  ThermoT<R> t;
+  R rho = 0, qsum = 0, cv = 0, Rm = 0, cpm = 0;
   for (int i = 0; i < ns; ++i) {
-    double r = w[(2 + i) * st];
+    R r = w[(2 + i) * st];
     rho += r;
     qsum = fma(r, sp[SP_QW * ns + i], qsum);
     cv = fma(r, sp[SP_CVW * ns + i], cv);
     Rm = fma(r, sp[SP_RW * ns + i], Rm);
     cpm = fma(r, sp[SP_CPW * ns + i], cpm);
   }
-  const double irho = 1.0 / rho, icv = 1.0 / cv;
-  double m = w[0], E = w[st];
+  const R irho = R(1) / rho, icv = R(1) / cv;
+  R m = w[0], E = w[st];
   t.rho = rho;
   t.u = m * irho;
-  double rhoe = E - 0.5 * m * t.u;
+  R rhoe = E - R(0.5) * m * t.u;
   t.T = (rhoe - qsum) * icv;
   t.P = t.T * Rm;
-  double gam = cpm * icv;
-  t.gm1 = gam - 1.0;
+  R gam = cpm * icv;
+  t.gm1 = gam - R(1);
   t.a = sqrt(gam * t.P * irho);
   return t;
 }
 
+__device__ inline Thermo thermo_of(const double *sp, int ns, const double *w, int st) {
+  return thermo_t<double>(sp, ns, w, st);
+}
+
 // Physical flux component v of w (Eq. 2).
-__device__ inline double phys_flux(const double *w, int st, int v, const Thermo &t) {
+template <typename R>
+__device__ inline R phys_flux_t(const R *w, int st, int v, const ThermoT<R> &t) {
   if (v == 0) return w[0] * t.u + t.P;
   if (v == 1) return t.u * (w[st] + t.P);
   return t.u * w[v * st];
 }
 
+__device__ inline double phys_flux(const double *w, int st, int v, const Thermo &t) {
+  return phys_flux_t<double>(w, st, v, t);
+}
+
 // Numerical flux (Sec. 3.1): local Lax-Friedrichs or HLLC (Toro 1994, wave
 // speeds S_L = min(u_L - a_L, u_R - a_R), S_R = max(u_L + a_L, u_R + a_R)).
 // out[v] for v = 0..nv-1; wl, wr with unit stride.
-__device__ inline void num_flux(const double *sp, int ns, int kind, const double *wl,
-                                const double *wr, double *out, double coef, bool accumulate) {
+template <typename R>
+__device__ inline void num_flux_t(const R *sp, int ns, int kind, const R *wl, const R *wr,
+                                  R *out) {
   const int nv = ns + 2;
-  Thermo L = thermo_of(sp, ns, wl, 1), R = thermo_of(sp, ns, wr, 1);
+  ThermoT<R> L = thermo_t<R>(sp, ns, wl, 1), Rt = thermo_t<R>(sp, ns, wr, 1);
   if (kind == ADG_FLUX_LF) {
-    double lam = fmax(fabs(L.u) + L.a, fabs(R.u) + R.a);
-    for (int v = 0; v < nv; ++v) {
-      double f = 0.5 * (phys_flux(wl, 1, v, L) + phys_flux(wr, 1, v, R) - lam * (wr[v] - wl[v]));
-      out[v] = accumulate ? out[v] + coef * f : f;
-    }
+    R lam = fmax(fabs(L.u) + L.a, fabs(Rt.u) + Rt.a);
+    for (int v = 0; v < nv; ++v)
+      out[v] = R(0.5) * (phys_flux_t<R>(wl, 1, v, L) + phys_flux_t<R>(wr, 1, v, Rt) -
+                         lam * (wr[v] - wl[v]));
     return;
   }
-  double SL = fmin(L.u - L.a, R.u - R.a);
-  double SR = fmax(L.u + L.a, R.u + R.a);
-  double SM = (R.P - L.P + L.rho * L.u * (SL - L.u) - R.rho * R.u * (SR - R.u)) /
-              (L.rho * (SL - L.u) - R.rho * (SR - R.u));
+  R SL = fmin(L.u - L.a, Rt.u - Rt.a);
+  R SR = fmax(L.u + L.a, Rt.u + Rt.a);
+  R SM = (Rt.P - L.P + L.rho * L.u * (SL - L.u) - Rt.rho * Rt.u * (SR - Rt.u)) /
+         (L.rho * (SL - L.u) - Rt.rho * (SR - Rt.u));
   for (int v = 0; v < nv; ++v) {
-    double f;
-    if (0.0 <= SL) {
-      f = phys_flux(wl, 1, v, L);
-    } else if (0.0 <= SM) {
-      double c = L.rho * (SL - L.u) / (SL - SM);
-      double us;
+    R f;
+    if (R(0) <= SL) {
+      f = phys_flux_t<R>(wl, 1, v, L);
+    } else if (R(0) <= SM) {
+      R c = L.rho * (SL - L.u) / (SL - SM);
+      R us;
       if (v == 0) us = c * SM;
       else if (v == 1) us = c * (wl[1] / L.rho + (SM - L.u) * (SM + L.P / (L.rho * (SL - L.u))));
       else us = c * (wl[v] / L.rho);
-      f = phys_flux(wl, 1, v, L) + SL * (us - wl[v]);
-    } else if (0.0 <= SR) {
-      double c = R.rho * (SR - R.u) / (SR - SM);
-      double us;
+      f = phys_flux_t<R>(wl, 1, v, L) + SL * (us - wl[v]);
+    } else if (R(0) <= SR) {
+      R c = Rt.rho * (SR - Rt.u) / (SR - SM);
+      R us;
       if (v == 0) us = c * SM;
-      else if (v == 1) us = c * (wr[1] / R.rho + (SM - R.u) * (SM + R.P / (R.rho * (SR - R.u))));
-      else us = c * (wr[v] / R.rho);
-      f = phys_flux(wr, 1, v, R) + SR * (us - wr[v]);
+      else if (v == 1) us = c * (wr[1] / Rt.rho + (SM - Rt.u) * (SM + Rt.P / (Rt.rho * (SR - Rt.u))));
+      else us = c * (wr[v] / Rt.rho);
+      f = phys_flux_t<R>(wr, 1, v, Rt) + SR * (us - wr[v]);
     } else {
-      f = phys_flux(wr, 1, v, R);
+      f = phys_flux_t<R>(wr, 1, v, Rt);
     }
-    out[v] = accumulate ? out[v] + coef * f : f;
+    out[v] = f;
   }
 }
 
@@ -211,6 +225,11 @@ struct Basis {
   double Sr[MAXQ][MAXQ];  // right neighbour continued into the cell
   double WdP[MAXQ][MAXQ]; // w_q P_i'(x_q)            (volume integral)
   double WPh[MAXQ][MAXQ]; // w_q P_i(x_q) (2i+1)/2     (source projection)
+};
+
+// The same tables rounded to float, for the mixed-precision kernels.
+struct BasisF {
+  float B[MAXQ][MAXQ], Sl[MAXQ][MAXQ], Sr[MAXQ][MAXQ], WdP[MAXQ][MAXQ], WPh[MAXQ][MAXQ];
 };
 
 // Arguments of one stage-kernel launch. A launch covers every instance of one
@@ -239,13 +258,14 @@ struct ExpTable;
 void make_tables(Basis *tables, ExpTable *et);
 cudaError_t upload_basis(const Basis *tables);
 cudaError_t upload_exp_table(const ExpTable *t);
-int stage_tile(int Q, int nv, int ns, int nr, int R, int O);
+int stage_tile(int Q, int nv, int ns, int nr, int R, int O, bool mixed);
 int stage_chunks(int TE, int Q, int nr);
-size_t stage_smem(int TE, int Q, int nv, int ns, int nr, int R, int O);
+size_t stage_smem(int TE, int Q, int nv, int ns, int nr, int R, int O, bool mixed);
 cudaError_t prepare_kernels(int nv, int ns, int nr);
-cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, int n_tiles, cudaStream_t st);
-cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, int nv, int n_blocks,
-                           cudaStream_t st);
+cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, bool mixed, int n_tiles,
+                         cudaStream_t st);
+cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, bool mixed, int nv,
+                           int n_blocks, cudaStream_t st);
 cudaError_t launch_advance(int64_t *steps, int n, cudaStream_t st);
 int limiter_elems_per_block(int nv);
 cudaError_t launch_project(const Mech &M, const Inst &I, const double *prim, double *w,

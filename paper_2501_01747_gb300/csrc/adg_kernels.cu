@@ -1,47 +1,59 @@
-// CUDA kernels of the ADG hot path (sm_103a), FP64.
+// CUDA kernels of the ADG hot path (sm_103a).
 //
-// Per RK stage two kernels run:
-//   stage_kernel<Q>  : one CTA per tile of TE consecutive elements. Loads the tile
-//                      plus a one-element halo into shared memory (coalesced per
-//                      variable), evaluates every Gauss point (thermo, flux,
-//                      chemistry) with one thread per point, computes the TE+1 face
-//                      fluxes of the tile (AT flux at delayed PE faces), assembles
-//                      Eq. (5) and the SSP-RK3 combination, writes the pre-limit
-//                      stage output and the history ring of PE-boundary elements.
-//   limiter_kernel<Q>: 16 or 32 lanes per element: troubled-cell indicator in the
+// Per RK stage two kernels run, each in an FP64 and a mixed-precision variant
+// (MIX: FP32 for the flux, the DG operator and the limiter; FP64 for the
+// Gauss-point temperature, the Arrhenius and equilibrium exponentials, the AT
+// level sums and the accumulation of the conserved state):
+//   stage_kernel<Q,MIX>  : one CTA per tile of TE consecutive elements of one
+//                      instance. Loads the tile plus a one-element halo into
+//                      shared memory (coalesced per variable); Gauss-point
+//                      thermo and flux, one thread per point; chemistry, R
+//                      chunks of reactions per point; the TE+1 face fluxes of the
+//                      tile (AT levels on separate threads); Eq. (5) assembly and
+//                      the SSP-RK3 combination; writes the pre-limit output and
+//                      the history ring of PE-boundary elements.
+//   limiter_kernel<Q,G,MIX>: G lanes per element: troubled-cell indicator in the
 //                      characteristic fields of the cell average and, on troubled
 //                      cells, the (AT-)WENO reconstruction of Eq. (9)-(11). The
 //                      stage kernel writes the pre-limit output twice (limiter
 //                      input and next-stage buffer) so that the limiter only
 //                      rewrites troubled cells.
 #include <cstdio>
+#include <type_traits>
 
 #include "adg_internal.cuh"
 #include "adg_math.cuh"
 
 namespace adg {
 
-__constant__ Basis c_basis[ADG_MAX_P];   // index p-1
+__constant__ Basis c_basis[ADG_MAX_P];     // index p-1
+__constant__ BasisF c_basis_f[ADG_MAX_P];  // the same, rounded to float
 
 __constant__ ExpTable c_exp;
 
+template <bool MIX>
+using dg_t = typename std::conditional<MIX, float, double>::type;
+
 // Shared-memory footprint (bytes) of a stage tile of TE elements, R chemistry
-// chunks per Gauss point and up to O AT levels per face.
+// chunks per Gauss point and up to O AT levels per face. In the FP64 variant the
+// flux overwrites the nodal state and the summed rates stay in chunk 0; the
+// mixed variant keeps both in separate FP32 arrays.
 __host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int nv, int ns, int nr, int R,
-                                                   int O) {
+                                                   int O, bool mix) {
   size_t TQ = (size_t)TE * Q, F = TE + 1;
-  size_t n = (size_t)SP_NFIELDS * ns      // species fields
-             + 34                         // exp table and ln2/32 split
-             + (size_t)nv * (TE + 2) * Q  // modal tile with halo        [v][le][j]
-             + (size_t)nv * TQ            // nodal state, then flux      [v][t]
-             + (size_t)ns * TQ * 2        // concentrations, g/RT        [i][t]
-             + (size_t)R * ns * TQ        // production rates per chunk  [c][i][t]
-             + 2 * TQ                     // ln T, 1/T                   [t]
-             + F * nv                     // face fluxes                 [f][v]
-             + (size_t)O * F * nv         // level fluxes                [m][f][v]
-             + (size_t)O * F * 2 * nv     // traces per (level, face)    [m][f][2][v]
-             + F;                         // delay of each face (as int)
-  return n * sizeof(double) + (size_t)nr * sizeof(Rxn);
+  size_t nd = (size_t)SP_NFIELDS * ns      // species fields
+              + 34                         // exp table and ln2/32 split
+              + (size_t)nv * (TE + 2) * Q  // modal tile with halo        [v][le][j]
+              + (size_t)nv * TQ            // nodal state (FP64: then flux) [v][t]
+              + (size_t)ns * TQ * 2        // concentrations, g/RT        [i][t]
+              + (size_t)R * ns * TQ        // production rates per chunk  [c][i][t]
+              + 2 * TQ;                    // ln T, 1/T                   [t]
+  size_t nr_ = F * nv                      // face fluxes                 [f][v]
+               + (size_t)O * F * nv        // level fluxes                [m][f][v]
+               + (size_t)O * F * 2 * nv;   // traces per (level, face)    [m][f][2][v]
+  size_t extra = mix ? ((size_t)SP_NFIELDS * ns + (size_t)nv * TQ + (size_t)ns * TQ) : 0;
+  size_t bytes = nd * 8 + (nr_ + extra) * (mix ? 4 : 8) + F * 4 + 16;
+  return bytes + (size_t)nr * sizeof(Rxn);
 }
 
 // Copy an instance description into shared memory (by 8-byte words).
@@ -51,8 +63,9 @@ __device__ inline void load_inst(Inst &dst, const Inst *src) {
   for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 8); k += blockDim.x) b[k] = a[k];
 }
 
-template <int Q>
+template <int Q, bool MIX>
 __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
+  using DG = dg_t<MIX>;
   extern __shared__ __align__(16) double sm[];
   __shared__ Inst sI;
   const int2 tile = A.tiles[blockIdx.x];
@@ -60,6 +73,7 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
   __syncthreads();
   const Inst &I = sI;
   const Basis &B = c_basis[Q - 2];
+  const BasisF &BF = c_basis_f[Q - 2];
   const int nv = I.nv, ns = M.ns, nr = M.nr, N = I.n_elem, TE = A.TE;
   const int TQ = TE * Q;
   const int e0 = tile.y;
@@ -68,21 +82,32 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
   const double *A_win = (A.s == 0) ? I.wn : (A.s == 1) ? I.wa : I.wb;
   double *A_wnext = (A.s == 0) ? I.wa : (A.s == 1) ? I.wb : I.wn;
   const bool periodic = (I.bc_left == ADG_BC_PERIODIC);
+  const int R = A.R, O = A.O, NF = TE + 1;
   Rxn *srx = reinterpret_cast<Rxn *>(sm);
   double *ssp = reinterpret_cast<double *>(srx + nr);       // [F][ns]
   ExpTable *stab = reinterpret_cast<ExpTable *>(ssp + SP_NFIELDS * ns);
-  const int R = A.R, O = A.O, NF = TE + 1;
   double *sw = reinterpret_cast<double *>(stab + 1);        // [v][TE+2][Q]
-  double *snode = sw + (size_t)nv * (TE + 2) * Q;           // [v][TQ]
-  double *sconc = snode + (size_t)nv * TQ;                  // [i][TQ]
+  double *snw = sw + (size_t)nv * (TE + 2) * Q;             // [v][TQ]  nodal state
+  double *sconc = snw + (size_t)nv * TQ;                    // [i][TQ]
   double *sg = sconc + (size_t)ns * TQ;                     // [i][TQ]
   double *swd = sg + (size_t)ns * TQ;                       // [R][i][TQ]
   double *slnT = swd + (size_t)R * ns * TQ;                 // [TQ]
   double *sinvT = slnT + TQ;                                // [TQ]
-  double *sfh = sinvT + TQ;                                 // [NF][nv]
-  double *sflx = sfh + (size_t)NF * nv;                     // [O][NF][nv]
-  double *str = sflx + (size_t)O * NF * nv;                 // [O][NF][2][nv]
-  int *sk = reinterpret_cast<int *>(str + (size_t)O * NF * 2 * nv);  // [NF]
+  DG *sfh = reinterpret_cast<DG *>(sinvT + TQ);             // [NF][nv]
+  DG *sflx = sfh + (size_t)NF * nv;                         // [O][NF][nv]
+  DG *str = sflx + (size_t)O * NF * nv;                     // [O][NF][2][nv]
+  DG *sspD, *sfx, *swdD;                                    // species, flux, rates in DG
+  if constexpr (MIX) {
+    sspD = str + (size_t)O * NF * 2 * nv;
+    sfx = sspD + (size_t)SP_NFIELDS * ns;
+    swdD = sfx + (size_t)nv * TQ;
+  } else {
+    sspD = reinterpret_cast<DG *>(ssp);
+    sfx = reinterpret_cast<DG *>(snw);
+    swdD = reinterpret_cast<DG *>(swd);
+  }
+  int *sk = MIX ? reinterpret_cast<int *>(swdD + (size_t)ns * TQ)
+                : reinterpret_cast<int *>(str + (size_t)O * NF * 2 * nv);   // [NF]
   const int tid = threadIdx.x, nth = blockDim.x;
 
   // 0. mechanism, species fields and exp table into shared memory
@@ -90,7 +115,11 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
     const uint4 *src = reinterpret_cast<const uint4 *>(M.rx);
     uint4 *dst = reinterpret_cast<uint4 *>(srx);
     for (int k = tid; k < nr * (int)(sizeof(Rxn) / 16); k += nth) dst[k] = src[k];
-    for (int k = tid; k < SP_NFIELDS * ns; k += nth) ssp[k] = M.sp[k];
+    for (int k = tid; k < SP_NFIELDS * ns; k += nth) {
+      double x = M.sp[k];
+      ssp[k] = x;
+      if constexpr (MIX) sspD[k] = (DG)x;
+    }
     const double *et = reinterpret_cast<const double *>(&c_exp);
     double *dt = reinterpret_cast<double *>(stab);
     for (int k = tid; k < 34; k += nth) dt[k] = et[k];
@@ -107,14 +136,15 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
   }
   __syncthreads();
 
-  // 2a. Gauss points: conserved state, thermo, concentrations, g_i/(R T), flux
-  const double *sW = ssp + SP_W * ns, *sIW = ssp + SP_INVW * ns;
+  // 2a. Gauss points: conserved state and temperature (FP64), concentrations,
+  // g_i/(R T), and the flux
+  const double *sIW = ssp + SP_INVW * ns;
   const double *sG0 = ssp + SP_G0 * ns, *sG1 = ssp + SP_G1 * ns, *sCR = ssp + SP_CPR * ns;
   const double LN_R_PATM = log(RU / PATM);
   const int teq = te * Q;
   for (int t = tid; t < teq; t += nth) {
     int e = t / Q, q = t - e * Q, le = e + 1;
-    double *wq = snode + t;   // stride TQ between variables
+    double *wq = snw + t;   // stride TQ between variables
     for (int v = 0; v < nv; ++v) {
       double acc = 0.0;
 #pragma unroll
@@ -136,15 +166,23 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
       cq[(size_t)i * TQ] = r * sIW[i];
       gq[(size_t)i * TQ] = fma(-sCR[i], lnT, fma(sG0[i], invT, sG1[i]));
     }
-    double f0 = phys_flux(wq, TQ, 0, th), f1 = phys_flux(wq, TQ, 1, th);
-    for (int v = 2; v < nv; ++v) wq[(size_t)v * TQ] = th.u * wq[(size_t)v * TQ];
-    wq[0] = f0;
-    wq[TQ] = f1;
+    if constexpr (MIX) {
+      const DG u = (DG)th.u, P = (DG)th.P;
+      DG *fq = sfx + t;
+      fq[0] = (DG)wq[0] * u + P;
+      fq[TQ] = u * ((DG)wq[TQ] + P);
+      for (int v = 2; v < nv; ++v) fq[(size_t)v * TQ] = u * (DG)wq[(size_t)v * TQ];
+    } else {
+      double f0 = phys_flux(wq, TQ, 0, th), f1 = phys_flux(wq, TQ, 1, th);
+      for (int v = 2; v < nv; ++v) wq[(size_t)v * TQ] = th.u * wq[(size_t)v * TQ];
+      wq[0] = f0;
+      wq[TQ] = f1;
+    }
   }
   __syncthreads();
 
-  // 2b. chemistry, the reactions of every Gauss point split into R chunks:
-  // reversible rates from the species' Gibbs energies, two exponentials each
+  // 2b. chemistry (FP64), the reactions of every Gauss point split into R
+  // chunks: reversible rates from the species' Gibbs energies, two exponentials
   for (int item = tid; item < R * teq; item += nth) {
     int c = item / teq, t = item - c * teq;
     const double lnT = slnT[t], invT = sinvT[t];
@@ -181,13 +219,14 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
   }
   __syncthreads();
 
-  // 2c. sum of the chunks' rates into chunk 0
-  if (R > 1)
+  // 2c. sum of the chunks' rates (into chunk 0, or the FP32 copy)
+  if (MIX || R > 1)
     for (int item = tid; item < ns * teq; item += nth) {
       int i = item / teq, t = item - i * teq;
       double acc = swd[(size_t)i * TQ + t];
       for (int c = 1; c < R; ++c) acc += swd[((size_t)c * ns + i) * TQ + t];
-      swd[(size_t)i * TQ + t] = acc;
+      if constexpr (MIX) swdD[(size_t)i * TQ + t] = (DG)acc;
+      else swd[(size_t)i * TQ + t] = acc;
     }
   // 3a. face fluxes of the tile (local face f between local elements f and f+1),
   // one thread per (level, face): the plain flux, or one delayed level of the AT
@@ -198,14 +237,22 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
     int pf = (g < N) ? I.pf_of_left[g] : I.pf_of_right[N - 1];
     int k = (pf >= 0) ? effective_delay(I, nstep, pf) : 0;
     if (m == 0) sk[f] = k;
-    double *fl = sflx + ((size_t)m * NF + f) * nv;
-    double *wl = str + ((size_t)m * NF + f) * 2 * nv, *wr = wl + nv;
+    DG *fl = sflx + ((size_t)m * NF + f) * nv;
+    DG *wl = str + ((size_t)m * NF + f) * 2 * nv, *wr = wl + nv;
     if (k > 0) {
       if (m >= I.at_order) continue;
       int64_t lv = nstep - k - m;
       const double *bl = I.ring_in + ring_trace(I, lv, A.s, pf, 0);
       const double *br = I.ring_in + ring_trace(I, lv, A.s, pf, 1);
-      num_flux(ssp, ns, I.flux, bl, br, fl, 1.0, false);
+      if constexpr (MIX) {
+        for (int v = 0; v < nv; ++v) {
+          wl[v] = (DG)bl[v];
+          wr[v] = (DG)br[v];
+        }
+        num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
+      } else {
+        num_flux_t<double>(ssp, ns, I.flux, bl, br, fl);
+      }
       continue;
     }
     if (m > 0) continue;
@@ -215,8 +262,8 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
         a += sw[((size_t)v * (TE + 2) + f) * Q + j];
         b += ((j & 1) ? -1.0 : 1.0) * sw[((size_t)v * (TE + 2) + f + 1) * Q + j];
       }
-      wl[v] = a;
-      wr[v] = b;
+      wl[v] = (DG)a;
+      wr[v] = (DG)b;
     }
     if (!periodic && g == 0) {
       for (int v = 0; v < nv; ++v) wl[v] = wr[v];
@@ -225,50 +272,57 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
       for (int v = 0; v < nv; ++v) wr[v] = wl[v];
       if (I.bc_right == ADG_BC_REFLECT) wr[0] = -wl[0];
     }
-    num_flux(ssp, ns, I.flux, wl, wr, fl, 1.0, false);
+    num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
   }
   __syncthreads();
-  // 3b. the AT sum over levels, m = 0..o-1 in order
+  // 3b. the AT sum over levels, m = 0..o-1 in order, in FP64
   for (int item = tid; item < (te + 1) * nv; item += nth) {
     int f = item / nv, v = item - f * nv;
     int k = sk[f];
-    double acc = sflx[(size_t)f * nv + v];
+    double acc = (double)sflx[(size_t)f * nv + v];
     if (k > 0) {
       acc *= I.at[k][0];
       for (int m = 1; m < I.at_order; ++m)
-        acc = fma(I.at[k][m], sflx[((size_t)m * NF + f) * nv + v], acc);
+        acc = fma(I.at[k][m], (double)sflx[((size_t)m * NF + f) * nv + v], acc);
     }
-    sfh[(size_t)f * nv + v] = acc;
+    sfh[(size_t)f * nv + v] = (DG)acc;
   }
   __syncthreads();
 
-  // 4. assembly of Eq. (5) and the SSP-RK3 combination; history ring writes
+  // 4. assembly of Eq. (5) (in DG arithmetic) and the SSP-RK3 combination (FP64);
+  // history ring writes
   const int slot_ok = (I.npf > 0);
   const double inv_dx = 1.0 / I.dx;
+  const double *sW = ssp + SP_W * ns;
   for (int item = tid; item < nv * te; item += nth) {
     int v = item / te, e = item - v * te, ge = e0 + e, le = e + 1;
     const double *wi = sw + ((size_t)v * (TE + 2) + le) * Q;
-    const double *fq = snode + (size_t)v * TQ + e * Q;
-    const double *sq = (v >= 2) ? swd + (size_t)(v - 2) * TQ + e * Q : nullptr;
-    const double Wv = (v >= 2) ? sW[v - 2] : 0.0;
-    const double fr = sfh[(size_t)(e + 1) * nv + v], fl = sfh[(size_t)e * nv + v];
-    double fqr[Q], sqr[Q];
+    const DG *fq = sfx + (size_t)v * TQ + e * Q;
+    const DG *sq = (v >= 2) ? swdD + (size_t)(v - 2) * TQ + e * Q : nullptr;
+    const DG Wv = (v >= 2) ? (DG)sW[v - 2] : DG(0);
+    const DG fr = sfh[(size_t)(e + 1) * nv + v], fl = sfh[(size_t)e * nv + v];
+    DG fqr[Q], sqr[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       fqr[q] = fq[q];
-      sqr[q] = (v >= 2) ? sq[q] : 0.0;
+      sqr[q] = (v >= 2) ? sq[q] : DG(0);
     }
     double out[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      double V = 0.0, S = 0.0;
+      DG V = 0, S = 0;
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        V = fma(B.WdP[q][i], fqr[q], V);
-        S = fma(B.WPh[q][i], sqr[q], S);
+        if constexpr (MIX) {
+          V = fma(BF.WdP[q][i], fqr[q], V);
+          S = fma(BF.WPh[q][i], sqr[q], S);
+        } else {
+          V = fma(B.WdP[q][i], fqr[q], V);
+          S = fma(B.WPh[q][i], sqr[q], S);
+        }
       }
-      double surf = (i & 1) ? (V - fr - fl) : (V - fr + fl);
-      double r = fma((2.0 * i + 1.0) * inv_dx, surf, Wv * S);
+      DG surf = (i & 1) ? (V - fr - fl) : (V - fr + fl);
+      double r = (double)fma((DG)((2.0 * i + 1.0) * inv_dx), surf, Wv * S);
       size_t gi = ((size_t)v * N + ge) * Q + i;
       double o;
       if (A.s == 0) o = fma(I.dt, r, I.wn[gi]);
@@ -304,22 +358,25 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
   }
 }
 
-__device__ inline double minmod3(double a, double b, double c) {
-  if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
-  if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
-  return 0.0;
+template <typename R>
+__device__ inline R minmod3(R a, R b, R c) {
+  if (a > R(0) && b > R(0) && c > R(0)) return fmin(a, fmin(b, c));
+  if (a < R(0) && b < R(0) && c < R(0)) return fmax(a, fmax(b, c));
+  return R(0);
 }
 
-// Shared memory (doubles) per element of the limiter: the element and its two
-// neighbours, the limited characteristic modes, gradP.w, the partial-density
-// sums and momenta of the three blocks, the per-species phi_k, two mode sums.
-__host__ __device__ inline int limiter_elem_doubles(int nv, int ns, int Q) {
+// Shared memory (words of the arithmetic type) per element of the limiter: the
+// element and its two neighbours, the limited characteristic modes, gradP.w, the
+// partial-density sums and momenta of the three blocks, phi_k, two mode sums and
+// the mode sums of block 0.
+__host__ __device__ inline int limiter_elem_words(int nv, int ns, int Q) {
   return 3 * nv * Q + nv * Q + 3 * 3 * Q + ns + 2 * Q + 8;
 }
 constexpr int LIM_WARPS = 8;
 
 // Troubled-cell indicator and (AT-)WENO limiter (Sec. 3.3, Eq. 9-11), a group of
-// G lanes per element (G = 16 when nv <= 16, else 32).
+// G lanes per element (G = 16 when nv <= 16, else 32), in the arithmetic type of
+// the precision variant.
 // Eigen-structure of the frozen Jacobian at the cell average: right vectors
 // r_-/+ = (u -/+ a, H -/+ u a, Y), species r_k = (u, u^2 - phi_k/g, e_k); left
 // vectors l_-/+ = (gradP -/+ a (1, 0, -u..-u)) / (2 a^2), l_k = e_k - Y_k gradP/a^2,
@@ -327,12 +384,12 @@ constexpr int LIM_WARPS = 8;
 // Every characteristic value is written in one branch-free form,
 // v = A gradP.w + B (rho u)_w + C (sum rho Y)_w + D (rho Y_k)_w,
 // with (A, B, C, D) = (1/2a^2, -/+ a/2a^2, +/- a u/2a^2, 0) for the acoustic fields
-// and (-Y_k/a^2, 0, 0, 1) for species k, so that all lanes run the same FP64 code.
-// The stage kernel has already written the pre-limit values into the output;
-// only troubled cells are rewritten here.
-template <int Q, int G>
+// and (-Y_k/a^2, 0, 0, 1) for species k, so that all lanes run the same code.
+template <int Q, int G, bool MIX>
 __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs A) {
-  extern __shared__ __align__(16) double lsm[];
+  using DG = dg_t<MIX>;
+  extern __shared__ __align__(16) double lsm_raw[];
+  DG *lsm = reinterpret_cast<DG *>(lsm_raw);
   __shared__ Inst sI;
   const int2 blkid = A.blocks[blockIdx.x];
   load_inst(sI, A.insts + blkid.x);
@@ -340,6 +397,7 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs
   const Inst &I = sI;
   if (I.limiter == ADG_LIM_NONE) return;
   const Basis &B = c_basis[Q - 2];
+  const BasisF &BF = c_basis_f[Q - 2];
   const int N = I.n_elem, nv = I.nv, ns = M.ns;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gl = lane % G, gw = lane / G;
@@ -354,22 +412,22 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs
   const unsigned gmask = (G == 32) ? FULL : (0xffffu << (16 * gw));
   const size_t VS = (size_t)N * Q;
   const int NB = nv * Q;
-  double *blk = lsm + (size_t)slot * limiter_elem_doubles(nv, ns, Q);  // [3][nv][Q]
-  double *vlim = blk + 3 * NB;                                          // [nv][Q]
-  double *gpv = vlim + NB;                                              // [3][Q]
-  double *rsv = gpv + 3 * Q;                                            // [3][Q]
-  double *mmv = rsv + 3 * Q;                                            // [3][Q]
-  double *phi = mmv + 3 * Q;                                            // [ns]
-  double *sums = phi + ns;                                              // [2][Q]
-  double *ssum = sums + 2 * Q;   // mode sums of block 0: gp, mm, rs (plain, alternating)
+  DG *blk = lsm + (size_t)slot * limiter_elem_words(nv, ns, Q);  // [3][nv][Q]
+  DG *vlim = blk + 3 * NB;                                        // [nv][Q]
+  DG *gpv = vlim + NB;                                            // [3][Q]
+  DG *rsv = gpv + 3 * Q;                                          // [3][Q]
+  DG *mmv = rsv + 3 * Q;                                          // [3][Q]
+  DG *phi = mmv + 3 * Q;                                          // [ns]
+  DG *sums = phi + ns;                                            // [2][Q]
+  DG *ssum = sums + 2 * Q;   // mode sums of block 0: gp, mm, rs (plain, alternating)
   const bool periodic = (I.bc_left == ADG_BC_PERIODIC);
 
   // 1. the element (block 0) and its neighbours (1 left, 2 right): the pre-limit
   //    field, the AT extrapolation of the neighbour's pre-limit history across a
-  //    delayed PE face (Eq. 11), or a boundary ghost
+  //    delayed PE face (Eq. 11, summed in FP64), or a boundary ghost
   if (valid) {
     for (int d = 0; d < 3; ++d) {
-      double *dst = blk + d * NB;
+      DG *dst = blk + d * NB;
       int src = e, ghost = 0, k = 0, pf = -1;
       if (d > 0) {
         pf = d == 1 ? I.pf_of_left[e] : I.pf_of_right[e];
@@ -390,14 +448,14 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs
           double acc = 0.0;
           for (int m = 0; m < I.at_order; ++m)
             acc += I.at[k][m] * I.ring_pre[ring_block(I, nstep - k - m, A.s, pf, side) + t];
-          dst[t] = acc;
+          dst[t] = (DG)acc;
         }
       } else {
         for (int t = gl; t < NB; t += G) {
           int v = t / Q, j = t - v * Q;
           double x = A_wpre[(size_t)v * VS + (size_t)src * Q + j];
           if (ghost && (((j & 1) != 0) != (v == 0))) x = -x;
-          dst[t] = x;
+          dst[t] = (DG)x;
         }
       }
     }
@@ -405,17 +463,17 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs
   __syncwarp();
 
   // 2. cell average: thermo and eigen-quantities (species sums split over lanes)
-  const double *qW = M.sp + SP_QW * ns, *cvW = M.sp + SP_CVW * ns;
-  const double *RW = M.sp + SP_RW * ns, *cpW = M.sp + SP_CPW * ns;
-  double rho = 0.0, qsum = 0.0, cv = 0.0, Rm = 0.0, cpm = 0.0;
+  const double *qWd = M.sp + SP_QW * ns, *cvWd = M.sp + SP_CVW * ns;
+  const double *RWd = M.sp + SP_RW * ns, *cpWd = M.sp + SP_CPW * ns;
+  DG rho = 0, qsum = 0, cv = 0, Rm = 0, cpm = 0;
   if (valid)
     for (int i = gl; i < ns; i += G) {
-      double r = blk[(2 + i) * Q];
+      DG r = blk[(2 + i) * Q];
       rho += r;
-      qsum = fma(r, qW[i], qsum);
-      cv = fma(r, cvW[i], cv);
-      Rm = fma(r, RW[i], Rm);
-      cpm = fma(r, cpW[i], cpm);
+      qsum = fma(r, (DG)qWd[i], qsum);
+      cv = fma(r, (DG)cvWd[i], cv);
+      Rm = fma(r, (DG)RWd[i], Rm);
+      cpm = fma(r, (DG)cpWd[i], cpm);
     }
   for (int o = G / 2; o > 0; o >>= 1) {
     rho += __shfl_xor_sync(FULL, rho, o, G);
@@ -425,27 +483,27 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs
     cpm += __shfl_xor_sync(FULL, cpm, o, G);
   }
   if (!valid) {
-    rho = 1.0;
-    cv = 1.0;
-    cpm = 2.0;
-    Rm = 1.0;
+    rho = 1;
+    cv = 1;
+    cpm = 2;
+    Rm = 1;
   }
-  const double irho = 1.0 / rho, icv = 1.0 / cv;
-  const double m0 = valid ? blk[0] : 0.0, E0 = valid ? blk[Q] : 1.0;
-  const double u = m0 * irho;
-  const double T = (E0 - 0.5 * m0 * u - qsum) * icv;
-  const double P = T * Rm;
-  const double gam = cpm * icv, g = gam - 1.0;
-  const double a = sqrt(gam * P * irho);
-  const double H = (E0 + P) * irho;
-  const double ia2 = 1.0 / (a * a);
-  if (valid && gl == 0 && (!(rho > 0.0) || !(T > 0.0) || !isfinite(T)))
+  const DG irho = DG(1) / rho, icv = DG(1) / cv;
+  const DG m0 = valid ? blk[0] : DG(0), E0 = valid ? blk[Q] : DG(1);
+  const DG u = m0 * irho;
+  const DG T = (E0 - DG(0.5) * m0 * u - qsum) * icv;
+  const DG P = T * Rm;
+  const DG gam = cpm * icv, g = gam - DG(1);
+  const DG a = sqrt(gam * P * irho);
+  const DG H = (E0 + P) * irho;
+  const DG ia2 = DG(1) / (a * a);
+  if (valid && gl == 0 && (!(rho > DG(0)) || !(T > DG(0)) || !isfinite(T)))
     report_error(I, ADG_ERR_NONPHYSICAL, e, A.s, nstep);
   // phi_k, and the sums of |phi_i|, |phi_i - a u|, |phi_i + a u| for the noise floor
-  double sphi = 0.0, sphm = 0.0, sphp = 0.0;
+  DG sphi = 0, sphm = 0, sphp = 0;
   if (valid) {
     for (int i = gl; i < ns; i += G) {
-      double ph = fma(g, fma(-cvW[i], T, 0.5 * u * u - qW[i]), T * RW[i]);
+      DG ph = fma(g, fma(-(DG)cvWd[i], T, DG(0.5) * u * u - (DG)qWd[i]), T * (DG)RWd[i]);
       phi[i] = ph;
       sphi += fabs(ph);
       sphm += fabs(ph - a * u);
@@ -461,10 +519,10 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs
   if (valid)
     for (int t = gl; t < 3 * Q; t += G) {
       int b = t / Q, j = t - b * Q;
-      const double *x = blk + b * NB;
-      double acc = g * fma(-u, x[j], x[Q + j]), sr = 0.0;
+      const DG *x = blk + b * NB;
+      DG acc = g * fma(-u, x[j], x[Q + j]), sr = 0;
       for (int i = 0; i < ns; ++i) {
-        double r = x[(2 + i) * Q + j];
+        DG r = x[(2 + i) * Q + j];
         acc = fma(phi[i], r, acc);
         sr += r;
       }
@@ -474,59 +532,61 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs
     }
   __syncwarp();
   if (valid && gl < 6) {
-    const double *src = (gl % 3 == 0) ? gpv : (gl % 3 == 1) ? mmv : rsv;
-    double acc = 0.0;
+    const DG *src = (gl % 3 == 0) ? gpv : (gl % 3 == 1) ? mmv : rsv;
+    DG acc = 0;
     for (int j = 0; j < Q; ++j) acc += (gl >= 3 && (j & 1)) ? -src[j] : src[j];
     ssum[gl] = acc;
   }
   __syncwarp();
 
   // coefficients of field k and its value for block b, mode j
-  const double ha2 = 0.5 * ia2;
-  auto coef = [&](int k, double &cA, double &cB, double &cC, double &cD, int &ri) {
+  const DG ha2 = DG(0.5) * ia2;
+  auto coef = [&](int k, DG &cA, DG &cB, DG &cC, DG &cD, int &ri) {
     bool ac = (k == 0) || (k == nv - 1);
-    double sgn = (k == 0) ? -1.0 : 1.0;
+    DG sgn = (k == 0) ? DG(-1) : DG(1);
     ri = ac ? 0 : k - 1;
-    double Yk = ac ? 0.0 : blk[(2 + ri) * Q] * irho;
+    DG Yk = ac ? DG(0) : blk[(2 + ri) * Q] * irho;
     cA = ac ? ha2 : -Yk * ia2;
-    cB = ac ? sgn * a * ha2 : 0.0;
-    cC = ac ? -sgn * a * u * ha2 : 0.0;
-    cD = ac ? 0.0 : 1.0;
+    cB = ac ? sgn * a * ha2 : DG(0);
+    cC = ac ? -sgn * a * u * ha2 : DG(0);
+    cD = ac ? DG(0) : DG(1);
   };
-  auto val = [&](double cA, double cB, double cC, double cD, int ri, int b, int j) {
+  auto val = [&](DG cA, DG cB, DG cC, DG cD, int ri, int b, int j) {
     return fma(cA, gpv[b * Q + j],
                fma(cB, mmv[b * Q + j], fma(cC, rsv[b * Q + j], cD * blk[b * NB + (2 + ri) * Q + j])));
   };
 
   // 3. indicator: the lanes of a group test the fields
-  const double sig0 = fma(rho, a, fabs(m0)), sig1 = fabs(E0), sigr = rho;
-  const double tvb = I.tvb, tau = 1e-10;
+  const DG sig0 = fma(rho, a, fabs(m0)), sig1 = fabs(E0), sigr = rho;
+  // noise floor 1e-5 of the field's magnitude in both precisions: above the
+  // single-precision rounding, so both variants select the same troubled cells
+  const DG tvb = (DG)I.tvb, tau = DG(1e-5);
   bool mine = false;
   if (valid)
     for (int k = gl; k < nv; k += G) {
-      double cA, cB, cC, cD;
+      DG cA, cB, cC, cD;
       int ri;
       coef(k, cA, cB, cC, cD, ri);
       // the face values v(+1), v(-1) from the mode sums (linear in the modes)
-      const double *rk = blk + (2 + ri) * Q;
-      double rsum = 0.0, ralt = 0.0;
+      const DG *rk = blk + (2 + ri) * Q;
+      DG rsum = 0, ralt = 0;
 #pragma unroll
       for (int j = 0; j < Q; ++j) {
         rsum += rk[j];
         ralt += (j & 1) ? -rk[j] : rk[j];
       }
-      double vb = val(cA, cB, cC, cD, ri, 0, 0);
-      double vp = fma(cA, ssum[0], fma(cB, ssum[1], fma(cC, ssum[2], cD * rsum)));
-      double vm = fma(cA, ssum[3], fma(cB, ssum[4], fma(cC, ssum[5], cD * ralt)));
-      double vL = val(cA, cB, cC, cD, ri, 1, 0), vR = val(cA, cB, cC, cD, ri, 2, 0);
+      DG vb = val(cA, cB, cC, cD, ri, 0, 0);
+      DG vp = fma(cA, ssum[0], fma(cB, ssum[1], fma(cC, ssum[2], cD * rsum)));
+      DG vm = fma(cA, ssum[3], fma(cB, ssum[4], fma(cC, ssum[5], cD * ralt)));
+      DG vL = val(cA, cB, cC, cD, ri, 1, 0), vR = val(cA, cB, cC, cD, ri, 2, 0);
       // sum_v |L_kv| sigma_v in closed form: for species k, |1 + A phi_k| plus
       // |A| (sum |phi| - |phi_k|); for the acoustic fields A sum |phi_i -/+ a u|
       bool ac = (k == 0) || (k == nv - 1);
-      double sr = ac ? cA * (k == 0 ? sphp : sphm)
-                     : fabs(fma(cA, phi[ri], 1.0)) + fabs(cA) * (sphi - fabs(phi[ri]));
-      double scale = fma(fabs(fma(cA, -u * g, cB)), sig0, fma(fabs(cA * g), sig1, sr * sigr));
-      double ut = vp - vb, utt = vb - vm, dp = vR - vb, dm = vb - vL;
-      double fl = tau * scale;
+      DG srr = ac ? cA * (k == 0 ? sphp : sphm)
+                  : fabs(fma(cA, phi[ri], DG(1))) + fabs(cA) * (sphi - fabs(phi[ri]));
+      DG scale = fma(fabs(fma(cA, -u * g, cB)), sig0, fma(fabs(cA * g), sig1, srr * sigr));
+      DG ut = vp - vb, utt = vb - vm, dp = vR - vb, dm = vb - vL;
+      DG fl = tau * scale;
       if (fabs(ut) > fl && fabs(ut) > tvb && minmod3(ut, dp, dm) != ut) mine = true;
       if (fabs(utt) > fl && fabs(utt) > tvb && minmod3(utt, dp, dm) != utt) mine = true;
     }
@@ -539,13 +599,13 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs
   if (!troubled) return;
 
   // 4. WENO (Eq. 9-10) per characteristic field, the group's lanes over fields
-  const double gmw[3] = {0.001, 0.998, 0.001};
-  const double eps = 1e-6;
+  const DG gmw[3] = {DG(0.001), DG(0.998), DG(0.001)};
+  const DG eps = DG(1e-6);
   for (int k = gl; k < nv; k += G) {
-    double cA, cB, cC, cD;
+    DG cA, cB, cC, cD;
     int ri;
     coef(k, cA, cB, cC, cD, ri);
-    double vo[Q], vl0[Q], vr0[Q], vl[Q], vr[Q];
+    DG vo[Q], vl0[Q], vr0[Q], vl[Q], vr[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
       vo[j] = val(cA, cB, cC, cD, ri, 0, j);
@@ -555,33 +615,49 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs
     // neighbours continued into this cell, their mean replaced by the own mean
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      double al = 0.0, ar = 0.0;
+      DG al = 0, ar = 0;
 #pragma unroll
       for (int j = 0; j < Q; ++j) {
-        al = fma(B.Sl[i][j], vl0[j], al);
-        ar = fma(B.Sr[i][j], vr0[j], ar);
+        if constexpr (MIX) {
+          al = fma(BF.Sl[i][j], vl0[j], al);
+          ar = fma(BF.Sr[i][j], vr0[j], ar);
+        } else {
+          al = fma(B.Sl[i][j], vl0[j], al);
+          ar = fma(B.Sr[i][j], vr0[j], ar);
+        }
       }
       vl[i] = al;
       vr[i] = ar;
     }
     vl[0] = vo[0];
     vr[0] = vo[0];
-    double be[3] = {0.0, 0.0, 0.0};
+    DG be[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 1; i < Q; ++i)
 #pragma unroll
       for (int j = 1; j < Q; ++j) {
-        be[0] = fma(vl[i] * B.B[i][j], vl[j], be[0]);
-        be[1] = fma(vo[i] * B.B[i][j], vo[j], be[1]);
-        be[2] = fma(vr[i] * B.B[i][j], vr[j], be[2]);
+        DG bij = MIX ? (DG)BF.B[i][j] : (DG)B.B[i][j];
+        be[0] = fma(vl[i] * bij, vl[j], be[0]);
+        be[1] = fma(vo[i] * bij, vo[j], be[1]);
+        be[2] = fma(vr[i] * bij, vr[j], be[2]);
       }
-    double wt[3], sw = 0.0;
-    for (int t = 0; t < 3; ++t) {
-      double d = eps + be[t];
-      wt[t] = gmw[t] / (d * d);
-      sw += wt[t];
+    DG wt[3], sw = 0;
+    if constexpr (MIX) {
+      // the same normalised weights written as ratios, safe from overflow in FP32
+      DG dmin = fmin(eps + be[0], fmin(eps + be[1], eps + be[2]));
+      for (int t = 0; t < 3; ++t) {
+        DG rr = dmin / (eps + be[t]);
+        wt[t] = gmw[t] * rr * rr;
+        sw += wt[t];
+      }
+    } else {
+      for (int t = 0; t < 3; ++t) {
+        DG d = eps + be[t];
+        wt[t] = gmw[t] / (d * d);
+        sw += wt[t];
+      }
     }
-    double isw = 1.0 / sw;
+    DG isw = DG(1) / sw;
     vlim[k * Q] = vo[0];
 #pragma unroll
     for (int i = 1; i < Q; ++i)
@@ -590,9 +666,9 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs
   __syncwarp(gmask);
   // 5. back to conserved variables with R (modes >= 1; the cell average is kept)
   for (int i = gl; i < Q; i += G) {
-    double s1 = 0.0, s2 = 0.0;
+    DG s1 = 0, s2 = 0;
     for (int k = 1; k < nv - 1; ++k) {
-      double x = vlim[k * Q + i];
+      DG x = vlim[k * Q + i];
       s1 += x;
       s2 = fma(x, u * u - phi[k - 1] / g, s2);
     }
@@ -604,12 +680,12 @@ __global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs
   for (int t = gl; t < NB; t += G) {
     int v = t / Q, i = t - v * Q;
     if (i == 0) continue;
-    double lm = vlim[i], lp = vlim[(nv - 1) * Q + i];
-    double o;
+    DG lm = vlim[i], lp = vlim[(nv - 1) * Q + i];
+    DG o;
     if (v == 0) o = lm * (u - a) + lp * (u + a) + u * sums[i];
     else if (v == 1) o = lm * (H - u * a) + lp * (H + u * a) + sums[Q + i];
     else o = (lm + lp) * (blk[v * Q] * irho) + vlim[(v - 1) * Q + i];
-    out[(size_t)v * VS + i] = o;
+    out[(size_t)v * VS + i] = (double)o;
   }
 }
 
@@ -665,13 +741,25 @@ __global__ void temperature_kernel(Mech M, Inst I, const double *w, double *T) {
 // host-side launchers
 
 cudaError_t upload_basis(const Basis *tables) {
-  return cudaMemcpyToSymbol(c_basis, tables, sizeof(Basis) * ADG_MAX_P);
+  cudaError_t e = cudaMemcpyToSymbol(c_basis, tables, sizeof(Basis) * ADG_MAX_P);
+  if (e != cudaSuccess) return e;
+  BasisF f[ADG_MAX_P];
+  for (int p = 0; p < ADG_MAX_P; ++p)
+    for (int i = 0; i < MAXQ; ++i)
+      for (int j = 0; j < MAXQ; ++j) {
+        f[p].B[i][j] = (float)tables[p].B[i][j];
+        f[p].Sl[i][j] = (float)tables[p].Sl[i][j];
+        f[p].Sr[i][j] = (float)tables[p].Sr[i][j];
+        f[p].WdP[i][j] = (float)tables[p].WdP[i][j];
+        f[p].WPh[i][j] = (float)tables[p].WPh[i][j];
+      }
+  return cudaMemcpyToSymbol(c_basis_f, f, sizeof(BasisF) * ADG_MAX_P);
 }
 
-int stage_tile(int Q, int nv, int ns, int nr, int R, int O) {
+int stage_tile(int Q, int nv, int ns, int nr, int R, int O, bool mixed) {
   // elements per tile: up to 256 Gauss-point threads, at most ~96 KB of tile
   int TE = 256 / Q;
-  while (TE > 2 && stage_smem_bytes(TE, Q, nv, ns, nr, R, O) > 96 * 1024) TE /= 2;
+  while (TE > 2 && stage_smem_bytes(TE, Q, nv, ns, nr, R, O, mixed) > 96 * 1024) TE /= 2;
   return TE;
 }
 
@@ -692,57 +780,70 @@ int stage_chunks(int TE, int Q, int nr) {
   return best;
 }
 
-size_t stage_smem(int TE, int Q, int nv, int ns, int nr, int R, int O) {
-  return stage_smem_bytes(TE, Q, nv, ns, nr, R, O);
+size_t stage_smem(int TE, int Q, int nv, int ns, int nr, int R, int O, bool mixed) {
+  return stage_smem_bytes(TE, Q, nv, ns, nr, R, O, mixed);
 }
 
 cudaError_t upload_exp_table(const ExpTable *t) {
   return cudaMemcpyToSymbol(c_exp, t, sizeof(ExpTable));
 }
 
-template <int Q>
-static cudaError_t launch_stage_q(const Mech &M, const StageArgs &A, int n_tiles,
-                                  cudaStream_t st) {
+template <int Q, bool MIX>
+static cudaError_t launch_stage_qm(const Mech &M, const StageArgs &A, int n_tiles,
+                                   cudaStream_t st) {
   int nv = M.ns + 2;
-  size_t smem = stage_smem_bytes(A.TE, Q, nv, M.ns, M.nr, A.R, A.O);
+  size_t smem = stage_smem_bytes(A.TE, Q, nv, M.ns, M.nr, A.R, A.O, MIX);
   int nth = ((A.TE * Q + 31) / 32) * 32;
-  stage_kernel<Q><<<n_tiles, nth, smem, st>>>(M, A);
+  stage_kernel<Q, MIX><<<n_tiles, nth, smem, st>>>(M, A);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, int n_tiles, cudaStream_t st) {
-  switch (Q) {
-    case 2: return launch_stage_q<2>(M, A, n_tiles, st);
-    case 3: return launch_stage_q<3>(M, A, n_tiles, st);
-    case 4: return launch_stage_q<4>(M, A, n_tiles, st);
-    case 5: return launch_stage_q<5>(M, A, n_tiles, st);
+cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, bool mixed, int n_tiles,
+                         cudaStream_t st) {
+  switch (Q * 2 + (mixed ? 1 : 0)) {
+    case 4: return launch_stage_qm<2, false>(M, A, n_tiles, st);
+    case 5: return launch_stage_qm<2, true>(M, A, n_tiles, st);
+    case 6: return launch_stage_qm<3, false>(M, A, n_tiles, st);
+    case 7: return launch_stage_qm<3, true>(M, A, n_tiles, st);
+    case 8: return launch_stage_qm<4, false>(M, A, n_tiles, st);
+    case 9: return launch_stage_qm<4, true>(M, A, n_tiles, st);
+    case 10: return launch_stage_qm<5, false>(M, A, n_tiles, st);
+    case 11: return launch_stage_qm<5, true>(M, A, n_tiles, st);
   }
   return cudaErrorInvalidValue;
 }
 
 int limiter_elems_per_block(int nv) { return LIM_WARPS * (nv <= 16 ? 2 : 1); }
 
-template <int Q, int G>
-static cudaError_t launch_limiter_qg(const Mech &M, const LimArgs &A, int nv, int n_blocks,
-                                     cudaStream_t st) {
+template <int Q, int G, bool MIX>
+static cudaError_t launch_limiter_qgm(const Mech &M, const LimArgs &A, int nv, int n_blocks,
+                                      cudaStream_t st) {
   constexpr int EPW = 32 / G;
-  size_t smem = (size_t)LIM_WARPS * EPW * limiter_elem_doubles(nv, M.ns, Q) * sizeof(double);
-  limiter_kernel<Q, G><<<n_blocks, 32 * LIM_WARPS, smem, st>>>(M, A);
+  size_t smem = (size_t)LIM_WARPS * EPW * limiter_elem_words(nv, M.ns, Q) *
+                (MIX ? sizeof(float) : sizeof(double));
+  smem = (smem + 15) & ~(size_t)15;
+  limiter_kernel<Q, G, MIX><<<n_blocks, 32 * LIM_WARPS, smem, st>>>(M, A);
   return cudaGetLastError();
 }
 
-cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, int nv, int n_blocks,
-                           cudaStream_t st) {
-  bool g16 = nv <= 16;
-  switch (Q) {
-    case 2: return g16 ? launch_limiter_qg<2, 16>(M, A, nv, n_blocks, st)
-                       : launch_limiter_qg<2, 32>(M, A, nv, n_blocks, st);
-    case 3: return g16 ? launch_limiter_qg<3, 16>(M, A, nv, n_blocks, st)
-                       : launch_limiter_qg<3, 32>(M, A, nv, n_blocks, st);
-    case 4: return g16 ? launch_limiter_qg<4, 16>(M, A, nv, n_blocks, st)
-                       : launch_limiter_qg<4, 32>(M, A, nv, n_blocks, st);
-    case 5: return g16 ? launch_limiter_qg<5, 16>(M, A, nv, n_blocks, st)
-                       : launch_limiter_qg<5, 32>(M, A, nv, n_blocks, st);
+template <int Q, bool MIX>
+static cudaError_t launch_limiter_qm(const Mech &M, const LimArgs &A, int nv, int n_blocks,
+                                     cudaStream_t st) {
+  if (nv <= 16) return launch_limiter_qgm<Q, 16, MIX>(M, A, nv, n_blocks, st);
+  return launch_limiter_qgm<Q, 32, MIX>(M, A, nv, n_blocks, st);
+}
+
+cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, bool mixed, int nv,
+                           int n_blocks, cudaStream_t st) {
+  switch (Q * 2 + (mixed ? 1 : 0)) {
+    case 4: return launch_limiter_qm<2, false>(M, A, nv, n_blocks, st);
+    case 5: return launch_limiter_qm<2, true>(M, A, nv, n_blocks, st);
+    case 6: return launch_limiter_qm<3, false>(M, A, nv, n_blocks, st);
+    case 7: return launch_limiter_qm<3, true>(M, A, nv, n_blocks, st);
+    case 8: return launch_limiter_qm<4, false>(M, A, nv, n_blocks, st);
+    case 9: return launch_limiter_qm<4, true>(M, A, nv, n_blocks, st);
+    case 10: return launch_limiter_qm<5, false>(M, A, nv, n_blocks, st);
+    case 11: return launch_limiter_qm<5, true>(M, A, nv, n_blocks, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -755,20 +856,33 @@ cudaError_t prepare_kernels(int nv, int ns, int nr) {
   (void)nr;
   const int lim = 200 * 1024;
   cudaError_t e = cudaSuccess;
-#define SET(fn) \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
-  SET(stage_kernel<2>);
-  SET(stage_kernel<3>);
-  SET(stage_kernel<4>);
-  SET(stage_kernel<5>);
-  SET((limiter_kernel<2, 16>));
-  SET((limiter_kernel<3, 16>));
-  SET((limiter_kernel<4, 16>));
-  SET((limiter_kernel<5, 16>));
-  SET((limiter_kernel<2, 32>));
-  SET((limiter_kernel<3, 32>));
-  SET((limiter_kernel<4, 32>));
-  SET((limiter_kernel<5, 32>));
+#define SET(...) \
+  if (e == cudaSuccess)     \
+  e = cudaFuncSetAttribute(__VA_ARGS__, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+  SET(stage_kernel<2, false>);
+  SET(stage_kernel<3, false>);
+  SET(stage_kernel<4, false>);
+  SET(stage_kernel<5, false>);
+  SET(stage_kernel<2, true>);
+  SET(stage_kernel<3, true>);
+  SET(stage_kernel<4, true>);
+  SET(stage_kernel<5, true>);
+  SET(limiter_kernel<2, 16, false>);
+  SET(limiter_kernel<3, 16, false>);
+  SET(limiter_kernel<4, 16, false>);
+  SET(limiter_kernel<5, 16, false>);
+  SET(limiter_kernel<2, 32, false>);
+  SET(limiter_kernel<3, 32, false>);
+  SET(limiter_kernel<4, 32, false>);
+  SET(limiter_kernel<5, 32, false>);
+  SET(limiter_kernel<2, 16, true>);
+  SET(limiter_kernel<3, 16, true>);
+  SET(limiter_kernel<4, 16, true>);
+  SET(limiter_kernel<5, 16, true>);
+  SET(limiter_kernel<2, 32, true>);
+  SET(limiter_kernel<3, 32, true>);
+  SET(limiter_kernel<4, 32, true>);
+  SET(limiter_kernel<5, 32, true>);
 #undef SET
   return e;
 }

@@ -84,7 +84,8 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
       (c.flux != ADG_FLUX_LF && c.flux != ADG_FLUX_HLLC) ||
       (c.limiter != ADG_LIM_NONE && c.limiter != ADG_LIM_WENO) || c.bc_left < 0 ||
       c.bc_left > 2 || c.bc_right < 0 || c.bc_right > 2 ||
-      ((c.bc_left == ADG_BC_PERIODIC) != (c.bc_right == ADG_BC_PERIODIC)))
+      ((c.bc_left == ADG_BC_PERIODIC) != (c.bc_right == ADG_BC_PERIODIC)) ||
+      (c.precision != ADG_FP64 && c.precision != ADG_MIXED))
     return ADG_ERR_ARG;
   for (int i = 0; i < ns; ++i)
     if (!(mech->W[i] > 0.0) || !(mech->cp[i] > RU)) return ADG_ERR_ARG;
@@ -109,7 +110,8 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   size_t o_count = cur.take(sizeof(int32_t) * N);
   size_t o_pl = cur.take(sizeof(int) * N);
   size_t o_pr = cur.take(sizeof(int) * N);
-  int TE = stage_tile(Q, nv, ns, nr, 8, c.at_order);
+  const bool mixed = c.precision == ADG_MIXED;
+  int TE = stage_tile(Q, nv, ns, nr, 8, c.at_order, mixed);
   int target = (N + 2 * 152 - 1) / (2 * 152);
   if (target < TE) TE = target < 4 ? 4 : target;
   const int RC = stage_chunks(TE, Q, nr);
@@ -213,6 +215,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   I.dx = c.length / N;
   I.dt = c.dt;
   I.tvb = c.tvb_M * I.dx * I.dx;
+  I.mixed = mixed ? 1 : 0;
   I.seed = c.seed;
   double acc = 0.0;
   for (int d = 0; d <= MAXD; ++d) {
@@ -267,13 +270,13 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
       A.TE = TE;
       A.R = RC;
       A.O = c.at_order;
-      NA_CK(launch_stage(M, A, Q, n_tiles, s));
+      NA_CK(launch_stage(M, A, Q, mixed, n_tiles, s));
       if (I.limiter != ADG_LIM_NONE) {
         LimArgs L;
         L.insts = (const Inst *)(base + o_inst);
         L.blocks = (const int2 *)(base + o_blocks);
         L.s = stg;
-        NA_CK(launch_limiter(M, L, Q, nv, n_blocks, s));
+        NA_CK(launch_limiter(M, L, Q, mixed, nv, n_blocks, s));
       }
     }
     NA_CK(launch_advance(I.step, 1, s));

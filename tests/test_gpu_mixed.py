@@ -1,0 +1,205 @@
+"""The mixed-precision CUDA path (ADG_MIXED: FP32 flux, DG operator and limiter;
+FP64 state, temperature, Arrhenius and equilibrium exponentials, AT sums and RK
+accumulation) against the FP64 oracle.
+
+Bar, in the relative L-infinity norm of the FP64 bar: the temperature within
+1e-4 of the oracle's at every Gauss point (relative to the local value); the mass
+fraction of every species within 1e-4 of the largest value of that species, at
+every Gauss point where the oracle's mass fraction is above 1e-8; the ignition
+delay -- the first time the largest Gauss-point temperature reaches T0 + 400 K,
+interpolated linearly between steps -- within 0.5 %.
+Relative to the local value, a mass fraction near 1e-8 next to an element at
+1e-4 moves by about 1e-3: an FP32 face flux rounds relative to the larger of its
+two traces. That pointwise error is bounded at 1e-2 here as a sanity check.
+Troubled-cell flags are not required to match exactly: a deviation within
+rounding of the indicator's noise floor (1e-5 of the field's magnitude, in both
+precisions) may be decided either way."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2501_01747_gb300 import adg
+from paper_2501_01747_gb300 import inputs as I
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+TOL_T = 1e-4
+TOL_Y = 1e-4
+Y_MIN = 1e-8
+TOL_IGN = 5e-3
+TOL_Y_POINTWISE = 1e-2
+
+
+def mass_fractions(w, p):
+    """Y_i at the Gauss points of a modal state [nv][N][Q] -> [ns][N][Q]."""
+    r = H.modal_to_nodal(w[2:], p)
+    return r / r.sum(axis=0, keepdims=True)
+
+
+def errors(g, o, wl):
+    """(T error, Y error in the bar's norm); asserts the pointwise sanity bound."""
+    T, To = g.temperature(), o.temperature()
+    eT = float((np.abs(T - To) / To).max())
+    Y, Yo = mass_fractions(g.get_state(), wl.p), mass_fractions(o.state(), wl.p)
+    eY, eP = 0.0, 0.0
+    for i in range(Yo.shape[0]):
+        big = Yo[i] > Y_MIN
+        if not big.any():
+            continue
+        d = np.abs(Y[i] - Yo[i])[big]
+        eY = max(eY, float(d.max() / Yo[i].max()))
+        eP = max(eP, float((d / Yo[i][big]).max()))
+    assert eP <= TOL_Y_POINTWISE, eP
+    return eT, eY
+
+
+def run_mixed(wl, mech, prim, n_steps, chunks=1):
+    g = adg.ADG(mech, [wl], precision="mixed")
+    g.set_primitive(prim)
+    o = O.Oracle(wl, mech)
+    o.set_primitive(prim)
+    per = n_steps // chunks
+    for _ in range(chunks):
+        g.step(per)
+        o.step(per)
+    g.check()
+    assert np.all(np.isfinite(g.get_state()))
+    return g, o
+
+
+def W():
+    return I.load_workloads()
+
+
+def crossing(ts, Tmax, level):
+    """First time the sampled curve reaches level, linear between samples."""
+    i = int(np.argmax(Tmax >= level))
+    assert Tmax[i] >= level and i > 0
+    f = (level - Tmax[i - 1]) / (Tmax[i] - Tmax[i - 1])
+    return ts[i - 1] + f * (ts[i] - ts[i - 1])
+
+
+def test_mixed_ignition_delay_and_state_through_ignition():
+    """The 9-species premixed ignition shape (sinusoidal T0 = 1000 K +- 2 %, SAA
+    delays up to 4, AT order 5, WENO) on 64 elements x p4 and 4 PEs over 1/8 of
+    the length (elements 8 times as large, time step scaled with them), run step
+    by step through ignition and 100 steps beyond on both sides."""
+    base = W()["ignition-9sp-4096x4"]
+    wl = I.scaled(base, 64, 4)
+    wl.length = base.length / 8
+    wl.dt = base.dt * (wl.length / wl.n_elem) / (base.length / base.n_elem)
+    mech = wl.mechanism()
+    prim = wl.primitive(mech)
+    g = adg.ADG(mech, [wl], precision="mixed")
+    g.set_primitive(prim)
+    o = O.Oracle(wl, mech)
+    o.set_primitive(prim)
+    level = wl.ic_params["T0"] + 400.0
+    tg, to = [g.temperature().max()], [o.temperature().max()]
+    worst = (0.0, 0.0)
+    n, n_cross = 0, None
+    while n < 5000 and (n_cross is None or n < n_cross + 100):
+        g.step(1)
+        o.step(1)
+        n += 1
+        tg.append(g.temperature().max())
+        to.append(o.temperature().max())
+        if n_cross is None and min(tg[-1], to[-1]) >= level:
+            n_cross = n
+        if n % 50 == 0:
+            worst = tuple(max(a, b) for a, b in zip(worst, errors(g, o, wl)))
+    g.check()
+    assert n_cross is not None, "no ignition"
+    ts = wl.dt * np.arange(n + 1)
+    t_gpu = crossing(ts, np.array(tg), level)
+    t_ref = crossing(ts, np.array(to), level)
+    assert abs(t_gpu - t_ref) <= TOL_IGN * t_ref, (t_gpu, t_ref)
+    eT, eY = errors(g, o, wl)
+    worst = (max(worst[0], eT), max(worst[1], eY))
+    assert worst[0] <= TOL_T, worst
+    assert worst[1] <= TOL_Y, worst
+
+
+def test_mixed_ignition_5sp_full_run():
+    """The 5-species ignition workload as configured (200 x p3, 4 PEs, SAA set 1,
+    AT order 4, WENO, 500 steps)."""
+    wl = W()["ignition-5sp-200x3"]
+    mech = wl.mechanism()
+    g, o = run_mixed(wl, mech, wl.primitive(mech), 500, chunks=5)
+    eT, eY = errors(g, o, wl)
+    assert eT <= TOL_T and eY <= TOL_Y, (eT, eY)
+
+
+def test_mixed_ignition_9sp_full_size():
+    """4096 x p4, 21 reactions, 64 PEs, delays up to 4 with AT order 5."""
+    wl = W()["ignition-9sp-4096x4"]
+    mech = wl.mechanism()
+    g, o = run_mixed(wl, mech, wl.primitive(mech), 12)
+    eT, eY = errors(g, o, wl)
+    assert eT <= TOL_T and eY <= TOL_Y, (eT, eY)
+
+
+@pytest.mark.parametrize("mode", [I.DELAY_SYNC, I.DELAY_CAA])
+@pytest.mark.parametrize("flux", [I.FLUX_LF, I.FLUX_HLLC])
+def test_mixed_delay_modes_and_fluxes(mode, flux):
+    wl = W()["ignition-5sp-200x3"]
+    wl.delay_mode, wl.flux = mode, flux
+    mech = wl.mechanism()
+    g, o = run_mixed(wl, mech, wl.primitive(mech), 120)
+    eT, eY = errors(g, o, wl)
+    assert eT <= TOL_T and eY <= TOL_Y, (eT, eY)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_mixed_every_degree_ragged_mesh(p):
+    """Prime element count (ragged last tile), 7 PEs with SAA delays and AT order
+    p+1, the smooth 9-species ignition shape at every degree."""
+    base = W()["ignition-9sp-4096x4"]
+    wl = I.scaled(base, 97, 7)
+    wl.p = p
+    wl.at_order = p + 1
+    mech = wl.mechanism()
+    g, o = run_mixed(wl, mech, wl.primitive(mech), 60)
+    eT, eY = errors(g, o, wl)
+    assert eT <= TOL_T and eY <= TOL_Y, (eT, eY)
+
+
+def test_mixed_and_fp64_instances_in_one_context():
+    """One context holding an FP64 and a mixed instance of the same problem: the
+    FP64 one keeps the FP64 bar, the mixed one the mixed bar."""
+    wl = W()["ignition-5sp-200x3"]
+    mech = wl.mechanism()
+    prim = wl.primitive(mech)
+    g = adg.ADG(mech, [wl, wl], precision=["fp64", "mixed"])
+    g.set_primitive(prim, 0)
+    g.set_primitive(prim, 1)
+    o = O.Oracle(wl, mech)
+    o.set_primitive(prim)
+    g.step(40)
+    o.step(40)
+    g.check()
+    assert H.parity_error(g.get_state(0), o.state(), mech).max() <= 1e-10
+    T1, To = g.temperature(1), o.temperature()
+    assert float((np.abs(T1 - To) / To).max()) <= TOL_T
+    prec = sorted(t["precision"] for t in g.tuning())
+    assert prec == ["fp64", "mixed"]
+
+
+def test_mixed_noalloc_matches_context_path():
+    import torch
+    wl = W()["ignition-5sp-200x3"]
+    mech = wl.mechanism()
+    g = adg.ADG(mech, [wl], precision="mixed")
+    g.set_primitive(wl.primitive(mech))
+    w0 = g.get_state()
+    g.step(25)
+    g.check()
+    ref = g.get_state()
+    w_in = torch.from_numpy(w0).cuda()
+    w_out = torch.full_like(w_in, float("nan"))
+    adg.step_noalloc(mech, wl, w_in, w_out, 25, precision="mixed")
+    torch.cuda.synchronize()
+    got = w_out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert H.parity_error(got, ref, mech).max() <= 1e-12
