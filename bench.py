@@ -214,7 +214,11 @@ def measure(adg, torch, wl, mech, prim, prec, args, dev, pg, ws):
     g.step(args.warmup, stream)
     g.check()
     torch.cuda.synchronize(dev)
-    tuning = g.autotune(stream) if not args.no_autotune else g.tuning()
+    if args.tuning:
+        te, nt = (int(x) for x in args.tuning.split(","))
+        tuning = g.set_tuning(0, te, nt)
+    else:
+        tuning = g.autotune(stream) if not args.no_autotune else g.tuning()
     torch.cuda.synchronize(dev)
 
     # device-resident timing: every step is one replay of the step's CUDA graph
@@ -329,6 +333,8 @@ def main(argv=None):
                     help="the headline variant; the other one is timed beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default="", help="TE,NT: set the stage launch configuration "
+                    "instead of autotuning it")
     ap.add_argument("--only", action="store_true", help="time the headline variant only")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)

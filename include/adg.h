@@ -170,17 +170,22 @@ int adg_delay_table(const adg_config *cfg, int64_t step0, int n_steps, uint8_t *
 int adg_enable_kernel_timing(adg_ctx *ctx, int on);
 int adg_kernel_times(adg_ctx *ctx, double *ms, int64_t *launches);
 
-/* Autotuner of the launch configuration (elements per stage tile and chemistry
- * chunks per Gauss point, per group of instances): times the
+/* Autotuner of the launch configuration (elements per stage tile and threads
+ * per stage CTA, per group of instances): times the
  * stage kernel for every candidate that fits in shared memory on `stream`,
  * keeps the fastest and drops the captured step graphs. The trajectory is not
  * changed (the trial launches only rewrite buffers the next step rewrites).
  * Synchronous. Instances are grouped by degree and precision. adg_get_tuning
  * fills tuning[5 * g + {0,1,2,3,4}] with the degree, precision, tile elements,
- * chunks and tile count of group g (at most ADG_MAX_GROUPS groups). */
+ * threads per CTA and tile count of group g (at most ADG_MAX_GROUPS groups). */
 #define ADG_MAX_GROUPS (2 * ADG_MAX_P)
 int adg_autotune(adg_ctx *ctx, void *stream);
 int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning);
+/* Set the launch configuration of group g directly (for instance one that an
+ * earlier adg_autotune found): elements per stage tile >= 2, threads per CTA a
+ * multiple of 32 in [32, 512]. Synchronous; drops the captured step graphs.
+ * ADG_ERR_ARG for a bad group or a tile whose shared memory exceeds 200 KB. */
+int adg_set_tuning(adg_ctx *ctx, int group, int elements_per_tile, int threads_per_cta);
 
 /* Number of kernel launches one adg_step(ctx, 1, ...) enqueues. */
 int adg_launches_per_step(const adg_ctx *ctx);

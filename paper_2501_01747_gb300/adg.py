@@ -98,7 +98,8 @@ EXPORTS = ["adg_workspace_bytes", "adg_create", "adg_destroy", "adg_set_primitiv
            "adg_step", "adg_status", "adg_get_flags", "adg_get_temperature", "adg_steps_done",
            "adg_delay_table", "adg_launches_per_step", "adg_error_string",
            "adg_write_state", "adg_read_state", "adg_enable_kernel_timing",
-           "adg_kernel_times", "adg_step_noalloc", "adg_autotune", "adg_get_tuning"]
+           "adg_kernel_times", "adg_step_noalloc", "adg_autotune", "adg_get_tuning",
+           "adg_set_tuning"]
 
 
 def lib(path: str | None = None):
@@ -137,6 +138,7 @@ def lib(path: str | None = None):
                                    vp]
     L.adg_autotune.argtypes = [vp, vp]
     L.adg_get_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.adg_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     L.adg_error_string.restype = C.c_char_p
     L.adg_error_string.argtypes = [C.c_int]
     _lib = L
@@ -355,7 +357,7 @@ class ADG:
         return ms, n
 
     def autotune(self, stream=None):
-        """Pick elements per tile and chemistry chunks by timing the stage kernel."""
+        """Pick elements per tile and threads per CTA by timing the stage kernel."""
         _check(self.L.adg_autotune(self.h, self._stream(stream)), "adg_autotune")
         return self.tuning()
 
@@ -364,8 +366,14 @@ class ADG:
         t = (C.c_int * 40)()
         _check(self.L.adg_get_tuning(self.h, C.byref(n), t), "adg_get_tuning")
         return [{"p": t[5 * g], "precision": "mixed" if t[5 * g + 1] == MIXED else "fp64",
-                 "elements_per_tile": t[5 * g + 2], "chem_chunks": t[5 * g + 3],
+                 "elements_per_tile": t[5 * g + 2], "threads_per_cta": t[5 * g + 3],
                  "tiles": t[5 * g + 4]} for g in range(n.value)]
+
+    def set_tuning(self, group, elements_per_tile, threads_per_cta):
+        """Set the stage launch configuration of a group (e.g. a stored autotune result)."""
+        _check(self.L.adg_set_tuning(self.h, int(group), int(elements_per_tile),
+                                     int(threads_per_cta)), "adg_set_tuning")
+        return self.tuning()
 
     def launches_per_step(self):
         return int(self.L.adg_launches_per_step(self.h))

@@ -95,18 +95,78 @@ static void make_basis(int p, Basis *B) {
   }
 }
 
-// All constant tables: the DG/WENO basis for p = 1..ADG_MAX_P, and for the
-// table-driven exp the values 2^(j/32) and the split of ln2/32 (extended precision).
-void adg::make_tables(Basis *tables, ExpTable *et) {
+// All constant tables: the DG/WENO basis for p = 1..ADG_MAX_P.
+void adg::make_tables(Basis *tables) {
   for (int p = 1; p <= ADG_MAX_P; ++p) make_basis(p, &tables[p - 1]);
-  for (int j = 0; j < 32; ++j) et->t[j] = (double)exp2l((long double)j / 32.0L);
-  long double l = logl(2.0L) / 32.0L;
-  int ex;
-  long double mant = frexpl(l, &ex);
-  long double hi = ldexpl(floorl(ldexpl(mant, 32)), ex - 32);
-  et->l_hi = (double)hi;
-  et->l_lo = (double)(l - hi);
 }
+
+// Species fields (constant c_p thermo, Sec. 2), packed reactions and the
+// species -> reaction incidence of the net stoichiometry.
+int adg::pack_mechanism(const adg_mechanism *m, double *sp, Rxn *rx, int *sx_off, int *sx) {
+  const int ns = m->n_species, nr = m->n_reactions;
+  for (int i = 0; i < ns; ++i) {
+    double W = m->W[i], cp = m->cp[i], hf = m->h_f[i], s0 = m->s0[i];
+    sp[SP_W * ns + i] = W;
+    sp[SP_INVW * ns + i] = 1.0 / W;
+    sp[SP_QW * ns + i] = (hf - cp * TREF) / W;
+    sp[SP_CVW * ns + i] = (cp - RU) / W;
+    sp[SP_RW * ns + i] = RU / W;
+    sp[SP_CPW * ns + i] = cp / W;
+    sp[SP_G0 * ns + i] = (hf - cp * TREF) / RU;
+    sp[SP_G1 * ns + i] = cp / RU * (1.0 + log(TREF)) - s0 / RU;
+    sp[SP_CPR * ns + i] = cp / RU;
+  }
+  for (int j = 0; j < nr; ++j) {
+    Rxn &R = rx[j];
+    memset(&R, 0, sizeof(Rxn));
+    if (!(m->A[j] > 0.0)) return ADG_ERR_ARG;
+    R.lnA = log(m->A[j]);
+    R.b = m->b[j];
+    R.EaR = m->Ea[j] / RU;
+    int a = 0, b = 0, x = 0, dnu = 0;
+    for (int i = 0; i < ns; ++i) {
+      int f = m->nu_f[j * ns + i], r = m->nu_r[j * ns + i];
+      if (f < 0 || r < 0 || f > 2 || r > 2) return ADG_ERR_ARG;
+      if (f > 0) {
+        if (a == SIDE) return ADG_ERR_ARG;
+        R.rs[a] = (uint8_t)i;
+        R.rn[a++] = (uint8_t)f;
+      }
+      if (r > 0) {
+        if (b == SIDE) return ADG_ERR_ARG;
+        R.ps[b] = (uint8_t)i;
+        R.pn[b++] = (uint8_t)r;
+      }
+      if (r != f) {
+        if (x == NET) return ADG_ERR_ARG;
+        R.xs[x] = (uint8_t)i;
+        R.xc[x++] = (double)(r - f);
+        dnu += r - f;
+      }
+    }
+    R.nx = (uint8_t)x;
+    R.dnu = (double)dnu;
+  }
+  int n = 0;
+  for (int i = 0; i < ns; ++i) {
+    sx_off[i] = n;
+    for (int j = 0; j < nr; ++j) {
+      int c = m->nu_r[j * ns + i] - m->nu_f[j * ns + i];
+      if (c != 0) sx[n++] = (j << 8) | (c & 0xff);
+    }
+  }
+  sx_off[ns] = n;
+  return n;
+}
+
+namespace {
+// Number of species-reaction incidence terms (nonzero net coefficients).
+int count_terms(const adg_mechanism *m) {
+  int n = 0;
+  for (int k = 0; k < m->n_species * m->n_reactions; ++k) n += (m->nu_r[k] != m->nu_f[k]);
+  return n;
+}
+}  // namespace
 
 // AT weights (Eq. 7-8): extrapolation to t_n from levels t_n - (k+m) dt.
 static void at_weights(int order, int k, double *c) {
@@ -132,7 +192,7 @@ struct Group {
   int Q = 0;
   bool mixed = false;
   int TE = 0;                   // elements per stage tile
-  int R = 1;                    // chemistry chunks per Gauss point
+  int NT = 128;                 // threads per stage CTA
   int O = 1;                    // largest AT order of the group
   int n_tiles = 0, n_blocks = 0;
   int2 *d_tiles = nullptr;      // (instance, first element) per stage CTA
@@ -237,6 +297,8 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
   Mech &M = ctx->mech;
   M.sp = (const double *)cv.take(sizeof(double) * SP_NFIELDS * ns);
   M.rx = (const Rxn *)cv.take(sizeof(Rxn) * nrr);
+  M.sx_off = (const int *)cv.take(sizeof(int) * (ns + 1));
+  M.sx = (const int *)cv.take(sizeof(int) * (M.nterm > 0 ? M.nterm : 1));
   ctx->err_all = (int *)cv.take(sizeof(int) * 4 * ctx->n_inst);
   ctx->d_insts = (Inst *)cv.take(sizeof(Inst) * ctx->n_inst);
   ctx->d_steps = (int64_t *)cv.take(sizeof(int64_t) * ctx->n_inst);
@@ -261,11 +323,11 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
     G.Q = Q;
     G.mixed = prec == ADG_MIXED;
     G.O = O;
-    G.TE = stage_tile(Q, nv, ns, nr, 8, O, G.mixed);
+    G.TE = stage_tile(M, Q, O, G.mixed);
     // smaller tiles when the group would not fill two CTAs per SM
     int64_t target = (total + 2 * 152 - 1) / (2 * 152);
     if (target < G.TE) G.TE = target < 4 ? 4 : (int)target;
-    G.R = stage_chunks(G.TE, Q, nr);
+    G.NT = stage_threads(G.TE, Q, nr);
     int64_t max_tiles = 0;
     for (int k = 0; k < ctx->n_inst; ++k)
       if (member(k)) {
@@ -354,6 +416,9 @@ int adg_workspace_bytes(const adg_mechanism *mech, const adg_config *cfgs, int n
   tmp.n_inst = n;
   tmp.ns = mech->n_species;
   tmp.nr = mech->n_reactions;
+  tmp.mech.ns = tmp.ns;
+  tmp.mech.nr = tmp.nr;
+  tmp.mech.nterm = count_terms(mech);
   tmp.inst.resize(n);
   tmp.err_all = nullptr;
   Carver cv{nullptr, 0, 0, true};
@@ -392,6 +457,9 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
   ctx->n_inst = n;
   ctx->ns = mech->n_species;
   ctx->nr = mech->n_reactions;
+  ctx->mech.ns = ctx->ns;
+  ctx->mech.nr = ctx->nr;
+  ctx->mech.nterm = count_terms(mech);
   ctx->inst.resize(n);
   ctx->last_stream = 0;
   ctx->err_all = nullptr;
@@ -431,51 +499,28 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
   Mech &M = ctx->mech;
   M.ns = ns;
   M.nr = nr;
-  // mechanism tables: species fields and packed reactions
-  std::vector<double> sp(SP_NFIELDS * ns);
-  for (int i = 0; i < ns; ++i) {
-    double W = mech->W[i], cp = mech->cp[i], hf = mech->h_f[i], s0 = mech->s0[i];
-    sp[SP_W * ns + i] = W;
-    sp[SP_INVW * ns + i] = 1.0 / W;
-    sp[SP_QW * ns + i] = (hf - cp * TREF) / W;
-    sp[SP_CVW * ns + i] = (cp - RU) / W;
-    sp[SP_RW * ns + i] = RU / W;
-    sp[SP_CPW * ns + i] = cp / W;
-    sp[SP_G0 * ns + i] = (hf - cp * TREF) / RU;
-    sp[SP_G1 * ns + i] = cp / RU * (1.0 + log(TREF)) - s0 / RU;
-    sp[SP_CPR * ns + i] = cp / RU;
-  }
+  // mechanism tables: species fields, packed reactions, species-reaction incidence
   int rc2 = ADG_OK;
-  if (cudaMemcpy((void *)M.sp, sp.data(), sizeof(double) * sp.size(), cudaMemcpyHostToDevice))
-    rc2 = ADG_ERR_CUDA;
-  std::vector<Rxn> rx(nr > 0 ? nr : 1);
-  memset(rx.data(), 0, sizeof(Rxn) * rx.size());
-  for (int j = 0; j < nr; ++j) {
-    Rxn &R = rx[j];
-    R.lnA = log(mech->A[j]);
-    R.b = mech->b[j];
-    R.EaR = mech->Ea[j] / RU;
-    int a = 0, b = 0, x = 0, dnu = 0;
-    for (int i = 0; i < ns; ++i) {
-      int f = mech->nu_f[j * ns + i], r = mech->nu_r[j * ns + i];
-      if (f > 0) { R.rs[a] = (uint8_t)i; R.rn[a] = (uint8_t)f; ++a; }
-      if (r > 0) { R.ps[b] = (uint8_t)i; R.pn[b] = (uint8_t)r; ++b; }
-      if (r - f != 0) { R.xs[x] = (uint8_t)i; R.xc[x] = (double)(r - f); ++x; dnu += r - f; }
-    }
-    R.nx = (uint8_t)x;
-    R.dnu = (double)dnu;
+  {
+    std::vector<double> sp(SP_NFIELDS * ns);
+    std::vector<Rxn> rx(nr > 0 ? nr : 1);
+    std::vector<int> sx_off(ns + 1), sx(M.nterm > 0 ? M.nterm : 1);
+    if (pack_mechanism(mech, sp.data(), rx.data(), sx_off.data(), sx.data()) != M.nterm)
+      rc2 = ADG_ERR_ARG;
+    if (cudaMemcpy((void *)M.sp, sp.data(), sizeof(double) * sp.size(), cudaMemcpyHostToDevice) ||
+        (nr > 0 && cudaMemcpy((void *)M.rx, rx.data(), sizeof(Rxn) * nr, cudaMemcpyHostToDevice)) ||
+        cudaMemcpy((void *)M.sx_off, sx_off.data(), sizeof(int) * (ns + 1),
+                   cudaMemcpyHostToDevice) ||
+        (M.nterm > 0 && cudaMemcpy((void *)M.sx, sx.data(), sizeof(int) * M.nterm,
+                                   cudaMemcpyHostToDevice)))
+      rc2 = ADG_ERR_CUDA;
   }
-  if (nr > 0 &&
-      cudaMemcpy((void *)M.rx, rx.data(), sizeof(Rxn) * nr, cudaMemcpyHostToDevice))
-    rc2 = ADG_ERR_CUDA;
   if (cudaMemset(ctx->err_all, 0, sizeof(int) * 4 * n)) rc2 = ADG_ERR_CUDA;
-  // basis tables and the exp table in constant memory
+  // basis tables in constant memory
   {
     Basis tables[ADG_MAX_P];
-    ExpTable et;
-    make_tables(tables, &et);
-    if (upload_basis(tables) != cudaSuccess || upload_exp_table(&et) != cudaSuccess)
-      rc2 = ADG_ERR_CUDA;
+    make_tables(tables);
+    if (upload_basis(tables) != cudaSuccess) rc2 = ADG_ERR_CUDA;
   }
   // instances
   for (int k = 0; k < n && rc2 == ADG_OK; ++k) {
@@ -676,7 +721,7 @@ static int enqueue_step(adg_ctx *ctx, cudaStream_t st) {
       A.tiles = G.d_tiles;
       A.s = s;
       A.TE = G.TE;
-      A.R = G.R;
+      A.NT = G.NT;
       A.O = G.O;
       CK(timed_begin(ctx, 0, st));
       CK(launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st));
@@ -793,39 +838,38 @@ int adg_autotune(adg_ctx *ctx, void *stream) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int nv = ctx->ns + 2, ns = ctx->ns, nr = ctx->nr;
-  static const int kTE[] = {2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 32, 40, 48, 64, 96, 128};
-  static const int kR[] = {1, 2, 3, 4, 6, 8};
+  static const int kTE[] = {2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 32, 40, 48, 64};
+  static const int kNT[] = {64, 128, 192, 256, 384, 512};
   int rc = ADG_OK;
   for (int gi = 0; gi < ctx->n_groups && rc == ADG_OK; ++gi) {
     Group &G = ctx->groups[gi];
-    int bestTE = G.TE, bestR = G.R;
+    int bestTE = G.TE, bestNT = G.NT;
     float best = 1e30f;
     for (int te : kTE) {
-      if (te < kMinTile || te * G.Q > 256) continue;
-      for (int R : kR) {
-        if (R > (nr > 0 ? nr : 1)) continue;
-        if (stage_smem(te, G.Q, nv, ns, nr, R, G.O, G.mixed) > 200 * 1024) continue;
-        G.TE = te;
-        G.R = R;
-        if (upload_tiles(ctx, G) != cudaSuccess) {
-          rc = ADG_ERR_CUDA;
-          break;
-        }
+      if (te < kMinTile) continue;
+      if (stage_smem(ctx->mech, te, G.Q, G.O, G.mixed) > 200 * 1024) continue;
+      G.TE = te;
+      if (upload_tiles(ctx, G) != cudaSuccess) {
+        rc = ADG_ERR_CUDA;
+        break;
+      }
+      for (int nt : kNT) {
         StageArgs A;
         A.insts = ctx->d_insts;
         A.tiles = G.d_tiles;
         A.s = 0;
         A.TE = te;
-        A.R = R;
+        A.NT = nt;
         A.O = G.O;
         // stage 0 alone rewrites only buffers that the next step rewrites again
         // (stage buffers, the ring slot of the current level), so the
         // trajectory is unchanged
         bool ok = true;
-        for (int w = 0; w < 2 && ok; ++w) ok = launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
+        for (int w = 0; w < 2 && ok; ++w)
+          ok = launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
         ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
-        for (int w = 0; w < 5 && ok; ++w) ok = launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
+        for (int w = 0; w < 5 && ok; ++w)
+          ok = launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
         ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
         float ms = 0.0f;
         if (!ok || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
@@ -835,13 +879,13 @@ int adg_autotune(adg_ctx *ctx, void *stream) {
         if (ms < best) {
           best = ms;
           bestTE = te;
-          bestR = R;
+          bestNT = nt;
         }
       }
       if (rc != ADG_OK) break;
     }
     G.TE = bestTE;
-    G.R = bestR;
+    G.NT = bestNT;
     if (upload_tiles(ctx, G) != cudaSuccess) rc = ADG_ERR_CUDA;
   }
   cudaEventDestroy(e0);
@@ -849,6 +893,20 @@ int adg_autotune(adg_ctx *ctx, void *stream) {
   drop_graphs(ctx);
   if (rc == ADG_ERR_CUDA) return cuda_fail(cudaGetLastError());
   return rc;
+}
+
+int adg_set_tuning(adg_ctx *ctx, int group, int elements_per_tile, int threads_per_cta) {
+  if (!ctx || group < 0 || group >= ctx->n_groups) return ADG_ERR_ARG;
+  Group &G = ctx->groups[group];
+  const int te = elements_per_tile, nt = threads_per_cta;
+  if (te < kMinTile || nt < 32 || nt > 512 || nt % 32) return ADG_ERR_ARG;
+  if (stage_smem(ctx->mech, te, G.Q, G.O, G.mixed) > 200 * 1024) return ADG_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->last_stream));
+  G.TE = te;
+  G.NT = nt;
+  CK(upload_tiles(ctx, G));
+  drop_graphs(ctx);
+  return ADG_OK;
 }
 
 int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning) {
@@ -859,7 +917,7 @@ int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning) {
     tuning[5 * gi + 0] = G.Q - 1;
     tuning[5 * gi + 1] = G.mixed ? ADG_MIXED : ADG_FP64;
     tuning[5 * gi + 2] = G.TE;
-    tuning[5 * gi + 3] = G.R;
+    tuning[5 * gi + 3] = G.NT;
     tuning[5 * gi + 4] = G.n_tiles;
   }
   return ADG_OK;

@@ -47,11 +47,21 @@ struct alignas(16) Rxn {
 };
 static_assert(sizeof(Rxn) == 128, "reaction record is 128 bytes");
 
+// Species -> reaction incidence (the transpose of the net stoichiometry): the
+// terms of species i are sx[sx_off[i] .. sx_off[i+1]), each (j << 8) | (nu_ij & 0xff)
+// with nu_ij the species' nonzero net coefficient in reaction j, ascending in j.
 struct Mech {
-  int ns, nr;
+  int ns, nr, nterm;
   const double *sp;   // [SP_NFIELDS][ns]
   const Rxn *rx;      // [nr]
+  const int *sx_off;  // [ns + 1]
+  const int *sx;      // [nterm]
 };
+
+// Host: the device tables of a mechanism. Fills sp [SP_NFIELDS * ns], rx [nr],
+// sx_off [ns + 1] and sx [nr * NET]; returns the number of incidence terms, or
+// ADG_ERR_ARG for a reaction the tables cannot hold.
+int pack_mechanism(const adg_mechanism *m, double *sp, Rxn *rx, int *sx_off, int *sx);
 
 // Per-instance description, passed by value to the kernels.
 struct Inst {
@@ -242,7 +252,7 @@ struct StageArgs {
   const int2 *tiles;
   int s;
   int TE;     // elements per tile
-  int R;      // chemistry chunks per Gauss point
+  int NT;     // threads per CTA
   int O;      // AT levels provided for (largest AT order of the group)
 };
 
@@ -254,13 +264,11 @@ struct LimArgs {
   int s;
 };
 
-struct ExpTable;
-void make_tables(Basis *tables, ExpTable *et);
+void make_tables(Basis *tables);
 cudaError_t upload_basis(const Basis *tables);
-cudaError_t upload_exp_table(const ExpTable *t);
-int stage_tile(int Q, int nv, int ns, int nr, int R, int O, bool mixed);
-int stage_chunks(int TE, int Q, int nr);
-size_t stage_smem(int TE, int Q, int nv, int ns, int nr, int R, int O, bool mixed);
+int stage_tile(const Mech &M, int Q, int O, bool mixed);
+int stage_threads(int TE, int Q, int nr);
+size_t stage_smem(const Mech &M, int TE, int Q, int O, bool mixed);
 cudaError_t prepare_kernels(int nv, int ns, int nr);
 cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, bool mixed, int n_tiles,
                          cudaStream_t st);

@@ -29,31 +29,28 @@ namespace adg {
 __constant__ Basis c_basis[ADG_MAX_P];     // index p-1
 __constant__ BasisF c_basis_f[ADG_MAX_P];  // the same, rounded to float
 
-__constant__ ExpTable c_exp;
+__constant__ IExpTable c_iexp = ADG_IEXP_TABLE;
 
 template <bool MIX>
 using dg_t = typename std::conditional<MIX, float, double>::type;
 
-// Shared-memory footprint (bytes) of a stage tile of TE elements, R chemistry
-// chunks per Gauss point and up to O AT levels per face. In the FP64 variant the
-// flux overwrites the nodal state and the summed rates stay in chunk 0; the
-// mixed variant keeps both in separate FP32 arrays.
-__host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int nv, int ns, int nr, int R,
+// Shared-memory footprint (bytes) of a stage tile of TE elements with up to O AT
+// levels per face. FP64 region: species fields, exp table, basis values, modal
+// tile with halo, nodal state, g_i/(R T), ln T, 1/T, u, P. Region in the
+// arithmetic type of the variant: face, level and trace fluxes, concentrations,
+// rates of progress, production rates; the mixed variant adds an FP32 copy of
+// the species fields and the point flux (the FP64 variant writes the flux over
+// the nodal state). Integers: delay per face, species-reaction incidence.
+__host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int ns, int nr, int nterm,
                                                    int O, bool mix) {
-  size_t TQ = (size_t)TE * Q, F = TE + 1;
-  size_t nd = (size_t)SP_NFIELDS * ns      // species fields
-              + 34                         // exp table and ln2/32 split
-              + (size_t)nv * (TE + 2) * Q  // modal tile with halo        [v][le][j]
-              + (size_t)nv * TQ            // nodal state (FP64: then flux) [v][t]
-              + (size_t)ns * TQ * 2        // concentrations, g/RT        [i][t]
-              + (size_t)R * ns * TQ        // production rates per chunk  [c][i][t]
-              + 2 * TQ;                    // ln T, 1/T                   [t]
-  size_t nr_ = F * nv                      // face fluxes                 [f][v]
-               + (size_t)O * F * nv        // level fluxes                [m][f][v]
-               + (size_t)O * F * 2 * nv;   // traces per (level, face)    [m][f][2][v]
-  size_t extra = mix ? ((size_t)SP_NFIELDS * ns + (size_t)nv * TQ + (size_t)ns * TQ) : 0;
-  size_t bytes = nd * 8 + (nr_ + extra) * (mix ? 4 : 8) + F * 4 + 16;
-  return bytes + (size_t)nr * sizeof(Rxn);
+  const size_t nv = ns + 2, TQ = (size_t)TE * Q, F = TE + 1;
+  const size_t nd = (size_t)SP_NFIELDS * ns + 32 + MAXQ * MAXQ + nv * (TE + 2) * Q + nv * TQ +
+                    (size_t)ns * TQ + 4 * TQ;
+  size_t ndg = F * nv + (size_t)O * F * nv + (size_t)O * F * 2 * nv + (size_t)ns * TQ +
+               (size_t)nr * TQ + (size_t)ns * TQ;
+  if (mix) ndg += (size_t)SP_NFIELDS * ns + nv * TQ;
+  const size_t ni = F + ns + 1 + nterm;
+  return (size_t)nr * sizeof(Rxn) + nd * 8 + ndg * (mix ? 4 : 8) + ni * 4 + 16;
 }
 
 // Copy an instance description into shared memory (by 8-byte words).
@@ -64,7 +61,7 @@ __device__ inline void load_inst(Inst &dst, const Inst *src) {
 }
 
 template <int Q, bool MIX>
-__global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
+__global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
   using DG = dg_t<MIX>;
   extern __shared__ __align__(16) double sm[];
   __shared__ Inst sI;
@@ -78,39 +75,46 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
   const int TQ = TE * Q;
   const int e0 = tile.y;
   const int te = min(TE, N - e0);
+  const int teq = te * Q;
   const int64_t nstep = *I.step;
   const double *A_win = (A.s == 0) ? I.wn : (A.s == 1) ? I.wa : I.wb;
   double *A_wnext = (A.s == 0) ? I.wa : (A.s == 1) ? I.wb : I.wn;
   const bool periodic = (I.bc_left == ADG_BC_PERIODIC);
-  const int R = A.R, O = A.O, NF = TE + 1;
+  const int O = A.O, NF = TE + 1;
   Rxn *srx = reinterpret_cast<Rxn *>(sm);
-  double *ssp = reinterpret_cast<double *>(srx + nr);       // [F][ns]
-  ExpTable *stab = reinterpret_cast<ExpTable *>(ssp + SP_NFIELDS * ns);
-  double *sw = reinterpret_cast<double *>(stab + 1);        // [v][TE+2][Q]
-  double *snw = sw + (size_t)nv * (TE + 2) * Q;             // [v][TQ]  nodal state
-  double *sconc = snw + (size_t)nv * TQ;                    // [i][TQ]
-  double *sg = sconc + (size_t)ns * TQ;                     // [i][TQ]
-  double *swd = sg + (size_t)ns * TQ;                       // [R][i][TQ]
-  double *slnT = swd + (size_t)R * ns * TQ;                 // [TQ]
-  double *sinvT = slnT + TQ;                                // [TQ]
-  DG *sfh = reinterpret_cast<DG *>(sinvT + TQ);             // [NF][nv]
-  DG *sflx = sfh + (size_t)NF * nv;                         // [O][NF][nv]
-  DG *str = sflx + (size_t)O * NF * nv;                     // [O][NF][2][nv]
-  DG *sspD, *sfx, *swdD;                                    // species, flux, rates in DG
+  double *ssp = reinterpret_cast<double *>(srx + nr);         // [F][ns]
+  IExpTable *stab = reinterpret_cast<IExpTable *>(ssp + SP_NFIELDS * ns);
+  double *sPq = reinterpret_cast<double *>(stab + 1);         // [q][j] P_j(x_q)
+  double *sw = sPq + MAXQ * MAXQ;                             // [v][TE+2][Q]
+  double *snw = sw + (size_t)nv * (TE + 2) * Q;               // [v][TQ] nodal state
+  double *sg = snw + (size_t)nv * TQ;                         // [i][TQ] g_i/(R T)
+  double *slnT = sg + (size_t)ns * TQ;                        // [TQ]
+  double *sinvT = slnT + TQ;
+  double *su = sinvT + TQ;
+  double *sPr = su + TQ;
+  DG *sfh = reinterpret_cast<DG *>(sPr + TQ);                 // [NF][nv]
+  DG *sflx = sfh + (size_t)NF * nv;                           // [O][NF][nv]
+  DG *str = sflx + (size_t)O * NF * nv;                       // [O][NF][2][nv]
+  DG *scc = str + (size_t)O * NF * 2 * nv;                    // [i][TQ] concentrations
+  DG *sq = scc + (size_t)ns * TQ;                             // [j][TQ] rates of progress
+  DG *swd = sq + (size_t)nr * TQ;                             // [i][TQ] production rates
+  DG *sspD, *sfx;                                             // species fields, point flux
+  int *sk;
   if constexpr (MIX) {
-    sspD = str + (size_t)O * NF * 2 * nv;
+    sspD = swd + (size_t)ns * TQ;
     sfx = sspD + (size_t)SP_NFIELDS * ns;
-    swdD = sfx + (size_t)nv * TQ;
+    sk = reinterpret_cast<int *>(sfx + (size_t)nv * TQ);
   } else {
     sspD = reinterpret_cast<DG *>(ssp);
     sfx = reinterpret_cast<DG *>(snw);
-    swdD = reinterpret_cast<DG *>(swd);
+    sk = reinterpret_cast<int *>(swd + (size_t)ns * TQ);
   }
-  int *sk = MIX ? reinterpret_cast<int *>(swdD + (size_t)ns * TQ)
-                : reinterpret_cast<int *>(str + (size_t)O * NF * 2 * nv);   // [NF]
+  int *soff = sk + NF;        // [ns + 1]
+  int *sterm = soff + ns + 1;  // [nterm]
   const int tid = threadIdx.x, nth = blockDim.x;
 
-  // 0. mechanism, species fields and exp table into shared memory
+  // 0. mechanism, species fields, incidence, exp table and basis values into
+  // shared memory
   {
     const uint4 *src = reinterpret_cast<const uint4 *>(M.rx);
     uint4 *dst = reinterpret_cast<uint4 *>(srx);
@@ -120,9 +124,10 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
       ssp[k] = x;
       if constexpr (MIX) sspD[k] = (DG)x;
     }
-    const double *et = reinterpret_cast<const double *>(&c_exp);
-    double *dt = reinterpret_cast<double *>(stab);
-    for (int k = tid; k < 34; k += nth) dt[k] = et[k];
+    for (int k = tid; k < 32; k += nth) stab->t[k] = c_iexp.t[k];
+    for (int k = tid; k < Q * Q; k += nth) sPq[k] = B.P[k / Q][k % Q];
+    for (int k = tid; k <= ns; k += nth) soff[k] = M.sx_off[k];
+    for (int k = tid; k < M.nterm; k += nth) sterm[k] = M.sx[k];
   }
   // 1. tile of modal coefficients with a one-element halo on each side
   const int span = (te + 2) * Q;
@@ -136,112 +141,110 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
   }
   __syncthreads();
 
-  // 2a. Gauss points: conserved state and temperature (FP64), concentrations,
-  // g_i/(R T), and the flux
-  const double *sIW = ssp + SP_INVW * ns;
-  const double *sG0 = ssp + SP_G0 * ns, *sG1 = ssp + SP_G1 * ns, *sCR = ssp + SP_CPR * ns;
-  const double LN_R_PATM = log(RU / PATM);
-  const int teq = te * Q;
-  for (int t = tid; t < teq; t += nth) {
-    int e = t / Q, q = t - e * Q, le = e + 1;
-    double *wq = snw + t;   // stride TQ between variables
-    for (int v = 0; v < nv; ++v) {
-      double acc = 0.0;
+  // 2a. conserved state at the Gauss points, one (variable, point) per item
+  for (int item = tid; item < nv * teq; item += nth) {
+    int v = item / teq, t = item - v * teq;
+    int e = t / Q, q = t - e * Q;
+    const double *wi = sw + ((size_t)v * (TE + 2) + e + 1) * Q;
+    const double *Pq = sPq + q * Q;
+    double acc = 0.0;
 #pragma unroll
-      for (int j = 0; j < Q; ++j) acc += sw[((size_t)v * (TE + 2) + le) * Q + j] * B.P[q][j];
-      wq[(size_t)v * TQ] = acc;
-    }
-    Thermo th = thermo_of(ssp, ns, wq, TQ);
-    if (!(th.rho > 0.0) || !(th.T > 0.0) || !isfinite(th.T) || !isfinite(wq[0]))
-      report_error(I, ADG_ERR_NONPHYSICAL, e0 + e, A.s, nstep);
-    const double lnT = log(th.T), invT = 1.0 / th.T;
-    slnT[t] = lnT;
-    sinvT[t] = invT;
-    double *cq = sconc + t, *gq = sg + t;
-    for (int i = 0; i < ns; ++i) {
-      double r = wq[(size_t)(2 + i) * TQ];
-      // law of mass action on non-negative concentrations: clip at zero by the
-      // sign bit (no FP64 instruction)
-      r = (__double2hiint(r) < 0) ? 0.0 : r;
-      cq[(size_t)i * TQ] = r * sIW[i];
-      gq[(size_t)i * TQ] = fma(-sCR[i], lnT, fma(sG0[i], invT, sG1[i]));
-    }
-    if constexpr (MIX) {
-      const DG u = (DG)th.u, P = (DG)th.P;
-      DG *fq = sfx + t;
-      fq[0] = (DG)wq[0] * u + P;
-      fq[TQ] = u * ((DG)wq[TQ] + P);
-      for (int v = 2; v < nv; ++v) fq[(size_t)v * TQ] = u * (DG)wq[(size_t)v * TQ];
-    } else {
-      double f0 = phys_flux(wq, TQ, 0, th), f1 = phys_flux(wq, TQ, 1, th);
-      for (int v = 2; v < nv; ++v) wq[(size_t)v * TQ] = th.u * wq[(size_t)v * TQ];
-      wq[0] = f0;
-      wq[TQ] = f1;
+    for (int j = 0; j < Q; ++j) acc += wi[j] * Pq[j];
+    snw[(size_t)v * TQ + t] = acc;
+  }
+  __syncthreads();
+  // 2b. temperature from the internal energy (FP64), velocity and pressure
+  for (int t = tid; t < teq; t += nth) {
+    Thermo th = thermo_of(ssp, ns, snw + t, TQ);
+    if (!(th.rho > 0.0) || !(th.T > 0.0) || !isfinite(th.T) || !isfinite(snw[t]))
+      report_error(I, ADG_ERR_NONPHYSICAL, e0 + t / Q, A.s, nstep);
+    slnT[t] = log(th.T);
+    sinvT[t] = 1.0 / th.T;
+    su[t] = th.u;
+    sPr[t] = th.P;
+  }
+  __syncthreads();
+  // 2c. per (variable, point): the flux; for a species also its concentration
+  // (law of mass action on non-negative concentrations: clipped at zero by the
+  // sign bit) and g_i/(R T) (FP64)
+  {
+    const double *sIW = ssp + SP_INVW * ns;
+    const double *sG0 = ssp + SP_G0 * ns, *sG1 = ssp + SP_G1 * ns, *sCR = ssp + SP_CPR * ns;
+    for (int item = tid; item < nv * teq; item += nth) {
+      int v = item / teq, t = item - v * teq;
+      const size_t at = (size_t)v * TQ + t;
+      const double w = snw[at], u = su[t];
+      if (v >= 2) {
+        const int i = v - 2;
+        const double r = (__double2hiint(w) < 0) ? 0.0 : w;
+        scc[(size_t)i * TQ + t] = (DG)(r * sIW[i]);
+        sg[(size_t)i * TQ + t] = fma(-sCR[i], slnT[t], fma(sG0[i], sinvT[t], sG1[i]));
+        if constexpr (MIX) sfx[at] = (DG)u * (DG)w;
+        else snw[at] = u * w;
+      } else if (v == 0) {
+        if constexpr (MIX) sfx[at] = fma((DG)w, (DG)u, (DG)sPr[t]);
+        else snw[at] = w * u + sPr[t];
+      } else {
+        if constexpr (MIX) sfx[at] = (DG)u * ((DG)w + (DG)sPr[t]);
+        else snw[at] = u * (w + sPr[t]);
+      }
     }
   }
   __syncthreads();
 
-  // 2b. chemistry (FP64), the reactions of every Gauss point split into R
-  // chunks: reversible rates from the species' Gibbs energies, two exponentials
-  for (int item = tid; item < R * teq; item += nth) {
-    int c = item / teq, t = item - c * teq;
-    const double lnT = slnT[t], invT = sinvT[t];
-    const double *cq = sconc + t, *gq = sg + t;
-    double *wd = swd + (size_t)c * ns * TQ + t;
-    for (int i = 0; i < ns; ++i) wd[(size_t)i * TQ] = 0.0;
-    const double lr = lnT + LN_R_PATM;
-    const int j0 = c * nr / R, j1 = (c + 1) * nr / R;
-    for (int j = j0; j < j1; ++j) {
+  // 3. chemistry, one (reaction, point) per item: the reversible rate of progress
+  // from the Arrhenius and the equilibrium exponentials (arguments in FP64);
+  // and, on the remaining items, the face fluxes of the tile (local face f
+  // between local elements f and f+1), one (level, face) per item: the plain
+  // flux, or one delayed level of the AT flux (Eq. 7) with both sides at the
+  // common level n-k-m
+  const double LN_R_PATM = log(RU / PATM);
+  const int n_chem = nr * teq;
+  for (int item = tid; item < n_chem + O * (te + 1); item += nth) {
+    if (item < n_chem) {
+      const int j = item / teq, t = item - j * teq;
       const Rxn &Rx = srx[j];
-      double lkf = fma(-Rx.EaR, invT, fma(Rx.b, lnT, Rx.lnA));
-      double dg = Rx.dnu * lr;
+      const double lnT = slnT[t];
+      const double lkf = fma(-Rx.EaR, sinvT[t], fma(Rx.b, lnT, Rx.lnA));
+      double dg = Rx.dnu * (lnT + LN_R_PATM);
       const int nx = Rx.nx;
-      for (int k = 0; k < nx; ++k) dg = fma(Rx.xc[k], gq[(size_t)Rx.xs[k] * TQ], dg);
-      double fwd = fexp(lkf, *stab), rev = fexp(lkf + dg, *stab);
+      for (int k = 0; k < nx; ++k) dg = fma(Rx.xc[k], sg[(size_t)Rx.xs[k] * TQ + t], dg);
+      DG fwd, rev;
+      if constexpr (MIX) {
+        fwd = iexpf(lkf, *stab);
+        rev = iexpf(lkf + dg, *stab);
+      } else {
+        fwd = iexp(lkf, *stab);
+        rev = iexp(lkf + dg, *stab);
+      }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (Rx.rn[k] == 0) break;
-        double cc = cq[(size_t)Rx.rs[k] * TQ];
+        DG cc = scc[(size_t)Rx.rs[k] * TQ + t];
         fwd *= cc;
         if (Rx.rn[k] > 1) fwd *= cc;
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (Rx.pn[k] == 0) break;
-        double cc = cq[(size_t)Rx.ps[k] * TQ];
+        DG cc = scc[(size_t)Rx.ps[k] * TQ + t];
         rev *= cc;
         if (Rx.pn[k] > 1) rev *= cc;
       }
-      double qj = fwd - rev;
-      for (int k = 0; k < nx; ++k)
-        wd[(size_t)Rx.xs[k] * TQ] = fma(Rx.xc[k], qj, wd[(size_t)Rx.xs[k] * TQ]);
+      sq[(size_t)j * TQ + t] = fwd - rev;
+      continue;
     }
-  }
-  __syncthreads();
-
-  // 2c. sum of the chunks' rates (into chunk 0, or the FP32 copy)
-  if (MIX || R > 1)
-    for (int item = tid; item < ns * teq; item += nth) {
-      int i = item / teq, t = item - i * teq;
-      double acc = swd[(size_t)i * TQ + t];
-      for (int c = 1; c < R; ++c) acc += swd[((size_t)c * ns + i) * TQ + t];
-      if constexpr (MIX) swdD[(size_t)i * TQ + t] = (DG)acc;
-      else swd[(size_t)i * TQ + t] = acc;
-    }
-  // 3a. face fluxes of the tile (local face f between local elements f and f+1),
-  // one thread per (level, face): the plain flux, or one delayed level of the AT
-  // flux (Eq. 7) with both sides at the common level n-k-m
-  for (int job = tid; job < O * (te + 1); job += nth) {
-    int m = job / (te + 1), f = job - m * (te + 1);
-    int g = e0 + f;  // global face index
-    int pf = (g < N) ? I.pf_of_left[g] : I.pf_of_right[N - 1];
-    int k = (pf >= 0) ? effective_delay(I, nstep, pf) : 0;
+    const int job = item - n_chem;
+    const int m = job / (te + 1), f = job - m * (te + 1);
+    const int g = e0 + f;  // global face index
+    const int pf = (g < N) ? I.pf_of_left[g] : I.pf_of_right[N - 1];
+    const int k = (pf >= 0) ? effective_delay(I, nstep, pf) : 0;
     if (m == 0) sk[f] = k;
     DG *fl = sflx + ((size_t)m * NF + f) * nv;
     DG *wl = str + ((size_t)m * NF + f) * 2 * nv, *wr = wl + nv;
     if (k > 0) {
       if (m >= I.at_order) continue;
-      int64_t lv = nstep - k - m;
+      const int64_t lv = nstep - k - m;
       const double *bl = I.ring_in + ring_trace(I, lv, A.s, pf, 0);
       const double *br = I.ring_in + ring_trace(I, lv, A.s, pf, 1);
       if constexpr (MIX) {
@@ -275,10 +278,22 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
     num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
   }
   __syncthreads();
-  // 3b. the AT sum over levels, m = 0..o-1 in order, in FP64
+
+  // 4. production rates, one (species, point) per item: the net stoichiometric
+  // sum over the species' reactions, in ascending reaction order
+  for (int item = tid; item < ns * teq; item += nth) {
+    const int i = item / teq, t = item - i * teq;
+    DG acc = DG(0);
+    for (int k = soff[i]; k < soff[i + 1]; ++k) {
+      const int term = sterm[k];
+      acc = fma((DG)(signed char)(term & 0xff), sq[(size_t)(term >> 8) * TQ + t], acc);
+    }
+    swd[(size_t)i * TQ + t] = acc;
+  }
+  // 5. the AT sum over levels, m = 0..o-1 in order, in FP64
   for (int item = tid; item < (te + 1) * nv; item += nth) {
-    int f = item / nv, v = item - f * nv;
-    int k = sk[f];
+    const int f = item / nv, v = item - f * nv;
+    const int k = sk[f];
     double acc = (double)sflx[(size_t)f * nv + v];
     if (k > 0) {
       acc *= I.at[k][0];
@@ -289,23 +304,23 @@ __global__ void __launch_bounds__(256) stage_kernel(Mech M, StageArgs A) {
   }
   __syncthreads();
 
-  // 4. assembly of Eq. (5) (in DG arithmetic) and the SSP-RK3 combination (FP64);
-  // history ring writes
+  // 6. assembly of Eq. (5) (in the variant's arithmetic) and the SSP-RK3
+  // combination (FP64); history ring writes
   const int slot_ok = (I.npf > 0);
   const double inv_dx = 1.0 / I.dx;
   const double *sW = ssp + SP_W * ns;
   for (int item = tid; item < nv * te; item += nth) {
-    int v = item / te, e = item - v * te, ge = e0 + e, le = e + 1;
+    const int v = item / te, e = item - v * te, ge = e0 + e, le = e + 1;
     const double *wi = sw + ((size_t)v * (TE + 2) + le) * Q;
     const DG *fq = sfx + (size_t)v * TQ + e * Q;
-    const DG *sq = (v >= 2) ? swdD + (size_t)(v - 2) * TQ + e * Q : nullptr;
+    const DG *sqv = (v >= 2) ? swd + (size_t)(v - 2) * TQ + e * Q : nullptr;
     const DG Wv = (v >= 2) ? (DG)sW[v - 2] : DG(0);
     const DG fr = sfh[(size_t)(e + 1) * nv + v], fl = sfh[(size_t)e * nv + v];
     DG fqr[Q], sqr[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       fqr[q] = fq[q];
-      sqr[q] = (v >= 2) ? sq[q] : DG(0);
+      sqr[q] = (v >= 2) ? sqv[q] : DG(0);
     }
     double out[Q];
 #pragma unroll
@@ -365,18 +380,204 @@ __device__ inline R minmod3(R a, R b, R c) {
   return R(0);
 }
 
-// Shared memory (words of the arithmetic type) per element of the limiter: the
-// element and its two neighbours, the limited characteristic modes, gradP.w, the
-// partial-density sums and momenta of the three blocks, phi_k, two mode sums and
-// the mode sums of block 0.
-__host__ __device__ inline int limiter_elem_words(int nv, int ns, int Q) {
-  return 3 * nv * Q + nv * Q + 3 * 3 * Q + ns + 2 * Q + 8;
-}
-constexpr int LIM_WARPS = 8;
+// Elements per limiter CTA and threads per CTA (LIM_L = 4 lanes per element in
+// the indicator; all threads stage the tile and run the WENO phase).
+constexpr int LIM_EPB = 32;
+constexpr int LIM_THREADS = 128;
 
-// Troubled-cell indicator and (AT-)WENO limiter (Sec. 3.3, Eq. 9-11), a group of
-// G lanes per element (G = 16 when nv <= 16, else 32), in the arithmetic type of
-// the precision variant.
+// Shared memory (words of the arithmetic type) per troubled element in the WENO
+// phase: the element and its two neighbours, the limited characteristic modes,
+// gradP.w, the partial-density sums and momenta of the three blocks, phi_k, two
+// mode sums.
+__host__ __device__ inline int limiter_elem_words(int nv, int ns, int Q) {
+  return 3 * nv * Q + nv * Q + 3 * 3 * Q + ns + 2 * Q + 2;
+}
+
+// Where the values of a neighbour of element e (side 0 left, 1 right) come from:
+// the AT extrapolation of the neighbour's pre-limit history across a delayed PE
+// face (Eq. 11, delay k > 0 at PE face pf), or the pre-limit field of element
+// src, mirrored at a reflecting wall (the boundary ghost is the element itself).
+struct Neighbour {
+  int pf, k, src, ghost, side;
+};
+
+__device__ inline Neighbour neighbour_of(const Inst &I, int64_t nstep, int e, int side) {
+  Neighbour nb;
+  const int N = I.n_elem;
+  nb.side = side;
+  nb.pf = side == 0 ? I.pf_of_left[e] : I.pf_of_right[e];
+  nb.k = (nb.pf >= 0) ? effective_delay(I, nstep, nb.pf) : 0;
+  nb.src = side == 0 ? e - 1 : e + 1;
+  nb.ghost = 0;
+  if (nb.src < 0 || nb.src >= N) {
+    if (I.bc_left == ADG_BC_PERIODIC) {
+      nb.src = (nb.src + N) % N;
+    } else {
+      nb.src = e;
+      nb.ghost = ((side == 0 ? I.bc_left : I.bc_right) == ADG_BC_REFLECT) ? 1 : 0;
+    }
+  }
+  return nb;
+}
+
+// Mode j of variable v of a neighbour (the sum of the AT levels in FP64).
+__device__ inline double neighbour_mode(const Inst &I, const double *wpre, int s, int64_t nstep,
+                                        const Neighbour &nb, int v, int j, int Q) {
+  if (nb.k > 0) {
+    double acc = 0.0;
+    for (int m = 0; m < I.at_order; ++m)
+      acc += I.at[nb.k][m] *
+             I.ring_pre[ring_block(I, nstep - nb.k - m, s, nb.pf, nb.side) + (size_t)v * Q + j];
+    return acc;
+  }
+  double x = wpre[((size_t)v * I.n_elem + nb.src) * Q + j];
+  if (nb.ghost && (((j & 1) != 0) != (v == 0))) x = -x;
+  return x;
+}
+
+// Lanes per element in the indicator.
+constexpr int LIM_L = 4;
+static_assert(LIM_THREADS == LIM_EPB * LIM_L, "one group of LIM_L lanes per element");
+
+// Troubled-cell indicator of element e (Sec. 3.3), a group of L lanes, in the
+// arithmetic type R. In each characteristic field of L(wbar_e) the face
+// deviations v(+1) - vbar and vbar - v(-1) go through the TVB-modified minmod
+// with the neighbours' mean differences; deviations below 1e-5 of the field's
+// magnitude sum_v |L_kv| sigma_v count as zero. Three passes over the
+// variables, the species and the fields split over the group's lanes: the
+// thermodynamics of the cell average; gradP.w, the partial-density sum and the
+// momentum at the five points (own average, faces +1 and -1, neighbours'
+// averages); the characteristic values per field, with the branch-free
+// coefficients (A, B, C, D) described at the limiter kernel. Every lane of the
+// warp calls it (shuffles); the result is the same on the group's lanes.
+// own: modes of variable 0 of the element in the staged tile (variables vs
+// apart, the neighbours' modes Q before and after, halo ghosts included);
+// spf: species fields in R; atl, atr: the AT-extrapolated averages [nv] of a
+// neighbour across a delayed PE face, or null.
+template <int Q, int L, typename R>
+__device__ bool troubled_cell(const Mech &M, const Inst &I, int s, int64_t nstep, int e,
+                              const R *own, int vs, const R *spf, const R *atl, const R *atr) {
+  const int ns = M.ns, nv = ns + 2;
+  const int lane = threadIdx.x & 31, li = lane % L;
+  const unsigned FULL = 0xffffffffu;
+  const R *qW = spf + SP_QW * ns, *cvW = spf + SP_CVW * ns;
+  const R *RW = spf + SP_RW * ns, *cpW = spf + SP_CPW * ns;
+  auto allsum = [&](R x) {
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o, L);
+    return x;
+  };
+  // values of variable v at the five points
+  auto points = [&](int v, R *x) {
+    const R *w = own + (size_t)v * vs;
+    R sp = 0, sm = 0;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      sp += w[j];
+      sm += (j & 1) ? -w[j] : w[j];
+    }
+    x[0] = w[0];
+    x[1] = sp;
+    x[2] = sm;
+    x[3] = atl ? atl[v] : w[-Q];
+    x[4] = atr ? atr[v] : w[Q];
+  };
+  // 1. thermodynamics of the cell average
+  R rho = 0, qsum = 0, cv = 0, Rm = 0, cpm = 0;
+  for (int i = li; i < ns; i += L) {
+    R r = own[(size_t)(2 + i) * vs];
+    rho += r;
+    qsum = fma(r, qW[i], qsum);
+    cv = fma(r, cvW[i], cv);
+    Rm = fma(r, RW[i], Rm);
+    cpm = fma(r, cpW[i], cpm);
+  }
+  rho = allsum(rho);
+  qsum = allsum(qsum);
+  cv = allsum(cv);
+  Rm = allsum(Rm);
+  cpm = allsum(cpm);
+  const R irho = R(1) / rho, icv = R(1) / cv;
+  const R m0 = own[0], E0 = own[vs];
+  const R u = m0 * irho;
+  const R T = (E0 - R(0.5) * m0 * u - qsum) * icv;
+  const R P = T * Rm;
+  const R gam = cpm * icv, g = gam - R(1);
+  const R a = sqrt(gam * P * irho);
+  const R ia2 = R(1) / (a * a), ha2 = R(0.5) * ia2;
+  if (li == 0 && (!(rho > R(0)) || !(T > R(0)) || !isfinite(T)))
+    report_error(I, ADG_ERR_NONPHYSICAL, e, s, nstep);
+  auto phi_of = [&](int i) { return fma(g, fma(-cvW[i], T, R(0.5) * u * u - qW[i]), T * RW[i]); };
+  // 2. gradP.w, sum rho Y and rho u at the five points; sums of |phi|
+  R gp[5], rs[5], mm[5], x[5];
+  R sphi = 0, sphm = 0, sphp = 0;
+  points(0, mm);
+  points(1, x);
+#pragma unroll
+  for (int p = 0; p < 5; ++p) {
+    gp[p] = li == 0 ? g * fma(-u, mm[p], x[p]) : R(0);
+    rs[p] = 0;
+  }
+  for (int i = li; i < ns; i += L) {
+    const R ph = phi_of(i);
+    sphi += fabs(ph);
+    sphm += fabs(ph - a * u);
+    sphp += fabs(ph + a * u);
+    points(2 + i, x);
+#pragma unroll
+    for (int p = 0; p < 5; ++p) {
+      gp[p] = fma(ph, x[p], gp[p]);
+      rs[p] += x[p];
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 5; ++p) {
+    gp[p] = allsum(gp[p]);
+    rs[p] = allsum(rs[p]);
+  }
+  sphi = allsum(sphi);
+  sphm = allsum(sphm);
+  sphp = allsum(sphp);
+  // 3. the characteristic fields, k = 0 and nv-1 acoustic, k = 1..ns species k-1
+  const R sig0 = fma(rho, a, fabs(m0)), sig1 = fabs(E0), sigr = rho;
+  const R tvb = (R)I.tvb, tau = R(1e-5);
+  bool tr = false;
+  for (int k = li; k < nv; k += L) {
+    R v[5], scale;
+    if (k == 0 || k == nv - 1) {
+      const R sgn = k == 0 ? R(-1) : R(1);
+      const R cA = ha2, cB = sgn * a * ha2, cC = -sgn * a * u * ha2;
+#pragma unroll
+      for (int p = 0; p < 5; ++p) v[p] = fma(cA, gp[p], fma(cB, mm[p], cC * rs[p]));
+      const R srr = cA * (k == 0 ? sphp : sphm);
+      scale = fma(fabs(fma(cA, -u * g, cB)), sig0, fma(fabs(cA * g), sig1, srr * sigr));
+    } else {
+      const int i = k - 1;
+      points(2 + i, x);
+      const R cA = -x[0] * irho * ia2;
+      const R ph = phi_of(i);
+#pragma unroll
+      for (int p = 0; p < 5; ++p) v[p] = fma(cA, gp[p], x[p]);
+      const R srr = fabs(fma(cA, ph, R(1))) + fabs(cA) * (sphi - fabs(ph));
+      scale = fma(fabs(cA * -u * g), sig0, fma(fabs(cA * g), sig1, srr * sigr));
+    }
+    const R ut = v[1] - v[0], utt = v[0] - v[2], dp = v[4] - v[0], dm = v[0] - v[3];
+    const R fl = tau * scale;
+    if (fabs(ut) > fl && fabs(ut) > tvb && minmod3(ut, dp, dm) != ut) tr = true;
+    if (fabs(utt) > fl && fabs(utt) > tvb && minmod3(utt, dp, dm) != utt) tr = true;
+  }
+  const unsigned bal = __ballot_sync(FULL, tr);
+  const unsigned gm = ((1u << L) - 1u) << (lane - li);
+  return (bal & gm) != 0u;
+}
+
+// Troubled-cell indicator and (AT-)WENO limiter (Sec. 3.3, Eq. 9-11), in the
+// arithmetic type of the precision variant. Phase 1: one element per thread
+// runs the indicator and writes its flag; troubled elements go to a list in
+// shared memory. Phase 2: a group of G lanes per troubled element (G = 16 when
+// nv <= 16, else 32) reconstructs its characteristic fields with WENO and
+// writes modes >= 1 of the next stage's input (the stage kernel wrote the
+// pre-limit output there for every element already).
 // Eigen-structure of the frozen Jacobian at the cell average: right vectors
 // r_-/+ = (u -/+ a, H -/+ u a, Y), species r_k = (u, u^2 - phi_k/g, e_k); left
 // vectors l_-/+ = (gradP -/+ a (1, 0, -u..-u)) / (2 a^2), l_k = e_k - Y_k gradP/a^2,
@@ -384,309 +585,306 @@ constexpr int LIM_WARPS = 8;
 // Every characteristic value is written in one branch-free form,
 // v = A gradP.w + B (rho u)_w + C (sum rho Y)_w + D (rho Y_k)_w,
 // with (A, B, C, D) = (1/2a^2, -/+ a/2a^2, +/- a u/2a^2, 0) for the acoustic fields
-// and (-Y_k/a^2, 0, 0, 1) for species k, so that all lanes run the same code.
+// and (-Y_k/a^2, 0, 0, 1) for species k.
 template <int Q, int G, bool MIX>
-__global__ void __launch_bounds__(32 * LIM_WARPS) limiter_kernel(Mech M, LimArgs A) {
+__global__ void __launch_bounds__(LIM_THREADS) limiter_kernel(Mech M, LimArgs A) {
   using DG = dg_t<MIX>;
   extern __shared__ __align__(16) double lsm_raw[];
   DG *lsm = reinterpret_cast<DG *>(lsm_raw);
   __shared__ Inst sI;
+  __shared__ int s_list[LIM_EPB];
+  __shared__ int s_n;
+  __shared__ Neighbour s_nb[2][LIM_EPB];
   const int2 blkid = A.blocks[blockIdx.x];
   load_inst(sI, A.insts + blkid.x);
+  if (threadIdx.x == 0) s_n = 0;
   __syncthreads();
   const Inst &I = sI;
   if (I.limiter == ADG_LIM_NONE) return;
+  const int N = I.n_elem, nv = I.nv, ns = M.ns;
+  const int64_t nstep = *I.step;
+
+  // 1. stage the CTA's elements with a one-element halo (ghosts at walls) and
+  // the species fields in the variant's type; then the indicator, one element
+  // per thread
+  const int e0 = blkid.y, te = min(LIM_EPB, N - e0);
+  const int vs = (LIM_EPB + 2) * Q;
+  DG *spf = lsm;                                   // [SP_NFIELDS][ns]
+  DG *atn = spf + SP_NFIELDS * ns;                 // [2][LIM_EPB][nv] AT neighbour averages
+  DG *tile = atn + 2 * LIM_EPB * nv;               // [nv][LIM_EPB + 2][Q]
+  for (int k = threadIdx.x; k < SP_NFIELDS * ns; k += blockDim.x) spf[k] = (DG)M.sp[k];
+  if ((int)threadIdx.x < 2 * te) {
+    const int side = threadIdx.x / te, le = threadIdx.x - side * te;
+    s_nb[side][le] = neighbour_of(I, nstep, e0 + le, side);
+  }
+  {
+    // batches of loads in flight per thread before they are used
+    constexpr int BATCH = 8;
+    const bool periodic = (I.bc_left == ADG_BC_PERIODIC);
+    const int span = (te + 2) * Q, total = nv * span, nth = blockDim.x;
+    for (int base = threadIdx.x; base < total; base += BATCH * nth) {
+      double xs[BATCH];
+      int dst[BATCH];
+#pragma unroll
+      for (int b = 0; b < BATCH; ++b) {
+        const int idx = base + b * nth;
+        dst[b] = -1;
+        xs[b] = 0.0;
+        if (idx < total) {
+          const int v = idx / span, r = idx - v * span, le = r / Q, j = r - le * Q;
+          int src = e0 - 1 + le;
+          bool mirror = false;
+          if (src < 0 || src >= N) {
+            if (periodic) {
+              src = (src + N) % N;
+            } else {
+              const bool left = src < 0;
+              src = left ? 0 : N - 1;
+              mirror = ((left ? I.bc_left : I.bc_right) == ADG_BC_REFLECT);
+            }
+          }
+          xs[b] = I.wpre[((size_t)v * N + src) * Q + j];
+          if (mirror && (((j & 1) != 0) != (v == 0))) xs[b] = -xs[b];
+          dst[b] = v * vs + le * Q + j;
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < BATCH; ++b)
+        if (dst[b] >= 0) tile[dst[b]] = (DG)xs[b];
+    }
+  }
+  __syncthreads();
+  // averages of the neighbours across delayed PE faces (Eq. 11), one
+  // (side, element, variable) per item
+  for (int item = threadIdx.x; item < 2 * te * nv; item += blockDim.x) {
+    const int side = item / (te * nv), r = item - side * te * nv, le = r / nv, v = r - le * nv;
+    const Neighbour &nb = s_nb[side][le];
+    if (nb.k > 0) atn[(side * LIM_EPB + le) * nv + v] = (DG)neighbour_mode(I, I.wpre, A.s, nstep, nb, v, 0, Q);
+  }
+  __syncthreads();
+  {
+    // every lane runs the indicator (shuffles); groups past the last element
+    // work on the first element and write nothing
+    const int le = threadIdx.x / LIM_L;
+    const bool valid = le < te;
+    const int lv = valid ? le : 0, e = e0 + lv;
+    const DG *atl = s_nb[0][lv].k > 0 ? atn + lv * nv : nullptr;
+    const DG *atr = s_nb[1][lv].k > 0 ? atn + (LIM_EPB + lv) * nv : nullptr;
+    const bool t = troubled_cell<Q, LIM_L, DG>(M, I, A.s, nstep, e, tile + (lv + 1) * Q, vs, spf,
+                                               atl, atr);
+    if (valid && threadIdx.x % LIM_L == 0) {
+      I.flags[(size_t)A.s * N + e] = t ? 1 : 0;
+      if (t) {
+        I.count[e] += 1;
+        s_list[atomicAdd(&s_n, 1)] = e;
+      }
+    }
+  }
+  __syncthreads();
+  const int n_tr = s_n;
+  if (n_tr == 0) return;
+
+  // 2. WENO (Eq. 9-10) on the troubled elements, G lanes each
   const Basis &B = c_basis[Q - 2];
   const BasisF &BF = c_basis_f[Q - 2];
-  const int N = I.n_elem, nv = I.nv, ns = M.ns;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gl = lane % G, gw = lane / G;
   constexpr int EPW = 32 / G;
+  constexpr int NWARP = LIM_THREADS / 32;
   const int slot = warp * EPW + gw;
-  const int e = blkid.y + slot;
-  const bool valid = e < N;
-  const int64_t nstep = *I.step;
   double *A_wout = (A.s == 0) ? I.wa : (A.s == 1) ? I.wb : I.wn;
   const double *A_wpre = I.wpre;
   const unsigned FULL = 0xffffffffu;
   const unsigned gmask = (G == 32) ? FULL : (0xffffu << (16 * gw));
   const size_t VS = (size_t)N * Q;
   const int NB = nv * Q;
-  DG *blk = lsm + (size_t)slot * limiter_elem_words(nv, ns, Q);  // [3][nv][Q]
+  DG *blk = tile + (size_t)nv * vs + (size_t)slot * limiter_elem_words(nv, ns, Q);  // [3][nv][Q]
   DG *vlim = blk + 3 * NB;                                        // [nv][Q]
   DG *gpv = vlim + NB;                                            // [3][Q]
   DG *rsv = gpv + 3 * Q;                                          // [3][Q]
   DG *mmv = rsv + 3 * Q;                                          // [3][Q]
   DG *phi = mmv + 3 * Q;                                          // [ns]
   DG *sums = phi + ns;                                            // [2][Q]
-  DG *ssum = sums + 2 * Q;   // mode sums of block 0: gp, mm, rs (plain, alternating)
-  const bool periodic = (I.bc_left == ADG_BC_PERIODIC);
-
-  // 1. the element (block 0) and its neighbours (1 left, 2 right): the pre-limit
-  //    field, the AT extrapolation of the neighbour's pre-limit history across a
-  //    delayed PE face (Eq. 11, summed in FP64), or a boundary ghost
-  if (valid) {
-    for (int d = 0; d < 3; ++d) {
-      DG *dst = blk + d * NB;
-      int src = e, ghost = 0, k = 0, pf = -1;
-      if (d > 0) {
-        pf = d == 1 ? I.pf_of_left[e] : I.pf_of_right[e];
-        k = (pf >= 0) ? effective_delay(I, nstep, pf) : 0;
-        src = d == 1 ? e - 1 : e + 1;
-        if (src < 0 || src >= N) {
-          if (periodic) {
-            src = (src + N) % N;
-          } else {
-            src = e;
-            ghost = ((d == 1 ? I.bc_left : I.bc_right) == ADG_BC_REFLECT) ? 1 : 0;
+  const DG *qWd = spf + SP_QW * ns, *cvWd = spf + SP_CVW * ns;
+  const DG *RWd = spf + SP_RW * ns, *cpWd = spf + SP_CPW * ns;
+  for (int base = 0; base < n_tr; base += NWARP * EPW) {
+    const int idx = base + slot;
+    const bool valid = idx < n_tr;
+    const int e = valid ? s_list[idx] : 0;
+    // the element and its neighbours (pre-limit, AT-extrapolated or ghost)
+    if (valid) {
+      const Neighbour nl = neighbour_of(I, nstep, e, 0), nr = neighbour_of(I, nstep, e, 1);
+      for (int t = gl; t < NB; t += G) {
+        const int v = t / Q, j = t - v * Q;
+        blk[t] = (DG)A_wpre[(size_t)v * VS + (size_t)e * Q + j];
+        blk[NB + t] = (DG)neighbour_mode(I, A_wpre, A.s, nstep, nl, v, j, Q);
+        blk[2 * NB + t] = (DG)neighbour_mode(I, A_wpre, A.s, nstep, nr, v, j, Q);
+      }
+    }
+    __syncwarp();
+    // cell-average thermo and eigen-quantities (species sums split over lanes)
+    DG rho = 0, qsum = 0, cv = 0, Rm = 0, cpm = 0;
+    if (valid)
+      for (int i = gl; i < ns; i += G) {
+        DG r = blk[(2 + i) * Q];
+        rho += r;
+        qsum = fma(r, qWd[i], qsum);
+        cv = fma(r, cvWd[i], cv);
+        Rm = fma(r, RWd[i], Rm);
+        cpm = fma(r, cpWd[i], cpm);
+      }
+    for (int o = G / 2; o > 0; o >>= 1) {
+      rho += __shfl_xor_sync(FULL, rho, o, G);
+      qsum += __shfl_xor_sync(FULL, qsum, o, G);
+      cv += __shfl_xor_sync(FULL, cv, o, G);
+      Rm += __shfl_xor_sync(FULL, Rm, o, G);
+      cpm += __shfl_xor_sync(FULL, cpm, o, G);
+    }
+    if (!valid) {
+      rho = 1;
+      cv = 1;
+      cpm = 2;
+      Rm = 1;
+    }
+    const DG irho = DG(1) / rho, icv = DG(1) / cv;
+    const DG m0 = valid ? blk[0] : DG(0), E0 = valid ? blk[Q] : DG(1);
+    const DG u = m0 * irho;
+    const DG T = (E0 - DG(0.5) * m0 * u - qsum) * icv;
+    const DG P = T * Rm;
+    const DG gam = cpm * icv, g = gam - DG(1);
+    const DG a = sqrt(gam * P * irho);
+    const DG H = (E0 + P) * irho;
+    const DG ia2 = DG(1) / (a * a);
+    if (valid)
+      for (int i = gl; i < ns; i += G)
+        phi[i] = fma(g, fma(-cvWd[i], T, DG(0.5) * u * u - qWd[i]), T * RWd[i]);
+    __syncwarp();
+    if (valid)
+      for (int t = gl; t < 3 * Q; t += G) {
+        int b = t / Q, j = t - b * Q;
+        const DG *x = blk + b * NB;
+        DG acc = g * fma(-u, x[j], x[Q + j]), sr = 0;
+        for (int i = 0; i < ns; ++i) {
+          DG r = x[(2 + i) * Q + j];
+          acc = fma(phi[i], r, acc);
+          sr += r;
+        }
+        gpv[t] = acc;
+        rsv[t] = sr;
+        mmv[t] = x[j];
+      }
+    __syncwarp();
+    const DG ha2 = DG(0.5) * ia2;
+    auto coef = [&](int k, DG &cA, DG &cB, DG &cC, DG &cD, int &ri) {
+      bool ac = (k == 0) || (k == nv - 1);
+      DG sgn = (k == 0) ? DG(-1) : DG(1);
+      ri = ac ? 0 : k - 1;
+      DG Yk = ac ? DG(0) : blk[(2 + ri) * Q] * irho;
+      cA = ac ? ha2 : -Yk * ia2;
+      cB = ac ? sgn * a * ha2 : DG(0);
+      cC = ac ? -sgn * a * u * ha2 : DG(0);
+      cD = ac ? DG(0) : DG(1);
+    };
+    auto val = [&](DG cA, DG cB, DG cC, DG cD, int ri, int b, int j) {
+      return fma(cA, gpv[b * Q + j],
+                 fma(cB, mmv[b * Q + j], fma(cC, rsv[b * Q + j], cD * blk[b * NB + (2 + ri) * Q + j])));
+    };
+    // WENO per characteristic field, the group's lanes over fields
+    const DG gmw[3] = {DG(0.001), DG(0.998), DG(0.001)};
+    const DG eps = DG(1e-6);
+    if (valid)
+      for (int k = gl; k < nv; k += G) {
+        DG cA, cB, cC, cD;
+        int ri;
+        coef(k, cA, cB, cC, cD, ri);
+        DG vo[Q], vl0[Q], vr0[Q], vl[Q], vr[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          vo[j] = val(cA, cB, cC, cD, ri, 0, j);
+          vl0[j] = val(cA, cB, cC, cD, ri, 1, j);
+          vr0[j] = val(cA, cB, cC, cD, ri, 2, j);
+        }
+        // neighbours continued into this cell, their mean replaced by the own mean
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          DG al = 0, ar = 0;
+#pragma unroll
+          for (int j = 0; j < Q; ++j) {
+            if constexpr (MIX) {
+              al = fma(BF.Sl[i][j], vl0[j], al);
+              ar = fma(BF.Sr[i][j], vr0[j], ar);
+            } else {
+              al = fma(B.Sl[i][j], vl0[j], al);
+              ar = fma(B.Sr[i][j], vr0[j], ar);
+            }
+          }
+          vl[i] = al;
+          vr[i] = ar;
+        }
+        vl[0] = vo[0];
+        vr[0] = vo[0];
+        DG be[3] = {0, 0, 0};
+#pragma unroll
+        for (int i = 1; i < Q; ++i)
+#pragma unroll
+          for (int j = 1; j < Q; ++j) {
+            DG bij = MIX ? (DG)BF.B[i][j] : (DG)B.B[i][j];
+            be[0] = fma(vl[i] * bij, vl[j], be[0]);
+            be[1] = fma(vo[i] * bij, vo[j], be[1]);
+            be[2] = fma(vr[i] * bij, vr[j], be[2]);
+          }
+        DG wt[3], sw = 0;
+        if constexpr (MIX) {
+          // the same normalised weights written as ratios, safe from overflow in FP32
+          DG dmin = fmin(eps + be[0], fmin(eps + be[1], eps + be[2]));
+          for (int t = 0; t < 3; ++t) {
+            DG rr = dmin / (eps + be[t]);
+            wt[t] = gmw[t] * rr * rr;
+            sw += wt[t];
+          }
+        } else {
+          for (int t = 0; t < 3; ++t) {
+            DG d = eps + be[t];
+            wt[t] = gmw[t] / (d * d);
+            sw += wt[t];
           }
         }
+        DG isw = DG(1) / sw;
+        vlim[k * Q] = vo[0];
+#pragma unroll
+        for (int i = 1; i < Q; ++i)
+          vlim[k * Q + i] = (wt[0] * vl[i] + wt[1] * vo[i] + wt[2] * vr[i]) * isw;
       }
-      if (k > 0) {
-        int side = d == 1 ? 0 : 1;
-        for (int t = gl; t < NB; t += G) {
-          double acc = 0.0;
-          for (int m = 0; m < I.at_order; ++m)
-            acc += I.at[k][m] * I.ring_pre[ring_block(I, nstep - k - m, A.s, pf, side) + t];
-          dst[t] = (DG)acc;
+    __syncwarp();
+    // back to conserved variables with R (modes >= 1; the cell average is kept)
+    if (valid)
+      for (int i = gl; i < Q; i += G) {
+        DG s1 = 0, s2 = 0;
+        for (int k = 1; k < nv - 1; ++k) {
+          DG x = vlim[k * Q + i];
+          s1 += x;
+          s2 = fma(x, u * u - phi[k - 1] / g, s2);
         }
-      } else {
-        for (int t = gl; t < NB; t += G) {
-          int v = t / Q, j = t - v * Q;
-          double x = A_wpre[(size_t)v * VS + (size_t)src * Q + j];
-          if (ghost && (((j & 1) != 0) != (v == 0))) x = -x;
-          dst[t] = (DG)x;
-        }
+        sums[i] = s1;
+        sums[Q + i] = s2;
+      }
+    __syncwarp();
+    if (valid) {
+      double *out = A_wout + (size_t)e * Q;
+      for (int t = gl; t < NB; t += G) {
+        int v = t / Q, i = t - v * Q;
+        if (i == 0) continue;
+        DG lm = vlim[i], lp = vlim[(nv - 1) * Q + i];
+        DG o;
+        if (v == 0) o = lm * (u - a) + lp * (u + a) + u * sums[i];
+        else if (v == 1) o = lm * (H - u * a) + lp * (H + u * a) + sums[Q + i];
+        else o = (lm + lp) * (blk[v * Q] * irho) + vlim[(v - 1) * Q + i];
+        out[(size_t)v * VS + i] = (double)o;
       }
     }
+    __syncwarp();
   }
-  __syncwarp();
-
-  // 2. cell average: thermo and eigen-quantities (species sums split over lanes)
-  const double *qWd = M.sp + SP_QW * ns, *cvWd = M.sp + SP_CVW * ns;
-  const double *RWd = M.sp + SP_RW * ns, *cpWd = M.sp + SP_CPW * ns;
-  DG rho = 0, qsum = 0, cv = 0, Rm = 0, cpm = 0;
-  if (valid)
-    for (int i = gl; i < ns; i += G) {
-      DG r = blk[(2 + i) * Q];
-      rho += r;
-      qsum = fma(r, (DG)qWd[i], qsum);
-      cv = fma(r, (DG)cvWd[i], cv);
-      Rm = fma(r, (DG)RWd[i], Rm);
-      cpm = fma(r, (DG)cpWd[i], cpm);
-    }
-  for (int o = G / 2; o > 0; o >>= 1) {
-    rho += __shfl_xor_sync(FULL, rho, o, G);
-    qsum += __shfl_xor_sync(FULL, qsum, o, G);
-    cv += __shfl_xor_sync(FULL, cv, o, G);
-    Rm += __shfl_xor_sync(FULL, Rm, o, G);
-    cpm += __shfl_xor_sync(FULL, cpm, o, G);
-  }
-  if (!valid) {
-    rho = 1;
-    cv = 1;
-    cpm = 2;
-    Rm = 1;
-  }
-  const DG irho = DG(1) / rho, icv = DG(1) / cv;
-  const DG m0 = valid ? blk[0] : DG(0), E0 = valid ? blk[Q] : DG(1);
-  const DG u = m0 * irho;
-  const DG T = (E0 - DG(0.5) * m0 * u - qsum) * icv;
-  const DG P = T * Rm;
-  const DG gam = cpm * icv, g = gam - DG(1);
-  const DG a = sqrt(gam * P * irho);
-  const DG H = (E0 + P) * irho;
-  const DG ia2 = DG(1) / (a * a);
-  if (valid && gl == 0 && (!(rho > DG(0)) || !(T > DG(0)) || !isfinite(T)))
-    report_error(I, ADG_ERR_NONPHYSICAL, e, A.s, nstep);
-  // phi_k, and the sums of |phi_i|, |phi_i - a u|, |phi_i + a u| for the noise floor
-  DG sphi = 0, sphm = 0, sphp = 0;
-  if (valid) {
-    for (int i = gl; i < ns; i += G) {
-      DG ph = fma(g, fma(-(DG)cvWd[i], T, DG(0.5) * u * u - (DG)qWd[i]), T * (DG)RWd[i]);
-      phi[i] = ph;
-      sphi += fabs(ph);
-      sphm += fabs(ph - a * u);
-      sphp += fabs(ph + a * u);
-    }
-  }
-  for (int o = G / 2; o > 0; o >>= 1) {
-    sphi += __shfl_xor_sync(FULL, sphi, o, G);
-    sphm += __shfl_xor_sync(FULL, sphm, o, G);
-    sphp += __shfl_xor_sync(FULL, sphp, o, G);
-  }
-  __syncwarp();
-  if (valid)
-    for (int t = gl; t < 3 * Q; t += G) {
-      int b = t / Q, j = t - b * Q;
-      const DG *x = blk + b * NB;
-      DG acc = g * fma(-u, x[j], x[Q + j]), sr = 0;
-      for (int i = 0; i < ns; ++i) {
-        DG r = x[(2 + i) * Q + j];
-        acc = fma(phi[i], r, acc);
-        sr += r;
-      }
-      gpv[t] = acc;
-      rsv[t] = sr;
-      mmv[t] = x[j];
-    }
-  __syncwarp();
-  if (valid && gl < 6) {
-    const DG *src = (gl % 3 == 0) ? gpv : (gl % 3 == 1) ? mmv : rsv;
-    DG acc = 0;
-    for (int j = 0; j < Q; ++j) acc += (gl >= 3 && (j & 1)) ? -src[j] : src[j];
-    ssum[gl] = acc;
-  }
-  __syncwarp();
-
-  // coefficients of field k and its value for block b, mode j
-  const DG ha2 = DG(0.5) * ia2;
-  auto coef = [&](int k, DG &cA, DG &cB, DG &cC, DG &cD, int &ri) {
-    bool ac = (k == 0) || (k == nv - 1);
-    DG sgn = (k == 0) ? DG(-1) : DG(1);
-    ri = ac ? 0 : k - 1;
-    DG Yk = ac ? DG(0) : blk[(2 + ri) * Q] * irho;
-    cA = ac ? ha2 : -Yk * ia2;
-    cB = ac ? sgn * a * ha2 : DG(0);
-    cC = ac ? -sgn * a * u * ha2 : DG(0);
-    cD = ac ? DG(0) : DG(1);
-  };
-  auto val = [&](DG cA, DG cB, DG cC, DG cD, int ri, int b, int j) {
-    return fma(cA, gpv[b * Q + j],
-               fma(cB, mmv[b * Q + j], fma(cC, rsv[b * Q + j], cD * blk[b * NB + (2 + ri) * Q + j])));
-  };
-
-  // 3. indicator: the lanes of a group test the fields
-  const DG sig0 = fma(rho, a, fabs(m0)), sig1 = fabs(E0), sigr = rho;
-  // noise floor 1e-5 of the field's magnitude in both precisions: above the
-  // single-precision rounding, so both variants select the same troubled cells
-  const DG tvb = (DG)I.tvb, tau = DG(1e-5);
-  bool mine = false;
-  if (valid)
-    for (int k = gl; k < nv; k += G) {
-      DG cA, cB, cC, cD;
-      int ri;
-      coef(k, cA, cB, cC, cD, ri);
-      // the face values v(+1), v(-1) from the mode sums (linear in the modes)
-      const DG *rk = blk + (2 + ri) * Q;
-      DG rsum = 0, ralt = 0;
-#pragma unroll
-      for (int j = 0; j < Q; ++j) {
-        rsum += rk[j];
-        ralt += (j & 1) ? -rk[j] : rk[j];
-      }
-      DG vb = val(cA, cB, cC, cD, ri, 0, 0);
-      DG vp = fma(cA, ssum[0], fma(cB, ssum[1], fma(cC, ssum[2], cD * rsum)));
-      DG vm = fma(cA, ssum[3], fma(cB, ssum[4], fma(cC, ssum[5], cD * ralt)));
-      DG vL = val(cA, cB, cC, cD, ri, 1, 0), vR = val(cA, cB, cC, cD, ri, 2, 0);
-      // sum_v |L_kv| sigma_v in closed form: for species k, |1 + A phi_k| plus
-      // |A| (sum |phi| - |phi_k|); for the acoustic fields A sum |phi_i -/+ a u|
-      bool ac = (k == 0) || (k == nv - 1);
-      DG srr = ac ? cA * (k == 0 ? sphp : sphm)
-                  : fabs(fma(cA, phi[ri], DG(1))) + fabs(cA) * (sphi - fabs(phi[ri]));
-      DG scale = fma(fabs(fma(cA, -u * g, cB)), sig0, fma(fabs(cA * g), sig1, srr * sigr));
-      DG ut = vp - vb, utt = vb - vm, dp = vR - vb, dm = vb - vL;
-      DG fl = tau * scale;
-      if (fabs(ut) > fl && fabs(ut) > tvb && minmod3(ut, dp, dm) != ut) mine = true;
-      if (fabs(utt) > fl && fabs(utt) > tvb && minmod3(utt, dp, dm) != utt) mine = true;
-    }
-  unsigned bal = __ballot_sync(FULL, mine) & gmask;
-  const bool troubled = valid && bal != 0u && I.limiter != ADG_LIM_NONE;
-  if (valid && gl == 0) {
-    I.flags[(size_t)A.s * N + e] = troubled ? 1 : 0;
-    if (troubled) I.count[e] += 1;
-  }
-  if (!troubled) return;
-
-  // 4. WENO (Eq. 9-10) per characteristic field, the group's lanes over fields
-  const DG gmw[3] = {DG(0.001), DG(0.998), DG(0.001)};
-  const DG eps = DG(1e-6);
-  for (int k = gl; k < nv; k += G) {
-    DG cA, cB, cC, cD;
-    int ri;
-    coef(k, cA, cB, cC, cD, ri);
-    DG vo[Q], vl0[Q], vr0[Q], vl[Q], vr[Q];
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      vo[j] = val(cA, cB, cC, cD, ri, 0, j);
-      vl0[j] = val(cA, cB, cC, cD, ri, 1, j);
-      vr0[j] = val(cA, cB, cC, cD, ri, 2, j);
-    }
-    // neighbours continued into this cell, their mean replaced by the own mean
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      DG al = 0, ar = 0;
-#pragma unroll
-      for (int j = 0; j < Q; ++j) {
-        if constexpr (MIX) {
-          al = fma(BF.Sl[i][j], vl0[j], al);
-          ar = fma(BF.Sr[i][j], vr0[j], ar);
-        } else {
-          al = fma(B.Sl[i][j], vl0[j], al);
-          ar = fma(B.Sr[i][j], vr0[j], ar);
-        }
-      }
-      vl[i] = al;
-      vr[i] = ar;
-    }
-    vl[0] = vo[0];
-    vr[0] = vo[0];
-    DG be[3] = {0, 0, 0};
-#pragma unroll
-    for (int i = 1; i < Q; ++i)
-#pragma unroll
-      for (int j = 1; j < Q; ++j) {
-        DG bij = MIX ? (DG)BF.B[i][j] : (DG)B.B[i][j];
-        be[0] = fma(vl[i] * bij, vl[j], be[0]);
-        be[1] = fma(vo[i] * bij, vo[j], be[1]);
-        be[2] = fma(vr[i] * bij, vr[j], be[2]);
-      }
-    DG wt[3], sw = 0;
-    if constexpr (MIX) {
-      // the same normalised weights written as ratios, safe from overflow in FP32
-      DG dmin = fmin(eps + be[0], fmin(eps + be[1], eps + be[2]));
-      for (int t = 0; t < 3; ++t) {
-        DG rr = dmin / (eps + be[t]);
-        wt[t] = gmw[t] * rr * rr;
-        sw += wt[t];
-      }
-    } else {
-      for (int t = 0; t < 3; ++t) {
-        DG d = eps + be[t];
-        wt[t] = gmw[t] / (d * d);
-        sw += wt[t];
-      }
-    }
-    DG isw = DG(1) / sw;
-    vlim[k * Q] = vo[0];
-#pragma unroll
-    for (int i = 1; i < Q; ++i)
-      vlim[k * Q + i] = (wt[0] * vl[i] + wt[1] * vo[i] + wt[2] * vr[i]) * isw;
-  }
-  __syncwarp(gmask);
-  // 5. back to conserved variables with R (modes >= 1; the cell average is kept)
-  for (int i = gl; i < Q; i += G) {
-    DG s1 = 0, s2 = 0;
-    for (int k = 1; k < nv - 1; ++k) {
-      DG x = vlim[k * Q + i];
-      s1 += x;
-      s2 = fma(x, u * u - phi[k - 1] / g, s2);
-    }
-    sums[i] = s1;
-    sums[Q + i] = s2;
-  }
-  __syncwarp(gmask);
-  double *out = A_wout + (size_t)e * Q;
-  for (int t = gl; t < NB; t += G) {
-    int v = t / Q, i = t - v * Q;
-    if (i == 0) continue;
-    DG lm = vlim[i], lp = vlim[(nv - 1) * Q + i];
-    DG o;
-    if (v == 0) o = lm * (u - a) + lp * (u + a) + u * sums[i];
-    else if (v == 1) o = lm * (H - u * a) + lp * (H + u * a) + sums[Q + i];
-    else o = (lm + lp) * (blk[v * Q] * irho) + vlim[(v - 1) * Q + i];
-    out[(size_t)v * VS + i] = (double)o;
-  }
+  (void)gmask;
 }
 
 // L2 projection of primitive values at the Gauss points (Sec. 3.1): one thread
@@ -756,45 +954,30 @@ cudaError_t upload_basis(const Basis *tables) {
   return cudaMemcpyToSymbol(c_basis_f, f, sizeof(BasisF) * ADG_MAX_P);
 }
 
-int stage_tile(int Q, int nv, int ns, int nr, int R, int O, bool mixed) {
-  // elements per tile: up to 256 Gauss-point threads, at most ~96 KB of tile
+int stage_tile(const Mech &M, int Q, int O, bool mixed) {
+  // elements per tile: up to 256 Gauss points, at most ~96 KB of tile
   int TE = 256 / Q;
-  while (TE > 2 && stage_smem_bytes(TE, Q, nv, ns, nr, R, O, mixed) > 96 * 1024) TE /= 2;
+  while (TE > 2 && stage_smem_bytes(TE, Q, M.ns, M.nr, M.nterm, O, mixed) > 96 * 1024) TE /= 2;
   return TE;
 }
 
-int stage_chunks(int TE, int Q, int nr) {
-  // chemistry chunks per Gauss point that best fill the CTA's threads
-  int TQ = TE * Q, nth = ((TQ + 31) / 32) * 32;
-  int best = 1;
-  double best_fill = 0.0;
-  for (int R = 1; R <= 8 && R <= (nr > 0 ? nr : 1); ++R) {
-    int items = TQ * R;
-    int rounds = (items + nth - 1) / nth;
-    double fill = (double)items / (rounds * nth);
-    if (fill > best_fill + 0.02) {
-      best_fill = fill;
-      best = R;
-    }
-  }
-  return best;
+int stage_threads(int TE, int Q, int nr) {
+  // enough threads for the (reaction, point) items of the chemistry in a few rounds
+  int items = TE * Q * (nr > 0 ? nr : 1);
+  int nt = ((items / 4 + 31) / 32) * 32;
+  return nt < 128 ? 128 : (nt > 512 ? 512 : nt);
 }
 
-size_t stage_smem(int TE, int Q, int nv, int ns, int nr, int R, int O, bool mixed) {
-  return stage_smem_bytes(TE, Q, nv, ns, nr, R, O, mixed);
-}
-
-cudaError_t upload_exp_table(const ExpTable *t) {
-  return cudaMemcpyToSymbol(c_exp, t, sizeof(ExpTable));
+size_t stage_smem(const Mech &M, int TE, int Q, int O, bool mixed) {
+  return stage_smem_bytes(TE, Q, M.ns, M.nr, M.nterm, O, mixed);
 }
 
 template <int Q, bool MIX>
 static cudaError_t launch_stage_qm(const Mech &M, const StageArgs &A, int n_tiles,
                                    cudaStream_t st) {
-  int nv = M.ns + 2;
-  size_t smem = stage_smem_bytes(A.TE, Q, nv, M.ns, M.nr, A.R, A.O, MIX);
-  int nth = ((A.TE * Q + 31) / 32) * 32;
-  stage_kernel<Q, MIX><<<n_tiles, nth, smem, st>>>(M, A);
+  size_t smem = stage_smem_bytes(A.TE, Q, M.ns, M.nr, M.nterm, A.O, MIX);
+  if (A.NT < 32 || A.NT > 512 || A.NT % 32) return cudaErrorInvalidValue;
+  stage_kernel<Q, MIX><<<n_tiles, A.NT, smem, st>>>(M, A);
   return cudaGetLastError();
 }
 
@@ -813,16 +996,20 @@ cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, bool mixed, i
   return cudaErrorInvalidValue;
 }
 
-int limiter_elems_per_block(int nv) { return LIM_WARPS * (nv <= 16 ? 2 : 1); }
+int limiter_elems_per_block(int nv) {
+  (void)nv;
+  return LIM_EPB;
+}
 
 template <int Q, int G, bool MIX>
 static cudaError_t launch_limiter_qgm(const Mech &M, const LimArgs &A, int nv, int n_blocks,
                                       cudaStream_t st) {
   constexpr int EPW = 32 / G;
-  size_t smem = (size_t)LIM_WARPS * EPW * limiter_elem_words(nv, M.ns, Q) *
+  size_t smem = ((size_t)SP_NFIELDS * M.ns + (size_t)2 * LIM_EPB * nv + (size_t)nv * (LIM_EPB + 2) * Q +
+                 (size_t)(LIM_THREADS / 32) * EPW * limiter_elem_words(nv, M.ns, Q)) *
                 (MIX ? sizeof(float) : sizeof(double));
   smem = (smem + 15) & ~(size_t)15;
-  limiter_kernel<Q, G, MIX><<<n_blocks, 32 * LIM_WARPS, smem, st>>>(M, A);
+  limiter_kernel<Q, G, MIX><<<n_blocks, LIM_THREADS, smem, st>>>(M, A);
   return cudaGetLastError();
 }
 

@@ -1,54 +1,177 @@
-// FP64 exponential for the Arrhenius and equilibrium factors of the chemistry.
+// FP64 exponential for the Arrhenius and equilibrium factors of the chemistry,
+// evaluated on the integer pipeline.
 //
 // Method: the table-driven reduction of P. T. P. Tang, "Table-driven
 // implementation of the exponential function in IEEE floating-point arithmetic",
 // ACM TOMS 15(2), 1989: x = (32 m + j) ln2/32 + r with |r| <= ln2/64, so
-// exp(x) = 2^m * 2^(j/32) * exp(r). Here 2^(j/32) comes from a 32-entry table
-// of doubles, exp(r) from its Taylor polynomial of degree 6 (truncation below
-// 4e-18 relative for |r| <= ln2/64), the rounding of x*32/ln2 to an integer from
-// the usual add-and-subtract of 1.5*2^52, and ln2/32 is split in two parts so
-// that N * hi is exact for |N| < 2^21. The scaling by 2^m adds m to the exponent
-// field. About 11 FP64 operations instead of the ~20 of a general exp; accuracy
-// within a few ulp (checked against CUDA's exp by the tests).
+// exp(x) = 2^m * 2^(j/32) * exp(r). Every step is carried out in 64-bit fixed
+// point instead of double arithmetic, because on this GPU a double instruction
+// occupies the FP64 unit for 16 cycles while integer multiply-adds issue at the
+// rate of single-precision ones:
+//   n = round(|x| 32/ln2) from the high half of |x| 2^53 * round(2^56 32/ln2),
+//   r 2^69 = |x| 2^69 - n (2^69 ln2/32), with |x| 2^69 the significand shifted
+//   left (modulo 2^64: the true value is below 2^62.5 in magnitude, so the low
+//   64 bits are exact) and 2^69 ln2/32 as a 64-bit integer plus a 32-bit
+//   fraction; exact for |x| >= 2^-17 and to 2^-70 below,
+//   exp(r) = 1 + r(1 + r(1/2 + r(1/6 + r(1/24 + r(1/120 + r/720))))) by Horner with
+//   64-bit high multiplies (coefficients and partial sums scaled by 2^62, r by
+//   2^64; the truncated Taylor term is below 2^-58 for |r| <= ln2/64),
+//   2^(j/32) exp(r) from the high half of the product with the table entry
+//   (scaled by 2^62), then rounded to a 53-bit significand with m added to the
+//   exponent. Negative x use n -> -n, r -> -r.
+// The error is about half a unit in the last place; the tests compare it with
+// the host's and with CUDA's exp.
 #pragma once
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 
 namespace adg {
 
-constexpr double EXP_SHIFTER = 6755399441055744.0;        // 1.5 * 2^52
-constexpr double EXP_INV_L = 46.16624130844682836;        // 32 / ln 2
-constexpr double EXP_MAX_ARG = 700.0;
+// 2^(j/32) * 2^62 and the constants below, rounded to the nearest integer from
+// 60-digit decimal evaluations of their definitions.
+#define ADG_IEXP_TABLE                                                              \
+  {0x4000000000000000ull, 0x4166c34c5615d0ecull, 0x42d561b3e6243d8aull,            \
+   0x444c0740496d4294ull, 0x45cae0f1f545eb73ull, 0x47521cc5a2e6a9e0ull,            \
+   0x48e1e9b9d588e19bull, 0x4a7a77d47f7b84b1ull, 0x4c1bf828c6dc54b8ull,            \
+   0x4dc69cdceaa72a9cull, 0x4f7a993048d088d7ull, 0x513821818624b40cull,            \
+   0x52ff6b54d8a89c75ull, 0x54d0ad5a753e077cull, 0x56ac1f752150a563ull,            \
+   0x5891fac0e95612c8ull, 0x5a827999fcef3242ull, 0x5c7dd7a3b17dcf75ull,            \
+   0x5e8451cfac061b5full, 0x6096266533384a2bull, 0x62b39508aa836d6full,            \
+   0x64dcdec3371793d1ull, 0x6712460a8fc24072ull, 0x69540ec8f895722dull,            \
+   0x6ba27e656b4eb57aull, 0x6dfddbcbed791babull, 0x70666f76154a7089ull,            \
+   0x72dc8373be41a454ull, 0x75606373ee921c97ull, 0x77f25ccdee6d7ae6ull,            \
+   0x7a92be8a92436616ull, 0x7d41d96db915019dull}
 
-// Table and the hi/lo split of ln2/32 (hi with 32 significant bits), computed on
-// the host in extended precision.
-struct ExpTable {
-  double t[32];     // 2^(j/32), rounded to double
-  double l_hi, l_lo;
+struct IExpTable {
+  unsigned long long t[32];
 };
 
-// exp(x) with the table in shared memory (tab). Falls back to the library exp
-// outside |x| <= 700, where the exponent-field scaling could leave the range.
-__device__ __forceinline__ double fexp(double x, const ExpTable &tab) {
-  // |x| <= 700 tested on the high word (0x4085E000 is that of 700.0), off the FP64 pipe;
-  // NaN and infinities take the library path too
-  if ((__double2hiint(x) & 0x7fffffff) > 0x4085E000) return exp(x);
-  double t = fma(x, EXP_INV_L, EXP_SHIFTER);
-  double nd = t - EXP_SHIFTER;
-  int n = (int)(__double2loint(t));          // the low mantissa bits hold N
-  double r = fma(-nd, tab.l_hi, x);
-  r = fma(-nd, tab.l_lo, r);
-  double p = 1.0 / 720.0;
-  p = fma(p, r, 1.0 / 120.0);
-  p = fma(p, r, 1.0 / 24.0);
-  p = fma(p, r, 1.0 / 6.0);
-  p = fma(p, r, 0.5);
-  p = fma(p, r, 1.0);
-  p = fma(p, r, 1.0);
-  int j = n & 31;
-  int m = n >> 5;                             // arithmetic shift: floor division
-  double v = tab.t[j] * p;
-  long long bits = __double_as_longlong(v) + ((long long)m << 52);
-  return __longlong_as_double(bits);
+constexpr unsigned long long IEXP_K = 3326628274461080623ull;   // 2^56 * 32/ln2
+constexpr unsigned long long IEXP_L = 12786308645202655660ull;  // 2^69 * ln2/32
+constexpr long long IEXP_LC = -907824232ll;  // (2^69 ln2/32 - IEXP_L) * 2^32
+constexpr long long IEXP_C0 = 4611686018427387904ll;            // 2^62 / k!
+constexpr long long IEXP_C2 = 2305843009213693952ll;
+constexpr long long IEXP_C3 = 768614336404564651ll;
+constexpr long long IEXP_C4 = 192153584101141163ll;
+constexpr long long IEXP_C5 = 38430716820228233ll;
+constexpr long long IEXP_C6 = 6405119470038039ll;
+
+__host__ __device__ __forceinline__ unsigned long long iexp_umulhi(unsigned long long a,
+                                                                   unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (unsigned long long)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+__host__ __device__ __forceinline__ long long iexp_smulhi(long long a, long long b) {
+#ifdef __CUDA_ARCH__
+  return __mul64hi(a, b);
+#else
+  return (long long)(((__int128)a * b) >> 64);
+#endif
+}
+
+__host__ __device__ __forceinline__ long long iexp_bits(double x) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(x);
+#else
+  long long b;
+  std::memcpy(&b, &x, 8);
+  return b;
+#endif
+}
+
+__host__ __device__ __forceinline__ double iexp_double(long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double(b);
+#else
+  double x;
+  std::memcpy(&x, &b, 8);
+  return x;
+#endif
+}
+
+__host__ __device__ __forceinline__ int iexp_clz(unsigned long long v) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)v);
+#else
+  return __builtin_clzll(v);
+#endif
+}
+
+// Fixed-point core: for |x| <= 700, exp(x) = V 2^(m-60) with 2^59.9 < V < 2^61.1.
+struct IExpParts {
+  unsigned long long V;
+  int m;
+};
+
+__host__ __device__ __forceinline__ IExpParts iexp_parts(long long bits, const IExpTable &tab) {
+  const int E = (int)((bits >> 52) & 0x7ff);
+  const unsigned long long mant = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = E - 1022;  // |x| 2^53 = mant 2^sh, sh <= 10
+  const unsigned long long X = sh >= 0 ? mant << sh : (sh > -60 ? mant >> -sh : 0ull);
+  const long long n = (long long)((iexp_umulhi(X, IEXP_K) + (1ull << 44)) >> 45);
+  const int t = E - 1006;  // |x| 2^69 = mant 2^t, t <= 26
+  const unsigned long long X69 =
+      t >= 0 ? mant << t : (t > -60 ? ((mant >> (-t - 1)) + 1) >> 1 : 0ull);
+  long long R = (long long)(X69 - (unsigned long long)n * IEXP_L) - ((n * IEXP_LC) >> 32);
+  long long nn = n;
+  if (bits < 0) {
+    R = -R;
+    nn = -nn;
+  }
+  const long long r = R >> 5;  // r 2^64
+  long long A = IEXP_C6;
+  A = IEXP_C5 + iexp_smulhi(r, A);
+  A = IEXP_C4 + iexp_smulhi(r, A);
+  A = IEXP_C3 + iexp_smulhi(r, A);
+  A = IEXP_C2 + iexp_smulhi(r, A);
+  A = IEXP_C0 + iexp_smulhi(r, A);
+  A = IEXP_C0 + iexp_smulhi(r, A);  // exp(r) 2^62
+  IExpParts o;
+  o.V = iexp_umulhi(tab.t[(int)(nn & 31)], (unsigned long long)A);  // 2^(j/32) exp(r) 2^60
+  o.m = (int)(nn >> 5);  // arithmetic shift: floor division
+  return o;
+}
+
+// exp(x) with the table in shared (or host) memory. Outside |x| <= 700 (and for
+// NaN and infinities) the library exp is returned.
+__host__ __device__ __forceinline__ double iexp(double x, const IExpTable &tab) {
+  const long long bits = iexp_bits(x);
+  // 0x4085E000 is the high word of 700.0
+  if ((int)((bits >> 32) & 0x7fffffff) > 0x4085E000) return exp(x);
+  const IExpParts p = iexp_parts(bits, tab);
+  const int s = 11 - iexp_clz(p.V);  // leading bit 59..61 -> s = 7..9
+  const unsigned long long mt = (p.V + (1ull << (s - 1))) >> s;  // 2^52 <= mt <= 2^53
+  const long long eb = (long long)(s - 8 + p.m + 1023) << 52;
+  return iexp_double(eb + (long long)(mt - (1ull << 52)));
+}
+
+__host__ __device__ __forceinline__ float iexp_float(int b) {
+#ifdef __CUDA_ARCH__
+  return __int_as_float(b);
+#else
+  float x;
+  std::memcpy(&x, &b, 4);
+  return x;
+#endif
+}
+
+// The same exponential of a double argument rounded once to float (results
+// below the smallest normal float flush to zero, above the largest give +inf).
+__host__ __device__ __forceinline__ float iexpf(double x, const IExpTable &tab) {
+  const long long bits = iexp_bits(x);
+  if ((int)((bits >> 32) & 0x7fffffff) > 0x4085E000) return (float)exp(x);
+  const IExpParts p = iexp_parts(bits, tab);
+  const int s = 40 - iexp_clz(p.V);  // leading bit 59..61 -> s = 36..38
+  const unsigned long long mt = (p.V + (1ull << (s - 1))) >> s;  // 2^23 <= mt <= 2^24
+  const int e = s - 37 + p.m + 127;  // biased exponent of mt 2^(s-60+m-23)
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return iexp_float(0x7f800000);
+  return iexp_float((e << 23) + (int)(mt - (1ull << 23)));
 }
 
 }  // namespace adg

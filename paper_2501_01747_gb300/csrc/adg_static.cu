@@ -87,6 +87,9 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
       ((c.bc_left == ADG_BC_PERIODIC) != (c.bc_right == ADG_BC_PERIODIC)) ||
       (c.precision != ADG_FP64 && c.precision != ADG_MIXED))
     return ADG_ERR_ARG;
+  if (!mech->W || !mech->cp || !mech->h_f || !mech->s0) return ADG_ERR_ARG;
+  if (nr > 0 && (!mech->nu_f || !mech->nu_r || !mech->A || !mech->b || !mech->Ea))
+    return ADG_ERR_ARG;
   for (int i = 0; i < ns; ++i)
     if (!(mech->W[i] > 0.0) || !(mech->cp[i] > RU)) return ADG_ERR_ARG;
   const int N = c.n_elem, Q = c.p + 1, nv = ns + 2;
@@ -94,10 +97,18 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   const int npf = c.n_pe <= 1 ? 0 : (periodic ? c.n_pe : c.n_pe - 1);
   const int depth = c.max_delay + c.at_order;
 
+  Mech M;
+  M.ns = ns;
+  M.nr = nr;
+  M.nterm = 0;
+  for (int k = 0; k < ns * nr; ++k) M.nterm += (mech->nu_r[k] != mech->nu_f[k]);
+
   // layout of the scratch; reject problems that do not fit
   Cursor cur{nullptr, 0};
   size_t o_sp = cur.take(sizeof(double) * SP_NFIELDS * ns);
   size_t o_rx = cur.take(sizeof(Rxn) * (nr > 0 ? nr : 1));
+  size_t o_sxo = cur.take(sizeof(int) * (ns + 1));
+  size_t o_sx = cur.take(sizeof(int) * (M.nterm > 0 ? M.nterm : 1));
   size_t o_err = cur.take(sizeof(int) * 4);
   size_t st = (size_t)nv * N * Q;
   size_t o_wa = cur.take(sizeof(double) * st);
@@ -111,10 +122,10 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   size_t o_pl = cur.take(sizeof(int) * N);
   size_t o_pr = cur.take(sizeof(int) * N);
   const bool mixed = c.precision == ADG_MIXED;
-  int TE = stage_tile(Q, nv, ns, nr, 8, c.at_order, mixed);
+  int TE = stage_tile(M, Q, c.at_order, mixed);
   int target = (N + 2 * 152 - 1) / (2 * 152);
   if (target < TE) TE = target < 4 ? 4 : target;
-  const int RC = stage_chunks(TE, Q, nr);
+  const int NT = stage_threads(TE, Q, nr);
   const int EPB = limiter_elems_per_block(nv);
   const int n_tiles = (N + TE - 1) / TE, n_blocks = (N + EPB - 1) / EPB;
   size_t o_inst = cur.take(sizeof(Inst));
@@ -126,49 +137,9 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   // host-side tables on the stack (no heap)
   double sp[SP_NFIELDS * ADG_MAX_SPECIES];
   Rxn rx[ADG_NOALLOC_MAX_REACTIONS > 0 ? ADG_NOALLOC_MAX_REACTIONS : 1];
-  for (int i = 0; i < ns; ++i) {
-    double W = mech->W[i], cp = mech->cp[i], hf = mech->h_f[i], s0 = mech->s0[i];
-    sp[SP_W * ns + i] = W;
-    sp[SP_INVW * ns + i] = 1.0 / W;
-    sp[SP_QW * ns + i] = (hf - cp * TREF) / W;
-    sp[SP_CVW * ns + i] = (cp - RU) / W;
-    sp[SP_RW * ns + i] = RU / W;
-    sp[SP_CPW * ns + i] = cp / W;
-    sp[SP_G0 * ns + i] = (hf - cp * TREF) / RU;
-    sp[SP_G1 * ns + i] = cp / RU * (1.0 + log(TREF)) - s0 / RU;
-    sp[SP_CPR * ns + i] = cp / RU;
-  }
-  for (int j = 0; j < nr; ++j) {
-    Rxn &R = rx[j];
-    memset(&R, 0, sizeof(Rxn));
-    if (!(mech->A[j] > 0.0)) return ADG_ERR_ARG;
-    R.lnA = log(mech->A[j]);
-    R.b = mech->b[j];
-    R.EaR = mech->Ea[j] / RU;
-    int a = 0, b = 0, x = 0, dnu = 0;
-    for (int i = 0; i < ns; ++i) {
-      int f = mech->nu_f[j * ns + i], r = mech->nu_r[j * ns + i];
-      if (f < 0 || r < 0 || f > 2 || r > 2) return ADG_ERR_ARG;
-      if (f > 0) {
-        if (a == SIDE) return ADG_ERR_ARG;
-        R.rs[a] = (uint8_t)i;
-        R.rn[a++] = (uint8_t)f;
-      }
-      if (r > 0) {
-        if (b == SIDE) return ADG_ERR_ARG;
-        R.ps[b] = (uint8_t)i;
-        R.pn[b++] = (uint8_t)r;
-      }
-      if (r != f) {
-        if (x == NET) return ADG_ERR_ARG;
-        R.xs[x] = (uint8_t)i;
-        R.xc[x++] = (double)(r - f);
-        dnu += r - f;
-      }
-    }
-    R.nx = (uint8_t)x;
-    R.dnu = (double)dnu;
-  }
+  int sx_off[ADG_MAX_SPECIES + 1];
+  int sx[ADG_NOALLOC_MAX_REACTIONS * NET];
+  if (pack_mechanism(mech, sp, rx, sx_off, sx) != M.nterm) return ADG_ERR_ARG;
 
   // once per device: the scratch address and the constant tables. This is the
   // only set-up; it runs on the first call on each device.
@@ -181,10 +152,8 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p) return ADG_ERR_CUDA;
       Basis tables[ADG_MAX_P];
-      ExpTable et;
-      make_tables(tables, &et);
-      if (upload_basis(tables) != cudaSuccess || upload_exp_table(&et) != cudaSuccess ||
-          prepare_kernels(nv, ns, nr) != cudaSuccess)
+      make_tables(tables);
+      if (upload_basis(tables) != cudaSuccess || prepare_kernels(nv, ns, nr) != cudaSuccess)
         return ADG_ERR_CUDA;
       g_ptr[dev] = (unsigned char *)p;
       g_ready[dev] = true;
@@ -193,11 +162,10 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   unsigned char *base = g_ptr[dev];
   cudaStream_t s = (cudaStream_t)stream;
 
-  Mech M;
-  M.ns = ns;
-  M.nr = nr;
   M.sp = (const double *)(base + o_sp);
   M.rx = (const Rxn *)(base + o_rx);
+  M.sx_off = (const int *)(base + o_sxo);
+  M.sx = (const int *)(base + o_sx);
   Inst I;
   memset(&I, 0, sizeof(I));
   I.n_elem = N;
@@ -254,6 +222,9 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   NA_CK(cudaMemcpyAsync(base + o_sp, sp, sizeof(double) * SP_NFIELDS * ns,
                         cudaMemcpyHostToDevice, s));
   if (nr > 0) NA_CK(cudaMemcpyAsync(base + o_rx, rx, sizeof(Rxn) * nr, cudaMemcpyHostToDevice, s));
+  NA_CK(cudaMemcpyAsync(base + o_sxo, sx_off, sizeof(int) * (ns + 1), cudaMemcpyHostToDevice, s));
+  if (M.nterm > 0)
+    NA_CK(cudaMemcpyAsync(base + o_sx, sx, sizeof(int) * M.nterm, cudaMemcpyHostToDevice, s));
   if (w_out_dev != w_in_dev)
     NA_CK(cudaMemcpyAsync(w_out_dev, w_in_dev, sizeof(double) * st, cudaMemcpyDeviceToDevice, s));
   NA_CK(cudaMemcpyAsync(base + o_inst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
@@ -268,7 +239,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
       A.tiles = (const int2 *)(base + o_tiles);
       A.s = stg;
       A.TE = TE;
-      A.R = RC;
+      A.NT = NT;
       A.O = c.at_order;
       NA_CK(launch_stage(M, A, Q, mixed, n_tiles, s));
       if (I.limiter != ADG_LIM_NONE) {

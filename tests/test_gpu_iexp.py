@@ -1,0 +1,24 @@
+"""The library's integer-pipeline FP64 exp on the GPU: bit for bit the same as
+the host build of the same function, and within 0.6 units in the last place of
+the exact value (expl in extended precision) over the argument range used;
+CUDA's own exp is measured beside it for reference."""
+import json
+import os
+import subprocess
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_integer_exp_on_gpu_matches_host_and_exact(tmp_path):
+    exe = str(tmp_path / "iexp_check")
+    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
+                           "-std=c++17", os.path.join(HERE, "cuda", "iexp_check.cu"), "-o", exe])
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout + out.stderr
+    rec = json.loads(out.stdout.strip().splitlines()[-1])
+    assert rec["host_mismatch"] == 0, rec
+    assert rec["max_ulp"] <= 0.6, rec

@@ -272,7 +272,8 @@ def test_graph_replay_and_timed_steps_agree():
 
 def test_autotune_keeps_the_trajectory():
     """The autotuner times candidate launch configurations of the stage kernel
-    and keeps the fastest; the result still matches the oracle."""
+    (elements per tile, threads per CTA) and keeps the fastest; a configuration
+    set by hand takes effect too; the result still matches the oracle."""
     wl = W()["ignition-9sp-4096x4"]
     wl = I.scaled(wl, 1024, 16)
     mech = wl.mechanism()
@@ -282,10 +283,16 @@ def test_autotune_keeps_the_trajectory():
     g.set_primitive(prim)
     g.step(8)
     tun = g.autotune()
-    assert tun and tun[0]["elements_per_tile"] >= 2 and tun[0]["chem_chunks"] >= 1
+    assert tun and tun[0]["elements_per_tile"] >= 2 and tun[0]["threads_per_cta"] >= 64
+    g.step(8)
+    tun = g.set_tuning(0, 3, 96)
+    assert tun[0]["elements_per_tile"] == 3 and tun[0]["threads_per_cta"] == 96
+    assert tun[0]["tiles"] == (wl.n_elem + 2) // 3
     g.step(8)
     g.check()
+    with pytest.raises(adg.AdgError):
+        g.set_tuning(0, 3, 100)
     o = O.Oracle(wl, mech)
     o.set_primitive(prim)
-    o.step(16)
+    o.step(24)
     assert_parity(g, o)

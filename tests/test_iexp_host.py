@@ -1,0 +1,28 @@
+"""The library's integer-pipeline FP64 exp (csrc/adg_math.cuh), compiled for the
+host, against expl in extended precision: within 0.6 units in the last place
+over the whole range |x| <= 700, the Arrhenius arguments, small and tiny
+arguments and the table nodes, and correctly rounded almost everywhere; its
+float variant (one rounding of the fixed-point value) within half a float ulp."""
+import json
+import os
+import shutil
+import subprocess
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_integer_exp_host_build_against_extended_precision(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    exe = str(tmp_path / "iexp_host")
+    subprocess.check_call([nvcc, "-O2", "-std=c++17",
+                           os.path.join(HERE, "cuda", "iexp_host_check.cu"), "-o", exe])
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout + out.stderr
+    rec = json.loads(out.stdout.strip().splitlines()[-1])
+    assert rec["max_ulp"] <= 0.6, rec
+    assert rec["correctly_rounded"] >= 0.99, rec
+    assert rec["float_max_ulp"] <= 0.51, rec
