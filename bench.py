@@ -40,42 +40,36 @@ L2_BYTES = 129 * 1024 * 1024
 # (4 flop) per clock per SM x 2.07 GHz = 1.259 TFLOP/s (a microbenchmark of
 # independent FMA chains measured 1.19 TFLOP/s at 1.99 GHz on this machine).
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-# FP64 elementary functions counted by the FP64-pipe time they take on this GPU:
-# a double exp runs at 29.5 G/s, i.e. the time of 40 flops at the FMA peak.
-FLOP_EXP = 40.0
-FLOP_LOG = 40.0
+ENSEMBLE = "ensemble-9sp-512"
 
 
-def stage_kernel_flops(wl, mech, mixed=False):
-    """Algorithmic flops of one stage-kernel launch, counted on the minimal
-    formulation of the method (FMA = 2, add/mul/div/sqrt = 1, exp/log = 40):
-    per Gauss point: modal->nodal 2 nv Q; thermo 10 ns + 12; ln T and 1/T 41;
-    per species concentration and g_i/(R T) 6; per reaction ln k_f 4, the Gibbs
-    sum 1 + 2 per species with nonzero net nu, k_f and k_r one exp each (80),
-    the mass-action products (sum of the coefficients), q 1, the accumulation 2
-    per net species; flux nv + 4. Per element: one face flux (2 thermo + 6 nv),
-    volume and source quadrature 7 nv Q^2, assembly 8 nv Q and the SSP-RK3
-    update 4 nv Q. Returns (FP64 flops, FP32 flops): in the mixed variant the
-    point flux, the face flux, the quadratures and the assembly are FP32."""
+def stage_kernel_flops(wl, mech):
+    """Algorithmic flops of one RK stage of one instance, the per-Gauss-point
+    count of the method: DG operator nv (4 (p+1) + 6) FMA (modal-to-nodal, flux,
+    volume and source quadrature, surface terms, update), thermodynamics 3 ns FMA,
+    chemistry 12 nr flops (Arrhenius and equilibrium arguments, mass action,
+    accumulation), with FMA = 2 flops. The 2 nr exponentials per point are
+    counted apart (returned second): they run on the integer pipeline."""
     ns, nr = mech.ns, mech.nr
     nv, Q = ns + 2, wl.p + 1
-    pt64 = 2 * nv * Q + (10 * ns + 12) + (FLOP_LOG + 1) + 6 * ns
-    for j in range(nr):
-        nx = int(np.count_nonzero(mech.nu_r[j].astype(int) - mech.nu_f[j].astype(int)))
-        prods = int(mech.nu_f[j].sum() + mech.nu_r[j].sum())
-        pt64 += 4 + (1 + 2 * nx) + 2 * FLOP_EXP + prods + 1 + 2 * nx
-    pt_dg = nv + 4
-    el_dg = 2 * (10 * ns + 12) + 6 * nv + 7 * nv * Q * Q + 8 * nv * Q
-    el64 = 4 * nv * Q
-    if mixed:
-        return wl.n_elem * (Q * pt64 + el64), wl.n_elem * (Q * pt_dg + el_dg)
-    return wl.n_elem * (Q * (pt64 + pt_dg) + el_dg + el64), 0.0
+    per_pt = 2 * nv * (4 * Q + 6) + 2 * 3 * ns + 12 * nr
+    pts = wl.n_elem * Q
+    return pts * per_pt, pts * 2 * nr
 
 
 def stage_kernel_bytes(wl, mech):
-    """Algorithmic DRAM bytes of one stage launch: read w^n and w^(s), write
-    w^(s+1), FP64, n_vars per vector DOF (24 n_vars bytes per DOF)."""
+    """Algorithmic DRAM bytes of one stage of one instance: read w^n and w^(s),
+    write w^(s+1), FP64, n_vars per vector DOF (24 n_vars bytes per DOF)."""
     return 24.0 * (mech.ns + 2) * wl.n_elem * (wl.p + 1)
+
+
+def bench_workloads(name):
+    """The instances of a bench workload and their shared mechanism."""
+    if name == ENSEMBLE:
+        wls = I.ensemble_workloads()
+        return wls, wls[0].mechanism()
+    wl = I.load_workloads()[name]
+    return [wl], wl.mechanism()
 
 
 def load_peaks():
@@ -148,10 +142,11 @@ def dist_setup():
     return ws, rank, local
 
 
-def cpu_baseline(wl, mech, budget_s=12.0, max_steps=40):
-    """The FP64 oracle (single-threaded C) on this host: the workload's first steps,
-    as many as fit in about budget_s seconds."""
+def cpu_baseline(wls, mech, budget_s=12.0, max_steps=40):
+    """The FP64 oracle (single-threaded C) on this host: the first steps of the
+    workload's first instance, as many as fit in about budget_s seconds."""
     import oracle as O
+    wl = wls[0]
     o = O.Oracle(wl, mech)
     o.set_primitive(wl.primitive(mech))
     t0 = time.perf_counter()
@@ -167,18 +162,21 @@ def cpu_baseline(wl, mech, budget_s=12.0, max_steps=40):
             "sample": "%s, first %d steps (%.1f s, 1 thread)" % (wl.name, n, dt)}
 
 
+def dof_stages_per_step(wls):
+    return sum(w.n_elem * (w.p + 1) * 3 for w in wls)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
-    wl = I.load_workloads()[args.workload]
-    mech = wl.mechanism()
-    cb = cpu_baseline(wl, mech, budget_s=max(5.0, 60.0 / max(1, args.steps + args.warmup)),
+    wls, mech = bench_workloads(args.workload)
+    cb = cpu_baseline(wls, mech, budget_s=max(5.0, 60.0 / max(1, args.steps + args.warmup)),
                       max_steps=max(1, args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"],
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * wl.n_elem * (wl.p + 1) * 3 / cb["value"],
+            "ms_per_step": 1e3 * dof_stages_per_step(wls) / cb["value"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(wl, mech, args),
+            "data": "synthetic", "config": workload_config(wls, mech, args),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -186,14 +184,22 @@ def run_reference(args, ws, rank):
     return 0
 
 
-def workload_config(wl, mech, args):
-    return {"workload": wl.name, "n_elem": wl.n_elem, "p": wl.p, "n_species": mech.ns,
-            "n_reactions": mech.nr, "n_pe": wl.n_pe, "max_delay": wl.max_delay,
-            "at_order": wl.at_order, "delay_mode": ["sync", "caa", "saa"][wl.delay_mode],
-            "flux": ["lf", "hllc"][wl.flux], "limiter": ["none", "weno"][wl.limiter],
-            "dt": wl.dt, "precision": args.precision,
-            "l2": "flushed between timed steps (256 MiB write)", "launch": "CUDA graph per step",
-            "parallelism": "replicas" if args.gpus > 1 else "single"}
+def workload_config(wls, mech, args):
+    common = {"n_species": mech.ns, "n_reactions": mech.nr, "precision": args.precision,
+              "l2": "flushed between timed steps (256 MiB write)",
+              "launch": "CUDA graph per step",
+              "parallelism": "replicas" if args.gpus > 1 else "single"}
+    if len(wls) > 1:
+        return dict(common, workload=args.workload, instances=len(wls),
+                    n_elem_total=sum(w.n_elem for w in wls),
+                    gauss_points=sum(w.n_elem * (w.p + 1) for w in wls),
+                    degrees=sorted(set(w.p for w in wls)), delay_mode="saa",
+                    max_delay=max(w.max_delay for w in wls), limiter="weno", flux="lf")
+    wl = wls[0]
+    return dict(common, workload=wl.name, n_elem=wl.n_elem, p=wl.p, n_pe=wl.n_pe,
+                max_delay=wl.max_delay, at_order=wl.at_order,
+                delay_mode=["sync", "caa", "saa"][wl.delay_mode],
+                flux=["lf", "hllc"][wl.flux], limiter=["none", "weno"][wl.limiter], dt=wl.dt)
 
 
 def mass_fractions(w, p):
@@ -203,11 +209,12 @@ def mass_fractions(w, p):
     return r / r.sum(axis=0, keepdims=True)
 
 
-def measure(adg, torch, wl, mech, prim, prec, args, dev, pg, ws):
-    """Warm-up, autotune, K device-timed steps and the end-to-end run of one
+def measure(adg, torch, wls, mech, prims, prec, args, dev, pg, ws, steps, autotune=True):
+    """Warm-up, autotune, device-timed steps and the end-to-end run of one
     precision variant on its own context."""
-    g = adg.ADG(mech, [wl], device=dev, precision=prec)
-    g.set_primitive(prim)
+    g = adg.ADG(mech, wls, device=dev, precision=prec)
+    for k, prim in enumerate(prims):
+        g.set_primitive(prim, k)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -218,7 +225,7 @@ def measure(adg, torch, wl, mech, prim, prec, args, dev, pg, ws):
         te, nt = (int(x) for x in args.tuning.split(","))
         tuning = g.set_tuning(0, te, nt)
     else:
-        tuning = g.autotune(stream) if not args.no_autotune else g.tuning()
+        tuning = g.autotune(stream) if autotune and not args.no_autotune else g.tuning()
     torch.cuda.synchronize(dev)
 
     # device-resident timing: every step is one replay of the step's CUDA graph
@@ -232,7 +239,7 @@ def measure(adg, torch, wl, mech, prim, prec, args, dev, pg, ws):
     time.sleep(0.3)
     g.enable_kernel_timing(True)
     wall0 = time.perf_counter()
-    for k in range(args.steps):
+    for k in range(steps):
         flush.zero_()
         g.step(1, stream)
     torch.cuda.synchronize(dev)
@@ -246,23 +253,28 @@ def measure(adg, torch, wl, mech, prim, prec, args, dev, pg, ws):
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
-    dof_stage = wl.n_elem * (wl.p + 1) * 3
-    value = dof_stage * args.steps * ws / (ms / 1e3)
+    dof_stage = dof_stages_per_step(wls)
+    value = dof_stage * steps * ws / (ms / 1e3)
 
     # end to end through the C ABI with host buffers: H2D state, step, D2H state
-    nbytes = g.nv * wl.n_elem * (wl.p + 1) * 8
-    host_in = torch.empty(nbytes // 8, dtype=torch.float64, pin_memory=True)
-    host_out = torch.empty(nbytes // 8, dtype=torch.float64, pin_memory=True)
-    g.read_state(host_in.numpy(), stream=stream)
+    host_in, host_out, nbytes = [], [], 0
+    for k, wl in enumerate(wls):
+        n = g.nv * wl.n_elem * (wl.p + 1)
+        host_in.append(torch.empty(n, dtype=torch.float64, pin_memory=True))
+        host_out.append(torch.empty(n, dtype=torch.float64, pin_memory=True))
+        g.read_state(host_in[-1].numpy(), k=k, stream=stream)
+        nbytes += 8 * n
     torch.cuda.synchronize(dev)
-    n_e2e = max(10, args.steps // 3)
+    n_e2e = max(3, steps // 3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     e0.record(stream)
-    for k in range(n_e2e):
-        g.write_state(host_in.numpy(), stream=stream)
+    for _ in range(n_e2e):
+        for k in range(len(wls)):
+            g.write_state(host_in[k].numpy(), k=k, stream=stream)
         g.step(1, stream)
-        g.read_state(host_out.numpy(), stream=stream)
+        for k in range(len(wls)):
+            g.read_state(host_out[k].numpy(), k=k, stream=stream)
         stream.synchronize()
     e1.record(stream)
     torch.cuda.synchronize(dev)
@@ -271,13 +283,13 @@ def measure(adg, torch, wl, mech, prim, prec, args, dev, pg, ws):
     e2e_value = dof_stage * n_e2e * ws / (e2e_ms / 1e3)
     g.close()
     del flush
-    return {"value": value, "ms": ms, "kms": kms, "kn": kn, "tuning": tuning,
+    return {"value": value, "ms": ms, "kms": kms, "kn": kn, "tuning": tuning, "steps": steps,
             "clocks": clocks, "wall": wall, "nbytes": nbytes,
             "e2e": {"value": e2e_value, "unit": "DOF-stage/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes}}
 
 
-def mixed_error(adg, torch, wl, mech, prim, dev, n_steps):
+def mixed_error(adg, torch, wls, mech, prims, dev, n_steps):
     """Error of the mixed path against the FP64 path (which matches the FP64
     oracle to 1e-10) after n_steps from the same state: the largest relative
     error of T at the Gauss points, and the error of every mass fraction at the
@@ -285,41 +297,60 @@ def mixed_error(adg, torch, wl, mech, prim, dev, n_steps):
     species (relative L-infinity) and, for information, to the local value."""
     out = {}
     for prec in ("fp64", "mixed"):
-        g = adg.ADG(mech, [wl], device=dev, precision=prec)
-        g.set_primitive(prim)
+        g = adg.ADG(mech, wls, device=dev, precision=prec)
+        for k, prim in enumerate(prims):
+            g.set_primitive(prim, k)
         g.step(n_steps)
         g.check()
-        out[prec] = (g.temperature(), mass_fractions(g.get_state(), wl.p))
+        out[prec] = [(g.temperature(k), mass_fractions(g.get_state(k), wl.p))
+                     for k, wl in enumerate(wls)]
         g.close()
-    (T0, Y0), (T1, Y1) = out["fp64"], out["mixed"]
-    eY, eP = 0.0, 0.0
-    for i in range(Y0.shape[0]):
-        big = Y0[i] > 1e-8
-        if big.any():
-            d = np.abs(Y1[i] - Y0[i])[big]
-            eY = max(eY, float(d.max() / Y0[i].max()))
-            eP = max(eP, float((d / Y0[i][big]).max()))
+    eT, eY, eP = 0.0, 0.0, 0.0
+    for (T0, Y0), (T1, Y1) in zip(out["fp64"], out["mixed"]):
+        eT = max(eT, float((np.abs(T1 - T0) / T0).max()))
+        for i in range(Y0.shape[0]):
+            big = Y0[i] > 1e-8
+            if big.any():
+                d = np.abs(Y1[i] - Y0[i])[big]
+                eY = max(eY, float(d.max() / Y0[i].max()))
+                eP = max(eP, float((d / Y0[i][big]).max()))
     return {"steps": n_steps, "reference": "FP64 GPU path (<= 1e-10 from the FP64 oracle)",
-            "T_rel_max": float((np.abs(T1 - T0) / T0).max()),
-            "Y_rel_linf": eY, "Y_rel_pointwise": eP,
+            "T_rel_max": eT, "Y_rel_linf": eY, "Y_rel_pointwise": eP,
             "bar": "1e-4: T at every Gauss point; Y_i relative to max Y_i where Y_i > 1e-8"}
 
 
-def roofline(wl, mech, r, mixed, peaks, src):
-    stage_ms = r["kms"][0] / max(1, r["kn"][0])
-    f64, f32 = stage_kernel_flops(wl, mech, mixed)
-    achieved = f64 / (stage_ms / 1e3) / 1e12
-    hbm = stage_kernel_bytes(wl, mech) / (stage_ms / 1e3) / 1e9
-    traffic = STAGE_TRAFFIC.get((wl.name, KERNEL_REV, "mixed" if mixed else "fp64"))
+def roofline(wls, mech, r, mixed, peaks, src):
+    """Roofline of the stage kernel (the dominant one): the algorithmic flops of
+    one RK stage of every instance over the stage kernels' time for one stage
+    (all degree groups), against the FP64 peak, the pipe that bounds it."""
+    stage_s = r["kms"][0] / 1e3 / (3 * r["steps"])
+    flops = sum(stage_kernel_flops(w, mech)[0] for w in wls)
+    n_exp = sum(stage_kernel_flops(w, mech)[1] for w in wls)
+    achieved = flops / stage_s / 1e12
+    hbm = sum(stage_kernel_bytes(w, mech) for w in wls) / stage_s / 1e9
+    traffic = STAGE_TRAFFIC.get((wls[0].name if len(wls) == 1 else ENSEMBLE, KERNEL_REV,
+                                 "mixed" if mixed else "fp64"))
     return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-            "kernel": "stage_kernel<%d,%s>" % (wl.p + 1, "mixed" if mixed else "fp64"),
-            "kernel_ms": stage_ms, "fp32_tflops": f32 / (stage_ms / 1e3) / 1e12,
+            "kernel": "stage_kernel (%s)" % ("mixed" if mixed else "fp64"),
+            "kernel_ms": stage_s * 1e3, "exp_per_s": n_exp / stage_s,
             "kernel_share": r["kms"][0] / max(1e-9, r["kms"][0] + r["kms"][1]),
+            "limiter_ms": r["kms"][1] / (3 * r["steps"]),
             "peak_source": "FP64 pipe: 152 SM x 4 flop/clk x 2.07 GHz (derived)",
             "hbm_achieved_gbs": hbm, "hbm_peak_gbs": peaks.get("hbm_gbs"),
-            "hbm_frac": hbm / peaks.get("hbm_gbs", 6800.0),
-            "hbm_peak_source": src}
+            "hbm_frac": hbm / peaks.get("hbm_gbs", 6800.0), "hbm_peak_source": src}
+
+
+def compare(adg, torch, wls, mech, prims, args, dev, pg, ws, steps, autotune=True,
+            err_steps=200):
+    """Both precision variants on the same workload, the headline one first."""
+    other_prec = "fp64" if args.precision == "mixed" else "mixed"
+    head = measure(adg, torch, wls, mech, prims, args.precision, args, dev, pg, ws, steps,
+                   autotune)
+    other = None if args.only else measure(adg, torch, wls, mech, prims, other_prec, args, dev,
+                                           pg, ws, steps, autotune)
+    err = None if args.only else mixed_error(adg, torch, wls, mech, prims, dev, err_steps)
+    return head, other, other_prec, err
 
 
 def main(argv=None):
@@ -328,7 +359,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    help="a base workload name or %s" % ENSEMBLE)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="the headline variant; the other one is timed beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -336,6 +368,9 @@ def main(argv=None):
     ap.add_argument("--tuning", default="", help="TE,NT: set the stage launch configuration "
                     "instead of autotuning it")
     ap.add_argument("--only", action="store_true", help="time the headline variant only")
+    ap.add_argument("--ensemble-steps", type=int, default=20,
+                    help="timed steps of the batched-ensemble measurement added to the line "
+                    "(0: none)")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -352,14 +387,20 @@ def main(argv=None):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
-    wl = I.load_workloads()[args.workload]
-    mech = wl.mechanism()
-    prim = wl.primitive(mech)
-    head = measure(adg, torch, wl, mech, prim, args.precision, args, dev, pg, ws)
-    other_prec = "fp64" if args.precision == "mixed" else "mixed"
-    other = None if args.only else measure(adg, torch, wl, mech, prim, other_prec, args, dev,
-                                           pg, ws)
-    err = mixed_error(adg, torch, wl, mech, prim, dev, 200) if not args.only else None
+    wls, mech = bench_workloads(args.workload)
+    prims = [w.primitive(mech) for w in wls]
+    err_steps = 200 if len(wls) == 1 else 20
+    head, other, other_prec, err = compare(adg, torch, wls, mech, prims, args, dev, pg, ws,
+                                           args.steps, err_steps=err_steps)
+    ens = None
+    if args.ensemble_steps > 0 and args.workload != ENSEMBLE and not args.only:
+        ewls, emech = bench_workloads(ENSEMBLE)
+        eprims = [w.primitive(emech) for w in ewls]
+        eargs = argparse.Namespace(**vars(args))
+        eargs.tuning = ""
+        ens = compare(adg, torch, ewls, emech, eprims, eargs, dev, pg, ws, args.ensemble_steps,
+                      err_steps=10)
+        ens = (ewls, emech) + ens
 
     if rank != 0:
         return 0
@@ -370,9 +411,9 @@ def main(argv=None):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if mixed else "f64",
-        "data": "synthetic", "config": dict(workload_config(wl, mech, args),
+        "data": "synthetic", "config": dict(workload_config(wls, mech, args),
                                             tuning=head["tuning"]),
-        "roofline": roofline(wl, mech, head, mixed, peaks, src),
+        "roofline": roofline(wls, mech, head, mixed, peaks, src),
         "clocks": head["clocks"],
         "e2e": head["e2e"],
         "gpu_launches": int(head["kn"][0] + head["kn"][1] + head["kn"][2]),
@@ -381,24 +422,42 @@ def main(argv=None):
     if other is not None:
         line[other_prec] = {
             "value": other["value"], "ms_per_step": other["ms"] / args.steps,
-            "e2e": other["e2e"], "roofline": roofline(wl, mech, other, not mixed, peaks, src),
+            "e2e": other["e2e"], "roofline": roofline(wls, mech, other, not mixed, peaks, src),
             "clocks": other["clocks"], "tuning": other["tuning"]}
         fp64_v = other["value"] if mixed else head["value"]
         mix_v = head["value"] if mixed else other["value"]
         line["speedup_mixed_vs_fp64"] = mix_v / fp64_v
     if err is not None:
         line["mixed_error"] = err
+    if ens is not None:
+        ewls, emech, eh, eo, eop, ee = ens
+        rec = {"config": dict(workload_config(ewls, emech, args), tuning=eh["tuning"]),
+               "steps": args.ensemble_steps, "value": eh["value"],
+               "ms_per_step": eh["ms"] / args.ensemble_steps, "e2e": eh["e2e"],
+               "roofline": roofline(ewls, emech, eh, mixed, peaks, src)}
+        if eo is not None:
+            rec[eop] = {"value": eo["value"], "ms_per_step": eo["ms"] / args.ensemble_steps,
+                        "roofline": roofline(ewls, emech, eo, not mixed, peaks, src),
+                        "tuning": eo["tuning"]}
+            rec["speedup_mixed_vs_fp64"] = (eh["value"] / eo["value"]) if mixed else (
+                eo["value"] / eh["value"])
+        if ee is not None:
+            rec["mixed_error"] = ee
+        line["ensemble"] = rec
     if not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_baseline(wl, mech)
+        line["cpu_baseline"] = cpu_baseline(wls, mech)
     print(json.dumps(line))
     return 0
 
 
 # DRAM bytes (read + write) per stage-kernel launch from ncu, per (workload,
 # kernel revision, precision); the summaries are under profiles/.
-STAGE_TRAFFIC = {}
+STAGE_TRAFFIC = {
+    ("ignition-9sp-4096x4", "v9", "mixed"): 2.029824e6,
+    ("ignition-9sp-4096x4", "v9", "fp64"): 2.053632e6,
+}
 
-KERNEL_REV = "v8"
+KERNEL_REV = "v9"
 
 if __name__ == "__main__":
     sys.exit(main())

@@ -865,10 +865,9 @@ int adg_autotune(adg_ctx *ctx, void *stream) {
         // (stage buffers, the ring slot of the current level), so the
         // trajectory is unchanged
         bool ok = true;
-        for (int w = 0; w < 2 && ok; ++w)
-          ok = launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
+        ok = launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
         ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
-        for (int w = 0; w < 5 && ok; ++w)
+        for (int w = 0; w < 2 && ok; ++w)
           ok = launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
         ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
         float ms = 0.0f;
