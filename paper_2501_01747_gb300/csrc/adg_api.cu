@@ -122,8 +122,9 @@ int adg::pack_mechanism(const adg_mechanism *m, double *sp, Rxn *rx, int *sx_off
     if (!(m->A[j] > 0.0)) return ADG_ERR_ARG;
     R.lnA = log(m->A[j]);
     R.b = m->b[j];
-    R.EaR = m->Ea[j] / RU;
+    R.mEaR = -m->Ea[j] / RU;
     int a = 0, b = 0, x = 0, dnu = 0;
+    double g0 = 0.0, g1 = 0.0, cpr = 0.0;
     for (int i = 0; i < ns; ++i) {
       int f = m->nu_f[j * ns + i], r = m->nu_r[j * ns + i];
       if (f < 0 || r < 0 || f > 2 || r > 2) return ADG_ERR_ARG;
@@ -138,14 +139,17 @@ int adg::pack_mechanism(const adg_mechanism *m, double *sp, Rxn *rx, int *sx_off
         R.pn[b++] = (uint8_t)r;
       }
       if (r != f) {
-        if (x == NET) return ADG_ERR_ARG;
-        R.xs[x] = (uint8_t)i;
-        R.xc[x++] = (double)(r - f);
+        if (++x > NET) return ADG_ERR_ARG;
+        const double nu = (double)(r - f);
         dnu += r - f;
+        g0 = fma(nu, sp[SP_G0 * ns + i], g0);
+        g1 = fma(nu, sp[SP_G1 * ns + i], g1);
+        cpr = fma(nu, sp[SP_CPR * ns + i], cpr);
       }
     }
-    R.nx = (uint8_t)x;
-    R.dnu = (double)dnu;
+    R.kr0 = R.lnA + (double)dnu * log(RU / PATM) + g1;
+    R.kr1 = R.b + (double)dnu - cpr;
+    R.kr2 = R.mEaR + g0;
   }
   int n = 0;
   for (int i = 0; i < ns; ++i) {

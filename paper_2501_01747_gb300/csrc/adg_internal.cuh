@@ -34,18 +34,20 @@ enum SpeciesField {
   SP_NFIELDS
 };
 
-// One reversible reaction, 128 bytes: ln k_f = lnA + b ln T - EaR / T and
-// ln k_r = ln k_f + sum_i nu_i g_i/(R T) + dnu ln(R T / P_atm).
+// One reversible reaction, 64 bytes. With g_i/(R T) = G0_i/T + G1_i - CPR_i ln T
+// (constant c_p), both rate constants are linear in (1, ln T, 1/T):
+//   ln k_f = lnA + b ln T - EaR / T,
+//   ln k_r = ln k_f + sum_i nu_i g_i/(R T) + dnu ln(R T / P_atm)
+//          = kr0 + kr1 ln T + kr2 / T,
+// kr0 = lnA + dnu ln(R/P_atm) + sum_i nu_i G1_i, kr1 = b + dnu - sum_i nu_i CPR_i,
+// kr2 = -EaR + sum_i nu_i G0_i (nu the net coefficients, dnu their sum).
 struct alignas(16) Rxn {
-  double lnA, b, EaR, dnu;
-  double xc[8];           // net coefficient nu_i of species xs[t]
-  uint8_t xs[8];          // species with nonzero net coefficient, ascending
+  double lnA, b, mEaR;    // ln k_f = lnA + b ln T + mEaR / T
+  double kr0, kr1, kr2;   // ln k_r = kr0 + kr1 ln T + kr2 / T
   uint8_t rs[4], rn[4];   // reactants: species, coefficient (rn = 0 ends)
   uint8_t ps[4], pn[4];   // products
-  uint8_t nx;             // number of entries of xs/xc
-  uint8_t pad[7];
 };
-static_assert(sizeof(Rxn) == 128, "reaction record is 128 bytes");
+static_assert(sizeof(Rxn) == 64, "reaction record is 64 bytes");
 
 // Species -> reaction incidence (the transpose of the net stoichiometry): the
 // terms of species i are sx[sx_off[i] .. sx_off[i+1]), each (j << 8) | (nu_ij & 0xff)

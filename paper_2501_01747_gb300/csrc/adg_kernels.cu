@@ -36,7 +36,7 @@ using dg_t = typename std::conditional<MIX, float, double>::type;
 
 // Shared-memory footprint (bytes) of a stage tile of TE elements with up to O AT
 // levels per face. FP64 region: species fields, exp table, basis values, modal
-// tile with halo, nodal state, g_i/(R T), ln T, 1/T, u, P. Region in the
+// tile with halo, nodal state, ln T, 1/T, u, P. Region in the
 // arithmetic type of the variant: face, level and trace fluxes, concentrations,
 // rates of progress, production rates; the mixed variant adds an FP32 copy of
 // the species fields and the point flux (the FP64 variant writes the flux over
@@ -45,7 +45,7 @@ __host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int ns, int nr
                                                    int O, bool mix) {
   const size_t nv = ns + 2, TQ = (size_t)TE * Q, F = TE + 1;
   const size_t nd = (size_t)SP_NFIELDS * ns + 32 + MAXQ * MAXQ + nv * (TE + 2) * Q + nv * TQ +
-                    (size_t)ns * TQ + 4 * TQ;
+                    4 * TQ;
   size_t ndg = F * nv + (size_t)O * F * nv + (size_t)O * F * 2 * nv + (size_t)ns * TQ +
                (size_t)nr * TQ + (size_t)ns * TQ;
   if (mix) ndg += (size_t)SP_NFIELDS * ns + nv * TQ;
@@ -87,8 +87,7 @@ __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
   double *sPq = reinterpret_cast<double *>(stab + 1);         // [q][j] P_j(x_q)
   double *sw = sPq + MAXQ * MAXQ;                             // [v][TE+2][Q]
   double *snw = sw + (size_t)nv * (TE + 2) * Q;               // [v][TQ] nodal state
-  double *sg = snw + (size_t)nv * TQ;                         // [i][TQ] g_i/(R T)
-  double *slnT = sg + (size_t)ns * TQ;                        // [TQ]
+  double *slnT = snw + (size_t)nv * TQ;                       // [TQ]
   double *sinvT = slnT + TQ;
   double *su = sinvT + TQ;
   double *sPr = su + TQ;
@@ -153,23 +152,37 @@ __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
     snw[(size_t)v * TQ + t] = acc;
   }
   __syncthreads();
-  // 2b. temperature from the internal energy (FP64), velocity and pressure
-  for (int t = tid; t < teq; t += nth) {
-    Thermo th = thermo_of(ssp, ns, snw + t, TQ);
-    if (!(th.rho > 0.0) || !(th.T > 0.0) || !isfinite(th.T) || !isfinite(snw[t]))
-      report_error(I, ADG_ERR_NONPHYSICAL, e0 + t / Q, A.s, nstep);
-    slnT[t] = log(th.T);
-    sinvT[t] = 1.0 / th.T;
-    su[t] = th.u;
-    sPr[t] = th.P;
+  // 2b. temperature from the internal energy (the closed form of the Newton step
+  // for constant c_p), ln T, 1/T, velocity and pressure, in FP64
+  {
+    const double *sQW = ssp + SP_QW * ns, *sCVW = ssp + SP_CVW * ns, *sRW = ssp + SP_RW * ns;
+    for (int t = tid; t < teq; t += nth) {
+      const double *wq = snw + t;
+      double rho = 0.0, qsum = 0.0, cv = 0.0, Rm = 0.0;
+      for (int i = 0; i < ns; ++i) {
+        const double r = wq[(size_t)(2 + i) * TQ];
+        rho += r;
+        qsum = fma(r, sQW[i], qsum);
+        cv = fma(r, sCVW[i], cv);
+        Rm = fma(r, sRW[i], Rm);
+      }
+      const double m = wq[0], u = m / rho;
+      const double num = wq[TQ] - 0.5 * m * u - qsum;
+      const double T = num / cv;
+      if (!(rho > 0.0) || !(T > 0.0) || !isfinite(T) || !isfinite(m))
+        report_error(I, ADG_ERR_NONPHYSICAL, e0 + t / Q, A.s, nstep);
+      slnT[t] = log(T);
+      sinvT[t] = cv / num;
+      su[t] = u;
+      sPr[t] = T * Rm;
+    }
   }
   __syncthreads();
-  // 2c. per (variable, point): the flux; for a species also its concentration
+  // 2c. per (variable, point): the flux, and for a species its concentration
   // (law of mass action on non-negative concentrations: clipped at zero by the
-  // sign bit) and g_i/(R T) (FP64)
+  // sign bit)
   {
     const double *sIW = ssp + SP_INVW * ns;
-    const double *sG0 = ssp + SP_G0 * ns, *sG1 = ssp + SP_G1 * ns, *sCR = ssp + SP_CPR * ns;
     for (int item = tid; item < nv * teq; item += nth) {
       int v = item / teq, t = item - v * teq;
       const size_t at = (size_t)v * TQ + t;
@@ -178,7 +191,6 @@ __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
         const int i = v - 2;
         const double r = (__double2hiint(w) < 0) ? 0.0 : w;
         scc[(size_t)i * TQ + t] = (DG)(r * sIW[i]);
-        sg[(size_t)i * TQ + t] = fma(-sCR[i], slnT[t], fma(sG0[i], sinvT[t], sG1[i]));
         if constexpr (MIX) sfx[at] = (DG)u * (DG)w;
         else snw[at] = u * w;
       } else if (v == 0) {
@@ -198,24 +210,21 @@ __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
   // between local elements f and f+1), one (level, face) per item: the plain
   // flux, or one delayed level of the AT flux (Eq. 7) with both sides at the
   // common level n-k-m
-  const double LN_R_PATM = log(RU / PATM);
   const int n_chem = nr * teq;
   for (int item = tid; item < n_chem + O * (te + 1); item += nth) {
     if (item < n_chem) {
       const int j = item / teq, t = item - j * teq;
       const Rxn &Rx = srx[j];
-      const double lnT = slnT[t];
-      const double lkf = fma(-Rx.EaR, sinvT[t], fma(Rx.b, lnT, Rx.lnA));
-      double dg = Rx.dnu * (lnT + LN_R_PATM);
-      const int nx = Rx.nx;
-      for (int k = 0; k < nx; ++k) dg = fma(Rx.xc[k], sg[(size_t)Rx.xs[k] * TQ + t], dg);
+      const double lnT = slnT[t], invT = sinvT[t];
+      const double lkf = fma(Rx.mEaR, invT, fma(Rx.b, lnT, Rx.lnA));
+      const double lkr = fma(Rx.kr2, invT, fma(Rx.kr1, lnT, Rx.kr0));
       DG fwd, rev;
       if constexpr (MIX) {
         fwd = iexpf(lkf, *stab);
-        rev = iexpf(lkf + dg, *stab);
+        rev = iexpf(lkr, *stab);
       } else {
         fwd = iexp(lkf, *stab);
-        rev = iexp(lkf + dg, *stab);
+        rev = iexp(lkr, *stab);
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
