@@ -29,14 +29,14 @@ namespace adg {
 __constant__ Basis c_basis[ADG_MAX_P];     // index p-1
 __constant__ BasisF c_basis_f[ADG_MAX_P];  // the same, rounded to float
 
-__constant__ IExpTable c_iexp = ADG_IEXP_TABLE;
+__constant__ IExpTable c_iexp = {ADG_IEXP_TABLE, ADG_IEXP_TABLE32};
 
 template <bool MIX>
 using dg_t = typename std::conditional<MIX, float, double>::type;
 
 // Shared-memory footprint (bytes) of a stage tile of TE elements with up to O AT
 // levels per face. FP64 region: species fields, exp table, basis values, modal
-// tile with halo, nodal state, ln T, 1/T, u, P. Region in the
+// tile with halo, w^n of the tile, nodal state, ln T, 1/T, u, P. Region in the
 // arithmetic type of the variant: face, level and trace fluxes, concentrations,
 // rates of progress, production rates; the mixed variant adds an FP32 copy of
 // the species fields and the point flux (the FP64 variant writes the flux over
@@ -44,8 +44,8 @@ using dg_t = typename std::conditional<MIX, float, double>::type;
 __host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int ns, int nr, int nterm,
                                                    int O, bool mix) {
   const size_t nv = ns + 2, TQ = (size_t)TE * Q, F = TE + 1;
-  const size_t nd = (size_t)SP_NFIELDS * ns + 32 + MAXQ * MAXQ + nv * (TE + 2) * Q + nv * TQ +
-                    4 * TQ;
+  const size_t nd = (size_t)SP_NFIELDS * ns + sizeof(IExpTable) / 8 + MAXQ * MAXQ +
+                    nv * (TE + 2) * Q + 2 * nv * TQ + 4 * TQ;
   size_t ndg = F * nv + (size_t)O * F * nv + (size_t)O * F * 2 * nv + (size_t)ns * TQ +
                (size_t)nr * TQ + (size_t)ns * TQ;
   if (mix) ndg += (size_t)SP_NFIELDS * ns + nv * TQ;
@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
   double *sinvT = slnT + TQ;
   double *su = sinvT + TQ;
   double *sPr = su + TQ;
-  DG *sfh = reinterpret_cast<DG *>(sPr + TQ);                 // [NF][nv]
+  double *swn = sPr + TQ;                                     // [v][TQ] modes of w^n
+  DG *sfh = reinterpret_cast<DG *>(swn + (size_t)nv * TQ);    // [NF][nv]
   DG *sflx = sfh + (size_t)NF * nv;                           // [O][NF][nv]
   DG *str = sflx + (size_t)O * NF * nv;                       // [O][NF][2][nv]
   DG *scc = str + (size_t)O * NF * 2 * nv;                    // [i][TQ] concentrations
@@ -123,20 +124,46 @@ __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
       ssp[k] = x;
       if constexpr (MIX) sspD[k] = (DG)x;
     }
-    for (int k = tid; k < 32; k += nth) stab->t[k] = c_iexp.t[k];
+    for (int k = tid; k < 32; k += nth) {
+      stab->t[k] = c_iexp.t[k];
+      stab->t32[k] = c_iexp.t32[k];
+    }
     for (int k = tid; k < Q * Q; k += nth) sPq[k] = B.P[k / Q][k % Q];
     for (int k = tid; k <= ns; k += nth) soff[k] = M.sx_off[k];
     for (int k = tid; k < M.nterm; k += nth) sterm[k] = M.sx[k];
   }
-  // 1. tile of modal coefficients with a one-element halo on each side
-  const int span = (te + 2) * Q;
-  for (int idx = tid; idx < nv * span; idx += nth) {
-    int v = idx / span, r = idx - v * span;
-    int le = r / Q, j = r - le * Q;
-    int e = e0 - 1 + le;
-    if (e < 0) e = periodic ? e + N : 0;
-    if (e >= N) e = periodic ? e - N : N - 1;
-    sw[((size_t)v * (TE + 2) + le) * Q + j] = A_win[((size_t)v * N + e) * Q + j];
+  // 1. tile of modal coefficients with a one-element halo on each side and, for
+  // stages 1 and 2, the tile's modes of w^n (batches of loads in flight)
+  {
+    constexpr int BATCH = 4;
+    const int span = (te + 2) * Q, n_tile = nv * span;
+    const int n_wn = (A.s == 0) ? 0 : nv * te * Q;
+    const int total = n_tile + n_wn;
+    for (int base = tid; base < total; base += BATCH * nth) {
+      double xs[BATCH];
+      double *dst[BATCH];
+#pragma unroll
+      for (int b = 0; b < BATCH; ++b) {
+        const int idx = base + b * nth;
+        dst[b] = nullptr;
+        if (idx < n_tile) {
+          const int v = idx / span, r = idx - v * span;
+          const int le = r / Q, j = r - le * Q;
+          int e = e0 - 1 + le;
+          if (e < 0) e = periodic ? e + N : 0;
+          if (e >= N) e = periodic ? e - N : N - 1;
+          xs[b] = A_win[((size_t)v * N + e) * Q + j];
+          dst[b] = sw + ((size_t)v * (TE + 2) + le) * Q + j;
+        } else if (idx < total) {
+          const int k = idx - n_tile, v = k / (te * Q), r = k - v * te * Q;
+          xs[b] = I.wn[((size_t)v * N + e0) * Q + r];
+          dst[b] = swn + (size_t)v * TQ + r;
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < BATCH; ++b)
+        if (dst[b]) *dst[b] = xs[b];
+    }
   }
   __syncthreads();
 
@@ -204,16 +231,16 @@ __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
   }
   __syncthreads();
 
-  // 3. chemistry, one (reaction, point) per item: the reversible rate of progress
-  // from the Arrhenius and the equilibrium exponentials (arguments in FP64);
-  // and, on the remaining items, the face fluxes of the tile (local face f
-  // between local elements f and f+1), one (level, face) per item: the plain
-  // flux, or one delayed level of the AT flux (Eq. 7) with both sides at the
-  // common level n-k-m
-  const int n_chem = nr * teq;
-  for (int item = tid; item < n_chem + O * (te + 1); item += nth) {
-    if (item < n_chem) {
-      const int j = item / teq, t = item - j * teq;
+  // 3. the face fluxes of the tile (local face f between local elements f and
+  // f+1), one (level, face) per item: the plain flux, or one delayed level of
+  // the AT flux (Eq. 7) with both sides at the common level n-k-m; then the
+  // chemistry, one (reaction, point) per item: the reversible rate of progress
+  // from the Arrhenius and the equilibrium exponentials (arguments in FP64).
+  // The face items, the longest, come first so that they overlap the chemistry.
+  const int n_face = O * (te + 1);
+  for (int item = tid; item < n_face + nr * teq; item += nth) {
+    if (item >= n_face) {
+      const int j = (item - n_face) / teq, t = (item - n_face) - j * teq;
       const Rxn &Rx = srx[j];
       const double lnT = slnT[t], invT = sinvT[t];
       const double lkf = fma(Rx.mEaR, invT, fma(Rx.b, lnT, Rx.lnA));
@@ -243,8 +270,7 @@ __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
       sq[(size_t)j * TQ + t] = fwd - rev;
       continue;
     }
-    const int job = item - n_chem;
-    const int m = job / (te + 1), f = job - m * (te + 1);
+    const int m = item / (te + 1), f = item - m * (te + 1);
     const int g = e0 + f;  // global face index
     const int pf = (g < N) ? I.pf_of_left[g] : I.pf_of_right[N - 1];
     const int k = (pf >= 0) ? effective_delay(I, nstep, pf) : 0;
@@ -349,9 +375,13 @@ __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
       double r = (double)fma((DG)((2.0 * i + 1.0) * inv_dx), surf, Wv * S);
       size_t gi = ((size_t)v * N + ge) * Q + i;
       double o;
-      if (A.s == 0) o = fma(I.dt, r, I.wn[gi]);
-      else if (A.s == 1) o = fma(0.25, fma(I.dt, r, wi[i]), 0.75 * I.wn[gi]);
-      else o = fma(2.0 / 3.0, fma(I.dt, r, wi[i]), (1.0 / 3.0) * I.wn[gi]);
+      if (A.s == 0) {
+        o = fma(I.dt, r, wi[i]);  // the stage input is w^n
+      } else {
+        const double wn = swn[(size_t)v * TQ + e * Q + i];
+        if (A.s == 1) o = fma(0.25, fma(I.dt, r, wi[i]), 0.75 * wn);
+        else o = fma(2.0 / 3.0, fma(I.dt, r, wi[i]), (1.0 / 3.0) * wn);
+      }
       out[i] = o;
       I.wpre[gi] = o;
       A_wnext[gi] = o;

@@ -43,8 +43,18 @@ namespace adg {
    0x72dc8373be41a454ull, 0x75606373ee921c97ull, 0x77f25ccdee6d7ae6ull,            \
    0x7a92be8a92436616ull, 0x7d41d96db915019dull}
 
+// 2^(j/32) * 2^31, rounded to the nearest integer (the float-result variant).
+#define ADG_IEXP_TABLE32                                                            \
+  {0x80000000u, 0x82cd8699u, 0x85aac368u, 0x88980e81u, 0x8b95c1e4u, 0x8ea4398bu,   \
+   0x91c3d374u, 0x94f4efa9u, 0x9837f052u, 0x9b8d39bau, 0x9ef53261u, 0xa2704303u,   \
+   0xa5fed6aau, 0xa9a15ab5u, 0xad583eeau, 0xb123f582u, 0xb504f334u, 0xb8fbaf47u,   \
+   0xbd08a39fu, 0xc12c4ccau, 0xc5672a11u, 0xc9b9bd86u, 0xce248c15u, 0xd2a81d92u,   \
+   0xd744fccbu, 0xdbfbb798u, 0xe0ccdeecu, 0xe5b906e7u, 0xeac0c6e8u, 0xefe4b99cu,   \
+   0xf5257d15u, 0xfa83b2dbu}
+
 struct IExpTable {
   unsigned long long t[32];
+  unsigned int t32[32];
 };
 
 constexpr unsigned long long IEXP_K = 3326628274461080623ull;   // 2^56 * 32/ln2
@@ -56,6 +66,10 @@ constexpr long long IEXP_C3 = 768614336404564651ll;
 constexpr long long IEXP_C4 = 192153584101141163ll;
 constexpr long long IEXP_C5 = 38430716820228233ll;
 constexpr long long IEXP_C6 = 6405119470038039ll;
+constexpr int IEXPF_C0 = 1073741824;  // 2^30 / k!
+constexpr int IEXPF_C2 = 536870912;
+constexpr int IEXPF_C3 = 178956971;
+constexpr int IEXPF_C4 = 44739243;
 
 __host__ __device__ __forceinline__ unsigned long long iexp_umulhi(unsigned long long a,
                                                                    unsigned long long b) {
@@ -102,13 +116,37 @@ __host__ __device__ __forceinline__ int iexp_clz(unsigned long long v) {
 #endif
 }
 
-// Fixed-point core: for |x| <= 700, exp(x) = V 2^(m-60) with 2^59.9 < V < 2^61.1.
-struct IExpParts {
-  unsigned long long V;
-  int m;
+__host__ __device__ __forceinline__ int iexp_mulhi32(int a, int b) {
+#ifdef __CUDA_ARCH__
+  return __mulhi(a, b);
+#else
+  return (int)(((long long)a * b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ unsigned int iexp_umulhi32(unsigned int a, unsigned int b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (unsigned int)(((unsigned long long)a * b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ int iexp_clz32(unsigned int v) {
+#ifdef __CUDA_ARCH__
+  return __clz((int)v);
+#else
+  return __builtin_clz(v);
+#endif
+}
+
+// Argument reduction, exact in 64-bit fixed point: for |x| <= 700,
+// x = n ln2/32 + r with r 2^69 = R, |r| <= ln2/64.
+struct IExpRed {
+  long long R, n;
 };
 
-__host__ __device__ __forceinline__ IExpParts iexp_parts(long long bits, const IExpTable &tab) {
+__host__ __device__ __forceinline__ IExpRed iexp_reduce(long long bits) {
   const int E = (int)((bits >> 52) & 0x7ff);
   const unsigned long long mant = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
   const int sh = E - 1022;  // |x| 2^53 = mant 2^sh, sh <= 10
@@ -117,13 +155,25 @@ __host__ __device__ __forceinline__ IExpParts iexp_parts(long long bits, const I
   const int t = E - 1006;  // |x| 2^69 = mant 2^t, t <= 26
   const unsigned long long X69 =
       t >= 0 ? mant << t : (t > -60 ? ((mant >> (-t - 1)) + 1) >> 1 : 0ull);
-  long long R = (long long)(X69 - (unsigned long long)n * IEXP_L) - ((n * IEXP_LC) >> 32);
-  long long nn = n;
+  IExpRed o;
+  o.R = (long long)(X69 - (unsigned long long)n * IEXP_L) - ((n * IEXP_LC) >> 32);
+  o.n = n;
   if (bits < 0) {
-    R = -R;
-    nn = -nn;
+    o.R = -o.R;
+    o.n = -o.n;
   }
-  const long long r = R >> 5;  // r 2^64
+  return o;
+}
+
+// Fixed-point core: for |x| <= 700, exp(x) = V 2^(m-60) with 2^59.9 < V < 2^61.1.
+struct IExpParts {
+  unsigned long long V;
+  int m;
+};
+
+__host__ __device__ __forceinline__ IExpParts iexp_parts(long long bits, const IExpTable &tab) {
+  const IExpRed red = iexp_reduce(bits);
+  const long long r = red.R >> 5;  // r 2^64
   long long A = IEXP_C6;
   A = IEXP_C5 + iexp_smulhi(r, A);
   A = IEXP_C4 + iexp_smulhi(r, A);
@@ -132,8 +182,8 @@ __host__ __device__ __forceinline__ IExpParts iexp_parts(long long bits, const I
   A = IEXP_C0 + iexp_smulhi(r, A);
   A = IEXP_C0 + iexp_smulhi(r, A);  // exp(r) 2^62
   IExpParts o;
-  o.V = iexp_umulhi(tab.t[(int)(nn & 31)], (unsigned long long)A);  // 2^(j/32) exp(r) 2^60
-  o.m = (int)(nn >> 5);  // arithmetic shift: floor division
+  o.V = iexp_umulhi(tab.t[(int)(red.n & 31)], (unsigned long long)A);  // 2^(j/32) exp(r) 2^60
+  o.m = (int)(red.n >> 5);  // arithmetic shift: floor division
   return o;
 }
 
@@ -160,18 +210,30 @@ __host__ __device__ __forceinline__ float iexp_float(int b) {
 #endif
 }
 
-// The same exponential of a double argument rounded once to float (results
-// below the smallest normal float flush to zero, above the largest give +inf).
+// The exponential of a double argument rounded once to float (results below the
+// smallest normal float flush to zero, above the largest give +inf). The
+// reduction is the exact 64-bit one above; a float needs only 24 bits of exp(r)
+// and 2^(j/32), so those run in 32-bit fixed point: degree-4 Taylor Horner with
+// r scaled by 2^32 and the partial sums by 2^30 (truncation r^5/120 < 2^-39),
+// the table scaled by 2^31. The value before the rounding is good to ~2^-29.
 __host__ __device__ __forceinline__ float iexpf(double x, const IExpTable &tab) {
   const long long bits = iexp_bits(x);
   if ((int)((bits >> 32) & 0x7fffffff) > 0x4085E000) return (float)exp(x);
-  const IExpParts p = iexp_parts(bits, tab);
-  const int s = 40 - iexp_clz(p.V);  // leading bit 59..61 -> s = 36..38
-  const unsigned long long mt = (p.V + (1ull << (s - 1))) >> s;  // 2^23 <= mt <= 2^24
-  const int e = s - 37 + p.m + 127;  // biased exponent of mt 2^(s-60+m-23)
+  const IExpRed red = iexp_reduce(bits);
+  const int r = (int)(red.R >> 37);  // r 2^32, |r| < 2^26
+  int A = IEXPF_C4;
+  A = IEXPF_C3 + iexp_mulhi32(r, A);
+  A = IEXPF_C2 + iexp_mulhi32(r, A);
+  A = IEXPF_C0 + iexp_mulhi32(r, A);
+  A = IEXPF_C0 + iexp_mulhi32(r, A);  // exp(r) 2^30
+  const unsigned int V = iexp_umulhi32(tab.t32[(int)(red.n & 31)], (unsigned int)A);  // 2^29 scale
+  const int m = (int)(red.n >> 5);
+  const int s = 8 - iexp_clz32(V);  // leading bit 28..30 -> s = 5..7
+  const unsigned int mt = (V + (1u << (s - 1))) >> s;  // 2^23 <= mt <= 2^24
+  const int e = s - 6 + m + 127;  // biased exponent of mt 2^(s-29+m-23)
   if (e <= 0) return 0.0f;
   if (e >= 255) return iexp_float(0x7f800000);
-  return iexp_float((e << 23) + (int)(mt - (1ull << 23)));
+  return iexp_float((e << 23) + (int)(mt - (1u << 23)));
 }
 
 }  // namespace adg

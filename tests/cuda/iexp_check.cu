@@ -34,7 +34,7 @@ int main() {
     else if (i % 5 == 3) x[i] = ldexp(u - 0.5, -(i % 60));  // tiny arguments
     else x[i] = (double)((i / 5) % 2000 - 1000) * (0.6931471805599453 / 32.0);  // table nodes
   }
-  const adg::IExpTable tab = {ADG_IEXP_TABLE};
+  const adg::IExpTable tab = {ADG_IEXP_TABLE, ADG_IEXP_TABLE32};
   double *dx, *dm, *dr;
   if (cudaMalloc(&dx, n * 8) || cudaMalloc(&dm, n * 8) || cudaMalloc(&dr, n * 8)) return 2;
   cudaMemcpy(dx, x.data(), n * 8, cudaMemcpyHostToDevice);

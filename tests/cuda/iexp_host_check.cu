@@ -9,7 +9,7 @@
 #include "../../paper_2501_01747_gb300/csrc/adg_math.cuh"
 
 int main() {
-  const adg::IExpTable tab = {ADG_IEXP_TABLE};
+  const adg::IExpTable tab = {ADG_IEXP_TABLE, ADG_IEXP_TABLE32};
   const int n = 1 << 22;
   srand(2501);
   double max_ulp = 0.0, worst = 0.0, max_ulp_f = 0.0;

@@ -2,7 +2,8 @@
 host, against expl in extended precision: within 0.6 units in the last place
 over the whole range |x| <= 700, the Arrhenius arguments, small and tiny
 arguments and the table nodes, and correctly rounded almost everywhere; its
-float variant (one rounding of the fixed-point value) within half a float ulp."""
+float variant (exact reduction, 32-bit polynomial good to ~2^-29, one rounding)
+within 0.53 float ulp."""
 import json
 import os
 import shutil
@@ -25,4 +26,4 @@ def test_integer_exp_host_build_against_extended_precision(tmp_path):
     rec = json.loads(out.stdout.strip().splitlines()[-1])
     assert rec["max_ulp"] <= 0.6, rec
     assert rec["correctly_rounded"] >= 0.99, rec
-    assert rec["float_max_ulp"] <= 0.51, rec
+    assert rec["float_max_ulp"] <= 0.53, rec
