@@ -197,6 +197,7 @@ struct Group {
   bool mixed = false;
   int TE = 0;                   // elements per stage tile
   int NT = 128;                 // threads per stage CTA
+  int EPB = 32;                 // elements per limiter CTA
   int O = 1;                    // largest AT order of the group
   int n_tiles = 0, n_blocks = 0;
   int2 *d_tiles = nullptr;      // (instance, first element) per stage CTA
@@ -308,7 +309,6 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
   ctx->d_steps = (int64_t *)cv.take(sizeof(int64_t) * ctx->n_inst);
   // groups of equal degree and precision: tile sizes and tables
   ctx->n_groups = 0;
-  const int epb = limiter_elems_per_block(nv);
   for (int gk = 0; gk < ADG_MAX_GROUPS; ++gk) {
     const int Q = 2 + gk / 2, prec = gk % 2;
     auto member = [&](int k) { return cfgs[k].p + 1 == Q && cfgs[k].precision == prec; };
@@ -332,6 +332,8 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
     int64_t target = (total + 2 * 152 - 1) / (2 * 152);
     if (target < G.TE) G.TE = target < 4 ? 4 : (int)target;
     G.NT = stage_threads(G.TE, Q, nr);
+    G.EPB = limiter_elems_per_block(total, G.mixed);
+    const int epb = G.EPB;
     int64_t max_tiles = 0;
     for (int k = 0; k < ctx->n_inst; ++k)
       if (member(k)) {
@@ -587,9 +589,9 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
     if (cudaMemcpy(ctx->d_insts, hi.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice) ||
         cudaMemset(ctx->d_steps, 0, sizeof(int64_t) * n))
       rc2 = ADG_ERR_CUDA;
-    const int epb = limiter_elems_per_block(nv);
     for (int gi = 0; gi < ctx->n_groups && rc2 == ADG_OK; ++gi) {
       Group &G = ctx->groups[gi];
+      const int epb = G.EPB;
       std::vector<int2> bl;
       for (int k = 0; k < n; ++k) {
         if (cfgs[k].p + 1 != G.Q || (cfgs[k].precision == ADG_MIXED) != G.mixed) continue;
@@ -738,6 +740,7 @@ static int enqueue_step(adg_ctx *ctx, cudaStream_t st) {
       L.insts = ctx->d_insts;
       L.blocks = G.d_blocks;
       L.s = s;
+      L.EPB = G.EPB;
       CK(timed_begin(ctx, 1, st));
       CK(launch_limiter(ctx->mech, L, G.Q, G.mixed, ctx->ns + 2, G.n_blocks, st));
       CK(timed_end(ctx, st));

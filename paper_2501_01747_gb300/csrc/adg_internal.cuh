@@ -264,6 +264,7 @@ struct LimArgs {
   const Inst *insts;
   const int2 *blocks;
   int s;
+  int EPB;    // elements per CTA (limiter_elems_per_block)
 };
 
 void make_tables(Basis *tables);
@@ -277,7 +278,7 @@ cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, bool mixed, i
 cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, bool mixed, int nv,
                            int n_blocks, cudaStream_t st);
 cudaError_t launch_advance(int64_t *steps, int n, cudaStream_t st);
-int limiter_elems_per_block(int nv);
+int limiter_elems_per_block(int64_t n_elem_group, bool mixed);
 cudaError_t launch_project(const Mech &M, const Inst &I, const double *prim, double *w,
                            cudaStream_t st);
 cudaError_t launch_temperature(const Mech &M, const Inst &I, const double *w, double *T,

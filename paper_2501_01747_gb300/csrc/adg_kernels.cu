@@ -47,7 +47,7 @@ __host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int ns, int nr
   const size_t nd = (size_t)SP_NFIELDS * ns + sizeof(IExpTable) / 8 + MAXQ * MAXQ +
                     nv * (TE + 2) * Q + 2 * nv * TQ + 4 * TQ;
   size_t ndg = F * nv + (size_t)O * F * nv + (size_t)O * F * 2 * nv + (size_t)ns * TQ +
-               (size_t)nr * TQ + (size_t)ns * TQ;
+               (size_t)nr * TQ + (size_t)ns * TQ + nterm;
   if (mix) ndg += (size_t)SP_NFIELDS * ns + nv * TQ;
   const size_t ni = F + ns + 1 + nterm;
   return (size_t)nr * sizeof(Rxn) + nd * 8 + ndg * (mix ? 4 : 8) + ni * 4 + 16;
@@ -98,19 +98,20 @@ __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
   DG *scc = str + (size_t)O * NF * 2 * nv;                    // [i][TQ] concentrations
   DG *sq = scc + (size_t)ns * TQ;                             // [j][TQ] rates of progress
   DG *swd = sq + (size_t)nr * TQ;                             // [i][TQ] production rates
+  DG *scoef = swd + (size_t)ns * TQ;                          // [nterm] incidence coefficients
   DG *sspD, *sfx;                                             // species fields, point flux
   int *sk;
   if constexpr (MIX) {
-    sspD = swd + (size_t)ns * TQ;
+    sspD = scoef + M.nterm;
     sfx = sspD + (size_t)SP_NFIELDS * ns;
     sk = reinterpret_cast<int *>(sfx + (size_t)nv * TQ);
   } else {
     sspD = reinterpret_cast<DG *>(ssp);
     sfx = reinterpret_cast<DG *>(snw);
-    sk = reinterpret_cast<int *>(swd + (size_t)ns * TQ);
+    sk = reinterpret_cast<int *>(scoef + M.nterm);
   }
   int *soff = sk + NF;        // [ns + 1]
-  int *sterm = soff + ns + 1;  // [nterm]
+  int *sterm = soff + ns + 1;  // [nterm] reaction of each incidence term
   const int tid = threadIdx.x, nth = blockDim.x;
 
   // 0. mechanism, species fields, incidence, exp table and basis values into
@@ -130,7 +131,11 @@ __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
     }
     for (int k = tid; k < Q * Q; k += nth) sPq[k] = B.P[k / Q][k % Q];
     for (int k = tid; k <= ns; k += nth) soff[k] = M.sx_off[k];
-    for (int k = tid; k < M.nterm; k += nth) sterm[k] = M.sx[k];
+    for (int k = tid; k < M.nterm; k += nth) {
+      const int term = M.sx[k];
+      sterm[k] = term >> 8;
+      scoef[k] = (DG)(signed char)(term & 0xff);
+    }
   }
   // 1. tile of modal coefficients with a one-element halo on each side and, for
   // stages 1 and 2, the tile's modes of w^n (batches of loads in flight)
@@ -319,10 +324,8 @@ __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
   for (int item = tid; item < ns * teq; item += nth) {
     const int i = item / teq, t = item - i * teq;
     DG acc = DG(0);
-    for (int k = soff[i]; k < soff[i + 1]; ++k) {
-      const int term = sterm[k];
-      acc = fma((DG)(signed char)(term & 0xff), sq[(size_t)(term >> 8) * TQ + t], acc);
-    }
+    for (int k = soff[i]; k < soff[i + 1]; ++k)
+      acc = fma(scoef[k], sq[(size_t)sterm[k] * TQ + t], acc);
     swd[(size_t)i * TQ + t] = acc;
   }
   // 5. the AT sum over levels, m = 0..o-1 in order, in FP64
@@ -419,10 +422,12 @@ __device__ inline R minmod3(R a, R b, R c) {
   return R(0);
 }
 
-// Elements per limiter CTA and threads per CTA (LIM_L = 4 lanes per element in
-// the indicator; all threads stage the tile and run the WENO phase).
-constexpr int LIM_EPB = 32;
+// Threads per limiter CTA. A CTA limits EPB = 32 elements (4 lanes per element
+// in the indicator) or, for small mixed-precision groups, EPB = 16 (8 lanes), so
+// that small meshes still spread over every SM; all threads stage the tile and
+// run the WENO phase.
 constexpr int LIM_THREADS = 128;
+constexpr int LIM_EPB_MAX = 32;
 
 // Shared memory (words of the arithmetic type) per troubled element in the WENO
 // phase: the element and its two neighbours, the limited characteristic modes,
@@ -474,9 +479,6 @@ __device__ inline double neighbour_mode(const Inst &I, const double *wpre, int s
   return x;
 }
 
-// Lanes per element in the indicator.
-constexpr int LIM_L = 4;
-static_assert(LIM_THREADS == LIM_EPB * LIM_L, "one group of LIM_L lanes per element");
 
 // Troubled-cell indicator of element e (Sec. 3.3), a group of L lanes, in the
 // arithmetic type R. In each characteristic field of L(wbar_e) the face
@@ -625,15 +627,16 @@ __device__ bool troubled_cell(const Mech &M, const Inst &I, int s, int64_t nstep
 // v = A gradP.w + B (rho u)_w + C (sum rho Y)_w + D (rho Y_k)_w,
 // with (A, B, C, D) = (1/2a^2, -/+ a/2a^2, +/- a u/2a^2, 0) for the acoustic fields
 // and (-Y_k/a^2, 0, 0, 1) for species k.
-template <int Q, int G, bool MIX>
+template <int Q, int G, bool MIX, int EPB>
 __global__ void __launch_bounds__(LIM_THREADS) limiter_kernel(Mech M, LimArgs A) {
+  constexpr int LIM_L = LIM_THREADS / EPB;  // lanes per element in the indicator
   using DG = dg_t<MIX>;
   extern __shared__ __align__(16) double lsm_raw[];
   DG *lsm = reinterpret_cast<DG *>(lsm_raw);
   __shared__ Inst sI;
-  __shared__ int s_list[LIM_EPB];
+  __shared__ int s_list[EPB];
   __shared__ int s_n;
-  __shared__ Neighbour s_nb[2][LIM_EPB];
+  __shared__ Neighbour s_nb[2][EPB];
   const int2 blkid = A.blocks[blockIdx.x];
   load_inst(sI, A.insts + blkid.x);
   if (threadIdx.x == 0) s_n = 0;
@@ -646,11 +649,11 @@ __global__ void __launch_bounds__(LIM_THREADS) limiter_kernel(Mech M, LimArgs A)
   // 1. stage the CTA's elements with a one-element halo (ghosts at walls) and
   // the species fields in the variant's type; then the indicator, one element
   // per thread
-  const int e0 = blkid.y, te = min(LIM_EPB, N - e0);
-  const int vs = (LIM_EPB + 2) * Q;
+  const int e0 = blkid.y, te = min(EPB, N - e0);
+  const int vs = (EPB + 2) * Q;
   DG *spf = lsm;                                   // [SP_NFIELDS][ns]
-  DG *atn = spf + SP_NFIELDS * ns;                 // [2][LIM_EPB][nv] AT neighbour averages
-  DG *tile = atn + 2 * LIM_EPB * nv;               // [nv][LIM_EPB + 2][Q]
+  DG *atn = spf + SP_NFIELDS * ns;                 // [2][EPB][nv] AT neighbour averages
+  DG *tile = atn + 2 * EPB * nv;               // [nv][EPB + 2][Q]
   for (int k = threadIdx.x; k < SP_NFIELDS * ns; k += blockDim.x) spf[k] = (DG)M.sp[k];
   if ((int)threadIdx.x < 2 * te) {
     const int side = threadIdx.x / te, le = threadIdx.x - side * te;
@@ -698,7 +701,7 @@ __global__ void __launch_bounds__(LIM_THREADS) limiter_kernel(Mech M, LimArgs A)
   for (int item = threadIdx.x; item < 2 * te * nv; item += blockDim.x) {
     const int side = item / (te * nv), r = item - side * te * nv, le = r / nv, v = r - le * nv;
     const Neighbour &nb = s_nb[side][le];
-    if (nb.k > 0) atn[(side * LIM_EPB + le) * nv + v] = (DG)neighbour_mode(I, I.wpre, A.s, nstep, nb, v, 0, Q);
+    if (nb.k > 0) atn[(side * EPB + le) * nv + v] = (DG)neighbour_mode(I, I.wpre, A.s, nstep, nb, v, 0, Q);
   }
   __syncthreads();
   {
@@ -708,7 +711,7 @@ __global__ void __launch_bounds__(LIM_THREADS) limiter_kernel(Mech M, LimArgs A)
     const bool valid = le < te;
     const int lv = valid ? le : 0, e = e0 + lv;
     const DG *atl = s_nb[0][lv].k > 0 ? atn + lv * nv : nullptr;
-    const DG *atr = s_nb[1][lv].k > 0 ? atn + (LIM_EPB + lv) * nv : nullptr;
+    const DG *atr = s_nb[1][lv].k > 0 ? atn + (EPB + lv) * nv : nullptr;
     const bool t = troubled_cell<Q, LIM_L, DG>(M, I, A.s, nstep, e, tile + (lv + 1) * Q, vs, spf,
                                                atl, atr);
     if (valid && threadIdx.x % LIM_L == 0) {
@@ -1035,28 +1038,35 @@ cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, bool mixed, i
   return cudaErrorInvalidValue;
 }
 
-int limiter_elems_per_block(int nv) {
-  (void)nv;
-  return LIM_EPB;
+int limiter_elems_per_block(int64_t n_elem_group, bool mixed) {
+  // 16 elements per CTA (8 lanes each) while 32 would give fewer than two CTAs
+  // per SM, in the mixed variant only: in FP64 the lanes of an element repeat
+  // its FP64 divisions and square root, which costs more than the latency saved
+  return mixed && n_elem_group < (int64_t)2 * 152 * LIM_EPB_MAX ? 16 : LIM_EPB_MAX;
 }
 
-template <int Q, int G, bool MIX>
-static cudaError_t launch_limiter_qgm(const Mech &M, const LimArgs &A, int nv, int n_blocks,
-                                      cudaStream_t st) {
+template <int Q, int G, bool MIX, int EPB>
+static cudaError_t launch_limiter_qgme(const Mech &M, const LimArgs &A, int nv, int n_blocks,
+                                       cudaStream_t st) {
   constexpr int EPW = 32 / G;
-  size_t smem = ((size_t)SP_NFIELDS * M.ns + (size_t)2 * LIM_EPB * nv + (size_t)nv * (LIM_EPB + 2) * Q +
+  size_t smem = ((size_t)SP_NFIELDS * M.ns + (size_t)2 * EPB * nv + (size_t)nv * (EPB + 2) * Q +
                  (size_t)(LIM_THREADS / 32) * EPW * limiter_elem_words(nv, M.ns, Q)) *
                 (MIX ? sizeof(float) : sizeof(double));
   smem = (smem + 15) & ~(size_t)15;
-  limiter_kernel<Q, G, MIX><<<n_blocks, LIM_THREADS, smem, st>>>(M, A);
+  limiter_kernel<Q, G, MIX, EPB><<<n_blocks, LIM_THREADS, smem, st>>>(M, A);
   return cudaGetLastError();
 }
 
 template <int Q, bool MIX>
 static cudaError_t launch_limiter_qm(const Mech &M, const LimArgs &A, int nv, int n_blocks,
                                      cudaStream_t st) {
-  if (nv <= 16) return launch_limiter_qgm<Q, 16, MIX>(M, A, nv, n_blocks, st);
-  return launch_limiter_qgm<Q, 32, MIX>(M, A, nv, n_blocks, st);
+  if (A.EPB == 16) {
+    if (nv <= 16) return launch_limiter_qgme<Q, 16, MIX, 16>(M, A, nv, n_blocks, st);
+    return launch_limiter_qgme<Q, 32, MIX, 16>(M, A, nv, n_blocks, st);
+  }
+  if (A.EPB != LIM_EPB_MAX) return cudaErrorInvalidValue;
+  if (nv <= 16) return launch_limiter_qgme<Q, 16, MIX, LIM_EPB_MAX>(M, A, nv, n_blocks, st);
+  return launch_limiter_qgme<Q, 32, MIX, LIM_EPB_MAX>(M, A, nv, n_blocks, st);
 }
 
 cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, bool mixed, int nv,
@@ -1093,22 +1103,38 @@ cudaError_t prepare_kernels(int nv, int ns, int nr) {
   SET(stage_kernel<3, true>);
   SET(stage_kernel<4, true>);
   SET(stage_kernel<5, true>);
-  SET(limiter_kernel<2, 16, false>);
-  SET(limiter_kernel<3, 16, false>);
-  SET(limiter_kernel<4, 16, false>);
-  SET(limiter_kernel<5, 16, false>);
-  SET(limiter_kernel<2, 32, false>);
-  SET(limiter_kernel<3, 32, false>);
-  SET(limiter_kernel<4, 32, false>);
-  SET(limiter_kernel<5, 32, false>);
-  SET(limiter_kernel<2, 16, true>);
-  SET(limiter_kernel<3, 16, true>);
-  SET(limiter_kernel<4, 16, true>);
-  SET(limiter_kernel<5, 16, true>);
-  SET(limiter_kernel<2, 32, true>);
-  SET(limiter_kernel<3, 32, true>);
-  SET(limiter_kernel<4, 32, true>);
-  SET(limiter_kernel<5, 32, true>);
+  SET(limiter_kernel<2, 16, false, 16>);
+  SET(limiter_kernel<3, 16, false, 16>);
+  SET(limiter_kernel<4, 16, false, 16>);
+  SET(limiter_kernel<5, 16, false, 16>);
+  SET(limiter_kernel<2, 32, false, 16>);
+  SET(limiter_kernel<3, 32, false, 16>);
+  SET(limiter_kernel<4, 32, false, 16>);
+  SET(limiter_kernel<5, 32, false, 16>);
+  SET(limiter_kernel<2, 16, true, 16>);
+  SET(limiter_kernel<3, 16, true, 16>);
+  SET(limiter_kernel<4, 16, true, 16>);
+  SET(limiter_kernel<5, 16, true, 16>);
+  SET(limiter_kernel<2, 32, true, 16>);
+  SET(limiter_kernel<3, 32, true, 16>);
+  SET(limiter_kernel<4, 32, true, 16>);
+  SET(limiter_kernel<5, 32, true, 16>);
+  SET(limiter_kernel<2, 16, false, 32>);
+  SET(limiter_kernel<3, 16, false, 32>);
+  SET(limiter_kernel<4, 16, false, 32>);
+  SET(limiter_kernel<5, 16, false, 32>);
+  SET(limiter_kernel<2, 32, false, 32>);
+  SET(limiter_kernel<3, 32, false, 32>);
+  SET(limiter_kernel<4, 32, false, 32>);
+  SET(limiter_kernel<5, 32, false, 32>);
+  SET(limiter_kernel<2, 16, true, 32>);
+  SET(limiter_kernel<3, 16, true, 32>);
+  SET(limiter_kernel<4, 16, true, 32>);
+  SET(limiter_kernel<5, 16, true, 32>);
+  SET(limiter_kernel<2, 32, true, 32>);
+  SET(limiter_kernel<3, 32, true, 32>);
+  SET(limiter_kernel<4, 32, true, 32>);
+  SET(limiter_kernel<5, 32, true, 32>);
 #undef SET
   return e;
 }

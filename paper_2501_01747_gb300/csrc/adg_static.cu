@@ -126,7 +126,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   int target = (N + 2 * 152 - 1) / (2 * 152);
   if (target < TE) TE = target < 4 ? 4 : target;
   const int NT = stage_threads(TE, Q, nr);
-  const int EPB = limiter_elems_per_block(nv);
+  const int EPB = limiter_elems_per_block(N, mixed);
   const int n_tiles = (N + TE - 1) / TE, n_blocks = (N + EPB - 1) / EPB;
   size_t o_inst = cur.take(sizeof(Inst));
   size_t o_step = cur.take(sizeof(int64_t));
@@ -247,6 +247,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
         L.insts = (const Inst *)(base + o_inst);
         L.blocks = (const int2 *)(base + o_blocks);
         L.s = stg;
+        L.EPB = EPB;
         NA_CK(launch_limiter(M, L, Q, mixed, nv, n_blocks, s));
       }
     }
