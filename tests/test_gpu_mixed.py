@@ -203,3 +203,35 @@ def test_mixed_noalloc_matches_context_path():
     got = w_out.cpu().numpy()
     assert np.all(np.isfinite(got))
     assert H.parity_error(got, ref, mech).max() <= 1e-12
+
+
+def test_mixed_ensemble_512_full_size_sampled():
+    """The batched 512-instance ensemble in the mixed variant, autotuned, 3 steps;
+    sampled instances (smallest, largest, one per degree) against the oracle."""
+    ens = I.ensemble_workloads()
+    mech = ens[0].mechanism()
+    g = adg.ADG(mech, ens, precision="mixed")
+    for k, wl in enumerate(ens):
+        g.set_primitive(wl.primitive(mech), k)
+    g.step(1)
+    g.autotune()
+    g.step(2)
+    g.check()
+    ks = {min(range(len(ens)), key=lambda k: ens[k].n_elem),
+          max(range(len(ens)), key=lambda k: ens[k].n_elem)}
+    for p in (2, 3, 4):
+        ks.add(next(k for k, w in enumerate(ens) if w.p == p))
+    for k in sorted(ks):
+        wl = ens[k]
+        o = O.Oracle(wl, mech)
+        o.set_primitive(wl.primitive(mech))
+        o.step(3)
+        T, To = g.temperature(k), o.temperature()
+        eT = float((np.abs(T - To) / To).max())
+        Y, Yo = mass_fractions(g.get_state(k), wl.p), mass_fractions(o.state(), wl.p)
+        eY = 0.0
+        for i in range(Yo.shape[0]):
+            big = Yo[i] > Y_MIN
+            if big.any():
+                eY = max(eY, float(np.abs(Y[i] - Yo[i])[big].max() / Yo[i].max()))
+        assert eT <= TOL_T and eY <= TOL_Y, (k, eT, eY)

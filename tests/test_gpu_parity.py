@@ -296,3 +296,35 @@ def test_autotune_keeps_the_trajectory():
     o.set_primitive(prim)
     o.step(24)
     assert_parity(g, o)
+
+
+def ensemble_sample(ens):
+    """The smallest and largest instance and the first of each degree."""
+    ks = {min(range(len(ens)), key=lambda k: ens[k].n_elem),
+          max(range(len(ens)), key=lambda k: ens[k].n_elem)}
+    for p in (2, 3, 4):
+        ks.add(next(k for k, w in enumerate(ens) if w.p == p))
+    return sorted(ks)
+
+
+def test_ensemble_512_full_size_sampled():
+    """The batched 512-instance ensemble (8.58 M Gauss points, three degree
+    groups) in one context, in the autotuned launch configuration the benchmark
+    times, 3 steps; sampled instances against the oracle run on them alone."""
+    ens = I.ensemble_workloads()
+    mech = ens[0].mechanism()
+    g = adg.ADG(mech, ens)
+    for k, wl in enumerate(ens):
+        g.set_primitive(wl.primitive(mech), k)
+    g.step(1)
+    g.autotune()
+    g.step(2)
+    g.check()
+    for k in ensemble_sample(ens):
+        wl = ens[k]
+        o = O.Oracle(wl, mech)
+        o.set_primitive(wl.primitive(mech))
+        o.step(3)
+        err = rel_err(g.get_state(k), o.state(), mech)
+        assert err.max() <= TOL, (k, err)
+        assert np.array_equal(g.flags(k)[1], o.flags()[1]), k
