@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libadg.so")
-SOURCES = ["adg_kernels.cu", "adg_api.cu", "adg_static.cu"]
+SOURCES = ["adg_k64.cu", "adg_k32.cu", "adg_kernels.cu", "adg_api.cu", "adg_static.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", ARCH]
 

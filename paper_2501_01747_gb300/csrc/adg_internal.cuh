@@ -278,6 +278,19 @@ cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, bool mixed, i
 cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, bool mixed, int nv,
                            int n_blocks, cudaStream_t st);
 cudaError_t launch_advance(int64_t *steps, int n, cudaStream_t st);
+// per-variant units (adg_k64.cu, adg_k32.cu)
+cudaError_t launch_stage_fp64(const Mech &M, const StageArgs &A, int Q, int n_tiles,
+                              cudaStream_t st);
+cudaError_t launch_stage_mixed(const Mech &M, const StageArgs &A, int Q, int n_tiles,
+                               cudaStream_t st);
+cudaError_t launch_limiter_fp64(const Mech &M, const LimArgs &A, int Q, int nv, int n_blocks,
+                                cudaStream_t st);
+cudaError_t launch_limiter_mixed(const Mech &M, const LimArgs &A, int Q, int nv, int n_blocks,
+                                 cudaStream_t st);
+cudaError_t prepare_fp64();
+cudaError_t prepare_mixed();
+cudaError_t upload_tables_fp64(const Basis *tables);
+cudaError_t upload_tables_mixed(const Basis *tables);
 int limiter_elems_per_block(int64_t n_elem_group, bool mixed);
 cudaError_t launch_project(const Mech &M, const Inst &I, const double *prim, double *w,
                            cudaStream_t st);

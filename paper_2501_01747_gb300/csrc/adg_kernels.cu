@@ -1,933 +1,9 @@
-// CUDA kernels of the ADG hot path (sm_103a).
-//
-// Per RK stage two kernels run, each in an FP64 and a mixed-precision variant
-// (MIX: FP32 for the flux, the DG operator and the limiter; FP64 for the
-// Gauss-point temperature, the Arrhenius and equilibrium exponentials, the AT
-// level sums and the accumulation of the conserved state):
-//   stage_kernel<Q,MIX>  : one CTA per tile of TE consecutive elements of one
-//                      instance. Loads the tile plus a one-element halo into
-//                      shared memory (coalesced per variable); Gauss-point
-//                      thermo and flux, one thread per point; chemistry, R
-//                      chunks of reactions per point; the TE+1 face fluxes of the
-//                      tile (AT levels on separate threads); Eq. (5) assembly and
-//                      the SSP-RK3 combination; writes the pre-limit output and
-//                      the history ring of PE-boundary elements.
-//   limiter_kernel<Q,G,MIX>: G lanes per element: troubled-cell indicator in the
-//                      characteristic fields of the cell average and, on troubled
-//                      cells, the (AT-)WENO reconstruction of Eq. (9)-(11). The
-//                      stage kernel writes the pre-limit output twice (limiter
-//                      input and next-stage buffer) so that the limiter only
-//                      rewrites troubled cells.
-#include <cstdio>
-#include <type_traits>
-
-#include "adg_internal.cuh"
-#include "adg_math.cuh"
+// Host-side dispatch of the ADG kernels and the set-up kernels (projection of
+// primitive values, temperature, step counters). The stage and limiter kernels
+// of each precision variant live in adg_k64.cu and adg_k32.cu.
+#include "adg_device.cuh"
 
 namespace adg {
-
-__constant__ Basis c_basis[ADG_MAX_P];     // index p-1
-__constant__ BasisF c_basis_f[ADG_MAX_P];  // the same, rounded to float
-
-__constant__ IExpTable c_iexp = {ADG_IEXP_TABLE, ADG_IEXP_TABLE32};
-
-template <bool MIX>
-using dg_t = typename std::conditional<MIX, float, double>::type;
-
-// Shared-memory footprint (bytes) of a stage tile of TE elements with up to O AT
-// levels per face. FP64 region: species fields, exp table, basis values, modal
-// tile with halo, w^n of the tile, nodal state, ln T, 1/T, u, P. Region in the
-// arithmetic type of the variant: face, level and trace fluxes, concentrations,
-// rates of progress, production rates; the mixed variant adds an FP32 copy of
-// the species fields and the point flux (the FP64 variant writes the flux over
-// the nodal state). Integers: delay per face, species-reaction incidence.
-__host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int ns, int nr, int nterm,
-                                                   int O, bool mix) {
-  const size_t nv = ns + 2, TQ = (size_t)TE * Q, F = TE + 1;
-  const size_t nd = (size_t)SP_NFIELDS * ns + sizeof(IExpTable) / 8 + MAXQ * MAXQ +
-                    nv * (TE + 2) * Q + 2 * nv * TQ + 4 * TQ;
-  size_t ndg = F * nv + (size_t)O * F * nv + (size_t)O * F * 2 * nv + (size_t)ns * TQ +
-               (size_t)nr * TQ + (size_t)ns * TQ + nterm;
-  if (mix) ndg += (size_t)SP_NFIELDS * ns + nv * TQ;
-  const size_t ni = F + ns + 1 + nterm;
-  return (size_t)nr * sizeof(Rxn) + nd * 8 + ndg * (mix ? 4 : 8) + ni * 4 + 16;
-}
-
-// Copy an instance description into shared memory (by 8-byte words).
-__device__ inline void load_inst(Inst &dst, const Inst *src) {
-  const unsigned long long *a = reinterpret_cast<const unsigned long long *>(src);
-  unsigned long long *b = reinterpret_cast<unsigned long long *>(&dst);
-  for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 8); k += blockDim.x) b[k] = a[k];
-}
-
-template <int Q, bool MIX>
-__global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
-  using DG = dg_t<MIX>;
-  extern __shared__ __align__(16) double sm[];
-  __shared__ Inst sI;
-  const int2 tile = A.tiles[blockIdx.x];
-  load_inst(sI, A.insts + tile.x);
-  __syncthreads();
-  const Inst &I = sI;
-  const Basis &B = c_basis[Q - 2];
-  const BasisF &BF = c_basis_f[Q - 2];
-  const int nv = I.nv, ns = M.ns, nr = M.nr, N = I.n_elem, TE = A.TE;
-  const int TQ = TE * Q;
-  const int e0 = tile.y;
-  const int te = min(TE, N - e0);
-  const int teq = te * Q;
-  const int64_t nstep = *I.step;
-  const double *A_win = (A.s == 0) ? I.wn : (A.s == 1) ? I.wa : I.wb;
-  double *A_wnext = (A.s == 0) ? I.wa : (A.s == 1) ? I.wb : I.wn;
-  const bool periodic = (I.bc_left == ADG_BC_PERIODIC);
-  const int O = A.O, NF = TE + 1;
-  Rxn *srx = reinterpret_cast<Rxn *>(sm);
-  double *ssp = reinterpret_cast<double *>(srx + nr);         // [F][ns]
-  IExpTable *stab = reinterpret_cast<IExpTable *>(ssp + SP_NFIELDS * ns);
-  double *sPq = reinterpret_cast<double *>(stab + 1);         // [q][j] P_j(x_q)
-  double *sw = sPq + MAXQ * MAXQ;                             // [v][TE+2][Q]
-  double *snw = sw + (size_t)nv * (TE + 2) * Q;               // [v][TQ] nodal state
-  double *slnT = snw + (size_t)nv * TQ;                       // [TQ]
-  double *sinvT = slnT + TQ;
-  double *su = sinvT + TQ;
-  double *sPr = su + TQ;
-  double *swn = sPr + TQ;                                     // [v][TQ] modes of w^n
-  DG *sfh = reinterpret_cast<DG *>(swn + (size_t)nv * TQ);    // [NF][nv]
-  DG *sflx = sfh + (size_t)NF * nv;                           // [O][NF][nv]
-  DG *str = sflx + (size_t)O * NF * nv;                       // [O][NF][2][nv]
-  DG *scc = str + (size_t)O * NF * 2 * nv;                    // [i][TQ] concentrations
-  DG *sq = scc + (size_t)ns * TQ;                             // [j][TQ] rates of progress
-  DG *swd = sq + (size_t)nr * TQ;                             // [i][TQ] production rates
-  DG *scoef = swd + (size_t)ns * TQ;                          // [nterm] incidence coefficients
-  DG *sspD, *sfx;                                             // species fields, point flux
-  int *sk;
-  if constexpr (MIX) {
-    sspD = scoef + M.nterm;
-    sfx = sspD + (size_t)SP_NFIELDS * ns;
-    sk = reinterpret_cast<int *>(sfx + (size_t)nv * TQ);
-  } else {
-    sspD = reinterpret_cast<DG *>(ssp);
-    sfx = reinterpret_cast<DG *>(snw);
-    sk = reinterpret_cast<int *>(scoef + M.nterm);
-  }
-  int *soff = sk + NF;        // [ns + 1]
-  int *sterm = soff + ns + 1;  // [nterm] reaction of each incidence term
-  const int tid = threadIdx.x, nth = blockDim.x;
-
-  // 0. mechanism, species fields, incidence, exp table and basis values into
-  // shared memory
-  {
-    const uint4 *src = reinterpret_cast<const uint4 *>(M.rx);
-    uint4 *dst = reinterpret_cast<uint4 *>(srx);
-    for (int k = tid; k < nr * (int)(sizeof(Rxn) / 16); k += nth) dst[k] = src[k];
-    for (int k = tid; k < SP_NFIELDS * ns; k += nth) {
-      double x = M.sp[k];
-      ssp[k] = x;
-      if constexpr (MIX) sspD[k] = (DG)x;
-    }
-    for (int k = tid; k < 32; k += nth) {
-      stab->t[k] = c_iexp.t[k];
-      stab->t32[k] = c_iexp.t32[k];
-    }
-    for (int k = tid; k < Q * Q; k += nth) sPq[k] = B.P[k / Q][k % Q];
-    for (int k = tid; k <= ns; k += nth) soff[k] = M.sx_off[k];
-    for (int k = tid; k < M.nterm; k += nth) {
-      const int term = M.sx[k];
-      sterm[k] = term >> 8;
-      scoef[k] = (DG)(signed char)(term & 0xff);
-    }
-  }
-  // 1. tile of modal coefficients with a one-element halo on each side and, for
-  // stages 1 and 2, the tile's modes of w^n (batches of loads in flight)
-  {
-    constexpr int BATCH = 4;
-    const int span = (te + 2) * Q, n_tile = nv * span;
-    const int n_wn = (A.s == 0) ? 0 : nv * te * Q;
-    const int total = n_tile + n_wn;
-    for (int base = tid; base < total; base += BATCH * nth) {
-      double xs[BATCH];
-      double *dst[BATCH];
-#pragma unroll
-      for (int b = 0; b < BATCH; ++b) {
-        const int idx = base + b * nth;
-        dst[b] = nullptr;
-        if (idx < n_tile) {
-          const int v = idx / span, r = idx - v * span;
-          const int le = r / Q, j = r - le * Q;
-          int e = e0 - 1 + le;
-          if (e < 0) e = periodic ? e + N : 0;
-          if (e >= N) e = periodic ? e - N : N - 1;
-          xs[b] = A_win[((size_t)v * N + e) * Q + j];
-          dst[b] = sw + ((size_t)v * (TE + 2) + le) * Q + j;
-        } else if (idx < total) {
-          const int k = idx - n_tile, v = k / (te * Q), r = k - v * te * Q;
-          xs[b] = I.wn[((size_t)v * N + e0) * Q + r];
-          dst[b] = swn + (size_t)v * TQ + r;
-        }
-      }
-#pragma unroll
-      for (int b = 0; b < BATCH; ++b)
-        if (dst[b]) *dst[b] = xs[b];
-    }
-  }
-  __syncthreads();
-
-  // 2a. conserved state at the Gauss points, one (variable, point) per item
-  for (int item = tid; item < nv * teq; item += nth) {
-    int v = item / teq, t = item - v * teq;
-    int e = t / Q, q = t - e * Q;
-    const double *wi = sw + ((size_t)v * (TE + 2) + e + 1) * Q;
-    const double *Pq = sPq + q * Q;
-    double acc = 0.0;
-#pragma unroll
-    for (int j = 0; j < Q; ++j) acc += wi[j] * Pq[j];
-    snw[(size_t)v * TQ + t] = acc;
-  }
-  __syncthreads();
-  // 2b. temperature from the internal energy (the closed form of the Newton step
-  // for constant c_p), ln T, 1/T, velocity and pressure, in FP64
-  {
-    const double *sQW = ssp + SP_QW * ns, *sCVW = ssp + SP_CVW * ns, *sRW = ssp + SP_RW * ns;
-    for (int t = tid; t < teq; t += nth) {
-      const double *wq = snw + t;
-      double rho = 0.0, qsum = 0.0, cv = 0.0, Rm = 0.0;
-      for (int i = 0; i < ns; ++i) {
-        const double r = wq[(size_t)(2 + i) * TQ];
-        rho += r;
-        qsum = fma(r, sQW[i], qsum);
-        cv = fma(r, sCVW[i], cv);
-        Rm = fma(r, sRW[i], Rm);
-      }
-      const double m = wq[0], u = m / rho;
-      const double num = wq[TQ] - 0.5 * m * u - qsum;
-      const double T = num / cv;
-      if (!(rho > 0.0) || !(T > 0.0) || !isfinite(T) || !isfinite(m))
-        report_error(I, ADG_ERR_NONPHYSICAL, e0 + t / Q, A.s, nstep);
-      slnT[t] = log(T);
-      sinvT[t] = cv / num;
-      su[t] = u;
-      sPr[t] = T * Rm;
-    }
-  }
-  __syncthreads();
-  // 2c. per (variable, point): the flux, and for a species its concentration
-  // (law of mass action on non-negative concentrations: clipped at zero by the
-  // sign bit)
-  {
-    const double *sIW = ssp + SP_INVW * ns;
-    for (int item = tid; item < nv * teq; item += nth) {
-      int v = item / teq, t = item - v * teq;
-      const size_t at = (size_t)v * TQ + t;
-      const double w = snw[at], u = su[t];
-      if (v >= 2) {
-        const int i = v - 2;
-        const double r = (__double2hiint(w) < 0) ? 0.0 : w;
-        scc[(size_t)i * TQ + t] = (DG)(r * sIW[i]);
-        if constexpr (MIX) sfx[at] = (DG)u * (DG)w;
-        else snw[at] = u * w;
-      } else if (v == 0) {
-        if constexpr (MIX) sfx[at] = fma((DG)w, (DG)u, (DG)sPr[t]);
-        else snw[at] = w * u + sPr[t];
-      } else {
-        if constexpr (MIX) sfx[at] = (DG)u * ((DG)w + (DG)sPr[t]);
-        else snw[at] = u * (w + sPr[t]);
-      }
-    }
-  }
-  __syncthreads();
-
-  // 3. the face fluxes of the tile (local face f between local elements f and
-  // f+1), one (level, face) per item: the plain flux, or one delayed level of
-  // the AT flux (Eq. 7) with both sides at the common level n-k-m; then the
-  // chemistry, one (reaction, point) per item: the reversible rate of progress
-  // from the Arrhenius and the equilibrium exponentials (arguments in FP64).
-  // The face items, the longest, come first so that they overlap the chemistry.
-  const int n_face = O * (te + 1);
-  for (int item = tid; item < n_face + nr * teq; item += nth) {
-    if (item >= n_face) {
-      const int j = (item - n_face) / teq, t = (item - n_face) - j * teq;
-      const Rxn &Rx = srx[j];
-      const double lnT = slnT[t], invT = sinvT[t];
-      const double lkf = fma(Rx.mEaR, invT, fma(Rx.b, lnT, Rx.lnA));
-      const double lkr = fma(Rx.kr2, invT, fma(Rx.kr1, lnT, Rx.kr0));
-      DG fwd, rev;
-      if constexpr (MIX) {
-        fwd = iexpf(lkf, *stab);
-        rev = iexpf(lkr, *stab);
-      } else {
-        fwd = iexp(lkf, *stab);
-        rev = iexp(lkr, *stab);
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (Rx.rn[k] == 0) break;
-        DG cc = scc[(size_t)Rx.rs[k] * TQ + t];
-        fwd *= cc;
-        if (Rx.rn[k] > 1) fwd *= cc;
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (Rx.pn[k] == 0) break;
-        DG cc = scc[(size_t)Rx.ps[k] * TQ + t];
-        rev *= cc;
-        if (Rx.pn[k] > 1) rev *= cc;
-      }
-      sq[(size_t)j * TQ + t] = fwd - rev;
-      continue;
-    }
-    const int m = item / (te + 1), f = item - m * (te + 1);
-    const int g = e0 + f;  // global face index
-    const int pf = (g < N) ? I.pf_of_left[g] : I.pf_of_right[N - 1];
-    const int k = (pf >= 0) ? effective_delay(I, nstep, pf) : 0;
-    if (m == 0) sk[f] = k;
-    DG *fl = sflx + ((size_t)m * NF + f) * nv;
-    DG *wl = str + ((size_t)m * NF + f) * 2 * nv, *wr = wl + nv;
-    if (k > 0) {
-      if (m >= I.at_order) continue;
-      const int64_t lv = nstep - k - m;
-      const double *bl = I.ring_in + ring_trace(I, lv, A.s, pf, 0);
-      const double *br = I.ring_in + ring_trace(I, lv, A.s, pf, 1);
-      if constexpr (MIX) {
-        for (int v = 0; v < nv; ++v) {
-          wl[v] = (DG)bl[v];
-          wr[v] = (DG)br[v];
-        }
-        num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
-      } else {
-        num_flux_t<double>(ssp, ns, I.flux, bl, br, fl);
-      }
-      continue;
-    }
-    if (m > 0) continue;
-    for (int v = 0; v < nv; ++v) {
-      double a = 0.0, b = 0.0;
-      for (int j = 0; j < Q; ++j) {
-        a += sw[((size_t)v * (TE + 2) + f) * Q + j];
-        b += ((j & 1) ? -1.0 : 1.0) * sw[((size_t)v * (TE + 2) + f + 1) * Q + j];
-      }
-      wl[v] = (DG)a;
-      wr[v] = (DG)b;
-    }
-    if (!periodic && g == 0) {
-      for (int v = 0; v < nv; ++v) wl[v] = wr[v];
-      if (I.bc_left == ADG_BC_REFLECT) wl[0] = -wr[0];
-    } else if (!periodic && g == N) {
-      for (int v = 0; v < nv; ++v) wr[v] = wl[v];
-      if (I.bc_right == ADG_BC_REFLECT) wr[0] = -wl[0];
-    }
-    num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
-  }
-  __syncthreads();
-
-  // 4. production rates, one (species, point) per item: the net stoichiometric
-  // sum over the species' reactions, in ascending reaction order
-  for (int item = tid; item < ns * teq; item += nth) {
-    const int i = item / teq, t = item - i * teq;
-    DG acc = DG(0);
-    for (int k = soff[i]; k < soff[i + 1]; ++k)
-      acc = fma(scoef[k], sq[(size_t)sterm[k] * TQ + t], acc);
-    swd[(size_t)i * TQ + t] = acc;
-  }
-  // 5. the AT sum over levels, m = 0..o-1 in order, in FP64
-  for (int item = tid; item < (te + 1) * nv; item += nth) {
-    const int f = item / nv, v = item - f * nv;
-    const int k = sk[f];
-    double acc = (double)sflx[(size_t)f * nv + v];
-    if (k > 0) {
-      acc *= I.at[k][0];
-      for (int m = 1; m < I.at_order; ++m)
-        acc = fma(I.at[k][m], (double)sflx[((size_t)m * NF + f) * nv + v], acc);
-    }
-    sfh[(size_t)f * nv + v] = (DG)acc;
-  }
-  __syncthreads();
-
-  // 6. assembly of Eq. (5) (in the variant's arithmetic) and the SSP-RK3
-  // combination (FP64); history ring writes
-  const int slot_ok = (I.npf > 0);
-  const double inv_dx = 1.0 / I.dx;
-  const double *sW = ssp + SP_W * ns;
-  for (int item = tid; item < nv * te; item += nth) {
-    const int v = item / te, e = item - v * te, ge = e0 + e, le = e + 1;
-    const double *wi = sw + ((size_t)v * (TE + 2) + le) * Q;
-    const DG *fq = sfx + (size_t)v * TQ + e * Q;
-    const DG *sqv = (v >= 2) ? swd + (size_t)(v - 2) * TQ + e * Q : nullptr;
-    const DG Wv = (v >= 2) ? (DG)sW[v - 2] : DG(0);
-    const DG fr = sfh[(size_t)(e + 1) * nv + v], fl = sfh[(size_t)e * nv + v];
-    DG fqr[Q], sqr[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      fqr[q] = fq[q];
-      sqr[q] = (v >= 2) ? sqv[q] : DG(0);
-    }
-    double out[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      DG V = 0, S = 0;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        if constexpr (MIX) {
-          V = fma(BF.WdP[q][i], fqr[q], V);
-          S = fma(BF.WPh[q][i], sqr[q], S);
-        } else {
-          V = fma(B.WdP[q][i], fqr[q], V);
-          S = fma(B.WPh[q][i], sqr[q], S);
-        }
-      }
-      DG surf = (i & 1) ? (V - fr - fl) : (V - fr + fl);
-      double r = (double)fma((DG)((2.0 * i + 1.0) * inv_dx), surf, Wv * S);
-      size_t gi = ((size_t)v * N + ge) * Q + i;
-      double o;
-      if (A.s == 0) {
-        o = fma(I.dt, r, wi[i]);  // the stage input is w^n
-      } else {
-        const double wn = swn[(size_t)v * TQ + e * Q + i];
-        if (A.s == 1) o = fma(0.25, fma(I.dt, r, wi[i]), 0.75 * wn);
-        else o = fma(2.0 / 3.0, fma(I.dt, r, wi[i]), (1.0 / 3.0) * wn);
-      }
-      out[i] = o;
-      I.wpre[gi] = o;
-      A_wnext[gi] = o;
-    }
-    if (slot_ok) {
-      int pr = I.pf_of_right[ge], pl = I.pf_of_left[ge];
-      if (pr >= 0) {
-        // left element of the PE face: its trace at xi = +1
-        size_t b = ring_block(I, nstep, A.s, pr, 0) + (size_t)v * Q;
-        double tr = 0.0;
-        for (int i = 0; i < Q; ++i) {
-          tr += wi[i];
-          I.ring_pre[b + i] = out[i];
-        }
-        I.ring_in[ring_trace(I, nstep, A.s, pr, 0) + v] = tr;
-      }
-      if (pl >= 0) {
-        // right element of the PE face: its trace at xi = -1
-        size_t b = ring_block(I, nstep, A.s, pl, 1) + (size_t)v * Q;
-        double tr = 0.0;
-        for (int i = 0; i < Q; ++i) {
-          tr += ((i & 1) ? -1.0 : 1.0) * wi[i];
-          I.ring_pre[b + i] = out[i];
-        }
-        I.ring_in[ring_trace(I, nstep, A.s, pl, 1) + v] = tr;
-      }
-    }
-  }
-}
-
-template <typename R>
-__device__ inline R minmod3(R a, R b, R c) {
-  if (a > R(0) && b > R(0) && c > R(0)) return fmin(a, fmin(b, c));
-  if (a < R(0) && b < R(0) && c < R(0)) return fmax(a, fmax(b, c));
-  return R(0);
-}
-
-// Threads per limiter CTA. A CTA limits EPB = 32 elements (4 lanes per element
-// in the indicator) or, for small mixed-precision groups, EPB = 16 (8 lanes), so
-// that small meshes still spread over every SM; all threads stage the tile and
-// run the WENO phase.
-constexpr int LIM_THREADS = 128;
-constexpr int LIM_EPB_MAX = 32;
-
-// Shared memory (words of the arithmetic type) per troubled element in the WENO
-// phase: the element and its two neighbours, the limited characteristic modes,
-// gradP.w, the partial-density sums and momenta of the three blocks, phi_k, two
-// mode sums.
-__host__ __device__ inline int limiter_elem_words(int nv, int ns, int Q) {
-  return 3 * nv * Q + nv * Q + 3 * 3 * Q + ns + 2 * Q + 2;
-}
-
-// Where the values of a neighbour of element e (side 0 left, 1 right) come from:
-// the AT extrapolation of the neighbour's pre-limit history across a delayed PE
-// face (Eq. 11, delay k > 0 at PE face pf), or the pre-limit field of element
-// src, mirrored at a reflecting wall (the boundary ghost is the element itself).
-struct Neighbour {
-  int pf, k, src, ghost, side;
-};
-
-__device__ inline Neighbour neighbour_of(const Inst &I, int64_t nstep, int e, int side) {
-  Neighbour nb;
-  const int N = I.n_elem;
-  nb.side = side;
-  nb.pf = side == 0 ? I.pf_of_left[e] : I.pf_of_right[e];
-  nb.k = (nb.pf >= 0) ? effective_delay(I, nstep, nb.pf) : 0;
-  nb.src = side == 0 ? e - 1 : e + 1;
-  nb.ghost = 0;
-  if (nb.src < 0 || nb.src >= N) {
-    if (I.bc_left == ADG_BC_PERIODIC) {
-      nb.src = (nb.src + N) % N;
-    } else {
-      nb.src = e;
-      nb.ghost = ((side == 0 ? I.bc_left : I.bc_right) == ADG_BC_REFLECT) ? 1 : 0;
-    }
-  }
-  return nb;
-}
-
-// Mode j of variable v of a neighbour (the sum of the AT levels in FP64).
-__device__ inline double neighbour_mode(const Inst &I, const double *wpre, int s, int64_t nstep,
-                                        const Neighbour &nb, int v, int j, int Q) {
-  if (nb.k > 0) {
-    double acc = 0.0;
-    for (int m = 0; m < I.at_order; ++m)
-      acc += I.at[nb.k][m] *
-             I.ring_pre[ring_block(I, nstep - nb.k - m, s, nb.pf, nb.side) + (size_t)v * Q + j];
-    return acc;
-  }
-  double x = wpre[((size_t)v * I.n_elem + nb.src) * Q + j];
-  if (nb.ghost && (((j & 1) != 0) != (v == 0))) x = -x;
-  return x;
-}
-
-
-// Troubled-cell indicator of element e (Sec. 3.3), a group of L lanes, in the
-// arithmetic type R. In each characteristic field of L(wbar_e) the face
-// deviations v(+1) - vbar and vbar - v(-1) go through the TVB-modified minmod
-// with the neighbours' mean differences; deviations below 1e-5 of the field's
-// magnitude sum_v |L_kv| sigma_v count as zero. Three passes over the
-// variables, the species and the fields split over the group's lanes: the
-// thermodynamics of the cell average; gradP.w, the partial-density sum and the
-// momentum at the five points (own average, faces +1 and -1, neighbours'
-// averages); the characteristic values per field, with the branch-free
-// coefficients (A, B, C, D) described at the limiter kernel. Every lane of the
-// warp calls it (shuffles); the result is the same on the group's lanes.
-// own: modes of variable 0 of the element in the staged tile (variables vs
-// apart, the neighbours' modes Q before and after, halo ghosts included);
-// spf: species fields in R; atl, atr: the AT-extrapolated averages [nv] of a
-// neighbour across a delayed PE face, or null.
-template <int Q, int L, typename R>
-__device__ bool troubled_cell(const Mech &M, const Inst &I, int s, int64_t nstep, int e,
-                              const R *own, int vs, const R *spf, const R *atl, const R *atr) {
-  const int ns = M.ns, nv = ns + 2;
-  const int lane = threadIdx.x & 31, li = lane % L;
-  const unsigned FULL = 0xffffffffu;
-  const R *qW = spf + SP_QW * ns, *cvW = spf + SP_CVW * ns;
-  const R *RW = spf + SP_RW * ns, *cpW = spf + SP_CPW * ns;
-  auto allsum = [&](R x) {
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o, L);
-    return x;
-  };
-  // values of variable v at the five points
-  auto points = [&](int v, R *x) {
-    const R *w = own + (size_t)v * vs;
-    R sp = 0, sm = 0;
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      sp += w[j];
-      sm += (j & 1) ? -w[j] : w[j];
-    }
-    x[0] = w[0];
-    x[1] = sp;
-    x[2] = sm;
-    x[3] = atl ? atl[v] : w[-Q];
-    x[4] = atr ? atr[v] : w[Q];
-  };
-  // 1. thermodynamics of the cell average
-  R rho = 0, qsum = 0, cv = 0, Rm = 0, cpm = 0;
-  for (int i = li; i < ns; i += L) {
-    R r = own[(size_t)(2 + i) * vs];
-    rho += r;
-    qsum = fma(r, qW[i], qsum);
-    cv = fma(r, cvW[i], cv);
-    Rm = fma(r, RW[i], Rm);
-    cpm = fma(r, cpW[i], cpm);
-  }
-  rho = allsum(rho);
-  qsum = allsum(qsum);
-  cv = allsum(cv);
-  Rm = allsum(Rm);
-  cpm = allsum(cpm);
-  const R irho = R(1) / rho, icv = R(1) / cv;
-  const R m0 = own[0], E0 = own[vs];
-  const R u = m0 * irho;
-  const R T = (E0 - R(0.5) * m0 * u - qsum) * icv;
-  const R P = T * Rm;
-  const R gam = cpm * icv, g = gam - R(1);
-  const R a = sqrt(gam * P * irho);
-  const R ia2 = R(1) / (a * a), ha2 = R(0.5) * ia2;
-  if (li == 0 && (!(rho > R(0)) || !(T > R(0)) || !isfinite(T)))
-    report_error(I, ADG_ERR_NONPHYSICAL, e, s, nstep);
-  auto phi_of = [&](int i) { return fma(g, fma(-cvW[i], T, R(0.5) * u * u - qW[i]), T * RW[i]); };
-  // 2. gradP.w, sum rho Y and rho u at the five points; sums of |phi|
-  R gp[5], rs[5], mm[5], x[5];
-  R sphi = 0, sphm = 0, sphp = 0;
-  points(0, mm);
-  points(1, x);
-#pragma unroll
-  for (int p = 0; p < 5; ++p) {
-    gp[p] = li == 0 ? g * fma(-u, mm[p], x[p]) : R(0);
-    rs[p] = 0;
-  }
-  for (int i = li; i < ns; i += L) {
-    const R ph = phi_of(i);
-    sphi += fabs(ph);
-    sphm += fabs(ph - a * u);
-    sphp += fabs(ph + a * u);
-    points(2 + i, x);
-#pragma unroll
-    for (int p = 0; p < 5; ++p) {
-      gp[p] = fma(ph, x[p], gp[p]);
-      rs[p] += x[p];
-    }
-  }
-#pragma unroll
-  for (int p = 0; p < 5; ++p) {
-    gp[p] = allsum(gp[p]);
-    rs[p] = allsum(rs[p]);
-  }
-  sphi = allsum(sphi);
-  sphm = allsum(sphm);
-  sphp = allsum(sphp);
-  // 3. the characteristic fields, k = 0 and nv-1 acoustic, k = 1..ns species k-1
-  const R sig0 = fma(rho, a, fabs(m0)), sig1 = fabs(E0), sigr = rho;
-  const R tvb = (R)I.tvb, tau = R(1e-5);
-  bool tr = false;
-  for (int k = li; k < nv; k += L) {
-    R v[5], scale;
-    if (k == 0 || k == nv - 1) {
-      const R sgn = k == 0 ? R(-1) : R(1);
-      const R cA = ha2, cB = sgn * a * ha2, cC = -sgn * a * u * ha2;
-#pragma unroll
-      for (int p = 0; p < 5; ++p) v[p] = fma(cA, gp[p], fma(cB, mm[p], cC * rs[p]));
-      const R srr = cA * (k == 0 ? sphp : sphm);
-      scale = fma(fabs(fma(cA, -u * g, cB)), sig0, fma(fabs(cA * g), sig1, srr * sigr));
-    } else {
-      const int i = k - 1;
-      points(2 + i, x);
-      const R cA = -x[0] * irho * ia2;
-      const R ph = phi_of(i);
-#pragma unroll
-      for (int p = 0; p < 5; ++p) v[p] = fma(cA, gp[p], x[p]);
-      const R srr = fabs(fma(cA, ph, R(1))) + fabs(cA) * (sphi - fabs(ph));
-      scale = fma(fabs(cA * -u * g), sig0, fma(fabs(cA * g), sig1, srr * sigr));
-    }
-    const R ut = v[1] - v[0], utt = v[0] - v[2], dp = v[4] - v[0], dm = v[0] - v[3];
-    const R fl = tau * scale;
-    if (fabs(ut) > fl && fabs(ut) > tvb && minmod3(ut, dp, dm) != ut) tr = true;
-    if (fabs(utt) > fl && fabs(utt) > tvb && minmod3(utt, dp, dm) != utt) tr = true;
-  }
-  const unsigned bal = __ballot_sync(FULL, tr);
-  const unsigned gm = ((1u << L) - 1u) << (lane - li);
-  return (bal & gm) != 0u;
-}
-
-// Troubled-cell indicator and (AT-)WENO limiter (Sec. 3.3, Eq. 9-11), in the
-// arithmetic type of the precision variant. Phase 1: one element per thread
-// runs the indicator and writes its flag; troubled elements go to a list in
-// shared memory. Phase 2: a group of G lanes per troubled element (G = 16 when
-// nv <= 16, else 32) reconstructs its characteristic fields with WENO and
-// writes modes >= 1 of the next stage's input (the stage kernel wrote the
-// pre-limit output there for every element already).
-// Eigen-structure of the frozen Jacobian at the cell average: right vectors
-// r_-/+ = (u -/+ a, H -/+ u a, Y), species r_k = (u, u^2 - phi_k/g, e_k); left
-// vectors l_-/+ = (gradP -/+ a (1, 0, -u..-u)) / (2 a^2), l_k = e_k - Y_k gradP/a^2,
-// gradP = (-u g, g, phi_1..phi_ns), g = gamma - 1, phi_k = g (u^2/2 - e_k) + R T / W_k.
-// Every characteristic value is written in one branch-free form,
-// v = A gradP.w + B (rho u)_w + C (sum rho Y)_w + D (rho Y_k)_w,
-// with (A, B, C, D) = (1/2a^2, -/+ a/2a^2, +/- a u/2a^2, 0) for the acoustic fields
-// and (-Y_k/a^2, 0, 0, 1) for species k.
-template <int Q, int G, bool MIX, int EPB>
-__global__ void __launch_bounds__(LIM_THREADS) limiter_kernel(Mech M, LimArgs A) {
-  constexpr int LIM_L = LIM_THREADS / EPB;  // lanes per element in the indicator
-  using DG = dg_t<MIX>;
-  extern __shared__ __align__(16) double lsm_raw[];
-  DG *lsm = reinterpret_cast<DG *>(lsm_raw);
-  __shared__ Inst sI;
-  __shared__ int s_list[EPB];
-  __shared__ int s_n;
-  __shared__ Neighbour s_nb[2][EPB];
-  const int2 blkid = A.blocks[blockIdx.x];
-  load_inst(sI, A.insts + blkid.x);
-  if (threadIdx.x == 0) s_n = 0;
-  __syncthreads();
-  const Inst &I = sI;
-  if (I.limiter == ADG_LIM_NONE) return;
-  const int N = I.n_elem, nv = I.nv, ns = M.ns;
-  const int64_t nstep = *I.step;
-
-  // 1. stage the CTA's elements with a one-element halo (ghosts at walls) and
-  // the species fields in the variant's type; then the indicator, one element
-  // per thread
-  const int e0 = blkid.y, te = min(EPB, N - e0);
-  const int vs = (EPB + 2) * Q;
-  DG *spf = lsm;                                   // [SP_NFIELDS][ns]
-  DG *atn = spf + SP_NFIELDS * ns;                 // [2][EPB][nv] AT neighbour averages
-  DG *tile = atn + 2 * EPB * nv;               // [nv][EPB + 2][Q]
-  for (int k = threadIdx.x; k < SP_NFIELDS * ns; k += blockDim.x) spf[k] = (DG)M.sp[k];
-  if ((int)threadIdx.x < 2 * te) {
-    const int side = threadIdx.x / te, le = threadIdx.x - side * te;
-    s_nb[side][le] = neighbour_of(I, nstep, e0 + le, side);
-  }
-  {
-    // batches of loads in flight per thread before they are used
-    constexpr int BATCH = 8;
-    const bool periodic = (I.bc_left == ADG_BC_PERIODIC);
-    const int span = (te + 2) * Q, total = nv * span, nth = blockDim.x;
-    for (int base = threadIdx.x; base < total; base += BATCH * nth) {
-      double xs[BATCH];
-      int dst[BATCH];
-#pragma unroll
-      for (int b = 0; b < BATCH; ++b) {
-        const int idx = base + b * nth;
-        dst[b] = -1;
-        xs[b] = 0.0;
-        if (idx < total) {
-          const int v = idx / span, r = idx - v * span, le = r / Q, j = r - le * Q;
-          int src = e0 - 1 + le;
-          bool mirror = false;
-          if (src < 0 || src >= N) {
-            if (periodic) {
-              src = (src + N) % N;
-            } else {
-              const bool left = src < 0;
-              src = left ? 0 : N - 1;
-              mirror = ((left ? I.bc_left : I.bc_right) == ADG_BC_REFLECT);
-            }
-          }
-          xs[b] = I.wpre[((size_t)v * N + src) * Q + j];
-          if (mirror && (((j & 1) != 0) != (v == 0))) xs[b] = -xs[b];
-          dst[b] = v * vs + le * Q + j;
-        }
-      }
-#pragma unroll
-      for (int b = 0; b < BATCH; ++b)
-        if (dst[b] >= 0) tile[dst[b]] = (DG)xs[b];
-    }
-  }
-  __syncthreads();
-  // averages of the neighbours across delayed PE faces (Eq. 11), one
-  // (side, element, variable) per item
-  for (int item = threadIdx.x; item < 2 * te * nv; item += blockDim.x) {
-    const int side = item / (te * nv), r = item - side * te * nv, le = r / nv, v = r - le * nv;
-    const Neighbour &nb = s_nb[side][le];
-    if (nb.k > 0) atn[(side * EPB + le) * nv + v] = (DG)neighbour_mode(I, I.wpre, A.s, nstep, nb, v, 0, Q);
-  }
-  __syncthreads();
-  {
-    // every lane runs the indicator (shuffles); groups past the last element
-    // work on the first element and write nothing
-    const int le = threadIdx.x / LIM_L;
-    const bool valid = le < te;
-    const int lv = valid ? le : 0, e = e0 + lv;
-    const DG *atl = s_nb[0][lv].k > 0 ? atn + lv * nv : nullptr;
-    const DG *atr = s_nb[1][lv].k > 0 ? atn + (EPB + lv) * nv : nullptr;
-    const bool t = troubled_cell<Q, LIM_L, DG>(M, I, A.s, nstep, e, tile + (lv + 1) * Q, vs, spf,
-                                               atl, atr);
-    if (valid && threadIdx.x % LIM_L == 0) {
-      I.flags[(size_t)A.s * N + e] = t ? 1 : 0;
-      if (t) {
-        I.count[e] += 1;
-        s_list[atomicAdd(&s_n, 1)] = e;
-      }
-    }
-  }
-  __syncthreads();
-  const int n_tr = s_n;
-  if (n_tr == 0) return;
-
-  // 2. WENO (Eq. 9-10) on the troubled elements, G lanes each
-  const Basis &B = c_basis[Q - 2];
-  const BasisF &BF = c_basis_f[Q - 2];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gl = lane % G, gw = lane / G;
-  constexpr int EPW = 32 / G;
-  constexpr int NWARP = LIM_THREADS / 32;
-  const int slot = warp * EPW + gw;
-  double *A_wout = (A.s == 0) ? I.wa : (A.s == 1) ? I.wb : I.wn;
-  const double *A_wpre = I.wpre;
-  const unsigned FULL = 0xffffffffu;
-  const unsigned gmask = (G == 32) ? FULL : (0xffffu << (16 * gw));
-  const size_t VS = (size_t)N * Q;
-  const int NB = nv * Q;
-  DG *blk = tile + (size_t)nv * vs + (size_t)slot * limiter_elem_words(nv, ns, Q);  // [3][nv][Q]
-  DG *vlim = blk + 3 * NB;                                        // [nv][Q]
-  DG *gpv = vlim + NB;                                            // [3][Q]
-  DG *rsv = gpv + 3 * Q;                                          // [3][Q]
-  DG *mmv = rsv + 3 * Q;                                          // [3][Q]
-  DG *phi = mmv + 3 * Q;                                          // [ns]
-  DG *sums = phi + ns;                                            // [2][Q]
-  const DG *qWd = spf + SP_QW * ns, *cvWd = spf + SP_CVW * ns;
-  const DG *RWd = spf + SP_RW * ns, *cpWd = spf + SP_CPW * ns;
-  for (int base = 0; base < n_tr; base += NWARP * EPW) {
-    const int idx = base + slot;
-    const bool valid = idx < n_tr;
-    const int e = valid ? s_list[idx] : 0;
-    // the element and its neighbours (pre-limit, AT-extrapolated or ghost)
-    if (valid) {
-      const Neighbour nl = neighbour_of(I, nstep, e, 0), nr = neighbour_of(I, nstep, e, 1);
-      for (int t = gl; t < NB; t += G) {
-        const int v = t / Q, j = t - v * Q;
-        blk[t] = (DG)A_wpre[(size_t)v * VS + (size_t)e * Q + j];
-        blk[NB + t] = (DG)neighbour_mode(I, A_wpre, A.s, nstep, nl, v, j, Q);
-        blk[2 * NB + t] = (DG)neighbour_mode(I, A_wpre, A.s, nstep, nr, v, j, Q);
-      }
-    }
-    __syncwarp();
-    // cell-average thermo and eigen-quantities (species sums split over lanes)
-    DG rho = 0, qsum = 0, cv = 0, Rm = 0, cpm = 0;
-    if (valid)
-      for (int i = gl; i < ns; i += G) {
-        DG r = blk[(2 + i) * Q];
-        rho += r;
-        qsum = fma(r, qWd[i], qsum);
-        cv = fma(r, cvWd[i], cv);
-        Rm = fma(r, RWd[i], Rm);
-        cpm = fma(r, cpWd[i], cpm);
-      }
-    for (int o = G / 2; o > 0; o >>= 1) {
-      rho += __shfl_xor_sync(FULL, rho, o, G);
-      qsum += __shfl_xor_sync(FULL, qsum, o, G);
-      cv += __shfl_xor_sync(FULL, cv, o, G);
-      Rm += __shfl_xor_sync(FULL, Rm, o, G);
-      cpm += __shfl_xor_sync(FULL, cpm, o, G);
-    }
-    if (!valid) {
-      rho = 1;
-      cv = 1;
-      cpm = 2;
-      Rm = 1;
-    }
-    const DG irho = DG(1) / rho, icv = DG(1) / cv;
-    const DG m0 = valid ? blk[0] : DG(0), E0 = valid ? blk[Q] : DG(1);
-    const DG u = m0 * irho;
-    const DG T = (E0 - DG(0.5) * m0 * u - qsum) * icv;
-    const DG P = T * Rm;
-    const DG gam = cpm * icv, g = gam - DG(1);
-    const DG a = sqrt(gam * P * irho);
-    const DG H = (E0 + P) * irho;
-    const DG ia2 = DG(1) / (a * a);
-    if (valid)
-      for (int i = gl; i < ns; i += G)
-        phi[i] = fma(g, fma(-cvWd[i], T, DG(0.5) * u * u - qWd[i]), T * RWd[i]);
-    __syncwarp();
-    if (valid)
-      for (int t = gl; t < 3 * Q; t += G) {
-        int b = t / Q, j = t - b * Q;
-        const DG *x = blk + b * NB;
-        DG acc = g * fma(-u, x[j], x[Q + j]), sr = 0;
-        for (int i = 0; i < ns; ++i) {
-          DG r = x[(2 + i) * Q + j];
-          acc = fma(phi[i], r, acc);
-          sr += r;
-        }
-        gpv[t] = acc;
-        rsv[t] = sr;
-        mmv[t] = x[j];
-      }
-    __syncwarp();
-    const DG ha2 = DG(0.5) * ia2;
-    auto coef = [&](int k, DG &cA, DG &cB, DG &cC, DG &cD, int &ri) {
-      bool ac = (k == 0) || (k == nv - 1);
-      DG sgn = (k == 0) ? DG(-1) : DG(1);
-      ri = ac ? 0 : k - 1;
-      DG Yk = ac ? DG(0) : blk[(2 + ri) * Q] * irho;
-      cA = ac ? ha2 : -Yk * ia2;
-      cB = ac ? sgn * a * ha2 : DG(0);
-      cC = ac ? -sgn * a * u * ha2 : DG(0);
-      cD = ac ? DG(0) : DG(1);
-    };
-    auto val = [&](DG cA, DG cB, DG cC, DG cD, int ri, int b, int j) {
-      return fma(cA, gpv[b * Q + j],
-                 fma(cB, mmv[b * Q + j], fma(cC, rsv[b * Q + j], cD * blk[b * NB + (2 + ri) * Q + j])));
-    };
-    // WENO per characteristic field, the group's lanes over fields
-    const DG gmw[3] = {DG(0.001), DG(0.998), DG(0.001)};
-    const DG eps = DG(1e-6);
-    if (valid)
-      for (int k = gl; k < nv; k += G) {
-        DG cA, cB, cC, cD;
-        int ri;
-        coef(k, cA, cB, cC, cD, ri);
-        DG vo[Q], vl0[Q], vr0[Q], vl[Q], vr[Q];
-#pragma unroll
-        for (int j = 0; j < Q; ++j) {
-          vo[j] = val(cA, cB, cC, cD, ri, 0, j);
-          vl0[j] = val(cA, cB, cC, cD, ri, 1, j);
-          vr0[j] = val(cA, cB, cC, cD, ri, 2, j);
-        }
-        // neighbours continued into this cell, their mean replaced by the own mean
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          DG al = 0, ar = 0;
-#pragma unroll
-          for (int j = 0; j < Q; ++j) {
-            if constexpr (MIX) {
-              al = fma(BF.Sl[i][j], vl0[j], al);
-              ar = fma(BF.Sr[i][j], vr0[j], ar);
-            } else {
-              al = fma(B.Sl[i][j], vl0[j], al);
-              ar = fma(B.Sr[i][j], vr0[j], ar);
-            }
-          }
-          vl[i] = al;
-          vr[i] = ar;
-        }
-        vl[0] = vo[0];
-        vr[0] = vo[0];
-        DG be[3] = {0, 0, 0};
-#pragma unroll
-        for (int i = 1; i < Q; ++i)
-#pragma unroll
-          for (int j = 1; j < Q; ++j) {
-            DG bij = MIX ? (DG)BF.B[i][j] : (DG)B.B[i][j];
-            be[0] = fma(vl[i] * bij, vl[j], be[0]);
-            be[1] = fma(vo[i] * bij, vo[j], be[1]);
-            be[2] = fma(vr[i] * bij, vr[j], be[2]);
-          }
-        DG wt[3], sw = 0;
-        if constexpr (MIX) {
-          // the same normalised weights written as ratios, safe from overflow in FP32
-          DG dmin = fmin(eps + be[0], fmin(eps + be[1], eps + be[2]));
-          for (int t = 0; t < 3; ++t) {
-            DG rr = dmin / (eps + be[t]);
-            wt[t] = gmw[t] * rr * rr;
-            sw += wt[t];
-          }
-        } else {
-          for (int t = 0; t < 3; ++t) {
-            DG d = eps + be[t];
-            wt[t] = gmw[t] / (d * d);
-            sw += wt[t];
-          }
-        }
-        DG isw = DG(1) / sw;
-        vlim[k * Q] = vo[0];
-#pragma unroll
-        for (int i = 1; i < Q; ++i)
-          vlim[k * Q + i] = (wt[0] * vl[i] + wt[1] * vo[i] + wt[2] * vr[i]) * isw;
-      }
-    __syncwarp();
-    // back to conserved variables with R (modes >= 1; the cell average is kept)
-    if (valid)
-      for (int i = gl; i < Q; i += G) {
-        DG s1 = 0, s2 = 0;
-        for (int k = 1; k < nv - 1; ++k) {
-          DG x = vlim[k * Q + i];
-          s1 += x;
-          s2 = fma(x, u * u - phi[k - 1] / g, s2);
-        }
-        sums[i] = s1;
-        sums[Q + i] = s2;
-      }
-    __syncwarp();
-    if (valid) {
-      double *out = A_wout + (size_t)e * Q;
-      for (int t = gl; t < NB; t += G) {
-        int v = t / Q, i = t - v * Q;
-        if (i == 0) continue;
-        DG lm = vlim[i], lp = vlim[(nv - 1) * Q + i];
-        DG o;
-        if (v == 0) o = lm * (u - a) + lp * (u + a) + u * sums[i];
-        else if (v == 1) o = lm * (H - u * a) + lp * (H + u * a) + sums[Q + i];
-        else o = (lm + lp) * (blk[v * Q] * irho) + vlim[(v - 1) * Q + i];
-        out[(size_t)v * VS + i] = (double)o;
-      }
-    }
-    __syncwarp();
-  }
-  (void)gmask;
-}
 
 // L2 projection of primitive values at the Gauss points (Sec. 3.1): one thread
 // per (element, variable); prim layout [ns+3][N][Q] (T, P, u, Y_i).
@@ -981,19 +57,32 @@ __global__ void temperature_kernel(Mech M, Inst I, const double *w, double *T) {
 // host-side launchers
 
 cudaError_t upload_basis(const Basis *tables) {
-  cudaError_t e = cudaMemcpyToSymbol(c_basis, tables, sizeof(Basis) * ADG_MAX_P);
-  if (e != cudaSuccess) return e;
-  BasisF f[ADG_MAX_P];
-  for (int p = 0; p < ADG_MAX_P; ++p)
-    for (int i = 0; i < MAXQ; ++i)
-      for (int j = 0; j < MAXQ; ++j) {
-        f[p].B[i][j] = (float)tables[p].B[i][j];
-        f[p].Sl[i][j] = (float)tables[p].Sl[i][j];
-        f[p].Sr[i][j] = (float)tables[p].Sr[i][j];
-        f[p].WdP[i][j] = (float)tables[p].WdP[i][j];
-        f[p].WPh[i][j] = (float)tables[p].WPh[i][j];
-      }
-  return cudaMemcpyToSymbol(c_basis_f, f, sizeof(BasisF) * ADG_MAX_P);
+  cudaError_t e = upload_unit_tables(tables);
+  if (e == cudaSuccess) e = upload_tables_fp64(tables);
+  if (e == cudaSuccess) e = upload_tables_mixed(tables);
+  return e;
+}
+
+cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, bool mixed, int n_tiles,
+                         cudaStream_t st) {
+  return mixed ? launch_stage_mixed(M, A, Q, n_tiles, st) : launch_stage_fp64(M, A, Q, n_tiles, st);
+}
+
+cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, bool mixed, int nv,
+                           int n_blocks, cudaStream_t st) {
+  return mixed ? launch_limiter_mixed(M, A, Q, nv, n_blocks, st)
+               : launch_limiter_fp64(M, A, Q, nv, n_blocks, st);
+}
+
+// Raise the dynamic shared-memory limit of every kernel instance (before any
+// launch or stream capture).
+cudaError_t prepare_kernels(int nv, int ns, int nr) {
+  (void)nv;
+  (void)ns;
+  (void)nr;
+  cudaError_t e = prepare_fp64();
+  if (e == cudaSuccess) e = prepare_mixed();
+  return e;
 }
 
 int stage_tile(const Mech &M, int Q, int O, bool mixed) {
@@ -1014,129 +103,11 @@ size_t stage_smem(const Mech &M, int TE, int Q, int O, bool mixed) {
   return stage_smem_bytes(TE, Q, M.ns, M.nr, M.nterm, O, mixed);
 }
 
-template <int Q, bool MIX>
-static cudaError_t launch_stage_qm(const Mech &M, const StageArgs &A, int n_tiles,
-                                   cudaStream_t st) {
-  size_t smem = stage_smem_bytes(A.TE, Q, M.ns, M.nr, M.nterm, A.O, MIX);
-  if (A.NT < 32 || A.NT > 512 || A.NT % 32) return cudaErrorInvalidValue;
-  stage_kernel<Q, MIX><<<n_tiles, A.NT, smem, st>>>(M, A);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, bool mixed, int n_tiles,
-                         cudaStream_t st) {
-  switch (Q * 2 + (mixed ? 1 : 0)) {
-    case 4: return launch_stage_qm<2, false>(M, A, n_tiles, st);
-    case 5: return launch_stage_qm<2, true>(M, A, n_tiles, st);
-    case 6: return launch_stage_qm<3, false>(M, A, n_tiles, st);
-    case 7: return launch_stage_qm<3, true>(M, A, n_tiles, st);
-    case 8: return launch_stage_qm<4, false>(M, A, n_tiles, st);
-    case 9: return launch_stage_qm<4, true>(M, A, n_tiles, st);
-    case 10: return launch_stage_qm<5, false>(M, A, n_tiles, st);
-    case 11: return launch_stage_qm<5, true>(M, A, n_tiles, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
 int limiter_elems_per_block(int64_t n_elem_group, bool mixed) {
   // 16 elements per CTA (8 lanes each) while 32 would give fewer than two CTAs
   // per SM, in the mixed variant only: in FP64 the lanes of an element repeat
   // its FP64 divisions and square root, which costs more than the latency saved
   return mixed && n_elem_group < (int64_t)2 * 152 * LIM_EPB_MAX ? 16 : LIM_EPB_MAX;
-}
-
-template <int Q, int G, bool MIX, int EPB>
-static cudaError_t launch_limiter_qgme(const Mech &M, const LimArgs &A, int nv, int n_blocks,
-                                       cudaStream_t st) {
-  constexpr int EPW = 32 / G;
-  size_t smem = ((size_t)SP_NFIELDS * M.ns + (size_t)2 * EPB * nv + (size_t)nv * (EPB + 2) * Q +
-                 (size_t)(LIM_THREADS / 32) * EPW * limiter_elem_words(nv, M.ns, Q)) *
-                (MIX ? sizeof(float) : sizeof(double));
-  smem = (smem + 15) & ~(size_t)15;
-  limiter_kernel<Q, G, MIX, EPB><<<n_blocks, LIM_THREADS, smem, st>>>(M, A);
-  return cudaGetLastError();
-}
-
-template <int Q, bool MIX>
-static cudaError_t launch_limiter_qm(const Mech &M, const LimArgs &A, int nv, int n_blocks,
-                                     cudaStream_t st) {
-  if (A.EPB == 16) {
-    if (nv <= 16) return launch_limiter_qgme<Q, 16, MIX, 16>(M, A, nv, n_blocks, st);
-    return launch_limiter_qgme<Q, 32, MIX, 16>(M, A, nv, n_blocks, st);
-  }
-  if (A.EPB != LIM_EPB_MAX) return cudaErrorInvalidValue;
-  if (nv <= 16) return launch_limiter_qgme<Q, 16, MIX, LIM_EPB_MAX>(M, A, nv, n_blocks, st);
-  return launch_limiter_qgme<Q, 32, MIX, LIM_EPB_MAX>(M, A, nv, n_blocks, st);
-}
-
-cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, bool mixed, int nv,
-                           int n_blocks, cudaStream_t st) {
-  switch (Q * 2 + (mixed ? 1 : 0)) {
-    case 4: return launch_limiter_qm<2, false>(M, A, nv, n_blocks, st);
-    case 5: return launch_limiter_qm<2, true>(M, A, nv, n_blocks, st);
-    case 6: return launch_limiter_qm<3, false>(M, A, nv, n_blocks, st);
-    case 7: return launch_limiter_qm<3, true>(M, A, nv, n_blocks, st);
-    case 8: return launch_limiter_qm<4, false>(M, A, nv, n_blocks, st);
-    case 9: return launch_limiter_qm<4, true>(M, A, nv, n_blocks, st);
-    case 10: return launch_limiter_qm<5, false>(M, A, nv, n_blocks, st);
-    case 11: return launch_limiter_qm<5, true>(M, A, nv, n_blocks, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
-// Raise the dynamic shared-memory limit of every kernel instance (before any
-// launch or stream capture).
-cudaError_t prepare_kernels(int nv, int ns, int nr) {
-  (void)nv;
-  (void)ns;
-  (void)nr;
-  const int lim = 200 * 1024;
-  cudaError_t e = cudaSuccess;
-#define SET(...) \
-  if (e == cudaSuccess)     \
-  e = cudaFuncSetAttribute(__VA_ARGS__, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
-  SET(stage_kernel<2, false>);
-  SET(stage_kernel<3, false>);
-  SET(stage_kernel<4, false>);
-  SET(stage_kernel<5, false>);
-  SET(stage_kernel<2, true>);
-  SET(stage_kernel<3, true>);
-  SET(stage_kernel<4, true>);
-  SET(stage_kernel<5, true>);
-  SET(limiter_kernel<2, 16, false, 16>);
-  SET(limiter_kernel<3, 16, false, 16>);
-  SET(limiter_kernel<4, 16, false, 16>);
-  SET(limiter_kernel<5, 16, false, 16>);
-  SET(limiter_kernel<2, 32, false, 16>);
-  SET(limiter_kernel<3, 32, false, 16>);
-  SET(limiter_kernel<4, 32, false, 16>);
-  SET(limiter_kernel<5, 32, false, 16>);
-  SET(limiter_kernel<2, 16, true, 16>);
-  SET(limiter_kernel<3, 16, true, 16>);
-  SET(limiter_kernel<4, 16, true, 16>);
-  SET(limiter_kernel<5, 16, true, 16>);
-  SET(limiter_kernel<2, 32, true, 16>);
-  SET(limiter_kernel<3, 32, true, 16>);
-  SET(limiter_kernel<4, 32, true, 16>);
-  SET(limiter_kernel<5, 32, true, 16>);
-  SET(limiter_kernel<2, 16, false, 32>);
-  SET(limiter_kernel<3, 16, false, 32>);
-  SET(limiter_kernel<4, 16, false, 32>);
-  SET(limiter_kernel<5, 16, false, 32>);
-  SET(limiter_kernel<2, 32, false, 32>);
-  SET(limiter_kernel<3, 32, false, 32>);
-  SET(limiter_kernel<4, 32, false, 32>);
-  SET(limiter_kernel<5, 32, false, 32>);
-  SET(limiter_kernel<2, 16, true, 32>);
-  SET(limiter_kernel<3, 16, true, 32>);
-  SET(limiter_kernel<4, 16, true, 32>);
-  SET(limiter_kernel<5, 16, true, 32>);
-  SET(limiter_kernel<2, 32, true, 32>);
-  SET(limiter_kernel<3, 32, true, 32>);
-  SET(limiter_kernel<4, 32, true, 32>);
-  SET(limiter_kernel<5, 32, true, 32>);
-#undef SET
-  return e;
 }
 
 __global__ void advance_kernel(int64_t *steps, int n) {
