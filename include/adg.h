@@ -40,6 +40,7 @@ extern "C" {
 #define ADG_ERR_NONPHYSICAL -4  /* density, temperature or state not finite/positive */
 #define ADG_ERR_HISTORY -5      /* a delayed level is missing from the history ring */
 #define ADG_ERR_NOLIB -6        /* no CUDA device is available */
+#define ADG_ERR_TIMEOUT -7      /* a wait of the unsynchronised mode gave up */
 
 #define ADG_BC_PERIODIC 0
 #define ADG_BC_REFLECT 1
@@ -191,6 +192,41 @@ int adg_set_tuning(adg_ctx *ctx, int group, int elements_per_tile, int threads_p
 int adg_launches_per_step(const adg_ctx *ctx);
 
 const char *adg_error_string(int code);
+
+/* Truly unsynchronised mode (the emulated PEs run without any lockstep; the
+ * seeded CAA/SAA delays of Sec. 4 are replaced by the delays that actually
+ * occur). adg_step_unsync advances instance `instance` by n_steps SSP-RK3 steps
+ * in one cooperative launch with one CTA per PE. A PE publishes, per step and
+ * stage, its stage input's traces at its PE faces and the pre-limit output of
+ * its PE-boundary elements to the history rings, and observes the delay
+ * k = max(0, n - L) of the newest level L its neighbour has published. The
+ * flux at a PE face (Eq. 7) uses one delay on both sides, the common (older)
+ * level of Sec. 3.2: the first side to reach step n and stage s fixes k from
+ * the other side's newest level and the second adopts it, so the flux stays
+ * single-valued and the scheme conservative. The AT-WENO neighbour (Eq. 11) of
+ * each side takes the delay that side observed. No PE runs more than the
+ * config's max_delay steps ahead of a neighbour (it waits); until the levels an
+ * AT extrapolation needs exist, it waits for k = 0. The result depends on
+ * timing and is not reproducible; with max_delay = 0 it reproduces adg_step's
+ * synchronous result exactly. Asynchronous on `stream`; the instance's step
+ * counter advances by n_steps. One unsynchronised launch per context may be in
+ * flight at a time. ADG_ERR_ARG for a bad instance or more PEs than fit on the
+ * GPU at once; a wait that does not end within the bound set by
+ * adg_set_unsync_wait stops the launch and reports ADG_ERR_TIMEOUT through
+ * adg_status.
+ * adg_unsync_delays copies the histogram of the delays used since the last
+ * call into hist[2][ADG_MAX_DELAY + 1] (row 0: flux, row 1: limiter; one count
+ * per PE face side and stage) and clears it (synchronous). */
+int adg_step_unsync(adg_ctx *ctx, int instance, int n_steps, void *stream);
+int adg_unsync_delays(adg_ctx *ctx, uint64_t *hist);
+
+/* Bound of every wait of the unsynchronised mode, in polls of a counter
+ * (default 2^22, a few seconds), and a PE that never publishes anything
+ * (withheld_pe >= 0; -1, the default, for none): with it set, the PEs that wait
+ * on it give up after max_polls polls and the launch ends with ADG_ERR_TIMEOUT,
+ * which is how the timeout path is tested. ADG_ERR_ARG for max_polls < 0 or
+ * withheld_pe < -1. */
+int adg_set_unsync_wait(adg_ctx *ctx, long long max_polls, int withheld_pe);
 
 /* ---------------------------------------------------------------------------
  * Time step without any device allocation. The paper has no counterpart: this

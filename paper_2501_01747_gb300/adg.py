@@ -19,13 +19,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libadg.so")
-SOURCES = ["adg_k64.cu", "adg_k32.cu", "adg_kernels.cu", "adg_api.cu", "adg_static.cu"]
+SOURCES = ["adg_k64.cu", "adg_k32.cu", "adg_unsync.cu", "adg_kernels.cu", "adg_api.cu",
+           "adg_static.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", ARCH]
 
 ADG_OK = 0
 ERRORS = {-1: "ADG_ERR_ARG", -2: "ADG_ERR_CUDA", -3: "ADG_ERR_NOMEM",
-          -4: "ADG_ERR_NONPHYSICAL", -5: "ADG_ERR_HISTORY", -6: "ADG_ERR_NOLIB"}
+          -4: "ADG_ERR_NONPHYSICAL", -5: "ADG_ERR_HISTORY", -6: "ADG_ERR_NOLIB",
+          -7: "ADG_ERR_TIMEOUT"}
+MAX_DELAY = 7  # ADG_MAX_DELAY
 
 
 class AdgError(RuntimeError):
@@ -99,7 +102,8 @@ EXPORTS = ["adg_workspace_bytes", "adg_create", "adg_destroy", "adg_set_primitiv
            "adg_delay_table", "adg_launches_per_step", "adg_error_string",
            "adg_write_state", "adg_read_state", "adg_enable_kernel_timing",
            "adg_kernel_times", "adg_step_noalloc", "adg_autotune", "adg_get_tuning",
-           "adg_set_tuning"]
+           "adg_set_tuning", "adg_step_unsync", "adg_unsync_delays",
+           "adg_set_unsync_wait"]
 
 
 def lib(path: str | None = None):
@@ -139,6 +143,9 @@ def lib(path: str | None = None):
     L.adg_autotune.argtypes = [vp, vp]
     L.adg_get_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.adg_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+    L.adg_step_unsync.argtypes = [vp, C.c_int, C.c_int, vp]
+    L.adg_unsync_delays.argtypes = [vp, C.POINTER(C.c_uint64)]
+    L.adg_set_unsync_wait.argtypes = [vp, C.c_longlong, C.c_int]
     L.adg_error_string.restype = C.c_char_p
     L.adg_error_string.argtypes = [C.c_int]
     _lib = L
@@ -374,6 +381,26 @@ class ADG:
         _check(self.L.adg_set_tuning(self.h, int(group), int(elements_per_tile),
                                      int(threads_per_cta)), "adg_set_tuning")
         return self.tuning()
+
+    def step_unsync(self, n=1, k=0, stream=None):
+        """n steps of instance k in the truly unsynchronised mode (one CTA per PE,
+        each PE using the newest level its neighbours have published)."""
+        _check(self.L.adg_step_unsync(self.h, self._k(k), int(n), self._stream(stream)),
+               "adg_step_unsync")
+
+    def set_unsync_wait(self, max_polls=1 << 22, withheld_pe=-1):
+        """Bound of the unsynchronised mode's waits (polls of a counter), and a PE
+        that never publishes (to exercise the timeout), -1 for none."""
+        _check(self.L.adg_set_unsync_wait(self.h, int(max_polls), int(withheld_pe)),
+               "adg_set_unsync_wait")
+
+    def unsync_delays(self):
+        """Delays used by the unsynchronised mode since the last call: array
+        [2][MAX_DELAY + 1] (row 0: flux, row 1: limiter)."""
+        h = np.zeros(2 * (MAX_DELAY + 1), dtype=np.uint64)
+        _check(self.L.adg_unsync_delays(self.h, h.ctypes.data_as(C.POINTER(C.c_uint64))),
+               "adg_unsync_delays")
+        return h.reshape(2, MAX_DELAY + 1)
 
     def launches_per_step(self):
         return int(self.L.adg_launches_per_step(self.h))

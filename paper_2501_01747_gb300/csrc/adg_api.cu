@@ -188,6 +188,7 @@ struct InstHost {
   Inst d;         // device view (a copy lives in the device instance table)
   int64_t n;      // steps done (host mirror of the device counter)
   double *prim;   // staging for projection / temperature
+  int n_pe;       // PEs of the instance
 };
 
 // Instances of one polynomial degree and precision share the stage and limiter
@@ -228,6 +229,11 @@ struct adg_ctx {
   bool owns_mem;
   size_t bytes;
   int *err_all;   // device error words [n_inst][4]
+  int *pub_in, *pub_pre;         // unsynchronised mode: stages published per PE [max PEs]
+  unsigned long long *agree;     // unsynchronised mode: common flux levels [max PEs][3][MAXD + 1]
+  unsigned long long *delay_hist;  // unsynchronised mode: delays observed [2][MAXD + 1]
+  long long unsync_polls;        // unsynchronised mode: polls before a wait gives up
+  int unsync_withheld;           // unsynchronised mode: PE that never publishes, or -1
   cudaStream_t last_stream;
   cudaStream_t cap_stream;       // private stream for graph capture
   cudaGraph_t graph;
@@ -307,6 +313,12 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
   ctx->err_all = (int *)cv.take(sizeof(int) * 4 * ctx->n_inst);
   ctx->d_insts = (Inst *)cv.take(sizeof(Inst) * ctx->n_inst);
   ctx->d_steps = (int64_t *)cv.take(sizeof(int64_t) * ctx->n_inst);
+  int max_pe = 1;
+  for (int k = 0; k < ctx->n_inst; ++k) max_pe = cfgs[k].n_pe > max_pe ? cfgs[k].n_pe : max_pe;
+  ctx->pub_in = (int *)cv.take(sizeof(int) * max_pe);
+  ctx->pub_pre = (int *)cv.take(sizeof(int) * max_pe);
+  ctx->agree = (unsigned long long *)cv.take(sizeof(unsigned long long) * max_pe * 3 * (MAXD + 1));
+  ctx->delay_hist = (unsigned long long *)cv.take(sizeof(unsigned long long) * 2 * (MAXD + 1));
   // groups of equal degree and precision: tile sizes and tables
   ctx->n_groups = 0;
   for (int gk = 0; gk < ADG_MAX_GROUPS; ++gk) {
@@ -358,7 +370,9 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
     I.wa = (double *)cv.take(sizeof(double) * st);
     I.wb = (double *)cv.take(sizeof(double) * st);
     I.wpre = (double *)cv.take(sizeof(double) * st);
-    size_t rs = (size_t)(c.max_delay + c.at_order) * 3 * (npf > 0 ? npf : 1) * 2 * nv;
+    // ring depth 2d + o: the synchronous modes need d + o levels, the
+    // unsynchronised one up to 2d + o (a neighbour may run d steps ahead)
+    size_t rs = (size_t)(2 * c.max_delay + c.at_order) * 3 * (npf > 0 ? npf : 1) * 2 * nv;
     I.ring_in = (double *)cv.take(sizeof(double) * rs);
     I.ring_pre = (double *)cv.take(sizeof(double) * rs * Q);
     I.flags = (uint8_t *)cv.take((size_t)3 * N);
@@ -399,6 +413,7 @@ const char *adg_error_string(int code) {
     case ADG_ERR_NONPHYSICAL: return "non-physical state (density or temperature)";
     case ADG_ERR_HISTORY: return "delayed level missing from the history ring";
     case ADG_ERR_NOLIB: return "no CUDA device";
+    case ADG_ERR_TIMEOUT: return "a wait of the unsynchronised mode gave up";
   }
   return "unknown error";
 }
@@ -468,6 +483,8 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
   ctx->mech.nterm = count_terms(mech);
   ctx->inst.resize(n);
   ctx->last_stream = 0;
+  ctx->unsync_polls = 1ll << 22;  // polls of ~0.5 us: a few seconds
+  ctx->unsync_withheld = -1;
   ctx->err_all = nullptr;
   ctx->ev_used = 0;
   ctx->timing = false;
@@ -521,7 +538,9 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
                                    cudaMemcpyHostToDevice)))
       rc2 = ADG_ERR_CUDA;
   }
-  if (cudaMemset(ctx->err_all, 0, sizeof(int) * 4 * n)) rc2 = ADG_ERR_CUDA;
+  if (cudaMemset(ctx->err_all, 0, sizeof(int) * 4 * n) ||
+      cudaMemset(ctx->delay_hist, 0, sizeof(unsigned long long) * 2 * (MAXD + 1)))
+    rc2 = ADG_ERR_CUDA;
   // basis tables in constant memory
   {
     Basis tables[ADG_MAX_P];
@@ -538,7 +557,7 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
     I.p = c.p;
     I.nv = nv;
     I.npf = npf;
-    I.depth = c.max_delay + c.at_order;
+    I.depth = 2 * c.max_delay + c.at_order;
     I.at_order = c.at_order;
     I.bc_left = c.bc_left;
     I.bc_right = c.bc_right;
@@ -581,6 +600,7 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
         cudaMemset(I.wn, 0, sizeof(double) * (size_t)nv * N * Q))
       rc2 = ADG_ERR_CUDA;
     h.n = 0;
+    h.n_pe = c.n_pe;
     I.step = ctx->d_steps + k;
   }
   if (rc2 == ADG_OK) {
@@ -926,6 +946,58 @@ int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning) {
     tuning[5 * gi + 3] = G.NT;
     tuning[5 * gi + 4] = G.n_tiles;
   }
+  return ADG_OK;
+}
+
+int adg_step_unsync(adg_ctx *ctx, int instance, int n_steps, void *stream) {
+  if (!ctx || instance < 0 || instance >= ctx->n_inst || n_steps < 0) return ADG_ERR_ARG;
+  if (n_steps == 0) return ADG_OK;
+  InstHost &h = ctx->inst[instance];
+  const Inst &I = h.d;
+  const int Q = I.p + 1;
+  const bool mixed = I.mixed != 0;
+  const Group *G = nullptr;
+  for (int gi = 0; gi < ctx->n_groups; ++gi)
+    if (ctx->groups[gi].Q == Q && ctx->groups[gi].mixed == mixed) G = &ctx->groups[gi];
+  if (!G) return ADG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  UnsyncArgs U;
+  U.inst = ctx->d_insts + instance;
+  U.n_pe = h.n_pe;
+  U.npf = I.npf;
+  U.n_steps = n_steps;
+  U.TE = G->TE;
+  U.O = G->O;
+  U.pub_in = ctx->pub_in;
+  U.pub_pre = ctx->pub_pre;
+  U.agree = ctx->agree;
+  U.hist = ctx->delay_hist;
+  U.spin_limit = ctx->unsync_polls;
+  U.withheld = ctx->unsync_withheld;
+  cudaError_t e = launch_unsync(ctx->mech, U, Q, mixed, I.nv, st);
+  if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorInvalidValue) {
+    cudaGetLastError();
+    return ADG_ERR_ARG;
+  }
+  CK(e);
+  CK(launch_advance_by(I.step, n_steps, st));
+  h.n += n_steps;
+  return ADG_OK;
+}
+
+int adg_set_unsync_wait(adg_ctx *ctx, long long max_polls, int withheld_pe) {
+  if (!ctx || max_polls < 0 || withheld_pe < -1) return ADG_ERR_ARG;
+  ctx->unsync_polls = max_polls;
+  ctx->unsync_withheld = withheld_pe;
+  return ADG_OK;
+}
+
+int adg_unsync_delays(adg_ctx *ctx, uint64_t *hist) {
+  if (!ctx || !hist) return ADG_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->last_stream));
+  CK(cudaMemcpy(hist, ctx->delay_hist, sizeof(uint64_t) * 2 * (MAXD + 1), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(ctx->delay_hist, 0, sizeof(uint64_t) * 2 * (MAXD + 1)));
   return ADG_OK;
 }
 

@@ -86,6 +86,15 @@ struct PeDelays {
   int k[2];
 };
 
+// A value of the history ring. Written by another CTA of the same launch in the
+// unsynchronised mode, so read from L2 (the point of coherence), not from a
+// possibly stale L1 line of an earlier level in the same slot.
+template <bool UNSYNC>
+__device__ __forceinline__ double ring_load(const double *p) {
+  if constexpr (UNSYNC) return __ldcg(p);
+  else return *p;
+}
+
 // Stage s of one tile: elements [e0, e0 + te) of instance I at step level nstep.
 // With UNSYNC the PE faces of the tile take the delays pd->k observed by a PE
 // that runs without synchronisation and read both sides from the history ring,
@@ -316,10 +325,10 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       const int64_t lv = nstep - k - m;
       const double *bl = I.ring_in + ring_trace(I, lv, A.s, pf, 0);
       const double *br = I.ring_in + ring_trace(I, lv, A.s, pf, 1);
-      if constexpr (MIX) {
+      if constexpr (MIX || UNSYNC) {
         for (int v = 0; v < nv; ++v) {
-          wl[v] = (DG)bl[v];
-          wr[v] = (DG)br[v];
+          wl[v] = (DG)ring_load<UNSYNC>(bl + v);
+          wr[v] = (DG)ring_load<UNSYNC>(br + v);
         }
         num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
       } else {
@@ -514,13 +523,15 @@ __device__ inline Neighbour neighbour_of(const Inst &I, int64_t nstep, int e, in
 
 // Mode j of variable v of a neighbour (from the ring: the sum of the AT levels
 // in FP64).
+template <bool UNSYNC>
 __device__ inline double neighbour_mode(const Inst &I, const double *wpre, int s, int64_t nstep,
                                         const Neighbour &nb, int v, int j, int Q) {
   if (nb.ring) {
     double acc = 0.0;
     for (int m = 0; m < (nb.k > 0 ? I.at_order : 1); ++m)
-      acc += I.at[nb.k][m] *
-             I.ring_pre[ring_block(I, nstep - nb.k - m, s, nb.pf, nb.side) + (size_t)v * Q + j];
+      acc += I.at[nb.k][m] * ring_load<UNSYNC>(I.ring_pre + ring_block(I, nstep - nb.k - m, s,
+                                                                        nb.pf, nb.side) +
+                                               (size_t)v * Q + j);
     return acc;
   }
   double x = wpre[((size_t)v * I.n_elem + nb.src) * Q + j];
@@ -748,7 +759,9 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
   for (int item = threadIdx.x; item < 2 * te * nv; item += blockDim.x) {
     const int side = item / (te * nv), r = item - side * te * nv, le = r / nv, v = r - le * nv;
     const Neighbour &nb = s_nb[side][le];
-    if (nb.ring) atn[(side * EPB + le) * nv + v] = (DG)neighbour_mode(I, I.wpre, A.s, nstep, nb, v, 0, Q);
+    if (nb.ring)
+      atn[(side * EPB + le) * nv + v] =
+          (DG)neighbour_mode<UNSYNC>(I, I.wpre, A.s, nstep, nb, v, 0, Q);
   }
   __syncthreads();
   {
@@ -807,8 +820,8 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
       for (int t = gl; t < NB; t += G) {
         const int v = t / Q, j = t - v * Q;
         blk[t] = (DG)A_wpre[(size_t)v * VS + (size_t)e * Q + j];
-        blk[NB + t] = (DG)neighbour_mode(I, A_wpre, A.s, nstep, nl, v, j, Q);
-        blk[2 * NB + t] = (DG)neighbour_mode(I, A_wpre, A.s, nstep, nr, v, j, Q);
+        blk[NB + t] = (DG)neighbour_mode<UNSYNC>(I, A_wpre, A.s, nstep, nl, v, j, Q);
+        blk[2 * NB + t] = (DG)neighbour_mode<UNSYNC>(I, A_wpre, A.s, nstep, nr, v, j, Q);
       }
     }
     __syncwarp();

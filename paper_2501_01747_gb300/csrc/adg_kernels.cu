@@ -60,6 +60,7 @@ cudaError_t upload_basis(const Basis *tables) {
   cudaError_t e = upload_unit_tables(tables);
   if (e == cudaSuccess) e = upload_tables_fp64(tables);
   if (e == cudaSuccess) e = upload_tables_mixed(tables);
+  if (e == cudaSuccess) e = upload_tables_unsync(tables);
   return e;
 }
 
@@ -82,6 +83,7 @@ cudaError_t prepare_kernels(int nv, int ns, int nr) {
   (void)nr;
   cudaError_t e = prepare_fp64();
   if (e == cudaSuccess) e = prepare_mixed();
+  if (e == cudaSuccess) e = prepare_unsync();
   return e;
 }
 
@@ -113,6 +115,13 @@ int limiter_elems_per_block(int64_t n_elem_group, bool mixed) {
 __global__ void advance_kernel(int64_t *steps, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) steps[i] += 1;
+}
+
+__global__ void advance_by_kernel(int64_t *step, int64_t n) { *step += n; }
+
+cudaError_t launch_advance_by(int64_t *step, int64_t n, cudaStream_t st) {
+  advance_by_kernel<<<1, 1, 0, st>>>(step, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_advance(int64_t *steps, int n, cudaStream_t st) {
