@@ -228,6 +228,13 @@ int adg_unsync_delays(adg_ctx *ctx, uint64_t *hist);
  * withheld_pe < -1. */
 int adg_set_unsync_wait(adg_ctx *ctx, long long max_polls, int withheld_pe);
 
+/* Emulated load imbalance for the unsynchronised mode (Sec. 3.2 names load
+ * imbalance as a source of delays): PE slow_pe idles about slow_us microseconds
+ * per stage before it publishes, so its neighbours run ahead of it and observe
+ * delays up to max_delay. slow_pe = -1 (the default) for none. ADG_ERR_ARG for
+ * slow_pe < -1 or slow_us outside [0, 10000]. */
+int adg_set_unsync_imbalance(adg_ctx *ctx, int slow_pe, int slow_us);
+
 /* ---------------------------------------------------------------------------
  * Time step without any device allocation. The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc, for instance code

@@ -19,8 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libadg.so")
-SOURCES = ["adg_k64.cu", "adg_k32.cu", "adg_unsync.cu", "adg_kernels.cu", "adg_api.cu",
-           "adg_static.cu"]
+SOURCES = ["adg_k64.cu", "adg_k32.cu", "adg_u64.cu", "adg_u32.cu", "adg_kernels.cu",
+           "adg_api.cu", "adg_static.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", ARCH]
 
@@ -103,7 +103,7 @@ EXPORTS = ["adg_workspace_bytes", "adg_create", "adg_destroy", "adg_set_primitiv
            "adg_write_state", "adg_read_state", "adg_enable_kernel_timing",
            "adg_kernel_times", "adg_step_noalloc", "adg_autotune", "adg_get_tuning",
            "adg_set_tuning", "adg_step_unsync", "adg_unsync_delays",
-           "adg_set_unsync_wait"]
+           "adg_set_unsync_wait", "adg_set_unsync_imbalance"]
 
 
 def lib(path: str | None = None):
@@ -146,6 +146,7 @@ def lib(path: str | None = None):
     L.adg_step_unsync.argtypes = [vp, C.c_int, C.c_int, vp]
     L.adg_unsync_delays.argtypes = [vp, C.POINTER(C.c_uint64)]
     L.adg_set_unsync_wait.argtypes = [vp, C.c_longlong, C.c_int]
+    L.adg_set_unsync_imbalance.argtypes = [vp, C.c_int, C.c_int]
     L.adg_error_string.restype = C.c_char_p
     L.adg_error_string.argtypes = [C.c_int]
     _lib = L
@@ -393,6 +394,12 @@ class ADG:
         that never publishes (to exercise the timeout), -1 for none."""
         _check(self.L.adg_set_unsync_wait(self.h, int(max_polls), int(withheld_pe)),
                "adg_set_unsync_wait")
+
+    def set_unsync_imbalance(self, slow_pe=-1, slow_us=0):
+        """PE slow_pe idles about slow_us microseconds per stage in the
+        unsynchronised mode (emulated load imbalance); -1 for none."""
+        _check(self.L.adg_set_unsync_imbalance(self.h, int(slow_pe), int(slow_us)),
+               "adg_set_unsync_imbalance")
 
     def unsync_delays(self):
         """Delays used by the unsynchronised mode since the last call: array

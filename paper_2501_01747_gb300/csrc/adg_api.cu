@@ -234,6 +234,7 @@ struct adg_ctx {
   unsigned long long *delay_hist;  // unsynchronised mode: delays observed [2][MAXD + 1]
   long long unsync_polls;        // unsynchronised mode: polls before a wait gives up
   int unsync_withheld;           // unsynchronised mode: PE that never publishes, or -1
+  int unsync_slow_pe, unsync_slow_us;  // unsynchronised mode: emulated load imbalance
   cudaStream_t last_stream;
   cudaStream_t cap_stream;       // private stream for graph capture
   cudaGraph_t graph;
@@ -485,6 +486,8 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
   ctx->last_stream = 0;
   ctx->unsync_polls = 1ll << 22;  // polls of ~0.5 us: a few seconds
   ctx->unsync_withheld = -1;
+  ctx->unsync_slow_pe = -1;
+  ctx->unsync_slow_us = 0;
   ctx->err_all = nullptr;
   ctx->ev_used = 0;
   ctx->timing = false;
@@ -969,12 +972,15 @@ int adg_step_unsync(adg_ctx *ctx, int instance, int n_steps, void *stream) {
   U.n_steps = n_steps;
   U.TE = G->TE;
   U.O = G->O;
+  U.EPB = G->EPB;
   U.pub_in = ctx->pub_in;
   U.pub_pre = ctx->pub_pre;
   U.agree = ctx->agree;
   U.hist = ctx->delay_hist;
   U.spin_limit = ctx->unsync_polls;
   U.withheld = ctx->unsync_withheld;
+  U.slow_pe = ctx->unsync_slow_pe;
+  U.slow_us = ctx->unsync_slow_us;
   cudaError_t e = launch_unsync(ctx->mech, U, Q, mixed, I.nv, st);
   if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorInvalidValue) {
     cudaGetLastError();
@@ -990,6 +996,13 @@ int adg_set_unsync_wait(adg_ctx *ctx, long long max_polls, int withheld_pe) {
   if (!ctx || max_polls < 0 || withheld_pe < -1) return ADG_ERR_ARG;
   ctx->unsync_polls = max_polls;
   ctx->unsync_withheld = withheld_pe;
+  return ADG_OK;
+}
+
+int adg_set_unsync_imbalance(adg_ctx *ctx, int slow_pe, int slow_us) {
+  if (!ctx || slow_pe < -1 || slow_us < 0 || slow_us > 10000) return ADG_ERR_ARG;
+  ctx->unsync_slow_pe = slow_pe;
+  ctx->unsync_slow_us = slow_us;
   return ADG_OK;
 }
 

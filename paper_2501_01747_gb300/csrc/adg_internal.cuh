@@ -292,20 +292,30 @@ cudaError_t prepare_mixed();
 cudaError_t upload_tables_fp64(const Basis *tables);
 cudaError_t upload_tables_mixed(const Basis *tables);
 int limiter_elems_per_block(int64_t n_elem_group, bool mixed);
-// the unsynchronised mode (adg_unsync.cu): one cooperative launch per instance
+// the unsynchronised mode (adg_unsync.cuh): one cooperative launch per instance
 struct UnsyncArgs {
   const Inst *inst;               // the instance's device record
   int n_pe, npf, n_steps, TE, O;  // PEs, PE faces, steps, elements per stage tile, AT levels
+  int EPB;                        // elements per limiter block (as the group's launches)
   int *pub_in, *pub_pre;          // [n_pe] stages published (stage inputs, pre-limit outputs)
   unsigned long long *agree;      // [npf][3][MAXD + 1] common flux level: (level + 1) << 8 | k
   unsigned long long *hist;       // [2][MAXD + 1] delays observed: flux, limiter
   long long spin_limit;           // polls of a counter before a wait gives up
   int withheld;                   // a PE that never publishes (tests the timeout), or -1
+  int slow_pe, slow_us;           // a PE that idles slow_us microseconds per stage, or -1
 };
 cudaError_t launch_unsync(const Mech &M, const UnsyncArgs &U, int Q, bool mixed, int nv,
                           cudaStream_t st);
 cudaError_t prepare_unsync();
 cudaError_t upload_tables_unsync(const Basis *tables);
+cudaError_t launch_unsync_fp64(const Mech &M, const UnsyncArgs &U, int Q, int nv,
+                               cudaStream_t st);
+cudaError_t launch_unsync_mixed(const Mech &M, const UnsyncArgs &U, int Q, int nv,
+                                cudaStream_t st);
+cudaError_t prepare_unsync_fp64();
+cudaError_t prepare_unsync_mixed();
+cudaError_t upload_tables_unsync_fp64(const Basis *tables);
+cudaError_t upload_tables_unsync_mixed(const Basis *tables);
 cudaError_t launch_advance_by(int64_t *step, int64_t n, cudaStream_t st);
 cudaError_t launch_project(const Mech &M, const Inst &I, const double *prim, double *w,
                            cudaStream_t st);

@@ -75,6 +75,23 @@ cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, bool mixed, i
                : launch_limiter_fp64(M, A, Q, nv, n_blocks, st);
 }
 
+cudaError_t launch_unsync(const Mech &M, const UnsyncArgs &U, int Q, bool mixed, int nv,
+                          cudaStream_t st) {
+  return mixed ? launch_unsync_mixed(M, U, Q, nv, st) : launch_unsync_fp64(M, U, Q, nv, st);
+}
+
+cudaError_t prepare_unsync() {
+  cudaError_t e = prepare_unsync_fp64();
+  if (e == cudaSuccess) e = prepare_unsync_mixed();
+  return e;
+}
+
+cudaError_t upload_tables_unsync(const Basis *tables) {
+  cudaError_t e = upload_tables_unsync_fp64(tables);
+  if (e == cudaSuccess) e = upload_tables_unsync_mixed(tables);
+  return e;
+}
+
 // Raise the dynamic shared-memory limit of every kernel instance (before any
 // launch or stream capture).
 cudaError_t prepare_kernels(int nv, int ns, int nr) {

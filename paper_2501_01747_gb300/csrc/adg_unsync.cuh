@@ -27,6 +27,15 @@
 // the launch cannot deadlock. Each wait polls a bounded number of times; past
 // the bound the CTA reports ADG_ERR_TIMEOUT through the instance's error word
 // and returns, and its neighbours time out in turn.
+//
+// Template code, instantiated per precision variant by adg_u64.cu (FP64) and
+// adg_u32.cu (mixed) with the limiter's elements per CTA of the synchronous
+// launches, so that with maximum delay 0 both modes do the same arithmetic.
+//
+// One PE may be made slower by a fixed idle time per stage (emulated load
+// imbalance, one of the sources of delay named in Sec. 3.2), which makes its
+// neighbours run ahead and observe delays up to d.
+#pragma once
 #include "adg_device.cuh"
 
 namespace adg {
@@ -87,7 +96,7 @@ __device__ inline unsigned long long *agree_slot(const UnsyncArgs &U, int pf, in
 
 }  // namespace
 
-template <int Q, int G, bool MIX>
+template <int Q, int G, bool MIX, int EPB>
 __global__ void __launch_bounds__(LIM_THREADS) unsync_kernel(Mech M, UnsyncArgs U) {
   __shared__ Inst sI;
   __shared__ PeDelays pdi, pdp;  // delays used by the flux and by the limiter
@@ -116,7 +125,7 @@ __global__ void __launch_bounds__(LIM_THREADS) unsync_kernel(Mech M, UnsyncArgs 
   LimArgs L;
   L.insts = nullptr;
   L.blocks = nullptr;
-  L.EPB = LIM_EPB_MAX;
+  L.EPB = EPB;
   for (long long n = n0; n < n0 + U.n_steps; ++n) {
     for (int s = 0; s < 3; ++s) {
       const int c = (int)(3 * n + s);
@@ -139,9 +148,12 @@ __global__ void __launch_bounds__(LIM_THREADS) unsync_kernel(Mech M, UnsyncArgs 
         }
       }
       __syncthreads();
-      // b. publish them, observe the neighbours' stage inputs, and agree on the
-      // common level of each PE face's flux
+      // b. publish them (after the emulated extra work of a slow PE), observe
+      // the neighbours' stage inputs, and agree on the common level of each PE
+      // face's flux
       if (tid == 0) {
+        if (q == U.slow_pe)
+          for (int t = 0; t < U.slow_us; ++t) __nanosleep(1000);
         if (q != U.withheld) {
           __threadfence();
           atomicExch(&U.pub_in[q], c + 1);
@@ -196,9 +208,8 @@ __global__ void __launch_bounds__(LIM_THREADS) unsync_kernel(Mech M, UnsyncArgs 
       if (s_abort) return;
       // e. the limiter, block by block
       L.s = s;
-      for (int e0 = first; e0 <= last; e0 += LIM_EPB_MAX) {
-        limiter_body<Q, G, MIX, LIM_EPB_MAX, true>(M, L, I, e0, min(LIM_EPB_MAX, last + 1 - e0),
-                                                   n, &pdp);
+      for (int e0 = first; e0 <= last; e0 += EPB) {
+        limiter_body<Q, G, MIX, EPB, true>(M, L, I, e0, min(EPB, last + 1 - e0), n, &pdp);
         __syncthreads();
       }
     }
@@ -207,7 +218,7 @@ __global__ void __launch_bounds__(LIM_THREADS) unsync_kernel(Mech M, UnsyncArgs 
 
 // Counters of every PE: all stages before the instance's current step
 // published; agreement slots of every PE face empty.
-__global__ void unsync_reset_kernel(const Inst *inst, int *pub_in, int *pub_pre,
+static __global__ void unsync_reset_kernel(const Inst *inst, int *pub_in, int *pub_pre,
                                     unsigned long long *agree, int n_pe, int npf) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < n_pe) {
@@ -218,17 +229,15 @@ __global__ void unsync_reset_kernel(const Inst *inst, int *pub_in, int *pub_pre,
   if (q < npf * 3 * (MAXD + 1)) agree[q] = 0ull;
 }
 
-namespace {
-
-template <int Q, int G, bool MIX>
-cudaError_t launch_q(const Mech &M, const UnsyncArgs &U, int nv, cudaStream_t st) {
+template <int Q, int G, bool MIX, int EPB>
+cudaError_t unsync_launch_q(const Mech &M, const UnsyncArgs &U, int nv, cudaStream_t st) {
   const size_t smem_stage = stage_smem_bytes(U.TE, Q, M.ns, M.nr, M.nterm, U.O, MIX);
-  const size_t smem_lim = limiter_smem_bytes<Q, G, MIX, LIM_EPB_MAX>(nv, M.ns);
+  const size_t smem_lim = limiter_smem_bytes<Q, G, MIX, EPB>(nv, M.ns);
   const size_t smem = smem_stage > smem_lim ? smem_stage : smem_lim;
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   int per_sm = 0, dev = 0, n_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, unsync_kernel<Q, G, MIX>, LIM_THREADS, smem);
+      &per_sm, unsync_kernel<Q, G, MIX, EPB>, LIM_THREADS, smem);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
@@ -241,59 +250,46 @@ cudaError_t launch_q(const Mech &M, const UnsyncArgs &U, int nv, cudaStream_t st
   Mech m = M;
   UnsyncArgs u = U;
   void *args[] = {&m, &u};
-  return cudaLaunchCooperativeKernel((const void *)unsync_kernel<Q, G, MIX>, dim3(U.n_pe),
+  return cudaLaunchCooperativeKernel((const void *)unsync_kernel<Q, G, MIX, EPB>, dim3(U.n_pe),
                                      dim3(LIM_THREADS), args, smem, st);
 }
 
-template <int Q, bool MIX>
-cudaError_t launch_qm(const Mech &M, const UnsyncArgs &U, int nv, cudaStream_t st) {
-  if (nv <= 16) return launch_q<Q, 16, MIX>(M, U, nv, st);
-  return launch_q<Q, 32, MIX>(M, U, nv, st);
+template <int Q, bool MIX, int EPB>
+cudaError_t unsync_launch_qe(const Mech &M, const UnsyncArgs &U, int nv, cudaStream_t st) {
+  if (nv <= 16) return unsync_launch_q<Q, 16, MIX, EPB>(M, U, nv, st);
+  return unsync_launch_q<Q, 32, MIX, EPB>(M, U, nv, st);
 }
 
-}  // namespace
-
-cudaError_t launch_unsync(const Mech &M, const UnsyncArgs &U, int Q, bool mixed, int nv,
-                          cudaStream_t st) {
-  switch (Q * 2 + (mixed ? 1 : 0)) {
-    case 4: return launch_qm<2, false>(M, U, nv, st);
-    case 5: return launch_qm<2, true>(M, U, nv, st);
-    case 6: return launch_qm<3, false>(M, U, nv, st);
-    case 7: return launch_qm<3, true>(M, U, nv, st);
-    case 8: return launch_qm<4, false>(M, U, nv, st);
-    case 9: return launch_qm<4, true>(M, U, nv, st);
-    case 10: return launch_qm<5, false>(M, U, nv, st);
-    case 11: return launch_qm<5, true>(M, U, nv, st);
+// One variant (precision MIX, limiter CTAs of EPB elements) of the mode.
+template <bool MIX, int EPB>
+cudaError_t unsync_launch_variant(const Mech &M, const UnsyncArgs &U, int Q, int nv,
+                                  cudaStream_t st) {
+  switch (Q) {
+    case 2: return unsync_launch_qe<2, MIX, EPB>(M, U, nv, st);
+    case 3: return unsync_launch_qe<3, MIX, EPB>(M, U, nv, st);
+    case 4: return unsync_launch_qe<4, MIX, EPB>(M, U, nv, st);
+    case 5: return unsync_launch_qe<5, MIX, EPB>(M, U, nv, st);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t prepare_unsync() {
+template <bool MIX, int EPB>
+cudaError_t unsync_prepare_variant() {
   const int lim = 200 * 1024;
   cudaError_t e = cudaSuccess;
 #define ADG_SET(...) \
   if (e == cudaSuccess) \
   e = cudaFuncSetAttribute(__VA_ARGS__, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
-  ADG_SET(unsync_kernel<2, 16, false>);
-  ADG_SET(unsync_kernel<3, 16, false>);
-  ADG_SET(unsync_kernel<4, 16, false>);
-  ADG_SET(unsync_kernel<5, 16, false>);
-  ADG_SET(unsync_kernel<2, 32, false>);
-  ADG_SET(unsync_kernel<3, 32, false>);
-  ADG_SET(unsync_kernel<4, 32, false>);
-  ADG_SET(unsync_kernel<5, 32, false>);
-  ADG_SET(unsync_kernel<2, 16, true>);
-  ADG_SET(unsync_kernel<3, 16, true>);
-  ADG_SET(unsync_kernel<4, 16, true>);
-  ADG_SET(unsync_kernel<5, 16, true>);
-  ADG_SET(unsync_kernel<2, 32, true>);
-  ADG_SET(unsync_kernel<3, 32, true>);
-  ADG_SET(unsync_kernel<4, 32, true>);
-  ADG_SET(unsync_kernel<5, 32, true>);
+  ADG_SET(unsync_kernel<2, 16, MIX, EPB>);
+  ADG_SET(unsync_kernel<3, 16, MIX, EPB>);
+  ADG_SET(unsync_kernel<4, 16, MIX, EPB>);
+  ADG_SET(unsync_kernel<5, 16, MIX, EPB>);
+  ADG_SET(unsync_kernel<2, 32, MIX, EPB>);
+  ADG_SET(unsync_kernel<3, 32, MIX, EPB>);
+  ADG_SET(unsync_kernel<4, 32, MIX, EPB>);
+  ADG_SET(unsync_kernel<5, 32, MIX, EPB>);
 #undef ADG_SET
   return e;
 }
-
-cudaError_t upload_tables_unsync(const Basis *tables) { return upload_unit_tables(tables); }
 
 }  // namespace adg
