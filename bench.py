@@ -289,6 +289,49 @@ def measure(adg, torch, wls, mech, prims, prec, args, dev, pg, ws, steps, autotu
                     "d2h_bytes_per_step": nbytes}}
 
 
+def unsync_measure(adg, torch, wl, mech, prim, prec, dev, warmup, steps):
+    """The truly unsynchronised mode on the same instance: one cooperative launch
+    of `steps` steps (one CTA per PE, no lockstep), device-timed; the delays the
+    PEs used; its distance from the seeded-delay synchronous run of the same
+    number of steps (relative L-infinity per conserved variable, scaled by the
+    variable's largest magnitude); the drift of total mass and energy."""
+    stream = torch.cuda.current_stream(dev)
+    g = adg.ADG(mech, [wl], device=dev, precision=prec)
+    g.set_primitive(prim)
+    w0 = g.get_state()
+    g.step_unsync(warmup, stream=stream)
+    g.check()
+    g.unsync_delays()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    g.step_unsync(steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    g.check()
+    hist = g.unsync_delays()
+    w = g.get_state()
+    g.close()
+    ref = adg.ADG(mech, [wl], device=dev, precision=prec)
+    ref.set_primitive(prim)
+    ref.step(warmup + steps, stream)
+    ref.check()
+    wr = ref.get_state()
+    ref.close()
+    scale = np.maximum(np.abs(wr).max(axis=(1, 2)), 1e-300)
+    err = float((np.abs(w - wr).max(axis=(1, 2)) / scale).max())
+    drift = {"mass": float(abs(w[2:, :, 0].sum() - w0[2:, :, 0].sum()) / w0[2:, :, 0].sum()),
+             "energy": float(abs(w[1, :, 0].sum() - w0[1, :, 0].sum()) / abs(w0[1, :, 0].sum()))}
+    value = dof_stages_per_step([wl]) * steps / (ms / 1e3)
+    return {"value": value, "unit": "DOF-stage/s", "ms_per_step": ms / steps, "steps": steps,
+            "warmup": warmup, "precision": prec, "launches": 3,
+            "l2": "resident (one launch runs every step)",
+            "delays_flux": [int(x) for x in hist[0, :wl.max_delay + 1]],
+            "delays_limiter": [int(x) for x in hist[1, :wl.max_delay + 1]],
+            "error_vs_seeded": err, "relative_drift": drift}
+
+
 def mixed_error(adg, torch, wls, mech, prims, dev, n_steps):
     """Error of the mixed path against the FP64 path (which matches the FP64
     oracle to 1e-10) after n_steps from the same state: the largest relative
@@ -368,6 +411,9 @@ def main(argv=None):
     ap.add_argument("--tuning", default="", help="TE,NT: set the stage launch configuration "
                     "instead of autotuning it")
     ap.add_argument("--only", action="store_true", help="time the headline variant only")
+    ap.add_argument("--unsync-steps", type=int, default=100,
+                    help="steps of the unsynchronised-mode measurement added to the line "
+                         "(single-instance workloads; 0 to skip)")
     ap.add_argument("--ensemble-steps", type=int, default=20,
                     help="timed steps of the batched-ensemble measurement added to the line "
                     "(0: none)")
@@ -392,6 +438,10 @@ def main(argv=None):
     err_steps = 200 if len(wls) == 1 else 20
     head, other, other_prec, err = compare(adg, torch, wls, mech, prims, args, dev, pg, ws,
                                            args.steps, err_steps=err_steps)
+    uns = None
+    if args.unsync_steps > 0 and len(wls) == 1 and not args.only:
+        uns = unsync_measure(adg, torch, wls[0], mech, prims[0], args.precision, dev,
+                             args.warmup, args.unsync_steps)
     ens = None
     if args.ensemble_steps > 0 and args.workload != ENSEMBLE and not args.only:
         ewls, emech = bench_workloads(ENSEMBLE)
@@ -429,6 +479,8 @@ def main(argv=None):
         line["speedup_mixed_vs_fp64"] = mix_v / fp64_v
     if err is not None:
         line["mixed_error"] = err
+    if uns is not None:
+        line["unsync"] = uns
     if ens is not None:
         ewls, emech, eh, eo, eop, ee = ens
         rec = {"config": dict(workload_config(ewls, emech, args), tuning=eh["tuning"]),
