@@ -16,6 +16,7 @@ timing is the maximum over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -289,12 +290,34 @@ def measure(adg, torch, wls, mech, prims, prec, args, dev, pg, ws, steps, autotu
                     "d2h_bytes_per_step": nbytes}}
 
 
+def state_scales(w, mech):
+    """Physical scale of every conserved variable of a modal state [nv][N][Q]:
+    max rho (|u| + a) for the momentum (the acoustic scale: at early times the
+    momentum itself is near zero), max |rho E| for the energy, and
+    max(max rho Y_i, 1e-5 max rho) for the partial densities (cell averages)."""
+    ru = 8.314462618
+    scale = np.abs(w).max(axis=(1, 2))
+    r = w[2:, :, 0]
+    rho = r.sum(axis=0)
+    u = w[0, :, 0] / rho
+    q = ((mech.h_f - mech.cp * 298.15) / mech.W)[:, None]
+    cv = ((mech.cp - ru) / mech.W)[:, None]
+    T = (w[1, :, 0] - 0.5 * rho * u * u - (r * q).sum(0)) / (r * cv).sum(0)
+    cpm = (r * (mech.cp / mech.W)[:, None]).sum(0)
+    cvm = (r * cv).sum(0)
+    a = np.sqrt(np.abs(cpm / cvm * (cpm - cvm) / rho * T))
+    scale[0] = max(scale[0], float(np.max(rho * (np.abs(u) + a))))
+    scale[2:] = np.maximum(scale[2:], 1e-5 * rho.max())
+    return np.maximum(scale, 1e-300)
+
+
 def unsync_measure(adg, torch, wl, mech, prim, prec, dev, warmup, steps):
     """The truly unsynchronised mode on the same instance: one cooperative launch
     of `steps` steps (one CTA per PE, no lockstep), device-timed; the delays the
     PEs used; its distance from the seeded-delay synchronous run of the same
-    number of steps (relative L-infinity per conserved variable, scaled by the
-    variable's largest magnitude); the drift of total mass and energy."""
+    number of steps (L-infinity per conserved variable in the scales of
+    state_scales), beside the same distance of the synchronous run without
+    delays; the drift of total mass and energy."""
     stream = torch.cuda.current_stream(dev)
     g = adg.ADG(mech, [wl], device=dev, precision=prec)
     g.set_primitive(prim)
@@ -313,14 +336,18 @@ def unsync_measure(adg, torch, wl, mech, prim, prec, dev, warmup, steps):
     hist = g.unsync_delays()
     w = g.get_state()
     g.close()
-    ref = adg.ADG(mech, [wl], device=dev, precision=prec)
-    ref.set_primitive(prim)
-    ref.step(warmup + steps, stream)
-    ref.check()
-    wr = ref.get_state()
-    ref.close()
-    scale = np.maximum(np.abs(wr).max(axis=(1, 2)), 1e-300)
-    err = float((np.abs(w - wr).max(axis=(1, 2)) / scale).max())
+    ref = {}
+    for mode, cfg in (("seeded", wl), ("sync", dataclasses.replace(wl, delay_mode=I.DELAY_SYNC))):
+        r = adg.ADG(mech, [cfg], device=dev, precision=prec)
+        r.set_primitive(prim)
+        r.step(warmup + steps, stream)
+        r.check()
+        ref[mode] = r.get_state()
+        r.close()
+    wr = ref["seeded"]
+    scale = state_scales(wr, mech)
+    ev = np.abs(w - wr).max(axis=(1, 2)) / scale
+    es = np.abs(ref["sync"] - wr).max(axis=(1, 2)) / scale
     drift = {"mass": float(abs(w[2:, :, 0].sum() - w0[2:, :, 0].sum()) / w0[2:, :, 0].sum()),
              "energy": float(abs(w[1, :, 0].sum() - w0[1, :, 0].sum()) / abs(w0[1, :, 0].sum()))}
     value = dof_stages_per_step([wl]) * steps / (ms / 1e3)
@@ -329,7 +356,12 @@ def unsync_measure(adg, torch, wl, mech, prim, prec, dev, warmup, steps):
             "l2": "resident (one launch runs every step)",
             "delays_flux": [int(x) for x in hist[0, :wl.max_delay + 1]],
             "delays_limiter": [int(x) for x in hist[1, :wl.max_delay + 1]],
-            "error_vs_seeded": err, "relative_drift": drift}
+            "error_vs_seeded": float(ev.max()),
+            "error_vs_seeded_per_variable": [float(x) for x in ev],
+            "sync_vs_seeded": float(es.max()),
+            "error_scales": "momentum: max rho(|u|+a); energy: max|rho E|; "
+                            "rho Y_i: max(max rho Y_i, 1e-5 max rho)",
+            "relative_drift": drift}
 
 
 def mixed_error(adg, torch, wls, mech, prims, dev, n_steps):
