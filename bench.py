@@ -537,11 +537,11 @@ def main(argv=None):
 # DRAM bytes (read + write) per stage-kernel launch from ncu, per (workload,
 # kernel revision, precision); the summaries are under profiles/.
 STAGE_TRAFFIC = {
-    ("ignition-9sp-4096x4", "v9", "mixed"): 2.029824e6,
-    ("ignition-9sp-4096x4", "v9", "fp64"): 2.053632e6,
+    ("ignition-9sp-4096x4", "v10", "mixed"): 2.020096e6,
+    ("ignition-9sp-4096x4", "v10", "fp64"): 2.049792e6,
 }
 
-KERNEL_REV = "v9"
+KERNEL_REV = "v10"
 
 if __name__ == "__main__":
     sys.exit(main())
