@@ -47,7 +47,7 @@ class Cfg(C.Structure):
                 ("bc_left", C.c_int), ("bc_right", C.c_int), ("flux", C.c_int),
                 ("limiter", C.c_int), ("at_order", C.c_int), ("delay_mode", C.c_int),
                 ("max_delay", C.c_int), ("delay_probs", C.POINTER(C.c_double)),
-                ("seed", C.c_uint64), ("tvb_M", C.c_double)]
+                ("seed", C.c_uint64), ("tvb_M", C.c_double), ("integrator", C.c_int)]
 
 
 _lib = None
@@ -70,6 +70,8 @@ def lib():
         _lib.or_legendre.argtypes = [C.c_int, C.c_double, d, d]
         _lib.or_gauss.argtypes = [C.c_int, d, d]
         _lib.or_at_coeffs.argtypes = [C.c_int, C.c_int, d]
+        _lib.or_rk_stages.argtypes = [C.c_int]
+        _lib.or_lserk_coeffs.argtypes = [C.c_int, d, d, d]
         _lib.or_delay.argtypes = [C.POINTER(Cfg), C.c_int64, C.c_int]
         _lib.or_splitmix64.restype = C.c_uint64
         _lib.or_splitmix64.argtypes = [C.c_uint64]
@@ -118,8 +120,20 @@ def make_cfg(wl, dt=None):
                                           dtype=np.float64))
     cfg = Cfg(wl.n_elem, wl.p, wl.n_pe, wl.x0, wl.length, wl.dt if dt is None else dt,
               wl.bc_left, wl.bc_right, wl.flux, wl.limiter, wl.at_order, wl.delay_mode,
-              wl.max_delay, _dp(probs), wl.seed & ((1 << 64) - 1), wl.tvb_M)
+              wl.max_delay, _dp(probs), wl.seed & ((1 << 64) - 1), wl.tvb_M,
+              getattr(wl, "integrator", 0))
     return cfg, probs
+
+
+def rk_stages(integrator):
+    return int(lib().or_rk_stages(int(integrator)))
+
+
+def lserk_coeffs(integrator):
+    """(A, B, C) of the 2N-storage LSERK scheme `integrator` (1 or 2)."""
+    a, b, c = np.zeros(5), np.zeros(5), np.zeros(5)
+    n = lib().or_lserk_coeffs(int(integrator), _dp(a), _dp(b), _dp(c))
+    return a[:n], b[:n], c[:n]
 
 
 class Oracle:
@@ -164,7 +178,7 @@ class Oracle:
         return int(lib().or_steps_done(self.h))
 
     def flags(self):
-        last = np.zeros((3, self.wl.n_elem), dtype=np.uint8)
+        last = np.zeros((rk_stages(self.cfg.integrator), self.wl.n_elem), dtype=np.uint8)
         cnt = np.zeros(self.wl.n_elem, dtype=np.int32)
         lib().or_get_flags(self.h, last.ctypes.data_as(C.POINTER(C.c_uint8)),
                            cnt.ctypes.data_as(C.POINTER(C.c_int32)))

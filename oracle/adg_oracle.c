@@ -434,8 +434,10 @@ struct or_ctx {
   int *face_pf;            /* per mesh face 0..ne: PE face id or -1 */
   int *elem_pf_right;      /* per element: PE face on its right or -1 */
   int *elem_pf_left;       /* per element: PE face on its left or -1 */
+  int S;                 /* RK stages per step */
   double *w, *w0, *win, *wpre, *rhs, *fhat;
-  double *ring_in, *ring_pre; /* [depth][3][npf][2][nv*np1] */
+  double *dq;            /* LSERK register (2N storage) */
+  double *ring_in, *ring_pre; /* [depth][S][npf][2][nv*np1] */
   int64_t *ring_level;
   int *keff;
   int64_t n;
@@ -446,12 +448,59 @@ struct or_ctx {
 static double *ring_at(or_ctx *c, double *ring, int64_t level, int s, int pf, int side) {
   int slot = (int)(level % c->depth);
   size_t blk = (size_t)c->nv * c->np1;
-  return ring + ((((size_t)slot * 3 + s) * c->npf + pf) * 2 + side) * blk;
+  return ring + ((((size_t)slot * c->S + s) * c->npf + pf) * 2 + side) * blk;
+}
+
+/* Low-storage explicit RK in Williamson's 2N form (Sec. 3.1 cites Williamson
+ * 1980 and Kennedy, Carpenter & Lewis 2000): per stage s,
+ *   dq <- A_s dq + dt L(w),  w <- w + B_s dq,  at time t_n + C_s dt.
+ * 1: Williamson's 3-stage 3rd-order scheme; 2: the 5-stage 4th-order scheme of
+ * Carpenter & Kennedy (1994), the coefficients as published (rational
+ * approximations of the optimised values). */
+int or_rk_stages(int integrator) {
+  return integrator == 1 ? 3 : integrator == 2 ? 5 : 3;
+}
+
+int or_lserk_coeffs(int integrator, double *A, double *B, double *C) {
+  if (integrator == 1) {
+    const double a[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+    const double b[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+    const double cc[3] = {0.0, 1.0 / 3.0, 3.0 / 4.0};
+    for (int s = 0; s < 3; ++s) {
+      A[s] = a[s];
+      B[s] = b[s];
+      C[s] = cc[s];
+    }
+    return 3;
+  }
+  if (integrator == 2) {
+    const double a[5] = {0.0, -567301805773.0 / 1357537059087.0,
+                         -2404267990393.0 / 2016746695238.0,
+                         -3550918686646.0 / 2091501179385.0,
+                         -1275806237668.0 / 842570457699.0};
+    const double b[5] = {1432997174477.0 / 9575080441755.0,
+                         5161836677717.0 / 13612068292357.0,
+                         1720146321549.0 / 2090206949498.0,
+                         3134564353537.0 / 4481467310338.0,
+                         2277821191437.0 / 14882151754819.0};
+    const double cc[5] = {0.0, 1432997174477.0 / 9575080441755.0,
+                          2526269341429.0 / 6820363962896.0,
+                          2006345519317.0 / 3224310063776.0,
+                          2802321613138.0 / 2924317926251.0};
+    for (int s = 0; s < 5; ++s) {
+      A[s] = a[s];
+      B[s] = b[s];
+      C[s] = cc[s];
+    }
+    return 5;
+  }
+  return 0;
 }
 
 or_ctx *or_create(const or_cfg *cfg, const or_mech *m) {
   if (cfg->p < 0 || cfg->p + 1 > MAXQ || m->ns + 2 > MAXV || cfg->n_elem < 1 ||
-      cfg->n_pe < 1 || cfg->n_pe > cfg->n_elem || cfg->at_order < 1)
+      cfg->n_pe < 1 || cfg->n_pe > cfg->n_elem || cfg->at_order < 1 ||
+      cfg->integrator < 0 || cfg->integrator > 2)
     return NULL;
   or_ctx *c = (or_ctx *)calloc(1, sizeof(or_ctx));
   c->cfg = *cfg;
@@ -491,6 +540,7 @@ or_ctx *or_create(const or_cfg *cfg, const or_mech *m) {
   c->ne = cfg->n_elem;
   c->dx = cfg->length / cfg->n_elem;
   c->depth = cfg->max_delay + cfg->at_order;
+  c->S = or_rk_stages(cfg->integrator);
   int q = c->np1;
   or_gauss(q, c->xq, c->wq);
   for (int k = 0; k < q; ++k) {
@@ -535,14 +585,15 @@ or_ctx *or_create(const or_cfg *cfg, const or_mech *m) {
   c->win = (double *)calloc(sz, sizeof(double));
   c->wpre = (double *)calloc(sz, sizeof(double));
   c->rhs = (double *)calloc(sz, sizeof(double));
+  c->dq = (double *)calloc(sz, sizeof(double));
   c->fhat = (double *)calloc((size_t)(ne + 1) * c->nv, sizeof(double));
-  size_t rsz = (size_t)c->depth * 3 * (c->npf > 0 ? c->npf : 1) * 2 * c->nv * q;
+  size_t rsz = (size_t)c->depth * c->S * (c->npf > 0 ? c->npf : 1) * 2 * c->nv * q;
   c->ring_in = (double *)calloc(rsz, sizeof(double));
   c->ring_pre = (double *)calloc(rsz, sizeof(double));
   c->ring_level = (int64_t *)malloc(sizeof(int64_t) * c->depth);
   for (int s = 0; s < c->depth; ++s) c->ring_level[s] = -1;
   c->keff = (int *)calloc(c->npf > 0 ? c->npf : 1, sizeof(int));
-  c->flags_last = (uint8_t *)calloc((size_t)3 * ne, 1);
+  c->flags_last = (uint8_t *)calloc((size_t)c->S * ne, 1);
   c->flag_count = (int32_t *)calloc(ne, sizeof(int32_t));
   c->n = 0;
   return c;
@@ -563,6 +614,7 @@ void or_destroy(or_ctx *c) {
   free(c->win);
   free(c->wpre);
   free(c->rhs);
+  free(c->dq);
   free(c->fhat);
   free(c->ring_in);
   free(c->ring_pre);
@@ -618,7 +670,7 @@ int or_get_state(const or_ctx *c, double *w) {
 int64_t or_steps_done(const or_ctx *c) { return c->n; }
 
 int or_get_flags(const or_ctx *c, uint8_t *last, int32_t *count) {
-  if (last) memcpy(last, c->flags_last, (size_t)3 * c->ne);
+  if (last) memcpy(last, c->flags_last, (size_t)c->S * c->ne);
   if (count) memcpy(count, c->flag_count, sizeof(int32_t) * c->ne);
   return 0;
 }
@@ -924,14 +976,19 @@ static int limit_stage(or_ctx *c, int s, uint8_t *flags) {
 
 /* One step of SSP-RK3 (Shu-Osher form) with limiting after every stage:
  *   w1 = w0 + dt L(w0);  w2 = 3/4 w0 + 1/4 (w1 + dt L(w1));
- *   w^{n+1} = 1/3 w0 + 2/3 (w2 + dt L(w2)).
+ *   w^{n+1} = 1/3 w0 + 2/3 (w2 + dt L(w2)),
+ * or of an LSERK scheme (or_lserk_coeffs) with limiting after every stage:
+ *   dq = A_s dq + dt L(w_s),  w_{s+1} = w_s + B_s dq.
  * Stage s of step n reads stage s of the delayed steps (one delay per PE face per
- * step, common to both sides and to all stages; synchronous until the history
+ * step, common to both sides and to all stages: CAA skips the exchange of every
+ * intermediate stage of a delayed step, Sec. 4.1; synchronous until the history
  * holds the levels the AT stencil needs). */
 int or_step(or_ctx *c, int n_steps) {
   int nv = c->nv, q = c->np1, ne = c->ne, o = c->cfg.at_order;
   size_t sz = (size_t)nv * ne * q, blk = (size_t)nv * q;
   double dt = c->cfg.dt;
+  double lsA[5], lsB[5], lsC[5];
+  const int lserk = or_lserk_coeffs(c->cfg.integrator, lsA, lsB, lsC) > 0;
   for (int it = 0; it < n_steps; ++it) {
     int64_t n = c->n;
     for (int f = 0; f < c->npf; ++f) {
@@ -942,7 +999,7 @@ int or_step(or_ctx *c, int n_steps) {
     c->ring_level[slot] = n;
     memcpy(c->w0, c->w, sizeof(double) * sz);
     memcpy(c->win, c->w, sizeof(double) * sz);
-    for (int s = 0; s < 3; ++s) {
+    for (int s = 0; s < c->S; ++s) {
       /* history of the stage input (for the AT flux) */
       for (int f = 0; f < c->npf; ++f) {
         double *dl = ring_at(c, c->ring_in, n, s, f, 0);
@@ -954,7 +1011,10 @@ int or_step(or_ctx *c, int n_steps) {
       if (err) return err;
       for (size_t t = 0; t < sz; ++t) {
         double r = c->rhs[t];
-        if (s == 0)
+        if (lserk) {
+          c->dq[t] = lsA[s] * c->dq[t] + dt * r;
+          c->wpre[t] = c->win[t] + lsB[s] * c->dq[t];
+        } else if (s == 0)
           c->wpre[t] = c->w0[t] + dt * r;
         else if (s == 1)
           c->wpre[t] = 0.75 * c->w0[t] + 0.25 * (c->win[t] + dt * r);

@@ -37,6 +37,9 @@ typedef struct {
   const double *delay_probs; /* [max_delay+1] (SAA) */
   uint64_t seed;
   double tvb_M;
+  int integrator;        /* 0 SSP-RK3 (Shu-Osher), 1 LSERK 3-stage 3rd order
+                            (Williamson 1980), 2 LSERK 5-stage 4th order
+                            (Carpenter-Kennedy, 2N storage) */
 } or_cfg;
 
 typedef struct or_ctx or_ctx;
@@ -44,6 +47,10 @@ typedef struct or_ctx or_ctx;
 /* quadrature and basis */
 void or_legendre(int n, double x, double *P, double *dP);
 int or_gauss(int q, double *x, double *w);
+/* stages of an integrator, and the 2N-storage coefficients A_s, B_s, C_s of an
+ * LSERK scheme (returns the number of stages, 0 for SSP-RK3) */
+int or_rk_stages(int integrator);
+int or_lserk_coeffs(int integrator, double *A, double *B, double *C);
 /* AT coefficients c_m(k), m = 0..order-1 (Eq. 7-8) */
 void or_at_coeffs(int order, int k, double *c);
 int or_delay(const or_cfg *cfg, int64_t step, int face);
@@ -75,7 +82,7 @@ int or_set_state(or_ctx *c, const double *w);
 int or_get_state(const or_ctx *c, double *w);
 int or_step(or_ctx *c, int n_steps);
 int64_t or_steps_done(const or_ctx *c);
-/* troubled-cell flags: stages of the last step [3][n_elem] and per-element count */
+/* troubled-cell flags: stages of the last step [stages][n_elem] and per-element count */
 int or_get_flags(const or_ctx *c, uint8_t *last, int32_t *count);
 int or_get_temperature(const or_ctx *c, double *T);
 /* one synchronous right-hand side L(w) (Eq. 5), no delays */

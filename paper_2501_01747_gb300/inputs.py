@@ -42,6 +42,9 @@ BC_PERIODIC, BC_REFLECT, BC_OUTFLOW = 0, 1, 2
 FLUX_LF, FLUX_HLLC = 0, 1
 LIM_NONE, LIM_WENO = 0, 1
 DELAY_SYNC, DELAY_CAA, DELAY_SAA = 0, 1, 2
+# time integrators: SSP-RK3 (Shu-Osher), and the low-storage explicit RK schemes
+# of Sec. 3.1 (Williamson's 3-stage 3rd order, Carpenter-Kennedy 5-stage 4th order)
+RK_SSP3, RK_LS3, RK_LS4 = 0, 1, 2
 
 # Delay probability sets of Sec. 4.2 (SAA), for a maximum delay of 2 (three bins).
 SAA_SETS = {1: (0.3, 0.4, 0.3), 2: (0.5, 0.3, 0.2), 3: (0.8, 0.1, 0.1)}
@@ -227,6 +230,7 @@ class Workload:
     tvb_M: float = 0.0
     x0: float = 0.0
     attempts: Optional[list] = None
+    integrator: int = RK_SSP3
 
     def mechanism(self) -> Mechanism:
         return make_mechanism(self.ns, self.nr, self.mech_seed, self.attempts)
