@@ -52,6 +52,17 @@ extern "C" {
 #define ADG_SYNC 0
 #define ADG_CAA 1
 #define ADG_SAA 2
+/* Time integrator, with limiting after every stage. ADG_RK_SSP3: SSP-RK3 in
+ * Shu-Osher form. The low-storage explicit RK schemes (LSERK) of Sec. 3.1, in
+ * Williamson's 2N form dq <- A_s dq + dt L(w), w <- w + B_s dq: ADG_RK_LS3,
+ * Williamson's (1980) 3-stage 3rd-order scheme; ADG_RK_LS4, the 5-stage
+ * 4th-order scheme of Carpenter and Kennedy (1994), the family of Kennedy,
+ * Carpenter and Lewis (2000). Stage s of step n reads stage s of the delayed
+ * steps; CAA skips the exchange at every stage of a delayed step (Sec. 4.1). */
+#define ADG_RK_SSP3 0
+#define ADG_RK_LS3 1
+#define ADG_RK_LS4 2
+#define ADG_MAX_STAGES 5
 /* Arithmetic of the RK-stage right-hand side (Sec. 5, mixed-precision runs).
  * ADG_FP64: every step in double precision.
  * ADG_MIXED: the numerical flux, the DG volume/surface/source assembly and the
@@ -92,6 +103,7 @@ typedef struct {
   uint64_t seed;           /* SAA delay seed */
   double tvb_M;            /* TVB constant of the indicator (0 = TVD) */
   int precision;           /* ADG_FP64 | ADG_MIXED */
+  int integrator;          /* ADG_RK_SSP3 | ADG_RK_LS3 | ADG_RK_LS4 */
 } adg_config;
 
 typedef struct adg_ctx adg_ctx;
@@ -144,8 +156,9 @@ int adg_step(adg_ctx *ctx, int n_steps, void *stream);
  * stage where it happened (any pointer may be NULL); clears it. */
 int adg_status(adg_ctx *ctx, int *instance, int *element, int64_t *step, int *stage);
 
-/* Troubled-cell flags of the three stages of the last step ([3][n_elem] bytes)
- * and per-element counts of flagged stages since the last set ([n_elem] int32). */
+/* Troubled-cell flags of the stages of the last step ([stages][n_elem] bytes:
+ * 3 stages for ADG_RK_SSP3 and ADG_RK_LS3, 5 for ADG_RK_LS4) and per-element
+ * counts of flagged stages since the last set ([n_elem] int32). */
 int adg_get_flags(adg_ctx *ctx, int instance, uint8_t *last_host, int32_t *count_host);
 
 /* Temperature at the Gauss points of the current state, [n_elem][p+1]. */
@@ -176,10 +189,11 @@ int adg_kernel_times(adg_ctx *ctx, double *ms, int64_t *launches);
  * stage kernel for every candidate that fits in shared memory on `stream`,
  * keeps the fastest and drops the captured step graphs. The trajectory is not
  * changed (the trial launches only rewrite buffers the next step rewrites).
- * Synchronous. Instances are grouped by degree and precision. adg_get_tuning
- * fills tuning[5 * g + {0,1,2,3,4}] with the degree, precision, tile elements,
- * threads per CTA and tile count of group g (at most ADG_MAX_GROUPS groups). */
-#define ADG_MAX_GROUPS (2 * ADG_MAX_P)
+ * Synchronous. Instances are grouped by degree, precision and number of RK
+ * stages. adg_get_tuning fills tuning[6 * g + {0,1,2,3,4,5}] with the degree,
+ * precision, tile elements, threads per CTA, tile count and RK stages of group
+ * g (at most ADG_MAX_GROUPS groups). */
+#define ADG_MAX_GROUPS (4 * ADG_MAX_P)
 int adg_autotune(adg_ctx *ctx, void *stream);
 int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning);
 /* Set the launch configuration of group g directly (for instance one that an
@@ -255,7 +269,8 @@ int adg_set_unsync_imbalance(adg_ctx *ctx, int slow_pe, int slow_us);
  *   uploads the constant tables; make that first call before any stream
  *   capture on that device.
  * - A problem whose scratch does not fit returns ADG_ERR_NOMEM (nothing is
- *   enqueued); more than ADG_NOALLOC_MAX_REACTIONS reactions returns ADG_ERR_ARG.
+ *   enqueued); more than ADG_NOALLOC_MAX_REACTIONS reactions, or an integrator
+ *   other than ADG_RK_SSP3, returns ADG_ERR_ARG.
  * - Every call reuses the same array: calls that overlap on the GPU (on
  *   different streams, or on one device from several threads without ordering)
  *   race and corrupt each other. The call clears what must start at zero.

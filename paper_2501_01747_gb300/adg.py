@@ -29,6 +29,7 @@ ERRORS = {-1: "ADG_ERR_ARG", -2: "ADG_ERR_CUDA", -3: "ADG_ERR_NOMEM",
           -4: "ADG_ERR_NONPHYSICAL", -5: "ADG_ERR_HISTORY", -6: "ADG_ERR_NOLIB",
           -7: "ADG_ERR_TIMEOUT"}
 MAX_DELAY = 7  # ADG_MAX_DELAY
+MAX_GROUPS = 16  # ADG_MAX_GROUPS
 
 
 class AdgError(RuntimeError):
@@ -92,7 +93,8 @@ class Config_(C.Structure):
                 ("bc_left", C.c_int), ("bc_right", C.c_int), ("flux", C.c_int),
                 ("limiter", C.c_int), ("at_order", C.c_int), ("delay_mode", C.c_int),
                 ("max_delay", C.c_int), ("delay_probs", C.POINTER(C.c_double)),
-                ("seed", C.c_uint64), ("tvb_M", C.c_double), ("precision", C.c_int)]
+                ("seed", C.c_uint64), ("tvb_M", C.c_double), ("precision", C.c_int),
+                ("integrator", C.c_int)]
 
 
 _lib = None
@@ -193,8 +195,14 @@ def config_struct(wl, precision=FP64):
     probs = np.ascontiguousarray(np.array(wl.delay_probs or [1.0], dtype=np.float64))
     c = Config_(wl.n_elem, wl.p, wl.n_pe, wl.x0, wl.length, wl.dt, wl.bc_left, wl.bc_right,
                 wl.flux, wl.limiter, wl.at_order, wl.delay_mode, wl.max_delay, _dp(probs),
-                wl.seed & ((1 << 64) - 1), wl.tvb_M, _precision(precision))
+                wl.seed & ((1 << 64) - 1), wl.tvb_M, _precision(precision),
+                int(getattr(wl, "integrator", 0)))
     return c, probs
+
+
+def rk_stages(wl):
+    """RK stages per step of a workload's integrator (5 for LSERK4, else 3)."""
+    return 5 if int(getattr(wl, "integrator", 0)) == 2 else 3
 
 
 def delay_table(wl, step0, n_steps):
@@ -327,8 +335,9 @@ class ADG:
             raise AdgError(rc, "device error at instance/element/step/stage %s" % (where,))
 
     def flags(self, k=0):
-        n = self.workloads[self._k(k)].n_elem
-        last = np.zeros((3, n), dtype=np.uint8)
+        wl = self.workloads[self._k(k)]
+        n = wl.n_elem
+        last = np.zeros((rk_stages(wl), n), dtype=np.uint8)
         cnt = np.zeros(n, dtype=np.int32)
         _check(self.L.adg_get_flags(self.h, k, last.ctypes.data_as(C.POINTER(C.c_uint8)),
                                     cnt.ctypes.data_as(C.POINTER(C.c_int32))), "adg_get_flags")
@@ -371,11 +380,11 @@ class ADG:
 
     def tuning(self):
         n = C.c_int(0)
-        t = (C.c_int * 40)()
+        t = (C.c_int * (6 * MAX_GROUPS))()
         _check(self.L.adg_get_tuning(self.h, C.byref(n), t), "adg_get_tuning")
-        return [{"p": t[5 * g], "precision": "mixed" if t[5 * g + 1] == MIXED else "fp64",
-                 "elements_per_tile": t[5 * g + 2], "threads_per_cta": t[5 * g + 3],
-                 "tiles": t[5 * g + 4]} for g in range(n.value)]
+        return [{"p": t[6 * g], "precision": "mixed" if t[6 * g + 1] == MIXED else "fp64",
+                 "elements_per_tile": t[6 * g + 2], "threads_per_cta": t[6 * g + 3],
+                 "tiles": t[6 * g + 4], "stages": t[6 * g + 5]} for g in range(n.value)]
 
     def set_tuning(self, group, elements_per_tile, threads_per_cta):
         """Set the stage launch configuration of a group (e.g. a stored autotune result)."""

@@ -196,6 +196,7 @@ struct InstHost {
 struct Group {
   int Q = 0;
   bool mixed = false;
+  int S = 3;                    // RK stages per step
   int TE = 0;                   // elements per stage tile
   int NT = 128;                 // threads per stage CTA
   int EPB = 32;                 // elements per limiter CTA
@@ -292,9 +293,44 @@ int check_args(const adg_mechanism *m, const adg_config *cfgs, int n) {
     if (lp != rp) return ADG_ERR_ARG;
     if (c.bc_left < 0 || c.bc_left > 2 || c.bc_right < 0 || c.bc_right > 2) return ADG_ERR_ARG;
     if (c.precision != ADG_FP64 && c.precision != ADG_MIXED) return ADG_ERR_ARG;
+    if (c.integrator < ADG_RK_SSP3 || c.integrator > ADG_RK_LS4) return ADG_ERR_ARG;
     if ((int64_t)c.n_elem * (c.p + 1) * (m->n_species + 3) > (int64_t)1 << 31) return ADG_ERR_ARG;
   }
   return ADG_OK;
+}
+
+// RK stages per step, and the 2N-storage coefficients of an LSERK scheme
+// (Sec. 3.1: Williamson 1980; Carpenter and Kennedy's 5-stage 4th-order scheme of
+// the Kennedy-Carpenter-Lewis family), as published. Returns 0 for SSP-RK3.
+int rk_stages(int integrator) { return integrator == ADG_RK_LS4 ? 5 : 3; }
+
+static int lserk_coefficients(int integrator, double *a, double *b) {
+  if (integrator == ADG_RK_LS3) {
+    const double A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+    const double B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+    for (int s = 0; s < 3; ++s) {
+      a[s] = A[s];
+      b[s] = B[s];
+    }
+    return 3;
+  }
+  if (integrator == ADG_RK_LS4) {
+    const double A[5] = {0.0, -567301805773.0 / 1357537059087.0,
+                         -2404267990393.0 / 2016746695238.0,
+                         -3550918686646.0 / 2091501179385.0,
+                         -1275806237668.0 / 842570457699.0};
+    const double B[5] = {1432997174477.0 / 9575080441755.0,
+                         5161836677717.0 / 13612068292357.0,
+                         1720146321549.0 / 2090206949498.0,
+                         3134564353537.0 / 4481467310338.0,
+                         2277821191437.0 / 14882151754819.0};
+    for (int s = 0; s < 5; ++s) {
+      a[s] = A[s];
+      b[s] = B[s];
+    }
+    return 5;
+  }
+  return 0;
 }
 
 int n_pe_faces(const adg_config &c) {
@@ -318,13 +354,17 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
   for (int k = 0; k < ctx->n_inst; ++k) max_pe = cfgs[k].n_pe > max_pe ? cfgs[k].n_pe : max_pe;
   ctx->pub_in = (int *)cv.take(sizeof(int) * max_pe);
   ctx->pub_pre = (int *)cv.take(sizeof(int) * max_pe);
-  ctx->agree = (unsigned long long *)cv.take(sizeof(unsigned long long) * max_pe * 3 * (MAXD + 1));
+  ctx->agree = (unsigned long long *)cv.take(sizeof(unsigned long long) * max_pe *
+                                              ADG_MAX_STAGES * (MAXD + 1));
   ctx->delay_hist = (unsigned long long *)cv.take(sizeof(unsigned long long) * 2 * (MAXD + 1));
   // groups of equal degree and precision: tile sizes and tables
   ctx->n_groups = 0;
   for (int gk = 0; gk < ADG_MAX_GROUPS; ++gk) {
-    const int Q = 2 + gk / 2, prec = gk % 2;
-    auto member = [&](int k) { return cfgs[k].p + 1 == Q && cfgs[k].precision == prec; };
+    const int Q = 2 + (gk / 2) % ADG_MAX_P, prec = gk % 2, S = gk < 2 * ADG_MAX_P ? 3 : 5;
+    auto member = [&](int k) {
+      return cfgs[k].p + 1 == Q && cfgs[k].precision == prec &&
+             rk_stages(cfgs[k].integrator) == S;
+    };
     int64_t total = 0, tiles = 0, blocks = 0;
     bool lim = false, any = false;
     int O = 1;
@@ -339,6 +379,7 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
     Group &G = ctx->groups[ctx->n_groups++];
     G.Q = Q;
     G.mixed = prec == ADG_MIXED;
+    G.S = S;
     G.O = O;
     G.TE = stage_tile(M, Q, O, G.mixed);
     // smaller tiles when the group would not fill two CTAs per SM
@@ -371,12 +412,14 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
     I.wa = (double *)cv.take(sizeof(double) * st);
     I.wb = (double *)cv.take(sizeof(double) * st);
     I.wpre = (double *)cv.take(sizeof(double) * st);
+    const int S = rk_stages(c.integrator);
+    I.wq = (c.integrator != ADG_RK_SSP3) ? (double *)cv.take(sizeof(double) * st) : nullptr;
     // ring depth 2d + o: the synchronous modes need d + o levels, the
     // unsynchronised one up to 2d + o (a neighbour may run d steps ahead)
-    size_t rs = (size_t)(2 * c.max_delay + c.at_order) * 3 * (npf > 0 ? npf : 1) * 2 * nv;
+    size_t rs = (size_t)(2 * c.max_delay + c.at_order) * S * (npf > 0 ? npf : 1) * 2 * nv;
     I.ring_in = (double *)cv.take(sizeof(double) * rs);
     I.ring_pre = (double *)cv.take(sizeof(double) * rs * Q);
-    I.flags = (uint8_t *)cv.take((size_t)3 * N);
+    I.flags = (uint8_t *)cv.take((size_t)S * N);
     I.count = (int32_t *)cv.take(sizeof(int32_t) * N);
     I.pf_of_left = (const int *)cv.take(sizeof(int) * N);
     I.pf_of_right = (const int *)cv.take(sizeof(int) * N);
@@ -396,7 +439,7 @@ static cudaError_t upload_tiles(adg_ctx *ctx, Group &G) {
   std::vector<int2> tl;
   for (int k = 0; k < ctx->n_inst; ++k) {
     const Inst &I = ctx->inst[k].d;
-    if (I.p + 1 != G.Q || (I.mixed != 0) != G.mixed) continue;
+    if (I.p + 1 != G.Q || (I.mixed != 0) != G.mixed || I.n_stages != G.S) continue;
     for (int e = 0; e < I.n_elem; e += G.TE) tl.push_back(make_int2(k, e));
   }
   G.n_tiles = (int)tl.size();
@@ -561,6 +604,9 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
     I.nv = nv;
     I.npf = npf;
     I.depth = 2 * c.max_delay + c.at_order;
+    I.n_stages = rk_stages(c.integrator);
+    for (int s = 0; s < ADG_MAX_STAGES; ++s) I.rk_a[s] = I.rk_b[s] = 0.0;
+    I.lserk = lserk_coefficients(c.integrator, I.rk_a, I.rk_b) > 0;
     I.at_order = c.at_order;
     I.bc_left = c.bc_left;
     I.bc_right = c.bc_right;
@@ -599,7 +645,7 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
     if (cudaMemcpy((void *)I.pf_of_left, pl.data(), sizeof(int) * N, cudaMemcpyHostToDevice) ||
         cudaMemcpy((void *)I.pf_of_right, pr.data(), sizeof(int) * N, cudaMemcpyHostToDevice) ||
         cudaMemcpy((void *)I.pf_elem, pe.data(), sizeof(int) * pe.size(), cudaMemcpyHostToDevice) ||
-        cudaMemset(I.flags, 0, (size_t)3 * N) || cudaMemset(I.count, 0, sizeof(int32_t) * N) ||
+        cudaMemset(I.flags, 0, (size_t)I.n_stages * N) || cudaMemset(I.count, 0, sizeof(int32_t) * N) ||
         cudaMemset(I.wn, 0, sizeof(double) * (size_t)nv * N * Q))
       rc2 = ADG_ERR_CUDA;
     h.n = 0;
@@ -617,7 +663,9 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
       const int epb = G.EPB;
       std::vector<int2> bl;
       for (int k = 0; k < n; ++k) {
-        if (cfgs[k].p + 1 != G.Q || (cfgs[k].precision == ADG_MIXED) != G.mixed) continue;
+        if (cfgs[k].p + 1 != G.Q || (cfgs[k].precision == ADG_MIXED) != G.mixed ||
+            rk_stages(cfgs[k].integrator) != G.S)
+          continue;
         for (int e = 0; e < cfgs[k].n_elem; e += epb) bl.push_back(make_int2(k, e));
       }
       if (upload_tiles(ctx, G) != cudaSuccess ||
@@ -663,7 +711,8 @@ static cudaError_t reset_history(adg_ctx *ctx, int k, cudaStream_t st) {
   h.n = 0;
   cudaError_t e = cudaMemsetAsync(ctx->d_steps + k, 0, sizeof(int64_t), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h.d.count, 0, sizeof(int32_t) * h.d.n_elem, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h.d.flags, 0, (size_t)3 * h.d.n_elem, st);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h.d.flags, 0, (size_t)h.d.n_stages * h.d.n_elem, st);
   return e;
 }
 
@@ -739,12 +788,16 @@ static cudaError_t timed_end(adg_ctx *ctx, cudaStream_t st) {
   return r;
 }
 
-// One SSP-RK3 step of every instance: per stage, the stage kernel and the
-// limiter of every degree group, then the step counters advance.
+// One step of every instance: per RK stage, the stage kernel and the limiter
+// of every group that has that stage, then the step counters advance.
 static int enqueue_step(adg_ctx *ctx, cudaStream_t st) {
-  for (int s = 0; s < 3; ++s) {
+  int max_s = 0;
+  for (int gi = 0; gi < ctx->n_groups; ++gi)
+    max_s = ctx->groups[gi].S > max_s ? ctx->groups[gi].S : max_s;
+  for (int s = 0; s < max_s; ++s) {
     for (int gi = 0; gi < ctx->n_groups; ++gi) {
       const Group &G = ctx->groups[gi];
+      if (s >= G.S) continue;
       StageArgs A;
       A.insts = ctx->d_insts;
       A.tiles = G.d_tiles;
@@ -758,7 +811,7 @@ static int enqueue_step(adg_ctx *ctx, cudaStream_t st) {
     }
     for (int gi = 0; gi < ctx->n_groups; ++gi) {
       const Group &G = ctx->groups[gi];
-      if (!G.any_limiter) continue;
+      if (!G.any_limiter || s >= G.S) continue;
       LimArgs L;
       L.insts = ctx->d_insts;
       L.blocks = G.d_blocks;
@@ -943,11 +996,12 @@ int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning) {
   *n_groups = ctx->n_groups;
   for (int gi = 0; gi < ctx->n_groups; ++gi) {
     const Group &G = ctx->groups[gi];
-    tuning[5 * gi + 0] = G.Q - 1;
-    tuning[5 * gi + 1] = G.mixed ? ADG_MIXED : ADG_FP64;
-    tuning[5 * gi + 2] = G.TE;
-    tuning[5 * gi + 3] = G.NT;
-    tuning[5 * gi + 4] = G.n_tiles;
+    tuning[6 * gi + 0] = G.Q - 1;
+    tuning[6 * gi + 1] = G.mixed ? ADG_MIXED : ADG_FP64;
+    tuning[6 * gi + 2] = G.TE;
+    tuning[6 * gi + 3] = G.NT;
+    tuning[6 * gi + 4] = G.n_tiles;
+    tuning[6 * gi + 5] = G.S;
   }
   return ADG_OK;
 }
@@ -961,7 +1015,9 @@ int adg_step_unsync(adg_ctx *ctx, int instance, int n_steps, void *stream) {
   const bool mixed = I.mixed != 0;
   const Group *G = nullptr;
   for (int gi = 0; gi < ctx->n_groups; ++gi)
-    if (ctx->groups[gi].Q == Q && ctx->groups[gi].mixed == mixed) G = &ctx->groups[gi];
+    if (ctx->groups[gi].Q == Q && ctx->groups[gi].mixed == mixed &&
+        ctx->groups[gi].S == I.n_stages)
+      G = &ctx->groups[gi];
   if (!G) return ADG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = st;
@@ -1017,7 +1073,8 @@ int adg_unsync_delays(adg_ctx *ctx, uint64_t *hist) {
 int adg_launches_per_step(const adg_ctx *ctx) {
   if (!ctx) return 0;
   int n = 1;
-  for (int gi = 0; gi < ctx->n_groups; ++gi) n += ctx->groups[gi].any_limiter ? 6 : 3;
+  for (int gi = 0; gi < ctx->n_groups; ++gi)
+    n += ctx->groups[gi].S * (ctx->groups[gi].any_limiter ? 2 : 1);
   return n;
 }
 
@@ -1086,7 +1143,8 @@ int adg_get_flags(adg_ctx *ctx, int k, uint8_t *last, int32_t *count) {
   if (!inst_ok(ctx, k)) return ADG_ERR_ARG;
   InstHost &h = ctx->inst[k];
   CK(cudaStreamSynchronize(ctx->last_stream));
-  if (last) CK(cudaMemcpy(last, h.d.flags, (size_t)3 * h.d.n_elem, cudaMemcpyDeviceToHost));
+  if (last)
+    CK(cudaMemcpy(last, h.d.flags, (size_t)h.d.n_stages * h.d.n_elem, cudaMemcpyDeviceToHost));
   if (count)
     CK(cudaMemcpy(count, h.d.count, sizeof(int32_t) * h.d.n_elem, cudaMemcpyDeviceToHost));
   return ADG_OK;

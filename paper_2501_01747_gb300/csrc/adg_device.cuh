@@ -111,8 +111,11 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   const int nv = I.nv, ns = M.ns, nr = M.nr, N = I.n_elem, TE = A.TE;
   const int TQ = TE * Q;
   const int teq = te * Q;
-  const double *A_win = (A.s == 0) ? I.wn : (A.s == 1) ? I.wa : I.wb;
-  double *A_wnext = (A.s == 0) ? I.wa : (A.s == 1) ? I.wb : I.wn;
+  const double *A_win = stage_input(I, A.s);
+  double *A_wnext = stage_output(I, A.s);
+  // stages after the first also read, per element, w^n (SSP-RK3) or the LSERK
+  // register dq
+  const double *A_wacc = I.lserk ? I.wq : I.wn;
   const bool periodic = (I.bc_left == ADG_BC_PERIODIC);
   const int O = A.O, NF = TE + 1;
   Rxn *srx = reinterpret_cast<Rxn *>(sm);
@@ -172,7 +175,8 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
     }
   }
   // 1. tile of modal coefficients with a one-element halo on each side and, for
-  // stages 1 and 2, the tile's modes of w^n (batches of loads in flight)
+  // stages after the first, the tile's modes of w^n or dq (batches of loads in
+  // flight)
   {
     constexpr int BATCH = 4;
     const int span = (te + 2) * Q, n_tile = nv * span;
@@ -195,7 +199,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
           dst[b] = sw + ((size_t)v * (TE + 2) + le) * Q + j;
         } else if (idx < total) {
           const int k = idx - n_tile, v = k / (te * Q), r = k - v * te * Q;
-          xs[b] = I.wn[((size_t)v * N + e0) * Q + r];
+          xs[b] = A_wacc[((size_t)v * N + e0) * Q + r];
           dst[b] = swn + (size_t)v * TQ + r;
         }
       }
@@ -416,7 +420,13 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       double r = (double)fma((DG)((2.0 * i + 1.0) * inv_dx), surf, Wv * S);
       size_t gi = ((size_t)v * N + ge) * Q + i;
       double o;
-      if (A.s == 0) {
+      if (I.lserk) {
+        // 2N-storage LSERK: dq <- A_s dq + dt L, w <- w + B_s dq (A_0 = 0)
+        const double dq =
+            (A.s == 0) ? I.dt * r : fma(I.rk_a[A.s], swn[(size_t)v * TQ + e * Q + i], I.dt * r);
+        I.wq[gi] = dq;
+        o = fma(I.rk_b[A.s], dq, wi[i]);
+      } else if (A.s == 0) {
         o = fma(I.dt, r, wi[i]);  // the stage input is w^n
       } else {
         const double wn = swn[(size_t)v * TQ + e * Q + i];
@@ -794,7 +804,7 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
   constexpr int EPW = 32 / G;
   constexpr int NWARP = LIM_THREADS / 32;
   const int slot = warp * EPW + gw;
-  double *A_wout = (A.s == 0) ? I.wa : (A.s == 1) ? I.wb : I.wn;
+  double *A_wout = stage_output(I, A.s);
   const double *A_wpre = I.wpre;
   const unsigned FULL = 0xffffffffu;
   const unsigned gmask = (G == 32) ? FULL : (0xffffu << (16 * gw));

@@ -68,15 +68,18 @@ int pack_mechanism(const adg_mechanism *m, double *sp, Rxn *rx, int *sx_off, int
 // Per-instance description, passed by value to the kernels.
 struct Inst {
   int n_elem, p, nv, npf, depth, at_order;
+  int n_stages, lserk;                  // RK stages per step; 2N-storage LSERK scheme
+  double rk_a[ADG_MAX_STAGES], rk_b[ADG_MAX_STAGES];  // its A_s, B_s
   int bc_left, bc_right, flux, limiter, delay_mode, max_delay;
   double dx, dt, tvb;
   uint64_t seed;
   double cum[MAXD + 1];                 // cumulative SAA probabilities
   double at[MAXD + 1][MAXO];            // AT weights c_m(k)
-  double *wn, *wa, *wb, *wpre;          // [nv][N][Q]: w^n, stage 1 and 2 inputs, pre-limit
-  double *ring_in;   // history of the stage inputs' face traces [depth][3][npf][2][nv]
-  double *ring_pre;  // history of the pre-limit outputs [depth][3][npf][2][nv][p+1]
-  uint8_t *flags;                       // [3][N]
+  double *wn, *wa, *wb, *wpre;          // [nv][N][Q]: w^n, stage inputs, pre-limit
+  double *wq;                           // [nv][N][Q]: the LSERK register dq (or null)
+  double *ring_in;   // history of the stage inputs' face traces [depth][S][npf][2][nv]
+  double *ring_pre;  // history of the pre-limit outputs [depth][S][npf][2][nv][p+1]
+  uint8_t *flags;                       // [S][N]
   int32_t *count;                       // [N]
   const int *pf_of_left;                // per element: PE face on its left face or -1
   const int *pf_of_right;               // per element: PE face on its right face or -1
@@ -114,13 +117,24 @@ __device__ inline int effective_delay(const Inst &I, int64_t n, int f) {
 
 __device__ inline size_t ring_block(const Inst &I, int64_t level, int s, int pf, int side) {
   int slot = (int)(level % I.depth);
-  return ((((size_t)slot * 3 + s) * I.npf + pf) * 2 + side) * (size_t)I.nv * (I.p + 1);
+  return ((((size_t)slot * I.n_stages + s) * I.npf + pf) * 2 + side) * (size_t)I.nv * (I.p + 1);
+}
+
+// Stage buffers: stage s reads w^n (s = 0) or the previous stage's output, and
+// writes the next stage's input, the last stage w^{n+1}; the two intermediate
+// buffers alternate (3 stages: w^n -> wa -> wb -> w^n; 5 stages: w^n -> wa ->
+// wb -> wa -> wb -> w^n).
+__host__ __device__ inline const double *stage_input(const Inst &I, int s) {
+  return s == 0 ? I.wn : (s & 1) ? I.wa : I.wb;
+}
+__host__ __device__ inline double *stage_output(const Inst &I, int s) {
+  return s == I.n_stages - 1 ? I.wn : (s & 1) ? I.wb : I.wa;
 }
 
 // Offset of the face-trace record (nv values) of one side of a PE face.
 __device__ inline size_t ring_trace(const Inst &I, int64_t level, int s, int pf, int side) {
   int slot = (int)(level % I.depth);
-  return ((((size_t)slot * 3 + s) * I.npf + pf) * 2 + side) * (size_t)I.nv;
+  return ((((size_t)slot * I.n_stages + s) * I.npf + pf) * 2 + side) * (size_t)I.nv;
 }
 
 __device__ inline void report_error(const Inst &I, int code, int elem, int stage, int64_t n) {
@@ -298,7 +312,8 @@ struct UnsyncArgs {
   int n_pe, npf, n_steps, TE, O;  // PEs, PE faces, steps, elements per stage tile, AT levels
   int EPB;                        // elements per limiter block (as the group's launches)
   int *pub_in, *pub_pre;          // [n_pe] stages published (stage inputs, pre-limit outputs)
-  unsigned long long *agree;      // [npf][3][MAXD + 1] common flux level: (level + 1) << 8 | k
+  unsigned long long *agree;      // [npf][ADG_MAX_STAGES][MAXD + 1] common flux level:
+                                  // (level + 1) << 8 | k
   unsigned long long *hist;       // [2][MAXD + 1] delays observed: flux, limiter
   long long spin_limit;           // polls of a counter before a wait gives up
   int withheld;                   // a PE that never publishes (tests the timeout), or -1

@@ -85,7 +85,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
       (c.limiter != ADG_LIM_NONE && c.limiter != ADG_LIM_WENO) || c.bc_left < 0 ||
       c.bc_left > 2 || c.bc_right < 0 || c.bc_right > 2 ||
       ((c.bc_left == ADG_BC_PERIODIC) != (c.bc_right == ADG_BC_PERIODIC)) ||
-      (c.precision != ADG_FP64 && c.precision != ADG_MIXED))
+      (c.precision != ADG_FP64 && c.precision != ADG_MIXED) || c.integrator != ADG_RK_SSP3)
     return ADG_ERR_ARG;
   if (!mech->W || !mech->cp || !mech->h_f || !mech->s0) return ADG_ERR_ARG;
   if (nr > 0 && (!mech->nu_f || !mech->nu_r || !mech->A || !mech->b || !mech->Ea))
@@ -173,6 +173,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   I.nv = nv;
   I.npf = npf;
   I.depth = depth;
+  I.n_stages = 3;  // SSP-RK3 (memset left lserk = 0, wq = null)
   I.at_order = c.at_order;
   I.bc_left = c.bc_left;
   I.bc_right = c.bc_right;

@@ -43,11 +43,11 @@ namespace adg {
 namespace {
 
 // Newest level with stage s published by a neighbour that has published `done`
-// stages (3 n + s + 1 after stage s of step n), and the usable delay at step n:
-// k = max(0, n - L) when k = 0, or k <= d with levels L - o + 1 .. L present;
-// else -1 (wait).
-__device__ inline int usable_delay(int done, long long n, int s, int d, int o) {
-  const long long L = done >= s + 1 ? (long long)(done - s - 1) / 3 : -1;
+// stages (S n + s + 1 after stage s of step n, S stages per step), and the
+// usable delay at step n: k = max(0, n - L) when k = 0, or k <= d with levels
+// L - o + 1 .. L present; else -1 (wait).
+__device__ inline int usable_delay(int done, long long n, int s, int S, int d, int o) {
+  const long long L = done >= s + 1 ? (long long)(done - s - 1) / S : -1;
   const long long k = L >= n ? 0 : n - L;
   if (k == 0) return 0;
   if (k <= d && L >= o - 1) return (int)k;
@@ -55,11 +55,11 @@ __device__ inline int usable_delay(int done, long long n, int s, int d, int o) {
 }
 
 // Spin (thread 0) until the neighbour's counter gives a usable delay.
-__device__ inline int wait_delay(const int *pub, long long n, int s, int d, int o,
+__device__ inline int wait_delay(const int *pub, long long n, int s, int S, int d, int o,
                                  long long limit) {
   for (long long it = 0; it <= limit; ++it) {
     const int done = *(const volatile int *)pub;
-    const int k = usable_delay(done, n, s, d, o);
+    const int k = usable_delay(done, n, s, S, d, o);
     if (k >= 0) {
       __threadfence();  // what the neighbour wrote before its counter is now visible
       return k;
@@ -91,7 +91,7 @@ __device__ inline int agree_delay(unsigned long long *slot, long long n, int k) 
 
 __device__ inline unsigned long long *agree_slot(const UnsyncArgs &U, int pf, int s,
                                                  long long n) {
-  return U.agree + ((size_t)pf * 3 + s) * (MAXD + 1) + (size_t)(n % (MAXD + 1));
+  return U.agree + ((size_t)pf * ADG_MAX_STAGES + s) * (MAXD + 1) + (size_t)(n % (MAXD + 1));
 }
 
 }  // namespace
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(LIM_THREADS) unsync_kernel(Mech M, UnsyncArgs 
   const int first = (int)((long long)q * N / P), last = (int)((long long)(q + 1) * N / P) - 1;
   const int pfl = I.pf_of_left[first], pfr = I.pf_of_right[last];
   const int ql = (q + P - 1) % P, qr = (q + 1) % P;
-  const int d = I.max_delay, o = I.at_order;
+  const int d = I.max_delay, o = I.at_order, S = I.n_stages;
   const long long n0 = *I.step;
   if (tid == 0) {
     pdi.first = pdp.first = first;
@@ -127,9 +127,9 @@ __global__ void __launch_bounds__(LIM_THREADS) unsync_kernel(Mech M, UnsyncArgs 
   L.blocks = nullptr;
   L.EPB = EPB;
   for (long long n = n0; n < n0 + U.n_steps; ++n) {
-    for (int s = 0; s < 3; ++s) {
-      const int c = (int)(3 * n + s);
-      const double *win = (s == 0) ? I.wn : (s == 1) ? I.wa : I.wb;
+    for (int s = 0; s < S; ++s) {
+      const int c = (int)(S * n + s);
+      const double *win = stage_input(I, s);
       // a. the traces of the stage input at the PE faces: the first element's at
       // xi = -1 (right side of the left PE face), the last element's at xi = +1
       // (left side of the right PE face), summed as the stage kernel sums them
@@ -160,11 +160,11 @@ __global__ void __launch_bounds__(LIM_THREADS) unsync_kernel(Mech M, UnsyncArgs 
         }
         int kl = 0, kr = 0;
         if (pfl >= 0) {
-          kl = wait_delay(&U.pub_in[ql], n, s, d, o, U.spin_limit);
+          kl = wait_delay(&U.pub_in[ql], n, s, S, d, o, U.spin_limit);
           if (kl >= 0) kl = agree_delay(agree_slot(U, pfl, s, n), n, kl);
         }
         if (pfr >= 0 && kl >= 0) {
-          kr = wait_delay(&U.pub_in[qr], n, s, d, o, U.spin_limit);
+          kr = wait_delay(&U.pub_in[qr], n, s, S, d, o, U.spin_limit);
           if (kr >= 0) kr = agree_delay(agree_slot(U, pfr, s, n), n, kr);
         }
         pdi.k[0] = kl;
@@ -192,8 +192,8 @@ __global__ void __launch_bounds__(LIM_THREADS) unsync_kernel(Mech M, UnsyncArgs 
           atomicExch(&U.pub_pre[q], c + 1);
         }
         int kl = 0, kr = 0;
-        if (pfl >= 0) kl = wait_delay(&U.pub_pre[ql], n, s, d, o, U.spin_limit);
-        if (pfr >= 0 && kl >= 0) kr = wait_delay(&U.pub_pre[qr], n, s, d, o, U.spin_limit);
+        if (pfl >= 0) kl = wait_delay(&U.pub_pre[ql], n, s, S, d, o, U.spin_limit);
+        if (pfr >= 0 && kl >= 0) kr = wait_delay(&U.pub_pre[qr], n, s, S, d, o, U.spin_limit);
         pdp.k[0] = kl;
         pdp.k[1] = kr;
         if (kl < 0 || kr < 0) {
@@ -222,11 +222,11 @@ static __global__ void unsync_reset_kernel(const Inst *inst, int *pub_in, int *p
                                     unsigned long long *agree, int n_pe, int npf) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < n_pe) {
-    const int c = (int)(3 * *inst->step);
+    const int c = (int)(inst->n_stages * *inst->step);
     pub_in[q] = c;
     pub_pre[q] = c;
   }
-  if (q < npf * 3 * (MAXD + 1)) agree[q] = 0ull;
+  if (q < npf * ADG_MAX_STAGES * (MAXD + 1)) agree[q] = 0ull;
 }
 
 template <int Q, int G, bool MIX, int EPB>
@@ -242,7 +242,8 @@ cudaError_t unsync_launch_q(const Mech &M, const UnsyncArgs &U, int nv, cudaStre
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   if ((long long)per_sm * n_sm < U.n_pe) return cudaErrorCooperativeLaunchTooLarge;
-  const int n_reset = U.n_pe > U.npf * 3 * (MAXD + 1) ? U.n_pe : U.npf * 3 * (MAXD + 1);
+  const int n_agree = U.npf * ADG_MAX_STAGES * (MAXD + 1);
+  const int n_reset = U.n_pe > n_agree ? U.n_pe : n_agree;
   unsync_reset_kernel<<<(n_reset + 127) / 128, 128, 0, st>>>(U.inst, U.pub_in, U.pub_pre,
                                                              U.agree, U.n_pe, U.npf);
   e = cudaGetLastError();
