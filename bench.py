@@ -163,8 +163,12 @@ def cpu_baseline(wls, mech, budget_s=12.0, max_steps=40):
             "sample": "%s, first %d steps (%.1f s, 1 thread)" % (wl.name, n, dt)}
 
 
+def rk_stages(w):
+    return 5 if getattr(w, "integrator", I.RK_SSP3) == I.RK_LS4 else 3
+
+
 def dof_stages_per_step(wls):
-    return sum(w.n_elem * (w.p + 1) * 3 for w in wls)
+    return sum(w.n_elem * (w.p + 1) * rk_stages(w) for w in wls)
 
 
 def run_reference(args, ws, rank):
@@ -446,6 +450,9 @@ def main(argv=None):
     ap.add_argument("--unsync-steps", type=int, default=100,
                     help="steps of the unsynchronised-mode measurement added to the line "
                          "(single-instance workloads; 0 to skip)")
+    ap.add_argument("--lserk-steps", type=int, default=100,
+                    help="timed steps of the LSERK4 measurement (the 5-stage 4th-order "
+                         "low-storage integrator) added to the line; 0 to skip")
     ap.add_argument("--ensemble-steps", type=int, default=20,
                     help="timed steps of the batched-ensemble measurement added to the line "
                     "(0: none)")
@@ -474,6 +481,11 @@ def main(argv=None):
     if args.unsync_steps > 0 and len(wls) == 1 and not args.only:
         uns = unsync_measure(adg, torch, wls[0], mech, prims[0], args.precision, dev,
                              args.warmup, args.unsync_steps)
+    lsk = None
+    if args.lserk_steps > 0 and len(wls) == 1 and not args.only:
+        lw = dataclasses.replace(wls[0], integrator=I.RK_LS4, name=wls[0].name + "-lserk4")
+        lsk = (lw, measure(adg, torch, [lw], mech, prims, args.precision, args, dev, pg, ws,
+                           args.lserk_steps))
     ens = None
     if args.ensemble_steps > 0 and args.workload != ENSEMBLE and not args.only:
         ewls, emech = bench_workloads(ENSEMBLE)
@@ -513,6 +525,14 @@ def main(argv=None):
         line["mixed_error"] = err
     if uns is not None:
         line["unsync"] = uns
+    if lsk is not None:
+        lw, r = lsk
+        line["lserk4"] = {
+            "integrator": "LSERK 5-stage 4th order (2N storage), limiter after every stage",
+            "stages_per_step": 5, "value": r["value"], "unit": "DOF-stage/s",
+            "steps": args.lserk_steps, "ms_per_step": r["ms"] / args.lserk_steps,
+            "e2e": r["e2e"], "roofline": roofline([lw], mech, r, mixed, peaks, src),
+            "clocks": r["clocks"], "tuning": r["tuning"]}
     if ens is not None:
         ewls, emech, eh, eo, eop, ee = ens
         rec = {"config": dict(workload_config(ewls, emech, args), tuning=eh["tuning"]),
