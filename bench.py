@@ -402,7 +402,8 @@ def roofline(wls, mech, r, mixed, peaks, src):
     """Roofline of the stage kernel (the dominant one): the algorithmic flops of
     one RK stage of every instance over the stage kernels' time for one stage
     (all degree groups), against the FP64 peak, the pipe that bounds it."""
-    stage_s = r["kms"][0] / 1e3 / (3 * r["steps"])
+    n_st = max(rk_stages(w) for w in wls)  # stage launches per step (uniform here)
+    stage_s = r["kms"][0] / 1e3 / (n_st * r["steps"])
     flops = sum(stage_kernel_flops(w, mech)[0] for w in wls)
     n_exp = sum(stage_kernel_flops(w, mech)[1] for w in wls)
     achieved = flops / stage_s / 1e12
@@ -414,7 +415,7 @@ def roofline(wls, mech, r, mixed, peaks, src):
             "kernel": "stage_kernel (%s)" % ("mixed" if mixed else "fp64"),
             "kernel_ms": stage_s * 1e3, "exp_per_s": n_exp / stage_s,
             "kernel_share": r["kms"][0] / max(1e-9, r["kms"][0] + r["kms"][1]),
-            "limiter_ms": r["kms"][1] / (3 * r["steps"]),
+            "limiter_ms": r["kms"][1] / (n_st * r["steps"]),
             "peak_source": "FP64 pipe: 152 SM x 4 flop/clk x 2.07 GHz (derived)",
             "hbm_achieved_gbs": hbm, "hbm_peak_gbs": peaks.get("hbm_gbs"),
             "hbm_frac": hbm / peaks.get("hbm_gbs", 6800.0), "hbm_peak_source": src}
