@@ -38,7 +38,7 @@ class Mech(C.Structure):
                 ("hf", C.POINTER(C.c_double)), ("s0", C.POINTER(C.c_double)),
                 ("nu_f", C.POINTER(C.c_byte)), ("nu_r", C.POINTER(C.c_byte)),
                 ("A", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)),
-                ("Ea", C.POINTER(C.c_double))]
+                ("Ea", C.POINTER(C.c_double)), ("Le", C.POINTER(C.c_double))]
 
 
 class Cfg(C.Structure):
@@ -47,7 +47,9 @@ class Cfg(C.Structure):
                 ("bc_left", C.c_int), ("bc_right", C.c_int), ("flux", C.c_int),
                 ("limiter", C.c_int), ("at_order", C.c_int), ("delay_mode", C.c_int),
                 ("max_delay", C.c_int), ("delay_probs", C.POINTER(C.c_double)),
-                ("seed", C.c_uint64), ("tvb_M", C.c_double), ("integrator", C.c_int)]
+                ("seed", C.c_uint64), ("tvb_M", C.c_double), ("integrator", C.c_int),
+                ("viscous", C.c_int), ("mu_ref", C.c_double), ("T_mu", C.c_double),
+                ("mu_exp", C.c_double), ("prandtl", C.c_double)]
 
 
 _lib = None
@@ -87,6 +89,10 @@ def lib():
         _lib.or_beta_matrix.argtypes = [C.c_int, d]
         _lib.or_shift_matrix.argtypes = [C.c_int, C.c_int, d]
         _lib.or_rhs_sync.argtypes = [C.POINTER(Cfg), C.POINTER(Mech), d, d]
+        _lib.or_aux_sync.argtypes = [C.POINTER(Cfg), C.POINTER(Mech), d, d]
+        _lib.or_transport.argtypes = [C.POINTER(Mech), C.POINTER(Cfg), C.c_double, C.c_double,
+                                      d, d, d, d]
+        _lib.or_visc_flux.argtypes = [C.POINTER(Mech), C.POINTER(Cfg), d, d, d]
         _lib.or_reactor0d.argtypes = [C.POINTER(Mech), d, C.c_double, C.c_double, C.c_int]
     return _lib
 
@@ -105,10 +111,13 @@ class MechHandle:
         self.nu_r = np.ascontiguousarray(mech.nu_r, dtype=np.int8)
         W, cp, hf, s0, A, b, Ea = self.arrays
         self.ns, self.nr = int(W.shape[0]), int(A.shape[0])
+        le = getattr(mech, "Le", None)
+        self.Le = None if le is None else np.ascontiguousarray(le, dtype=np.float64)
         self.s = Mech(self.ns, self.nr, _dp(W), _dp(cp), _dp(hf), _dp(s0),
                       self.nu_f.ctypes.data_as(C.POINTER(C.c_byte)),
                       self.nu_r.ctypes.data_as(C.POINTER(C.c_byte)),
-                      _dp(A), _dp(b), _dp(Ea))
+                      _dp(A), _dp(b), _dp(Ea),
+                      _dp(self.Le) if self.Le is not None else C.POINTER(C.c_double)())
 
     @property
     def ref(self):
@@ -121,8 +130,44 @@ def make_cfg(wl, dt=None):
     cfg = Cfg(wl.n_elem, wl.p, wl.n_pe, wl.x0, wl.length, wl.dt if dt is None else dt,
               wl.bc_left, wl.bc_right, wl.flux, wl.limiter, wl.at_order, wl.delay_mode,
               wl.max_delay, _dp(probs), wl.seed & ((1 << 64) - 1), wl.tvb_M,
-              getattr(wl, "integrator", 0))
+              getattr(wl, "integrator", 0), getattr(wl, "viscous", 0),
+              getattr(wl, "mu_ref", 0.0), getattr(wl, "T_mu", 300.0),
+              getattr(wl, "mu_exp", 0.7), getattr(wl, "prandtl", 0.7))
     return cfg, probs
+
+
+def visc_flux(wl, mech, w, q):
+    """f^d(w, q) at one point (w, q: [nv])."""
+    cfg, probs = make_cfg(wl)
+    mh = MechHandle(mech)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    fd = np.zeros_like(w)
+    lib().or_visc_flux(mh.ref, C.byref(cfg), _dp(w), _dp(q), _dp(fd))
+    return fd
+
+
+def transport(wl, mech, rho, T, Y):
+    """(mu, k, D[ns]) of the synthetic transport model."""
+    cfg, probs = make_cfg(wl)
+    mh = MechHandle(mech)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    mu, kc, D = np.zeros(1), np.zeros(1), np.zeros(mh.ns)
+    lib().or_transport(mh.ref, C.byref(cfg), float(rho), float(T), _dp(Y), _dp(mu), _dp(kc),
+                       _dp(D))
+    return float(mu[0]), float(kc[0]), D
+
+
+def aux_sync(wl, mech, w):
+    """The LDG auxiliary variable q = dw/dx of a modal state (no delays)."""
+    cfg, probs = make_cfg(wl)
+    mh = MechHandle(mech)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    q = np.zeros_like(w)
+    rc = lib().or_aux_sync(C.byref(cfg), mh.ref, _dp(w), _dp(q))
+    if rc != 0:
+        raise RuntimeError("or_aux_sync failed (%d)" % rc)
+    return q
 
 
 def rk_stages(integrator):

@@ -296,6 +296,82 @@ void or_phys_flux(const or_mech *m, const double *w, double *f) {
   for (int i = 0; i < m->ns; ++i) f[2 + i] = u * w[2 + i];
 }
 
+/* Mixture transport (Sec. 2 names the viscosity mu, the conductivity k and the
+ * mixture-averaged diffusion coefficients D_i^mix; the paper takes them from
+ * Cantera). Reading, a synthetic model: mu = mu_ref (T/T_mu)^mu_exp for the
+ * mixture, k = mu cp / Pr with cp the mixture's specific heat per unit mass, and
+ * D_i = k / (rho cp Le_i) with a Lewis number per species. */
+void or_transport(const or_mech *m, const or_cfg *cfg, double rho, double T, const double *Y,
+                  double *mu, double *kc, double *D) {
+  double cpm = 0.0;
+  for (int i = 0; i < m->ns; ++i) cpm += Y[i] * m->cp[i] / m->W[i];
+  *mu = cfg->mu_ref * pow(T / cfg->T_mu, cfg->mu_exp);
+  *kc = *mu * cpm / cfg->prandtl;
+  for (int i = 0; i < m->ns; ++i) D[i] = *kc / (rho * cpm * (m->Le ? m->Le[i] : 1.0));
+}
+
+/* Diffusive flux of Sec. 2 at one point, from the conserved state w and its
+ * x-derivative q (the LDG auxiliary variable): (tau, tau u - q_h, -J_1 .. -J_Ns)
+ * with tau = 4/3 mu du/dx, q_h = -k dT/dx + sum h_i J_i, J_i = rho Y_i V_i and
+ * V_i = -(D_i / X_i) dX_i/dx. Reading: the correction velocity
+ * V_c = -sum Y_j V_j is added to every V_i so that sum J_i = 0, as the density
+ * equation carries no diffusive flux. The primitive derivatives follow from q by
+ * the chain rule: rho_x = sum q_{rho Y_i}, u_x = (q_{rho u} - u rho_x) / rho,
+ * Y_i,x = (q_{rho Y_i} - Y_i rho_x) / rho, and from
+ * rho E - (rho u) u / 2 = sum rho Y_i e_i(T):
+ * T_x = (q_{rho E} - (q_{rho u} u + rho u u_x) / 2 - sum q_{rho Y_i} e_i(T))
+ *       / sum rho Y_i c_v,i.
+ * X_i = (Y_i / W_i) / n with n = sum Y_j / W_j, so Y_i / X_i = W_i n and
+ * J_i = -rho D_i W_i n dX_i/dx, with dX_i/dx = (Y_i,x / W_i - X_i n_x) / n. */
+void or_visc_flux(const or_mech *m, const or_cfg *cfg, const double *w, const double *q,
+                  double *fd) {
+  int ns = m->ns;
+  const double *r = w + 2, *qr = q + 2;
+  double rho = 0.0, rho_x = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    rho += r[i];
+    rho_x += qr[i];
+  }
+  double u = w[0] / rho;
+  double u_x = (q[0] - u * rho_x) / rho;
+  double Y[MAXV], Yx[MAXV], D[MAXV], J[MAXV];
+  for (int i = 0; i < ns; ++i) {
+    Y[i] = r[i] / rho;
+    Yx[i] = (qr[i] - Y[i] * rho_x) / rho;
+  }
+  double T;
+  or_temperature(m, r, w[1] - 0.5 * w[0] * u, 1000.0, &T);
+  double num = q[1] - 0.5 * (q[0] * u + w[0] * u_x), den = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    num -= qr[i] * sp_e(m, i, T);
+    den += r[i] * (m->cp[i] - RU) / m->W[i];
+  }
+  double T_x = num / den;
+  double n = 0.0, n_x = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    n += Y[i] / m->W[i];
+    n_x += Yx[i] / m->W[i];
+  }
+  double mu, kc;
+  or_transport(m, cfg, rho, T, Y, &mu, &kc, D);
+  double Jsum = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    double X = Y[i] / (m->W[i] * n);
+    double X_x = (Yx[i] / m->W[i] - X * n_x) / n;
+    J[i] = -rho * D[i] * m->W[i] * n * X_x;
+    Jsum += J[i];
+  }
+  double qh = -kc * T_x;
+  for (int i = 0; i < ns; ++i) {
+    J[i] -= Y[i] * Jsum; /* correction velocity */
+    qh += (m->hf[i] + m->cp[i] * (T - TREF)) / m->W[i] * J[i];
+  }
+  double tau = 4.0 / 3.0 * mu * u_x;
+  fd[0] = tau;
+  fd[1] = tau * u - qh;
+  for (int i = 0; i < ns; ++i) fd[2 + i] = -J[i];
+}
+
 /* kind 0: local Lax-Friedrichs (Sec. 3.1), lambda = max(|u|+a) of both sides.
  * kind 1: HLLC (Toro 1994) with wave speeds S_L = min(u_L - a_L, u_R - a_R),
  *         S_R = max(u_L + a_L, u_R + a_R); species ride with the contact. */
@@ -437,7 +513,10 @@ struct or_ctx {
   int S;                 /* RK stages per step */
   double *w, *w0, *win, *wpre, *rhs, *fhat;
   double *dq;            /* LSERK register (2N storage) */
+  double *qx;            /* LDG auxiliary variable q = dw/dx of the stage input */
+  double *what;          /* [ne+1][nv] central face values of w for q */
   double *ring_in, *ring_pre; /* [depth][S][npf][2][nv*np1] */
+  double *ring_q;        /* history of q of the PE-boundary elements, same layout */
   int64_t *ring_level;
   int *keff;
   int64_t n;
@@ -500,12 +579,13 @@ int or_lserk_coeffs(int integrator, double *A, double *B, double *C) {
 or_ctx *or_create(const or_cfg *cfg, const or_mech *m) {
   if (cfg->p < 0 || cfg->p + 1 > MAXQ || m->ns + 2 > MAXV || cfg->n_elem < 1 ||
       cfg->n_pe < 1 || cfg->n_pe > cfg->n_elem || cfg->at_order < 1 ||
+      (cfg->viscous && (!(cfg->mu_ref >= 0.0) || !(cfg->T_mu > 0.0) || !(cfg->prandtl > 0.0))) ||
       cfg->integrator < 0 || cfg->integrator > 2)
     return NULL;
   or_ctx *c = (or_ctx *)calloc(1, sizeof(or_ctx));
   c->cfg = *cfg;
   int ns = m->ns, nr = m->nr;
-  c->mbuf = (double *)malloc(sizeof(double) * (4 * ns + 3 * (nr > 0 ? nr : 1)));
+  c->mbuf = (double *)malloc(sizeof(double) * (5 * ns + 3 * (nr > 0 ? nr : 1)));
   c->nubuf = (signed char *)malloc((size_t)2 * (nr > 0 ? nr : 1) * ns);
   double *mb = c->mbuf;
   memcpy(mb, m->W, sizeof(double) * ns);
@@ -528,6 +608,11 @@ or_ctx *or_create(const or_cfg *cfg, const or_mech *m) {
   c->m.A = mb + 4 * ns;
   c->m.b = mb + 4 * ns + nr;
   c->m.Ea = mb + 4 * ns + 2 * nr;
+  {
+    double *le = mb + 4 * ns + 3 * (nr > 0 ? nr : 1);
+    for (int i = 0; i < ns; ++i) le[i] = m->Le ? m->Le[i] : 1.0;
+    c->m.Le = le;
+  }
   c->m.nu_f = c->nubuf;
   c->m.nu_r = c->nubuf + (size_t)nr * ns;
   c->probs = (double *)malloc(sizeof(double) * (cfg->max_delay + 1));
@@ -586,10 +671,13 @@ or_ctx *or_create(const or_cfg *cfg, const or_mech *m) {
   c->wpre = (double *)calloc(sz, sizeof(double));
   c->rhs = (double *)calloc(sz, sizeof(double));
   c->dq = (double *)calloc(sz, sizeof(double));
+  c->qx = (double *)calloc(sz, sizeof(double));
+  c->what = (double *)calloc((size_t)(ne + 1) * c->nv, sizeof(double));
   c->fhat = (double *)calloc((size_t)(ne + 1) * c->nv, sizeof(double));
   size_t rsz = (size_t)c->depth * c->S * (c->npf > 0 ? c->npf : 1) * 2 * c->nv * q;
   c->ring_in = (double *)calloc(rsz, sizeof(double));
   c->ring_pre = (double *)calloc(rsz, sizeof(double));
+  c->ring_q = (double *)calloc(rsz, sizeof(double));
   c->ring_level = (int64_t *)malloc(sizeof(int64_t) * c->depth);
   for (int s = 0; s < c->depth; ++s) c->ring_level[s] = -1;
   c->keff = (int *)calloc(c->npf > 0 ? c->npf : 1, sizeof(int));
@@ -615,6 +703,9 @@ void or_destroy(or_ctx *c) {
   free(c->wpre);
   free(c->rhs);
   free(c->dq);
+  free(c->qx);
+  free(c->what);
+  free(c->ring_q);
   free(c->fhat);
   free(c->ring_in);
   free(c->ring_pre);
@@ -698,6 +789,79 @@ static void ghost_trace(const or_ctx *c, int bc, const double *in, double *out) 
   if (bc == 1) out[0] = -in[0];
 }
 
+/* boundary ghost of a derivative trace: the x-derivative of the mirror image
+ * (reflecting wall: d(rho u)/dx kept, the others negated) or a copy (outflow) */
+static void ghost_qtrace(const or_ctx *c, int bc, const double *in, double *out) {
+  for (int v = 0; v < c->nv; ++v) out[v] = (bc == 1 && v > 0) ? -in[v] : in[v];
+}
+
+/* The LDG auxiliary variable q = dw/dx (Sec. 3.1: evaluated like w with a
+ * central flux) of the stage input, per element and mode:
+ *   (dx / (2i+1)) q_i = w_hat_{e+1} - (-1)^i w_hat_e - sum_k omega_k w(xi_k) P_i'(xi_k),
+ * w_hat the mean of the two traces at a face; at a PE face with delay k > 0 the
+ * AT extrapolation (Eq. 7) of the means at the common delayed levels n-k-m; at a
+ * physical boundary the mean with the ghost (reflecting wall: mirror image;
+ * outflow: a copy, so the interior trace). */
+static int aux_eval(or_ctx *c, const double *win, int s, int use_hist) {
+  int nv = c->nv, q = c->np1, ne = c->ne;
+  double blk[MAXV * MAXQ], wl[MAXV], wr[MAXV], g[MAXV], cm[16];
+  int periodic = (c->cfg.bc_left == 0);
+  for (int i = 0; i <= ne; ++i) {
+    double *wh = c->what + (size_t)i * nv;
+    if (periodic && i == ne) {
+      memcpy(wh, c->what, sizeof(double) * nv);
+      continue;
+    }
+    int pf = c->face_pf[i];
+    int k = (use_hist && pf >= 0) ? c->keff[pf] : 0;
+    if (k > 0) {
+      int o = c->cfg.at_order;
+      or_at_coeffs(o, k, cm);
+      for (int v = 0; v < nv; ++v) wh[v] = 0.0;
+      for (int mm = 0; mm < o; ++mm) {
+        int64_t lv = c->n - k - mm;
+        if (c->ring_level[lv % c->depth] != lv) return -3;
+        trace_of(c, ring_at(c, c->ring_in, lv, s, pf, 0), 1, wl);
+        trace_of(c, ring_at(c, c->ring_in, lv, s, pf, 1), 0, wr);
+        for (int v = 0; v < nv; ++v) wh[v] += cm[mm] * 0.5 * (wl[v] + wr[v]);
+      }
+      continue;
+    }
+    if (i == 0 && !periodic) {
+      elem_block(c, win, 0, blk);
+      trace_of(c, blk, 0, wr);
+      ghost_trace(c, c->cfg.bc_left, wr, g);
+      for (int v = 0; v < nv; ++v) wh[v] = 0.5 * (g[v] + wr[v]);
+    } else if (i == ne && !periodic) {
+      elem_block(c, win, ne - 1, blk);
+      trace_of(c, blk, 1, wl);
+      ghost_trace(c, c->cfg.bc_right, wl, g);
+      for (int v = 0; v < nv; ++v) wh[v] = 0.5 * (wl[v] + g[v]);
+    } else {
+      elem_block(c, win, (i == 0) ? ne - 1 : i - 1, blk);
+      trace_of(c, blk, 1, wl);
+      elem_block(c, win, i, blk);
+      trace_of(c, blk, 0, wr);
+      for (int v = 0; v < nv; ++v) wh[v] = 0.5 * (wl[v] + wr[v]);
+    }
+  }
+  for (int e = 0; e < ne; ++e)
+    for (int v = 0; v < nv; ++v)
+      for (int i = 0; i < q; ++i) {
+        double vol = 0.0;
+        for (int k = 0; k < q; ++k) {
+          double wk = 0.0;
+          for (int j = 0; j < q; ++j) wk += W_(win, v, e, j) * c->Pq[k * q + j];
+          vol += c->wq[k] * wk * c->dPq[k * q + i];
+        }
+        double sgn = (i % 2 == 0) ? 1.0 : -1.0;
+        W_(c->qx, v, e, i) = (2.0 * i + 1.0) / c->dx *
+                             (c->what[(size_t)(e + 1) * nv + v] - sgn * c->what[(size_t)e * nv + v] -
+                              vol);
+      }
+  return 0;
+}
+
 static int check_state(const or_ctx *c, const double *w) {
   double rho = 0.0;
   for (int i = 0; i < c->m.ns; ++i) rho += w[2 + i];
@@ -705,14 +869,29 @@ static int check_state(const or_ctx *c, const double *w) {
   return 0;
 }
 
+/* Numerical flux of the total flux f = f^c - f^d (Sec. 3.1) between two traces:
+ * the Riemann flux (LF or HLLC) of the convective part, minus the central mean of
+ * the diffusive part in viscous runs. */
+static void face_flux(const or_ctx *c, const double *wl, const double *ql, const double *wr,
+                      const double *qr, double *fh) {
+  or_num_flux(&c->m, c->cfg.flux, wl, wr, fh);
+  if (!c->cfg.viscous) return;
+  double dl[MAXV], dr[MAXV];
+  or_visc_flux(&c->m, &c->cfg, wl, ql, dl);
+  or_visc_flux(&c->m, &c->cfg, wr, qr, dr);
+  for (int v = 0; v < c->nv; ++v) fh[v] -= 0.5 * (dl[v] + dr[v]);
+}
+
 /* Semi-discrete right-hand side (Eq. 5) of stage s at step level n:
  * dw_i/dt = (2i+1)/dx [ sum_q w_q f(xi_q) P_i'(xi_q) - fhat_{e+1} + (-1)^i fhat_e ]
- *           + (2i+1)/2 sum_q w_q s(xi_q) P_i(xi_q).
+ *           + (2i+1)/2 sum_q w_q s(xi_q) P_i(xi_q),
+ * f = f^c - f^d(w, q) (q = c->qx in viscous runs).
  * At a PE face with delay k > 0 the flux is the AT flux (Eq. 7) of the fluxes at the
  * common delayed levels n-k-m (both sides of the face at the same level). */
 static int rhs_eval(or_ctx *c, const double *win, int s, int use_hist) {
   int ns = c->m.ns, nv = c->nv, q = c->np1, ne = c->ne;
-  double wn[MAXV], f[MAXV], conc[MAXV], wdot[MAXV];
+  const int visc = c->cfg.viscous;
+  double wn[MAXV], f[MAXV], conc[MAXV], wdot[MAXV], qn[MAXV], fd[MAXV];
   double V[MAXV][MAXQ], Sv[MAXV][MAXQ];
   int err = 0;
   /* volume and source terms */
@@ -730,6 +909,15 @@ static int rhs_eval(or_ctx *c, const double *win, int s, int use_hist) {
       or_state(&c->m, wn, &rho, &u, &T, &P, &a);
       if (!(T > 0.0) || !isfinite(T)) err = -1;
       or_phys_flux(&c->m, wn, f);
+      if (visc) {
+        for (int v = 0; v < nv; ++v) {
+          double acc = 0.0;
+          for (int j = 0; j < q; ++j) acc += W_(c->qx, v, e, j) * c->Pq[k * q + j];
+          qn[v] = acc;
+        }
+        or_visc_flux(&c->m, &c->cfg, wn, qn, fd);
+        for (int v = 0; v < nv; ++v) f[v] -= fd[v];
+      }
       /* law of mass action on non-negative concentrations: the polynomial of a
        * trace species may dip below zero at a Gauss point */
       for (int i = 0; i < ns; ++i) conc[i] = fmax(wn[2 + i], 0.0) / c->m.W[i];
@@ -749,6 +937,7 @@ static int rhs_eval(or_ctx *c, const double *win, int s, int use_hist) {
   }
   /* face fluxes */
   double blk[MAXV * MAXQ], wl[MAXV], wr[MAXV], g[MAXV], fa[MAXV], cm[16];
+  double ql[MAXV], qr[MAXV], qg[MAXV];
   int periodic = (c->cfg.bc_left == 0);
   for (int i = 0; i <= ne; ++i) {
     double *fh = c->fhat + (size_t)i * nv;
@@ -769,7 +958,11 @@ static int rhs_eval(or_ctx *c, const double *win, int s, int use_hist) {
         if (c->ring_level[lv % c->depth] != lv) return -3;
         trace_of(c, bl, 1, wl);
         trace_of(c, br, 0, wr);
-        or_num_flux(&c->m, c->cfg.flux, wl, wr, fa);
+        if (visc) {
+          trace_of(c, ring_at(c, c->ring_q, lv, s, pf, 0), 1, ql);
+          trace_of(c, ring_at(c, c->ring_q, lv, s, pf, 1), 0, qr);
+        }
+        face_flux(c, wl, ql, wr, qr, fa);
         for (int v = 0; v < nv; ++v) fh[v] += cm[mm] * fa[v];
       }
       continue;
@@ -778,19 +971,35 @@ static int rhs_eval(or_ctx *c, const double *win, int s, int use_hist) {
       elem_block(c, win, 0, blk);
       trace_of(c, blk, 0, wr);
       ghost_trace(c, c->cfg.bc_left, wr, g);
-      or_num_flux(&c->m, c->cfg.flux, g, wr, fh);
+      if (visc) {
+        elem_block(c, c->qx, 0, blk);
+        trace_of(c, blk, 0, qr);
+        ghost_qtrace(c, c->cfg.bc_left, qr, qg);
+      }
+      face_flux(c, g, qg, wr, qr, fh);
     } else if (i == ne && !periodic) {
       elem_block(c, win, ne - 1, blk);
       trace_of(c, blk, 1, wl);
       ghost_trace(c, c->cfg.bc_right, wl, g);
-      or_num_flux(&c->m, c->cfg.flux, wl, g, fh);
+      if (visc) {
+        elem_block(c, c->qx, ne - 1, blk);
+        trace_of(c, blk, 1, ql);
+        ghost_qtrace(c, c->cfg.bc_right, ql, qg);
+      }
+      face_flux(c, wl, ql, g, qg, fh);
     } else {
       int el = (i == 0) ? ne - 1 : i - 1;
       elem_block(c, win, el, blk);
       trace_of(c, blk, 1, wl);
       elem_block(c, win, i, blk);
       trace_of(c, blk, 0, wr);
-      or_num_flux(&c->m, c->cfg.flux, wl, wr, fh);
+      if (visc) {
+        elem_block(c, c->qx, el, blk);
+        trace_of(c, blk, 1, ql);
+        elem_block(c, c->qx, i, blk);
+        trace_of(c, blk, 0, qr);
+      }
+      face_flux(c, wl, ql, wr, qr, fh);
     }
   }
   /* assembly: rhs <- (2i+1)/dx (V_i - fhat_{e+1} + (-1)^i fhat_e) + source_i */
@@ -1007,6 +1216,15 @@ int or_step(or_ctx *c, int n_steps) {
         elem_block(c, c->win, c->pf_left[f], dl);
         elem_block(c, c->win, c->pf_right[f], dr);
       }
+      if (c->cfg.viscous) {
+        /* the auxiliary variable of the stage input, and its history */
+        int aerr = aux_eval(c, c->win, s, 1);
+        if (aerr) return aerr;
+        for (int f = 0; f < c->npf; ++f) {
+          elem_block(c, c->qx, c->pf_left[f], ring_at(c, c->ring_q, n, s, f, 0));
+          elem_block(c, c->qx, c->pf_right[f], ring_at(c, c->ring_q, n, s, f, 1));
+        }
+      }
       int err = rhs_eval(c, c->win, s, 1);
       if (err) return err;
       for (size_t t = 0; t < sz; ++t) {
@@ -1068,8 +1286,21 @@ int or_rhs_sync(const or_cfg *cfg, const or_mech *m, const double *w, double *rh
   if (!c) return -2;
   size_t sz = (size_t)c->nv * c->ne * c->np1;
   memcpy(c->win, w, sizeof(double) * sz);
-  int err = rhs_eval(c, c->win, 0, 0);
+  int err = c->cfg.viscous ? aux_eval(c, c->win, 0, 0) : 0;
+  if (!err) err = rhs_eval(c, c->win, 0, 0);
   memcpy(rhs, c->rhs, sizeof(double) * sz);
+  or_destroy(c);
+  return err;
+}
+
+/* The LDG auxiliary variable of a state, for tests (no delays). */
+int or_aux_sync(const or_cfg *cfg, const or_mech *m, const double *w, double *qout) {
+  or_ctx *c = or_create(cfg, m);
+  if (!c) return -2;
+  size_t sz = (size_t)c->nv * c->ne * c->np1;
+  memcpy(c->win, w, sizeof(double) * sz);
+  int err = aux_eval(c, c->win, 0, 0);
+  memcpy(qout, c->qx, sizeof(double) * sz);
   or_destroy(c);
   return err;
 }

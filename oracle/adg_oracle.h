@@ -23,6 +23,7 @@ typedef struct {
   const double *W, *cp, *hf, *s0;  /* [ns] kg/mol, J/mol/K, J/mol, J/mol/K */
   const signed char *nu_f, *nu_r;  /* [nr][ns] */
   const double *A, *b, *Ea;        /* [nr] SI, -, J/mol */
+  const double *Le;                /* [ns] Lewis numbers (viscous runs; NULL: all 1) */
 } or_mech;
 
 typedef struct {
@@ -40,6 +41,8 @@ typedef struct {
   int integrator;        /* 0 SSP-RK3 (Shu-Osher), 1 LSERK 3-stage 3rd order
                             (Williamson 1980), 2 LSERK 5-stage 4th order
                             (Carpenter-Kennedy, 2N storage) */
+  int viscous;           /* 0 Euler; 1 with the diffusive flux f^d (Sec. 2, LDG) */
+  double mu_ref, T_mu, mu_exp, prandtl; /* mu = mu_ref (T/T_mu)^mu_exp, k = mu cp/Pr */
 } or_cfg;
 
 typedef struct or_ctx or_ctx;
@@ -69,6 +72,11 @@ void or_phys_flux(const or_mech *m, const double *w, double *f);
 void or_num_flux(const or_mech *m, int kind, const double *wl, const double *wr,
                  double *f);
 void or_eigen(const or_mech *m, const double *wbar, double *R, double *L, double *lam);
+/* transport (mu, k, D_i) and the diffusive flux f^d(w, q) at one point, q = dw/dx */
+void or_transport(const or_mech *m, const or_cfg *cfg, double rho, double T, const double *Y,
+                  double *mu, double *kc, double *D);
+void or_visc_flux(const or_mech *m, const or_cfg *cfg, const double *w, const double *q,
+                  double *fd);
 
 /* DG tables for degree p (shift: neighbour polynomial continued into the cell) */
 void or_beta_matrix(int p, double *B);
@@ -87,6 +95,8 @@ int or_get_flags(const or_ctx *c, uint8_t *last, int32_t *count);
 int or_get_temperature(const or_ctx *c, double *T);
 /* one synchronous right-hand side L(w) (Eq. 5), no delays */
 int or_rhs_sync(const or_cfg *cfg, const or_mech *m, const double *w, double *rhs);
+/* the LDG auxiliary variable q = dw/dx of a state (central trace, no delays) */
+int or_aux_sync(const or_cfg *cfg, const or_mech *m, const double *w, double *q);
 int or_reactor0d(const or_mech *m, double *r, double rhoe, double dt, int n_steps);
 
 #ifdef __cplusplus

@@ -64,6 +64,7 @@ class Mechanism:
     Ea: np.ndarray       # [nr] J/mol
     comp: np.ndarray     # [ns, 4] element counts (bookkeeping only)
     names: list
+    Le: Optional[np.ndarray] = None  # [ns] Lewis numbers (viscous runs; None: all 1)
 
     @property
     def ns(self) -> int:
@@ -192,7 +193,14 @@ def make_mechanism(ns: int, nr: int, seed: int,
         Ea[j] = prng.uniform(0.0, 40.0) * KCAL
     names = ["fuel", "oxid"] + ["s%d" % i for i in range(2, ns - 1)] + ["bath"]
     return Mechanism(W=W, cp=cp, h_f=h_f, s0=s0, nu_f=nu_f, nu_r=nu_r, A=A, b=b,
-                     Ea=Ea, comp=comp, names=names)
+                     Ea=Ea, comp=comp, names=names, Le=lewis_numbers(W))
+
+
+def lewis_numbers(W: np.ndarray) -> np.ndarray:
+    """Synthetic Lewis numbers (the paper's mixture-averaged transport comes from
+    Cantera, not available): Le_i = sqrt(W_i / 0.029), which puts a light fuel
+    near 0.26, water-like species near 0.8 and the bath gas near 1."""
+    return np.sqrt(np.asarray(W, dtype=np.float64) / 0.029)
 
 
 def gauss_points(q: int) -> np.ndarray:
@@ -231,6 +239,13 @@ class Workload:
     x0: float = 0.0
     attempts: Optional[list] = None
     integrator: int = RK_SSP3
+    # diffusive flux of Sec. 2 (LDG), with the synthetic transport model
+    # mu = mu_ref (T / T_mu)^mu_exp, k = mu cp / Pr, D_i = k / (rho cp Le_i)
+    viscous: int = 0
+    mu_ref: float = 1.85e-5
+    T_mu: float = 300.0
+    mu_exp: float = 0.7
+    prandtl: float = 0.7
 
     def mechanism(self) -> Mechanism:
         return make_mechanism(self.ns, self.nr, self.mech_seed, self.attempts)
