@@ -87,6 +87,8 @@ typedef struct {
   const double *s0;                 /* [n_species] J/mol/K at 298.15 K, 1 atm */
   const signed char *nu_f, *nu_r;   /* [n_reactions][n_species] >= 0 */
   const double *A, *b, *Ea;         /* [n_reactions] SI, -, J/mol */
+  const double *Le;                 /* [n_species] Lewis numbers, used by viscous
+                                       instances only; NULL: all 1 */
 } adg_mechanism;
 
 /* One instance (one 1D domain [x0, x0+length] cut into n_pe PEs). */
@@ -104,6 +106,19 @@ typedef struct {
   double tvb_M;            /* TVB constant of the indicator (0 = TVD) */
   int precision;           /* ADG_FP64 | ADG_MIXED */
   int integrator;          /* ADG_RK_SSP3 | ADG_RK_LS3 | ADG_RK_LS4 */
+  /* Viscous terms (Sec. 2: f^d with the shear stress tau = 4/3 mu du/dx, the
+   * heat flux q = -k dT/dx + sum h_i J_i and mixture-averaged diffusion
+   * J_i = rho Y_i V_i, V_i = -(D_i/X_i) dX_i/dx, plus the correction velocity
+   * that makes sum J_i = 0), discretised by the local DG method of Sec. 3.1:
+   * q = dw/dx from a central trace of w, the Riemann flux of f^c minus the
+   * central mean of f^d at faces; at a delayed PE face both the trace of w for
+   * q and the face flux are AT-extrapolated. The transport model is synthetic
+   * (the paper's comes from Cantera): mu = mu_ref (T/T_mu)^mu_exp,
+   * k = mu c_p / prandtl (c_p of the mixture per unit mass) and
+   * D_i = k / (rho c_p Le_i) with the mechanism's Lewis numbers. viscous = 0
+   * ignores the other four fields. */
+  int viscous;             /* 0: Euler; 1: with f^d */
+  double mu_ref, T_mu, mu_exp, prandtl; /* Pa s, K, -, - (T_mu, prandtl > 0) */
 } adg_config;
 
 typedef struct adg_ctx adg_ctx;

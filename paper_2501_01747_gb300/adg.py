@@ -19,8 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libadg.so")
-SOURCES = ["adg_k64.cu", "adg_k32.cu", "adg_u64.cu", "adg_u32.cu", "adg_kernels.cu",
-           "adg_api.cu", "adg_static.cu"]
+SOURCES = ["adg_k64.cu", "adg_k32.cu", "adg_u64.cu", "adg_u32.cu", "adg_v64.cu",
+           "adg_v32.cu", "adg_kernels.cu", "adg_api.cu", "adg_static.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", ARCH]
 
@@ -84,7 +84,7 @@ class Mechanism_(C.Structure):
                 ("h_f", C.POINTER(C.c_double)), ("s0", C.POINTER(C.c_double)),
                 ("nu_f", C.POINTER(C.c_byte)), ("nu_r", C.POINTER(C.c_byte)),
                 ("A", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)),
-                ("Ea", C.POINTER(C.c_double))]
+                ("Ea", C.POINTER(C.c_double)), ("Le", C.POINTER(C.c_double))]
 
 
 class Config_(C.Structure):
@@ -94,7 +94,8 @@ class Config_(C.Structure):
                 ("limiter", C.c_int), ("at_order", C.c_int), ("delay_mode", C.c_int),
                 ("max_delay", C.c_int), ("delay_probs", C.POINTER(C.c_double)),
                 ("seed", C.c_uint64), ("tvb_M", C.c_double), ("precision", C.c_int),
-                ("integrator", C.c_int)]
+                ("integrator", C.c_int), ("viscous", C.c_int), ("mu_ref", C.c_double),
+                ("T_mu", C.c_double), ("mu_exp", C.c_double), ("prandtl", C.c_double)]
 
 
 _lib = None
@@ -171,10 +172,13 @@ class _MechArgs:
         self.nu_f = np.ascontiguousarray(mech.nu_f, dtype=np.int8)
         self.nu_r = np.ascontiguousarray(mech.nu_r, dtype=np.int8)
         W, cp, hf, s0, A, b, Ea = self.keep
+        le = getattr(mech, "Le", None)
+        self.Le = None if le is None else np.ascontiguousarray(le, dtype=np.float64)
         self.s = Mechanism_(W.shape[0], A.shape[0], _dp(W), _dp(cp), _dp(hf), _dp(s0),
                             self.nu_f.ctypes.data_as(C.POINTER(C.c_byte)),
                             self.nu_r.ctypes.data_as(C.POINTER(C.c_byte)),
-                            _dp(A), _dp(b), _dp(Ea))
+                            _dp(A), _dp(b), _dp(Ea),
+                            _dp(self.Le) if self.Le is not None else C.POINTER(C.c_double)())
 
 
 FP64, MIXED = 0, 1
@@ -196,7 +200,9 @@ def config_struct(wl, precision=FP64):
     c = Config_(wl.n_elem, wl.p, wl.n_pe, wl.x0, wl.length, wl.dt, wl.bc_left, wl.bc_right,
                 wl.flux, wl.limiter, wl.at_order, wl.delay_mode, wl.max_delay, _dp(probs),
                 wl.seed & ((1 << 64) - 1), wl.tvb_M, _precision(precision),
-                int(getattr(wl, "integrator", 0)))
+                int(getattr(wl, "integrator", 0)), int(getattr(wl, "viscous", 0)),
+                float(getattr(wl, "mu_ref", 0.0)), float(getattr(wl, "T_mu", 300.0)),
+                float(getattr(wl, "mu_exp", 0.7)), float(getattr(wl, "prandtl", 0.7)))
     return c, probs
 
 

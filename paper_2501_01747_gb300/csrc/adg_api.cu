@@ -115,6 +115,7 @@ int adg::pack_mechanism(const adg_mechanism *m, double *sp, Rxn *rx, int *sx_off
     sp[SP_G0 * ns + i] = (hf - cp * TREF) / RU;
     sp[SP_G1 * ns + i] = cp / RU * (1.0 + log(TREF)) - s0 / RU;
     sp[SP_CPR * ns + i] = cp / RU;
+    sp[SP_INVLE * ns + i] = m->Le ? 1.0 / m->Le[i] : 1.0;
   }
   for (int j = 0; j < nr; ++j) {
     Rxn &R = rx[j];
@@ -197,6 +198,7 @@ struct Group {
   int Q = 0;
   bool mixed = false;
   int S = 3;                    // RK stages per step
+  bool visc = false;            // has viscous instances (LDG auxiliary kernel per stage)
   int TE = 0;                   // elements per stage tile
   int NT = 128;                 // threads per stage CTA
   int EPB = 32;                 // elements per limiter CTA
@@ -265,7 +267,7 @@ int check_args(const adg_mechanism *m, const adg_config *cfgs, int n) {
   if (!m->W || !m->cp || !m->h_f || !m->s0) return ADG_ERR_ARG;
   if (m->n_reactions > 0 && (!m->nu_f || !m->nu_r || !m->A || !m->b || !m->Ea)) return ADG_ERR_ARG;
   for (int i = 0; i < m->n_species; ++i)
-    if (!(m->W[i] > 0.0) || !(m->cp[i] > RU)) return ADG_ERR_ARG;
+    if (!(m->W[i] > 0.0) || !(m->cp[i] > RU) || (m->Le && !(m->Le[i] > 0.0))) return ADG_ERR_ARG;
   for (int j = 0; j < m->n_reactions; ++j) {
     int nf = 0, nr = 0, nx = 0;
     for (int i = 0; i < m->n_species; ++i) {
@@ -294,6 +296,10 @@ int check_args(const adg_mechanism *m, const adg_config *cfgs, int n) {
     if (c.bc_left < 0 || c.bc_left > 2 || c.bc_right < 0 || c.bc_right > 2) return ADG_ERR_ARG;
     if (c.precision != ADG_FP64 && c.precision != ADG_MIXED) return ADG_ERR_ARG;
     if (c.integrator < ADG_RK_SSP3 || c.integrator > ADG_RK_LS4) return ADG_ERR_ARG;
+    if (c.viscous != 0 && c.viscous != 1) return ADG_ERR_ARG;
+    if (c.viscous && (!(c.mu_ref >= 0.0) || !(c.T_mu > 0.0) || !(c.prandtl > 0.0) ||
+                      !isfinite(c.mu_exp)))
+      return ADG_ERR_ARG;
     if ((int64_t)c.n_elem * (c.p + 1) * (m->n_species + 3) > (int64_t)1 << 31) return ADG_ERR_ARG;
   }
   return ADG_OK;
@@ -381,7 +387,9 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
     G.mixed = prec == ADG_MIXED;
     G.S = S;
     G.O = O;
-    G.TE = stage_tile(M, Q, O, G.mixed);
+    for (int k = 0; k < ctx->n_inst; ++k)
+      if (member(k) && cfgs[k].viscous) G.visc = true;
+    G.TE = stage_tile(M, Q, O, G.mixed, G.visc);
     // smaller tiles when the group would not fill two CTAs per SM
     int64_t target = (total + 2 * 152 - 1) / (2 * 152);
     if (target < G.TE) G.TE = target < 4 ? 4 : (int)target;
@@ -419,6 +427,8 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
     size_t rs = (size_t)(2 * c.max_delay + c.at_order) * S * (npf > 0 ? npf : 1) * 2 * nv;
     I.ring_in = (double *)cv.take(sizeof(double) * rs);
     I.ring_pre = (double *)cv.take(sizeof(double) * rs * Q);
+    I.qx = c.viscous ? (double *)cv.take(sizeof(double) * st) : nullptr;
+    I.ring_q = c.viscous ? (double *)cv.take(sizeof(double) * rs) : nullptr;
     I.flags = (uint8_t *)cv.take((size_t)S * N);
     I.count = (int32_t *)cv.take(sizeof(int32_t) * N);
     I.pf_of_left = (const int *)cv.take(sizeof(int) * N);
@@ -607,6 +617,12 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
     I.n_stages = rk_stages(c.integrator);
     for (int s = 0; s < ADG_MAX_STAGES; ++s) I.rk_a[s] = I.rk_b[s] = 0.0;
     I.lserk = lserk_coefficients(c.integrator, I.rk_a, I.rk_b) > 0;
+    I.viscous = c.viscous;
+    I.pad0 = 0;
+    I.mu_ref = c.viscous ? c.mu_ref : 0.0;
+    I.ln_T_mu = c.viscous ? log(c.T_mu) : 0.0;
+    I.mu_exp = c.viscous ? c.mu_exp : 0.0;
+    I.inv_prandtl = c.viscous ? 1.0 / c.prandtl : 0.0;
     I.at_order = c.at_order;
     I.bc_left = c.bc_left;
     I.bc_right = c.bc_right;
@@ -646,7 +662,8 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
         cudaMemcpy((void *)I.pf_of_right, pr.data(), sizeof(int) * N, cudaMemcpyHostToDevice) ||
         cudaMemcpy((void *)I.pf_elem, pe.data(), sizeof(int) * pe.size(), cudaMemcpyHostToDevice) ||
         cudaMemset(I.flags, 0, (size_t)I.n_stages * N) || cudaMemset(I.count, 0, sizeof(int32_t) * N) ||
-        cudaMemset(I.wn, 0, sizeof(double) * (size_t)nv * N * Q))
+        cudaMemset(I.wn, 0, sizeof(double) * (size_t)nv * N * Q) ||
+        (I.qx && cudaMemset(I.qx, 0, sizeof(double) * (size_t)nv * N * Q)))
       rc2 = ADG_ERR_CUDA;
     h.n = 0;
     h.n_pe = c.n_pe;
@@ -788,6 +805,16 @@ static cudaError_t timed_end(adg_ctx *ctx, cudaStream_t st) {
   return r;
 }
 
+// Arguments of the auxiliary kernel of a group: its limiter block table.
+static LimArgs aux_args(const adg_ctx *ctx, const Group &G, int s) {
+  LimArgs L;
+  L.insts = ctx->d_insts;
+  L.blocks = G.d_blocks;
+  L.s = s;
+  L.EPB = G.EPB;
+  return L;
+}
+
 // One step of every instance: per RK stage, the stage kernel and the limiter
 // of every group that has that stage, then the step counters advance.
 static int enqueue_step(adg_ctx *ctx, cudaStream_t st) {
@@ -805,7 +832,11 @@ static int enqueue_step(adg_ctx *ctx, cudaStream_t st) {
       A.TE = G.TE;
       A.NT = G.NT;
       A.O = G.O;
+      A.visc = G.visc;
       CK(timed_begin(ctx, 0, st));
+      // viscous groups: the LDG auxiliary variable of the stage input first
+      // (timed with the stage kernel)
+      if (G.visc) CK(launch_aux(aux_args(ctx, G, s), G.Q, G.n_blocks, st));
       CK(launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st));
       CK(timed_end(ctx, st));
     }
@@ -930,7 +961,7 @@ int adg_autotune(adg_ctx *ctx, void *stream) {
     float best = 1e30f;
     for (int te : kTE) {
       if (te < kMinTile) continue;
-      if (stage_smem(ctx->mech, te, G.Q, G.O, G.mixed) > 200 * 1024) continue;
+      if (stage_smem(ctx->mech, te, G.Q, G.O, G.mixed, G.visc) > 200 * 1024) continue;
       G.TE = te;
       if (upload_tiles(ctx, G) != cudaSuccess) {
         rc = ADG_ERR_CUDA;
@@ -944,11 +975,13 @@ int adg_autotune(adg_ctx *ctx, void *stream) {
         A.TE = te;
         A.NT = nt;
         A.O = G.O;
+        A.visc = G.visc;
         // stage 0 alone rewrites only buffers that the next step rewrites again
-        // (stage buffers, the ring slot of the current level), so the
+        // (stage buffers, q, the ring slots of the current level), so the
         // trajectory is unchanged
         bool ok = true;
-        ok = launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
+        if (G.visc) ok = launch_aux(aux_args(ctx, G, 0), G.Q, G.n_blocks, st) == cudaSuccess;
+        ok = ok && launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
         ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
         for (int w = 0; w < 2 && ok; ++w)
           ok = launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
@@ -982,7 +1015,7 @@ int adg_set_tuning(adg_ctx *ctx, int group, int elements_per_tile, int threads_p
   Group &G = ctx->groups[group];
   const int te = elements_per_tile, nt = threads_per_cta;
   if (te < kMinTile || nt < 32 || nt > 512 || nt % 32) return ADG_ERR_ARG;
-  if (stage_smem(ctx->mech, te, G.Q, G.O, G.mixed) > 200 * 1024) return ADG_ERR_ARG;
+  if (stage_smem(ctx->mech, te, G.Q, G.O, G.mixed, G.visc) > 200 * 1024) return ADG_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->last_stream));
   G.TE = te;
   G.NT = nt;
@@ -1011,6 +1044,7 @@ int adg_step_unsync(adg_ctx *ctx, int instance, int n_steps, void *stream) {
   if (n_steps == 0) return ADG_OK;
   InstHost &h = ctx->inst[instance];
   const Inst &I = h.d;
+  if (I.viscous) return ADG_ERR_ARG;  // the unsynchronised mode runs the Euler terms only
   const int Q = I.p + 1;
   const bool mixed = I.mixed != 0;
   const Group *G = nullptr;
@@ -1074,7 +1108,8 @@ int adg_launches_per_step(const adg_ctx *ctx) {
   if (!ctx) return 0;
   int n = 1;
   for (int gi = 0; gi < ctx->n_groups; ++gi)
-    n += ctx->groups[gi].S * (ctx->groups[gi].any_limiter ? 2 : 1);
+    n += ctx->groups[gi].S *
+         ((ctx->groups[gi].any_limiter ? 2 : 1) + (ctx->groups[gi].visc ? 1 : 0));
   return n;
 }
 

@@ -60,8 +60,16 @@ using dg_t = typename std::conditional<MIX, float, double>::type;
 // rates of progress, production rates; the mixed variant adds an FP32 copy of
 // the species fields and the point flux (the FP64 variant writes the flux over
 // the nodal state). Integers: delay per face, species-reaction incidence.
+// Viscous groups append, in FP64: the tile of q = dw/dx with halo, q at the
+// Gauss points (then f^d there), and per (level, face) the traces of w and q of
+// both sides (then f^d of both sides).
+__host__ __device__ inline size_t stage_visc_doubles(int TE, int Q, int ns, int O) {
+  const size_t nv = ns + 2;
+  return nv * (TE + 2) * Q + nv * (size_t)TE * Q + (size_t)O * (TE + 1) * 4 * nv;
+}
+
 __host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int ns, int nr, int nterm,
-                                                   int O, bool mix) {
+                                                   int O, bool mix, bool visc = false) {
   const size_t nv = ns + 2, TQ = (size_t)TE * Q, F = TE + 1;
   const size_t nd = (size_t)SP_NFIELDS * ns + sizeof(IExpTable) / 8 + MAXQ * MAXQ +
                     nv * (TE + 2) * Q + 2 * nv * TQ + 4 * TQ;
@@ -69,7 +77,64 @@ __host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int ns, int nr
                (size_t)nr * TQ + (size_t)ns * TQ + nterm;
   if (mix) ndg += (size_t)SP_NFIELDS * ns + nv * TQ;
   const size_t ni = F + ns + 1 + nterm;
-  return (size_t)nr * sizeof(Rxn) + nd * 8 + ndg * (mix ? 4 : 8) + ni * 4 + 16;
+  return (size_t)nr * sizeof(Rxn) + nd * 8 + ndg * (mix ? 4 : 8) + ni * 4 + 16 +
+         (visc ? stage_visc_doubles(TE, Q, ns, O) * 8 + 8 : 0);
+}
+
+// Diffusive flux of Sec. 2 at one point from the state w and its derivative
+// q = dw/dx (LDG), arrays strided (variable v at w[v * ws]); fd (stride fs) gets
+// (tau, tau u - q_h, -J_1 .. -J_Ns); fd may be q itself. T in closed form
+// (constant c_p), the primitive derivatives by the chain rule (rho_x = sum
+// q_{rho Y_i}, u_x = (q_{rho u} - u rho_x) / rho, Y_i,x = (q_{rho Y_i} - Y_i rho_x)
+// / rho, T_x from the derivative of rho E - (rho u) u / 2 = sum rho Y_i e_i(T)).
+// With X_i = Y_i / (W_i n), n = sum Y_j / W_j, the flux -rho D_i (Y_i / X_i) dX_i/dx
+// is -(mu / (Pr Le_i)) (Y_i,x - Y_i n_x / n), and the correction velocity makes
+// J_i = J_i* - Y_i sum_j J_j*. Transport: mu = mu_ref (T / T_mu)^mu_exp,
+// k = mu c_p / Pr, rho D_i = k / (c_p Le_i).
+__device__ inline void visc_flux_dev(const double *sp, int ns, const Inst &I, const double *w,
+                                     int ws, const double *q, int qs, double *fd, int fs) {
+  const double *sIW = sp + SP_INVW * ns, *sQW = sp + SP_QW * ns, *sCVW = sp + SP_CVW * ns;
+  const double *sCPW = sp + SP_CPW * ns, *sIL = sp + SP_INVLE * ns;
+  double rho = 0.0, rho_x = 0.0, qsum = 0.0, cv = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    const double r = w[(2 + i) * ws];
+    rho += r;
+    rho_x += q[(2 + i) * qs];
+    qsum = fma(r, sQW[i], qsum);
+    cv = fma(r, sCVW[i], cv);
+  }
+  const double irho = 1.0 / rho, m = w[0], u = m * irho;
+  const double u_x = (q[0] - u * rho_x) * irho;
+  const double T = (w[ws] - 0.5 * m * u - qsum) / cv;
+  double num = q[qs] - 0.5 * (q[0] * u + m * u_x), n = 0.0, n_x = 0.0, cpm = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    const double rx = q[(2 + i) * qs], Y = w[(2 + i) * ws] * irho;
+    const double Yx = (rx - Y * rho_x) * irho;
+    num -= rx * fma(sCVW[i], T, sQW[i]);
+    n = fma(Y, sIW[i], n);
+    n_x = fma(Yx, sIW[i], n_x);
+    cpm = fma(Y, sCPW[i], cpm);
+  }
+  const double T_x = num / cv;
+  const double mu = I.mu_ref * exp(I.mu_exp * (log(T) - I.ln_T_mu));
+  const double a = mu * I.inv_prandtl, kc = a * cpm, nxn = n_x / n;
+  double Jsum = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    const double Y = w[(2 + i) * ws] * irho;
+    const double Yx = (q[(2 + i) * qs] - Y * rho_x) * irho;
+    const double Js = -a * sIL[i] * (Yx - Y * nxn);
+    fd[(2 + i) * fs] = Js;
+    Jsum += Js;
+  }
+  double qh = -kc * T_x;
+  for (int i = 0; i < ns; ++i) {
+    const double J = fd[(2 + i) * fs] - w[(2 + i) * ws] * irho * Jsum;
+    qh = fma(fma(sCPW[i], T, sQW[i]), J, qh);
+    fd[(2 + i) * fs] = -J;
+  }
+  const double tau = (4.0 / 3.0) * mu * u_x;
+  fd[0] = tau;
+  fd[fs] = tau * u - qh;
 }
 
 // Copy an instance description into shared memory (by 8-byte words).
@@ -95,12 +160,22 @@ __device__ __forceinline__ double ring_load(const double *p) {
   else return *p;
 }
 
+// Viscous part of a face flux: from the traces vt = (w_l, w_r, q_l, q_r) [4][nv],
+// f^d of each side (over its q) and fl -= (f^d_l + f^d_r) / 2.
+template <typename DG>
+__device__ inline void visc_face(const double *sp, int ns, const Inst &I, int nv, double *vt,
+                                 DG *fl) {
+  visc_flux_dev(sp, ns, I, vt, 1, vt + 2 * nv, 1, vt + 2 * nv, 1);
+  visc_flux_dev(sp, ns, I, vt + nv, 1, vt + 3 * nv, 1, vt + 3 * nv, 1);
+  for (int v = 0; v < nv; ++v) fl[v] -= (DG)(0.5 * (vt[2 * nv + v] + vt[3 * nv + v]));
+}
+
 // Stage s of one tile: elements [e0, e0 + te) of instance I at step level nstep.
 // With UNSYNC the PE faces of the tile take the delays pd->k observed by a PE
 // that runs without synchronisation and read both sides from the history ring,
 // also at delay 0; the stage input's traces there are published beforehand by
 // the caller, not written in phase 6.
-template <int Q, bool MIX, bool UNSYNC>
+template <int Q, bool MIX, bool UNSYNC, bool VISC = false>
 __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, const Inst &I,
                                            const int e0, const int te, const int64_t nstep,
                                            const PeDelays *pd) {
@@ -149,6 +224,14 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   }
   int *soff = sk + NF;        // [ns + 1]
   int *sterm = soff + ns + 1;  // [nterm] reaction of each incidence term
+  // viscous region (groups with viscous instances), FP64, 8-byte aligned
+  double *sqw = reinterpret_cast<double *>(
+      (reinterpret_cast<uintptr_t>(sterm + M.nterm) + 7) & ~(uintptr_t)7);  // [v][TE+2][Q]
+  double *sqn = sqw + (size_t)nv * (TE + 2) * Q;                           // [v][TQ]
+  double *sqt = sqn + (size_t)nv * TQ;                                     // [O][NF][4][nv]
+  // viscous terms: compiled only into the viscous instances of the kernel (the
+  // Euler kernels keep their register budget), run for viscous instances
+  const bool visc = VISC && I.viscous;
   const int tid = threadIdx.x, nth = blockDim.x;
 
   // 0. mechanism, species fields, incidence, exp table and basis values into
@@ -208,6 +291,17 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         if (dst[b]) *dst[b] = xs[b];
     }
   }
+  // the tile of q = dw/dx with the same halo (viscous instances)
+  if (visc) {
+    const int span = (te + 2) * Q;
+    for (int idx = tid; idx < nv * span; idx += nth) {
+      const int v = idx / span, r = idx - v * span, le = r / Q, j = r - le * Q;
+      int e = e0 - 1 + le;
+      if (e < 0) e = periodic ? e + N : 0;
+      if (e >= N) e = periodic ? e - N : N - 1;
+      sqw[((size_t)v * (TE + 2) + le) * Q + j] = I.qx[((size_t)v * N + e) * Q + j];
+    }
+  }
   __syncthreads();
 
   // 2a. conserved state at the Gauss points, one (variable, point) per item
@@ -220,6 +314,13 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
 #pragma unroll
     for (int j = 0; j < Q; ++j) acc += wi[j] * Pq[j];
     snw[(size_t)v * TQ + t] = acc;
+    if (visc) {
+      const double *qi = sqw + ((size_t)v * (TE + 2) + e + 1) * Q;
+      double aq = 0.0;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) aq += qi[j] * Pq[j];
+      sqn[(size_t)v * TQ + t] = aq;
+    }
   }
   __syncthreads();
   // 2b. temperature from the internal energy (the closed form of the Newton step
@@ -245,6 +346,8 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       sinvT[t] = cv / num;
       su[t] = u;
       sPr[t] = T * Rm;
+      // the diffusive flux at the point, over its q
+      if (visc) visc_flux_dev(ssp, ns, I, wq, TQ, sqn + t, TQ, sqn + t, TQ);
     }
   }
   __syncthreads();
@@ -269,6 +372,11 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       } else {
         if constexpr (MIX) sfx[at] = (DG)u * ((DG)w + (DG)sPr[t]);
         else snw[at] = u * (w + sPr[t]);
+      }
+      // f = f^c - f^d
+      if (visc) {
+        if constexpr (MIX) sfx[at] -= (DG)sqn[at];
+        else snw[at] -= sqn[at];
       }
     }
   }
@@ -338,9 +446,23 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       } else {
         num_flux_t<double>(ssp, ns, I.flux, bl, br, fl);
       }
+      if (visc) {
+        // minus the central mean of f^d from the traces of w and q at this level
+        double *vt = sqt + ((size_t)m * NF + f) * 4 * nv;  // w_l, w_r, q_l, q_r
+        const double *ql = I.ring_q + ring_trace(I, lv, A.s, pf, 0);
+        const double *qr = I.ring_q + ring_trace(I, lv, A.s, pf, 1);
+        for (int v = 0; v < nv; ++v) {
+          vt[v] = ring_load<UNSYNC>(bl + v);
+          vt[nv + v] = ring_load<UNSYNC>(br + v);
+          vt[2 * nv + v] = ring_load<UNSYNC>(ql + v);
+          vt[3 * nv + v] = ring_load<UNSYNC>(qr + v);
+        }
+        visc_face(ssp, ns, I, nv, vt, fl);
+      }
       continue;
     }
     if (m > 0) continue;
+    double *vt = sqt + (size_t)f * 4 * nv;
     for (int v = 0; v < nv; ++v) {
       double a = 0.0, b = 0.0;
       for (int j = 0; j < Q; ++j) {
@@ -349,15 +471,41 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       }
       wl[v] = (DG)a;
       wr[v] = (DG)b;
+      if (visc) {
+        double qa = 0.0, qb = 0.0;
+        for (int j = 0; j < Q; ++j) {
+          qa += sqw[((size_t)v * (TE + 2) + f) * Q + j];
+          qb += ((j & 1) ? -1.0 : 1.0) * sqw[((size_t)v * (TE + 2) + f + 1) * Q + j];
+        }
+        vt[v] = a;
+        vt[nv + v] = b;
+        vt[2 * nv + v] = qa;
+        vt[3 * nv + v] = qb;
+      }
     }
+    // physical boundary: the ghost is the mirror image at a reflecting wall (rho u
+    // negated; of q, d(rho u)/dx kept and the others negated) or a copy (outflow)
     if (!periodic && g == 0) {
+      const bool refl = I.bc_left == ADG_BC_REFLECT;
       for (int v = 0; v < nv; ++v) wl[v] = wr[v];
-      if (I.bc_left == ADG_BC_REFLECT) wl[0] = -wr[0];
+      if (refl) wl[0] = -wr[0];
+      if (visc)
+        for (int v = 0; v < nv; ++v) {
+          vt[v] = (refl && v == 0) ? -vt[nv] : vt[nv + v];
+          vt[2 * nv + v] = (refl && v > 0) ? -vt[3 * nv + v] : vt[3 * nv + v];
+        }
     } else if (!periodic && g == N) {
+      const bool refl = I.bc_right == ADG_BC_REFLECT;
       for (int v = 0; v < nv; ++v) wr[v] = wl[v];
-      if (I.bc_right == ADG_BC_REFLECT) wr[0] = -wl[0];
+      if (refl) wr[0] = -wl[0];
+      if (visc)
+        for (int v = 0; v < nv; ++v) {
+          vt[nv + v] = (refl && v == 0) ? -vt[0] : vt[v];
+          vt[3 * nv + v] = (refl && v > 0) ? -vt[2 * nv + v] : vt[2 * nv + v];
+        }
     }
     num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
+    if (visc) visc_face(ssp, ns, I, nv, vt, fl);
   }
   __syncthreads();
 
@@ -463,13 +611,14 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   }
 }
 
-template <int Q, bool MIX>
+template <int Q, bool MIX, bool VISC>
 __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
   __shared__ Inst sI;
   const int2 tile = A.tiles[blockIdx.x];
   load_inst(sI, A.insts + tile.x);
   __syncthreads();
-  stage_body<Q, MIX, false>(M, A, sI, tile.y, min(A.TE, sI.n_elem - tile.y), *sI.step, nullptr);
+  stage_body<Q, MIX, false, VISC>(M, A, sI, tile.y, min(A.TE, sI.n_elem - tile.y), *sI.step,
+                                  nullptr);
 }
 
 template <typename R>
@@ -1021,25 +1170,40 @@ static size_t limiter_smem_bytes(int nv, int ns) {
 
 // Launchers and set-up of one precision variant (instantiated by the unit of
 // that variant only).
-template <int Q, bool MIX>
+template <int Q, bool MIX, bool VISC>
 static cudaError_t launch_stage_q(const Mech &M, const StageArgs &A, int n_tiles,
                                   cudaStream_t st) {
-  size_t smem = stage_smem_bytes(A.TE, Q, M.ns, M.nr, M.nterm, A.O, MIX);
+  if ((A.visc != 0) != VISC) return cudaErrorInvalidValue;
+  size_t smem = stage_smem_bytes(A.TE, Q, M.ns, M.nr, M.nterm, A.O, MIX, VISC);
   if (A.NT < 32 || A.NT > 512 || A.NT % 32) return cudaErrorInvalidValue;
-  stage_kernel<Q, MIX><<<n_tiles, A.NT, smem, st>>>(M, A);
+  stage_kernel<Q, MIX, VISC><<<n_tiles, A.NT, smem, st>>>(M, A);
   return cudaGetLastError();
 }
 
-template <bool MIX>
+template <bool MIX, bool VISC>
 static cudaError_t launch_stage_variant(const Mech &M, const StageArgs &A, int Q, int n_tiles,
                                         cudaStream_t st) {
   switch (Q) {
-    case 2: return launch_stage_q<2, MIX>(M, A, n_tiles, st);
-    case 3: return launch_stage_q<3, MIX>(M, A, n_tiles, st);
-    case 4: return launch_stage_q<4, MIX>(M, A, n_tiles, st);
-    case 5: return launch_stage_q<5, MIX>(M, A, n_tiles, st);
+    case 2: return launch_stage_q<2, MIX, VISC>(M, A, n_tiles, st);
+    case 3: return launch_stage_q<3, MIX, VISC>(M, A, n_tiles, st);
+    case 4: return launch_stage_q<4, MIX, VISC>(M, A, n_tiles, st);
+    case 5: return launch_stage_q<5, MIX, VISC>(M, A, n_tiles, st);
   }
   return cudaErrorInvalidValue;
+}
+
+// Raise the dynamic shared-memory limit of the stage kernels of one variant.
+template <bool MIX, bool VISC>
+static cudaError_t prepare_stage_variant() {
+  const int lim = 200 * 1024;
+  cudaError_t e = cudaSuccess;
+  const void *k[4] = {(const void *)stage_kernel<2, MIX, VISC>,
+                      (const void *)stage_kernel<3, MIX, VISC>,
+                      (const void *)stage_kernel<4, MIX, VISC>,
+                      (const void *)stage_kernel<5, MIX, VISC>};
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+    e = cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return e;
 }
 
 template <int Q, int G, bool MIX, int EPB>
@@ -1074,19 +1238,15 @@ static cudaError_t launch_limiter_variant(const Mech &M, const LimArgs &A, int Q
   return cudaErrorInvalidValue;
 }
 
-// Raise the dynamic shared-memory limit of every kernel instance of the variant
-// (before any launch or stream capture).
+// Raise the dynamic shared-memory limit of the Euler stage kernels and of every
+// limiter kernel of the variant (before any launch or stream capture).
 template <bool MIX>
 static cudaError_t prepare_variant() {
   const int lim = 200 * 1024;
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = prepare_stage_variant<MIX, false>();
 #define ADG_SET(...) \
   if (e == cudaSuccess) \
   e = cudaFuncSetAttribute(__VA_ARGS__, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
-  ADG_SET(stage_kernel<2, MIX>);
-  ADG_SET(stage_kernel<3, MIX>);
-  ADG_SET(stage_kernel<4, MIX>);
-  ADG_SET(stage_kernel<5, MIX>);
   ADG_SET(limiter_kernel<2, 16, MIX, 16>);
   ADG_SET(limiter_kernel<3, 16, MIX, 16>);
   ADG_SET(limiter_kernel<4, 16, MIX, 16>);

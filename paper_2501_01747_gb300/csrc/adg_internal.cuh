@@ -31,6 +31,7 @@ enum SpeciesField {
   SP_G0,        // (h_f - c_p T_ref)/R   : g_i/(R T) = G0/T + G1 - cpR ln T
   SP_G1,        // c_p/R (1 + ln T_ref) - s0/R
   SP_CPR,       // c_p/R
+  SP_INVLE,     // 1/Le (viscous runs)
   SP_NFIELDS
 };
 
@@ -69,6 +70,8 @@ int pack_mechanism(const adg_mechanism *m, double *sp, Rxn *rx, int *sx_off, int
 struct Inst {
   int n_elem, p, nv, npf, depth, at_order;
   int n_stages, lserk;                  // RK stages per step; 2N-storage LSERK scheme
+  int viscous, pad0;                    // with the diffusive flux (LDG)
+  double mu_ref, ln_T_mu, mu_exp, inv_prandtl;  // synthetic transport model
   double rk_a[ADG_MAX_STAGES], rk_b[ADG_MAX_STAGES];  // its A_s, B_s
   int bc_left, bc_right, flux, limiter, delay_mode, max_delay;
   double dx, dt, tvb;
@@ -77,6 +80,8 @@ struct Inst {
   double at[MAXD + 1][MAXO];            // AT weights c_m(k)
   double *wn, *wa, *wb, *wpre;          // [nv][N][Q]: w^n, stage inputs, pre-limit
   double *wq;                           // [nv][N][Q]: the LSERK register dq (or null)
+  double *qx;                           // [nv][N][Q]: LDG auxiliary q = dw/dx (or null)
+  double *ring_q;    // history of the PE-face traces of q [depth][S][npf][2][nv] (or null)
   double *ring_in;   // history of the stage inputs' face traces [depth][S][npf][2][nv]
   double *ring_pre;  // history of the pre-limit outputs [depth][S][npf][2][nv][p+1]
   uint8_t *flags;                       // [S][N]
@@ -270,6 +275,7 @@ struct StageArgs {
   int TE;     // elements per tile
   int NT;     // threads per CTA
   int O;      // AT levels provided for (largest AT order of the group)
+  int visc;   // the group has viscous instances (shared memory holds the viscous region)
 };
 
 // Arguments of one limiter launch: CTA b limits the elements of instance
@@ -283,15 +289,16 @@ struct LimArgs {
 
 void make_tables(Basis *tables);
 cudaError_t upload_basis(const Basis *tables);
-int stage_tile(const Mech &M, int Q, int O, bool mixed);
+int stage_tile(const Mech &M, int Q, int O, bool mixed, bool visc);
 int stage_threads(int TE, int Q, int nr);
-size_t stage_smem(const Mech &M, int TE, int Q, int O, bool mixed);
+size_t stage_smem(const Mech &M, int TE, int Q, int O, bool mixed, bool visc);
 cudaError_t prepare_kernels(int nv, int ns, int nr);
 cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, bool mixed, int n_tiles,
                          cudaStream_t st);
 cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, bool mixed, int nv,
                            int n_blocks, cudaStream_t st);
 cudaError_t launch_advance(int64_t *steps, int n, cudaStream_t st);
+cudaError_t launch_aux(const LimArgs &A, int Q, int n_blocks, cudaStream_t st);
 // per-variant units (adg_k64.cu, adg_k32.cu)
 cudaError_t launch_stage_fp64(const Mech &M, const StageArgs &A, int Q, int n_tiles,
                               cudaStream_t st);
@@ -303,6 +310,15 @@ cudaError_t launch_limiter_mixed(const Mech &M, const LimArgs &A, int Q, int nv,
                                  cudaStream_t st);
 cudaError_t prepare_fp64();
 cudaError_t prepare_mixed();
+// viscous stage kernels (adg_v64.cu, adg_v32.cu)
+cudaError_t launch_stage_visc_fp64(const Mech &M, const StageArgs &A, int Q, int n_tiles,
+                                   cudaStream_t st);
+cudaError_t launch_stage_visc_mixed(const Mech &M, const StageArgs &A, int Q, int n_tiles,
+                                    cudaStream_t st);
+cudaError_t prepare_visc_fp64();
+cudaError_t prepare_visc_mixed();
+cudaError_t upload_tables_visc_fp64(const Basis *tables);
+cudaError_t upload_tables_visc_mixed(const Basis *tables);
 cudaError_t upload_tables_fp64(const Basis *tables);
 cudaError_t upload_tables_mixed(const Basis *tables);
 int limiter_elems_per_block(int64_t n_elem_group, bool mixed);

@@ -6,7 +6,7 @@ namespace adg {
 
 cudaError_t launch_stage_fp64(const Mech &M, const StageArgs &A, int Q, int n_tiles,
                               cudaStream_t st) {
-  return launch_stage_variant<false>(M, A, Q, n_tiles, st);
+  return launch_stage_variant<false, false>(M, A, Q, n_tiles, st);
 }
 
 cudaError_t launch_limiter_fp64(const Mech &M, const LimArgs &A, int Q, int nv, int n_blocks,

@@ -53,19 +53,128 @@ __global__ void temperature_kernel(Mech M, Inst I, const double *w, double *T) {
   T[t] = thermo_of(M.sp, M.ns, wq, 1).T;
 }
 
+// Central value of variable v of the stage input at face g (between elements
+// g-1 and g) for the LDG auxiliary variable: the mean of the two traces; at a PE
+// face with delay k > 0 the AT extrapolation (Eq. 7) of the means at the common
+// delayed levels n-k-m from the trace ring; at a physical boundary the mean with
+// the ghost (reflecting wall: rho u -> 0, the others the interior trace;
+// outflow: the interior trace).
+template <int Q>
+__device__ double face_mean(const Inst &I, const double *win, int64_t nstep, int s, int g, int v,
+                            bool periodic) {
+  const int N = I.n_elem;
+  const int pf = (g < N) ? I.pf_of_left[g] : I.pf_of_right[N - 1];
+  const int k = pf >= 0 ? effective_delay(I, nstep, pf) : 0;
+  if (k > 0) {
+    double acc = 0.0;
+    for (int m = 0; m < I.at_order; ++m) {
+      const int64_t lv = nstep - k - m;
+      const double l = I.ring_in[ring_trace(I, lv, s, pf, 0) + v];
+      const double r = I.ring_in[ring_trace(I, lv, s, pf, 1) + v];
+      acc = fma(I.at[k][m], 0.5 * (l + r), acc);
+    }
+    return acc;
+  }
+  if (!periodic && (g == 0 || g == N)) {
+    const bool left = g == 0;
+    const double *w = win + ((size_t)v * N + (left ? 0 : N - 1)) * Q;
+    double tr = 0.0;
+    for (int j = 0; j < Q; ++j) tr += (left && (j & 1)) ? -w[j] : w[j];
+    const bool refl = (left ? I.bc_left : I.bc_right) == ADG_BC_REFLECT;
+    return (refl && v == 0) ? 0.0 : tr;
+  }
+  const int el = (g == 0) ? N - 1 : g - 1, er = (g == N) ? 0 : g;
+  const double *wl = win + ((size_t)v * N + el) * Q, *wr = win + ((size_t)v * N + er) * Q;
+  double a = 0.0, b = 0.0;
+  for (int j = 0; j < Q; ++j) {
+    a += wl[j];
+    b += ((j & 1) ? -1.0 : 1.0) * wr[j];
+  }
+  return 0.5 * (a + b);
+}
+
+// The LDG auxiliary variable q = dw/dx of stage s (Sec. 3.1: like w, with a
+// central flux) for the viscous instances of a group, one (element, variable)
+// per item over the group's block table:
+//   q_i = (2i+1)/dx (w_hat_{e+1} - (-1)^i w_hat_e - 2 sum_{j < i, i-j odd} w_j),
+// the last sum being the integral of w P_i' (int P_j P_i' = 2 for j < i with i-j
+// odd, 0 otherwise). Writes q and, for a PE-boundary element, the trace of q at
+// its PE face to the q ring (level n, stage s).
+template <int Q>
+__global__ void __launch_bounds__(128) aux_kernel(LimArgs A) {
+  __shared__ Inst sI;
+  const int2 blk = A.blocks[blockIdx.x];
+  load_inst(sI, A.insts + blk.x);
+  __syncthreads();
+  const Inst &I = sI;
+  if (!I.viscous) return;
+  const int N = I.n_elem, nv = I.nv, e0 = blk.y, te = min(A.EPB, N - e0);
+  const int64_t nstep = *I.step;
+  const double *win = stage_input(I, A.s);
+  const bool periodic = I.bc_left == ADG_BC_PERIODIC;
+  const double inv_dx = 1.0 / I.dx;
+  for (int item = threadIdx.x; item < te * nv; item += blockDim.x) {
+    const int v = item / te, e = e0 + (item - v * te);
+    const double *we = win + ((size_t)v * N + e) * Q;
+    double w[Q], q[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) w[j] = we[j];
+    const double whl = face_mean<Q>(I, win, nstep, A.s, e, v, periodic);
+    const double whr = face_mean<Q>(I, win, nstep, A.s, e + 1, v, periodic);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      double vol = 0.0;
+      for (int j = i - 1; j >= 0; j -= 2) vol += w[j];
+      q[i] = (2.0 * i + 1.0) * inv_dx * (whr - ((i & 1) ? -whl : whl) - 2.0 * vol);
+    }
+    double *qe = I.qx + ((size_t)v * N + e) * Q;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) qe[i] = q[i];
+    if (I.npf > 0) {
+      const int pr = I.pf_of_right[e], pl = I.pf_of_left[e];
+      if (pr >= 0) {
+        double tr = 0.0;
+        for (int i = 0; i < Q; ++i) tr += q[i];
+        I.ring_q[ring_trace(I, nstep, A.s, pr, 0) + v] = tr;
+      }
+      if (pl >= 0) {
+        double tr = 0.0;
+        for (int i = 0; i < Q; ++i) tr += ((i & 1) ? -1.0 : 1.0) * q[i];
+        I.ring_q[ring_trace(I, nstep, A.s, pl, 1) + v] = tr;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host-side launchers
+
+cudaError_t launch_aux(const LimArgs &A, int Q, int n_blocks, cudaStream_t st) {
+  switch (Q) {
+    case 2: aux_kernel<2><<<n_blocks, 128, 0, st>>>(A); break;
+    case 3: aux_kernel<3><<<n_blocks, 128, 0, st>>>(A); break;
+    case 4: aux_kernel<4><<<n_blocks, 128, 0, st>>>(A); break;
+    case 5: aux_kernel<5><<<n_blocks, 128, 0, st>>>(A); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t upload_basis(const Basis *tables) {
   cudaError_t e = upload_unit_tables(tables);
   if (e == cudaSuccess) e = upload_tables_fp64(tables);
   if (e == cudaSuccess) e = upload_tables_mixed(tables);
   if (e == cudaSuccess) e = upload_tables_unsync(tables);
+  if (e == cudaSuccess) e = upload_tables_visc_fp64(tables);
+  if (e == cudaSuccess) e = upload_tables_visc_mixed(tables);
   return e;
 }
 
 cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, bool mixed, int n_tiles,
                          cudaStream_t st) {
+  if (A.visc)
+    return mixed ? launch_stage_visc_mixed(M, A, Q, n_tiles, st)
+                 : launch_stage_visc_fp64(M, A, Q, n_tiles, st);
   return mixed ? launch_stage_mixed(M, A, Q, n_tiles, st) : launch_stage_fp64(M, A, Q, n_tiles, st);
 }
 
@@ -101,13 +210,16 @@ cudaError_t prepare_kernels(int nv, int ns, int nr) {
   cudaError_t e = prepare_fp64();
   if (e == cudaSuccess) e = prepare_mixed();
   if (e == cudaSuccess) e = prepare_unsync();
+  if (e == cudaSuccess) e = prepare_visc_fp64();
+  if (e == cudaSuccess) e = prepare_visc_mixed();
   return e;
 }
 
-int stage_tile(const Mech &M, int Q, int O, bool mixed) {
+int stage_tile(const Mech &M, int Q, int O, bool mixed, bool visc) {
   // elements per tile: up to 256 Gauss points, at most ~96 KB of tile
   int TE = 256 / Q;
-  while (TE > 2 && stage_smem_bytes(TE, Q, M.ns, M.nr, M.nterm, O, mixed) > 96 * 1024) TE /= 2;
+  while (TE > 2 && stage_smem_bytes(TE, Q, M.ns, M.nr, M.nterm, O, mixed, visc) > 96 * 1024)
+    TE /= 2;
   return TE;
 }
 
@@ -118,8 +230,8 @@ int stage_threads(int TE, int Q, int nr) {
   return nt < 128 ? 128 : (nt > 512 ? 512 : nt);
 }
 
-size_t stage_smem(const Mech &M, int TE, int Q, int O, bool mixed) {
-  return stage_smem_bytes(TE, Q, M.ns, M.nr, M.nterm, O, mixed);
+size_t stage_smem(const Mech &M, int TE, int Q, int O, bool mixed, bool visc) {
+  return stage_smem_bytes(TE, Q, M.ns, M.nr, M.nterm, O, mixed, visc);
 }
 
 int limiter_elems_per_block(int64_t n_elem_group, bool mixed) {

@@ -85,7 +85,8 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
       (c.limiter != ADG_LIM_NONE && c.limiter != ADG_LIM_WENO) || c.bc_left < 0 ||
       c.bc_left > 2 || c.bc_right < 0 || c.bc_right > 2 ||
       ((c.bc_left == ADG_BC_PERIODIC) != (c.bc_right == ADG_BC_PERIODIC)) ||
-      (c.precision != ADG_FP64 && c.precision != ADG_MIXED) || c.integrator != ADG_RK_SSP3)
+      (c.precision != ADG_FP64 && c.precision != ADG_MIXED) || c.integrator != ADG_RK_SSP3 ||
+      c.viscous != 0)
     return ADG_ERR_ARG;
   if (!mech->W || !mech->cp || !mech->h_f || !mech->s0) return ADG_ERR_ARG;
   if (nr > 0 && (!mech->nu_f || !mech->nu_r || !mech->A || !mech->b || !mech->Ea))
@@ -122,7 +123,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   size_t o_pl = cur.take(sizeof(int) * N);
   size_t o_pr = cur.take(sizeof(int) * N);
   const bool mixed = c.precision == ADG_MIXED;
-  int TE = stage_tile(M, Q, c.at_order, mixed);
+  int TE = stage_tile(M, Q, c.at_order, mixed, false);
   int target = (N + 2 * 152 - 1) / (2 * 152);
   if (target < TE) TE = target < 4 ? 4 : target;
   const int NT = stage_threads(TE, Q, nr);
@@ -242,6 +243,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
       A.TE = TE;
       A.NT = NT;
       A.O = c.at_order;
+      A.visc = 0;
       NA_CK(launch_stage(M, A, Q, mixed, n_tiles, s));
       if (I.limiter != ADG_LIM_NONE) {
         LimArgs L;

@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(LIM_THREADS) unsync_kernel(Mech M, UnsyncArgs 
   A.TE = U.TE;
   A.NT = nth;
   A.O = U.O;
+  A.visc = 0;  // viscous instances are not run unsynchronised
   LimArgs L;
   L.insts = nullptr;
   L.blocks = nullptr;

@@ -422,6 +422,18 @@ def load_workloads(path: str = WORKLOADS_JSON) -> dict:
     return w
 
 
+def viscous(wl: Workload, **kw) -> Workload:
+    """The viscous variant of a workload (the diffusive flux with the synthetic
+    transport model). The explicit diffusive limit of DG scales like
+    dx^2 / (nu (p+1)^4): on the ignition meshes (dx = 2.4 um) the workload's dt
+    is stable for p <= 3, and p = 4 needs dt/8 (found with the oracle: dt and
+    dt/2 blow up, dt/4 grows slowly, dt/8 stays flat over 2000 steps)."""
+    w = dataclasses.replace(wl, viscous=1, **kw)
+    if w.p >= 4 and "dt" not in kw:
+        w.dt = wl.dt / 8
+    return w
+
+
 def scaled(wl: Workload, n_elem: int, n_pe: int, name: Optional[str] = None) -> Workload:
     """The same workload on fewer elements (for tests): the element size and dt
     are kept and the domain shrinks in proportion."""
