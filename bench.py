@@ -454,6 +454,9 @@ def main(argv=None):
     ap.add_argument("--lserk-steps", type=int, default=100,
                     help="timed steps of the LSERK4 measurement (the 5-stage 4th-order "
                          "low-storage integrator) added to the line; 0 to skip")
+    ap.add_argument("--visc-steps", type=int, default=100,
+                    help="timed steps of the viscous measurement (the diffusive flux with "
+                         "the LDG auxiliary kernel) added to the line; 0 to skip")
     ap.add_argument("--ensemble-steps", type=int, default=20,
                     help="timed steps of the batched-ensemble measurement added to the line "
                     "(0: none)")
@@ -487,6 +490,11 @@ def main(argv=None):
         lw = dataclasses.replace(wls[0], integrator=I.RK_LS4, name=wls[0].name + "-lserk4")
         lsk = (lw, measure(adg, torch, [lw], mech, prims, args.precision, args, dev, pg, ws,
                            args.lserk_steps))
+    vis = None
+    if args.visc_steps > 0 and len(wls) == 1 and not args.only:
+        vw = I.viscous(wls[0], name=wls[0].name + "-viscous")
+        vis = (vw, measure(adg, torch, [vw], mech, prims, args.precision, args, dev, pg, ws,
+                           args.visc_steps))
     ens = None
     if args.ensemble_steps > 0 and args.workload != ENSEMBLE and not args.only:
         ewls, emech = bench_workloads(ENSEMBLE)
@@ -526,6 +534,18 @@ def main(argv=None):
         line["mixed_error"] = err
     if uns is not None:
         line["unsync"] = uns
+    if vis is not None:
+        vw, r = vis
+        line["viscous"] = {
+            "terms": "diffusive flux of Sec. 2 by LDG (auxiliary kernel + viscous stage "
+                     "kernel; the stage time includes the auxiliary kernel)",
+            "dt": vw.dt, "dt_note": "p = 4 runs the viscous terms at dt/8 (explicit "
+                                    "diffusive limit), so a step covers 1/8 of the time",
+            "value": r["value"], "unit": "DOF-stage/s", "steps": args.visc_steps,
+            "ms_per_step": r["ms"] / args.visc_steps, "e2e": r["e2e"],
+            "roofline": dict(roofline([vw], mech, r, mixed, peaks, src),
+                             note="algorithmic flops of the Euler terms only: a lower bound"),
+            "clocks": r["clocks"], "tuning": r["tuning"]}
     if lsk is not None:
         lw, r = lsk
         line["lserk4"] = {
