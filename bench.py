@@ -175,6 +175,8 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return 0
     wls, mech = bench_workloads(args.workload)
+    if args.viscous:
+        wls = [I.viscous(w, name=w.name + "-viscous") for w in wls]
     cb = cpu_baseline(wls, mech, budget_s=max(5.0, 60.0 / max(1, args.steps + args.warmup)),
                       max_steps=max(1, args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"],
@@ -454,6 +456,9 @@ def main(argv=None):
     ap.add_argument("--lserk-steps", type=int, default=100,
                     help="timed steps of the LSERK4 measurement (the 5-stage 4th-order "
                          "low-storage integrator) added to the line; 0 to skip")
+    ap.add_argument("--viscous", action="store_true",
+                    help="run the headline workload with the viscous terms (its viscous "
+                         "variant: dt/8 at p = 4)")
     ap.add_argument("--visc-steps", type=int, default=100,
                     help="timed steps of the viscous measurement (the diffusive flux with "
                          "the LDG auxiliary kernel) added to the line; 0 to skip")
@@ -491,7 +496,7 @@ def main(argv=None):
         lsk = (lw, measure(adg, torch, [lw], mech, prims, args.precision, args, dev, pg, ws,
                            args.lserk_steps))
     vis = None
-    if args.visc_steps > 0 and len(wls) == 1 and not args.only:
+    if args.visc_steps > 0 and len(wls) == 1 and not args.only and not args.viscous:
         vw = I.viscous(wls[0], name=wls[0].name + "-viscous")
         vis = (vw, measure(adg, torch, [vw], mech, prims, args.precision, args, dev, pg, ws,
                            args.visc_steps))
