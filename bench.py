@@ -482,6 +482,8 @@ def main(argv=None):
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
     wls, mech = bench_workloads(args.workload)
+    if args.viscous:
+        wls = [I.viscous(w, name=w.name + "-viscous") for w in wls]
     prims = [w.primitive(mech) for w in wls]
     err_steps = 200 if len(wls) == 1 else 20
     head, other, other_prec, err = compare(adg, torch, wls, mech, prims, args, dev, pg, ws,
