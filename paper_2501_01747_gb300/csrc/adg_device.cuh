@@ -91,50 +91,62 @@ __host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int ns, int nr
 // is -(mu / (Pr Le_i)) (Y_i,x - Y_i n_x / n), and the correction velocity makes
 // J_i = J_i* - Y_i sum_j J_j*. Transport: mu = mu_ref (T / T_mu)^mu_exp,
 // k = mu c_p / Pr, rho D_i = k / (c_p Le_i).
-__device__ inline void visc_flux_dev(const double *sp, int ns, const Inst &I, const double *w,
-                                     int ws, const double *q, int qs, double *fd, int fs) {
-  const double *sIW = sp + SP_INVW * ns, *sQW = sp + SP_QW * ns, *sCVW = sp + SP_CVW * ns;
-  const double *sCPW = sp + SP_CPW * ns, *sIL = sp + SP_INVLE * ns;
-  double rho = 0.0, rho_x = 0.0, qsum = 0.0, cv = 0.0;
+// R is the arithmetic type of everything but T, which is always formed in FP64
+// (the internal energy cancels against the formation energies); sp holds the
+// species fields in FP64, spr in R.
+template <typename R>
+__device__ inline void visc_flux_dev(const double *sp, const R *spr, int ns, const Inst &I,
+                                     const double *w, int ws, const double *q, int qs,
+                                     double *fd, int fs) {
+  const double *sQW = sp + SP_QW * ns, *sCVW = sp + SP_CVW * ns;
+  const R *rIW = spr + SP_INVW * ns, *rQW = spr + SP_QW * ns, *rCVW = spr + SP_CVW * ns;
+  const R *rCPW = spr + SP_CPW * ns, *rIL = spr + SP_INVLE * ns;
+  double rho_d = 0.0, qsum = 0.0, cv_d = 0.0;
+  R rho_x = R(0);
   for (int i = 0; i < ns; ++i) {
     const double r = w[(2 + i) * ws];
-    rho += r;
-    rho_x += q[(2 + i) * qs];
+    rho_d += r;
     qsum = fma(r, sQW[i], qsum);
-    cv = fma(r, sCVW[i], cv);
+    cv_d = fma(r, sCVW[i], cv_d);
+    rho_x += (R)q[(2 + i) * qs];
   }
-  const double irho = 1.0 / rho, m = w[0], u = m * irho;
-  const double u_x = (q[0] - u * rho_x) * irho;
-  const double T = (w[ws] - 0.5 * m * u - qsum) / cv;
-  double num = q[qs] - 0.5 * (q[0] * u + m * u_x), n = 0.0, n_x = 0.0, cpm = 0.0;
+  const double T_d = (w[ws] - 0.5 * w[0] * (w[0] / rho_d) - qsum) / cv_d;
+  const R T = (R)T_d, rho = (R)rho_d, cv = (R)cv_d;
+  const R irho = R(1) / rho, m = (R)w[0], u = m * irho;
+  const R u_x = ((R)q[0] - u * rho_x) * irho;
+  R num = (R)q[qs] - R(0.5) * ((R)q[0] * u + m * u_x), n = R(0), n_x = R(0), cpm = R(0);
   for (int i = 0; i < ns; ++i) {
-    const double rx = q[(2 + i) * qs], Y = w[(2 + i) * ws] * irho;
-    const double Yx = (rx - Y * rho_x) * irho;
-    num -= rx * fma(sCVW[i], T, sQW[i]);
-    n = fma(Y, sIW[i], n);
-    n_x = fma(Yx, sIW[i], n_x);
-    cpm = fma(Y, sCPW[i], cpm);
+    const R rx = (R)q[(2 + i) * qs], Y = (R)w[(2 + i) * ws] * irho;
+    const R Yx = (rx - Y * rho_x) * irho;
+    num -= rx * fma(rCVW[i], T, rQW[i]);
+    n = fma(Y, rIW[i], n);
+    n_x = fma(Yx, rIW[i], n_x);
+    cpm = fma(Y, rCPW[i], cpm);
   }
-  const double T_x = num / cv;
-  const double mu = I.mu_ref * exp(I.mu_exp * (log(T) - I.ln_T_mu));
-  const double a = mu * I.inv_prandtl, kc = a * cpm, nxn = n_x / n;
-  double Jsum = 0.0;
+  const R T_x = num / cv;
+  R mu;
+  if constexpr (std::is_same<R, float>::value)
+    mu = (float)I.mu_ref * expf((float)I.mu_exp * (logf(T) - (float)I.ln_T_mu));
+  else
+    mu = I.mu_ref * exp(I.mu_exp * (log(T) - I.ln_T_mu));
+  const R a = mu * (R)I.inv_prandtl, kc = a * cpm, nxn = n_x / n;
+  R Jsum = R(0);
   for (int i = 0; i < ns; ++i) {
-    const double Y = w[(2 + i) * ws] * irho;
-    const double Yx = (q[(2 + i) * qs] - Y * rho_x) * irho;
-    const double Js = -a * sIL[i] * (Yx - Y * nxn);
-    fd[(2 + i) * fs] = Js;
+    const R Y = (R)w[(2 + i) * ws] * irho;
+    const R Yx = ((R)q[(2 + i) * qs] - Y * rho_x) * irho;
+    const R Js = -a * rIL[i] * (Yx - Y * nxn);
+    fd[(2 + i) * fs] = (double)Js;
     Jsum += Js;
   }
-  double qh = -kc * T_x;
+  R qh = -kc * T_x;
   for (int i = 0; i < ns; ++i) {
-    const double J = fd[(2 + i) * fs] - w[(2 + i) * ws] * irho * Jsum;
-    qh = fma(fma(sCPW[i], T, sQW[i]), J, qh);
-    fd[(2 + i) * fs] = -J;
+    const R J = (R)fd[(2 + i) * fs] - (R)w[(2 + i) * ws] * irho * Jsum;
+    qh = fma(fma(rCPW[i], T, rQW[i]), J, qh);
+    fd[(2 + i) * fs] = (double)(-J);
   }
-  const double tau = (4.0 / 3.0) * mu * u_x;
-  fd[0] = tau;
-  fd[fs] = tau * u - qh;
+  const R tau = R(4.0 / 3.0) * mu * u_x;
+  fd[0] = (double)tau;
+  fd[fs] = (double)(tau * u - qh);
 }
 
 // Copy an instance description into shared memory (by 8-byte words).
@@ -163,10 +175,10 @@ __device__ __forceinline__ double ring_load(const double *p) {
 // Viscous part of a face flux: from the traces vt = (w_l, w_r, q_l, q_r) [4][nv],
 // f^d of each side (over its q) and fl -= (f^d_l + f^d_r) / 2.
 template <typename DG>
-__device__ inline void visc_face(const double *sp, int ns, const Inst &I, int nv, double *vt,
-                                 DG *fl) {
-  visc_flux_dev(sp, ns, I, vt, 1, vt + 2 * nv, 1, vt + 2 * nv, 1);
-  visc_flux_dev(sp, ns, I, vt + nv, 1, vt + 3 * nv, 1, vt + 3 * nv, 1);
+__device__ inline void visc_face(const double *sp, const DG *spr, int ns, const Inst &I, int nv,
+                                 double *vt, DG *fl) {
+  visc_flux_dev<DG>(sp, spr, ns, I, vt, 1, vt + 2 * nv, 1, vt + 2 * nv, 1);
+  visc_flux_dev<DG>(sp, spr, ns, I, vt + nv, 1, vt + 3 * nv, 1, vt + 3 * nv, 1);
   for (int v = 0; v < nv; ++v) fl[v] -= (DG)(0.5 * (vt[2 * nv + v] + vt[3 * nv + v]));
 }
 
@@ -347,7 +359,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       su[t] = u;
       sPr[t] = T * Rm;
       // the diffusive flux at the point, over its q
-      if (visc) visc_flux_dev(ssp, ns, I, wq, TQ, sqn + t, TQ, sqn + t, TQ);
+      if (visc) visc_flux_dev<DG>(ssp, sspD, ns, I, wq, TQ, sqn + t, TQ, sqn + t, TQ);
     }
   }
   __syncthreads();
@@ -457,7 +469,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
           vt[2 * nv + v] = ring_load<UNSYNC>(ql + v);
           vt[3 * nv + v] = ring_load<UNSYNC>(qr + v);
         }
-        visc_face(ssp, ns, I, nv, vt, fl);
+        visc_face<DG>(ssp, sspD, ns, I, nv, vt, fl);
       }
       continue;
     }
@@ -505,7 +517,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         }
     }
     num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
-    if (visc) visc_face(ssp, ns, I, nv, vt, fl);
+    if (visc) visc_face<DG>(ssp, sspD, ns, I, nv, vt, fl);
   }
   __syncthreads();
 
