@@ -94,24 +94,33 @@ __host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int ns, int nr
 // R is the arithmetic type of everything but T, which is always formed in FP64
 // (the internal energy cancels against the formation energies); sp holds the
 // species fields in FP64, spr in R.
+// T_known > 0: the temperature of w, already formed by the caller.
 template <typename R>
 __device__ inline void visc_flux_dev(const double *sp, const R *spr, int ns, const Inst &I,
                                      const double *w, int ws, const double *q, int qs,
-                                     double *fd, int fs) {
+                                     double *fd, int fs, double T_known = 0.0) {
   const double *sQW = sp + SP_QW * ns, *sCVW = sp + SP_CVW * ns;
   const R *rIW = spr + SP_INVW * ns, *rQW = spr + SP_QW * ns, *rCVW = spr + SP_CVW * ns;
   const R *rCPW = spr + SP_CPW * ns, *rIL = spr + SP_INVLE * ns;
-  double rho_d = 0.0, qsum = 0.0, cv_d = 0.0;
-  R rho_x = R(0);
+  R rho = R(0), cv = R(0), rho_x = R(0);
   for (int i = 0; i < ns; ++i) {
-    const double r = w[(2 + i) * ws];
-    rho_d += r;
-    qsum = fma(r, sQW[i], qsum);
-    cv_d = fma(r, sCVW[i], cv_d);
+    const R r = (R)w[(2 + i) * ws];
+    rho += r;
+    cv = fma(r, rCVW[i], cv);
     rho_x += (R)q[(2 + i) * qs];
   }
-  const double T_d = (w[ws] - 0.5 * w[0] * (w[0] / rho_d) - qsum) / cv_d;
-  const R T = (R)T_d, rho = (R)rho_d, cv = (R)cv_d;
+  double T_d = T_known;
+  if (!(T_d > 0.0)) {
+    double rho_d = 0.0, qsum = 0.0, cv_d = 0.0;
+    for (int i = 0; i < ns; ++i) {
+      const double r = w[(2 + i) * ws];
+      rho_d += r;
+      qsum = fma(r, sQW[i], qsum);
+      cv_d = fma(r, sCVW[i], cv_d);
+    }
+    T_d = (w[ws] - 0.5 * w[0] * (w[0] / rho_d) - qsum) / cv_d;
+  }
+  const R T = (R)T_d;
   const R irho = R(1) / rho, m = (R)w[0], u = m * irho;
   const R u_x = ((R)q[0] - u * rho_x) * irho;
   R num = (R)q[qs] - R(0.5) * ((R)q[0] * u + m * u_x), n = R(0), n_x = R(0), cpm = R(0);
@@ -359,7 +368,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       su[t] = u;
       sPr[t] = T * Rm;
       // the diffusive flux at the point, over its q
-      if (visc) visc_flux_dev<DG>(ssp, sspD, ns, I, wq, TQ, sqn + t, TQ, sqn + t, TQ);
+      if (visc) visc_flux_dev<DG>(ssp, sspD, ns, I, wq, TQ, sqn + t, TQ, sqn + t, TQ, T);
     }
   }
   __syncthreads();
