@@ -102,6 +102,13 @@ void adg::make_tables(Basis *tables) {
 
 // Species fields (constant c_p thermo, Sec. 2), packed reactions and the
 // species -> reaction incidence of the net stoichiometry.
+void adg::pack_rxf(const Rxn *rx, int nr, DF *rxf) {
+  for (int j = 0; j < nr; ++j) {
+    const double c[6] = {rx[j].lnA, rx[j].b, rx[j].mEaR, rx[j].kr0, rx[j].kr1, rx[j].kr2};
+    for (int k = 0; k < 6; ++k) rxf[6 * j + k] = df_split(c[k]);
+  }
+}
+
 int adg::pack_mechanism(const adg_mechanism *m, double *sp, Rxn *rx, int *sx_off, int *sx) {
   const int ns = m->n_species, nr = m->n_reactions;
   for (int i = 0; i < ns; ++i) {
@@ -351,6 +358,7 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
   Mech &M = ctx->mech;
   M.sp = (const double *)cv.take(sizeof(double) * SP_NFIELDS * ns);
   M.rx = (const Rxn *)cv.take(sizeof(Rxn) * nrr);
+  M.rxf = (const DF *)cv.take(sizeof(DF) * 6 * nrr);
   M.sx_off = (const int *)cv.take(sizeof(int) * (ns + 1));
   M.sx = (const int *)cv.take(sizeof(int) * (M.nterm > 0 ? M.nterm : 1));
   ctx->err_all = (int *)cv.take(sizeof(int) * 4 * ctx->n_inst);
@@ -586,8 +594,12 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
     std::vector<int> sx_off(ns + 1), sx(M.nterm > 0 ? M.nterm : 1);
     if (pack_mechanism(mech, sp.data(), rx.data(), sx_off.data(), sx.data()) != M.nterm)
       rc2 = ADG_ERR_ARG;
+    std::vector<DF> rxf(6 * (nr > 0 ? nr : 1));
+    pack_rxf(rx.data(), nr, rxf.data());
     if (cudaMemcpy((void *)M.sp, sp.data(), sizeof(double) * sp.size(), cudaMemcpyHostToDevice) ||
         (nr > 0 && cudaMemcpy((void *)M.rx, rx.data(), sizeof(Rxn) * nr, cudaMemcpyHostToDevice)) ||
+        (nr > 0 &&
+         cudaMemcpy((void *)M.rxf, rxf.data(), sizeof(DF) * 6 * nr, cudaMemcpyHostToDevice)) ||
         cudaMemcpy((void *)M.sx_off, sx_off.data(), sizeof(int) * (ns + 1),
                    cudaMemcpyHostToDevice) ||
         (M.nterm > 0 && cudaMemcpy((void *)M.sx, sx.data(), sizeof(int) * M.nterm,

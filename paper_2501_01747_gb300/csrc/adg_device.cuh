@@ -77,7 +77,9 @@ __host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int ns, int nr
                (size_t)nr * TQ + (size_t)ns * TQ + nterm;
   if (mix) ndg += (size_t)SP_NFIELDS * ns + nv * TQ;
   const size_t ni = F + ns + 1 + nterm;
-  return (size_t)nr * sizeof(Rxn) + nd * 8 + ndg * (mix ? 4 : 8) + ni * 4 + 16 +
+  // mixed variant: the df32 rate coefficients [nr][6] and (ln T, 1/T) per point
+  const size_t ndf = mix ? (size_t)nr * 6 + 2 * TQ : 0;
+  return (size_t)nr * sizeof(Rxn) + nd * 8 + ndg * (mix ? 4 : 8) + ni * 4 + 16 + ndf * 8 + 8 +
          (visc ? stage_visc_doubles(TE, Q, ns, O) * 8 + 8 : 0);
 }
 
@@ -172,6 +174,20 @@ struct PeDelays {
   int k[2];
 };
 
+// float -> double, exact, by moving the bit fields on the integer pipeline: on
+// this GPU a precision conversion occupies the FP64 unit like a double
+// instruction. Zeros and subnormal floats give a signed zero, infinities and NaN
+// keep their class.
+__device__ __forceinline__ double f2d_exact(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned s = u & 0x80000000u;
+  const unsigned ed = (e == 255u) ? 0x7ffu : e + 896u;
+  const unsigned hi = (e == 0u) ? s : (s | (ed << 20) | ((u >> 3) & 0xfffffu));
+  const unsigned lo = (e == 0u) ? 0u : (u << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // A value of the history ring. Written by another CTA of the same launch in the
 // unsynchronised mode, so read from L2 (the point of coherence), not from a
 // possibly stale L1 line of an earlier level in the same slot.
@@ -245,9 +261,12 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   }
   int *soff = sk + NF;        // [ns + 1]
   int *sterm = soff + ns + 1;  // [nterm] reaction of each incidence term
-  // viscous region (groups with viscous instances), FP64, 8-byte aligned
-  double *sqw = reinterpret_cast<double *>(
-      (reinterpret_cast<uintptr_t>(sterm + M.nterm) + 7) & ~(uintptr_t)7);  // [v][TE+2][Q]
+  // mixed variant: df32 rate coefficients and (ln T, 1/T) per point, 8-byte aligned
+  DF *srxf = reinterpret_cast<DF *>(
+      (reinterpret_cast<uintptr_t>(sterm + M.nterm) + 7) & ~(uintptr_t)7);  // [nr][6]
+  DF *sdfT = srxf + (size_t)nr * 6;                                          // [TQ][2]
+  // viscous region (groups with viscous instances), FP64
+  double *sqw = reinterpret_cast<double *>(MIX ? (void *)(sdfT + 2 * TQ) : (void *)srxf);  // [v][TE+2][Q]
   double *sqn = sqw + (size_t)nv * (TE + 2) * Q;                           // [v][TQ]
   double *sqt = sqn + (size_t)nv * TQ;                                     // [O][NF][4][nv]
   // viscous terms: compiled only into the viscous instances of the kernel (the
@@ -269,6 +288,10 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
     for (int k = tid; k < 32; k += nth) {
       stab->t[k] = c_iexp.t[k];
       stab->t32[k] = c_iexp.t32[k];
+      if constexpr (MIX) iexp_table_df(c_iexp.t32[k], &stab->tf[2 * k], &stab->tf[2 * k + 1]);
+    }
+    if constexpr (MIX) {
+      for (int k = tid; k < nr * 6; k += nth) srxf[k] = M.rxf[k];
     }
     for (int k = tid; k < Q * Q; k += nth) sPq[k] = B.P[k / Q][k % Q];
     for (int k = tid; k <= ns; k += nth) soff[k] = M.sx_off[k];
@@ -365,6 +388,10 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         report_error(I, ADG_ERR_NONPHYSICAL, e0 + t / Q, A.s, nstep);
       slnT[t] = log(T);
       sinvT[t] = cv / num;
+      if constexpr (MIX) {
+        sdfT[2 * t] = df_split(slnT[t]);
+        sdfT[2 * t + 1] = df_split(sinvT[t]);
+      }
       su[t] = u;
       sPr[t] = T * Rm;
       // the diffusive flux at the point, over its q
@@ -414,16 +441,17 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
     if (item >= n_face) {
       const int j = (item - n_face) / teq, t = (item - n_face) - j * teq;
       const Rxn &Rx = srx[j];
-      const double lnT = slnT[t], invT = sinvT[t];
-      const double lkf = fma(Rx.mEaR, invT, fma(Rx.b, lnT, Rx.lnA));
-      const double lkr = fma(Rx.kr2, invT, fma(Rx.kr1, lnT, Rx.kr0));
       DG fwd, rev;
       if constexpr (MIX) {
-        fwd = iexpf(lkf, *stab);
-        rev = iexpf(lkr, *stab);
+        // arguments in df32 and the FP32-pipe exp: no FP64 instruction and no
+        // precision conversion per item
+        const DF lnT = sdfT[2 * t], invT = sdfT[2 * t + 1], *c = srxf + 6 * j;
+        fwd = exp_df(df_fma(c[2], invT, df_fma(c[1], lnT, c[0])), stab->tf);
+        rev = exp_df(df_fma(c[5], invT, df_fma(c[4], lnT, c[3])), stab->tf);
       } else {
-        fwd = iexp(lkf, *stab);
-        rev = iexp(lkr, *stab);
+        const double lnT = slnT[t], invT = sinvT[t];
+        fwd = iexp(fma(Rx.mEaR, invT, fma(Rx.b, lnT, Rx.lnA)), *stab);
+        rev = iexp(fma(Rx.kr2, invT, fma(Rx.kr1, lnT, Rx.kr0)), *stab);
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -557,13 +585,15 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   // combination (FP64); history ring writes
   const int slot_ok = (I.npf > 0);
   const double inv_dx = 1.0 / I.dx;
-  const double *sW = ssp + SP_W * ns;
+  DG scale[Q];  // (2i+1)/dx in the variant's type, once per thread
+#pragma unroll
+  for (int i = 0; i < Q; ++i) scale[i] = (DG)((2.0 * i + 1.0) * inv_dx);
   for (int item = tid; item < nv * te; item += nth) {
     const int v = item / te, e = item - v * te, ge = e0 + e, le = e + 1;
     const double *wi = sw + ((size_t)v * (TE + 2) + le) * Q;
     const DG *fq = sfx + (size_t)v * TQ + e * Q;
     const DG *sqv = (v >= 2) ? swd + (size_t)(v - 2) * TQ + e * Q : nullptr;
-    const DG Wv = (v >= 2) ? (DG)sW[v - 2] : DG(0);
+    const DG Wv = (v >= 2) ? sspD[SP_W * ns + v - 2] : DG(0);
     const DG fr = sfh[(size_t)(e + 1) * nv + v], fl = sfh[(size_t)e * nv + v];
     DG fqr[Q], sqr[Q];
 #pragma unroll
@@ -586,7 +616,9 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         }
       }
       DG surf = (i & 1) ? (V - fr - fl) : (V - fr + fl);
-      double r = (double)fma((DG)((2.0 * i + 1.0) * inv_dx), surf, Wv * S);
+      double r;
+      if constexpr (MIX) r = f2d_exact(fmaf(scale[i], surf, Wv * S));
+      else r = fma(scale[i], surf, Wv * S);
       size_t gi = ((size_t)v * N + ge) * Q + i;
       double o;
       if (I.lserk) {

@@ -2,12 +2,13 @@
 //
 // Layout in HBM (per instance): modal state [nv][n_elem][p+1] FP64, SoA by
 // variable, so that a tile of consecutive elements of one variable is one
-// contiguous span; history ring [depth][3 stages][PE faces][2 sides][nv][p+1].
+// contiguous span; history ring [depth][RK stages][PE faces][2 sides][nv][p+1].
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "../../include/adg.h"
+#include "adg_math.cuh"
 
 namespace adg {
 
@@ -57,6 +58,7 @@ struct Mech {
   int ns, nr, nterm;
   const double *sp;   // [SP_NFIELDS][ns]
   const Rxn *rx;      // [nr]
+  const DF *rxf;      // [nr][6] lnA, b, mEaR, kr0, kr1, kr2 as df32 (mixed variant)
   const int *sx_off;  // [ns + 1]
   const int *sx;      // [nterm]
 };
@@ -65,6 +67,8 @@ struct Mech {
 // sx_off [ns + 1] and sx [nr * NET]; returns the number of incidence terms, or
 // ADG_ERR_ARG for a reaction the tables cannot hold.
 int pack_mechanism(const adg_mechanism *m, double *sp, Rxn *rx, int *sx_off, int *sx);
+// Host: the rate coefficients of nr reactions as df32, [nr][6].
+void pack_rxf(const Rxn *rx, int nr, DF *rxf);
 
 // Per-instance description, passed by value to the kernels.
 struct Inst {

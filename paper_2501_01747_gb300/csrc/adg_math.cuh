@@ -55,6 +55,7 @@ namespace adg {
 struct IExpTable {
   unsigned long long t[32];
   unsigned int t32[32];
+  float tf[64];  // 2^(j/32) as float pairs (iexp_table_df), filled where used
 };
 
 constexpr unsigned long long IEXP_K = 3326628274461080623ull;   // 2^56 * 32/ln2
@@ -234,6 +235,89 @@ __host__ __device__ __forceinline__ float iexpf(double x, const IExpTable &tab) 
   if (e <= 0) return 0.0f;
   if (e >= 255) return iexp_float(0x7f800000);
   return iexp_float((e << 23) + (int)(mt - (1u << 23)));
+}
+
+// ---------------------------------------------------------------------------
+// Float-float ("df32") arithmetic for the mixed-precision chemistry: a value is
+// hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits, on the FP32 pipe
+// (on this GPU FP64 instructions and double<->float conversions both occupy the
+// scarce FP64 unit). Error-free transforms: Dekker's product by a fused
+// multiply-add and Knuth's two-sum (Dekker, Numer. Math. 18, 1971; Knuth, TAOCP
+// vol. 2). The _rn intrinsics keep the compiler from contracting the sums.
+struct DF {
+  float hi, lo;
+};
+
+#ifdef __CUDA_ARCH__
+#define ADG_FADD(a, b) __fadd_rn(a, b)
+#define ADG_FSUB(a, b) __fsub_rn(a, b)
+#define ADG_FMUL(a, b) __fmul_rn(a, b)
+#else
+#define ADG_FADD(a, b) ((a) + (b))
+#define ADG_FSUB(a, b) ((a) - (b))
+#define ADG_FMUL(a, b) ((a) * (b))
+#endif
+
+// The df32 value nearest to x (hi the rounded float, lo the rounded remainder).
+__host__ __device__ __forceinline__ DF df_split(double x) {
+  const float h = (float)x;
+  return DF{h, (float)(x - (double)h)};
+}
+
+// a b + c, all df32 (relative error about 2^-46).
+__host__ __device__ __forceinline__ DF df_fma(DF a, DF b, DF c) {
+  const float p = ADG_FMUL(a.hi, b.hi);
+  float pe = fmaf(a.hi, b.hi, -p);  // the rounding error of p, exactly
+  pe = fmaf(a.hi, b.lo, pe);
+  pe = fmaf(a.lo, b.hi, pe);
+  const float s = ADG_FADD(p, c.hi);  // two-sum of p and c.hi
+  const float bb = ADG_FSUB(s, p);
+  float e = ADG_FADD(ADG_FSUB(p, ADG_FSUB(s, bb)), ADG_FSUB(c.hi, bb));
+  e = ADG_FADD(e, ADG_FADD(pe, c.lo));
+  const float h = ADG_FADD(s, e);  // renormalise
+  return DF{h, ADG_FSUB(e, ADG_FSUB(h, s))};
+}
+
+// 2^(j/32) as a float pair tf[2j] + tf[2j+1] (the rounded float and the
+// remainder), from the 32-bit table entry (scaled by 2^31): good to about 2^-32.
+__host__ __device__ __forceinline__ void iexp_table_df(unsigned int t32, float *hi, float *lo) {
+  const float h = (float)t32;                                 // 24 leading bits
+  const float l = (float)((long long)t32 - (long long)h);     // the rest, exactly
+  *hi = ADG_FMUL(h, 4.656612873077393e-10f);                  // 2^-31, exact
+  *lo = ADG_FMUL(l, 4.656612873077393e-10f);
+}
+
+// exp(x) for a df32 argument, float result, on the FP32 pipe: Tang's table
+// reduction (ACM TOMS 15(2), 1989) in float-float, t = x 32/ln2, n = rint(t),
+// r = (t - n) ln2/32 with |r| <= ln2/64, exp(x) = 2^(n >> 5) 2^((n & 31)/32) e^r
+// with e^r - 1 by the degree-4 Taylor polynomial (truncation below r^5/120 <
+// 2^-38) and the table entry as a float pair, combined as
+// t_hi + (t_hi (e^r - 1) + t_lo) so that one final rounding dominates: about half
+// a unit in the last place. Results below the normal range are flushed to zero;
+// above it the result is infinity.
+__host__ __device__ __forceinline__ float exp_df(DF x, const float *tf) {
+  const DF K = {46.16624069f, 6.1630817e-07f};  // 32/ln2 as df32
+  if (!(x.hi < 88.8f)) return (x.hi != x.hi) ? x.hi : iexp_float(0x7f800000);
+  if (!(x.hi > -103.0f)) return 0.0f;
+  const DF t = df_fma(x, K, DF{0.0f, 0.0f});
+  const float nf = rintf(t.hi);
+  const int n = (int)nf;
+  const float r = ADG_FMUL(ADG_FADD(ADG_FSUB(t.hi, nf), t.lo), 0.021660849f);  // ln2/32
+  float q = fmaf(r, 0.041666668f, 0.16666667f);
+  q = fmaf(r, q, 0.5f);
+  q = fmaf(r, q, 1.0f);
+  q = ADG_FMUL(r, q);  // e^r - 1
+  const float th = tf[2 * (n & 31)], tl = tf[2 * (n & 31) + 1];
+  const float v = ADG_FADD(th, fmaf(th, q, tl));  // in [0.98, 2.03)
+  int vb;
+  std::memcpy(&vb, &v, 4);
+  const int e = ((vb >> 23) & 0xff) + (n >> 5);
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return iexp_float(0x7f800000);
+  vb += (n >> 5) << 23;
+  float o;
+  std::memcpy(&o, &vb, 4);
+  return o;
 }
 
 }  // namespace adg

@@ -108,6 +108,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   Cursor cur{nullptr, 0};
   size_t o_sp = cur.take(sizeof(double) * SP_NFIELDS * ns);
   size_t o_rx = cur.take(sizeof(Rxn) * (nr > 0 ? nr : 1));
+  size_t o_rxf = cur.take(sizeof(DF) * 6 * (nr > 0 ? nr : 1));
   size_t o_sxo = cur.take(sizeof(int) * (ns + 1));
   size_t o_sx = cur.take(sizeof(int) * (M.nterm > 0 ? M.nterm : 1));
   size_t o_err = cur.take(sizeof(int) * 4);
@@ -141,6 +142,8 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   int sx_off[ADG_MAX_SPECIES + 1];
   int sx[ADG_NOALLOC_MAX_REACTIONS * NET];
   if (pack_mechanism(mech, sp, rx, sx_off, sx) != M.nterm) return ADG_ERR_ARG;
+  DF rxf[6 * (ADG_NOALLOC_MAX_REACTIONS > 0 ? ADG_NOALLOC_MAX_REACTIONS : 1)];
+  pack_rxf(rx, nr, rxf);
 
   // once per device: the scratch address and the constant tables. This is the
   // only set-up; it runs on the first call on each device.
@@ -165,6 +168,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
 
   M.sp = (const double *)(base + o_sp);
   M.rx = (const Rxn *)(base + o_rx);
+  M.rxf = (const DF *)(base + o_rxf);
   M.sx_off = (const int *)(base + o_sxo);
   M.sx = (const int *)(base + o_sx);
   Inst I;
@@ -224,6 +228,8 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   NA_CK(cudaMemcpyAsync(base + o_sp, sp, sizeof(double) * SP_NFIELDS * ns,
                         cudaMemcpyHostToDevice, s));
   if (nr > 0) NA_CK(cudaMemcpyAsync(base + o_rx, rx, sizeof(Rxn) * nr, cudaMemcpyHostToDevice, s));
+  if (nr > 0)
+    NA_CK(cudaMemcpyAsync(base + o_rxf, rxf, sizeof(DF) * 6 * nr, cudaMemcpyHostToDevice, s));
   NA_CK(cudaMemcpyAsync(base + o_sxo, sx_off, sizeof(int) * (ns + 1), cudaMemcpyHostToDevice, s));
   if (M.nterm > 0)
     NA_CK(cudaMemcpyAsync(base + o_sx, sx, sizeof(int) * M.nterm, cudaMemcpyHostToDevice, s));
