@@ -666,6 +666,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
 
 template <int Q, bool MIX, bool VISC>
 __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
+  pdl_enter();
   __shared__ Inst sI;
   const int2 tile = A.tiles[blockIdx.x];
   load_inst(sI, A.insts + tile.x);
@@ -1204,6 +1205,7 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
 
 template <int Q, int G, bool MIX, int EPB>
 __global__ void __launch_bounds__(LIM_THREADS) limiter_kernel(Mech M, LimArgs A) {
+  pdl_enter();
   __shared__ Inst sI;
   const int2 blkid = A.blocks[blockIdx.x];
   load_inst(sI, A.insts + blkid.x);
@@ -1229,8 +1231,7 @@ static cudaError_t launch_stage_q(const Mech &M, const StageArgs &A, int n_tiles
   if ((A.visc != 0) != VISC) return cudaErrorInvalidValue;
   size_t smem = stage_smem_bytes(A.TE, Q, M.ns, M.nr, M.nterm, A.O, MIX, VISC);
   if (A.NT < 32 || A.NT > 512 || A.NT % 32) return cudaErrorInvalidValue;
-  stage_kernel<Q, MIX, VISC><<<n_tiles, A.NT, smem, st>>>(M, A);
-  return cudaGetLastError();
+  return launch_pdl(stage_kernel<Q, MIX, VISC>, dim3(n_tiles), dim3(A.NT), smem, st, M, A);
 }
 
 template <bool MIX, bool VISC>
@@ -1263,8 +1264,8 @@ template <int Q, int G, bool MIX, int EPB>
 static cudaError_t launch_limiter_qge(const Mech &M, const LimArgs &A, int nv, int n_blocks,
                                       cudaStream_t st) {
   const size_t smem = limiter_smem_bytes<Q, G, MIX, EPB>(nv, M.ns);
-  limiter_kernel<Q, G, MIX, EPB><<<n_blocks, LIM_THREADS, smem, st>>>(M, A);
-  return cudaGetLastError();
+  return launch_pdl(limiter_kernel<Q, G, MIX, EPB>, dim3(n_blocks), dim3(LIM_THREADS), smem, st,
+                    M, A);
 }
 
 template <int Q, bool MIX>

@@ -102,6 +102,7 @@ __device__ double face_mean(const Inst &I, const double *win, int64_t nstep, int
 // its PE face to the q ring (level n, stage s).
 template <int Q>
 __global__ void __launch_bounds__(128) aux_kernel(LimArgs A) {
+  pdl_enter();
   __shared__ Inst sI;
   const int2 blk = A.blocks[blockIdx.x];
   load_inst(sI, A.insts + blk.x);
@@ -151,13 +152,12 @@ __global__ void __launch_bounds__(128) aux_kernel(LimArgs A) {
 
 cudaError_t launch_aux(const LimArgs &A, int Q, int n_blocks, cudaStream_t st) {
   switch (Q) {
-    case 2: aux_kernel<2><<<n_blocks, 128, 0, st>>>(A); break;
-    case 3: aux_kernel<3><<<n_blocks, 128, 0, st>>>(A); break;
-    case 4: aux_kernel<4><<<n_blocks, 128, 0, st>>>(A); break;
-    case 5: aux_kernel<5><<<n_blocks, 128, 0, st>>>(A); break;
-    default: return cudaErrorInvalidValue;
+    case 2: return launch_pdl(aux_kernel<2>, dim3(n_blocks), dim3(128), 0, st, A);
+    case 3: return launch_pdl(aux_kernel<3>, dim3(n_blocks), dim3(128), 0, st, A);
+    case 4: return launch_pdl(aux_kernel<4>, dim3(n_blocks), dim3(128), 0, st, A);
+    case 5: return launch_pdl(aux_kernel<5>, dim3(n_blocks), dim3(128), 0, st, A);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t upload_basis(const Basis *tables) {
@@ -242,6 +242,7 @@ int limiter_elems_per_block(int64_t n_elem_group, bool mixed) {
 }
 
 __global__ void advance_kernel(int64_t *steps, int n) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) steps[i] += 1;
 }
@@ -254,8 +255,7 @@ cudaError_t launch_advance_by(int64_t *step, int64_t n, cudaStream_t st) {
 }
 
 cudaError_t launch_advance(int64_t *steps, int n, cudaStream_t st) {
-  advance_kernel<<<(n + 127) / 128, 128, 0, st>>>(steps, n);
-  return cudaGetLastError();
+  return launch_pdl(advance_kernel, dim3((n + 127) / 128), dim3(128), 0, st, steps, n);
 }
 
 cudaError_t launch_project(const Mech &M, const Inst &I, const double *prim, double *w,
