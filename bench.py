@@ -589,7 +589,7 @@ STAGE_TRAFFIC = {
     ("ignition-9sp-4096x4", "v10", "fp64"): 2.049792e6,
 }
 
-KERNEL_REV = "v10"
+KERNEL_REV = "v11"
 
 if __name__ == "__main__":
     sys.exit(main())
