@@ -65,7 +65,8 @@ using dg_t = typename std::conditional<MIX, float, double>::type;
 // both sides (then f^d of both sides).
 __host__ __device__ inline size_t stage_visc_doubles(int TE, int Q, int ns, int O) {
   const size_t nv = ns + 2;
-  return nv * (TE + 2) * Q + nv * (size_t)TE * Q + (size_t)O * (TE + 1) * 4 * nv;
+  return nv * (TE + 2) * Q + nv * (size_t)TE * Q + (size_t)O * (TE + 1) * 4 * nv +
+         (size_t)TE * Q;
 }
 
 __host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int ns, int nr, int nterm,
@@ -83,82 +84,6 @@ __host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int ns, int nr
          (visc ? stage_visc_doubles(TE, Q, ns, O) * 8 + 8 : 0);
 }
 
-// Diffusive flux of Sec. 2 at one point from the state w and its derivative
-// q = dw/dx (LDG), arrays strided (variable v at w[v * ws]); fd (stride fs) gets
-// (tau, tau u - q_h, -J_1 .. -J_Ns); fd may be q itself. T in closed form
-// (constant c_p), the primitive derivatives by the chain rule (rho_x = sum
-// q_{rho Y_i}, u_x = (q_{rho u} - u rho_x) / rho, Y_i,x = (q_{rho Y_i} - Y_i rho_x)
-// / rho, T_x from the derivative of rho E - (rho u) u / 2 = sum rho Y_i e_i(T)).
-// With X_i = Y_i / (W_i n), n = sum Y_j / W_j, the flux -rho D_i (Y_i / X_i) dX_i/dx
-// is -(mu / (Pr Le_i)) (Y_i,x - Y_i n_x / n), and the correction velocity makes
-// J_i = J_i* - Y_i sum_j J_j*. Transport: mu = mu_ref (T / T_mu)^mu_exp,
-// k = mu c_p / Pr, rho D_i = k / (c_p Le_i).
-// R is the arithmetic type of everything but T, which is always formed in FP64
-// (the internal energy cancels against the formation energies); sp holds the
-// species fields in FP64, spr in R.
-// T_known > 0: the temperature of w, already formed by the caller.
-template <typename R>
-__device__ inline void visc_flux_dev(const double *sp, const R *spr, int ns, const Inst &I,
-                                     const double *w, int ws, const double *q, int qs,
-                                     double *fd, int fs, double T_known = 0.0) {
-  const double *sQW = sp + SP_QW * ns, *sCVW = sp + SP_CVW * ns;
-  const R *rIW = spr + SP_INVW * ns, *rQW = spr + SP_QW * ns, *rCVW = spr + SP_CVW * ns;
-  const R *rCPW = spr + SP_CPW * ns, *rIL = spr + SP_INVLE * ns;
-  R rho = R(0), cv = R(0), rho_x = R(0);
-  for (int i = 0; i < ns; ++i) {
-    const R r = (R)w[(2 + i) * ws];
-    rho += r;
-    cv = fma(r, rCVW[i], cv);
-    rho_x += (R)q[(2 + i) * qs];
-  }
-  double T_d = T_known;
-  if (!(T_d > 0.0)) {
-    double rho_d = 0.0, qsum = 0.0, cv_d = 0.0;
-    for (int i = 0; i < ns; ++i) {
-      const double r = w[(2 + i) * ws];
-      rho_d += r;
-      qsum = fma(r, sQW[i], qsum);
-      cv_d = fma(r, sCVW[i], cv_d);
-    }
-    T_d = (w[ws] - 0.5 * w[0] * (w[0] / rho_d) - qsum) / cv_d;
-  }
-  const R T = (R)T_d;
-  const R irho = R(1) / rho, m = (R)w[0], u = m * irho;
-  const R u_x = ((R)q[0] - u * rho_x) * irho;
-  R num = (R)q[qs] - R(0.5) * ((R)q[0] * u + m * u_x), n = R(0), n_x = R(0), cpm = R(0);
-  for (int i = 0; i < ns; ++i) {
-    const R rx = (R)q[(2 + i) * qs], Y = (R)w[(2 + i) * ws] * irho;
-    const R Yx = (rx - Y * rho_x) * irho;
-    num -= rx * fma(rCVW[i], T, rQW[i]);
-    n = fma(Y, rIW[i], n);
-    n_x = fma(Yx, rIW[i], n_x);
-    cpm = fma(Y, rCPW[i], cpm);
-  }
-  const R T_x = num / cv;
-  R mu;
-  if constexpr (std::is_same<R, float>::value)
-    mu = (float)I.mu_ref * expf((float)I.mu_exp * (logf(T) - (float)I.ln_T_mu));
-  else
-    mu = I.mu_ref * exp(I.mu_exp * (log(T) - I.ln_T_mu));
-  const R a = mu * (R)I.inv_prandtl, kc = a * cpm, nxn = n_x / n;
-  R Jsum = R(0);
-  for (int i = 0; i < ns; ++i) {
-    const R Y = (R)w[(2 + i) * ws] * irho;
-    const R Yx = ((R)q[(2 + i) * qs] - Y * rho_x) * irho;
-    const R Js = -a * rIL[i] * (Yx - Y * nxn);
-    fd[(2 + i) * fs] = (double)Js;
-    Jsum += Js;
-  }
-  R qh = -kc * T_x;
-  for (int i = 0; i < ns; ++i) {
-    const R J = (R)fd[(2 + i) * fs] - (R)w[(2 + i) * ws] * irho * Jsum;
-    qh = fma(fma(rCPW[i], T, rQW[i]), J, qh);
-    fd[(2 + i) * fs] = (double)(-J);
-  }
-  const R tau = R(4.0 / 3.0) * mu * u_x;
-  fd[0] = (double)tau;
-  fd[fs] = (double)(tau * u - qh);
-}
 
 // Copy an instance description into shared memory (by 8-byte words).
 __device__ inline void load_inst(Inst &dst, const Inst *src) {
@@ -197,15 +122,145 @@ __device__ __forceinline__ double ring_load(const double *p) {
   else return *p;
 }
 
-// Viscous part of a face flux: from the traces vt = (w_l, w_r, q_l, q_r) [4][nv],
-// f^d of each side (over its q) and fl -= (f^d_l + f^d_r) / 2.
-template <typename DG>
-__device__ inline void visc_face(const double *sp, const DG *spr, int ns, const Inst &I, int nv,
-                                 double *vt, DG *fl) {
-  visc_flux_dev<DG>(sp, spr, ns, I, vt, 1, vt + 2 * nv, 1, vt + 2 * nv, 1);
-  visc_flux_dev<DG>(sp, spr, ns, I, vt + nv, 1, vt + 3 * nv, 1, vt + 3 * nv, 1);
-  for (int v = 0; v < nv; ++v) fl[v] -= (DG)(0.5 * (vt[2 * nv + v] + vt[3 * nv + v]));
+// Diffusive flux of Sec. 2 at one point from the state w and its derivative
+// q = dw/dx (LDG), arrays strided (variable v at w[v * ws]); fd (stride fs) gets
+// (tau, tau u - q_h, -J_1 .. -J_Ns); fd may be q itself. T in closed form
+// (constant c_p), the primitive derivatives by the chain rule (rho_x = sum
+// q_{rho Y_i}, u_x = (q_{rho u} - u rho_x) / rho, Y_i,x = (q_{rho Y_i} - Y_i rho_x)
+// / rho, T_x from the derivative of rho E - (rho u) u / 2 = sum rho Y_i e_i(T)).
+// With X_i = Y_i / (W_i n), n = sum Y_j / W_j, the flux -rho D_i (Y_i / X_i) dX_i/dx
+// is -(mu / (Pr Le_i)) (Y_i,x - Y_i n_x / n), and the correction velocity makes
+// J_i = J_i* - Y_i sum_j J_j*. Transport: mu = mu_ref (T / T_mu)^mu_exp,
+// k = mu c_p / Pr, rho D_i = k / (c_p Le_i).
+// R is the arithmetic type of everything but T, which is formed in FP64 (the
+// internal energy cancels against the formation energies) unless T_known > 0
+// gives it; sp holds the species fields in FP64, spr in R.
+// A group of G consecutive lanes (G a power of two dividing 32) evaluates it:
+// the species loops are split over the lanes and the sums reduced by shuffles
+// within the group. Every lane of the warp must call it; a group without work
+// passes valid = false and writes nothing. Up to 4 G species.
+template <typename R, int G>
+__device__ inline void visc_flux_group(const double *sp, const R *spr, int ns, const Inst &I,
+                                       const double *w, int ws, const double *q, int qs,
+                                       double *fd, int fs, double T_known, bool valid) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & (G - 1);
+  auto red = [&](auto x) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o, G);
+    return x;
+  };
+  const double *sQW = sp + SP_QW * ns, *sCVW = sp + SP_CVW * ns;
+  const R *rIW = spr + SP_INVW * ns, *rQW = spr + SP_QW * ns, *rCVW = spr + SP_CVW * ns;
+  const R *rCPW = spr + SP_CPW * ns, *rIL = spr + SP_INVLE * ns;
+  R rho = R(0), cv = R(0), rho_x = R(0);
+  double rho_d = 0.0, qsum = 0.0, cv_d = 0.0;
+  const bool needT = !(T_known > 0.0);
+  for (int i = lane; i < ns; i += G) {
+    const double rd = w[(2 + i) * ws];
+    const R r = (R)rd;
+    rho += r;
+    cv = fma(r, rCVW[i], cv);
+    rho_x += (R)q[(2 + i) * qs];
+    if (needT) {
+      rho_d += rd;
+      qsum = fma(rd, sQW[i], qsum);
+      cv_d = fma(rd, sCVW[i], cv_d);
+    }
+  }
+  rho = red(rho);
+  cv = red(cv);
+  rho_x = red(rho_x);
+  double T_d = T_known;
+  if (needT) {
+    rho_d = red(rho_d);
+    qsum = red(qsum);
+    cv_d = red(cv_d);
+    T_d = (w[ws] - 0.5 * w[0] * (w[0] / rho_d) - qsum) / cv_d;
+  }
+  const R T = (R)T_d;
+  const R irho = R(1) / rho, m = (R)w[0], u = m * irho;
+  const R u_x = ((R)q[0] - u * rho_x) * irho;
+  R num = R(0), n = R(0), n_x = R(0), cpm = R(0);
+  for (int i = lane; i < ns; i += G) {
+    const R rx = (R)q[(2 + i) * qs], Y = (R)w[(2 + i) * ws] * irho;
+    const R Yx = (rx - Y * rho_x) * irho;
+    num -= rx * fma(rCVW[i], T, rQW[i]);
+    n = fma(Y, rIW[i], n);
+    n_x = fma(Yx, rIW[i], n_x);
+    cpm = fma(Y, rCPW[i], cpm);
+  }
+  num = red(num) + ((R)q[qs] - R(0.5) * ((R)q[0] * u + m * u_x));
+  n = red(n);
+  n_x = red(n_x);
+  cpm = red(cpm);
+  const R T_x = num / cv;
+  R mu;
+  if constexpr (std::is_same<R, float>::value)
+    mu = (float)I.mu_ref * expf((float)I.mu_exp * (logf(T) - (float)I.ln_T_mu));
+  else
+    mu = I.mu_ref * exp(I.mu_exp * (log(T) - I.ln_T_mu));
+  const R a = mu * (R)I.inv_prandtl, kc = a * cpm, nxn = n_x / n;
+  R Jsum = R(0);
+  R Js_own[4];  // this lane's species (G >= ns / 4)
+  int c = 0;
+  for (int i = lane; i < ns; i += G, ++c) {
+    const R Y = (R)w[(2 + i) * ws] * irho;
+    const R Yx = ((R)q[(2 + i) * qs] - Y * rho_x) * irho;
+    Js_own[c] = -a * rIL[i] * (Yx - Y * nxn);
+    Jsum += Js_own[c];
+  }
+  Jsum = red(Jsum);
+  R qh = R(0);
+  c = 0;
+  for (int i = lane; i < ns; i += G, ++c) {
+    const R J = Js_own[c] - (R)w[(2 + i) * ws] * irho * Jsum;
+    qh = fma(fma(rCPW[i], T, rQW[i]), J, qh);
+    if (valid) fd[(2 + i) * fs] = (double)(-J);
+  }
+  qh = red(qh) - kc * T_x;
+  if (valid && lane == 0) {
+    const R tau = R(4.0 / 3.0) * mu * u_x;
+    fd[0] = (double)tau;
+    fd[fs] = (double)(tau * u - qh);
+  }
 }
+
+// The diffusive flux at every Gauss point of a tile (over its nodal q), G lanes
+// per point; w, q [v][TQ], T [TQ] (the point temperatures).
+template <typename R, int G>
+__device__ inline void visc_points(const double *sp, const R *spr, int ns, const Inst &I,
+                                   const double *w, double *q, const double *T, int TQ,
+                                   int teq) {
+  const int ngr = blockDim.x / G, g = threadIdx.x / G;
+  for (int base = 0; base < teq; base += ngr) {
+    const int t = base + g;
+    const bool valid = t < teq;
+    const int tt = valid ? t : 0;
+    visc_flux_group<R, G>(sp, spr, ns, I, w + tt, TQ, q + tt, TQ, q + tt, TQ, T[tt], valid);
+  }
+}
+
+// The diffusive flux of both sides of every face level of a tile, G lanes per
+// (level, face, side): from the traces vt = (w_l, w_r, q_l, q_r) of the level,
+// f^d over q_l and q_r. Levels beyond the first only at delayed PE faces.
+template <typename R, int G>
+__device__ inline void visc_faces(const double *sp, const R *spr, int ns, const Inst &I,
+                                  double *sqt, const int *sk, int te, int NF, int O) {
+  const int nv = ns + 2, ngr = blockDim.x / G, g = threadIdx.x / G;
+  const int total = O * (te + 1) * 2;
+  for (int base = 0; base < total; base += ngr) {
+    int it = base + g;
+    bool valid = it < total;
+    if (!valid) it = 0;
+    const int side = it & 1, mf = it >> 1, m = mf / (te + 1), f = mf - m * (te + 1);
+    valid = valid && m < (sk[f] > 0 ? I.at_order : 1);
+    double *vt = sqt + ((size_t)m * NF + f) * 4 * nv;
+    visc_flux_group<R, G>(sp, spr, ns, I, vt + side * nv, 1, vt + (2 + side) * nv, 1,
+                          vt + (2 + side) * nv, 1, 0.0, valid);
+  }
+}
+
 
 // Stage s of one tile: elements [e0, e0 + te) of instance I at step level nstep.
 // With UNSYNC the PE faces of the tile take the delays pd->k observed by a PE
@@ -269,6 +324,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   double *sqw = reinterpret_cast<double *>(MIX ? (void *)(sdfT + 2 * TQ) : (void *)srxf);  // [v][TE+2][Q]
   double *sqn = sqw + (size_t)nv * (TE + 2) * Q;                           // [v][TQ]
   double *sqt = sqn + (size_t)nv * TQ;                                     // [O][NF][4][nv]
+  double *sTv = sqt + (size_t)O * NF * 4 * nv;                             // [TQ] T
   // viscous terms: compiled only into the viscous instances of the kernel (the
   // Euler kernels keep their register budget), run for viscous instances
   const bool visc = VISC && I.viscous;
@@ -394,8 +450,15 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       }
       su[t] = u;
       sPr[t] = T * Rm;
-      // the diffusive flux at the point, over its q
-      if (visc) visc_flux_dev<DG>(ssp, sspD, ns, I, wq, TQ, sqn + t, TQ, sqn + t, TQ, T);
+      if (visc) sTv[t] = T;
+    }
+  }
+  // the diffusive flux at every point, over its q, by groups of lanes
+  if constexpr (VISC) {
+    if (visc) {
+      __syncthreads();
+      if (ns <= 16) visc_points<DG, 4>(ssp, sspD, ns, I, snw, sqn, sTv, TQ, teq);
+      else visc_points<DG, 16>(ssp, sspD, ns, I, snw, sqn, sTv, TQ, teq);
     }
   }
   __syncthreads();
@@ -506,7 +569,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
           vt[2 * nv + v] = ring_load<UNSYNC>(ql + v);
           vt[3 * nv + v] = ring_load<UNSYNC>(qr + v);
         }
-        visc_face<DG>(ssp, sspD, ns, I, nv, vt, fl);
+        // f^d of both sides: in phase 4, subtracted in the AT sum of phase 5
       }
       continue;
     }
@@ -554,7 +617,6 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         }
     }
     num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
-    if (visc) visc_face<DG>(ssp, sspD, ns, I, nv, vt, fl);
   }
   __syncthreads();
 
@@ -567,15 +629,31 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       acc = fma(scoef[k], sq[(size_t)sterm[k] * TQ + t], acc);
     swd[(size_t)i * TQ + t] = acc;
   }
-  // 5. the AT sum over levels, m = 0..o-1 in order, in FP64
+  // the diffusive flux of both sides of every face level, by groups of lanes
+  if constexpr (VISC) {
+    if (visc) {
+      if (ns <= 16) visc_faces<DG, 4>(ssp, sspD, ns, I, sqt, sk, te, NF, O);
+      else visc_faces<DG, 16>(ssp, sspD, ns, I, sqt, sk, te, NF, O);
+    }
+    __syncthreads();
+  }
+  // 5. the AT sum over levels, m = 0..o-1 in order, in FP64, of the Riemann flux
+  // minus (viscous) the central mean of f^d
   for (int item = tid; item < (te + 1) * nv; item += nth) {
     const int f = item / nv, v = item - f * nv;
     const int k = sk[f];
-    double acc = (double)sflx[(size_t)f * nv + v];
+    auto level = [&](int m) {
+      double x = (double)sflx[((size_t)m * NF + f) * nv + v];
+      if (visc) {
+        const double *vt = sqt + ((size_t)m * NF + f) * 4 * nv;
+        x -= 0.5 * (vt[2 * nv + v] + vt[3 * nv + v]);
+      }
+      return x;
+    };
+    double acc = level(0);
     if (k > 0) {
       acc *= I.at[k][0];
-      for (int m = 1; m < I.at_order; ++m)
-        acc = fma(I.at[k][m], (double)sflx[((size_t)m * NF + f) * nv + v], acc);
+      for (int m = 1; m < I.at_order; ++m) acc = fma(I.at[k][m], level(m), acc);
     }
     sfh[(size_t)f * nv + v] = (DG)acc;
   }
