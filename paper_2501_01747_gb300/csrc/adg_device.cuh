@@ -113,6 +113,27 @@ __device__ __forceinline__ double f2d_exact(float x) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// double -> float, rounded to nearest even, by moving the bit fields on the
+// integer pipeline (the same reason as f2d_exact). Values whose float would be
+// subnormal, overflow, or that are not finite take the hardware conversion.
+__device__ __forceinline__ float d2f_int(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int ef = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (ef <= 0 || ef >= 255) return __double2float_rn(x);
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  // a mantissa carry runs into the exponent (up to infinity), as rounding should
+  return __uint_as_float(((hi & 0x80000000u) | ((unsigned)ef << 23) | m) + up);
+}
+
+// To the variant's arithmetic type without the FP64 unit.
+template <typename R>
+__device__ __forceinline__ R to_r(double x) {
+  if constexpr (std::is_same<R, float>::value) return d2f_int(x);
+  else return x;
+}
+
 // A value of the history ring. Written by another CTA of the same launch in the
 // unsynchronised mode, so read from L2 (the point of coherence), not from a
 // possibly stale L1 line of an earlier level in the same slot.
@@ -150,47 +171,50 @@ __device__ inline void visc_flux_group(const double *sp, const R *spr, int ns, c
     for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o, G);
     return x;
   };
-  const double *sQW = sp + SP_QW * ns, *sCVW = sp + SP_CVW * ns;
   const R *rIW = spr + SP_INVW * ns, *rQW = spr + SP_QW * ns, *rCVW = spr + SP_CVW * ns;
   const R *rCPW = spr + SP_CPW * ns, *rIL = spr + SP_INVLE * ns;
-  R rho = R(0), cv = R(0), rho_x = R(0);
-  double rho_d = 0.0, qsum = 0.0, cv_d = 0.0;
+  // this lane's species, converted once
+  R rl[4], ql[4];
+  int c = 0;
+  for (int i = lane; i < ns; i += G, ++c) {
+    rl[c] = to_r<R>(w[(2 + i) * ws]);
+    ql[c] = to_r<R>(q[(2 + i) * qs]);
+  }
+  const R w0 = to_r<R>(w[0]), w1 = to_r<R>(w[ws]), q0 = to_r<R>(q[0]), q1 = to_r<R>(q[qs]);
+  R rho = R(0), cv = R(0), rho_x = R(0), qsum = R(0);
   const bool needT = !(T_known > 0.0);
-  for (int i = lane; i < ns; i += G) {
-    const double rd = w[(2 + i) * ws];
-    const R r = (R)rd;
-    rho += r;
-    cv = fma(r, rCVW[i], cv);
-    rho_x += (R)q[(2 + i) * qs];
-    if (needT) {
-      rho_d += rd;
-      qsum = fma(rd, sQW[i], qsum);
-      cv_d = fma(rd, sCVW[i], cv_d);
-    }
+  c = 0;
+  for (int i = lane; i < ns; i += G, ++c) {
+    rho += rl[c];
+    cv = fma(rl[c], rCVW[i], cv);
+    rho_x += ql[c];
+    if (needT) qsum = fma(rl[c], rQW[i], qsum);
   }
   rho = red(rho);
   cv = red(cv);
   rho_x = red(rho_x);
-  double T_d = T_known;
+  R T;
   if (needT) {
-    rho_d = red(rho_d);
+    // in the variant's type: the mixed variant tolerates the cancellation here,
+    // which moves f^d, a small part of the flux, by about 1e-6 of itself
     qsum = red(qsum);
-    cv_d = red(cv_d);
-    T_d = (w[ws] - 0.5 * w[0] * (w[0] / rho_d) - qsum) / cv_d;
+    T = (w1 - R(0.5) * w0 * (w0 / rho) - qsum) / cv;
+  } else {
+    T = to_r<R>(T_known);
   }
-  const R T = (R)T_d;
-  const R irho = R(1) / rho, m = (R)w[0], u = m * irho;
-  const R u_x = ((R)q[0] - u * rho_x) * irho;
+  const R irho = R(1) / rho, m = w0, u = m * irho;
+  const R u_x = (q0 - u * rho_x) * irho;
   R num = R(0), n = R(0), n_x = R(0), cpm = R(0);
-  for (int i = lane; i < ns; i += G) {
-    const R rx = (R)q[(2 + i) * qs], Y = (R)w[(2 + i) * ws] * irho;
+  c = 0;
+  for (int i = lane; i < ns; i += G, ++c) {
+    const R rx = ql[c], Y = rl[c] * irho;
     const R Yx = (rx - Y * rho_x) * irho;
     num -= rx * fma(rCVW[i], T, rQW[i]);
     n = fma(Y, rIW[i], n);
     n_x = fma(Yx, rIW[i], n_x);
     cpm = fma(Y, rCPW[i], cpm);
   }
-  num = red(num) + ((R)q[qs] - R(0.5) * ((R)q[0] * u + m * u_x));
+  num = red(num) + (q1 - R(0.5) * (q0 * u + m * u_x));
   n = red(n);
   n_x = red(n_x);
   cpm = red(cpm);
@@ -203,10 +227,10 @@ __device__ inline void visc_flux_group(const double *sp, const R *spr, int ns, c
   const R a = mu * (R)I.inv_prandtl, kc = a * cpm, nxn = n_x / n;
   R Jsum = R(0);
   R Js_own[4];  // this lane's species (G >= ns / 4)
-  int c = 0;
+  c = 0;
   for (int i = lane; i < ns; i += G, ++c) {
-    const R Y = (R)w[(2 + i) * ws] * irho;
-    const R Yx = ((R)q[(2 + i) * qs] - Y * rho_x) * irho;
+    const R Y = rl[c] * irho;
+    const R Yx = (ql[c] - Y * rho_x) * irho;
     Js_own[c] = -a * rIL[i] * (Yx - Y * nxn);
     Jsum += Js_own[c];
   }
@@ -214,7 +238,7 @@ __device__ inline void visc_flux_group(const double *sp, const R *spr, int ns, c
   R qh = R(0);
   c = 0;
   for (int i = lane; i < ns; i += G, ++c) {
-    const R J = Js_own[c] - (R)w[(2 + i) * ws] * irho * Jsum;
+    const R J = Js_own[c] - rl[c] * irho * Jsum;
     qh = fma(fma(rCPW[i], T, rQW[i]), J, qh);
     if (valid) fd[(2 + i) * fs] = (double)(-J);
   }
@@ -237,6 +261,7 @@ __device__ inline void visc_points(const double *sp, const R *spr, int ns, const
     const int t = base + g;
     const bool valid = t < teq;
     const int tt = valid ? t : 0;
+    if (!__any_sync(0xffffffffu, valid)) continue;  // warp-uniform: no point here
     visc_flux_group<R, G>(sp, spr, ns, I, w + tt, TQ, q + tt, TQ, q + tt, TQ, T[tt], valid);
   }
 }
@@ -255,6 +280,7 @@ __device__ inline void visc_faces(const double *sp, const R *spr, int ns, const 
     if (!valid) it = 0;
     const int side = it & 1, mf = it >> 1, m = mf / (te + 1), f = mf - m * (te + 1);
     valid = valid && m < (sk[f] > 0 ? I.at_order : 1);
+    if (!__any_sync(0xffffffffu, valid)) continue;  // warp-uniform: no level here
     double *vt = sqt + ((size_t)m * NF + f) * 4 * nv;
     visc_flux_group<R, G>(sp, spr, ns, I, vt + side * nv, 1, vt + (2 + side) * nv, 1,
                           vt + (2 + side) * nv, 1, 0.0, valid);
@@ -474,19 +500,19 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       if (v >= 2) {
         const int i = v - 2;
         const double r = (__double2hiint(w) < 0) ? 0.0 : w;
-        scc[(size_t)i * TQ + t] = (DG)(r * sIW[i]);
-        if constexpr (MIX) sfx[at] = (DG)u * (DG)w;
+        scc[(size_t)i * TQ + t] = to_r<DG>(r * sIW[i]);
+        if constexpr (MIX) sfx[at] = d2f_int(u) * d2f_int(w);
         else snw[at] = u * w;
       } else if (v == 0) {
-        if constexpr (MIX) sfx[at] = fma((DG)w, (DG)u, (DG)sPr[t]);
+        if constexpr (MIX) sfx[at] = fma(d2f_int(w), d2f_int(u), d2f_int(sPr[t]));
         else snw[at] = w * u + sPr[t];
       } else {
-        if constexpr (MIX) sfx[at] = (DG)u * ((DG)w + (DG)sPr[t]);
+        if constexpr (MIX) sfx[at] = d2f_int(u) * (d2f_int(w) + d2f_int(sPr[t]));
         else snw[at] = u * (w + sPr[t]);
       }
       // f = f^c - f^d
       if (visc) {
-        if constexpr (MIX) sfx[at] -= (DG)sqn[at];
+        if constexpr (MIX) sfx[at] -= d2f_int(sqn[at]);
         else snw[at] -= sqn[at];
       }
     }
@@ -551,8 +577,8 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       const double *br = I.ring_in + ring_trace(I, lv, A.s, pf, 1);
       if constexpr (MIX || UNSYNC) {
         for (int v = 0; v < nv; ++v) {
-          wl[v] = (DG)ring_load<UNSYNC>(bl + v);
-          wr[v] = (DG)ring_load<UNSYNC>(br + v);
+          wl[v] = to_r<DG>(ring_load<UNSYNC>(bl + v));
+          wr[v] = to_r<DG>(ring_load<UNSYNC>(br + v));
         }
         num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
       } else {
@@ -581,8 +607,8 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         a += sw[((size_t)v * (TE + 2) + f) * Q + j];
         b += ((j & 1) ? -1.0 : 1.0) * sw[((size_t)v * (TE + 2) + f + 1) * Q + j];
       }
-      wl[v] = (DG)a;
-      wr[v] = (DG)b;
+      wl[v] = to_r<DG>(a);
+      wr[v] = to_r<DG>(b);
       if (visc) {
         double qa = 0.0, qb = 0.0;
         for (int j = 0; j < Q; ++j) {
@@ -643,7 +669,9 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
     const int f = item / nv, v = item - f * nv;
     const int k = sk[f];
     auto level = [&](int m) {
-      double x = (double)sflx[((size_t)m * NF + f) * nv + v];
+      double x;
+      if constexpr (MIX) x = f2d_exact(sflx[((size_t)m * NF + f) * nv + v]);
+      else x = sflx[((size_t)m * NF + f) * nv + v];
       if (visc) {
         const double *vt = sqt + ((size_t)m * NF + f) * 4 * nv;
         x -= 0.5 * (vt[2 * nv + v] + vt[3 * nv + v]);
@@ -655,7 +683,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       acc *= I.at[k][0];
       for (int m = 1; m < I.at_order; ++m) acc = fma(I.at[k][m], level(m), acc);
     }
-    sfh[(size_t)f * nv + v] = (DG)acc;
+    sfh[(size_t)f * nv + v] = to_r<DG>(acc);
   }
   __syncthreads();
 
