@@ -500,14 +500,14 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       if (v >= 2) {
         const int i = v - 2;
         const double r = (__double2hiint(w) < 0) ? 0.0 : w;
-        scc[(size_t)i * TQ + t] = to_r<DG>(r * sIW[i]);
-        if constexpr (MIX) sfx[at] = d2f_int(u) * d2f_int(w);
+        scc[(size_t)i * TQ + t] = (DG)(r * sIW[i]);
+        if constexpr (MIX) sfx[at] = (DG)u * (DG)w;
         else snw[at] = u * w;
       } else if (v == 0) {
-        if constexpr (MIX) sfx[at] = fma(d2f_int(w), d2f_int(u), d2f_int(sPr[t]));
+        if constexpr (MIX) sfx[at] = fma((DG)w, (DG)u, (DG)sPr[t]);
         else snw[at] = w * u + sPr[t];
       } else {
-        if constexpr (MIX) sfx[at] = d2f_int(u) * (d2f_int(w) + d2f_int(sPr[t]));
+        if constexpr (MIX) sfx[at] = (DG)u * ((DG)w + (DG)sPr[t]);
         else snw[at] = u * (w + sPr[t]);
       }
       // f = f^c - f^d
@@ -577,8 +577,8 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       const double *br = I.ring_in + ring_trace(I, lv, A.s, pf, 1);
       if constexpr (MIX || UNSYNC) {
         for (int v = 0; v < nv; ++v) {
-          wl[v] = to_r<DG>(ring_load<UNSYNC>(bl + v));
-          wr[v] = to_r<DG>(ring_load<UNSYNC>(br + v));
+          wl[v] = (DG)ring_load<UNSYNC>(bl + v);
+          wr[v] = (DG)ring_load<UNSYNC>(br + v);
         }
         num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
       } else {
@@ -607,8 +607,8 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         a += sw[((size_t)v * (TE + 2) + f) * Q + j];
         b += ((j & 1) ? -1.0 : 1.0) * sw[((size_t)v * (TE + 2) + f + 1) * Q + j];
       }
-      wl[v] = to_r<DG>(a);
-      wr[v] = to_r<DG>(b);
+      wl[v] = (DG)a;
+      wr[v] = (DG)b;
       if (visc) {
         double qa = 0.0, qb = 0.0;
         for (int j = 0; j < Q; ++j) {
@@ -669,9 +669,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
     const int f = item / nv, v = item - f * nv;
     const int k = sk[f];
     auto level = [&](int m) {
-      double x;
-      if constexpr (MIX) x = f2d_exact(sflx[((size_t)m * NF + f) * nv + v]);
-      else x = sflx[((size_t)m * NF + f) * nv + v];
+      double x = (double)sflx[((size_t)m * NF + f) * nv + v];
       if (visc) {
         const double *vt = sqt + ((size_t)m * NF + f) * 4 * nv;
         x -= 0.5 * (vt[2 * nv + v] + vt[3 * nv + v]);
@@ -683,7 +681,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       acc *= I.at[k][0];
       for (int m = 1; m < I.at_order; ++m) acc = fma(I.at[k][m], level(m), acc);
     }
-    sfh[(size_t)f * nv + v] = to_r<DG>(acc);
+    sfh[(size_t)f * nv + v] = (DG)acc;
   }
   __syncthreads();
 
