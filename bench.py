@@ -527,6 +527,7 @@ def main(argv=None):
         "clocks": head["clocks"],
         "e2e": head["e2e"],
         "gpu_launches": int(head["kn"][0] + head["kn"][1] + head["kn"][2]),
+        "value_scalar_dofs": head["value"] * (mech.ns + 2),  # x N_var conserved variables
         "wall_s": head["wall"],
     }
     if other is not None:

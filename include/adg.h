@@ -179,6 +179,16 @@ int adg_get_flags(adg_ctx *ctx, int instance, uint8_t *last_host, int32_t *count
 /* Temperature at the Gauss points of the current state, [n_elem][p+1]. */
 int adg_get_temperature(adg_ctx *ctx, int instance, double *T_host);
 
+/* One auxiliary field of an instance's current state (synchronous):
+ * ADG_AUX_TEMPERATURE and ADG_AUX_PRESSURE at every Gauss point (double
+ * [n_elem][p+1]; T from e as in Sec. 2, P = rho R_u T sum_i Y_i/W_i), or
+ * ADG_AUX_FLAGS, the troubled-cell flags of the last step's stages (uint8
+ * [stages][n_elem], as adg_get_flags). ADG_ERR_ARG for another `what`. */
+#define ADG_AUX_TEMPERATURE 0
+#define ADG_AUX_PRESSURE 1
+#define ADG_AUX_FLAGS 2
+int adg_get_aux(adg_ctx *ctx, int instance, int what, void *out_host);
+
 int64_t adg_steps_done(const adg_ctx *ctx, int instance);
 
 /* Delays the context draws (Sec. 4.1 CAA: k = n mod (max_delay+1); Sec. 4.2 SAA:

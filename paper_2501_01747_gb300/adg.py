@@ -106,7 +106,7 @@ EXPORTS = ["adg_workspace_bytes", "adg_create", "adg_destroy", "adg_set_primitiv
            "adg_write_state", "adg_read_state", "adg_enable_kernel_timing",
            "adg_kernel_times", "adg_step_noalloc", "adg_autotune", "adg_get_tuning",
            "adg_set_tuning", "adg_step_unsync", "adg_unsync_delays",
-           "adg_set_unsync_wait", "adg_set_unsync_imbalance"]
+           "adg_set_unsync_wait", "adg_set_unsync_imbalance", "adg_get_aux"]
 
 
 def lib(path: str | None = None):
@@ -133,6 +133,7 @@ def lib(path: str | None = None):
                              C.POINTER(C.c_int64), C.POINTER(C.c_int)]
     L.adg_get_flags.argtypes = [vp, C.c_int, C.POINTER(C.c_uint8), C.POINTER(C.c_int32)]
     L.adg_get_temperature.argtypes = [vp, C.c_int, d]
+    L.adg_get_aux.argtypes = [vp, C.c_int, C.c_int, vp]
     L.adg_steps_done.argtypes = [vp, C.c_int]
     L.adg_steps_done.restype = C.c_int64
     L.adg_delay_table.argtypes = [C.POINTER(Config_), C.c_int64, C.c_int, C.POINTER(C.c_uint8)]
@@ -423,6 +424,13 @@ class ADG:
         _check(self.L.adg_unsync_delays(self.h, h.ctypes.data_as(C.POINTER(C.c_uint64))),
                "adg_unsync_delays")
         return h.reshape(2, MAX_DELAY + 1)
+
+    def pressure(self, k=0):
+        """Pressure at every Gauss point of instance k, [n_elem, p+1]."""
+        wl = self.workloads[self._k(k)]
+        P = np.zeros((wl.n_elem, wl.p + 1))
+        _check(self.L.adg_get_aux(self.h, k, 1, P.ctypes.data_as(C.c_void_p)), "adg_get_aux")
+        return P
 
     def launches_per_step(self):
         return int(self.L.adg_launches_per_step(self.h))

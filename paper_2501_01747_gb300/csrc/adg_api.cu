@@ -1207,4 +1207,16 @@ int adg_get_temperature(adg_ctx *ctx, int k, double *T) {
   return ADG_OK;
 }
 
+int adg_get_aux(adg_ctx *ctx, int k, int what, void *out) {
+  if (!inst_ok(ctx, k) || !out) return ADG_ERR_ARG;
+  if (what == ADG_AUX_FLAGS) return adg_get_flags(ctx, k, (uint8_t *)out, nullptr);
+  if (what != ADG_AUX_TEMPERATURE && what != ADG_AUX_PRESSURE) return ADG_ERR_ARG;
+  InstHost &h = ctx->inst[k];
+  CK(cudaStreamSynchronize(ctx->last_stream));
+  CK(launch_temperature(ctx->mech, h.d, h.d.wn, h.prim, 0, what == ADG_AUX_PRESSURE ? 1 : 0));
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(out, h.prim, sizeof(double) * h.d.n_elem * (h.d.p + 1), cudaMemcpyDeviceToHost));
+  return ADG_OK;
+}
+
 }  // extern "C"

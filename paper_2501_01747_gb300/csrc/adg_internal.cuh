@@ -381,6 +381,6 @@ cudaError_t launch_advance_by(int64_t *step, int64_t n, cudaStream_t st);
 cudaError_t launch_project(const Mech &M, const Inst &I, const double *prim, double *w,
                            cudaStream_t st);
 cudaError_t launch_temperature(const Mech &M, const Inst &I, const double *w, double *T,
-                               cudaStream_t st);
+                               cudaStream_t st, int what = 0);
 
 }  // namespace adg

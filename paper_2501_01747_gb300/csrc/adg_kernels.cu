@@ -37,8 +37,10 @@ __global__ void project_kernel(Mech M, Inst I, const double *prim, double *w) {
   }
 }
 
+// Temperature (what = 0) or pressure (what = 1, P = rho R_u T sum Y_i / W_i) at
+// every Gauss point, [n_elem][p+1].
 template <int Q>
-__global__ void temperature_kernel(Mech M, Inst I, const double *w, double *T) {
+__global__ void temperature_kernel(Mech M, Inst I, const double *w, double *T, int what) {
   const Basis &B = c_basis[Q - 2];
   const int N = I.n_elem, nv = I.nv;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -50,7 +52,14 @@ __global__ void temperature_kernel(Mech M, Inst I, const double *w, double *T) {
     for (int j = 0; j < Q; ++j) acc += w[((size_t)v * N + e) * Q + j] * B.P[q][j];
     wq[v] = acc;
   }
-  T[t] = thermo_of(M.sp, M.ns, wq, 1).T;
+  const double Tt = thermo_of(M.sp, M.ns, wq, 1).T;
+  if (what == 1) {
+    double Rm = 0.0;
+    for (int i = 0; i < M.ns; ++i) Rm = fma(wq[2 + i], M.sp[SP_RW * M.ns + i], Rm);
+    T[t] = Tt * Rm;
+  } else {
+    T[t] = Tt;
+  }
 }
 
 // Central value of variable v of the stage input at face g (between elements
@@ -273,14 +282,14 @@ cudaError_t launch_project(const Mech &M, const Inst &I, const double *prim, dou
 }
 
 cudaError_t launch_temperature(const Mech &M, const Inst &I, const double *w, double *T,
-                               cudaStream_t st) {
+                               cudaStream_t st, int what) {
   int n = I.n_elem * (I.p + 1);
   int nblk = (n + 127) / 128;
   switch (I.p + 1) {
-    case 2: temperature_kernel<2><<<nblk, 128, 0, st>>>(M, I, w, T); break;
-    case 3: temperature_kernel<3><<<nblk, 128, 0, st>>>(M, I, w, T); break;
-    case 4: temperature_kernel<4><<<nblk, 128, 0, st>>>(M, I, w, T); break;
-    case 5: temperature_kernel<5><<<nblk, 128, 0, st>>>(M, I, w, T); break;
+    case 2: temperature_kernel<2><<<nblk, 128, 0, st>>>(M, I, w, T, what); break;
+    case 3: temperature_kernel<3><<<nblk, 128, 0, st>>>(M, I, w, T, what); break;
+    case 4: temperature_kernel<4><<<nblk, 128, 0, st>>>(M, I, w, T, what); break;
+    case 5: temperature_kernel<5><<<nblk, 128, 0, st>>>(M, I, w, T, what); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
