@@ -449,11 +449,109 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
     }
   }
   __syncthreads();
+  // The face fluxes of the tile (local face f between local elements f and f+1),
+  // one (level, face) per item: the plain flux, or one delayed level of the AT
+  // flux (Eq. 7) with both sides at the common level n-k-m. They need only the
+  // tile of phase 1 and run on the threads that the thermodynamics of phase 2b
+  // leaves idle (they were the critical path of the chemistry phase).
+  const int n_face = O * (te + 1);
+  auto face_item = [&](const int item) {
+    const int m = item / (te + 1), f = item - m * (te + 1);
+    const int g = e0 + f;  // global face index
+    const int pf = (g < N) ? I.pf_of_left[g] : I.pf_of_right[N - 1];
+    int k = 0;
+    if (pf >= 0) {
+      if constexpr (UNSYNC) k = pd->k[g == pd->first ? 0 : 1];
+      else k = effective_delay(I, nstep, pf);
+    }
+    if (m == 0) sk[f] = k;
+    DG *fl = sflx + ((size_t)m * NF + f) * nv;
+    DG *wl = str + ((size_t)m * NF + f) * 2 * nv, *wr = wl + nv;
+    if (k > 0 || (UNSYNC && pf >= 0)) {
+      if (m >= (k > 0 ? I.at_order : 1)) return;
+      const int64_t lv = nstep - k - m;
+      const double *bl = I.ring_in + ring_trace(I, lv, A.s, pf, 0);
+      const double *br = I.ring_in + ring_trace(I, lv, A.s, pf, 1);
+      if constexpr (MIX || UNSYNC) {
+        for (int v = 0; v < nv; ++v) {
+          wl[v] = (DG)ring_load<UNSYNC>(bl + v);
+          wr[v] = (DG)ring_load<UNSYNC>(br + v);
+        }
+        num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
+      } else {
+        num_flux_t<double>(ssp, ns, I.flux, bl, br, fl);
+      }
+      if (visc) {
+        // minus the central mean of f^d from the traces of w and q at this level
+        double *vt = sqt + ((size_t)m * NF + f) * 4 * nv;  // w_l, w_r, q_l, q_r
+        const double *ql = I.ring_q + ring_trace(I, lv, A.s, pf, 0);
+        const double *qr = I.ring_q + ring_trace(I, lv, A.s, pf, 1);
+        for (int v = 0; v < nv; ++v) {
+          vt[v] = ring_load<UNSYNC>(bl + v);
+          vt[nv + v] = ring_load<UNSYNC>(br + v);
+          vt[2 * nv + v] = ring_load<UNSYNC>(ql + v);
+          vt[3 * nv + v] = ring_load<UNSYNC>(qr + v);
+        }
+        // f^d of both sides: in phase 4, subtracted in the AT sum of phase 5
+      }
+      return;
+    }
+    if (m > 0) return;
+    double *vt = sqt + (size_t)f * 4 * nv;
+    for (int v = 0; v < nv; ++v) {
+      double a = 0.0, b = 0.0;
+      for (int j = 0; j < Q; ++j) {
+        a += sw[((size_t)v * (TE + 2) + f) * Q + j];
+        b += ((j & 1) ? -1.0 : 1.0) * sw[((size_t)v * (TE + 2) + f + 1) * Q + j];
+      }
+      wl[v] = (DG)a;
+      wr[v] = (DG)b;
+      if (visc) {
+        double qa = 0.0, qb = 0.0;
+        for (int j = 0; j < Q; ++j) {
+          qa += sqw[((size_t)v * (TE + 2) + f) * Q + j];
+          qb += ((j & 1) ? -1.0 : 1.0) * sqw[((size_t)v * (TE + 2) + f + 1) * Q + j];
+        }
+        vt[v] = a;
+        vt[nv + v] = b;
+        vt[2 * nv + v] = qa;
+        vt[3 * nv + v] = qb;
+      }
+    }
+    // physical boundary: the ghost is the mirror image at a reflecting wall (rho u
+    // negated; of q, d(rho u)/dx kept and the others negated) or a copy (outflow)
+    if (!periodic && g == 0) {
+      const bool refl = I.bc_left == ADG_BC_REFLECT;
+      for (int v = 0; v < nv; ++v) wl[v] = wr[v];
+      if (refl) wl[0] = -wr[0];
+      if (visc)
+        for (int v = 0; v < nv; ++v) {
+          vt[v] = (refl && v == 0) ? -vt[nv] : vt[nv + v];
+          vt[2 * nv + v] = (refl && v > 0) ? -vt[3 * nv + v] : vt[3 * nv + v];
+        }
+    } else if (!periodic && g == N) {
+      const bool refl = I.bc_right == ADG_BC_REFLECT;
+      for (int v = 0; v < nv; ++v) wr[v] = wl[v];
+      if (refl) wr[0] = -wl[0];
+      if (visc)
+        for (int v = 0; v < nv; ++v) {
+          vt[nv + v] = (refl && v == 0) ? -vt[0] : vt[v];
+          vt[3 * nv + v] = (refl && v > 0) ? -vt[2 * nv + v] : vt[2 * nv + v];
+        }
+    }
+    num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
+  };
+
   // 2b. temperature from the internal energy (the closed form of the Newton step
-  // for constant c_p), ln T, 1/T, velocity and pressure, in FP64
+  // for constant c_p), ln T, 1/T, velocity and pressure, in FP64; the face items
   {
     const double *sQW = ssp + SP_QW * ns, *sCVW = ssp + SP_CVW * ns, *sRW = ssp + SP_RW * ns;
-    for (int t = tid; t < teq; t += nth) {
+    for (int it = tid; it < teq + n_face; it += nth) {
+      if (it >= teq) {
+        face_item(it - teq);
+        continue;
+      }
+      const int t = it;
       const double *wq = snw + t;
       double rho = 0.0, qsum = 0.0, cv = 0.0, Rm = 0.0;
       for (int i = 0; i < ns; ++i) {
@@ -519,130 +617,39 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   }
   __syncthreads();
 
-  // 3. the face fluxes of the tile (local face f between local elements f and
-  // f+1), one (level, face) per item: the plain flux, or one delayed level of
-  // the AT flux (Eq. 7) with both sides at the common level n-k-m; then the
-  // chemistry, one (reaction, point) per item: the reversible rate of progress
-  // from the Arrhenius and the equilibrium exponentials (arguments in FP64).
-  // The face items, the longest, come first so that they overlap the chemistry.
-  const int n_face = O * (te + 1);
-  for (int item = tid; item < n_face + nr * teq; item += nth) {
-    if (item >= n_face) {
-      const int j = (item - n_face) / teq, t = (item - n_face) - j * teq;
-      const Rxn &Rx = srx[j];
-      DG fwd, rev;
-      if constexpr (MIX) {
-        // arguments in df32 and the FP32-pipe exp: no FP64 instruction and no
-        // precision conversion per item
-        const DF lnT = sdfT[2 * t], invT = sdfT[2 * t + 1], *c = srxf + 6 * j;
-        fwd = exp_df(df_fma(c[2], invT, df_fma(c[1], lnT, c[0])), stab->tf);
-        rev = exp_df(df_fma(c[5], invT, df_fma(c[4], lnT, c[3])), stab->tf);
-      } else {
-        const double lnT = slnT[t], invT = sinvT[t];
-        fwd = iexp(fma(Rx.mEaR, invT, fma(Rx.b, lnT, Rx.lnA)), *stab);
-        rev = iexp(fma(Rx.kr2, invT, fma(Rx.kr1, lnT, Rx.kr0)), *stab);
-      }
+  // 3. the chemistry, one (reaction, point) per item: the reversible rate of
+  // progress from the Arrhenius and the equilibrium exponentials (the face fluxes
+  // ran in phase 2b).
+  for (int item = tid; item < nr * teq; item += nth) {
+    const int j = item / teq, t = item - j * teq;
+    const Rxn &Rx = srx[j];
+    DG fwd, rev;
+    if constexpr (MIX) {
+      // arguments in df32 and the FP32-pipe exp: no FP64 instruction and no
+      // precision conversion per item
+      const DF lnT = sdfT[2 * t], invT = sdfT[2 * t + 1], *c = srxf + 6 * j;
+      fwd = exp_df(df_fma(c[2], invT, df_fma(c[1], lnT, c[0])), stab->tf);
+      rev = exp_df(df_fma(c[5], invT, df_fma(c[4], lnT, c[3])), stab->tf);
+    } else {
+      const double lnT = slnT[t], invT = sinvT[t];
+      fwd = iexp(fma(Rx.mEaR, invT, fma(Rx.b, lnT, Rx.lnA)), *stab);
+      rev = iexp(fma(Rx.kr2, invT, fma(Rx.kr1, lnT, Rx.kr0)), *stab);
+    }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (Rx.rn[k] == 0) break;
-        DG cc = scc[(size_t)Rx.rs[k] * TQ + t];
-        fwd *= cc;
-        if (Rx.rn[k] > 1) fwd *= cc;
-      }
+    for (int k = 0; k < 4; ++k) {
+      if (Rx.rn[k] == 0) break;
+      DG cc = scc[(size_t)Rx.rs[k] * TQ + t];
+      fwd *= cc;
+      if (Rx.rn[k] > 1) fwd *= cc;
+    }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (Rx.pn[k] == 0) break;
-        DG cc = scc[(size_t)Rx.ps[k] * TQ + t];
-        rev *= cc;
-        if (Rx.pn[k] > 1) rev *= cc;
-      }
-      sq[(size_t)j * TQ + t] = fwd - rev;
-      continue;
+    for (int k = 0; k < 4; ++k) {
+      if (Rx.pn[k] == 0) break;
+      DG cc = scc[(size_t)Rx.ps[k] * TQ + t];
+      rev *= cc;
+      if (Rx.pn[k] > 1) rev *= cc;
     }
-    const int m = item / (te + 1), f = item - m * (te + 1);
-    const int g = e0 + f;  // global face index
-    const int pf = (g < N) ? I.pf_of_left[g] : I.pf_of_right[N - 1];
-    int k = 0;
-    if (pf >= 0) {
-      if constexpr (UNSYNC) k = pd->k[g == pd->first ? 0 : 1];
-      else k = effective_delay(I, nstep, pf);
-    }
-    if (m == 0) sk[f] = k;
-    DG *fl = sflx + ((size_t)m * NF + f) * nv;
-    DG *wl = str + ((size_t)m * NF + f) * 2 * nv, *wr = wl + nv;
-    if (k > 0 || (UNSYNC && pf >= 0)) {
-      if (m >= (k > 0 ? I.at_order : 1)) continue;
-      const int64_t lv = nstep - k - m;
-      const double *bl = I.ring_in + ring_trace(I, lv, A.s, pf, 0);
-      const double *br = I.ring_in + ring_trace(I, lv, A.s, pf, 1);
-      if constexpr (MIX || UNSYNC) {
-        for (int v = 0; v < nv; ++v) {
-          wl[v] = (DG)ring_load<UNSYNC>(bl + v);
-          wr[v] = (DG)ring_load<UNSYNC>(br + v);
-        }
-        num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
-      } else {
-        num_flux_t<double>(ssp, ns, I.flux, bl, br, fl);
-      }
-      if (visc) {
-        // minus the central mean of f^d from the traces of w and q at this level
-        double *vt = sqt + ((size_t)m * NF + f) * 4 * nv;  // w_l, w_r, q_l, q_r
-        const double *ql = I.ring_q + ring_trace(I, lv, A.s, pf, 0);
-        const double *qr = I.ring_q + ring_trace(I, lv, A.s, pf, 1);
-        for (int v = 0; v < nv; ++v) {
-          vt[v] = ring_load<UNSYNC>(bl + v);
-          vt[nv + v] = ring_load<UNSYNC>(br + v);
-          vt[2 * nv + v] = ring_load<UNSYNC>(ql + v);
-          vt[3 * nv + v] = ring_load<UNSYNC>(qr + v);
-        }
-        // f^d of both sides: in phase 4, subtracted in the AT sum of phase 5
-      }
-      continue;
-    }
-    if (m > 0) continue;
-    double *vt = sqt + (size_t)f * 4 * nv;
-    for (int v = 0; v < nv; ++v) {
-      double a = 0.0, b = 0.0;
-      for (int j = 0; j < Q; ++j) {
-        a += sw[((size_t)v * (TE + 2) + f) * Q + j];
-        b += ((j & 1) ? -1.0 : 1.0) * sw[((size_t)v * (TE + 2) + f + 1) * Q + j];
-      }
-      wl[v] = (DG)a;
-      wr[v] = (DG)b;
-      if (visc) {
-        double qa = 0.0, qb = 0.0;
-        for (int j = 0; j < Q; ++j) {
-          qa += sqw[((size_t)v * (TE + 2) + f) * Q + j];
-          qb += ((j & 1) ? -1.0 : 1.0) * sqw[((size_t)v * (TE + 2) + f + 1) * Q + j];
-        }
-        vt[v] = a;
-        vt[nv + v] = b;
-        vt[2 * nv + v] = qa;
-        vt[3 * nv + v] = qb;
-      }
-    }
-    // physical boundary: the ghost is the mirror image at a reflecting wall (rho u
-    // negated; of q, d(rho u)/dx kept and the others negated) or a copy (outflow)
-    if (!periodic && g == 0) {
-      const bool refl = I.bc_left == ADG_BC_REFLECT;
-      for (int v = 0; v < nv; ++v) wl[v] = wr[v];
-      if (refl) wl[0] = -wr[0];
-      if (visc)
-        for (int v = 0; v < nv; ++v) {
-          vt[v] = (refl && v == 0) ? -vt[nv] : vt[nv + v];
-          vt[2 * nv + v] = (refl && v > 0) ? -vt[3 * nv + v] : vt[3 * nv + v];
-        }
-    } else if (!periodic && g == N) {
-      const bool refl = I.bc_right == ADG_BC_REFLECT;
-      for (int v = 0; v < nv; ++v) wr[v] = wl[v];
-      if (refl) wr[0] = -wl[0];
-      if (visc)
-        for (int v = 0; v < nv; ++v) {
-          vt[nv + v] = (refl && v == 0) ? -vt[0] : vt[v];
-          vt[3 * nv + v] = (refl && v > 0) ? -vt[2 * nv + v] : vt[2 * nv + v];
-        }
-    }
-    num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
+    sq[(size_t)j * TQ + t] = fwd - rev;
   }
   __syncthreads();
 
