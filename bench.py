@@ -590,7 +590,7 @@ STAGE_TRAFFIC = {
     ("ignition-9sp-4096x4", "v11", "fp64"): 2.05312e6,
 }
 
-KERNEL_REV = "v11"
+KERNEL_REV = "v12"
 
 if __name__ == "__main__":
     sys.exit(main())
