@@ -586,8 +586,8 @@ def main(argv=None):
 # DRAM bytes (read + write) per stage-kernel launch from ncu, per (workload,
 # kernel revision, precision); the summaries are under profiles/.
 STAGE_TRAFFIC = {
-    ("ignition-9sp-4096x4", "v11", "mixed"): 2.025472e6,
-    ("ignition-9sp-4096x4", "v11", "fp64"): 2.05312e6,
+    ("ignition-9sp-4096x4", "v12", "mixed"): 2.03392e6,
+    ("ignition-9sp-4096x4", "v12", "fp64"): 2.063104e6,
 }
 
 KERNEL_REV = "v12"
