@@ -1382,6 +1382,12 @@ static cudaError_t launch_limiter_qge(const Mech &M, const LimArgs &A, int nv, i
 template <int Q, bool MIX>
 static cudaError_t launch_limiter_q(const Mech &M, const LimArgs &A, int nv, int n_blocks,
                                     cudaStream_t st) {
+  if constexpr (MIX) {
+    if (A.EPB == 8) {
+      if (nv <= 16) return launch_limiter_qge<Q, 16, MIX, 8>(M, A, nv, n_blocks, st);
+      return launch_limiter_qge<Q, 32, MIX, 8>(M, A, nv, n_blocks, st);
+    }
+  }
   if (A.EPB == 16) {
     if (nv <= 16) return launch_limiter_qge<Q, 16, MIX, 16>(M, A, nv, n_blocks, st);
     return launch_limiter_qge<Q, 32, MIX, 16>(M, A, nv, n_blocks, st);
@@ -1412,6 +1418,16 @@ static cudaError_t prepare_variant() {
 #define ADG_SET(...) \
   if (e == cudaSuccess) \
   e = cudaFuncSetAttribute(__VA_ARGS__, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+  if constexpr (MIX) {
+    ADG_SET(limiter_kernel<2, 16, MIX, 8>);
+    ADG_SET(limiter_kernel<3, 16, MIX, 8>);
+    ADG_SET(limiter_kernel<4, 16, MIX, 8>);
+    ADG_SET(limiter_kernel<5, 16, MIX, 8>);
+    ADG_SET(limiter_kernel<2, 32, MIX, 8>);
+    ADG_SET(limiter_kernel<3, 32, MIX, 8>);
+    ADG_SET(limiter_kernel<4, 32, MIX, 8>);
+    ADG_SET(limiter_kernel<5, 32, MIX, 8>);
+  }
   ADG_SET(limiter_kernel<2, 16, MIX, 16>);
   ADG_SET(limiter_kernel<3, 16, MIX, 16>);
   ADG_SET(limiter_kernel<4, 16, MIX, 16>);

@@ -6,13 +6,15 @@ namespace adg {
 
 cudaError_t launch_unsync_mixed(const Mech &M, const UnsyncArgs &U, int Q, int nv,
                                 cudaStream_t st) {
+  if (U.EPB == 8) return unsync_launch_variant<true, 8>(M, U, Q, nv, st);
   if (U.EPB == 16) return unsync_launch_variant<true, 16>(M, U, Q, nv, st);
   if (U.EPB == LIM_EPB_MAX) return unsync_launch_variant<true, LIM_EPB_MAX>(M, U, Q, nv, st);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t prepare_unsync_mixed() {
-  cudaError_t e = unsync_prepare_variant<true, 16>();
+  cudaError_t e = unsync_prepare_variant<true, 8>();
+  if (e == cudaSuccess) e = unsync_prepare_variant<true, 16>();
   if (e == cudaSuccess) e = unsync_prepare_variant<true, LIM_EPB_MAX>();
   return e;
 }
