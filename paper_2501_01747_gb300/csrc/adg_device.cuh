@@ -691,6 +691,10 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
     sfh[(size_t)f * nv + v] = (DG)acc;
   }
   __syncthreads();
+  // The successor (the limiter) is released only now: released at entry, its
+  // CTAs, resident while they wait, piled onto the few SMs with room beside
+  // two stage CTAs and then ran their FP64 work there, several to an SM.
+  if constexpr (!UNSYNC) pdl_trigger();
 
   // 6. assembly of Eq. (5) (in the variant's arithmetic) and the SSP-RK3
   // combination (FP64); history ring writes
@@ -777,7 +781,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
 
 template <int Q, bool MIX, bool VISC>
 __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
-  pdl_enter();
+  pdl_wait();
   __shared__ Inst sI;
   const int2 tile = A.tiles[blockIdx.x];
   load_inst(sI, A.insts + tile.x);

@@ -101,12 +101,18 @@ struct Inst {
 
 // Programmatic dependent launch for the kernels of a step: each is launched so
 // that it may be scheduled while its predecessor drains, waits at entry until
-// the predecessor grid has completed and its writes are visible, and then lets
-// its own successor be scheduled. Without the launch attribute both
-// instructions are no-ops.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
+// the predecessor grid has completed and its writes are visible, and lets its
+// own successor be scheduled once every one of its CTAs has passed the
+// trigger. Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// Wait, then release the successor at once: for kernels whose successor's
+// waiting CTAs cannot crowd them out of an SM.
+__device__ __forceinline__ void pdl_enter() {
+  pdl_wait();
+  pdl_trigger();
 }
 
 template <typename... KArgs, typename... Args>
