@@ -1022,7 +1022,13 @@ template <int Q, int G, bool MIX, int EPB, bool UNSYNC>
 __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, const Inst &I,
                                              const int e0, const int te, const int64_t nstep,
                                              const PeDelays *pd) {
-  constexpr int LIM_L = LIM_THREADS / EPB;  // lanes per element in the indicator
+  // lanes per element in the indicator: every thread in the mixed variant; in
+  // FP64 two warps, since a warp instruction costs the FP64 pipe the same with
+  // one lane per element or four: 4 lanes for CTAs of 16 elements (groups too
+  // small for two CTAs of 32 per SM, where the element's serial chain bounds
+  // the time), 2 for CTAs of 32 (FP64 throughput bounds it)
+  constexpr int LIM_L = MIX ? LIM_THREADS / EPB : (EPB == LIM_EPB_MAX ? 2 : 4);
+  static_assert((EPB * LIM_L) % 32 == 0 && EPB * LIM_L <= LIM_THREADS, "indicator warps");
   using DG = dg_t<MIX>;
   extern __shared__ __align__(16) double lsm_raw[];
   DG *lsm = reinterpret_cast<DG *>(lsm_raw);
@@ -1092,7 +1098,7 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
           (DG)neighbour_mode<UNSYNC>(I, I.wpre, A.s, nstep, nb, v, 0, Q);
   }
   __syncthreads();
-  {
+  if (threadIdx.x < EPB * LIM_L) {
     // every lane runs the indicator (shuffles); groups past the last element
     // work on the first element and write nothing
     const int le = threadIdx.x / LIM_L;

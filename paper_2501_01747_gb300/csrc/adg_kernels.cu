@@ -245,10 +245,9 @@ size_t stage_smem(const Mech &M, int TE, int Q, int O, bool mixed, bool visc) {
 
 int limiter_elems_per_block(int64_t n_elem_group, bool mixed) {
   // fewer elements per CTA (more lanes each) while 32 would give fewer than two
-  // CTAs per SM: 16 (8 lanes), or 8 (16 lanes) while 16 would too; in the mixed
-  // variant only: in FP64 the lanes of an element repeat its FP64 divisions and
-  // square root, which costs more than the latency saved
-  if (!mixed) return LIM_EPB_MAX;
+  // CTAs per SM: 16 (8 lanes), or 8 (16 lanes) while 16 would too; in FP64 16
+  // (4 lanes) or 32 (2 lanes), as the limiter body sets its indicator lanes
+  if (!mixed) return n_elem_group < (int64_t)2 * 152 * LIM_EPB_MAX ? 16 : LIM_EPB_MAX;
   if (n_elem_group < (int64_t)2 * 152 * 16) return 8;
   return n_elem_group < (int64_t)2 * 152 * LIM_EPB_MAX ? 16 : LIM_EPB_MAX;
 }

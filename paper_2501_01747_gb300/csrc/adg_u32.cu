@@ -1,5 +1,5 @@
-// The unsynchronised mode, mixed-precision variant (the limiter's CTAs hold 16
-// or 32 elements, as the synchronous launches of the same group).
+// The unsynchronised mode, mixed-precision variant (the limiter's CTAs hold 8,
+// 16 or 32 elements, as the synchronous launches of the same group).
 #include "adg_unsync.cuh"
 
 namespace adg {
