@@ -430,8 +430,23 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   }
   __syncthreads();
 
-  // 2a. conserved state at the Gauss points, one (variable, point) per item
-  for (int item = tid; item < nv * teq; item += nth) {
+  // 2a. conserved state at the Gauss points, one (variable, point) per item;
+  // then (inviscid) the two sides' traces of every face of the tile at level 0,
+  // one (side, variable, face) per item: w(+1) = sum_j w_j of the left element,
+  // w(-1) = sum_j (-1)^j w_j of the right one (a delayed face's item in phase 2b
+  // overwrites them with the history's)
+  const int n_trace = visc ? 0 : 2 * nv * (te + 1);
+  for (int item = tid; item < nv * teq + n_trace; item += nth) {
+    if (item >= nv * teq) {
+      const int r = item - nv * teq, side = r & 1, vf = r >> 1;
+      const int v = vf / (te + 1), f = vf - v * (te + 1);
+      const double *wi = sw + ((size_t)v * (TE + 2) + f + side) * Q;
+      double a = 0.0;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) a += (side && (j & 1)) ? -wi[j] : wi[j];
+      str[(size_t)f * 2 * nv + side * nv + v] = (DG)a;
+      continue;
+    }
     int v = item / teq, t = item - v * teq;
     int e = t / Q, q = t - e * Q;
     const double *wi = sw + ((size_t)v * (TE + 2) + e + 1) * Q;
@@ -440,6 +455,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
 #pragma unroll
     for (int j = 0; j < Q; ++j) acc += wi[j] * Pq[j];
     snw[(size_t)v * TQ + t] = acc;
+    if constexpr (MIX) sfx[(size_t)v * TQ + t] = (DG)acc;  // converted once, for phase 2c
     if (visc) {
       const double *qi = sqw + ((size_t)v * (TE + 2) + e + 1) * Q;
       double aq = 0.0;
@@ -498,15 +514,16 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
     }
     if (m > 0) return;
     double *vt = sqt + (size_t)f * 4 * nv;
-    for (int v = 0; v < nv; ++v) {
-      double a = 0.0, b = 0.0;
-      for (int j = 0; j < Q; ++j) {
-        a += sw[((size_t)v * (TE + 2) + f) * Q + j];
-        b += ((j & 1) ? -1.0 : 1.0) * sw[((size_t)v * (TE + 2) + f + 1) * Q + j];
-      }
-      wl[v] = (DG)a;
-      wr[v] = (DG)b;
-      if (visc) {
+    if (visc) {
+      // the traces of w (phase 2a leaves them to this item) and of q
+      for (int v = 0; v < nv; ++v) {
+        double a = 0.0, b = 0.0;
+        for (int j = 0; j < Q; ++j) {
+          a += sw[((size_t)v * (TE + 2) + f) * Q + j];
+          b += ((j & 1) ? -1.0 : 1.0) * sw[((size_t)v * (TE + 2) + f + 1) * Q + j];
+        }
+        wl[v] = (DG)a;
+        wr[v] = (DG)b;
         double qa = 0.0, qb = 0.0;
         for (int j = 0; j < Q; ++j) {
           qa += sqw[((size_t)v * (TE + 2) + f) * Q + j];
@@ -546,11 +563,15 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   // for constant c_p), ln T, 1/T, velocity and pressure, in FP64; the face items
   {
     const double *sQW = ssp + SP_QW * ns, *sCVW = ssp + SP_CVW * ns, *sRW = ssp + SP_RW * ns;
-    for (int it = tid; it < teq + n_face; it += nth) {
-      if (it >= teq) {
-        face_item(it - teq);
+    // the face items start on a warp boundary: a warp holding points and faces
+    // ran both paths one after the other and was the phase's critical path
+    const int fb = (teq + 31) & ~31;
+    for (int it = tid; it < fb + n_face; it += nth) {
+      if (it >= fb) {
+        face_item(it - fb);
         continue;
       }
+      if (it >= teq) continue;
       const int t = it;
       const double *wq = snw + t;
       double rho = 0.0, qsum = 0.0, cv = 0.0, Rm = 0.0;
@@ -572,8 +593,15 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         sdfT[2 * t] = df_split(slnT[t]);
         sdfT[2 * t + 1] = df_split(sinvT[t]);
       }
-      su[t] = u;
-      sPr[t] = T * Rm;
+      if constexpr (MIX) {
+        // FP32 copies for phase 2c, in the storage of su (2 TQ floats)
+        float *suf = reinterpret_cast<float *>(su);
+        suf[t] = (float)u;
+        suf[TQ + t] = (float)(T * Rm);
+      } else {
+        su[t] = u;
+        sPr[t] = T * Rm;
+      }
       if (visc) sTv[t] = T;
     }
   }
@@ -589,7 +617,29 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   // 2c. per (variable, point): the flux, and for a species its concentration
   // (law of mass action on non-negative concentrations: clipped at zero by the
   // sign bit)
-  {
+  if constexpr (MIX) {
+    // in FP32 throughout, on the copies of phases 2a and 2b
+    const float *sIW = sspD + SP_INVW * ns, *suf = reinterpret_cast<const float *>(su);
+    for (int item = tid; item < nv * teq; item += nth) {
+      int v = item / teq, t = item - v * teq;
+      const size_t at = (size_t)v * TQ + t;
+      const float w = sfx[at], u = suf[t];
+      float f;
+      if (v >= 2) {
+        const int i = v - 2;
+        const float r = (__float_as_int(w) < 0) ? 0.0f : w;
+        scc[(size_t)i * TQ + t] = r * sIW[i];
+        f = u * w;
+      } else if (v == 0) {
+        f = fmaf(w, u, suf[TQ + t]);
+      } else {
+        f = u * (w + suf[TQ + t]);
+      }
+      // f = f^c - f^d
+      if (visc) f -= d2f_int(sqn[at]);
+      sfx[at] = f;
+    }
+  } else {
     const double *sIW = ssp + SP_INVW * ns;
     for (int item = tid; item < nv * teq; item += nth) {
       int v = item / teq, t = item - v * teq;
@@ -599,20 +649,14 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         const int i = v - 2;
         const double r = (__double2hiint(w) < 0) ? 0.0 : w;
         scc[(size_t)i * TQ + t] = (DG)(r * sIW[i]);
-        if constexpr (MIX) sfx[at] = (DG)u * (DG)w;
-        else snw[at] = u * w;
+        snw[at] = u * w;
       } else if (v == 0) {
-        if constexpr (MIX) sfx[at] = fma((DG)w, (DG)u, (DG)sPr[t]);
-        else snw[at] = w * u + sPr[t];
+        snw[at] = w * u + sPr[t];
       } else {
-        if constexpr (MIX) sfx[at] = (DG)u * ((DG)w + (DG)sPr[t]);
-        else snw[at] = u * (w + sPr[t]);
+        snw[at] = u * (w + sPr[t]);
       }
       // f = f^c - f^d
-      if (visc) {
-        if constexpr (MIX) sfx[at] -= d2f_int(sqn[at]);
-        else snw[at] -= sqn[at];
-      }
+      if (visc) snw[at] -= sqn[at];
     }
   }
   __syncthreads();
