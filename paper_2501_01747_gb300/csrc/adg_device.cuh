@@ -359,35 +359,50 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   // 0. mechanism, species fields, incidence, exp table and basis values into
   // shared memory
   {
+    // a thread's share of every table is loaded before any of it is stored, so
+    // that its global loads are in flight together (a store in between would
+    // hold the next load back: the tables' pointers may alias shared memory)
     const uint4 *src = reinterpret_cast<const uint4 *>(M.rx);
     uint4 *dst = reinterpret_cast<uint4 *>(srx);
-    for (int k = tid; k < nr * (int)(sizeof(Rxn) / 16); k += nth) dst[k] = src[k];
-    for (int k = tid; k < SP_NFIELDS * ns; k += nth) {
-      double x = M.sp[k];
-      ssp[k] = x;
-      if constexpr (MIX) sspD[k] = (DG)x;
-    }
-    for (int k = tid; k < 32; k += nth) {
-      stab->t[k] = c_iexp.t[k];
-      stab->t32[k] = c_iexp.t32[k];
-      if constexpr (MIX) iexp_table_df(c_iexp.t32[k], &stab->tf[2 * k], &stab->tf[2 * k + 1]);
-    }
-    if constexpr (MIX) {
-      for (int k = tid; k < nr * 6; k += nth) srxf[k] = M.rxf[k];
-    }
-    for (int k = tid; k < Q * Q; k += nth) sPq[k] = B.P[k / Q][k % Q];
-    for (int k = tid; k <= ns; k += nth) soff[k] = M.sx_off[k];
-    for (int k = tid; k < M.nterm; k += nth) {
-      const int term = M.sx[k];
-      sterm[k] = term >> 8;
-      scoef[k] = (DG)(signed char)(term & 0xff);
+    const int n_rx4 = nr * (int)(sizeof(Rxn) / 16), n_sp = SP_NFIELDS * ns;
+    const int n_rxf = MIX ? nr * 6 : 0, n_term = M.nterm;
+    const int n_all = max(max(max(n_rx4, n_sp), max(n_rxf, n_term)), max(max(32, Q * Q), ns + 1));
+    for (int k = tid; k < n_all; k += nth) {
+      uint4 rx4 = {};
+      double spv = 0.0;
+      DF rf = {};
+      int term = 0, off = 0;
+      if (k < n_rx4) rx4 = src[k];
+      if (k < n_sp) spv = M.sp[k];
+      if (k < n_rxf) rf = M.rxf[k];
+      if (k < n_term) term = M.sx[k];
+      if (k <= ns) off = M.sx_off[k];
+      if (k < n_rx4) dst[k] = rx4;
+      if (k < n_sp) {
+        ssp[k] = spv;
+        if constexpr (MIX) sspD[k] = (DG)spv;
+      }
+      if constexpr (MIX) {
+        if (k < n_rxf) srxf[k] = rf;
+      }
+      if (k < n_term) {
+        sterm[k] = term >> 8;
+        scoef[k] = (DG)(signed char)(term & 0xff);
+      }
+      if (k <= ns) soff[k] = off;
+      if (k < 32) {
+        stab->t[k] = c_iexp.t[k];
+        stab->t32[k] = c_iexp.t32[k];
+        if constexpr (MIX) iexp_table_df(c_iexp.t32[k], &stab->tf[2 * k], &stab->tf[2 * k + 1]);
+      }
+      if (k < Q * Q) sPq[k] = B.P[k / Q][k % Q];
     }
   }
   // 1. tile of modal coefficients with a one-element halo on each side and, for
   // stages after the first, the tile's modes of w^n or dq (batches of loads in
   // flight)
   {
-    constexpr int BATCH = 4;
+    constexpr int BATCH = 8;
     const int span = (te + 2) * Q, n_tile = nv * span;
     const int n_wn = (A.s == 0) ? 0 : nv * te * Q;
     const int total = n_tile + n_wn;
