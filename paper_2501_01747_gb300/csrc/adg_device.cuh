@@ -28,6 +28,7 @@ static __constant__ Basis c_basis[ADG_MAX_P];     // index p-1
 static __constant__ BasisF c_basis_f[ADG_MAX_P];  // the same, rounded to float
 
 static __constant__ IExpTable c_iexp = {ADG_IEXP_TABLE, ADG_IEXP_TABLE32};
+static __constant__ LogTable c_ltab = {ADG_LOG_TABLE_LN, ADG_LOG_TABLE_INV};
 
 // Upload the DG/WENO tables to this translation unit's constant memory.
 static cudaError_t upload_unit_tables(const Basis *tables) {
@@ -125,6 +126,29 @@ __device__ __forceinline__ float d2f_int(double x) {
   const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
   // a mantissa carry runs into the exponent (up to infinity), as rounding should
   return __uint_as_float(((hi & 0x80000000u) | ((unsigned)ef << 23) | m) + up);
+}
+
+// df_split on the integer pipeline (the same pair: both conversions round to
+// nearest, and the one back is exact).
+__device__ __forceinline__ DF df_split_int(double x) {
+  const float h = d2f_int(x);
+  return DF{h, d2f_int(x - f2d_exact(h))};
+}
+
+// 1/x to a relative error below 2^-44, for x whose float is normal: a float
+// seed (the fraction truncated to 23 bits on the integer pipeline, the
+// correctly rounded float reciprocal: within 1.5 2^-23) and one Newton-Raphson
+// step in FP64, r + r (1 - x r), which squares the seed's error. Two double
+// operations where a full-precision division takes several times that; other x
+// take the division.
+__device__ __forceinline__ double recip_nr(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int ef = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (ef <= 1 || ef >= 253) return 1.0 / x;
+  const float xf = __uint_as_float((hi & 0x80000000u) | ((unsigned)ef << 23) |
+                                   ((hi & 0xfffffu) << 3) | (lo >> 29));
+  const double r = f2d_exact(__frcp_rn(xf));
+  return fma(r, fma(-x, r, 1.0), r);
 }
 
 // To the variant's arithmetic type without the FP64 unit.
@@ -597,22 +621,32 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         cv = fma(r, sCVW[i], cv);
         Rm = fma(r, sRW[i], Rm);
       }
-      const double m = wq[0], u = m / rho;
-      const double num = wq[TQ] - 0.5 * m * u - qsum;
-      const double T = num / cv;
+      const double m = wq[0];
+      double u, num, T;
+      if constexpr (MIX) {
+        // ln T and 1/T feed float-float arguments (about 1e-12): reciprocals
+        // by one Newton step from a float seed, Tang's table logarithm, the
+        // float pairs split on the integer pipeline
+        u = m * recip_nr(rho);
+        num = wq[TQ] - 0.5 * m * u - qsum;
+        const double inum = recip_nr(num);
+        T = num * recip_nr(cv);
+        sdfT[2 * t] = df_split_int(log_tab(T, c_ltab));
+        sdfT[2 * t + 1] = df_split_int(cv * inum);
+      } else {
+        u = m / rho;
+        num = wq[TQ] - 0.5 * m * u - qsum;
+        T = num / cv;
+        slnT[t] = log(T);
+        sinvT[t] = cv / num;
+      }
       if (!(rho > 0.0) || !(T > 0.0) || !isfinite(T) || !isfinite(m))
         report_error(I, ADG_ERR_NONPHYSICAL, e0 + t / Q, A.s, nstep);
-      slnT[t] = log(T);
-      sinvT[t] = cv / num;
-      if constexpr (MIX) {
-        sdfT[2 * t] = df_split(slnT[t]);
-        sdfT[2 * t + 1] = df_split(sinvT[t]);
-      }
       if constexpr (MIX) {
         // FP32 copies for phase 2c, in the storage of su (2 TQ floats)
         float *suf = reinterpret_cast<float *>(su);
-        suf[t] = (float)u;
-        suf[TQ + t] = (float)(T * Rm);
+        suf[t] = d2f_int(u);
+        suf[TQ + t] = d2f_int(T * Rm);
       } else {
         su[t] = u;
         sPr[t] = T * Rm;
