@@ -600,11 +600,11 @@ def main(argv=None):
 # DRAM bytes (read + write) per stage-kernel launch from ncu, per (workload,
 # kernel revision, precision); the summaries are under profiles/.
 STAGE_TRAFFIC = {
-    ("ignition-9sp-4096x4", "v13", "mixed"): 2.019584e6,
-    ("ignition-9sp-4096x4", "v13", "fp64"): 2.055424e6,
+    ("ignition-9sp-4096x4", "v14", "mixed"): 2.0224e6,
+    ("ignition-9sp-4096x4", "v14", "fp64"): 2.056704e6,
 }
 
-KERNEL_REV = "v13"
+KERNEL_REV = "v14"
 
 if __name__ == "__main__":
     sys.exit(main())
