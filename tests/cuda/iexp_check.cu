@@ -1,19 +1,28 @@
 // Test harness (not part of the library): the library's integer-pipeline exp
 // (csrc/adg_math.cuh) on the GPU, against the same function compiled for the
 // host (bit for bit), and both it and CUDA's exp against expl in extended
-// precision on the host. Prints one JSON line.
+// precision on the host; the mixed variant's table logarithm likewise (against
+// its host build and logl), and its Newton-Raphson reciprocal (csrc/adg_device.cuh)
+// against the exact reciprocal. Prints one JSON line.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
 
-#include "../../paper_2501_01747_gb300/csrc/adg_math.cuh"
+#include "../../paper_2501_01747_gb300/csrc/adg_device.cuh"
 
 __global__ void eval(const double *x, double *mine, double *cuda_ref, int n, adg::IExpTable tab) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   mine[i] = adg::iexp(x[i], tab);
   cuda_ref[i] = exp(x[i]);
+}
+
+__global__ void eval_log(const double *x, double *ln, double *rc, int n, adg::LogTable tb) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  ln[i] = adg::log_tab(x[i], tb);
+  rc[i] = adg::recip_nr(x[i]);
 }
 
 static double ulp_err(double got, long double ref) {
@@ -52,7 +61,41 @@ int main() {
     if (e > max_ulp) max_ulp = e;
     if (ec > cuda_max_ulp) cuda_max_ulp = ec;
   }
+  // the table logarithm (outside [1/2, 2), where it takes the library's) and the
+  // reciprocal: temperatures, then positive and negative values over 60 decades
+  std::vector<double> y(n);
+  for (int i = 0; i < n; ++i) {
+    double u = (double)rand() / RAND_MAX;
+    if (i % 2 == 0) y[i] = 50.0 + 9950.0 * u;
+    else y[i] = ldexp(0.5 + 0.5 * u, (i / 2) % 200 - 100);
+    if (y[i] >= 0.5 && y[i] < 2.0) y[i] *= 4.0;
+    if (i % 4 == 3) y[i] = -y[i];  // the reciprocal's sign; the logarithm skips these
+  }
+  double *dy, *dl, *dc;
+  if (cudaMalloc(&dy, n * 8) || cudaMalloc(&dl, n * 8) || cudaMalloc(&dc, n * 8)) return 2;
+  cudaMemcpy(dy, y.data(), n * 8, cudaMemcpyHostToDevice);
+  const adg::LogTable ltab = {ADG_LOG_TABLE_LN, ADG_LOG_TABLE_INV};
+  eval_log<<<(n + 255) / 256, 256>>>(dy, dl, dc, n, ltab);
+  std::vector<double> l(n), c(n);
+  cudaMemcpy(l.data(), dl, n * 8, cudaMemcpyDeviceToHost);
+  cudaMemcpy(c.data(), dc, n * 8, cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  long long log_mismatch = 0;
+  double log_max_ulp = 0.0, recip_max_rel = 0.0;
+  for (int i = 0; i < n; ++i) {
+    if (y[i] > 0.0) {
+      if (l[i] != adg::log_tab(y[i], ltab)) ++log_mismatch;
+      const long double ref = logl((long double)y[i]);
+      const double rd = fabs((double)ref);
+      const double ulp = std::nextafter(rd, INFINITY) - rd;
+      log_max_ulp = fmax(log_max_ulp, (double)(fabsl((long double)l[i] - ref) / ulp));
+    }
+    const long double rr = 1.0L / (long double)y[i];
+    recip_max_rel = fmax(recip_max_rel, (double)fabsl(((long double)c[i] - rr) / rr));
+  }
   printf("{\"n\": %d, \"host_mismatch\": %lld, \"max_ulp\": %.4f, \"cuda_exp_max_ulp\": %.4f, "
-         "\"cuda\": \"%s\"}\n", n, mismatch, max_ulp, cuda_max_ulp, cudaGetErrorString(err));
+         "\"log_host_mismatch\": %lld, \"log_max_ulp\": %.4f, \"recip_max_rel\": %.3g, "
+         "\"cuda\": \"%s\"}\n", n, mismatch, max_ulp, cuda_max_ulp, log_mismatch, log_max_ulp,
+         recip_max_rel, cudaGetErrorString(err));
   return err == cudaSuccess ? 0 : 1;
 }

@@ -1,7 +1,9 @@
 """The library's integer-pipeline FP64 exp on the GPU: bit for bit the same as
 the host build of the same function, and within 0.6 units in the last place of
 the exact value (expl in extended precision) over the argument range used;
-CUDA's own exp is measured beside it for reference."""
+CUDA's own exp is measured beside it for reference. The mixed variant's table
+logarithm on the GPU: bit for bit its host build and within 1.5 units in the
+last place of logl; its Newton-Raphson reciprocal within 2^-44 of 1/x."""
 import json
 import os
 import subprocess
@@ -22,3 +24,6 @@ def test_integer_exp_on_gpu_matches_host_and_exact(tmp_path):
     rec = json.loads(out.stdout.strip().splitlines()[-1])
     assert rec["host_mismatch"] == 0, rec
     assert rec["max_ulp"] <= 0.6, rec
+    assert rec["log_host_mismatch"] == 0, rec
+    assert rec["log_max_ulp"] <= 1.5, rec
+    assert rec["recip_max_rel"] <= 2.0 ** -44, rec
