@@ -1192,8 +1192,9 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
   }
   __syncthreads();
   if (threadIdx.x < EPB * LIM_L) {
-    // every lane runs the indicator (shuffles); groups past the last element
-    // work on the first element and write nothing
+    // the first EPB LIM_L threads (whole warps) run the indicator, every lane of
+    // them (shuffles); groups past the last element work on the first element
+    // and write nothing
     const int le = threadIdx.x / LIM_L;
     const bool valid = le < te;
     const int lv = valid ? le : 0, e = e0 + lv;
