@@ -505,9 +505,10 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   }
   __syncthreads();
   // The face fluxes of the tile (local face f between local elements f and f+1),
-  // one (level, face) per item: the plain flux of the traces of phase 2a, or one
-  // delayed level of the AT flux (Eq. 7) with both sides at the common level
-  // n-k-m from the history ring. They run in phase 2b on the warps after those
+  // one (level, face) per item: the plain flux of the traces of phase 2a (a
+  // viscous instance's item sums its own, with those of q), or one delayed
+  // level of the AT flux (Eq. 7) with both sides at the common level n-k-m from
+  // the history ring. They run in phase 2b on the warps after those
   // of the thermodynamics (they were the critical path of the chemistry phase).
   const int n_face = O * (te + 1);
   auto face_item = [&](const int item) {
