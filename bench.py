@@ -32,6 +32,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 from paper_2501_01747_gb300 import inputs as I  # noqa: E402
+from paper_2501_01747_gb300 import shard as SH  # noqa: E402
 
 DEFAULT_WORKLOAD = "ignition-9sp-4096x4"
 METRIC = "DOF-stage updates/s (mixed vs FP64, same GB300) at stated error; % HBM roofline"
@@ -191,11 +192,13 @@ def run_reference(args, ws, rank):
     return 0
 
 
-def workload_config(wls, mech, args):
+def workload_config(wls, mech, args, mode="single", ws=1):
+    """The whole job's workload (`wls`: every instance, over all ranks)."""
+    par = {"single": "single", "replicas": "replicas x%d" % ws,
+           "sharded": "instances sharded over %d ranks" % ws}[mode if ws > 1 else "single"]
     common = {"n_species": mech.ns, "n_reactions": mech.nr, "precision": args.precision,
               "l2": "flushed between timed steps (256 MiB write)",
-              "launch": "CUDA graph per step",
-              "parallelism": "replicas" if args.gpus > 1 else "single"}
+              "launch": "CUDA graph per step", "parallelism": par}
     if len(wls) > 1:
         return dict(common, workload=args.workload, instances=len(wls),
                     n_elem_total=sum(w.n_elem for w in wls),
@@ -268,12 +271,11 @@ def measure(adg, torch, wls, mech, prims, prec, args, dev, pg, ws, steps, autotu
     clocks = sampler.stop()
     g.check()
     launches = g.launches_per_step() * steps
-    if pg:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    # the longest rank's time and the units of all ranks (this rank's instances:
+    # its shard of an ensemble, or a replica of a single problem)
     dof_stage = dof_stages_per_step(wls)
-    value = dof_stage * steps * ws / (ms / 1e3)
+    ms, dof_all = SH.reduce_rate(pg, ms, dof_stage, dev)
+    value = dof_all * steps / (ms / 1e3)
 
     # end to end through the C ABI with host buffers: H2D state, step, D2H state
     host_in, host_out, nbytes = [], [], 0
@@ -299,7 +301,8 @@ def measure(adg, torch, wls, mech, prims, prec, args, dev, pg, ws, steps, autotu
     torch.cuda.synchronize(dev)
     e2e_ms = max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3)
     g.check()
-    e2e_value = dof_stage * n_e2e * ws / (e2e_ms / 1e3)
+    e2e_ms, _ = SH.reduce_rate(pg, e2e_ms, dof_stage, dev)
+    e2e_value = dof_all * n_e2e / (e2e_ms / 1e3)
     g.close()
     del flush
     return {"value": value, "ms": ms, "kms": kms, "kn": kn, "launches": launches,
@@ -497,6 +500,9 @@ def main(argv=None):
     wls, mech = bench_workloads(args.workload)
     if args.viscous:
         wls = [I.viscous(w, name=w.name + "-viscous") for w in wls]
+    all_wls = wls
+    idx, mode = SH.assign(len(all_wls), rank, ws)
+    wls = [all_wls[i] for i in idx]
     prims = [w.primitive(mech) for w in wls]
     err_steps = 200 if len(wls) == 1 else 20
     head, other, other_prec, err = compare(adg, torch, wls, mech, prims, args, dev, pg, ws,
@@ -517,13 +523,15 @@ def main(argv=None):
                            args.visc_steps))
     ens = None
     if args.ensemble_steps > 0 and args.workload != ENSEMBLE and not args.only:
-        ewls, emech = bench_workloads(ENSEMBLE)
+        ewls_all, emech = bench_workloads(ENSEMBLE)
+        eidx, emode = SH.assign(len(ewls_all), rank, ws)
+        ewls = [ewls_all[i] for i in eidx]
         eprims = [w.primitive(emech) for w in ewls]
         eargs = argparse.Namespace(**vars(args))
         eargs.tuning = ""
         ens = compare(adg, torch, ewls, emech, eprims, eargs, dev, pg, ws, args.ensemble_steps,
                       err_steps=10)
-        ens = (ewls, emech) + ens
+        ens = (ewls, ewls_all, emode, emech) + ens
 
     if rank != 0:
         return 0
@@ -532,9 +540,11 @@ def main(argv=None):
     line = {
         "metric": METRIC, "value": head["value"], "unit": "DOF-stage/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True,
+        # replicas keep the per-GPU work fixed; a sharded ensemble, the total
+        "scaling": "strong" if (mode == "sharded" and ws > 1) else "weak", "vs_baseline": None,
         "dtype": "f32+f64" if mixed else "f64",
-        "data": "synthetic", "config": dict(workload_config(wls, mech, args),
+        "data": "synthetic", "config": dict(workload_config(all_wls, mech, args, mode, ws),
                                             tuning=head["tuning"]),
         "roofline": roofline(wls, mech, head, mixed, peaks, src),
         "clocks": head["clocks"],
@@ -577,9 +587,11 @@ def main(argv=None):
             "e2e": r["e2e"], "roofline": roofline([lw], mech, r, mixed, peaks, src),
             "clocks": r["clocks"], "tuning": r["tuning"]}
     if ens is not None:
-        ewls, emech, eh, eo, eop, ee = ens
-        rec = {"config": dict(workload_config(ewls, emech, args), tuning=eh["tuning"]),
+        ewls, ewls_all, emode, emech, eh, eo, eop, ee = ens
+        rec = {"config": dict(workload_config(ewls_all, emech, args, emode, ws),
+                              tuning=eh["tuning"]),
                "steps": args.ensemble_steps, "value": eh["value"],
+               "scaling": "strong" if (emode == "sharded" and ws > 1) else "weak",
                "ms_per_step": eh["ms"] / args.ensemble_steps, "e2e": eh["e2e"],
                "roofline": roofline(ewls, emech, eh, mixed, peaks, src)}
         if eo is not None:
