@@ -219,7 +219,7 @@ def mass_fractions(w, p):
     return r / r.sum(axis=0, keepdims=True)
 
 
-def measure(adg, torch, wls, mech, prims, prec, args, dev, pg, ws, steps, autotune=True):
+def measure(adg, torch, wls, mech, prims, prec, args, dev, pg, steps, autotune=True):
     """Warm-up, autotune, device-timed steps and the end-to-end run of one
     precision variant on its own context."""
     g = adg.ADG(mech, wls, device=dev, precision=prec)
@@ -439,14 +439,14 @@ def roofline(wls, mech, r, mixed, peaks, src):
             "hbm_frac": hbm / peaks.get("hbm_gbs", 6800.0), "hbm_peak_source": src}
 
 
-def compare(adg, torch, wls, mech, prims, args, dev, pg, ws, steps, autotune=True,
+def compare(adg, torch, wls, mech, prims, args, dev, pg, steps, autotune=True,
             err_steps=200):
     """Both precision variants on the same workload, the headline one first."""
     other_prec = "fp64" if args.precision == "mixed" else "mixed"
-    head = measure(adg, torch, wls, mech, prims, args.precision, args, dev, pg, ws, steps,
+    head = measure(adg, torch, wls, mech, prims, args.precision, args, dev, pg, steps,
                    autotune)
     other = None if args.only else measure(adg, torch, wls, mech, prims, other_prec, args, dev,
-                                           pg, ws, steps, autotune)
+                                           pg, steps, autotune)
     err = None if args.only else mixed_error(adg, torch, wls, mech, prims, dev, err_steps)
     return head, other, other_prec, err
 
@@ -505,7 +505,7 @@ def main(argv=None):
     wls = [all_wls[i] for i in idx]
     prims = [w.primitive(mech) for w in wls]
     err_steps = 200 if len(wls) == 1 else 20
-    head, other, other_prec, err = compare(adg, torch, wls, mech, prims, args, dev, pg, ws,
+    head, other, other_prec, err = compare(adg, torch, wls, mech, prims, args, dev, pg,
                                            args.steps, err_steps=err_steps)
     uns = None
     if args.unsync_steps > 0 and len(wls) == 1 and not args.only:
@@ -514,12 +514,12 @@ def main(argv=None):
     lsk = None
     if args.lserk_steps > 0 and len(wls) == 1 and not args.only:
         lw = dataclasses.replace(wls[0], integrator=I.RK_LS4, name=wls[0].name + "-lserk4")
-        lsk = (lw, measure(adg, torch, [lw], mech, prims, args.precision, args, dev, pg, ws,
+        lsk = (lw, measure(adg, torch, [lw], mech, prims, args.precision, args, dev, pg,
                            args.lserk_steps))
     vis = None
     if args.visc_steps > 0 and len(wls) == 1 and not args.only and not args.viscous:
         vw = I.viscous(wls[0], name=wls[0].name + "-viscous")
-        vis = (vw, measure(adg, torch, [vw], mech, prims, args.precision, args, dev, pg, ws,
+        vis = (vw, measure(adg, torch, [vw], mech, prims, args.precision, args, dev, pg,
                            args.visc_steps))
     ens = None
     if args.ensemble_steps > 0 and args.workload != ENSEMBLE and not args.only:
@@ -529,7 +529,7 @@ def main(argv=None):
         eprims = [w.primitive(emech) for w in ewls]
         eargs = argparse.Namespace(**vars(args))
         eargs.tuning = ""
-        ens = compare(adg, torch, ewls, emech, eprims, eargs, dev, pg, ws, args.ensemble_steps,
+        ens = compare(adg, torch, ewls, emech, eprims, eargs, dev, pg, args.ensemble_steps,
                       err_steps=10)
         ens = (ewls, ewls_all, emode, emech) + ens
 
