@@ -65,9 +65,11 @@ extern "C" {
 #define ADG_MAX_STAGES 5
 /* Arithmetic of the RK-stage right-hand side (Sec. 5, mixed-precision runs).
  * ADG_FP64: every step in double precision.
- * ADG_MIXED: the numerical flux, the DG volume/surface/source assembly and the
- * troubled-cell indicator and WENO reconstruction in float; the state, the
- * Gauss-point temperature, the Arrhenius and equilibrium exponentials, the AT
+ * ADG_MIXED: the numerical flux, the DG volume/surface/source assembly, the
+ * mass-action products and the troubled-cell indicator and WENO reconstruction
+ * in float; the Arrhenius and equilibrium exponents as float pairs (about 1e-12
+ * absolute) and their exponentials rounded once to float; the state at the
+ * Gauss points, the temperature (ln T and 1/T to about 1e-14 relative), the AT
  * level sums and the RK accumulation in double. The state arrays stay double. */
 #define ADG_FP64 0
 #define ADG_MIXED 1
