@@ -69,7 +69,7 @@ extern "C" {
  * mass-action products and the troubled-cell indicator and WENO reconstruction
  * in float; the Arrhenius and equilibrium exponents as float pairs (about 1e-12
  * absolute) and their exponentials rounded once to float; the state at the
- * Gauss points, the temperature (ln T and 1/T to about 1e-14 relative), the AT
+ * Gauss points, the temperature (T, ln T and 1/T to about 1e-13), the AT
  * level sums and the RK accumulation in double. The state arrays stay double. */
 #define ADG_FP64 0
 #define ADG_MIXED 1
