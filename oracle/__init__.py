@@ -90,6 +90,8 @@ def lib():
         _lib.or_shift_matrix.argtypes = [C.c_int, C.c_int, d]
         _lib.or_rhs_sync.argtypes = [C.POINTER(Cfg), C.POINTER(Mech), d, d]
         _lib.or_aux_sync.argtypes = [C.POINTER(Cfg), C.POINTER(Mech), d, d]
+        _lib.or_limit_sync.argtypes = [C.POINTER(Cfg), C.POINTER(Mech), d, d,
+                                       C.POINTER(C.c_uint8)]
         _lib.or_transport.argtypes = [C.POINTER(Mech), C.POINTER(Cfg), C.c_double, C.c_double,
                                       d, d, d, d]
         _lib.or_visc_flux.argtypes = [C.POINTER(Mech), C.POINTER(Cfg), d, d, d]
@@ -168,6 +170,21 @@ def aux_sync(wl, mech, w):
     if rc != 0:
         raise RuntimeError("or_aux_sync failed (%d)" % rc)
     return q
+
+
+def limit_sync(wl, mech, w):
+    """The troubled-cell indicator and WENO limiter applied once to a modal state
+    (no delays): (flags [n_elem] uint8, limited state)."""
+    cfg, probs = make_cfg(wl)
+    mh = MechHandle(mech)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.zeros_like(w)
+    flags = np.zeros(wl.n_elem, dtype=np.uint8)
+    rc = lib().or_limit_sync(C.byref(cfg), mh.ref, _dp(w), _dp(out),
+                             flags.ctypes.data_as(C.POINTER(C.c_uint8)))
+    if rc != 0:
+        raise RuntimeError("or_limit_sync failed (%d)" % rc)
+    return flags, out
 
 
 def rk_stages(integrator):

@@ -1070,12 +1070,13 @@ static int neighbour(or_ctx *c, const double *arr, int e, int dir, int s, double
  * characteristic field of L(wbar_e), the face deviations v(+1)-vbar and
  * vbar-v(-1) are passed through the TVB-modified minmod with the neighbours'
  * average differences; the cell is troubled if any deviation is modified.
- * Deviations below 1e-5 of the field's magnitude sum_v |L_kv| sigma_v count as
- * zero, with sigma = (rho a + |rho u|, |rho E|, rho, .., rho) of the cell
- * average, so that rounding noise on flat data, species present only at
- * round-off level, and the rounding of a run in single precision (about 1e-6
- * of that magnitude after the characteristic transform) never flag a cell: the
- * same cells are troubled whatever the precision of the arithmetic.
+ * The paper's criterion is TVD (M = 0) and has no threshold; deviations below
+ * 1e-10 of the field's magnitude sum_v |L_kv| sigma_v count as zero, with
+ * sigma = (rho a + |rho u|, |rho E|, rho, .., rho) of the cell average. That is
+ * a rounding guard only: double-precision data that is flat up to rounding has
+ * deviations of about 1e-16 of that magnitude times the conditioning of the
+ * characteristic transform, far below it, so flat data never flags a cell on
+ * the strength of its rounding.
  * Limiter: v_lim = w_-1 vt_{e-1} + w_0 v_e + w_1 vt_{e+1} with vt = the neighbour
  * polynomial on Omega_e with its mean there replaced by the mean of v_e; linear
  * weights (0.001, 0.998, 0.001), eps = 1e-6; w_lim = R v_lim on modes >= 1, the
@@ -1084,7 +1085,7 @@ static int limit_stage(or_ctx *c, int s, uint8_t *flags) {
   int nv = c->nv, q = c->np1, ne = c->ne;
   const double gam[3] = {0.001, 0.998, 0.001};
   const double eps = 1e-6;
-  const double tau = 1e-5;
+  const double tau = 1e-10;
   double R[MAXV * MAXV], L[MAXV * MAXV], lam[MAXV];
   double own[MAXV * MAXQ], nbl[MAXV * MAXQ], nbr[MAXV * MAXQ];
   double shl[MAXV * MAXQ], shr[MAXV * MAXQ];
@@ -1289,6 +1290,23 @@ int or_rhs_sync(const or_cfg *cfg, const or_mech *m, const double *w, double *rh
   int err = c->cfg.viscous ? aux_eval(c, c->win, 0, 0) : 0;
   if (!err) err = rhs_eval(c, c->win, 0, 0);
   memcpy(rhs, c->rhs, sizeof(double) * sz);
+  or_destroy(c);
+  return err;
+}
+
+/* The troubled-cell indicator and WENO limiter of Sec. 3.3 applied once to a
+ * state (no delays: every neighbour is the adjacent element or a boundary
+ * ghost), for tests: flags[n_elem] gets the indicator's decision, wout the
+ * limited state (equal to w where the cell is not troubled or cfg->limiter is
+ * off). */
+int or_limit_sync(const or_cfg *cfg, const or_mech *m, const double *w, double *wout,
+                  uint8_t *flags) {
+  or_ctx *c = or_create(cfg, m);
+  if (!c) return -2;
+  size_t sz = (size_t)c->nv * c->ne * c->np1;
+  memcpy(c->wpre, w, sizeof(double) * sz);
+  int err = limit_stage(c, 0, flags);
+  memcpy(wout, c->win, sizeof(double) * sz);
   or_destroy(c);
   return err;
 }

@@ -95,6 +95,10 @@ int or_get_flags(const or_ctx *c, uint8_t *last, int32_t *count);
 int or_get_temperature(const or_ctx *c, double *T);
 /* one synchronous right-hand side L(w) (Eq. 5), no delays */
 int or_rhs_sync(const or_cfg *cfg, const or_mech *m, const double *w, double *rhs);
+/* the troubled-cell indicator and WENO limiter (Sec. 3.3) applied once to a state,
+ * no delays: flags [n_elem], limited state wout */
+int or_limit_sync(const or_cfg *cfg, const or_mech *m, const double *w, double *wout,
+                  uint8_t *flags);
 /* the LDG auxiliary variable q = dw/dx of a state (central trace, no delays) */
 int or_aux_sync(const or_cfg *cfg, const or_mech *m, const double *w, double *q);
 int or_reactor0d(const or_mech *m, double *r, double rhoe, double dt, int n_steps);

@@ -115,6 +115,16 @@ def test_design_order_synchronous(p):
     assert _order(errs, ns) > p + 1 - 0.35
 
 
+@pytest.mark.parametrize("p,ns", [(3, [16, 32, 64]), (4, [32, 64, 128])])
+def test_design_order_synchronous_high_degree(p, ns):
+    """Design order p+1 of the DG operator (Sec. 3.1) at p = 3 and 4. SSP-RK3's
+    O(dt^3) error would hide it at a fixed CFL number, so dt shrinks like
+    dx^((p+1)/3) and both errors fall at the rate of dx^(p+1)."""
+    errs = [_advection_error(n, p, cfl=0.2 * (ns[0] / n) ** ((p + 1) / 3.0 - 1.0))[0]
+            for n in ns]
+    assert _order(errs, ns) > p + 1 - 0.35
+
+
 @pytest.mark.parametrize("p", [1, 2])
 def test_at_fluxes_keep_the_asynchrony_error_high_order(p):
     """Sec. 3.2: with AT order o = p+1 the deviation from the synchronous solution
@@ -212,10 +222,10 @@ def test_at_weno_shock_tube_agrees_with_synchronous(mode):
     shock computed with delays (12 PEs, delays up to 2) is as accurate as the
     synchronous one: its L1 error against the exact solution is no larger (within
     10 %), its deviation from the synchronous run is a fraction of that error, and
-    on the plateaus behind the shock and the contact its mean is no further from
-    the exact state than the synchronous mean (within 25 %). Limiter decisions
-    near the shock differ between the two runs, so the deviation is a fraction of
-    the discretisation error, not round-off."""
+    on the plateaus behind the shock and the contact its mean is much closer to
+    the synchronous mean than that is to the exact state. Limiter decisions near
+    the shock differ between the two runs, so the deviation is a fraction of the
+    discretisation error, not round-off."""
     mech = H.inert_mechanism()
     g = 29.1 / (29.1 - RU)
     rl, pl, rr, pr = 1.0, 1e5, 0.125, 1e4
@@ -243,7 +253,9 @@ def test_at_weno_shock_tube_agrees_with_synchronous(mode):
     e_async = l1(out[mode], out[I.DELAY_SYNC])
     assert 0 < e_async < 0.35 * e_exact
     assert l1(out[mode], ex) <= 1.1 * e_exact
+    # plateaus behind the shock and behind the contact: the delayed run is much
+    # closer to the synchronous one than the synchronous one is to the exact state
     for lo, hi in [(0.62, 0.72), (0.52, 0.58)]:
         msk = (x > lo) & (x < hi)
         s, a, e = out[I.DELAY_SYNC][msk].mean(), out[mode][msk].mean(), ex[msk].mean()
-        assert abs(a - e) <= 1.25 * abs(s - e)
+        assert abs(a - s) < 0.25 * abs(s - e)
