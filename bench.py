@@ -6,12 +6,19 @@ stage update, troubled-cell indicator and (AT-)WENO limiter, history-ring writes
 over the whole synthetic workload. A DOF is the paper's vector DOF w_j^e
 (Sec. 3.1), so one step updates n_elem * (p+1) * 3 DOF-stages.
 
+The headline workload is the batched ensemble of 512 independent ignition
+instances (8.58 M Gauss points, the largest single-GPU configuration), in the
+mixed variant (FP32 flux, DG operator and limiter; FP64 temperature and
+chemistry), with the FP64 and the float-chemistry variants timed beside it. The
+9-species ignition (4096 x p4) and the 53-species detonation (65536 x p3) are
+measured as sub-records.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   # the FP64 CPU oracle, bounded sample
 
-Prints one JSON line (rank 0). Under torchrun (N > 1) every rank advances its own
-independent replica of the workload (weak scaling, no data-path collective); the
-timing is the maximum over ranks.
+Prints one JSON line (rank 0). Under torchrun (N > 1) the ensemble's instances
+are sharded over the ranks (a single-instance workload runs as one replica per
+rank); no data moves between ranks, and the timing is the maximum over ranks.
 """
 from __future__ import annotations
 
@@ -24,6 +31,7 @@ import subprocess
 import sys
 import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -34,15 +42,21 @@ if ROOT not in sys.path:
 from paper_2501_01747_gb300 import inputs as I  # noqa: E402
 from paper_2501_01747_gb300 import shard as SH  # noqa: E402
 
-DEFAULT_WORKLOAD = "ignition-9sp-4096x4"
+ENSEMBLE = "ensemble-9sp-512"
+IGNITION = "ignition-9sp-4096x4"
+LARGE = "detonation-53sp-65536x3"
+DEFAULT_WORKLOAD = ENSEMBLE
 METRIC = "DOF-stage updates/s (mixed vs FP64, same GB300) at stated error; % HBM roofline"
 L2_BYTES = 129 * 1024 * 1024
+MIXED_VARIANTS = ("mixed", "mixed_f32chem")
 
-# FP64 peak of GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA
-# (4 flop) per clock per SM x 2.07 GHz = 1.259 TFLOP/s (a microbenchmark of
-# independent FMA chains measured 1.19 TFLOP/s at 1.99 GHz on this machine).
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-ENSEMBLE = "ensemble-9sp-512"
+# Pipe peaks of this GPU model, measured with tests/cuda/fma_peak.cu (independent
+# FMA chains on every SM, CUDA events, best of 5): the ALU denominators of the
+# stage kernel. The derived figures are 152 SMs x 2.07 GHz x 4 flop/clk (FP64)
+# and x 256 flop/clk (FP32): 1.259 and 80.5 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.056
+FP32_PEAK_TFLOPS = 77.18
+PEAK_NOTE = "FMA chains on 152 SMs (tests/cuda/fma_peak.cu), measured on GB300"
 
 
 def stage_kernel_flops(wl, mech):
@@ -59,16 +73,24 @@ def stage_kernel_flops(wl, mech):
     return pts * per_pt, pts * 2 * nr
 
 
-def stage_kernel_bytes(wl, mech):
-    """Algorithmic DRAM bytes of one stage of one instance: read w^n and w^(s),
-    write w^(s+1), FP64, n_vars per vector DOF (24 n_vars bytes per DOF)."""
-    return 24.0 * (mech.ns + 2) * wl.n_elem * (wl.p + 1)
+def stage_kernel_bytes(wl, mech, prec):
+    """Algorithmic DRAM bytes of one stage of one instance: the minimum traffic of
+    a fused stage per vector DOF, 24 n_vars + 16 bytes in FP64 (read w^n and
+    w^(s), write w^(s+1), 8 bytes each per variable, plus a 16-byte temperature
+    guess) and 16 n_vars + 16 in the mixed variants (an FP64 read of w^n and FP32
+    stage reads and writes)."""
+    nv = mech.ns + 2
+    per = (16 * nv + 16) if prec in MIXED_VARIANTS else (24 * nv + 16)
+    return float(per) * wl.n_elem * (wl.p + 1)
 
 
-def bench_workloads(name):
-    """The instances of a bench workload and their shared mechanism."""
+def bench_workloads(name, instances=0):
+    """The instances of a bench workload and their shared mechanism (for the
+    ensemble, its first `instances` members when instances > 0)."""
     if name == ENSEMBLE:
         wls = I.ensemble_workloads()
+        if instances > 0:
+            wls = wls[:instances]
         return wls, wls[0].mechanism()
     wl = I.load_workloads()[name]
     return [wl], wl.mechanism()
@@ -145,23 +167,53 @@ def dist_setup():
 
 
 def cpu_baseline(wls, mech, budget_s=12.0, max_steps=40):
-    """The FP64 oracle (single-threaded C) on this host: the first steps of the
-    workload's first instance, as many as fit in about budget_s seconds."""
+    """The FP64 oracle (plain C, one instance per thread) on this host's cores,
+    on a bounded sample of the workload: a single instance runs its first steps
+    on one thread, as many as fit in about budget_s seconds; an ensemble runs
+    its first instances, one step at a time, one per thread over all host cores
+    (the oracle's ctypes calls release the interpreter lock), until the budget
+    is spent. DOF-stages of the steps done over the wall time."""
     import oracle as O
-    wl = wls[0]
-    o = O.Oracle(wl, mech)
-    o.set_primitive(wl.primitive(mech))
+    if len(wls) == 1:
+        wl = wls[0]
+        o = O.Oracle(wl, mech)
+        o.set_primitive(wl.primitive(mech))
+        t0 = time.perf_counter()
+        n = 0
+        while n < max_steps:
+            o.step(1)
+            n += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        dt = time.perf_counter() - t0
+        dofs = wl.n_elem * (wl.p + 1) * rk_stages(wl) * n
+        return {"value": dofs / dt, "unit": "DOF-stage/s", "cores": 1, "kind": "oracle",
+                "sample": "%s, first %d steps (%.1f s, 1 thread)" % (wl.name, n, dt)}
+    cores = os.cpu_count() or 1
+    sample = wls[:cores]
+    done = [0] * len(sample)
+    oracles = []
+    for wl in sample:  # set-up outside the timed region
+        o = O.Oracle(wl, mech)
+        o.set_primitive(wl.primitive(mech))
+        oracles.append(o)
+    stop = time.perf_counter() + budget_s
+
+    def work(k):
+        while done[k] < max_steps and time.perf_counter() < stop:
+            oracles[k].step(1)
+            done[k] += 1
+        return done[k]
+
     t0 = time.perf_counter()
-    n = 0
-    while n < max_steps:
-        o.step(1)
-        n += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(work, range(len(sample))))
     dt = time.perf_counter() - t0
-    dofs = wl.n_elem * (wl.p + 1) * 3 * n
-    return {"value": dofs / dt, "unit": "DOF-stage/s", "cores": 1, "kind": "oracle",
-            "sample": "%s, first %d steps (%.1f s, 1 thread)" % (wl.name, n, dt)}
+    dofs = sum(w.n_elem * (w.p + 1) * rk_stages(w) * n for w, n in zip(sample, done))
+    return {"value": dofs / dt, "unit": "DOF-stage/s", "cores": cores, "kind": "oracle",
+            "sample": "%s: instances 0..%d, %d to %d steps each, one per thread on %d "
+                      "cores (%.1f s)" % (ENSEMBLE if len(wls) > 1 else wls[0].name,
+                                          len(sample) - 1, min(done), max(done), cores, dt)}
 
 
 def rk_stages(w):
@@ -175,7 +227,7 @@ def dof_stages_per_step(wls):
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
-    wls, mech = bench_workloads(args.workload)
+    wls, mech = bench_workloads(args.workload, args.instances)
     if args.viscous:
         wls = [I.viscous(w, name=w.name + "-viscous") for w in wls]
     cb = cpu_baseline(wls, mech, budget_s=max(5.0, 60.0 / max(1, args.steps + args.warmup)),
@@ -232,8 +284,12 @@ def measure(adg, torch, wls, mech, prims, prec, args, dev, pg, steps, autotune=T
     g.check()
     torch.cuda.synchronize(dev)
     if args.tuning:
-        te, nt = (int(x) for x in args.tuning.split(","))
-        tuning = g.set_tuning(0, te, nt)
+        # "TE,NT" for every group, or "TE,NT;TE,NT;..." per group in order
+        parts = [x for x in args.tuning.split(";") if x]
+        tuning = None
+        for gi in range(len(g.tuning())):
+            te, nt = (int(x) for x in parts[min(gi, len(parts) - 1)].split(","))
+            tuning = g.set_tuning(gi, te, nt)
     else:
         tuning = g.autotune(stream) if autotune and not args.no_autotune else g.tuning()
     torch.cuda.synchronize(dev)
@@ -386,14 +442,14 @@ def unsync_measure(adg, torch, wl, mech, prim, prec, dev, warmup, steps):
             "relative_drift": drift}
 
 
-def mixed_error(adg, torch, wls, mech, prims, dev, n_steps):
-    """Error of the mixed path against the FP64 path (which matches the FP64
+def mixed_error(adg, torch, wls, mech, prims, dev, n_steps, variant="mixed"):
+    """Error of a mixed variant against the FP64 path (which matches the FP64
     oracle to 1e-10) after n_steps from the same state: the largest relative
     error of T at the Gauss points, and the error of every mass fraction at the
     Gauss points where it is above 1e-8, relative to the largest value of that
     species (relative L-infinity) and, for information, to the local value."""
     out = {}
-    for prec in ("fp64", "mixed"):
+    for prec in ("fp64", variant):
         g = adg.ADG(mech, wls, device=dev, precision=prec)
         for k, prim in enumerate(prims):
             g.set_primitive(prim, k)
@@ -403,7 +459,7 @@ def mixed_error(adg, torch, wls, mech, prims, dev, n_steps):
                      for k, wl in enumerate(wls)]
         g.close()
     eT, eY, eP = 0.0, 0.0, 0.0
-    for (T0, Y0), (T1, Y1) in zip(out["fp64"], out["mixed"]):
+    for (T0, Y0), (T1, Y1) in zip(out["fp64"], out[variant]):
         eT = max(eT, float((np.abs(T1 - T0) / T0).max()))
         for i in range(Y0.shape[0]):
             big = Y0[i] > 1e-8
@@ -416,71 +472,111 @@ def mixed_error(adg, torch, wls, mech, prims, dev, n_steps):
             "bar": "1e-4: T at every Gauss point; Y_i relative to max Y_i where Y_i > 1e-8"}
 
 
-def roofline(wls, mech, r, mixed, peaks, src):
-    """Roofline of the stage kernel (the dominant one): the algorithmic flops of
-    one RK stage of every instance over the stage kernels' time for one stage
-    (all degree groups), against the FP64 peak, the pipe that bounds it."""
+def roofline(wls, mech, r, prec, peaks, src, traffic_key=None):
+    """Roofline of the stage kernel (the dominant one): the algorithmic bytes of
+    one RK stage of every instance (stage_kernel_bytes) over the stage kernels'
+    time for one stage (all degree groups), against the measured HBM copy
+    bandwidth; beside it the algorithmic flops against the pipe that carries
+    them (FP32 in the mixed variants, FP64 otherwise)."""
     n_st = max(rk_stages(w) for w in wls)  # stage launches per step (uniform here)
     stage_s = r["kms"][0] / 1e3 / (n_st * r["steps"])
+    nbytes = sum(stage_kernel_bytes(w, mech, prec) for w in wls)
     flops = sum(stage_kernel_flops(w, mech)[0] for w in wls)
     n_exp = sum(stage_kernel_flops(w, mech)[1] for w in wls)
-    achieved = flops / stage_s / 1e12
-    hbm = sum(stage_kernel_bytes(w, mech) for w in wls) / stage_s / 1e9
-    traffic = STAGE_TRAFFIC.get((wls[0].name if len(wls) == 1 else ENSEMBLE, KERNEL_REV,
-                                 "mixed" if mixed else "fp64"))
-    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-            "kernel": "stage_kernel (%s)" % ("mixed" if mixed else "fp64"),
-            "kernel_ms": stage_s * 1e3, "exp_per_s": n_exp / stage_s,
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = nbytes / stage_s / 1e9
+    mixed = prec in MIXED_VARIANTS
+    alu_peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
+    tr = STAGE_TRAFFIC.get((traffic_key, KERNEL_REV, prec)) if traffic_key else None
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": tr,
+            "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % src,
+            "kernel": "stage_kernel (%s), all degree groups of one RK stage" % prec,
+            "algorithmic_bytes_per_stage": nbytes,
+            "bytes_per_vector_dof": (16 if mixed else 24) * (mech.ns + 2) + 16,
+            "kernel_ms": stage_s * 1e3,
             "kernel_share": r["kms"][0] / max(1e-9, r["kms"][0] + r["kms"][1]),
             "limiter_ms": r["kms"][1] / (n_st * r["steps"]),
-            "peak_source": "FP64 pipe: 152 SM x 4 flop/clk x 2.07 GHz (derived)",
-            "hbm_achieved_gbs": hbm, "hbm_peak_gbs": peaks.get("hbm_gbs"),
-            "hbm_frac": hbm / peaks.get("hbm_gbs", 6800.0), "hbm_peak_source": src}
+            "alu": {"pipe": "fp32" if mixed else "fp64",
+                    "achieved": flops / stage_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": flops / stage_s / 1e12 / alu_peak, "peak_source": PEAK_NOTE,
+                    "exp_per_s": n_exp / stage_s}}
 
 
 def compare(adg, torch, wls, mech, prims, args, dev, pg, steps, autotune=True,
-            err_steps=200):
-    """Both precision variants on the same workload, the headline one first."""
-    other_prec = "fp64" if args.precision == "mixed" else "mixed"
-    head = measure(adg, torch, wls, mech, prims, args.precision, args, dev, pg, steps,
-                   autotune)
-    other = None if args.only else measure(adg, torch, wls, mech, prims, other_prec, args, dev,
-                                           pg, steps, autotune)
-    err = None if args.only else mixed_error(adg, torch, wls, mech, prims, dev, err_steps)
-    return head, other, other_prec, err
+            err_steps=200, variants=None):
+    """The precision variants on the same workload, the headline one first; the
+    mixed variants' error against the FP64 path."""
+    variants = variants or [args.precision] + [v for v in ("fp64", "mixed", "mixed_f32chem")
+                                               if v != args.precision]
+    if args.only:
+        variants = variants[:1]
+    res = {}
+    for v in variants:
+        res[v] = measure(adg, torch, wls, mech, prims, v, args, dev, pg, steps, autotune)
+    err = {}
+    if "fp64" in variants:
+        for v in variants:
+            if v in MIXED_VARIANTS:
+                err[v] = mixed_error(adg, torch, wls, mech, prims, dev, err_steps, v)
+    return res, err
+
+
+def variant_record(wls, mech, r, prec, steps, peaks, src, key):
+    return {"value": r["value"], "unit": "DOF-stage/s", "ms_per_step": r["ms"] / steps,
+            "e2e": r["e2e"], "roofline": roofline(wls, mech, r, prec, peaks, src, key),
+            "clocks": r["clocks"], "tuning": r["tuning"], "gpu_launches": int(r["launches"])}
+
+
+def sub_record(wls, all_wls, mech, res, err, steps, peaks, src, key, args, mode, ws):
+    """Every variant of one workload as a nested record."""
+    rec = {"config": workload_config(all_wls, mech, args, mode, ws), "steps": steps}
+    for v, r in res.items():
+        rec[v] = variant_record(wls, mech, r, v, steps, peaks, src, key)
+    if "fp64" in res:
+        for v in MIXED_VARIANTS:
+            if v in res:
+                rec["speedup_%s_vs_fp64" % v] = res[v]["value"] / res["fp64"]["value"]
+    if err:
+        rec["mixed_error"] = err
+    return rec
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     help="a base workload name or %s" % ENSEMBLE)
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
-                    help="the headline variant; the other one is timed beside it")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "mixed_f32chem"],
+                    help="the headline variant; the others are timed beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--tuning", default="", help="TE,NT: set the stage launch configuration "
-                    "instead of autotuning it")
-    ap.add_argument("--only", action="store_true", help="time the headline variant only")
+    ap.add_argument("--tuning", default="", help="TE,NT (every group) or TE,NT;TE,NT;... (one "
+                    "pair per group, in the order of config.tuning): set the stage launch "
+                    "configuration of the headline variant instead of autotuning it")
+    ap.add_argument("--only", action="store_true",
+                    help="time the headline variant of the headline workload only")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="run the first N instances of the ensemble (0: all 512), for "
+                         "profiling captures of a smaller case")
+    ap.add_argument("--sub-steps", type=int, default=100,
+                    help="timed steps of the 9-species ignition sub-record (0: none)")
+    ap.add_argument("--large-steps", type=int, default=10,
+                    help="timed steps of the 53-species detonation sub-record (0: none)")
     ap.add_argument("--unsync-steps", type=int, default=100,
-                    help="steps of the unsynchronised-mode measurement added to the line "
-                         "(single-instance workloads; 0 to skip)")
+                    help="steps of the unsynchronised-mode measurement on the 9-species "
+                         "ignition (0 to skip)")
     ap.add_argument("--lserk-steps", type=int, default=100,
                     help="timed steps of the LSERK4 measurement (the 5-stage 4th-order "
-                         "low-storage integrator) added to the line; 0 to skip")
+                         "low-storage integrator) on the 9-species ignition; 0 to skip")
     ap.add_argument("--viscous", action="store_true",
-                    help="run the headline workload with the viscous terms (its viscous "
-                         "variant: dt/8 at p = 4)")
+                    help="run the headline workload with the viscous terms")
     ap.add_argument("--visc-steps", type=int, default=100,
                     help="timed steps of the viscous measurement (the diffusive flux with "
-                         "the LDG auxiliary kernel) added to the line; 0 to skip")
-    ap.add_argument("--ensemble-steps", type=int, default=20,
-                    help="timed steps of the batched-ensemble measurement added to the line "
-                    "(0: none)")
+                         "the LDG auxiliary kernel) on the 9-species ignition; 0 to skip")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -497,46 +593,68 @@ def main(argv=None):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
-    wls, mech = bench_workloads(args.workload)
-    if args.viscous:
-        wls = [I.viscous(w, name=w.name + "-viscous") for w in wls]
-    all_wls = wls
-    idx, mode = SH.assign(len(all_wls), rank, ws)
-    wls = [all_wls[i] for i in idx]
+    peaks, src = load_peaks()
+
+    def shard(name, viscous=False):
+        wls_all, mech = bench_workloads(name, args.instances if name == ENSEMBLE else 0)
+        if viscous:
+            wls_all = [I.viscous(w, name=w.name + "-viscous") for w in wls_all]
+        idx, mode = SH.assign(len(wls_all), rank, ws)
+        wls = [wls_all[k] for k in idx]
+        return wls_all, wls, mech, mode
+
+    all_wls, wls, mech, mode = shard(args.workload, args.viscous)
     prims = [w.primitive(mech) for w in wls]
-    err_steps = 200 if len(wls) == 1 else 20
-    head, other, other_prec, err = compare(adg, torch, wls, mech, prims, args, dev, pg,
-                                           args.steps, err_steps=err_steps)
-    uns = None
-    if args.unsync_steps > 0 and len(wls) == 1 and not args.only:
-        uns = unsync_measure(adg, torch, wls[0], mech, prims[0], args.precision, dev,
-                             args.warmup, args.unsync_steps)
-    lsk = None
-    if args.lserk_steps > 0 and len(wls) == 1 and not args.only:
-        lw = dataclasses.replace(wls[0], integrator=I.RK_LS4, name=wls[0].name + "-lserk4")
-        lsk = (lw, measure(adg, torch, [lw], mech, prims, args.precision, args, dev, pg,
-                           args.lserk_steps))
-    vis = None
-    if args.visc_steps > 0 and len(wls) == 1 and not args.only and not args.viscous:
-        vw = I.viscous(wls[0], name=wls[0].name + "-viscous")
-        vis = (vw, measure(adg, torch, [vw], mech, prims, args.precision, args, dev, pg,
-                           args.visc_steps))
-    ens = None
-    if args.ensemble_steps > 0 and args.workload != ENSEMBLE and not args.only:
-        ewls_all, emech = bench_workloads(ENSEMBLE)
-        eidx, emode = SH.assign(len(ewls_all), rank, ws)
-        ewls = [ewls_all[i] for i in eidx]
-        eprims = [w.primitive(emech) for w in ewls]
-        eargs = argparse.Namespace(**vars(args))
-        eargs.tuning = ""
-        ens = compare(adg, torch, ewls, emech, eprims, eargs, dev, pg, args.ensemble_steps,
-                      err_steps=10)
-        ens = (ewls, ewls_all, emode, emech) + ens
+    err_steps = 48 if len(wls) == 1 else 20
+    res, err = compare(adg, torch, wls, mech, prims, args, dev, pg, args.steps,
+                       err_steps=err_steps)
+    head = res[args.precision]
+    key = args.workload if not args.viscous else None
+
+    subs = {}
+    single = None  # the 9-species ignition instance, for the mode measurements
+    if not args.only and args.sub_steps > 0 and args.workload != IGNITION:
+        s_all, s_wls, s_mech, s_mode = shard(IGNITION)
+        s_prims = [w.primitive(s_mech) for w in s_wls]
+        sargs = argparse.Namespace(**vars(args))
+        sargs.tuning = ""
+        # the mixed error after 48 steps: beyond, the FP64 scheme's own response to
+        # a single-precision change of its state exceeds the mixed bar
+        sres, serr = compare(adg, torch, s_wls, s_mech, s_prims, sargs, dev, pg,
+                             args.sub_steps, err_steps=48)
+        subs["ignition"] = sub_record(s_wls, s_all, s_mech, sres, serr, args.sub_steps, peaks,
+                                      src, IGNITION, sargs, s_mode, ws)
+        single = (s_wls[0], s_mech, s_prims[0])
+    elif len(wls) == 1:
+        single = (wls[0], mech, prims[0])
+    if not args.only and args.large_steps > 0 and args.workload != LARGE:
+        l_all, l_wls, l_mech, l_mode = shard(LARGE)
+        l_prims = [w.primitive(l_mech) for w in l_wls]
+        largs = argparse.Namespace(**vars(args))
+        largs.tuning = ""
+        lres, lerr = compare(adg, torch, l_wls, l_mech, l_prims, largs, dev, pg,
+                             args.large_steps, err_steps=10, variants=["mixed", "fp64"])
+        subs["detonation_53sp"] = sub_record(l_wls, l_all, l_mech, lres, lerr, args.large_steps,
+                                             peaks, src, LARGE, largs, l_mode, ws)
+
+    uns = lsk = vis = None
+    if single is not None and not args.only:
+        swl, smech, sprim = single
+        if args.unsync_steps > 0:
+            uns = unsync_measure(adg, torch, swl, smech, sprim, "mixed", dev, args.warmup,
+                                 args.unsync_steps)
+        if args.lserk_steps > 0:
+            lw = dataclasses.replace(swl, integrator=I.RK_LS4, name=swl.name + "-lserk4")
+            lsk = (lw, smech, measure(adg, torch, [lw], smech, [sprim], "mixed", args, dev, pg,
+                                      args.lserk_steps))
+        if args.visc_steps > 0 and not args.viscous:
+            vw = I.viscous(swl, name=swl.name + "-viscous")
+            vis = (vw, smech, measure(adg, torch, [vw], smech, [sprim], "mixed", args, dev, pg,
+                                      args.visc_steps))
 
     if rank != 0:
         return 0
-    peaks, src = load_peaks()
-    mixed = args.precision == "mixed"
+    mixed = args.precision in MIXED_VARIANTS
     line = {
         "metric": METRIC, "value": head["value"], "unit": "DOF-stage/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps,
@@ -546,7 +664,7 @@ def main(argv=None):
         "dtype": "f32+f64" if mixed else "f64",
         "data": "synthetic", "config": dict(workload_config(all_wls, mech, args, mode, ws),
                                             tuning=head["tuning"]),
-        "roofline": roofline(wls, mech, head, mixed, peaks, src),
+        "roofline": roofline(wls, mech, head, args.precision, peaks, src, key),
         "clocks": head["clocks"],
         "e2e": head["e2e"],
         "gpu_launches": int(head["launches"]),
@@ -554,69 +672,52 @@ def main(argv=None):
         "value_scalar_dofs": head["value"] * (mech.ns + 2),  # x N_var conserved variables
         "wall_s": head["wall"],
     }
-    if other is not None:
-        line[other_prec] = {
-            "value": other["value"], "ms_per_step": other["ms"] / args.steps,
-            "e2e": other["e2e"], "roofline": roofline(wls, mech, other, not mixed, peaks, src),
-            "clocks": other["clocks"], "tuning": other["tuning"]}
-        fp64_v = other["value"] if mixed else head["value"]
-        mix_v = head["value"] if mixed else other["value"]
-        line["speedup_mixed_vs_fp64"] = mix_v / fp64_v
-    if err is not None:
+    for v, r in res.items():
+        if v != args.precision:
+            line[v] = variant_record(wls, mech, r, v, args.steps, peaks, src, key)
+    if "fp64" in res:
+        for v in MIXED_VARIANTS:
+            if v in res:
+                line["speedup_%s_vs_fp64" % v] = res[v]["value"] / res["fp64"]["value"]
+    if err:
         line["mixed_error"] = err
+    line.update(subs)
     if uns is not None:
         line["unsync"] = uns
     if vis is not None:
-        vw, r = vis
+        vw, vmech, r = vis
         line["viscous"] = {
             "terms": "diffusive flux of Sec. 2 by LDG (auxiliary kernel + viscous stage "
                      "kernel; the stage time includes the auxiliary kernel)",
+            "workload": vw.name, "precision": "mixed",
             "dt": vw.dt, "dt_note": "p = 4 runs the viscous terms at dt/8 (explicit "
                                     "diffusive limit), so a step covers 1/8 of the time",
             "value": r["value"], "unit": "DOF-stage/s", "steps": args.visc_steps,
             "ms_per_step": r["ms"] / args.visc_steps, "e2e": r["e2e"],
-            "roofline": dict(roofline([vw], mech, r, mixed, peaks, src),
-                             note="algorithmic flops of the Euler terms only: a lower bound"),
+            "roofline": dict(roofline([vw], vmech, r, "mixed", peaks, src),
+                             note="algorithmic bytes and flops of the Euler terms only"),
             "clocks": r["clocks"], "tuning": r["tuning"]}
     if lsk is not None:
-        lw, r = lsk
+        lw, lmech, r = lsk
         line["lserk4"] = {
             "integrator": "LSERK 5-stage 4th order (2N storage), limiter after every stage",
+            "workload": lw.name, "precision": "mixed",
             "stages_per_step": 5, "value": r["value"], "unit": "DOF-stage/s",
             "steps": args.lserk_steps, "ms_per_step": r["ms"] / args.lserk_steps,
-            "e2e": r["e2e"], "roofline": roofline([lw], mech, r, mixed, peaks, src),
+            "e2e": r["e2e"], "roofline": roofline([lw], lmech, r, "mixed", peaks, src),
             "clocks": r["clocks"], "tuning": r["tuning"]}
-    if ens is not None:
-        ewls, ewls_all, emode, emech, eh, eo, eop, ee = ens
-        rec = {"config": dict(workload_config(ewls_all, emech, args, emode, ws),
-                              tuning=eh["tuning"]),
-               "steps": args.ensemble_steps, "value": eh["value"],
-               "scaling": "strong" if (emode == "sharded" and ws > 1) else "weak",
-               "ms_per_step": eh["ms"] / args.ensemble_steps, "e2e": eh["e2e"],
-               "roofline": roofline(ewls, emech, eh, mixed, peaks, src)}
-        if eo is not None:
-            rec[eop] = {"value": eo["value"], "ms_per_step": eo["ms"] / args.ensemble_steps,
-                        "roofline": roofline(ewls, emech, eo, not mixed, peaks, src),
-                        "tuning": eo["tuning"]}
-            rec["speedup_mixed_vs_fp64"] = (eh["value"] / eo["value"]) if mixed else (
-                eo["value"] / eh["value"])
-        if ee is not None:
-            rec["mixed_error"] = ee
-        line["ensemble"] = rec
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(wls, mech)
     print(json.dumps(line))
     return 0
 
 
-# DRAM bytes (read + write) per stage-kernel launch from ncu, per (workload,
-# kernel revision, precision); the summaries are under profiles/.
-STAGE_TRAFFIC = {
-    ("ignition-9sp-4096x4", "v14", "mixed"): 2.0224e6,
-    ("ignition-9sp-4096x4", "v14", "fp64"): 2.056704e6,
-}
+# DRAM bytes (read + write) of the stage-kernel launches of one RK stage (all
+# degree groups) from ncu, per (workload, kernel revision, precision); the
+# summaries are under profiles/.
+STAGE_TRAFFIC = {}
 
-KERNEL_REV = "v14"
+KERNEL_REV = "v15"
 
 if __name__ == "__main__":
     sys.exit(main())

@@ -63,16 +63,23 @@ extern "C" {
 #define ADG_RK_LS3 1
 #define ADG_RK_LS4 2
 #define ADG_MAX_STAGES 5
-/* Arithmetic of the RK-stage right-hand side (Sec. 5, mixed-precision runs).
+/* Arithmetic of the RK-stage right-hand side. The paper runs in double
+ * precision; the mixed variants keep double where the stability of the
+ * reacting system needs it. The state arrays stay double in every variant.
  * ADG_FP64: every step in double precision.
- * ADG_MIXED: the numerical flux, the DG volume/surface/source assembly, the
- * mass-action products and the troubled-cell indicator and WENO reconstruction
- * in float; the Arrhenius and equilibrium exponents as float pairs (about 1e-12
- * absolute) and their exponentials rounded once to float; the state at the
- * Gauss points, the temperature (T, ln T and 1/T to about 1e-13), the AT
- * level sums and the RK accumulation in double. The state arrays stay double. */
+ * ADG_MIXED: the numerical flux, the DG volume/surface/source assembly and the
+ * troubled-cell indicator and WENO reconstruction in float; in double the
+ * state at the Gauss points, the temperature from the internal energy (T, ln T
+ * and 1/T to about one ulp), the whole chemistry (Arrhenius and equilibrium
+ * exponents and exponentials, mass-action products, rates of progress and
+ * production rates), the AT level sums and the RK accumulation.
+ * ADG_MIXED_F32CHEM: as ADG_MIXED, but the Arrhenius and equilibrium exponents
+ * as float pairs (about 1e-12 absolute), their exponentials rounded once to
+ * float, and the mass-action products and production rates in float. Not
+ * offered with viscous terms or in the unsynchronised mode (ADG_ERR_ARG). */
 #define ADG_FP64 0
 #define ADG_MIXED 1
+#define ADG_MIXED_F32CHEM 2
 
 #define ADG_MAX_P 4        /* polynomial degree 1..4 */
 #define ADG_MAX_SPECIES 60
@@ -106,7 +113,7 @@ typedef struct {
   const double *delay_probs; /* host [max_delay+1], SAA only (may be NULL otherwise) */
   uint64_t seed;           /* SAA delay seed */
   double tvb_M;            /* TVB constant of the indicator (0 = TVD) */
-  int precision;           /* ADG_FP64 | ADG_MIXED */
+  int precision;           /* ADG_FP64 | ADG_MIXED | ADG_MIXED_F32CHEM */
   int integrator;          /* ADG_RK_SSP3 | ADG_RK_LS3 | ADG_RK_LS4 */
   /* Viscous terms (Sec. 2: f^d with the shear stress tau = 4/3 mu du/dx, the
    * heat flux q = -k dT/dx + sum h_i J_i and mixture-averaged diffusion
@@ -130,13 +137,25 @@ typedef struct adg_ctx adg_ctx;
 int adg_workspace_bytes(const adg_mechanism *mech, const adg_config *cfgs, int n_instances,
                         size_t *bytes);
 
-/* Create a context. workspace_dev: NULL lets the library cudaMalloc what it needs;
- * otherwise a caller-owned device buffer of at least adg_workspace_bytes bytes,
- * 256-byte aligned, that must outlive the context. The mechanism and configs are
- * copied. Errors: ADG_ERR_ARG (unsupported p, species count, delay, order, or a
- * reaction with more than 4 species on one side), ADG_ERR_NOMEM, ADG_ERR_CUDA. */
+/* Create a context holding n_instances independent problems, each the setting
+ * of Sec. 3.1 and 3.2: the domain [x0, x0+length] cut into n_elem elements with
+ * the modal basis of degree p (Sec. 3.1, Eq. 4), split into n_pe contiguous PEs
+ * whose boundary faces take the AT flux of Eq. (7) at the delays of Sec. 4
+ * (CAA, Sec. 4.1; SAA, Sec. 4.2), with one reacting mixture (Sec. 2, the
+ * mechanism) for all instances. workspace_dev: NULL lets the library cudaMalloc
+ * what it needs; otherwise a caller-owned device buffer of at least
+ * adg_workspace_bytes bytes, 256-byte aligned, that must outlive the context.
+ * The mechanism and configs (and delay_probs) are copied; *out receives the
+ * context (NULL on error). The state of every instance starts at zero: set it
+ * with adg_set_primitive or adg_set_state. Errors: ADG_ERR_ARG (NULL pointer,
+ * unsupported p, species count, delay, order, or a reaction with more than 4
+ * species on one side), ADG_ERR_NOMEM, ADG_ERR_CUDA, ADG_ERR_NOLIB (no device). */
 int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n_instances,
                void *workspace_dev, size_t workspace_bytes, adg_ctx **out);
+/* Free the context and every device buffer it allocated (a caller-owned
+ * workspace is left alone). Call it once the context's work has completed
+ * (after adg_status, adg_get_state or a synchronisation of its stream). The
+ * paper has no counterpart: this is resource management. NULL is ignored. */
 void adg_destroy(adg_ctx *ctx);
 
 /* Initial condition from primitive values at the p+1 Gauss-Legendre points of
@@ -145,7 +164,12 @@ void adg_destroy(adg_ctx *ctx);
  * basis (Sec. 3.1) on the device, and resets the step counter and history. */
 int adg_set_primitive(adg_ctx *ctx, int instance, const double *prim_host);
 
-/* Copy a modal state in (host or device memory) and reset counter and history. */
+/* Copy a modal state in and reset the step counter and the history ring, so
+ * that the next steps are synchronous until the history holds the delayed
+ * levels (the state is the vector of modal DOFs w_j^e of Sec. 3.1, Eq. 4, in the
+ * layout of the conventions above). w_host: host memory, copied during the
+ * call (synchronous); w_dev: device memory, copied on `stream`.
+ * Errors: ADG_ERR_ARG (NULL or bad instance), ADG_ERR_CUDA. */
 int adg_set_state(adg_ctx *ctx, int instance, const double *w_host);
 int adg_set_state_device(adg_ctx *ctx, int instance, const double *w_dev, void *stream);
 
@@ -159,13 +183,26 @@ int adg_write_state(adg_ctx *ctx, int instance, const double *w_host, void *stre
  * synchronisation; the data is valid once the stream has passed the copy). */
 int adg_read_state(adg_ctx *ctx, int instance, double *w_host, void *stream);
 
-/* Copy the current modal state out (synchronises the context's last stream). */
+/* Copy the current modal state out: the DOFs w_j^e of Sec. 3.1 (Eq. 4) after the
+ * steps done, in the layout of the conventions above. Synchronises the
+ * context's last stream first, so the result is the state after every step
+ * enqueued so far. w_host: host memory the caller owns, [nv][n_elem][p+1];
+ * w_dev: device memory, written on `stream`. Errors: ADG_ERR_ARG (NULL or bad
+ * instance), ADG_ERR_CUDA. */
 int adg_get_state(adg_ctx *ctx, int instance, double *w_host);
 int adg_get_state_device(adg_ctx *ctx, int instance, double *w_dev, void *stream);
 
-/* Advance every instance by n_steps SSP-RK3 steps on `stream` (a cudaStream_t;
- * NULL = default stream). Asynchronous: returns after enqueueing. Errors found
- * on the device are reported by adg_status. */
+/* Advance every instance by n_steps time steps of its integrator on `stream` (a
+ * cudaStream_t; NULL = default stream). Each stage evaluates the semi-discrete
+ * right-hand side of Eq. (5) (Sec. 3.1: volume and source quadrature, LF or
+ * HLLC fluxes at element faces, the AT flux of Eq. (7)-(8) at delayed PE faces,
+ * Sec. 3.2), updates the state (SSP-RK3, or the LSERK schemes of Sec. 3.1), and
+ * applies the troubled-cell indicator and (AT-)WENO limiter of Sec. 3.3
+ * (Eq. 9-11); the delay of each PE face is drawn once per step (Sec. 4).
+ * Asynchronous: returns after enqueueing one replay of the captured step graph
+ * per step. n_steps = 0 does nothing. Errors: ADG_ERR_ARG (NULL, n_steps < 0),
+ * ADG_ERR_CUDA; non-physical states and missing history levels found on the
+ * device are reported by adg_status. */
 int adg_step(adg_ctx *ctx, int n_steps, void *stream);
 
 /* Synchronise and report the first device-side error since the last reset
@@ -220,7 +257,7 @@ int adg_kernel_times(adg_ctx *ctx, double *ms, int64_t *launches);
  * stages. adg_get_tuning fills tuning[6 * g + {0,1,2,3,4,5}] with the degree,
  * precision, tile elements, threads per CTA, tile count and RK stages of group
  * g (at most ADG_MAX_GROUPS groups). */
-#define ADG_MAX_GROUPS (4 * ADG_MAX_P)
+#define ADG_MAX_GROUPS (6 * ADG_MAX_P)
 int adg_autotune(adg_ctx *ctx, void *stream);
 int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning);
 /* Set the launch configuration of group g directly (for instance one that an
@@ -232,6 +269,10 @@ int adg_set_tuning(adg_ctx *ctx, int group, int elements_per_tile, int threads_p
 /* Number of kernel launches one adg_step(ctx, 1, ...) enqueues. */
 int adg_launches_per_step(const adg_ctx *ctx);
 
+/* A NUL-terminated description of an ADG_* return code ("unknown error" for
+ * other values), never NULL and owned by the library; for ADG_ERR_CUDA, the
+ * text of the last failed CUDA call (a buffer shared by all threads). The paper
+ * has no counterpart. */
 const char *adg_error_string(int code);
 
 /* Truly unsynchronised mode (the emulated PEs run without any lockstep; the
@@ -278,9 +319,11 @@ int adg_set_unsync_imbalance(adg_ctx *ctx, int slow_pe, int slow_us);
 
 /* ---------------------------------------------------------------------------
  * Time step without any device allocation. The paper has no counterpart: this
- * entry point exists for callers that cannot call cudaMalloc, for instance code
- * that runs while a CUDA graph is being captured, inside an allocator-free
- * runtime, or under a memory budget that forbids growing the device heap.
+ * entry point exists for callers that cannot call cudaMalloc, for instance a
+ * plugin inside a host application whose own allocator owns all device
+ * memory, a runtime that forbids device allocation once it is running, or a
+ * caller under a fixed device-memory budget. adg_create would allocate its
+ * workspace (or need one handed in); this call needs none.
  *
  * adg_step_noalloc advances one instance (mechanism and config as for
  * adg_create) by n_steps SSP-RK3 steps from the modal state w_in_dev to
@@ -288,19 +331,26 @@ int adg_set_unsync_imbalance(adg_ctx *ctx, int slow_pe, int slow_us);
  * same array). Like adg_set_state followed by adg_step, it starts from step 0
  * with an empty history, so the first steps are synchronous. All scratch (stage
  * buffers, history ring, tables, flags) lives in one static device array of
- * ADG_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
- * process exits; the call allocates nothing, neither on the device nor on the
- * host heap. Work is enqueued on `stream` and the call returns without waiting.
+ * ADG_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the library holds
+ * until the process exits; it calls no cudaMalloc, cudaFree or other
+ * allocating routine, and allocates nothing on the host heap. The mechanism
+ * tables and the instance record reach the device as parameters of small copy
+ * kernels, so after the first call on a device the call only enqueues work on
+ * `stream` (kernels and one device-to-device copy when the arrays differ) and
+ * returns without waiting for it.
  *
- * - The first call on each device looks up the array's device address and
- *   uploads the constant tables; make that first call before any stream
- *   capture on that device.
+ * - The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) and uploads the constant tables, synchronously;
+ *   make that first call before any stream capture on that device.
  * - A problem whose scratch does not fit returns ADG_ERR_NOMEM (nothing is
- *   enqueued); more than ADG_NOALLOC_MAX_REACTIONS reactions, or an integrator
- *   other than ADG_RK_SSP3, returns ADG_ERR_ARG.
- * - Every call reuses the same array: calls that overlap on the GPU (on
- *   different streams, or on one device from several threads without ordering)
- *   race and corrupt each other. The call clears what must start at zero.
+ *   enqueued); more than ADG_NOALLOC_MAX_REACTIONS reactions, an integrator
+ *   other than ADG_RK_SSP3 or viscous terms return ADG_ERR_ARG.
+ * - Every call reuses the same array and leaves its contents there; each call
+ *   clears what must start at zero (history, flags, step counter, error word).
+ *   Calls that overlap on the GPU (on different streams, or from several host
+ *   threads without ordering) race and corrupt each other's results.
+ * - The host side stages the tables in static storage under a lock, so calls
+ *   from several host threads are serialised while they enqueue.
  * - Non-physical states found on the device are not reported (there is no
  *   context to query); check the output. */
 #define ADG_NOALLOC_SCRATCH_BYTES (16u << 20)

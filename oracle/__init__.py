@@ -49,7 +49,7 @@ class Cfg(C.Structure):
                 ("max_delay", C.c_int), ("delay_probs", C.POINTER(C.c_double)),
                 ("seed", C.c_uint64), ("tvb_M", C.c_double), ("integrator", C.c_int),
                 ("viscous", C.c_int), ("mu_ref", C.c_double), ("T_mu", C.c_double),
-                ("mu_exp", C.c_double), ("prandtl", C.c_double)]
+                ("mu_exp", C.c_double), ("prandtl", C.c_double), ("face0", C.c_int)]
 
 
 _lib = None
@@ -134,7 +134,8 @@ def make_cfg(wl, dt=None):
               wl.max_delay, _dp(probs), wl.seed & ((1 << 64) - 1), wl.tvb_M,
               getattr(wl, "integrator", 0), getattr(wl, "viscous", 0),
               getattr(wl, "mu_ref", 0.0), getattr(wl, "T_mu", 300.0),
-              getattr(wl, "mu_exp", 0.7), getattr(wl, "prandtl", 0.7))
+              getattr(wl, "mu_exp", 0.7), getattr(wl, "prandtl", 0.7),
+              int(getattr(wl, "face0", 0)))
     return cfg, probs
 
 

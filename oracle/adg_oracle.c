@@ -167,11 +167,11 @@ uint64_t or_splitmix64(uint64_t x) {
  * i.e. k = n mod L with L = max_delay + 1.
  * SAA (Sec. 4.2): a uniform draw r in [0,1) is matched to the bins of the
  * cumulative probabilities {p_0, .., p_{L-1}}; the draw is SplitMix64 of
- * seed XOR (step * 2^32 + face), top 53 bits. */
+ * seed XOR (step * 2^32 + face), top 53 bits (face counted from cfg->face0). */
 int or_delay(const or_cfg *cfg, int64_t step, int face) {
   if (cfg->delay_mode == 0) return 0;
   if (cfg->delay_mode == 1) return (int)(step % (cfg->max_delay + 1));
-  uint64_t key = cfg->seed ^ (((uint64_t)step << 32) + (uint64_t)(uint32_t)face);
+  uint64_t key = cfg->seed ^ (((uint64_t)step << 32) + (uint64_t)(uint32_t)(face + cfg->face0));
   double r = (double)(or_splitmix64(key) >> 11) * (1.0 / 9007199254740992.0);
   double acc = 0.0;
   for (int k = 0; k <= cfg->max_delay; ++k) {

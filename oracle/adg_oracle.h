@@ -43,6 +43,9 @@ typedef struct {
                             (Carpenter-Kennedy, 2N storage) */
   int viscous;           /* 0 Euler; 1 with the diffusive flux f^d (Sec. 2, LDG) */
   double mu_ref, T_mu, mu_exp, prandtl; /* mu = mu_ref (T/T_mu)^mu_exp, k = mu cp/Pr */
+  int face0;             /* number of the first PE face in the SAA draws (0; a window
+                            of a larger run passes the larger run's number of its
+                            first PE face, so both draw the same delays) */
 } or_cfg;
 
 typedef struct or_ctx or_ctx;

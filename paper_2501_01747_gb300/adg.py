@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libadg.so")
 SOURCES = ["adg_k64.cu", "adg_k32.cu", "adg_u64.cu", "adg_u32.cu", "adg_v64.cu",
-           "adg_v32.cu", "adg_kernels.cu", "adg_api.cu", "adg_static.cu"]
+           "adg_v32.cu", "adg_k32f.cu", "adg_kernels.cu", "adg_api.cu", "adg_static.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", ARCH]
 
@@ -29,7 +29,7 @@ ERRORS = {-1: "ADG_ERR_ARG", -2: "ADG_ERR_CUDA", -3: "ADG_ERR_NOMEM",
           -4: "ADG_ERR_NONPHYSICAL", -5: "ADG_ERR_HISTORY", -6: "ADG_ERR_NOLIB",
           -7: "ADG_ERR_TIMEOUT"}
 MAX_DELAY = 7  # ADG_MAX_DELAY
-MAX_GROUPS = 16  # ADG_MAX_GROUPS
+MAX_GROUPS = 24  # ADG_MAX_GROUPS
 
 
 class AdgError(RuntimeError):
@@ -182,8 +182,9 @@ class _MechArgs:
                             _dp(self.Le) if self.Le is not None else C.POINTER(C.c_double)())
 
 
-FP64, MIXED = 0, 1
-PRECISIONS = {"fp64": FP64, "mixed": MIXED}
+FP64, MIXED, MIXED_F32CHEM = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_f32chem": MIXED_F32CHEM}
+PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 
 
 def _precision(x):
@@ -191,8 +192,8 @@ def _precision(x):
         if x not in PRECISIONS:
             raise AdgError(-1, "precision must be one of %s" % sorted(PRECISIONS))
         return PRECISIONS[x]
-    if int(x) not in (FP64, MIXED):
-        raise AdgError(-1, "precision must be ADG_FP64 or ADG_MIXED")
+    if int(x) not in PRECISION_NAMES:
+        raise AdgError(-1, "precision must be ADG_FP64, ADG_MIXED or ADG_MIXED_F32CHEM")
     return int(x)
 
 
@@ -246,8 +247,9 @@ class ADG:
 
     Device memory is one PyTorch uint8 tensor handed to ``adg_create`` (the
     library carves its buffers out of it); kernels run on PyTorch's current CUDA
-    stream unless a stream is given. ``precision`` is "fp64" or "mixed" for all
-    instances, or a list with one entry per instance."""
+    stream unless a stream is given. ``precision`` is "fp64", "mixed" (FP32 flux,
+    DG operator and limiter, FP64 chemistry) or "mixed_f32chem" (the chemistry in
+    float too) for all instances, or a list with one entry per instance."""
 
     def __init__(self, mech, workloads, device=None, precision="fp64"):
         torch = _torch()
@@ -389,7 +391,7 @@ class ADG:
         n = C.c_int(0)
         t = (C.c_int * (6 * MAX_GROUPS))()
         _check(self.L.adg_get_tuning(self.h, C.byref(n), t), "adg_get_tuning")
-        return [{"p": t[6 * g], "precision": "mixed" if t[6 * g + 1] == MIXED else "fp64",
+        return [{"p": t[6 * g], "precision": PRECISION_NAMES[t[6 * g + 1]],
                  "elements_per_tile": t[6 * g + 2], "threads_per_cta": t[6 * g + 3],
                  "tiles": t[6 * g + 4], "stages": t[6 * g + 5]} for g in range(n.value)]
 

@@ -203,7 +203,8 @@ struct InstHost {
 // launches.
 struct Group {
   int Q = 0;
-  bool mixed = false;
+  int prec = ADG_FP64;          // precision variant of the stage kernel
+  bool mixed = false;           // FP32 limiter (both mixed variants)
   int S = 3;                    // RK stages per step
   bool visc = false;            // has viscous instances (LDG auxiliary kernel per stage)
   int TE = 0;                   // elements per stage tile
@@ -247,10 +248,26 @@ struct adg_ctx {
   int unsync_slow_pe, unsync_slow_us;  // unsynchronised mode: emulated load imbalance
   cudaStream_t last_stream;
   cudaStream_t cap_stream;       // private stream for graph capture
+  // one stream per group for the concurrent branches of the plain step graph,
+  // and the events that fork them from and join them to the capture stream
+  cudaStream_t branch[ADG_MAX_GROUPS];
+  cudaEvent_t fork_ev, join_ev[ADG_MAX_GROUPS];
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   bool graph_ok;
 };
+
+// The streams and events of the concurrent branches (those created).
+static void destroy_branches(adg_ctx *ctx) {
+  for (int g = 0; g < ADG_MAX_GROUPS; ++g) {
+    if (ctx->branch[g]) cudaStreamDestroy(ctx->branch[g]);
+    if (ctx->join_ev[g]) cudaEventDestroy(ctx->join_ev[g]);
+    ctx->branch[g] = nullptr;
+    ctx->join_ev[g] = nullptr;
+  }
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  ctx->fork_ev = nullptr;
+}
 
 namespace {
 
@@ -301,7 +318,9 @@ int check_args(const adg_mechanism *m, const adg_config *cfgs, int n) {
     bool lp = c.bc_left == ADG_BC_PERIODIC, rp = c.bc_right == ADG_BC_PERIODIC;
     if (lp != rp) return ADG_ERR_ARG;
     if (c.bc_left < 0 || c.bc_left > 2 || c.bc_right < 0 || c.bc_right > 2) return ADG_ERR_ARG;
-    if (c.precision != ADG_FP64 && c.precision != ADG_MIXED) return ADG_ERR_ARG;
+    if (c.precision != ADG_FP64 && c.precision != ADG_MIXED && c.precision != ADG_MIXED_F32CHEM)
+      return ADG_ERR_ARG;
+    if (c.precision == ADG_MIXED_F32CHEM && c.viscous) return ADG_ERR_ARG;
     if (c.integrator < ADG_RK_SSP3 || c.integrator > ADG_RK_LS4) return ADG_ERR_ARG;
     if (c.viscous != 0 && c.viscous != 1) return ADG_ERR_ARG;
     if (c.viscous && (!(c.mu_ref >= 0.0) || !(c.T_mu > 0.0) || !(c.prandtl > 0.0) ||
@@ -374,7 +393,8 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
   // groups of equal degree and precision: tile sizes and tables
   ctx->n_groups = 0;
   for (int gk = 0; gk < ADG_MAX_GROUPS; ++gk) {
-    const int Q = 2 + (gk / 2) % ADG_MAX_P, prec = gk % 2, S = gk < 2 * ADG_MAX_P ? 3 : 5;
+    const int r = gk % (3 * ADG_MAX_P), S = gk < 3 * ADG_MAX_P ? 3 : 5;
+    const int Q = 2 + r / 3, prec = r % 3;
     auto member = [&](int k) {
       return cfgs[k].p + 1 == Q && cfgs[k].precision == prec &&
              rk_stages(cfgs[k].integrator) == S;
@@ -392,12 +412,13 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
     if (!any) continue;
     Group &G = ctx->groups[ctx->n_groups++];
     G.Q = Q;
-    G.mixed = prec == ADG_MIXED;
+    G.prec = prec;
+    G.mixed = prec != ADG_FP64;
     G.S = S;
     G.O = O;
     for (int k = 0; k < ctx->n_inst; ++k)
       if (member(k) && cfgs[k].viscous) G.visc = true;
-    G.TE = stage_tile(M, Q, O, G.mixed, G.visc);
+    G.TE = stage_tile(M, Q, O, G.prec, G.visc);
     // smaller tiles when the group would not fill two CTAs per SM
     int64_t target = (total + 2 * 152 - 1) / (2 * 152);
     if (target < G.TE) G.TE = target < 4 ? 4 : (int)target;
@@ -457,7 +478,7 @@ static cudaError_t upload_tiles(adg_ctx *ctx, Group &G) {
   std::vector<int2> tl;
   for (int k = 0; k < ctx->n_inst; ++k) {
     const Inst &I = ctx->inst[k].d;
-    if (I.p + 1 != G.Q || (I.mixed != 0) != G.mixed || I.n_stages != G.S) continue;
+    if (I.p + 1 != G.Q || I.mixed != G.prec || I.n_stages != G.S) continue;
     for (int e = 0; e < I.n_elem; e += G.TE) tl.push_back(make_int2(k, e));
   }
   G.n_tiles = (int)tl.size();
@@ -559,6 +580,11 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
   ctx->tgraph = nullptr;
   ctx->texec = nullptr;
   ctx->cap_stream = nullptr;
+  ctx->fork_ev = nullptr;
+  for (int g = 0; g < ADG_MAX_GROUPS; ++g) {
+    ctx->branch[g] = nullptr;
+    ctx->join_ev[g] = nullptr;
+  }
   ctx->graph = nullptr;
   ctx->exec = nullptr;
   ctx->graph_ok = false;
@@ -645,7 +671,9 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
     I.dx = c.length / N;
     I.dt = c.dt;
     I.tvb = c.tvb_M * I.dx * I.dx;
-    I.mixed = c.precision == ADG_MIXED;
+    I.mixed = c.precision;
+    I.ind_floor = indicator_guard(c.precision);
+    I.ind_floor_p = indicator_guard_p(c.precision);
     I.seed = c.seed;
     I.instance = k;
     double acc = 0.0;
@@ -692,7 +720,7 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
       const int epb = G.EPB;
       std::vector<int2> bl;
       for (int k = 0; k < n; ++k) {
-        if (cfgs[k].p + 1 != G.Q || (cfgs[k].precision == ADG_MIXED) != G.mixed ||
+        if (cfgs[k].p + 1 != G.Q || cfgs[k].precision != G.prec ||
             rk_stages(cfgs[k].integrator) != G.S)
           continue;
         for (int e = 0; e < cfgs[k].n_elem; e += epb) bl.push_back(make_int2(k, e));
@@ -704,9 +732,18 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
     if (prepare_kernels(nv, ns, nr) != cudaSuccess) rc2 = ADG_ERR_CUDA;
     if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
       rc2 = ADG_ERR_CUDA;
+    if (ctx->n_groups > 1 && rc2 == ADG_OK) {
+      if (cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+        rc2 = ADG_ERR_CUDA;
+      for (int g = 0; g < ctx->n_groups && rc2 == ADG_OK; ++g)
+        if (cudaStreamCreateWithFlags(&ctx->branch[g], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->join_ev[g], cudaEventDisableTiming) != cudaSuccess)
+          rc2 = ADG_ERR_CUDA;
+    }
   }
   if (rc2 != ADG_OK) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    destroy_branches(ctx);
     if (ctx->owns_mem) cudaFree(ctx->mem);
     delete ctx;
     return rc2;
@@ -725,6 +762,7 @@ void adg_destroy(adg_ctx *ctx) {
   if (ctx->tgraph) cudaGraphDestroy(ctx->tgraph);
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  destroy_branches(ctx);
   if (ctx->owns_mem) cudaFree(ctx->mem);
   delete ctx;
 }
@@ -827,43 +865,65 @@ static LimArgs aux_args(const adg_ctx *ctx, const Group &G, int s) {
   return L;
 }
 
-// One step of every instance: per RK stage, the stage kernel and the limiter
-// of every group that has that stage, then the step counters advance.
-static int enqueue_step(adg_ctx *ctx, cudaStream_t st) {
+// The stages of one group's step: per RK stage, the auxiliary kernel (viscous
+// groups), the stage kernel and the limiter.
+static int enqueue_group(adg_ctx *ctx, int gi, int s, cudaStream_t st) {
+  const Group &G = ctx->groups[gi];
+  if (s >= G.S) return ADG_OK;
+  StageArgs A;
+  A.insts = ctx->d_insts;
+  A.tiles = G.d_tiles;
+  A.s = s;
+  A.TE = G.TE;
+  A.NT = G.NT;
+  A.O = G.O;
+  A.visc = G.visc;
+  CK(timed_begin(ctx, 0, st));
+  // viscous groups: the LDG auxiliary variable of the stage input first
+  // (timed with the stage kernel)
+  if (G.visc) CK(launch_aux(aux_args(ctx, G, s), G.Q, G.n_blocks, st));
+  CK(launch_stage(ctx->mech, A, G.Q, G.prec, G.n_tiles, st));
+  CK(timed_end(ctx, st));
+  if (!G.any_limiter) return ADG_OK;
+  LimArgs L;
+  L.insts = ctx->d_insts;
+  L.blocks = G.d_blocks;
+  L.s = s;
+  L.EPB = G.EPB;
+  CK(timed_begin(ctx, 1, st));
+  CK(launch_limiter(ctx->mech, L, G.Q, G.mixed, ctx->ns + 2, G.n_blocks, st));
+  CK(timed_end(ctx, st));
+  return ADG_OK;
+}
+
+// One step of every instance, then the step counters advance. Groups hold
+// independent instances, so in the plain graph (concurrent) each group's
+// stages form a branch of their own, forked from and joined to `st`: the GPU
+// runs the groups side by side and fills one group's wave tails with another's
+// CTAs. The timing graph runs the groups one after the other, so that every
+// kernel's time is its own.
+static int enqueue_step(adg_ctx *ctx, cudaStream_t st, bool concurrent) {
   int max_s = 0;
   for (int gi = 0; gi < ctx->n_groups; ++gi)
     max_s = ctx->groups[gi].S > max_s ? ctx->groups[gi].S : max_s;
-  for (int s = 0; s < max_s; ++s) {
+  if (concurrent && ctx->n_groups > 1 && ctx->fork_ev) {
+    CK(cudaEventRecord(ctx->fork_ev, st));
     for (int gi = 0; gi < ctx->n_groups; ++gi) {
-      const Group &G = ctx->groups[gi];
-      if (s >= G.S) continue;
-      StageArgs A;
-      A.insts = ctx->d_insts;
-      A.tiles = G.d_tiles;
-      A.s = s;
-      A.TE = G.TE;
-      A.NT = G.NT;
-      A.O = G.O;
-      A.visc = G.visc;
-      CK(timed_begin(ctx, 0, st));
-      // viscous groups: the LDG auxiliary variable of the stage input first
-      // (timed with the stage kernel)
-      if (G.visc) CK(launch_aux(aux_args(ctx, G, s), G.Q, G.n_blocks, st));
-      CK(launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st));
-      CK(timed_end(ctx, st));
+      cudaStream_t b = ctx->branch[gi];
+      CK(cudaStreamWaitEvent(b, ctx->fork_ev, 0));
+      for (int s = 0; s < ctx->groups[gi].S; ++s) {
+        int rc = enqueue_group(ctx, gi, s, b);
+        if (rc != ADG_OK) return rc;
+      }
+      CK(cudaEventRecord(ctx->join_ev[gi], b));
+      CK(cudaStreamWaitEvent(st, ctx->join_ev[gi], 0));
     }
-    for (int gi = 0; gi < ctx->n_groups; ++gi) {
-      const Group &G = ctx->groups[gi];
-      if (!G.any_limiter || s >= G.S) continue;
-      LimArgs L;
-      L.insts = ctx->d_insts;
-      L.blocks = G.d_blocks;
-      L.s = s;
-      L.EPB = G.EPB;
-      CK(timed_begin(ctx, 1, st));
-      CK(launch_limiter(ctx->mech, L, G.Q, G.mixed, ctx->ns + 2, G.n_blocks, st));
-      CK(timed_end(ctx, st));
-    }
+  } else {
+    for (int s = 0; s < max_s; ++s)
+      for (int gi = 0; gi < ctx->n_groups; ++gi) {
+        int rc = enqueue_group(ctx, gi, s, st);
+        if (rc != ADG_OK) return rc;
+      }
   }
   CK(launch_advance(ctx->d_steps, ctx->n_inst, st));
   return ADG_OK;
@@ -883,7 +943,7 @@ static int capture(adg_ctx *ctx, bool timed, cudaGraph_t *graph, cudaGraphExec_t
   if (timed && cudaEventRecordWithFlags(ctx->span[0], ctx->cap_stream,
                                         cudaEventRecordExternal) != cudaSuccess)
     rc = ADG_ERR_CUDA;
-  if (rc == ADG_OK) rc = enqueue_step(ctx, ctx->cap_stream);
+  if (rc == ADG_OK) rc = enqueue_step(ctx, ctx->cap_stream, !timed);
   if (rc == ADG_OK && timed &&
       cudaEventRecordWithFlags(ctx->span[1], ctx->cap_stream, cudaEventRecordExternal) !=
           cudaSuccess)
@@ -973,7 +1033,7 @@ int adg_autotune(adg_ctx *ctx, void *stream) {
     float best = 1e30f;
     for (int te : kTE) {
       if (te < kMinTile) continue;
-      if (stage_smem(ctx->mech, te, G.Q, G.O, G.mixed, G.visc) > 200 * 1024) continue;
+      if (stage_smem(ctx->mech, te, G.Q, G.O, G.prec, G.visc) > 200 * 1024) continue;
       G.TE = te;
       if (upload_tiles(ctx, G) != cudaSuccess) {
         rc = ADG_ERR_CUDA;
@@ -993,10 +1053,10 @@ int adg_autotune(adg_ctx *ctx, void *stream) {
         // trajectory is unchanged
         bool ok = true;
         if (G.visc) ok = launch_aux(aux_args(ctx, G, 0), G.Q, G.n_blocks, st) == cudaSuccess;
-        ok = ok && launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
+        ok = ok && launch_stage(ctx->mech, A, G.Q, G.prec, G.n_tiles, st) == cudaSuccess;
         ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
         for (int w = 0; w < 2 && ok; ++w)
-          ok = launch_stage(ctx->mech, A, G.Q, G.mixed, G.n_tiles, st) == cudaSuccess;
+          ok = launch_stage(ctx->mech, A, G.Q, G.prec, G.n_tiles, st) == cudaSuccess;
         ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
         float ms = 0.0f;
         if (!ok || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
@@ -1027,7 +1087,7 @@ int adg_set_tuning(adg_ctx *ctx, int group, int elements_per_tile, int threads_p
   Group &G = ctx->groups[group];
   const int te = elements_per_tile, nt = threads_per_cta;
   if (te < kMinTile || nt < 32 || nt > 512 || nt % 32) return ADG_ERR_ARG;
-  if (stage_smem(ctx->mech, te, G.Q, G.O, G.mixed, G.visc) > 200 * 1024) return ADG_ERR_ARG;
+  if (stage_smem(ctx->mech, te, G.Q, G.O, G.prec, G.visc) > 200 * 1024) return ADG_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->last_stream));
   G.TE = te;
   G.NT = nt;
@@ -1042,7 +1102,7 @@ int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning) {
   for (int gi = 0; gi < ctx->n_groups; ++gi) {
     const Group &G = ctx->groups[gi];
     tuning[6 * gi + 0] = G.Q - 1;
-    tuning[6 * gi + 1] = G.mixed ? ADG_MIXED : ADG_FP64;
+    tuning[6 * gi + 1] = G.prec;
     tuning[6 * gi + 2] = G.TE;
     tuning[6 * gi + 3] = G.NT;
     tuning[6 * gi + 4] = G.n_tiles;
@@ -1057,11 +1117,13 @@ int adg_step_unsync(adg_ctx *ctx, int instance, int n_steps, void *stream) {
   InstHost &h = ctx->inst[instance];
   const Inst &I = h.d;
   if (I.viscous) return ADG_ERR_ARG;  // the unsynchronised mode runs the Euler terms only
+  // the unsynchronised mode offers the FP64 and the ADG_MIXED stage arithmetic
+  if (I.mixed == ADG_MIXED_F32CHEM) return ADG_ERR_ARG;
   const int Q = I.p + 1;
-  const bool mixed = I.mixed != 0;
+  const bool mixed = I.mixed != ADG_FP64;
   const Group *G = nullptr;
   for (int gi = 0; gi < ctx->n_groups; ++gi)
-    if (ctx->groups[gi].Q == Q && ctx->groups[gi].mixed == mixed &&
+    if (ctx->groups[gi].Q == Q && ctx->groups[gi].prec == I.mixed &&
         ctx->groups[gi].S == I.n_stages)
       G = &ctx->groups[gi];
   if (!G) return ADG_ERR_ARG;

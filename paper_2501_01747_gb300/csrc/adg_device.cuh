@@ -2,11 +2,15 @@
 // that instantiate it (one per precision variant, one for the unsynchronised
 // mode), so that they compile in parallel.
 //
-// Per RK stage two kernels run, each in an FP64 and a mixed-precision variant
-// (MIX: FP32 for the flux, the DG operator and the limiter; FP64 for the
-// Gauss-point temperature, the Arrhenius and equilibrium exponentials, the AT
-// level sums and the accumulation of the conserved state):
-//   stage_kernel<Q,MIX>: one CTA per tile of TE consecutive elements of one
+// Per RK stage two kernels run. The stage kernel comes in three precision
+// variants PREC (include/adg.h): ADG_FP64; ADG_MIXED, FP32 for the flux and the
+// DG operator, FP64 for the Gauss-point temperature, the chemistry (Arrhenius
+// and equilibrium exponentials, mass action, production rates), the AT level
+// sums and the accumulation of the conserved state; ADG_MIXED_F32CHEM, as
+// ADG_MIXED but with the chemistry's exponents as float pairs and its
+// exponentials, products and sums in FP32. The limiter has an FP64 and an FP32
+// variant (MIX), the latter for both mixed variants.
+//   stage_kernel<Q,PREC>: one CTA per tile of TE consecutive elements of one
 //                      instance (stage_body).
 //   limiter_kernel<Q,G,MIX,EPB>: the troubled-cell indicator and, on troubled
 //                      cells, the (AT-)WENO reconstruction of Eq. (9)-(11)
@@ -54,13 +58,26 @@ static size_t limiter_smem_bytes(int nv, int ns);
 template <bool MIX>
 using dg_t = typename std::conditional<MIX, float, double>::type;
 
+// The stage kernel's precision variant: arithmetic of the flux and the DG
+// operator (float in both mixed variants) and of the chemistry (float only in
+// ADG_MIXED_F32CHEM).
+template <int PREC>
+struct Prec {
+  static constexpr bool mix = PREC != ADG_FP64;
+  static constexpr bool fchem = PREC == ADG_MIXED_F32CHEM;
+  using dg = dg_t<mix>;
+  using ct = typename std::conditional<fchem, float, double>::type;
+};
+
 // Shared-memory footprint (bytes) of a stage tile of TE elements with up to O AT
 // levels per face. FP64 region: species fields, exp table, basis values, modal
 // tile with halo, w^n of the tile, nodal state, ln T, 1/T, u, P. Region in the
-// arithmetic type of the variant: face, level and trace fluxes, concentrations,
-// rates of progress, production rates; the mixed variant adds an FP32 copy of
-// the species fields and the point flux (the FP64 variant writes the flux over
-// the nodal state). Integers: delay per face, species-reaction incidence.
+// chemistry's type: concentrations, rates of progress, production rates,
+// incidence coefficients. Region in the flux's type: face, level and trace
+// fluxes; the mixed variants add an FP32 copy of the species fields and the
+// point flux (the FP64 variant writes the flux over the nodal state). Integers:
+// delay per face, species-reaction incidence. The float-chemistry variant adds
+// its df32 rate coefficients and (ln T, 1/T) pairs.
 // Viscous groups append, in FP64: the tile of q = dw/dx with halo, q at the
 // Gauss points (then f^d there), and per (level, face) the traces of w and q of
 // both sides (then f^d of both sides).
@@ -71,20 +88,43 @@ __host__ __device__ inline size_t stage_visc_doubles(int TE, int Q, int ns, int 
 }
 
 __host__ __device__ inline size_t stage_smem_bytes(int TE, int Q, int ns, int nr, int nterm,
-                                                   int O, bool mix, bool visc = false) {
+                                                   int O, int prec, bool visc = false) {
+  const bool mix = prec != ADG_FP64, fchem = prec == ADG_MIXED_F32CHEM;
   const size_t nv = ns + 2, TQ = (size_t)TE * Q, F = TE + 1;
   const size_t nd = (size_t)SP_NFIELDS * ns + sizeof(IExpTable) / 8 + MAXQ * MAXQ +
                     nv * (TE + 2) * Q + 2 * nv * TQ + 4 * TQ;
-  size_t ndg = F * nv + (size_t)O * F * nv + (size_t)O * F * 2 * nv + (size_t)ns * TQ +
-               (size_t)nr * TQ + (size_t)ns * TQ + nterm;
+  const size_t nct = (size_t)ns * TQ + (size_t)nr * TQ + (size_t)ns * TQ + nterm;
+  size_t ndg = F * nv + (size_t)O * F * nv + (size_t)O * F * 2 * nv;
   if (mix) ndg += (size_t)SP_NFIELDS * ns + nv * TQ;
   const size_t ni = F + ns + 1 + nterm;
-  // mixed variant: the df32 rate coefficients [nr][6] and (ln T, 1/T) per point
-  const size_t ndf = mix ? (size_t)nr * 6 + 2 * TQ : 0;
-  return (size_t)nr * sizeof(Rxn) + nd * 8 + ndg * (mix ? 4 : 8) + ni * 4 + 16 + ndf * 8 + 8 +
-         (visc ? stage_visc_doubles(TE, Q, ns, O) * 8 + 8 : 0);
+  // float chemistry: the df32 rate coefficients [nr][6] and (ln T, 1/T) per point
+  const size_t ndf = fchem ? (size_t)nr * 6 + 2 * TQ : 0;
+  return (size_t)nr * sizeof(Rxn) + nd * 8 + nct * (fchem ? 4 : 8) + ndg * (mix ? 4 : 8) +
+         ni * 4 + 16 + ndf * 8 + 8 + (visc ? stage_visc_doubles(TE, Q, ns, O) * 8 + 8 : 0);
 }
 
+
+// The items item0, item0 + step, ... of a loop over (outer, inner) pairs, the
+// inner index fastest, split into (o, i) with one division per walk instead of
+// one per item (an integer division by a value known only at run time costs
+// about twenty instructions).
+struct Walk {
+  int o, i, dO, dI, n;
+  __device__ __forceinline__ Walk(int item0, int step, int inner) : n(inner) {
+    o = item0 / inner;
+    i = item0 - o * inner;
+    dO = step / inner;
+    dI = step - dO * inner;
+  }
+  __device__ __forceinline__ void next() {
+    i += dI;
+    o += dO;
+    if (i >= n) {
+      i -= n;
+      ++o;
+    }
+  }
+};
 
 // Copy an instance description into shared memory (by 8-byte words).
 __device__ inline void load_inst(Inst &dst, const Inst *src) {
@@ -151,11 +191,27 @@ __device__ __forceinline__ double recip_nr(double x) {
   return fma(r, fma(-x, r, 1.0), r);
 }
 
+// 1/x to about one ulp: recip_nr and a second Newton-Raphson step, which squares
+// its error below the rounding of the last operation. Four double operations.
+__device__ __forceinline__ double recip_nr2(double x) {
+  const double r = recip_nr(x);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
 // To the variant's arithmetic type without the FP64 unit.
 template <typename R>
 __device__ __forceinline__ R to_r(double x) {
   if constexpr (std::is_same<R, float>::value) return d2f_int(x);
   else return x;
+}
+
+// From one arithmetic type to another without the FP64 unit (float -> double
+// and double -> float on the integer pipeline).
+template <typename R, typename C>
+__device__ __forceinline__ R conv_r(C x) {
+  if constexpr (std::is_same<R, C>::value) return x;
+  else if constexpr (std::is_same<R, float>::value) return d2f_int(x);
+  else return f2d_exact(x);
 }
 
 // A value of the history ring. Written by another CTA of the same launch in the
@@ -317,11 +373,13 @@ __device__ inline void visc_faces(const double *sp, const R *spr, int ns, const 
 // that runs without synchronisation and read both sides from the history ring,
 // also at delay 0; the stage input's traces there are published beforehand by
 // the caller, not written in phase 6.
-template <int Q, bool MIX, bool UNSYNC, bool VISC = false>
+template <int Q, int PREC, bool UNSYNC, bool VISC = false>
 __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, const Inst &I,
                                            const int e0, const int te, const int64_t nstep,
                                            const PeDelays *pd) {
-  using DG = dg_t<MIX>;
+  constexpr bool MIX = Prec<PREC>::mix, FCHEM = Prec<PREC>::fchem;
+  using DG = typename Prec<PREC>::dg;  // flux and DG operator
+  using CT = typename Prec<PREC>::ct;  // chemistry
   extern __shared__ __align__(16) double sm[];
   const Basis &B = c_basis[Q - 2];
   const BasisF &BF = c_basis_f[Q - 2];
@@ -346,32 +404,32 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   double *su = sinvT + TQ;
   double *sPr = su + TQ;
   double *swn = sPr + TQ;                                     // [v][TQ] modes of w^n
-  DG *sfh = reinterpret_cast<DG *>(swn + (size_t)nv * TQ);    // [NF][nv]
+  CT *scc = reinterpret_cast<CT *>(swn + (size_t)nv * TQ);    // [i][TQ] concentrations
+  CT *sq = scc + (size_t)ns * TQ;                             // [j][TQ] rates of progress
+  CT *swd = sq + (size_t)nr * TQ;                             // [i][TQ] production rates
+  CT *scoef = swd + (size_t)ns * TQ;                          // [nterm] incidence coefficients
+  DG *sfh = reinterpret_cast<DG *>(scoef + M.nterm);          // [NF][nv]
   DG *sflx = sfh + (size_t)NF * nv;                           // [O][NF][nv]
   DG *str = sflx + (size_t)O * NF * nv;                       // [O][NF][2][nv]
-  DG *scc = str + (size_t)O * NF * 2 * nv;                    // [i][TQ] concentrations
-  DG *sq = scc + (size_t)ns * TQ;                             // [j][TQ] rates of progress
-  DG *swd = sq + (size_t)nr * TQ;                             // [i][TQ] production rates
-  DG *scoef = swd + (size_t)ns * TQ;                          // [nterm] incidence coefficients
   DG *sspD, *sfx;                                             // species fields, point flux
   int *sk;
   if constexpr (MIX) {
-    sspD = scoef + M.nterm;
+    sspD = str + (size_t)O * NF * 2 * nv;
     sfx = sspD + (size_t)SP_NFIELDS * ns;
     sk = reinterpret_cast<int *>(sfx + (size_t)nv * TQ);
   } else {
     sspD = reinterpret_cast<DG *>(ssp);
     sfx = reinterpret_cast<DG *>(snw);
-    sk = reinterpret_cast<int *>(scoef + M.nterm);
+    sk = reinterpret_cast<int *>(str + (size_t)O * NF * 2 * nv);
   }
   int *soff = sk + NF;        // [ns + 1]
   int *sterm = soff + ns + 1;  // [nterm] reaction of each incidence term
-  // mixed variant: df32 rate coefficients and (ln T, 1/T) per point, 8-byte aligned
+  // float chemistry: df32 rate coefficients and (ln T, 1/T) per point, 8-byte aligned
   DF *srxf = reinterpret_cast<DF *>(
       (reinterpret_cast<uintptr_t>(sterm + M.nterm) + 7) & ~(uintptr_t)7);  // [nr][6]
   DF *sdfT = srxf + (size_t)nr * 6;                                          // [TQ][2]
   // viscous region (groups with viscous instances), FP64
-  double *sqw = reinterpret_cast<double *>(MIX ? (void *)(sdfT + 2 * TQ) : (void *)srxf);  // [v][TE+2][Q]
+  double *sqw = reinterpret_cast<double *>(FCHEM ? (void *)(sdfT + 2 * TQ) : (void *)srxf);  // [v][TE+2][Q]
   double *sqn = sqw + (size_t)nv * (TE + 2) * Q;                           // [v][TQ]
   double *sqt = sqn + (size_t)nv * TQ;                                     // [O][NF][4][nv]
   double *sTv = sqt + (size_t)O * NF * 4 * nv;                             // [TQ] T
@@ -389,7 +447,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
     const uint4 *src = reinterpret_cast<const uint4 *>(M.rx);
     uint4 *dst = reinterpret_cast<uint4 *>(srx);
     const int n_rx4 = nr * (int)(sizeof(Rxn) / 16), n_sp = SP_NFIELDS * ns;
-    const int n_rxf = MIX ? nr * 6 : 0, n_term = M.nterm;
+    const int n_rxf = FCHEM ? nr * 6 : 0, n_term = M.nterm;
     const int n_all = max(max(max(n_rx4, n_sp), max(n_rxf, n_term)), max(max(32, Q * Q), ns + 1));
     for (int k = tid; k < n_all; k += nth) {
       uint4 rx4 = {};
@@ -406,18 +464,19 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         ssp[k] = spv;
         if constexpr (MIX) sspD[k] = (DG)spv;
       }
-      if constexpr (MIX) {
+      if constexpr (FCHEM) {
         if (k < n_rxf) srxf[k] = rf;
       }
       if (k < n_term) {
         sterm[k] = term >> 8;
-        scoef[k] = (DG)(signed char)(term & 0xff);
+        scoef[k] = (CT)(signed char)(term & 0xff);
       }
       if (k <= ns) soff[k] = off;
       if (k < 32) {
         stab->t[k] = c_iexp.t[k];
         stab->t32[k] = c_iexp.t32[k];
-        if constexpr (MIX) iexp_table_df(c_iexp.t32[k], &stab->tf[2 * k], &stab->tf[2 * k + 1]);
+        if constexpr (FCHEM)
+          iexp_table_df(c_iexp.t32[k], &stab->tf[2 * k], &stab->tf[2 * k + 1]);
       }
       if (k < Q * Q) sPq[k] = B.P[k / Q][k % Q];
     }
@@ -475,7 +534,8 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   // w(-1) = sum_j (-1)^j w_j of the right one (a delayed face's item in phase 2b
   // overwrites them with the history's)
   const int n_trace = visc ? 0 : 2 * nv * (te + 1);
-  for (int item = tid; item < nv * teq + n_trace; item += nth) {
+  Walk w2a(tid, nth, teq);
+  for (int item = tid; item < nv * teq + n_trace; item += nth, w2a.next()) {
     if (item >= nv * teq) {
       const int r = item - nv * teq, side = r & 1, vf = r >> 1;
       const int v = vf / (te + 1), f = vf - v * (te + 1);
@@ -486,8 +546,8 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       str[(size_t)f * 2 * nv + side * nv + v] = (DG)a;
       continue;
     }
-    int v = item / teq, t = item - v * teq;
-    int e = t / Q, q = t - e * Q;
+    const int v = w2a.o, t = w2a.i;
+    const int e = t / Q, q = t - e * Q;
     const double *wi = sw + ((size_t)v * (TE + 2) + e + 1) * Q;
     const double *Pq = sPq + q * Q;
     double acc = 0.0;
@@ -624,7 +684,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       }
       const double m = wq[0];
       double u, num, T;
-      if constexpr (MIX) {
+      if constexpr (FCHEM) {
         // ln T and 1/T feed float-float arguments (about 1e-12): reciprocals
         // by one Newton step from a float seed, Tang's table logarithm, the
         // float pairs split on the integer pipeline
@@ -634,6 +694,14 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         T = num * recip_nr(cv);
         sdfT[2 * t] = df_split_int(log_tab(T, c_ltab));
         sdfT[2 * t + 1] = df_split_int(cv * inum);
+      } else if constexpr (MIX) {
+        // FP64 to about one ulp for the FP64 chemistry: reciprocals by two Newton
+        // steps from a float seed, Tang's table logarithm (within 1.4 ulp)
+        u = m * recip_nr2(rho);
+        num = wq[TQ] - 0.5 * m * u - qsum;
+        T = num * recip_nr2(cv);
+        slnT[t] = log_tab(T, c_ltab);
+        sinvT[t] = cv * recip_nr2(num);
       } else {
         u = m / rho;
         num = wq[TQ] - 0.5 * m * u - qsum;
@@ -668,17 +736,25 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   // (law of mass action on non-negative concentrations: clipped at zero by the
   // sign bit)
   if constexpr (MIX) {
-    // in FP32 throughout, on the copies of phases 2a and 2b
+    // the flux in FP32 throughout, on the copies of phases 2a and 2b; the
+    // concentrations in the chemistry's type (FP64 from the FP64 nodal state)
     const float *sIW = sspD + SP_INVW * ns, *suf = reinterpret_cast<const float *>(su);
-    for (int item = tid; item < nv * teq; item += nth) {
-      int v = item / teq, t = item - v * teq;
+    Walk wk(tid, nth, teq);
+    for (int item = tid; item < nv * teq; item += nth, wk.next()) {
+      const int v = wk.o, t = wk.i;
       const size_t at = (size_t)v * TQ + t;
       const float w = sfx[at], u = suf[t];
       float f;
       if (v >= 2) {
         const int i = v - 2;
-        const float r = (__float_as_int(w) < 0) ? 0.0f : w;
-        scc[(size_t)i * TQ + t] = r * sIW[i];
+        if constexpr (FCHEM) {
+          const float r = (__float_as_int(w) < 0) ? 0.0f : w;
+          scc[(size_t)i * TQ + t] = r * sIW[i];
+        } else {
+          const double wd = snw[at];
+          const double r = (__double2hiint(wd) < 0) ? 0.0 : wd;
+          scc[(size_t)i * TQ + t] = r * ssp[SP_INVW * ns + i];
+        }
         f = u * w;
       } else if (v == 0) {
         f = fmaf(w, u, suf[TQ + t]);
@@ -691,14 +767,15 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
     }
   } else {
     const double *sIW = ssp + SP_INVW * ns;
-    for (int item = tid; item < nv * teq; item += nth) {
-      int v = item / teq, t = item - v * teq;
+    Walk wk(tid, nth, teq);
+    for (int item = tid; item < nv * teq; item += nth, wk.next()) {
+      const int v = wk.o, t = wk.i;
       const size_t at = (size_t)v * TQ + t;
       const double w = snw[at], u = su[t];
       if (v >= 2) {
         const int i = v - 2;
         const double r = (__double2hiint(w) < 0) ? 0.0 : w;
-        scc[(size_t)i * TQ + t] = (DG)(r * sIW[i]);
+        scc[(size_t)i * TQ + t] = r * sIW[i];
         snw[at] = u * w;
       } else if (v == 0) {
         snw[at] = w * u + sPr[t];
@@ -714,17 +791,19 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   // 3. the chemistry, one (reaction, point) per item: the reversible rate of
   // progress from the Arrhenius and the equilibrium exponentials (the face fluxes
   // ran in phase 2b).
-  for (int item = tid; item < nr * teq; item += nth) {
-    const int j = item / teq, t = item - j * teq;
+  Walk w3(tid, nth, teq);
+  for (int item = tid; item < nr * teq; item += nth, w3.next()) {
+    const int j = w3.o, t = w3.i;
     const Rxn &Rx = srx[j];
-    DG fwd, rev;
-    if constexpr (MIX) {
+    CT fwd, rev;
+    if constexpr (FCHEM) {
       // arguments in df32 and the FP32-pipe exp: no FP64 instruction and no
       // precision conversion per item
       const DF lnT = sdfT[2 * t], invT = sdfT[2 * t + 1], *c = srxf + 6 * j;
       fwd = exp_df(df_fma(c[2], invT, df_fma(c[1], lnT, c[0])), stab->tf);
       rev = exp_df(df_fma(c[5], invT, df_fma(c[4], lnT, c[3])), stab->tf);
     } else {
+      // FP64 arguments, the FP64 exponential on the integer pipeline
       const double lnT = slnT[t], invT = sinvT[t];
       fwd = iexp(fma(Rx.mEaR, invT, fma(Rx.b, lnT, Rx.lnA)), *stab);
       rev = iexp(fma(Rx.kr2, invT, fma(Rx.kr1, lnT, Rx.kr0)), *stab);
@@ -732,14 +811,14 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (Rx.rn[k] == 0) break;
-      DG cc = scc[(size_t)Rx.rs[k] * TQ + t];
+      CT cc = scc[(size_t)Rx.rs[k] * TQ + t];
       fwd *= cc;
       if (Rx.rn[k] > 1) fwd *= cc;
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (Rx.pn[k] == 0) break;
-      DG cc = scc[(size_t)Rx.ps[k] * TQ + t];
+      CT cc = scc[(size_t)Rx.ps[k] * TQ + t];
       rev *= cc;
       if (Rx.pn[k] > 1) rev *= cc;
     }
@@ -749,9 +828,10 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
 
   // 4. production rates, one (species, point) per item: the net stoichiometric
   // sum over the species' reactions, in ascending reaction order
-  for (int item = tid; item < ns * teq; item += nth) {
-    const int i = item / teq, t = item - i * teq;
-    DG acc = DG(0);
+  Walk w4(tid, nth, teq);
+  for (int item = tid; item < ns * teq; item += nth, w4.next()) {
+    const int i = w4.o, t = w4.i;
+    CT acc = CT(0);
     for (int k = soff[i]; k < soff[i + 1]; ++k)
       acc = fma(scoef[k], sq[(size_t)sterm[k] * TQ + t], acc);
     swd[(size_t)i * TQ + t] = acc;
@@ -766,8 +846,9 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   }
   // 5. the AT sum over levels, m = 0..o-1 in order, in FP64, of the Riemann flux
   // minus (viscous) the central mean of f^d
-  for (int item = tid; item < (te + 1) * nv; item += nth) {
-    const int f = item / nv, v = item - f * nv;
+  Walk w5(tid, nth, nv);
+  for (int item = tid; item < (te + 1) * nv; item += nth, w5.next()) {
+    const int f = w5.o, v = w5.i;
     const int k = sk[f];
     auto level = [&](int m) {
       double x = (double)sflx[((size_t)m * NF + f) * nv + v];
@@ -797,18 +878,20 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   DG scale[Q];  // (2i+1)/dx in the variant's type, once per thread
 #pragma unroll
   for (int i = 0; i < Q; ++i) scale[i] = (DG)((2.0 * i + 1.0) * inv_dx);
-  for (int item = tid; item < nv * te; item += nth) {
-    const int v = item / te, e = item - v * te, ge = e0 + e, le = e + 1;
+  Walk w6(tid, nth, te);
+  for (int item = tid; item < nv * te; item += nth, w6.next()) {
+    const int v = w6.o, e = w6.i, ge = e0 + e, le = e + 1;
     const double *wi = sw + ((size_t)v * (TE + 2) + le) * Q;
     const DG *fq = sfx + (size_t)v * TQ + e * Q;
-    const DG *sqv = (v >= 2) ? swd + (size_t)(v - 2) * TQ + e * Q : nullptr;
+    const CT *sqv = (v >= 2) ? swd + (size_t)(v - 2) * TQ + e * Q : nullptr;
     const DG Wv = (v >= 2) ? sspD[SP_W * ns + v - 2] : DG(0);
     const DG fr = sfh[(size_t)(e + 1) * nv + v], fl = sfh[(size_t)e * nv + v];
     DG fqr[Q], sqr[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       fqr[q] = fq[q];
-      sqr[q] = (v >= 2) ? sqv[q] : DG(0);
+      // the production rates in the flux's type (on the integer pipeline)
+      sqr[q] = (v >= 2) ? conv_r<DG>(sqv[q]) : DG(0);
     }
     double out[Q];
 #pragma unroll
@@ -873,15 +956,15 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   }
 }
 
-template <int Q, bool MIX, bool VISC>
+template <int Q, int PREC, bool VISC>
 __global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
   pdl_wait();
   __shared__ Inst sI;
   const int2 tile = A.tiles[blockIdx.x];
   load_inst(sI, A.insts + tile.x);
   __syncthreads();
-  stage_body<Q, MIX, false, VISC>(M, A, sI, tile.y, min(A.TE, sI.n_elem - tile.y), *sI.step,
-                                  nullptr);
+  stage_body<Q, PREC, false, VISC>(M, A, sI, tile.y, min(A.TE, sI.n_elem - tile.y), *sI.step,
+                                   nullptr);
 }
 
 template <typename R>
@@ -965,21 +1048,36 @@ __device__ inline double neighbour_mode(const Inst &I, const double *wpre, int s
 // Troubled-cell indicator of element e (Sec. 3.3), a group of L lanes, in the
 // arithmetic type R. In each characteristic field of L(wbar_e) the face
 // deviations v(+1) - vbar and vbar - v(-1) go through the TVB-modified minmod
-// with the neighbours' mean differences; deviations below 1e-5 of the field's
-// magnitude sum_v |L_kv| sigma_v count as zero. Three passes over the
-// variables, the species and the fields split over the group's lanes: the
-// thermodynamics of the cell average; gradP.w, the partial-density sum and the
-// momentum at the five points (own average, faces +1 and -1, neighbours'
-// averages); the characteristic values per field, with the branch-free
-// coefficients (A, B, C, D) described at the limiter kernel. Every lane of the
-// warp calls it (shuffles); the result is the same on the group's lanes.
+// with the neighbours' mean differences; deviations below I.ind_floor of the
+// field's magnitude sum_v |L_kv| sigma_v count as zero (the rounding guard of
+// indicator_guard: the paper's TVD criterion has no threshold). Three passes
+// over the variables, the species and the fields split over the group's lanes:
+// the thermodynamics of the cell average; gradP.w, the partial-density sum and the
+// momentum of the data the test compares; the characteristic values per field,
+// with the branch-free coefficients (A, B, C, D) described at the limiter
+// kernel. Every lane of the warp calls it (shuffles); the result is the same on
+// the group's lanes.
+// FP64: the data are the values at five points (own average, faces +1 and -1,
+// neighbours' averages), and the test takes their differences in
+// characteristic space. FP32: the transform is linear, so it is applied to the
+// four differences themselves, formed before any rounding to float can cancel:
+// the face deviations are sums of the modes >= 1 (sum_j w_j and
+// -sum_j (-1)^j w_j), and the neighbours' mean differences are taken on the
+// double means carried as float pairs (hi, lo). A float run then resolves
+// deviations far below the float rounding of the means themselves.
 // own: modes of variable 0 of the element in the staged tile (variables vs
 // apart, the neighbours' modes Q before and after, halo ghosts included);
-// spf: species fields in R; atl, atr: the AT-extrapolated averages [nv] of a
-// neighbour across a delayed PE face, or null.
+// own_lo (FP32): low parts of the element's means (variables ls apart,
+// neighbours 1 before and after); spf: species fields in R; atl, atr (and
+// atl_lo, atr_lo): the AT-extrapolated averages [nv] of a neighbour across a
+// delayed PE face, or null.
 template <int Q, int L, typename R>
 __device__ bool troubled_cell(const Mech &M, const Inst &I, int s, int64_t nstep, int e,
-                              const R *own, int vs, const R *spf, const R *atl, const R *atr) {
+                              const R *own, int vs, const R *spf, const R *atl, const R *atr,
+                              const R *own_lo = nullptr, int ls = 0, const R *atl_lo = nullptr,
+                              const R *atr_lo = nullptr) {
+  constexpr bool DIFF = std::is_same<R, float>::value;
+  constexpr int NP = DIFF ? 4 : 5;  // data per variable
   const int ns = M.ns, nv = ns + 2;
   const int lane = threadIdx.x & 31, li = lane % L;
   const unsigned FULL = 0xffffffffu;
@@ -990,20 +1088,37 @@ __device__ bool troubled_cell(const Mech &M, const Inst &I, int s, int64_t nstep
     for (int o = L / 2; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o, L);
     return x;
   };
-  // values of variable v at the five points
+  // the data of variable v: FP64, the values at the five points; FP32, the
+  // differences (v(+1) - vbar, vbar - v(-1), vbar_R - vbar, vbar - vbar_L)
   auto points = [&](int v, R *x) {
     const R *w = own + (size_t)v * vs;
-    R sp = 0, sm = 0;
+    if constexpr (DIFF) {
+      R sp = 0, sm = 0;
 #pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      sp += w[j];
-      sm += (j & 1) ? -w[j] : w[j];
+      for (int j = 1; j < Q; ++j) {
+        sp += w[j];
+        sm += (j & 1) ? w[j] : -w[j];
+      }
+      const R *lo = own_lo + (size_t)v * ls;
+      const R rh = atr ? atr[v] : w[Q], rl = atr ? atr_lo[v] : lo[1];
+      const R lh = atl ? atl[v] : w[-Q], ll = atl ? atl_lo[v] : lo[-1];
+      x[0] = sp;
+      x[1] = sm;
+      x[2] = (rh - w[0]) + (rl - lo[0]);
+      x[3] = (w[0] - lh) + (lo[0] - ll);
+    } else {
+      R sp = 0, sm = 0;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        sp += w[j];
+        sm += (j & 1) ? -w[j] : w[j];
+      }
+      x[0] = w[0];
+      x[1] = sp;
+      x[2] = sm;
+      x[3] = atl ? atl[v] : w[-Q];
+      x[4] = atr ? atr[v] : w[Q];
     }
-    x[0] = w[0];
-    x[1] = sp;
-    x[2] = sm;
-    x[3] = atl ? atl[v] : w[-Q];
-    x[4] = atr ? atr[v] : w[Q];
   };
   // 1. thermodynamics of the cell average
   R rho = 0, qsum = 0, cv = 0, Rm = 0, cpm = 0;
@@ -1031,13 +1146,13 @@ __device__ bool troubled_cell(const Mech &M, const Inst &I, int s, int64_t nstep
   if (li == 0 && (!(rho > R(0)) || !(T > R(0)) || !isfinite(T)))
     report_error(I, ADG_ERR_NONPHYSICAL, e, s, nstep);
   auto phi_of = [&](int i) { return fma(g, fma(-cvW[i], T, R(0.5) * u * u - qW[i]), T * RW[i]); };
-  // 2. gradP.w, sum rho Y and rho u at the five points; sums of |phi|
-  R gp[5], rs[5], mm[5], x[5];
+  // 2. gradP.w, sum rho Y and rho u of the data; sums of |phi|
+  R gp[NP], rs[NP], mm[NP], x[NP];
   R sphi = 0, sphm = 0, sphp = 0;
   points(0, mm);
   points(1, x);
 #pragma unroll
-  for (int p = 0; p < 5; ++p) {
+  for (int p = 0; p < NP; ++p) {
     gp[p] = li == 0 ? g * fma(-u, mm[p], x[p]) : R(0);
     rs[p] = 0;
   }
@@ -1048,13 +1163,13 @@ __device__ bool troubled_cell(const Mech &M, const Inst &I, int s, int64_t nstep
     sphp += fabs(ph + a * u);
     points(2 + i, x);
 #pragma unroll
-    for (int p = 0; p < 5; ++p) {
+    for (int p = 0; p < NP; ++p) {
       gp[p] = fma(ph, x[p], gp[p]);
       rs[p] += x[p];
     }
   }
 #pragma unroll
-  for (int p = 0; p < 5; ++p) {
+  for (int p = 0; p < NP; ++p) {
     gp[p] = allsum(gp[p]);
     rs[p] = allsum(rs[p]);
   }
@@ -1063,29 +1178,42 @@ __device__ bool troubled_cell(const Mech &M, const Inst &I, int s, int64_t nstep
   sphp = allsum(sphp);
   // 3. the characteristic fields, k = 0 and nv-1 acoustic, k = 1..ns species k-1
   const R sig0 = fma(rho, a, fabs(m0)), sig1 = fabs(E0), sigr = rho;
-  const R tvb = (R)I.tvb, tau = R(1e-5);
+  const R tvb = (R)I.tvb, tau = (R)I.ind_floor, taup = (R)I.ind_floor_p;
   bool tr = false;
   for (int k = li; k < nv; k += L) {
-    R v[5], scale;
+    R v[NP], scale, scale_p;  // the field's magnitude, and its momentum and energy part
     if (k == 0 || k == nv - 1) {
       const R sgn = k == 0 ? R(-1) : R(1);
       const R cA = ha2, cB = sgn * a * ha2, cC = -sgn * a * u * ha2;
 #pragma unroll
-      for (int p = 0; p < 5; ++p) v[p] = fma(cA, gp[p], fma(cB, mm[p], cC * rs[p]));
+      for (int p = 0; p < NP; ++p) v[p] = fma(cA, gp[p], fma(cB, mm[p], cC * rs[p]));
       const R srr = cA * (k == 0 ? sphp : sphm);
-      scale = fma(fabs(fma(cA, -u * g, cB)), sig0, fma(fabs(cA * g), sig1, srr * sigr));
+      scale_p = fma(fabs(fma(cA, -u * g, cB)), sig0, fabs(cA * g) * sig1);
+      scale = fma(srr, sigr, scale_p);
     } else {
       const int i = k - 1;
       points(2 + i, x);
-      const R cA = -x[0] * irho * ia2;
+      const R cA = -own[(size_t)(2 + i) * vs] * irho * ia2;
       const R ph = phi_of(i);
 #pragma unroll
-      for (int p = 0; p < 5; ++p) v[p] = fma(cA, gp[p], x[p]);
+      for (int p = 0; p < NP; ++p) v[p] = fma(cA, gp[p], x[p]);
       const R srr = fabs(fma(cA, ph, R(1))) + fabs(cA) * (sphi - fabs(ph));
-      scale = fma(fabs(cA * -u * g), sig0, fma(fabs(cA * g), sig1, srr * sigr));
+      scale_p = fma(fabs(cA * -u * g), sig0, fabs(cA * g) * sig1);
+      scale = fma(srr, sigr, scale_p);
     }
-    const R ut = v[1] - v[0], utt = v[0] - v[2], dp = v[4] - v[0], dm = v[0] - v[3];
-    const R fl = tau * scale;
+    R ut, utt, dp, dm;
+    if constexpr (DIFF) {
+      ut = v[0];
+      utt = v[1];
+      dp = v[2];
+      dm = v[3];
+    } else {
+      ut = v[1] - v[0];
+      utt = v[0] - v[2];
+      dp = v[4] - v[0];
+      dm = v[0] - v[3];
+    }
+    const R fl = fma(tau, scale, taup * scale_p);
     if (fabs(ut) > fl && fabs(ut) > tvb && minmod3(ut, dp, dm) != ut) tr = true;
     if (fabs(utt) > fl && fabs(utt) > tvb && minmod3(utt, dp, dm) != utt) tr = true;
   }
@@ -1136,10 +1264,14 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
   // 1. stage the CTA's elements with a one-element halo (ghosts at walls) and
   // the species fields in the variant's type; then the indicator, one element
   // per thread
-  const int vs = (EPB + 2) * Q;
+  const int vs = (EPB + 2) * Q, ls = EPB + 2;
+  constexpr int LO = MIX ? 1 : 0;                  // FP32: low parts of the means
   DG *spf = lsm;                                   // [SP_NFIELDS][ns]
   DG *atn = spf + SP_NFIELDS * ns;                 // [2][EPB][nv] AT neighbour averages
-  DG *tile = atn + 2 * EPB * nv;               // [nv][EPB + 2][Q]
+  DG *tile = atn + 2 * EPB * nv;                   // [nv][EPB + 2][Q]
+  DG *tlo = tile + (size_t)nv * vs;                // [nv][EPB + 2] (FP32) mean - (float) mean
+  DG *alo = tlo + (size_t)LO * nv * ls;            // [2][EPB][nv] (FP32) the same of atn
+  DG *wsp = alo + (size_t)LO * 2 * EPB * nv;       // WENO workspace
   for (int k = threadIdx.x; k < SP_NFIELDS * ns; k += blockDim.x) spf[k] = (DG)M.sp[k];
   if ((int)threadIdx.x < 2 * te) {
     const int side = threadIdx.x / te, le = threadIdx.x - side * te;
@@ -1178,7 +1310,14 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
       }
 #pragma unroll
       for (int b = 0; b < BATCH; ++b)
-        if (dst[b] >= 0) tile[dst[b]] = (DG)xs[b];
+        if (dst[b] >= 0) {
+          const DG hi = conv_r<DG>(xs[b]);
+          tile[dst[b]] = hi;
+          if constexpr (MIX) {
+            const int v = dst[b] / vs, r = dst[b] - v * vs;
+            if (r % Q == 0) tlo[v * ls + r / Q] = conv_r<DG>(xs[b] - f2d_exact(hi));
+          }
+        }
     }
   }
   __syncthreads();
@@ -1187,9 +1326,12 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
   for (int item = threadIdx.x; item < 2 * te * nv; item += blockDim.x) {
     const int side = item / (te * nv), r = item - side * te * nv, le = r / nv, v = r - le * nv;
     const Neighbour &nb = s_nb[side][le];
-    if (nb.ring)
-      atn[(side * EPB + le) * nv + v] =
-          (DG)neighbour_mode<UNSYNC>(I, I.wpre, A.s, nstep, nb, v, 0, Q);
+    if (nb.ring) {
+      const double x = neighbour_mode<UNSYNC>(I, I.wpre, A.s, nstep, nb, v, 0, Q);
+      const DG hi = conv_r<DG>(x);
+      atn[(side * EPB + le) * nv + v] = hi;
+      if constexpr (MIX) alo[(side * EPB + le) * nv + v] = conv_r<DG>(x - f2d_exact(hi));
+    }
   }
   __syncthreads();
   if (threadIdx.x < EPB * LIM_L) {
@@ -1201,8 +1343,10 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
     const int lv = valid ? le : 0, e = e0 + lv;
     const DG *atl = s_nb[0][lv].ring ? atn + lv * nv : nullptr;
     const DG *atr = s_nb[1][lv].ring ? atn + (EPB + lv) * nv : nullptr;
-    const bool t = troubled_cell<Q, LIM_L, DG>(M, I, A.s, nstep, e, tile + (lv + 1) * Q, vs, spf,
-                                               atl, atr);
+    const bool t = troubled_cell<Q, LIM_L, DG>(
+        M, I, A.s, nstep, e, tile + (lv + 1) * Q, vs, spf, atl, atr,
+        MIX ? tlo + lv + 1 : nullptr, ls, MIX ? alo + lv * nv : nullptr,
+        MIX ? alo + (EPB + lv) * nv : nullptr);
     if (valid && threadIdx.x % LIM_L == 0) {
       I.flags[(size_t)A.s * N + e] = t ? 1 : 0;
       if (t) {
@@ -1229,7 +1373,7 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
   const unsigned gmask = (G == 32) ? FULL : (0xffffu << (16 * gw));
   const size_t VS = (size_t)N * Q;
   const int NB = nv * Q;
-  DG *blk = tile + (size_t)nv * vs + (size_t)slot * limiter_elem_words(nv, ns, Q);  // [3][nv][Q]
+  DG *blk = wsp + (size_t)slot * limiter_elem_words(nv, ns, Q);  // [3][nv][Q]
   DG *vlim = blk + 3 * NB;                                        // [nv][Q]
   DG *gpv = vlim + NB;                                            // [3][Q]
   DG *rsv = gpv + 3 * Q;                                          // [3][Q]
@@ -1434,6 +1578,7 @@ template <int Q, int G, bool MIX, int EPB>
 static size_t limiter_smem_bytes(int nv, int ns) {
   constexpr int EPW = 32 / G;
   size_t smem = ((size_t)SP_NFIELDS * ns + (size_t)2 * EPB * nv + (size_t)nv * (EPB + 2) * Q +
+                 (MIX ? (size_t)nv * (EPB + 2) + (size_t)2 * EPB * nv : 0) +
                  (size_t)(LIM_THREADS / 32) * EPW * limiter_elem_words(nv, ns, Q)) *
                 (MIX ? sizeof(float) : sizeof(double));
   return (smem + 15) & ~(size_t)15;
@@ -1441,36 +1586,36 @@ static size_t limiter_smem_bytes(int nv, int ns) {
 
 // Launchers and set-up of one precision variant (instantiated by the unit of
 // that variant only).
-template <int Q, bool MIX, bool VISC>
+template <int Q, int PREC, bool VISC>
 static cudaError_t launch_stage_q(const Mech &M, const StageArgs &A, int n_tiles,
                                   cudaStream_t st) {
   if ((A.visc != 0) != VISC) return cudaErrorInvalidValue;
-  size_t smem = stage_smem_bytes(A.TE, Q, M.ns, M.nr, M.nterm, A.O, MIX, VISC);
+  size_t smem = stage_smem_bytes(A.TE, Q, M.ns, M.nr, M.nterm, A.O, PREC, VISC);
   if (A.NT < 32 || A.NT > 512 || A.NT % 32) return cudaErrorInvalidValue;
-  return launch_pdl(stage_kernel<Q, MIX, VISC>, dim3(n_tiles), dim3(A.NT), smem, st, M, A);
+  return launch_pdl(stage_kernel<Q, PREC, VISC>, dim3(n_tiles), dim3(A.NT), smem, st, M, A);
 }
 
-template <bool MIX, bool VISC>
+template <int PREC, bool VISC>
 static cudaError_t launch_stage_variant(const Mech &M, const StageArgs &A, int Q, int n_tiles,
                                         cudaStream_t st) {
   switch (Q) {
-    case 2: return launch_stage_q<2, MIX, VISC>(M, A, n_tiles, st);
-    case 3: return launch_stage_q<3, MIX, VISC>(M, A, n_tiles, st);
-    case 4: return launch_stage_q<4, MIX, VISC>(M, A, n_tiles, st);
-    case 5: return launch_stage_q<5, MIX, VISC>(M, A, n_tiles, st);
+    case 2: return launch_stage_q<2, PREC, VISC>(M, A, n_tiles, st);
+    case 3: return launch_stage_q<3, PREC, VISC>(M, A, n_tiles, st);
+    case 4: return launch_stage_q<4, PREC, VISC>(M, A, n_tiles, st);
+    case 5: return launch_stage_q<5, PREC, VISC>(M, A, n_tiles, st);
   }
   return cudaErrorInvalidValue;
 }
 
 // Raise the dynamic shared-memory limit of the stage kernels of one variant.
-template <bool MIX, bool VISC>
+template <int PREC, bool VISC>
 static cudaError_t prepare_stage_variant() {
   const int lim = 200 * 1024;
   cudaError_t e = cudaSuccess;
-  const void *k[4] = {(const void *)stage_kernel<2, MIX, VISC>,
-                      (const void *)stage_kernel<3, MIX, VISC>,
-                      (const void *)stage_kernel<4, MIX, VISC>,
-                      (const void *)stage_kernel<5, MIX, VISC>};
+  const void *k[4] = {(const void *)stage_kernel<2, PREC, VISC>,
+                      (const void *)stage_kernel<3, PREC, VISC>,
+                      (const void *)stage_kernel<4, PREC, VISC>,
+                      (const void *)stage_kernel<5, PREC, VISC>};
   for (int i = 0; i < 4 && e == cudaSuccess; ++i)
     e = cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   return e;
@@ -1514,12 +1659,12 @@ static cudaError_t launch_limiter_variant(const Mech &M, const LimArgs &A, int Q
   return cudaErrorInvalidValue;
 }
 
-// Raise the dynamic shared-memory limit of the Euler stage kernels and of every
-// limiter kernel of the variant (before any launch or stream capture).
+// Raise the dynamic shared-memory limit of every limiter kernel of the variant
+// (before any launch or stream capture).
 template <bool MIX>
-static cudaError_t prepare_variant() {
+static cudaError_t prepare_limiter_variant() {
   const int lim = 200 * 1024;
-  cudaError_t e = prepare_stage_variant<MIX, false>();
+  cudaError_t e = cudaSuccess;
 #define ADG_SET(...) \
   if (e == cudaSuccess) \
   e = cudaFuncSetAttribute(__VA_ARGS__, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)

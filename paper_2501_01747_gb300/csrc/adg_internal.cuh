@@ -96,8 +96,33 @@ struct Inst {
   int *err;                             // [4] code, element, stage, step (low bits)
   int64_t *step;                        // step counter of this instance (device)
   int instance;
-  int mixed;                            // ADG_MIXED: FP32 flux, DG operator, limiter
+  int mixed;                            // precision (ADG_FP64, ADG_MIXED, ADG_MIXED_F32CHEM):
+                                        // nonzero for FP32 flux, DG operator, limiter
+  double ind_floor, ind_floor_p;        // rounding guards of the indicator (indicator_guard)
 };
+
+// Rounding guards of the troubled-cell indicator (Sec. 3.3 gives a TVD test with
+// no threshold): a face deviation of characteristic field k counts as zero below
+// ind_floor * |field k| + ind_floor_p * |field k|_p, with |field k| =
+// sum_v |L_kv| sigma_v its magnitude and |field k|_p the part of it that comes
+// from the momentum and the energy.
+// FP64 data: 1e-10 of the magnitude, far above its rounding, and nothing else.
+// The mixed variants compute the flux and the DG operator in FP32. Their state
+// then differs from the FP64 state by about 1e-6 of the momentum and energy (the
+// pressure) and by a few 1e-8 of the partial densities, and a deviation below
+// that difference is not resolved by them: their guard is 3e-8 of the magnitude
+// plus 1e-6 of its momentum-and-energy part. A species field then keeps a guard
+// far below the deviations that the FP64 scheme limits (1e-7 and more on the
+// workloads here), while a field that carries the pressure ignores that noise.
+constexpr double kGuardFP64 = 1e-10;
+constexpr double kGuardMixed = 3e-8;
+constexpr double kGuardMixedP = 1e-6;
+inline double indicator_guard(int precision) {
+  return precision == ADG_FP64 ? kGuardFP64 : kGuardMixed;
+}
+inline double indicator_guard_p(int precision) {
+  return precision == ADG_FP64 ? 0.0 : kGuardMixedP;
+}
 
 // Programmatic dependent launch for the kernels of a step: each is launched so
 // that it may be scheduled while its predecessor drains, waits at entry until
@@ -325,27 +350,30 @@ struct LimArgs {
 
 void make_tables(Basis *tables);
 cudaError_t upload_basis(const Basis *tables);
-int stage_tile(const Mech &M, int Q, int O, bool mixed, bool visc);
+int stage_tile(const Mech &M, int Q, int O, int prec, bool visc);
 int stage_threads(int TE, int Q, int nr);
-size_t stage_smem(const Mech &M, int TE, int Q, int O, bool mixed, bool visc);
+size_t stage_smem(const Mech &M, int TE, int Q, int O, int prec, bool visc);
 cudaError_t prepare_kernels(int nv, int ns, int nr);
-cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, bool mixed, int n_tiles,
+cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, int prec, int n_tiles,
                          cudaStream_t st);
 cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, bool mixed, int nv,
                            int n_blocks, cudaStream_t st);
 cudaError_t launch_advance(int64_t *steps, int n, cudaStream_t st);
 cudaError_t launch_aux(const LimArgs &A, int Q, int n_blocks, cudaStream_t st);
-// per-variant units (adg_k64.cu, adg_k32.cu)
+// per-variant units (adg_k64.cu, adg_k32.cu, adg_k32f.cu)
 cudaError_t launch_stage_fp64(const Mech &M, const StageArgs &A, int Q, int n_tiles,
                               cudaStream_t st);
 cudaError_t launch_stage_mixed(const Mech &M, const StageArgs &A, int Q, int n_tiles,
                                cudaStream_t st);
+cudaError_t launch_stage_f32chem(const Mech &M, const StageArgs &A, int Q, int n_tiles,
+                                 cudaStream_t st);
 cudaError_t launch_limiter_fp64(const Mech &M, const LimArgs &A, int Q, int nv, int n_blocks,
                                 cudaStream_t st);
 cudaError_t launch_limiter_mixed(const Mech &M, const LimArgs &A, int Q, int nv, int n_blocks,
                                  cudaStream_t st);
 cudaError_t prepare_fp64();
 cudaError_t prepare_mixed();
+cudaError_t prepare_f32chem();
 // viscous stage kernels (adg_v64.cu, adg_v32.cu)
 cudaError_t launch_stage_visc_fp64(const Mech &M, const StageArgs &A, int Q, int n_tiles,
                                    cudaStream_t st);
@@ -357,6 +385,7 @@ cudaError_t upload_tables_visc_fp64(const Basis *tables);
 cudaError_t upload_tables_visc_mixed(const Basis *tables);
 cudaError_t upload_tables_fp64(const Basis *tables);
 cudaError_t upload_tables_mixed(const Basis *tables);
+cudaError_t upload_tables_f32chem(const Basis *tables);
 int limiter_elems_per_block(int64_t n_elem_group, bool mixed);
 // the unsynchronised mode (adg_unsync.cuh): one cooperative launch per instance
 struct UnsyncArgs {

@@ -173,18 +173,24 @@ cudaError_t upload_basis(const Basis *tables) {
   cudaError_t e = upload_unit_tables(tables);
   if (e == cudaSuccess) e = upload_tables_fp64(tables);
   if (e == cudaSuccess) e = upload_tables_mixed(tables);
+  if (e == cudaSuccess) e = upload_tables_f32chem(tables);
   if (e == cudaSuccess) e = upload_tables_unsync(tables);
   if (e == cudaSuccess) e = upload_tables_visc_fp64(tables);
   if (e == cudaSuccess) e = upload_tables_visc_mixed(tables);
   return e;
 }
 
-cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, bool mixed, int n_tiles,
+cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, int prec, int n_tiles,
                          cudaStream_t st) {
-  if (A.visc)
-    return mixed ? launch_stage_visc_mixed(M, A, Q, n_tiles, st)
-                 : launch_stage_visc_fp64(M, A, Q, n_tiles, st);
-  return mixed ? launch_stage_mixed(M, A, Q, n_tiles, st) : launch_stage_fp64(M, A, Q, n_tiles, st);
+  if (A.visc) {
+    if (prec == ADG_FP64) return launch_stage_visc_fp64(M, A, Q, n_tiles, st);
+    if (prec == ADG_MIXED) return launch_stage_visc_mixed(M, A, Q, n_tiles, st);
+    return cudaErrorInvalidValue;  // no viscous float-chemistry variant
+  }
+  if (prec == ADG_FP64) return launch_stage_fp64(M, A, Q, n_tiles, st);
+  if (prec == ADG_MIXED) return launch_stage_mixed(M, A, Q, n_tiles, st);
+  if (prec == ADG_MIXED_F32CHEM) return launch_stage_f32chem(M, A, Q, n_tiles, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, bool mixed, int nv,
@@ -218,16 +224,17 @@ cudaError_t prepare_kernels(int nv, int ns, int nr) {
   (void)nr;
   cudaError_t e = prepare_fp64();
   if (e == cudaSuccess) e = prepare_mixed();
+  if (e == cudaSuccess) e = prepare_f32chem();
   if (e == cudaSuccess) e = prepare_unsync();
   if (e == cudaSuccess) e = prepare_visc_fp64();
   if (e == cudaSuccess) e = prepare_visc_mixed();
   return e;
 }
 
-int stage_tile(const Mech &M, int Q, int O, bool mixed, bool visc) {
+int stage_tile(const Mech &M, int Q, int O, int prec, bool visc) {
   // elements per tile: up to 256 Gauss points, at most ~96 KB of tile
   int TE = 256 / Q;
-  while (TE > 2 && stage_smem_bytes(TE, Q, M.ns, M.nr, M.nterm, O, mixed, visc) > 96 * 1024)
+  while (TE > 2 && stage_smem_bytes(TE, Q, M.ns, M.nr, M.nterm, O, prec, visc) > 96 * 1024)
     TE /= 2;
   return TE;
 }
@@ -239,8 +246,8 @@ int stage_threads(int TE, int Q, int nr) {
   return nt < 128 ? 128 : (nt > 512 ? 512 : nt);
 }
 
-size_t stage_smem(const Mech &M, int TE, int Q, int O, bool mixed, bool visc) {
-  return stage_smem_bytes(TE, Q, M.ns, M.nr, M.nterm, O, mixed, visc);
+size_t stage_smem(const Mech &M, int TE, int Q, int O, int prec, bool visc) {
+  return stage_smem_bytes(TE, Q, M.ns, M.nr, M.nterm, O, prec, visc);
 }
 
 int limiter_elems_per_block(int64_t n_elem_group, bool mixed) {

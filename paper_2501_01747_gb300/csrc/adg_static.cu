@@ -46,12 +46,53 @@ __global__ void noalloc_maps_kernel(int N, int P, int npf, int periodic, int *pf
   pf_right[e] = r;
 }
 
+// Bytes that one launch of noalloc_put_kernel copies into the scratch. They
+// travel as the kernel's parameter, taken by value at launch, so no host buffer
+// has to outlive the call and no copy from pageable host memory is enqueued.
+constexpr int kPutBytes = 2048;
+struct PutChunk {
+  unsigned long long off;  // destination offset in the scratch
+  unsigned n, pad;         // bytes used of b
+  unsigned char b[kPutBytes];
+};
+
+__global__ void noalloc_put_kernel(unsigned char *base, PutChunk c) {
+  for (unsigned i = threadIdx.x; i < c.n; i += blockDim.x) base[c.off + i] = c.b[i];
+}
+
 namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 unsigned char *g_ptr[kMaxDevices];
 bool g_ready[kMaxDevices];
+
+// Host staging of the mechanism tables, at file scope (neither the heap nor a
+// large stack frame); used only while g_mutex is held.
+struct HostTables {
+  double sp[SP_NFIELDS * ADG_MAX_SPECIES];
+  Rxn rx[ADG_NOALLOC_MAX_REACTIONS > 0 ? ADG_NOALLOC_MAX_REACTIONS : 1];
+  DF rxf[6 * (ADG_NOALLOC_MAX_REACTIONS > 0 ? ADG_NOALLOC_MAX_REACTIONS : 1)];
+  int sx_off[ADG_MAX_SPECIES + 1];
+  int sx[ADG_NOALLOC_MAX_REACTIONS * NET];
+};
+HostTables g_host;
+
+// Copy n bytes from host memory to base + off on stream s, kPutBytes per launch.
+cudaError_t put(unsigned char *base, size_t off, const void *src, size_t n, cudaStream_t s) {
+  PutChunk c;
+  const unsigned char *p = static_cast<const unsigned char *>(src);
+  for (size_t k = 0; k < n; k += kPutBytes) {
+    c.off = off + k;
+    c.n = (unsigned)(n - k < (size_t)kPutBytes ? n - k : (size_t)kPutBytes);
+    c.pad = 0;
+    memcpy(c.b, p + k, c.n);
+    noalloc_put_kernel<<<1, 256, 0, s>>>(base, c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 struct Cursor {
   unsigned char *base;
@@ -85,7 +126,8 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
       (c.limiter != ADG_LIM_NONE && c.limiter != ADG_LIM_WENO) || c.bc_left < 0 ||
       c.bc_left > 2 || c.bc_right < 0 || c.bc_right > 2 ||
       ((c.bc_left == ADG_BC_PERIODIC) != (c.bc_right == ADG_BC_PERIODIC)) ||
-      (c.precision != ADG_FP64 && c.precision != ADG_MIXED) || c.integrator != ADG_RK_SSP3 ||
+      (c.precision != ADG_FP64 && c.precision != ADG_MIXED && c.precision != ADG_MIXED_F32CHEM) ||
+      c.integrator != ADG_RK_SSP3 ||
       c.viscous != 0)
     return ADG_ERR_ARG;
   if (!mech->W || !mech->cp || !mech->h_f || !mech->s0) return ADG_ERR_ARG;
@@ -123,8 +165,8 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   size_t o_count = cur.take(sizeof(int32_t) * N);
   size_t o_pl = cur.take(sizeof(int) * N);
   size_t o_pr = cur.take(sizeof(int) * N);
-  const bool mixed = c.precision == ADG_MIXED;
-  int TE = stage_tile(M, Q, c.at_order, mixed, false);
+  const bool mixed = c.precision != ADG_FP64;
+  int TE = stage_tile(M, Q, c.at_order, c.precision, false);
   int target = (N + 2 * 152 - 1) / (2 * 152);
   if (target < TE) TE = target < 4 ? 4 : target;
   const int NT = stage_threads(TE, Q, nr);
@@ -136,21 +178,17 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   size_t o_blocks = cur.take(sizeof(int2) * n_blocks);
   if (cur.off > (size_t)ADG_NOALLOC_SCRATCH_BYTES) return ADG_ERR_NOMEM;
 
-  // host-side tables on the stack (no heap)
-  double sp[SP_NFIELDS * ADG_MAX_SPECIES];
-  Rxn rx[ADG_NOALLOC_MAX_REACTIONS > 0 ? ADG_NOALLOC_MAX_REACTIONS : 1];
-  int sx_off[ADG_MAX_SPECIES + 1];
-  int sx[ADG_NOALLOC_MAX_REACTIONS * NET];
-  if (pack_mechanism(mech, sp, rx, sx_off, sx) != M.nterm) return ADG_ERR_ARG;
-  DF rxf[6 * (ADG_NOALLOC_MAX_REACTIONS > 0 ? ADG_NOALLOC_MAX_REACTIONS : 1)];
-  pack_rxf(rx, nr, rxf);
+  // the host staging of the tables and every launch below under one lock
+  std::lock_guard<std::mutex> lock(g_mutex);
+  HostTables &ht = g_host;
+  if (pack_mechanism(mech, ht.sp, ht.rx, ht.sx_off, ht.sx) != M.nterm) return ADG_ERR_ARG;
+  pack_rxf(ht.rx, nr, ht.rxf);
 
   // once per device: the scratch address and the constant tables. This is the
   // only set-up; it runs on the first call on each device.
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ADG_ERR_CUDA;
   {
-    std::lock_guard<std::mutex> lock(g_mutex);
     if (!g_ready[dev]) {
       void *p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -189,7 +227,9 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   I.dx = c.length / N;
   I.dt = c.dt;
   I.tvb = c.tvb_M * I.dx * I.dx;
-  I.mixed = mixed ? 1 : 0;
+  I.mixed = c.precision;
+  I.ind_floor = indicator_guard(c.precision);
+  I.ind_floor_p = indicator_guard_p(c.precision);
   I.seed = c.seed;
   double acc = 0.0;
   for (int d = 0; d <= MAXD; ++d) {
@@ -225,17 +265,14 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   do {                                         \
     if ((x) != cudaSuccess) return ADG_ERR_CUDA; \
   } while (0)
-  NA_CK(cudaMemcpyAsync(base + o_sp, sp, sizeof(double) * SP_NFIELDS * ns,
-                        cudaMemcpyHostToDevice, s));
-  if (nr > 0) NA_CK(cudaMemcpyAsync(base + o_rx, rx, sizeof(Rxn) * nr, cudaMemcpyHostToDevice, s));
-  if (nr > 0)
-    NA_CK(cudaMemcpyAsync(base + o_rxf, rxf, sizeof(DF) * 6 * nr, cudaMemcpyHostToDevice, s));
-  NA_CK(cudaMemcpyAsync(base + o_sxo, sx_off, sizeof(int) * (ns + 1), cudaMemcpyHostToDevice, s));
-  if (M.nterm > 0)
-    NA_CK(cudaMemcpyAsync(base + o_sx, sx, sizeof(int) * M.nterm, cudaMemcpyHostToDevice, s));
+  NA_CK(put(base, o_sp, ht.sp, sizeof(double) * SP_NFIELDS * ns, s));
+  if (nr > 0) NA_CK(put(base, o_rx, ht.rx, sizeof(Rxn) * nr, s));
+  if (nr > 0) NA_CK(put(base, o_rxf, ht.rxf, sizeof(DF) * 6 * nr, s));
+  NA_CK(put(base, o_sxo, ht.sx_off, sizeof(int) * (ns + 1), s));
+  if (M.nterm > 0) NA_CK(put(base, o_sx, ht.sx, sizeof(int) * M.nterm, s));
   if (w_out_dev != w_in_dev)
     NA_CK(cudaMemcpyAsync(w_out_dev, w_in_dev, sizeof(double) * st, cudaMemcpyDeviceToDevice, s));
-  NA_CK(cudaMemcpyAsync(base + o_inst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
+  NA_CK(put(base, o_inst, &I, sizeof(Inst), s));
   noalloc_maps_kernel<<<(N + 127) / 128, 128, 0, s>>>(
       N, c.n_pe, npf, periodic ? 1 : 0, (int *)I.pf_of_left, (int *)I.pf_of_right, I.count,
       I.flags, I.err, I.step, TE, (int2 *)(base + o_tiles), EPB, (int2 *)(base + o_blocks));
@@ -250,7 +287,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
       A.NT = NT;
       A.O = c.at_order;
       A.visc = 0;
-      NA_CK(launch_stage(M, A, Q, mixed, n_tiles, s));
+      NA_CK(launch_stage(M, A, Q, c.precision, n_tiles, s));
       if (I.limiter != ADG_LIM_NONE) {
         LimArgs L;
         L.insts = (const Inst *)(base + o_inst);

@@ -183,7 +183,8 @@ __global__ void __launch_bounds__(LIM_THREADS) unsync_kernel(Mech M, UnsyncArgs 
       // c. the stage, tile by tile
       A.s = s;
       for (int e0 = first; e0 <= last; e0 += U.TE) {
-        stage_body<Q, MIX, true>(M, A, I, e0, min(U.TE, last + 1 - e0), n, &pdi);
+        stage_body<Q, MIX ? ADG_MIXED : ADG_FP64, true>(M, A, I, e0, min(U.TE, last + 1 - e0),
+                                                        n, &pdi);
         __syncthreads();
       }
       // d. publish the pre-limit outputs, and observe the neighbours'
@@ -232,7 +233,8 @@ static __global__ void unsync_reset_kernel(const Inst *inst, int *pub_in, int *p
 
 template <int Q, int G, bool MIX, int EPB>
 cudaError_t unsync_launch_q(const Mech &M, const UnsyncArgs &U, int nv, cudaStream_t st) {
-  const size_t smem_stage = stage_smem_bytes(U.TE, Q, M.ns, M.nr, M.nterm, U.O, MIX);
+  const size_t smem_stage =
+      stage_smem_bytes(U.TE, Q, M.ns, M.nr, M.nterm, U.O, MIX ? ADG_MIXED : ADG_FP64);
   const size_t smem_lim = limiter_smem_bytes<Q, G, MIX, EPB>(nv, M.ns);
   const size_t smem = smem_stage > smem_lim ? smem_stage : smem_lim;
   if (smem > 200 * 1024) return cudaErrorInvalidValue;

@@ -7,10 +7,10 @@ namespace adg {
 
 cudaError_t launch_stage_visc_mixed(const Mech &M, const StageArgs &A, int Q, int n_tiles,
                                    cudaStream_t st) {
-  return launch_stage_variant<true, true>(M, A, Q, n_tiles, st);
+  return launch_stage_variant<ADG_MIXED, true>(M, A, Q, n_tiles, st);
 }
 
-cudaError_t prepare_visc_mixed() { return prepare_stage_variant<true, true>(); }
+cudaError_t prepare_visc_mixed() { return prepare_stage_variant<ADG_MIXED, true>(); }
 
 cudaError_t upload_tables_visc_mixed(const Basis *tables) { return upload_unit_tables(tables); }
 

@@ -7,10 +7,10 @@ namespace adg {
 
 cudaError_t launch_stage_visc_fp64(const Mech &M, const StageArgs &A, int Q, int n_tiles,
                                    cudaStream_t st) {
-  return launch_stage_variant<false, true>(M, A, Q, n_tiles, st);
+  return launch_stage_variant<ADG_FP64, true>(M, A, Q, n_tiles, st);
 }
 
-cudaError_t prepare_visc_fp64() { return prepare_stage_variant<false, true>(); }
+cudaError_t prepare_visc_fp64() { return prepare_stage_variant<ADG_FP64, true>(); }
 
 cudaError_t upload_tables_visc_fp64(const Basis *tables) { return upload_unit_tables(tables); }
 

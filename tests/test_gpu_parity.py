@@ -128,51 +128,79 @@ def test_no_limiter_and_tvb():
 
 
 def test_ignition_9sp_full_size():
-    """4096 x p4, 21 reactions, 64 PEs, delays up to 4 with AT order 5."""
+    """4096 x p4, 21 reactions, 64 PEs, delays up to 4 with AT order 5, 48 steps:
+    well past the first step (8) at which the largest delay can be in force."""
     wl = W()["ignition-9sp-4096x4"]
     mech = wl.mechanism()
-    g, o = run_both(wl, mech, wl.primitive(mech), 12)
+    g, o = run_both(wl, mech, wl.primitive(mech), 48, chunks=2)
     assert_parity(g, o)
 
 
 def test_detonation_9sp_full_size():
-    """16384 x p3, HLLC, WENO, reflecting/outflow, 256 PEs, delays up to 3."""
+    """16384 x p3, HLLC, WENO, reflecting/outflow, 256 PEs, delays up to 3, 40
+    steps (the largest delay can be in force from step 6)."""
     wl = W()["detonation-9sp-16384x3"]
     mech = wl.mechanism()
-    g, o = run_both(wl, mech, wl.primitive(mech), 8)
+    g, o = run_both(wl, mech, wl.primitive(mech), 40, chunks=2)
     assert_parity(g, o)
+    assert o.flags()[1].sum() > 0
 
 
-def test_detonation_53sp_full_size_sampled():
-    """65536 x p3 with 53 species / 325 reactions: one full-size GPU step, checked
-    on sampled elements. After one step an element depends only on the 6
-    neighbours on each side (a face flux and a limiter stencil per stage), and the
-    first step is synchronous, so the oracle runs 13-element windows around the
-    samples and their centres must match."""
+def test_detonation_53sp_full_size_windows():
+    """65536 x p3 with 53 species / 325 reactions, 1024 PEs, SAA delays up to 4
+    with AT order 4: 10 full-size GPU steps (the largest delay can be in force
+    from step 7), checked on windows of three whole PEs. An element's update in
+    one step depends on the elements within 6 of it (a face flux and a limiter
+    stencil in each of 3 stages), so an oracle run on the window alone, with its
+    PE faces numbered as in the full run (the same SAA draws), agrees with the
+    full run on the elements further than 60 from a cut; that part holds both of
+    the window's inner PE faces, where the AT flux and the AT-WENO neighbour
+    read the history ring. Windows: at the reflecting wall, across the driver's
+    shock, and in the ambient gas."""
+    from concurrent.futures import ThreadPoolExecutor
     wl = W()["detonation-53sp-65536x3"]
     mech = wl.mechanism()
     prim = wl.primitive(mech)
+    n_steps = 10
+    assert n_steps >= wl.max_delay + wl.at_order + 2
     g = adg.ADG(mech, [wl])
     g.set_primitive(prim)
-    g.step(1)
+    g.step(n_steps)
     g.check()
     w = g.get_state()
-    rng = np.random.default_rng(0)
+    gl, gc = g.flags()
+    scale = scales(w, mech)
+    epe = wl.n_elem // wl.n_pe
     dx = wl.length / wl.n_elem
-    samples = sorted(set([6, 3276, 3277, 3280, wl.n_elem - 7] +
-                         list(rng.integers(6, wl.n_elem - 7, size=6))))
-    for e in samples:
-        win = I.scaled(wl, 13, 1)
-        win.x0 = wl.x0 + (e - 6) * dx
-        win.bc_left = win.bc_right = I.BC_OUTFLOW
+    reach = 6 * n_steps
+
+    def window(j):
+        """Oracle on global PEs j-1, j, j+1: (first element, valid range, oracle)."""
+        e0 = epe * (j - 1)
+        win = I.scaled(wl, 3 * epe, 3)
+        win.x0 = wl.x0 + e0 * dx
+        win.face0 = j - 1
+        win.bc_left = wl.bc_left if j == 1 else I.BC_OUTFLOW
+        win.bc_right = wl.bc_right if j + 2 == wl.n_pe else I.BC_OUTFLOW
         o = O.Oracle(win, mech)
-        o.set_primitive(prim[:, e - 6:e + 7])
-        o.step(1)
-        ref = o.state()[:, 6:7]
-        got = w[:, e:e + 1]
-        scale = scales(w, mech)
+        o.set_primitive(prim[:, e0:e0 + 3 * epe])
+        o.step(n_steps)
+        lo = 0 if j == 1 else reach
+        hi = 3 * epe if j + 2 == wl.n_pe else 3 * epe - reach
+        return e0, lo, hi, o
+
+    shock = int(0.05 * wl.n_elem) // epe
+    with ThreadPoolExecutor(3) as ex:
+        res = list(ex.map(window, [1, shock, 700]))
+    for e0, lo, hi, o in res:
+        assert lo < epe and hi > 2 * epe  # both inner PE faces are checked
+        ref = o.state()[:, lo:hi]
+        got = w[:, e0 + lo:e0 + hi]
         err = (np.abs(got - ref) / np.maximum(scale, 1e-300)[:, None, None]).max()
-        assert err <= TOL, (e, err)
+        assert err <= TOL, (e0, err)
+        ol, oc = o.flags()
+        assert np.array_equal(gl[:, e0 + lo:e0 + hi], ol[:, lo:hi]), e0
+        assert np.array_equal(gc[e0 + lo:e0 + hi], oc[lo:hi]), e0
 
 
 def test_ensemble_of_instances_in_one_context():
