@@ -70,9 +70,11 @@ extern "C" {
  * ADG_MIXED: the numerical flux, the DG volume/surface/source assembly and the
  * troubled-cell indicator and WENO reconstruction in float; in double the
  * state at the Gauss points, the temperature from the internal energy (T, ln T
- * and 1/T to about one ulp), the whole chemistry (Arrhenius and equilibrium
- * exponents and exponentials, mass-action products, rates of progress and
- * production rates), the AT level sums and the RK accumulation.
+ * and 1/T to about one ulp), the Arrhenius and equilibrium exponents and their
+ * exponentials, the AT level sums and the RK accumulation; the mass-action
+ * products, rates of progress and production rates in float pairs (about 48
+ * significant bits) from the double rate constants, so that no rate constant
+ * is rounded to float before it is used.
  * ADG_MIXED_F32CHEM: as ADG_MIXED, but the Arrhenius and equilibrium exponents
  * as float pairs (about 1e-12 absolute), their exponentials rounded once to
  * float, and the mass-action products and production rates in float. Not

@@ -65,8 +65,10 @@ template <int PREC>
 struct Prec {
   static constexpr bool mix = PREC != ADG_FP64;
   static constexpr bool fchem = PREC == ADG_MIXED_F32CHEM;
+  static constexpr bool dfchem = PREC == ADG_MIXED;  // mass action in float pairs
   using dg = dg_t<mix>;
-  using ct = typename std::conditional<fchem, float, double>::type;
+  using ct = typename std::conditional<fchem, float,
+                                       typename std::conditional<dfchem, DF, double>::type>::type;
 };
 
 // Shared-memory footprint (bytes) of a stage tile of TE elements with up to O AT
@@ -175,6 +177,28 @@ __device__ __forceinline__ DF df_split_int(double x) {
   return DF{h, d2f_int(x - f2d_exact(h))};
 }
 
+// x as a float pair (hi + lo, about 48 significant bits) without the FP64 unit:
+// hi = x rounded to float (d2f_int), lo = the remainder x - hi, which is the
+// integer r formed by the 29 significand bits below float precision (less 2^29
+// when hi was rounded up) times 2^(E - 52), converted to float and scaled by
+// powers of two. For x outside the normal float range lo is 0 (hi is then 0, a
+// subnormal float or an infinity); below about 2^-97 lo itself underflows.
+__device__ __forceinline__ DF d2df_int(double x) {
+  const unsigned hi32 = (unsigned)__double2hiint(x), lo32 = (unsigned)__double2loint(x);
+  const int eb = (int)((hi32 >> 20) & 0x7ffu);
+  const float h = d2f_int(x);
+  const int ef = eb - 1023 + 127;
+  if (ef <= 0 || ef >= 255) return DF{h, 0.0f};
+  const unsigned rem = lo32 & 0x1fffffffu;
+  const unsigned mlow = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
+  const bool up = rem > 0x10000000u || (rem == 0x10000000u && (mlow & 1u));
+  const int r = up ? (int)rem - 0x20000000 : (int)rem;
+  // r 2^-52 is exact in float, and 2^(eb - 1023) is a normal float here
+  float lo = __fmul_rn(__fmul_rn((float)r, 2.220446049250313e-16f), __int_as_float(ef << 23));
+  if (hi32 & 0x80000000u) lo = -lo;
+  return DF{h, lo};
+}
+
 // 1/x to a relative error below 2^-44, for x whose float is normal: a float
 // seed (the fraction truncated to 23 bits on the integer pipeline, the
 // correctly rounded float reciprocal: within 1.5 2^-23) and one Newton-Raphson
@@ -210,6 +234,7 @@ __device__ __forceinline__ R to_r(double x) {
 template <typename R, typename C>
 __device__ __forceinline__ R conv_r(C x) {
   if constexpr (std::is_same<R, C>::value) return x;
+  else if constexpr (std::is_same<C, DF>::value) return __fadd_rn(x.hi, x.lo);
   else if constexpr (std::is_same<R, float>::value) return d2f_int(x);
   else return f2d_exact(x);
 }
@@ -377,7 +402,7 @@ template <int Q, int PREC, bool UNSYNC, bool VISC = false>
 __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, const Inst &I,
                                            const int e0, const int te, const int64_t nstep,
                                            const PeDelays *pd) {
-  constexpr bool MIX = Prec<PREC>::mix, FCHEM = Prec<PREC>::fchem;
+  constexpr bool MIX = Prec<PREC>::mix, FCHEM = Prec<PREC>::fchem, DFCHEM = Prec<PREC>::dfchem;
   using DG = typename Prec<PREC>::dg;  // flux and DG operator
   using CT = typename Prec<PREC>::ct;  // chemistry
   extern __shared__ __align__(16) double sm[];
@@ -469,7 +494,8 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       }
       if (k < n_term) {
         sterm[k] = term >> 8;
-        scoef[k] = (CT)(signed char)(term & 0xff);
+        if constexpr (DFCHEM) scoef[k] = DF{(float)(signed char)(term & 0xff), 0.0f};
+        else scoef[k] = (CT)(signed char)(term & 0xff);
       }
       if (k <= ns) soff[k] = off;
       if (k < 32) {
@@ -751,9 +777,10 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
           const float r = (__float_as_int(w) < 0) ? 0.0f : w;
           scc[(size_t)i * TQ + t] = r * sIW[i];
         } else {
+          // rho Y_i / W_i as a float pair from the FP64 nodal value, no FP64 op
           const double wd = snw[at];
-          const double r = (__double2hiint(wd) < 0) ? 0.0 : wd;
-          scc[(size_t)i * TQ + t] = r * ssp[SP_INVW * ns + i];
+          const DF r = (__double2hiint(wd) < 0) ? DF{0.0f, 0.0f} : d2df_int(wd);
+          scc[(size_t)i * TQ + t] = df_mul(r, d2df_int(ssp[SP_INVW * ns + i]));
         }
         f = u * w;
       } else if (v == 0) {
@@ -795,34 +822,81 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   for (int item = tid; item < nr * teq; item += nth, w3.next()) {
     const int j = w3.o, t = w3.i;
     const Rxn &Rx = srx[j];
-    CT fwd, rev;
-    if constexpr (FCHEM) {
-      // arguments in df32 and the FP32-pipe exp: no FP64 instruction and no
-      // precision conversion per item
-      const DF lnT = sdfT[2 * t], invT = sdfT[2 * t + 1], *c = srxf + 6 * j;
-      fwd = exp_df(df_fma(c[2], invT, df_fma(c[1], lnT, c[0])), stab->tf);
-      rev = exp_df(df_fma(c[5], invT, df_fma(c[4], lnT, c[3])), stab->tf);
-    } else {
-      // FP64 arguments, the FP64 exponential on the integer pipeline
+    if constexpr (DFCHEM) {
+      // FP64 arguments and FP64 exponentials (integer pipeline); the mass action
+      // in float pairs (48 bits) on the FP32 pipe, so that k_f and k_r reach
+      // the rate of progress unrounded without FP64 products
       const double lnT = slnT[t], invT = sinvT[t];
-      fwd = iexp(fma(Rx.mEaR, invT, fma(Rx.b, lnT, Rx.lnA)), *stab);
-      rev = iexp(fma(Rx.kr2, invT, fma(Rx.kr1, lnT, Rx.kr0)), *stab);
-    }
+      const double kf = iexp(fma(Rx.mEaR, invT, fma(Rx.b, lnT, Rx.lnA)), *stab);
+      const double kr = iexp(fma(Rx.kr2, invT, fma(Rx.kr1, lnT, Rx.kr0)), *stab);
+      DF fwd = d2df_int(kf), rev = d2df_int(kr);
+      if (!(fabsf(fwd.hi) < 3.0e38f) || !(fabsf(rev.hi) < 3.0e38f)) {
+        // a rate constant beyond the float range: this item in FP64
+        double f = kf, r = kr;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (Rx.rn[k] == 0) break;
-      CT cc = scc[(size_t)Rx.rs[k] * TQ + t];
-      fwd *= cc;
-      if (Rx.rn[k] > 1) fwd *= cc;
-    }
+        for (int k = 0; k < 4; ++k) {
+          if (Rx.rn[k] == 0) break;
+          const DF c = scc[(size_t)Rx.rs[k] * TQ + t];
+          const double cd = f2d_exact(c.hi) + f2d_exact(c.lo);
+          f *= cd;
+          if (Rx.rn[k] > 1) f *= cd;
+        }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (Rx.pn[k] == 0) break;
-      CT cc = scc[(size_t)Rx.ps[k] * TQ + t];
-      rev *= cc;
-      if (Rx.pn[k] > 1) rev *= cc;
+        for (int k = 0; k < 4; ++k) {
+          if (Rx.pn[k] == 0) break;
+          const DF c = scc[(size_t)Rx.ps[k] * TQ + t];
+          const double cd = f2d_exact(c.hi) + f2d_exact(c.lo);
+          r *= cd;
+          if (Rx.pn[k] > 1) r *= cd;
+        }
+        sq[(size_t)j * TQ + t] = d2df_int(f - r);
+        continue;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (Rx.rn[k] == 0) break;
+        const DF c = scc[(size_t)Rx.rs[k] * TQ + t];
+        fwd = df_mul(fwd, c);
+        if (Rx.rn[k] > 1) fwd = df_mul(fwd, c);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (Rx.pn[k] == 0) break;
+        const DF c = scc[(size_t)Rx.ps[k] * TQ + t];
+        rev = df_mul(rev, c);
+        if (Rx.pn[k] > 1) rev = df_mul(rev, c);
+      }
+      sq[(size_t)j * TQ + t] = df_sub(fwd, rev);
+    } else {
+      CT fwd, rev;
+      if constexpr (FCHEM) {
+        // arguments in df32 and the FP32-pipe exp: no FP64 instruction and no
+        // precision conversion per item
+        const DF lnT = sdfT[2 * t], invT = sdfT[2 * t + 1], *c = srxf + 6 * j;
+        fwd = exp_df(df_fma(c[2], invT, df_fma(c[1], lnT, c[0])), stab->tf);
+        rev = exp_df(df_fma(c[5], invT, df_fma(c[4], lnT, c[3])), stab->tf);
+      } else {
+        // FP64 arguments, the FP64 exponential on the integer pipeline
+        const double lnT = slnT[t], invT = sinvT[t];
+        fwd = iexp(fma(Rx.mEaR, invT, fma(Rx.b, lnT, Rx.lnA)), *stab);
+        rev = iexp(fma(Rx.kr2, invT, fma(Rx.kr1, lnT, Rx.kr0)), *stab);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (Rx.rn[k] == 0) break;
+        CT cc = scc[(size_t)Rx.rs[k] * TQ + t];
+        fwd *= cc;
+        if (Rx.rn[k] > 1) fwd *= cc;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (Rx.pn[k] == 0) break;
+        CT cc = scc[(size_t)Rx.ps[k] * TQ + t];
+        rev *= cc;
+        if (Rx.pn[k] > 1) rev *= cc;
+      }
+      sq[(size_t)j * TQ + t] = fwd - rev;
     }
-    sq[(size_t)j * TQ + t] = fwd - rev;
   }
   __syncthreads();
 
@@ -831,10 +905,17 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   Walk w4(tid, nth, teq);
   for (int item = tid; item < ns * teq; item += nth, w4.next()) {
     const int i = w4.o, t = w4.i;
-    CT acc = CT(0);
-    for (int k = soff[i]; k < soff[i + 1]; ++k)
-      acc = fma(scoef[k], sq[(size_t)sterm[k] * TQ + t], acc);
-    swd[(size_t)i * TQ + t] = acc;
+    if constexpr (DFCHEM) {
+      DF acc = {0.0f, 0.0f};
+      for (int k = soff[i]; k < soff[i + 1]; ++k)
+        acc = df_fma(scoef[k], sq[(size_t)sterm[k] * TQ + t], acc);
+      swd[(size_t)i * TQ + t] = acc;
+    } else {
+      CT acc = CT(0);
+      for (int k = soff[i]; k < soff[i + 1]; ++k)
+        acc = fma(scoef[k], sq[(size_t)sterm[k] * TQ + t], acc);
+      swd[(size_t)i * TQ + t] = acc;
+    }
   }
   // the diffusive flux of both sides of every face level, by groups of lanes
   if constexpr (VISC) {

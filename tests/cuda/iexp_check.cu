@@ -3,7 +3,8 @@
 // host (bit for bit), and both it and CUDA's exp against expl in extended
 // precision on the host; the mixed variant's table logarithm likewise (against
 // its host build and logl), and its Newton-Raphson reciprocal (csrc/adg_device.cuh)
-// against the exact reciprocal. Prints one JSON line.
+// against the exact reciprocal, and its two-step reciprocal and integer-pipe
+// split of a double into a float pair. Prints one JSON line.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -23,6 +24,15 @@ __global__ void eval_log(const double *x, double *ln, double *rc, int n, adg::Lo
   if (i >= n) return;
   ln[i] = adg::log_tab(x[i], tb);
   rc[i] = adg::recip_nr(x[i]);
+}
+
+__global__ void eval_split(const double *x, float *hi, float *lo, double *rc2, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const adg::DF d = adg::d2df_int(x[i]);
+  hi[i] = d.hi;
+  lo[i] = d.lo;
+  rc2[i] = adg::recip_nr2(x[i]);
 }
 
 static double ulp_err(double got, long double ref) {
@@ -93,9 +103,33 @@ int main() {
     const long double rr = 1.0L / (long double)y[i];
     recip_max_rel = fmax(recip_max_rel, (double)fabsl(((long double)c[i] - rr) / rr));
   }
+  // the float-pair split and the two-step reciprocal, on the same values and on
+  // rate-constant-like magnitudes over the float range
+  for (int i = 0; i < n; i += 3) y[i] = ldexp(0.5 + (double)rand() / RAND_MAX, (i / 3) % 216 - 96);
+  float *dh, *dlo;
+  double *dc2;
+  if (cudaMalloc(&dh, n * 4) || cudaMalloc(&dlo, n * 4) || cudaMalloc(&dc2, n * 8)) return 2;
+  cudaMemcpy(dy, y.data(), n * 8, cudaMemcpyHostToDevice);
+  eval_split<<<(n + 255) / 256, 256>>>(dy, dh, dlo, dc2, n);
+  std::vector<float> hh(n), ll(n);
+  std::vector<double> c2(n);
+  cudaMemcpy(hh.data(), dh, n * 4, cudaMemcpyDeviceToHost);
+  cudaMemcpy(ll.data(), dlo, n * 4, cudaMemcpyDeviceToHost);
+  cudaMemcpy(c2.data(), dc2, n * 8, cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  long long split_hi_mismatch = 0;
+  double split_max_rel = 0.0, recip2_max_rel = 0.0;
+  for (int i = 0; i < n; ++i) {
+    if (hh[i] != (float)y[i]) ++split_hi_mismatch;
+    const long double sum = (long double)hh[i] + (long double)ll[i];
+    split_max_rel = fmax(split_max_rel, (double)fabsl((sum - (long double)y[i]) / y[i]));
+    const long double rr = 1.0L / (long double)y[i];
+    recip2_max_rel = fmax(recip2_max_rel, (double)fabsl(((long double)c2[i] - rr) / rr));
+  }
   printf("{\"n\": %d, \"host_mismatch\": %lld, \"max_ulp\": %.4f, \"cuda_exp_max_ulp\": %.4f, "
          "\"log_host_mismatch\": %lld, \"log_max_ulp\": %.4f, \"recip_max_rel\": %.3g, "
+         "\"recip2_max_rel\": %.3g, \"split_hi_mismatch\": %lld, \"split_max_rel\": %.3g, "
          "\"cuda\": \"%s\"}\n", n, mismatch, max_ulp, cuda_max_ulp, log_mismatch, log_max_ulp,
-         recip_max_rel, cudaGetErrorString(err));
+         recip_max_rel, recip2_max_rel, split_hi_mismatch, split_max_rel, cudaGetErrorString(err));
   return err == cudaSuccess ? 0 : 1;
 }

@@ -3,7 +3,10 @@ the host build of the same function, and within 0.6 units in the last place of
 the exact value (expl in extended precision) over the argument range used;
 CUDA's own exp is measured beside it for reference. The mixed variant's table
 logarithm on the GPU: bit for bit its host build and within 1.5 units in the
-last place of logl; its Newton-Raphson reciprocal within 2^-44 of 1/x."""
+last place of logl; its Newton-Raphson reciprocal within 2^-44 of 1/x, and the
+two-step one within 2^-51. The integer-pipe split of a double into a float
+pair: the high part is the double rounded to float, and the pair is within
+2^-47 of the double, for magnitudes from 2^-97 to the float maximum."""
 import json
 import os
 import subprocess
@@ -27,3 +30,6 @@ def test_integer_exp_on_gpu_matches_host_and_exact(tmp_path):
     assert rec["log_host_mismatch"] == 0, rec
     assert rec["log_max_ulp"] <= 1.5, rec
     assert rec["recip_max_rel"] <= 2.0 ** -44, rec
+    assert rec["recip2_max_rel"] <= 2.0 ** -51, rec
+    assert rec["split_hi_mismatch"] == 0, rec
+    assert rec["split_max_rel"] <= 2.0 ** -47, rec
