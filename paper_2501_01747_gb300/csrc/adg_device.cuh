@@ -239,6 +239,19 @@ __device__ __forceinline__ R conv_r(C x) {
   else return f2d_exact(x);
 }
 
+// The trace of one variable's modes w[0..Q) at xi = +1 (right = false: sum_j
+// w_j) or at xi = -1 (right = true: sum_j (-1)^j w_j), in FP64 and in the order
+// of the stage kernel's face phase. Every trace that enters the history ring is
+// formed by it, so that a face reads the same value from the ring as it would
+// form itself.
+template <int Q>
+__device__ __forceinline__ double trace_of(const double *w, bool right) {
+  double a = 0.0;
+#pragma unroll
+  for (int j = 0; j < Q; ++j) a += (right && (j & 1)) ? -w[j] : w[j];
+  return a;
+}
+
 // A value of the history ring. Written by another CTA of the same launch in the
 // unsynchronised mode, so read from L2 (the point of coherence), not from a
 // possibly stale L1 line of an earlier level in the same slot.
@@ -487,7 +500,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       if (k < n_rx4) dst[k] = rx4;
       if (k < n_sp) {
         ssp[k] = spv;
-        if constexpr (MIX) sspD[k] = (DG)spv;
+        if constexpr (MIX) sspD[k] = conv_r<DG>(spv);
       }
       if constexpr (FCHEM) {
         if (k < n_rxf) srxf[k] = rf;
@@ -515,6 +528,11 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
     const int span = (te + 2) * Q, n_tile = nv * span;
     const int n_wn = (A.s == 0) ? 0 : nv * te * Q;
     const int total = n_tile + n_wn;
+    // (variable, position) of this thread's loads in the tile, without a
+    // division per load; the w^n region takes its own walk from its first load
+    Walk wt(tid, nth, span);
+    const int k0 = tid + ((n_tile - tid + nth - 1) / nth) * nth - n_tile;
+    Walk ww(k0 > 0 ? k0 : 0, nth, te * Q);
     for (int base = tid; base < total; base += BATCH * nth) {
       double xs[BATCH];
       double *dst[BATCH];
@@ -523,7 +541,8 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         const int idx = base + b * nth;
         dst[b] = nullptr;
         if (idx < n_tile) {
-          const int v = idx / span, r = idx - v * span;
+          const int v = wt.o, r = wt.i;
+          wt.next();
           const int le = r / Q, j = r - le * Q;
           int e = e0 - 1 + le;
           if (e < 0) e = periodic ? e + N : 0;
@@ -531,7 +550,8 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
           xs[b] = A_win[((size_t)v * N + e) * Q + j];
           dst[b] = sw + ((size_t)v * (TE + 2) + le) * Q + j;
         } else if (idx < total) {
-          const int k = idx - n_tile, v = k / (te * Q), r = k - v * te * Q;
+          const int v = ww.o, r = ww.i;
+          ww.next();
           xs[b] = A_wacc[((size_t)v * N + e0) * Q + r];
           dst[b] = swn + (size_t)v * TQ + r;
         }
@@ -569,7 +589,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       double a = 0.0;
 #pragma unroll
       for (int j = 0; j < Q; ++j) a += (side && (j & 1)) ? -wi[j] : wi[j];
-      str[(size_t)f * 2 * nv + side * nv + v] = (DG)a;
+      str[(size_t)f * 2 * nv + side * nv + v] = conv_r<DG>(a);
       continue;
     }
     const int v = w2a.o, t = w2a.i;
@@ -580,7 +600,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
 #pragma unroll
     for (int j = 0; j < Q; ++j) acc += wi[j] * Pq[j];
     snw[(size_t)v * TQ + t] = acc;
-    if constexpr (MIX) sfx[(size_t)v * TQ + t] = (DG)acc;  // converted once, for phase 2c
+    if constexpr (MIX) sfx[(size_t)v * TQ + t] = conv_r<DG>(acc);  // converted once, for phase 2c
     if (visc) {
       const double *qi = sqw + ((size_t)v * (TE + 2) + e + 1) * Q;
       double aq = 0.0;
@@ -616,8 +636,8 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       const double *br = I.ring_in + ring_trace(I, lv, A.s, pf, 1);
       if constexpr (MIX || UNSYNC) {
         for (int v = 0; v < nv; ++v) {
-          wl[v] = (DG)ring_load<UNSYNC>(bl + v);
-          wr[v] = (DG)ring_load<UNSYNC>(br + v);
+          wl[v] = conv_r<DG>(ring_load<UNSYNC>(bl + v));
+          wr[v] = conv_r<DG>(ring_load<UNSYNC>(br + v));
         }
         num_flux_t<DG>(sspD, ns, I.flux, wl, wr, fl);
       } else {
@@ -932,7 +952,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
     const int f = w5.o, v = w5.i;
     const int k = sk[f];
     auto level = [&](int m) {
-      double x = (double)sflx[((size_t)m * NF + f) * nv + v];
+      double x = conv_r<double>(sflx[((size_t)m * NF + f) * nv + v]);
       if (visc) {
         const double *vt = sqt + ((size_t)m * NF + f) * 4 * nv;
         x -= 0.5 * (vt[2 * nv + v] + vt[3 * nv + v]);
@@ -944,7 +964,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       acc *= I.at[k][0];
       for (int m = 1; m < I.at_order; ++m) acc = fma(I.at[k][m], level(m), acc);
     }
-    sfh[(size_t)f * nv + v] = (DG)acc;
+    sfh[(size_t)f * nv + v] = conv_r<DG>(acc);
   }
   __syncthreads();
   // The successor (the limiter) is released only now: released at entry, its
@@ -1016,22 +1036,16 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       if (pr >= 0) {
         // left element of the PE face: its trace at xi = +1
         size_t b = ring_block(I, nstep, A.s, pr, 0) + (size_t)v * Q;
-        double tr = 0.0;
-        for (int i = 0; i < Q; ++i) {
-          tr += wi[i];
-          I.ring_pre[b + i] = out[i];
-        }
-        if constexpr (!UNSYNC) I.ring_in[ring_trace(I, nstep, A.s, pr, 0) + v] = tr;
+        for (int i = 0; i < Q; ++i) I.ring_pre[b + i] = out[i];
+        if constexpr (!UNSYNC)
+          I.ring_in[ring_trace(I, nstep, A.s, pr, 0) + v] = trace_of<Q>(wi, false);
       }
       if (pl >= 0) {
         // right element of the PE face: its trace at xi = -1
         size_t b = ring_block(I, nstep, A.s, pl, 1) + (size_t)v * Q;
-        double tr = 0.0;
-        for (int i = 0; i < Q; ++i) {
-          tr += ((i & 1) ? -1.0 : 1.0) * wi[i];
-          I.ring_pre[b + i] = out[i];
-        }
-        if constexpr (!UNSYNC) I.ring_in[ring_trace(I, nstep, A.s, pl, 1) + v] = tr;
+        for (int i = 0; i < Q; ++i) I.ring_pre[b + i] = out[i];
+        if constexpr (!UNSYNC)
+          I.ring_in[ring_trace(I, nstep, A.s, pl, 1) + v] = trace_of<Q>(wi, true);
       }
     }
   }
@@ -1363,16 +1377,19 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
     constexpr int BATCH = 8;
     const bool periodic = (I.bc_left == ADG_BC_PERIODIC);
     const int span = (te + 2) * Q, total = nv * span, nth = blockDim.x;
+    Walk wk(threadIdx.x, nth, span);  // (variable, position in the span) of each load
     for (int base = threadIdx.x; base < total; base += BATCH * nth) {
       double xs[BATCH];
       int dst[BATCH];
 #pragma unroll
       for (int b = 0; b < BATCH; ++b) {
         const int idx = base + b * nth;
+        const int v = wk.o, r = wk.i;
+        wk.next();
         dst[b] = -1;
         xs[b] = 0.0;
         if (idx < total) {
-          const int v = idx / span, r = idx - v * span, le = r / Q, j = r - le * Q;
+          const int le = r / Q, j = r - le * Q;
           int src = e0 - 1 + le;
           bool mirror = false;
           if (src < 0 || src >= N) {

@@ -133,19 +133,15 @@ __global__ void __launch_bounds__(LIM_THREADS) unsync_kernel(Mech M, UnsyncArgs 
       const double *win = stage_input(I, s);
       // a. the traces of the stage input at the PE faces: the first element's at
       // xi = -1 (right side of the left PE face), the last element's at xi = +1
-      // (left side of the right PE face), summed as the stage kernel sums them
+      // (left side of the right PE face), formed as the stage kernel forms them
       for (int t = tid; t < 2 * nv; t += nth) {
         const int side = t / nv, v = t - side * nv;
         if (side == 0 && pfl >= 0) {
           const double *w = win + ((size_t)v * N + first) * Q;
-          double tr = 0.0;
-          for (int j = 0; j < Q; ++j) tr += ((j & 1) ? -1.0 : 1.0) * w[j];
-          I.ring_in[ring_trace(I, n, s, pfl, 1) + v] = tr;
+          I.ring_in[ring_trace(I, n, s, pfl, 1) + v] = trace_of<Q>(w, true);
         } else if (side == 1 && pfr >= 0) {
           const double *w = win + ((size_t)v * N + last) * Q;
-          double tr = 0.0;
-          for (int j = 0; j < Q; ++j) tr += w[j];
-          I.ring_in[ring_trace(I, n, s, pfr, 0) + v] = tr;
+          I.ring_in[ring_trace(I, n, s, pfr, 0) + v] = trace_of<Q>(w, false);
         }
       }
       __syncthreads();
