@@ -130,6 +130,14 @@ typedef struct {
    * ignores the other four fields. */
   int viscous;             /* 0: Euler; 1: with f^d */
   double mu_ref, T_mu, mu_exp, prandtl; /* Pa s, K, -, - (T_mu, prandtl > 0) */
+  /* Subdomain (Sec. 3.1: each PE's subdomain exchanges its boundary elements
+   * with its neighbours' buffer elements). pe_end = 0: the whole domain.
+   * pe_end > 0: the PEs [pe_begin, pe_end) of the domain the fields above
+   * describe (n_elem, n_pe, length and boundaries of the WHOLE domain), as an
+   * instance of its own with a buffer element at each side that borders another
+   * subdomain; see adg_part_layout and adg_part_block. Not with viscous terms,
+   * the unsynchronised mode or adg_step_noalloc. */
+  int pe_begin, pe_end;
 } adg_config;
 
 typedef struct adg_ctx adg_ctx;
@@ -206,6 +214,59 @@ int adg_get_state_device(adg_ctx *ctx, int instance, double *w_dev, void *stream
  * ADG_ERR_CUDA; non-physical states and missing history levels found on the
  * device are reported by adg_status. */
 int adg_step(adg_ctx *ctx, int n_steps, void *stream);
+
+/* ---- Domain decomposition (Sec. 3.1, Fig. 1: the PE boundary elements' DoFs go
+ * to the neighbours' buffer elements; Sec. 3.2: the buffers may hold delayed
+ * levels and the flux at a PE face uses the common delayed level; Sec. 3.3: the
+ * limiter's neighbours are exchanged after every stage; Sec. 4: the delays).
+ *
+ * A subdomain instance (adg_config.pe_end > 0) holds the elements of its PEs,
+ * [floor(pe_begin N / P), floor(pe_end N / P)) of the whole domain's N elements
+ * and P PEs, plus one buffer element at each cut side (a side that borders
+ * another subdomain, also across a periodic boundary). Its PE faces are its
+ * own PEs' plus the cut faces; their delays are the whole domain's (SAA draws
+ * by the whole domain's face number), and dx is the whole domain's. Beyond a
+ * buffer element the subdomain ends in an outflow boundary: the buffers are
+ * computed like the other elements, but the exchange overwrites their data
+ * before any owned element reads it, so that the owned elements advance exactly
+ * as in the whole-domain instance. Its arrays (states, primitives, flags) are
+ * [..][n_local][..] with the buffers included.
+ *
+ * adg_part_layout: for a config, the subdomain's element count n_local, the
+ * whole domain's index of its local element 0 (modulo n_elem: -1 for a
+ * periodic subdomain that starts at PE 0), and which sides are cut (0/1).
+ * The whole domain (pe_end = 0, or all PEs) gives n_elem, 0, 0, 0.
+ * Errors: ADG_ERR_ARG (NULL config, bad PE range). */
+int adg_part_layout(const adg_config *cfg, int *n_local, int *elem0, int *cut_left,
+                    int *cut_right);
+
+/* One half of RK stage `stage` of the current step of every instance, enqueued on
+ * `stream` as plain launches (no graph): half 0 the stage kernels (Eq. 5 and the
+ * RK update, giving the pre-limit output), half 1 the troubled-cell indicator
+ * and limiter (Sec. 3.3), and after the last stage the step counters' advance.
+ * The halves of stages 0..S-1 in order are one adg_step. Between them the
+ * caller moves the subdomains' boundary blocks (adg_part_block): before half 0
+ * of stage s the stage inputs, before half 1 the pre-limit outputs.
+ * Errors: ADG_ERR_ARG (NULL, stage or half out of range), ADG_ERR_CUDA. */
+int adg_step_stage(adg_ctx *ctx, int stage, int half, void *stream);
+
+/* Move one boundary block, [nv][p+1] doubles in caller-owned device memory
+ * blk_dev, of instance `instance` at side `side` (0 left, 1 right) for stage
+ * `stage` of the current step, on `stream` (asynchronous, device-to-device).
+ * what = ADG_PART_INPUT: the stage input (at stage 0 the state at the start of
+ * the step); ADG_PART_PRELIMIT: the pre-limit output of that stage.
+ * import = 0 (export): copies the owned element at that side (the neighbour's
+ * buffer) into blk_dev; import = 1: writes blk_dev into the buffer element at
+ * that side, and for ADG_PART_PRELIMIT also into the cut face's pre-limit
+ * history (the levels the AT-WENO neighbour of Eq. 11 reads). Call the exports
+ * of a stage's pre-limit output after its half 0 and the imports before its
+ * half 1; the stage inputs' before half 0 of the stage.
+ * Errors: ADG_ERR_ARG (NULL, bad instance, side that is not cut, bad what or
+ * stage), ADG_ERR_CUDA. */
+#define ADG_PART_INPUT 0
+#define ADG_PART_PRELIMIT 1
+int adg_part_block(adg_ctx *ctx, int instance, int what, int side, int stage, double *blk_dev,
+                   int import, void *stream);
 
 /* Synchronise and report the first device-side error since the last reset
  * (ADG_ERR_NONPHYSICAL or ADG_ERR_HISTORY), with the instance, element, step and

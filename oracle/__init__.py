@@ -49,7 +49,8 @@ class Cfg(C.Structure):
                 ("max_delay", C.c_int), ("delay_probs", C.POINTER(C.c_double)),
                 ("seed", C.c_uint64), ("tvb_M", C.c_double), ("integrator", C.c_int),
                 ("viscous", C.c_int), ("mu_ref", C.c_double), ("T_mu", C.c_double),
-                ("mu_exp", C.c_double), ("prandtl", C.c_double), ("face0", C.c_int)]
+                ("mu_exp", C.c_double), ("prandtl", C.c_double), ("face0", C.c_int),
+                ("pe_begin", C.c_int), ("pe_end", C.c_int)]
 
 
 _lib = None
@@ -66,6 +67,10 @@ def lib():
         for name in ("or_set_primitive", "or_set_state", "or_get_state", "or_get_temperature"):
             getattr(_lib, name).argtypes = [C.c_void_p, d]
         _lib.or_step.argtypes = [C.c_void_p, C.c_int]
+        _lib.or_stage.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        ip = C.POINTER(C.c_int)
+        _lib.or_part_layout.argtypes = [C.c_void_p, ip, ip, ip, ip]
+        _lib.or_part_block.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, d, C.c_int]
         _lib.or_steps_done.restype = C.c_int64
         _lib.or_steps_done.argtypes = [C.c_void_p]
         _lib.or_get_flags.argtypes = [C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_int32)]
@@ -135,7 +140,8 @@ def make_cfg(wl, dt=None):
               getattr(wl, "integrator", 0), getattr(wl, "viscous", 0),
               getattr(wl, "mu_ref", 0.0), getattr(wl, "T_mu", 300.0),
               getattr(wl, "mu_exp", 0.7), getattr(wl, "prandtl", 0.7),
-              int(getattr(wl, "face0", 0)))
+              int(getattr(wl, "face0", 0)), int(getattr(wl, "pe_begin", 0)),
+              int(getattr(wl, "pe_end", 0)))
     return cfg, probs
 
 
@@ -208,10 +214,14 @@ class Oracle:
         self.mh = MechHandle(self.mech)
         self.cfg, self._probs = make_cfg(wl)
         self.nv = self.mh.ns + 2
-        self.shape = (self.nv, wl.n_elem, wl.p + 1)
         self.h = lib().or_create(C.byref(self.cfg), self.mh.ref)
         if not self.h:
             raise ValueError("oracle rejected the configuration")
+        lay = [C.c_int(0) for _ in range(4)]
+        lib().or_part_layout(self.h, *[C.byref(x) for x in lay])
+        self.n_local, self.elem0 = lay[0].value, lay[1].value
+        self.cut = (bool(lay[2].value), bool(lay[3].value))
+        self.shape = (self.nv, self.n_local, wl.p + 1)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -236,19 +246,39 @@ class Oracle:
         if rc != 0:
             raise RuntimeError("oracle step failed (%d) at step %d" % (rc, self.steps_done))
 
+    def stage(self, s, half):
+        """One half of RK stage s (or_stage): 0 the right-hand side and pre-limit
+        output, 1 the limiter (and the end of the step after the last stage)."""
+        rc = lib().or_stage(self.h, int(s), int(half))
+        if rc != 0:
+            raise RuntimeError("oracle stage failed (%d) at step %d" % (rc, self.steps_done))
+
+    def export(self, what, side, s):
+        """The owned boundary block [nv, p+1] at `side` (or_part_block)."""
+        blk = np.zeros((self.nv, self.wl.p + 1))
+        if lib().or_part_block(self.h, int(what), int(side), int(s), _dp(blk), 0) != 0:
+            raise ValueError("no cut at side %d" % side)
+        return blk
+
+    def import_(self, what, side, s, blk):
+        """Write a neighbour's block into the buffer element at `side`."""
+        blk = np.ascontiguousarray(blk, dtype=np.float64)
+        if lib().or_part_block(self.h, int(what), int(side), int(s), _dp(blk), 1) != 0:
+            raise ValueError("no cut at side %d" % side)
+
     @property
     def steps_done(self):
         return int(lib().or_steps_done(self.h))
 
     def flags(self):
-        last = np.zeros((rk_stages(self.cfg.integrator), self.wl.n_elem), dtype=np.uint8)
-        cnt = np.zeros(self.wl.n_elem, dtype=np.int32)
+        last = np.zeros((rk_stages(self.cfg.integrator), self.n_local), dtype=np.uint8)
+        cnt = np.zeros(self.n_local, dtype=np.int32)
         lib().or_get_flags(self.h, last.ctypes.data_as(C.POINTER(C.c_uint8)),
                            cnt.ctypes.data_as(C.POINTER(C.c_int32)))
         return last, cnt
 
     def temperature(self):
-        T = np.zeros((self.wl.n_elem, self.wl.p + 1))
+        T = np.zeros((self.n_local, self.wl.p + 1))
         lib().or_get_temperature(self.h, _dp(T))
         return T
 

@@ -519,6 +519,10 @@ struct or_ctx {
   double *ring_q;        /* history of q of the PE-boundary elements, same layout */
   int64_t *ring_level;
   int *keff;
+  /* subdomain (pe_end > 0): buffer elements at the cut sides, the whole domain's
+   * index of local element 0, and the whole domain's number of local PE face f:
+   * (f + face_base) mod npf_draw */
+  int cut_l, cut_r, elem0, face_base, npf_draw;
   int64_t n;
   uint8_t *flags_last;
   int32_t *flag_count;
@@ -582,6 +586,10 @@ or_ctx *or_create(const or_cfg *cfg, const or_mech *m) {
       (cfg->viscous && (!(cfg->mu_ref >= 0.0) || !(cfg->T_mu > 0.0) || !(cfg->prandtl > 0.0))) ||
       cfg->integrator < 0 || cfg->integrator > 2)
     return NULL;
+  const int part = cfg->pe_end > 0 && !(cfg->pe_begin == 0 && cfg->pe_end == cfg->n_pe);
+  if (cfg->pe_end > 0 && (cfg->pe_begin < 0 || cfg->pe_begin >= cfg->pe_end ||
+                          cfg->pe_end > cfg->n_pe || (part && (cfg->viscous || cfg->face0))))
+    return NULL;
   or_ctx *c = (or_ctx *)calloc(1, sizeof(or_ctx));
   c->cfg = *cfg;
   int ns = m->ns, nr = m->nr;
@@ -624,6 +632,23 @@ or_ctx *or_create(const or_cfg *cfg, const or_mech *m) {
   c->np1 = cfg->p + 1;
   c->ne = cfg->n_elem;
   c->dx = cfg->length / cfg->n_elem;
+  /* a subdomain: PEs [pb, pe) own elements [E0, E1) of the whole domain's N
+   * (PE k owns [floor(k N / P), floor((k+1) N / P))), plus a buffer element at
+   * each cut side; the local mesh ends in outflow boundaries beyond the buffers
+   * (their updates are discarded: the exchange overwrites them) */
+  int pb = 0, pe = cfg->n_pe;
+  if (part) {
+    int64_t N = cfg->n_elem, P = cfg->n_pe;
+    pb = cfg->pe_begin;
+    pe = cfg->pe_end;
+    int gper = (cfg->bc_left == 0);
+    c->cut_l = (pb > 0 || gper);
+    c->cut_r = (pe < P || gper);
+    c->elem0 = (int)((pb * N) / P) - c->cut_l;
+    c->ne = (int)((pe * N) / P - (pb * N) / P) + c->cut_l + c->cut_r;
+    if (c->cut_l) c->cfg.bc_left = 2;
+    if (c->cut_r) c->cfg.bc_right = 2;
+  }
   c->depth = cfg->max_delay + cfg->at_order;
   c->S = or_rk_stages(cfg->integrator);
   int q = c->np1;
@@ -646,6 +671,14 @@ or_ctx *or_create(const or_cfg *cfg, const or_mech *m) {
   int P = cfg->n_pe, ne = c->ne;
   int periodic = (cfg->bc_left == 0);
   c->npf = (P > 1) ? (periodic ? P : P - 1) : 0;
+  c->face_base = 0;
+  c->npf_draw = c->npf;
+  if (part) {
+    /* the cut faces and the faces between the subdomain's own PEs, in order:
+     * whole-domain faces pb - cut_l .. pe - 1 + cut_r - 1 (mod npf) */
+    c->npf = c->cut_l + (pe - pb - 1) + c->cut_r;
+    c->face_base = pb - c->cut_l;
+  }
   c->pf_left = (int *)malloc(sizeof(int) * (c->npf > 0 ? c->npf : 1));
   c->pf_right = (int *)malloc(sizeof(int) * (c->npf > 0 ? c->npf : 1));
   c->face_pf = (int *)malloc(sizeof(int) * (ne + 1));
@@ -654,9 +687,26 @@ or_ctx *or_create(const or_cfg *cfg, const or_mech *m) {
   for (int i = 0; i <= ne; ++i) c->face_pf[i] = -1;
   for (int e = 0; e < ne; ++e) c->elem_pf_right[e] = c->elem_pf_left[e] = -1;
   for (int k = 0; k < c->npf; ++k) {
-    int first_next = (int)(((int64_t)((k + 1) % P) * ne) / P);
-    int face = (k == P - 1) ? 0 : first_next;
-    int el = (face == 0) ? ne - 1 : face - 1;
+    int first_next, face, el;
+    if (part) {
+      /* local face k is whole-domain face g = pb - cut_l + k, which sits left of
+       * the first element of PE g + 1: the buffer element and the first owned
+       * element for the left cut, the last owned element and the buffer for the
+       * right cut */
+      int g = pb - c->cut_l + k;
+      if (c->cut_l && k == 0)
+        first_next = 1;
+      else if (c->cut_r && k == c->npf - 1)
+        first_next = ne - 1;
+      else
+        first_next = (int)(((int64_t)(g + 1) * cfg->n_elem) / P) - c->elem0;
+      face = first_next;
+      el = face - 1;
+    } else {
+      first_next = (int)(((int64_t)((k + 1) % P) * ne) / P);
+      face = (k == P - 1) ? 0 : first_next;
+      el = (face == 0) ? ne - 1 : face - 1;
+    }
     c->pf_left[k] = el;
     c->pf_right[k] = first_next;
     c->face_pf[face] = k;
@@ -1192,73 +1242,141 @@ static int limit_stage(or_ctx *c, int s, uint8_t *flags) {
  * Stage s of step n reads stage s of the delayed steps (one delay per PE face per
  * step, common to both sides and to all stages: CAA skips the exchange of every
  * intermediate stage of a delayed step, Sec. 4.1; synchronous until the history
- * holds the levels the AT stencil needs). */
-int or_step(or_ctx *c, int n_steps) {
-  int nv = c->nv, q = c->np1, ne = c->ne, o = c->cfg.at_order;
-  size_t sz = (size_t)nv * ne * q, blk = (size_t)nv * q;
+ * holds the levels the AT stencil needs). The step is split into its stages'
+ * halves (or_stage) so that a subdomain can exchange its boundary elements
+ * between them. */
+
+/* the whole domain's number of local PE face f (the SAA draws use it) */
+static int face_number(const or_ctx *c, int f) {
+  if (c->npf_draw <= 0) return f;
+  int g = (f + c->face_base) % c->npf_draw;
+  return g < 0 ? g + c->npf_draw : g;
+}
+
+static void step_begin(or_ctx *c) {
+  size_t sz = (size_t)c->nv * c->ne * c->np1;
+  int64_t n = c->n;
+  for (int f = 0; f < c->npf; ++f) {
+    int k = or_delay(&c->cfg, n, face_number(c, f));
+    c->keff[f] = (n >= (int64_t)k + c->cfg.at_order - 1) ? k : 0;
+  }
+  c->ring_level[(int)(n % c->depth)] = n;
+  memcpy(c->w0, c->w, sizeof(double) * sz);
+  memcpy(c->win, c->w, sizeof(double) * sz);
+}
+
+/* half 0 of stage s: history of the stage input, L(w_s), the pre-limit output
+ * and its history */
+static int stage_rhs(or_ctx *c, int s) {
+  int ne = c->ne;
+  size_t sz = (size_t)c->nv * ne * c->np1;
   double dt = c->cfg.dt;
+  int64_t n = c->n;
   double lsA[5], lsB[5], lsC[5];
   const int lserk = or_lserk_coeffs(c->cfg.integrator, lsA, lsB, lsC) > 0;
-  for (int it = 0; it < n_steps; ++it) {
-    int64_t n = c->n;
+  /* history of the stage input (for the AT flux) */
+  for (int f = 0; f < c->npf; ++f) {
+    elem_block(c, c->win, c->pf_left[f], ring_at(c, c->ring_in, n, s, f, 0));
+    elem_block(c, c->win, c->pf_right[f], ring_at(c, c->ring_in, n, s, f, 1));
+  }
+  if (c->cfg.viscous) {
+    /* the auxiliary variable of the stage input, and its history */
+    int aerr = aux_eval(c, c->win, s, 1);
+    if (aerr) return aerr;
     for (int f = 0; f < c->npf; ++f) {
-      int k = or_delay(&c->cfg, n, f);
-      c->keff[f] = (n >= (int64_t)k + o - 1) ? k : 0;
+      elem_block(c, c->qx, c->pf_left[f], ring_at(c, c->ring_q, n, s, f, 0));
+      elem_block(c, c->qx, c->pf_right[f], ring_at(c, c->ring_q, n, s, f, 1));
     }
-    int slot = (int)(n % c->depth);
-    c->ring_level[slot] = n;
-    memcpy(c->w0, c->w, sizeof(double) * sz);
-    memcpy(c->win, c->w, sizeof(double) * sz);
-    for (int s = 0; s < c->S; ++s) {
-      /* history of the stage input (for the AT flux) */
-      for (int f = 0; f < c->npf; ++f) {
-        double *dl = ring_at(c, c->ring_in, n, s, f, 0);
-        double *dr = ring_at(c, c->ring_in, n, s, f, 1);
-        elem_block(c, c->win, c->pf_left[f], dl);
-        elem_block(c, c->win, c->pf_right[f], dr);
-      }
-      if (c->cfg.viscous) {
-        /* the auxiliary variable of the stage input, and its history */
-        int aerr = aux_eval(c, c->win, s, 1);
-        if (aerr) return aerr;
-        for (int f = 0; f < c->npf; ++f) {
-          elem_block(c, c->qx, c->pf_left[f], ring_at(c, c->ring_q, n, s, f, 0));
-          elem_block(c, c->qx, c->pf_right[f], ring_at(c, c->ring_q, n, s, f, 1));
-        }
-      }
-      int err = rhs_eval(c, c->win, s, 1);
-      if (err) return err;
-      for (size_t t = 0; t < sz; ++t) {
-        double r = c->rhs[t];
-        if (lserk) {
-          c->dq[t] = lsA[s] * c->dq[t] + dt * r;
-          c->wpre[t] = c->win[t] + lsB[s] * c->dq[t];
-        } else if (s == 0)
-          c->wpre[t] = c->w0[t] + dt * r;
-        else if (s == 1)
-          c->wpre[t] = 0.75 * c->w0[t] + 0.25 * (c->win[t] + dt * r);
-        else
-          c->wpre[t] = (1.0 / 3.0) * c->w0[t] + (2.0 / 3.0) * (c->win[t] + dt * r);
-      }
-      /* history of the pre-limit stage output (for the AT-WENO stencil) */
-      for (int f = 0; f < c->npf; ++f) {
-        double *dl = ring_at(c, c->ring_pre, n, s, f, 0);
-        double *dr = ring_at(c, c->ring_pre, n, s, f, 1);
-        elem_block(c, c->wpre, c->pf_left[f], dl);
-        elem_block(c, c->wpre, c->pf_right[f], dr);
-      }
-      (void)blk;
-      if (c->cfg.limiter) {
-        err = limit_stage(c, s, c->flags_last + (size_t)s * ne);
+  }
+  int err = rhs_eval(c, c->win, s, 1);
+  if (err) return err;
+  for (size_t t = 0; t < sz; ++t) {
+    double r = c->rhs[t];
+    if (lserk) {
+      c->dq[t] = lsA[s] * c->dq[t] + dt * r;
+      c->wpre[t] = c->win[t] + lsB[s] * c->dq[t];
+    } else if (s == 0)
+      c->wpre[t] = c->w0[t] + dt * r;
+    else if (s == 1)
+      c->wpre[t] = 0.75 * c->w0[t] + 0.25 * (c->win[t] + dt * r);
+    else
+      c->wpre[t] = (1.0 / 3.0) * c->w0[t] + (2.0 / 3.0) * (c->win[t] + dt * r);
+  }
+  /* history of the pre-limit stage output (for the AT-WENO stencil) */
+  for (int f = 0; f < c->npf; ++f) {
+    elem_block(c, c->wpre, c->pf_left[f], ring_at(c, c->ring_pre, n, s, f, 0));
+    elem_block(c, c->wpre, c->pf_right[f], ring_at(c, c->ring_pre, n, s, f, 1));
+  }
+  return 0;
+}
+
+/* half 1 of stage s: the limited stage output becomes the next stage input */
+static int stage_limit(or_ctx *c, int s) {
+  int ne = c->ne;
+  size_t sz = (size_t)c->nv * ne * c->np1;
+  if (c->cfg.limiter) {
+    int err = limit_stage(c, s, c->flags_last + (size_t)s * ne);
+    if (err) return err;
+    for (int e = 0; e < ne; ++e) c->flag_count[e] += c->flags_last[(size_t)s * ne + e];
+  } else {
+    memcpy(c->win, c->wpre, sizeof(double) * sz);
+    memset(c->flags_last + (size_t)s * ne, 0, ne);
+  }
+  return 0;
+}
+
+static void step_end(or_ctx *c) {
+  memcpy(c->w, c->win, sizeof(double) * (size_t)c->nv * c->ne * c->np1);
+  c->n += 1;
+}
+
+int or_stage(or_ctx *c, int s, int half) {
+  if (s < 0 || s >= c->S || half < 0 || half > 1) return -2;
+  if (half == 0) {
+    if (s == 0) step_begin(c);
+    return stage_rhs(c, s);
+  }
+  int err = stage_limit(c, s);
+  if (err) return err;
+  if (s == c->S - 1) step_end(c);
+  return 0;
+}
+
+int or_step(or_ctx *c, int n_steps) {
+  for (int it = 0; it < n_steps; ++it)
+    for (int s = 0; s < c->S; ++s)
+      for (int half = 0; half < 2; ++half) {
+        int err = or_stage(c, s, half);
         if (err) return err;
-        for (int e = 0; e < ne; ++e) c->flag_count[e] += c->flags_last[(size_t)s * ne + e];
-      } else {
-        memcpy(c->win, c->wpre, sizeof(double) * sz);
-        memset(c->flags_last + (size_t)s * ne, 0, ne);
       }
-    }
-    memcpy(c->w, c->win, sizeof(double) * sz);
-    c->n = n + 1;
+  return 0;
+}
+
+int or_part_layout(const or_ctx *c, int *n_local, int *elem0, int *cut_left, int *cut_right) {
+  if (n_local) *n_local = c->ne;
+  if (elem0) *elem0 = c->elem0;
+  if (cut_left) *cut_left = c->cut_l;
+  if (cut_right) *cut_right = c->cut_r;
+  return 0;
+}
+
+int or_part_block(or_ctx *c, int what, int side, int s, double *blk, int import) {
+  if (what < 0 || what > 1 || side < 0 || side > 1 || s < 0 || s >= c->S) return -2;
+  if (!(side == 0 ? c->cut_l : c->cut_r)) return -2;
+  int nv = c->nv, q = c->np1;
+  /* the stage input of stage 0 is the state at the start of the step */
+  double *arr = (what == 1) ? c->wpre : (s == 0) ? c->w : c->win;
+  int e = import ? (side == 0 ? 0 : c->ne - 1) : (side == 0 ? 1 : c->ne - 2);
+  if (!import) {
+    elem_block(c, arr, e, blk);
+    return 0;
+  }
+  for (int v = 0; v < nv; ++v)
+    for (int j = 0; j < q; ++j) W_(arr, v, e, j) = blk[v * q + j];
+  if (what == 1) {
+    /* the buffer side of the cut face's pre-limit history */
+    int pf = (side == 0) ? 0 : c->npf - 1;
+    memcpy(ring_at(c, c->ring_pre, c->n, s, pf, side), blk, sizeof(double) * nv * q);
   }
   return 0;
 }

@@ -46,6 +46,11 @@ typedef struct {
   int face0;             /* number of the first PE face in the SAA draws (0; a window
                             of a larger run passes the larger run's number of its
                             first PE face, so both draw the same delays) */
+  int pe_begin, pe_end;  /* 0, 0: the whole domain. pe_end > 0: the subdomain of PEs
+                            [pe_begin, pe_end) of the domain the other fields
+                            describe (n_elem, n_pe, length, bcs of the whole), with a
+                            buffer element at each side that borders another
+                            subdomain (see or_part_layout) */
 } or_cfg;
 
 typedef struct or_ctx or_ctx;
@@ -96,6 +101,37 @@ int64_t or_steps_done(const or_ctx *c);
 /* troubled-cell flags: stages of the last step [stages][n_elem] and per-element count */
 int or_get_flags(const or_ctx *c, uint8_t *last, int32_t *count);
 int or_get_temperature(const or_ctx *c, double *T);
+
+/* Domain decomposition (Sec. 3.1: the subdomains of the PEs exchange the DoFs of
+ * their boundary elements with the buffer elements of their neighbours; Sec. 3.2:
+ * the buffers may hold delayed levels, the flux uses the common delayed level;
+ * Sec. 3.3: the limiter's neighbours are exchanged after every stage; Sec. 4:
+ * CAA and SAA decide the delays). A context made with pe_end > 0 holds the
+ * subdomain's elements plus one buffer element at each cut side (a side that
+ * borders another subdomain): local element 0 and/or n_local - 1. Its PE faces
+ * are the subdomain's own plus the cut faces, with the delays of the whole
+ * domain's face numbers, and dx is the whole domain's. The buffer elements are
+ * computed like the others, but their data is overwritten by the exchange
+ * before it is used, so the owned elements follow the whole-domain scheme
+ * exactly. Viscous subdomains are not supported (NULL from or_create).
+ *
+ * or_part_layout: n_local elements, global index of local element 0, and which
+ * sides are cut. */
+int or_part_layout(const or_ctx *c, int *n_local, int *elem0, int *cut_left, int *cut_right);
+/* One half of RK stage s of the current step: half 0 (at s = 0 it first starts
+ * the step: delays, history level, w0) the history writes of the stage input and
+ * the right-hand side, giving the pre-limit output; half 1 the limiter (or the
+ * copy without one), and at the last stage the end of the step. or_step(c, 1) is
+ * the same sequence without the exchange calls in between. */
+int or_stage(or_ctx *c, int s, int half);
+/* The exchange at one side (0 left, 1 right) for stage s, one block [nv][p+1]:
+ * what 0 = the stage input (at s = 0 the state at the start of the step), what 1
+ * = the pre-limit output of stage s. Export (import = 0) copies the owned
+ * boundary element of that side into blk; import (1) writes blk into that side's
+ * buffer element, and for what 1 also into the history of the cut face. The
+ * order per stage: import what 0 before half 0, import what 1 between half 0 and
+ * half 1. -2 for a side that is not cut. */
+int or_part_block(or_ctx *c, int what, int side, int s, double *blk, int import);
 /* one synchronous right-hand side L(w) (Eq. 5), no delays */
 int or_rhs_sync(const or_cfg *cfg, const or_mech *m, const double *w, double *rhs);
 /* the troubled-cell indicator and WENO limiter (Sec. 3.3) applied once to a state,

@@ -95,7 +95,8 @@ class Config_(C.Structure):
                 ("max_delay", C.c_int), ("delay_probs", C.POINTER(C.c_double)),
                 ("seed", C.c_uint64), ("tvb_M", C.c_double), ("precision", C.c_int),
                 ("integrator", C.c_int), ("viscous", C.c_int), ("mu_ref", C.c_double),
-                ("T_mu", C.c_double), ("mu_exp", C.c_double), ("prandtl", C.c_double)]
+                ("T_mu", C.c_double), ("mu_exp", C.c_double), ("prandtl", C.c_double),
+                ("pe_begin", C.c_int), ("pe_end", C.c_int)]
 
 
 _lib = None
@@ -106,7 +107,8 @@ EXPORTS = ["adg_workspace_bytes", "adg_create", "adg_destroy", "adg_set_primitiv
            "adg_write_state", "adg_read_state", "adg_enable_kernel_timing",
            "adg_kernel_times", "adg_step_noalloc", "adg_autotune", "adg_get_tuning",
            "adg_set_tuning", "adg_step_unsync", "adg_unsync_delays",
-           "adg_set_unsync_wait", "adg_set_unsync_imbalance", "adg_get_aux"]
+           "adg_set_unsync_wait", "adg_set_unsync_imbalance", "adg_get_aux",
+           "adg_part_layout", "adg_step_stage", "adg_part_block"]
 
 
 def lib(path: str | None = None):
@@ -151,6 +153,10 @@ def lib(path: str | None = None):
     L.adg_unsync_delays.argtypes = [vp, C.POINTER(C.c_uint64)]
     L.adg_set_unsync_wait.argtypes = [vp, C.c_longlong, C.c_int]
     L.adg_set_unsync_imbalance.argtypes = [vp, C.c_int, C.c_int]
+    ip = C.POINTER(C.c_int)
+    L.adg_part_layout.argtypes = [C.POINTER(Config_), ip, ip, ip, ip]
+    L.adg_step_stage.argtypes = [vp, C.c_int, C.c_int, vp]
+    L.adg_part_block.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp]
     L.adg_error_string.restype = C.c_char_p
     L.adg_error_string.argtypes = [C.c_int]
     _lib = L
@@ -204,8 +210,20 @@ def config_struct(wl, precision=FP64):
                 wl.seed & ((1 << 64) - 1), wl.tvb_M, _precision(precision),
                 int(getattr(wl, "integrator", 0)), int(getattr(wl, "viscous", 0)),
                 float(getattr(wl, "mu_ref", 0.0)), float(getattr(wl, "T_mu", 300.0)),
-                float(getattr(wl, "mu_exp", 0.7)), float(getattr(wl, "prandtl", 0.7)))
+                float(getattr(wl, "mu_exp", 0.7)), float(getattr(wl, "prandtl", 0.7)),
+                int(getattr(wl, "pe_begin", 0)), int(getattr(wl, "pe_end", 0)))
     return c, probs
+
+
+PART_INPUT, PART_PRELIMIT = 0, 1
+
+
+def part_layout(wl):
+    """adg_part_layout: (n_local, elem0, cut_left, cut_right) of a (sub)domain."""
+    cfg, probs = config_struct(wl)
+    out = [C.c_int(0) for _ in range(4)]
+    _check(lib().adg_part_layout(C.byref(cfg), *[C.byref(o) for o in out]), "adg_part_layout")
+    return tuple(int(o.value) for o in out)
 
 
 def rk_stages(wl):
@@ -217,6 +235,10 @@ def delay_table(wl, step0, n_steps):
     """Delays [n_steps][n_pe_faces] as the library draws them."""
     cfg, probs = config_struct(wl)
     npf = 0 if wl.n_pe <= 1 else (wl.n_pe if wl.bc_left == 0 else wl.n_pe - 1)
+    pb, pe = int(getattr(wl, "pe_begin", 0)), int(getattr(wl, "pe_end", 0))
+    if pe > 0 and not (pb == 0 and pe == wl.n_pe):
+        _, _, cut_l, cut_r = part_layout(wl)
+        npf = cut_l + (pe - pb - 1) + cut_r
     out = np.zeros((n_steps, max(npf, 0)), dtype=np.uint8)
     _check(lib().adg_delay_table(C.byref(cfg), int(step0), int(n_steps),
                                  out.ctypes.data_as(C.POINTER(C.c_uint8))), "adg_delay_table")
@@ -281,6 +303,8 @@ class ADG:
         _check(self.L.adg_create(C.byref(self._m.s), arr, len(cfgs), C.c_void_p(aligned),
                                  C.c_size_t(int(nbytes.value)), C.byref(h)), "adg_create")
         self.h = h
+        # elements of each instance's arrays (a subdomain's include its buffers)
+        self.n_local = [part_layout(w)[0] for w in self.workloads]
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:
@@ -300,7 +324,7 @@ class ADG:
 
     def shape(self, k=0):
         wl = self.workloads[self._k(k)]
-        return (self.nv, wl.n_elem, wl.p + 1)
+        return (self.nv, self.n_local[self._k(k)], wl.p + 1)
 
     def _stream(self, stream):
         if stream is None:
@@ -333,6 +357,20 @@ class ADG:
     def step(self, n=1, stream=None):
         _check(self.L.adg_step(self.h, int(n), self._stream(stream)), "adg_step")
 
+
+    def step_stage(self, stage, half, stream=None):
+        """adg_step_stage: half 0 (stage kernels) or 1 (limiters, and after the
+        last stage the step counters) of RK stage `stage` of every instance."""
+        _check(self.L.adg_step_stage(self.h, int(stage), int(half), self._stream(stream)),
+               "adg_step_stage")
+
+    def part_block(self, k, what, side, stage, blk_dev, import_, stream=None):
+        """adg_part_block: export (import_ False) the owned boundary block of
+        instance k at `side` into the device tensor blk_dev [nv, p+1], or import
+        blk_dev into that side's buffer element."""
+        _check(self.L.adg_part_block(self.h, self._k(k), int(what), int(side), int(stage),
+                                     C.c_void_p(blk_dev.data_ptr()), 1 if import_ else 0,
+                                     self._stream(stream)), "adg_part_block")
     def status(self):
         inst, el, st, sg = C.c_int(-1), C.c_int(-1), C.c_int64(-1), C.c_int(-1)
         rc = self.L.adg_status(self.h, C.byref(inst), C.byref(el), C.byref(st), C.byref(sg))
@@ -345,7 +383,7 @@ class ADG:
 
     def flags(self, k=0):
         wl = self.workloads[self._k(k)]
-        n = wl.n_elem
+        n = self.n_local[k]
         last = np.zeros((rk_stages(wl), n), dtype=np.uint8)
         cnt = np.zeros(n, dtype=np.int32)
         _check(self.L.adg_get_flags(self.h, k, last.ctypes.data_as(C.POINTER(C.c_uint8)),
@@ -354,7 +392,7 @@ class ADG:
 
     def temperature(self, k=0):
         wl = self.workloads[self._k(k)]
-        T = np.zeros((wl.n_elem, wl.p + 1))
+        T = np.zeros((self.n_local[k], wl.p + 1))
         _check(self.L.adg_get_temperature(self.h, k, _dp(T)), "adg_get_temperature")
         return T
 
@@ -430,7 +468,7 @@ class ADG:
     def pressure(self, k=0):
         """Pressure at every Gauss point of instance k, [n_elem, p+1]."""
         wl = self.workloads[self._k(k)]
-        P = np.zeros((wl.n_elem, wl.p + 1))
+        P = np.zeros((self.n_local[k], wl.p + 1))
         _check(self.L.adg_get_aux(self.h, k, 1, P.ctypes.data_as(C.c_void_p)), "adg_get_aux")
         return P
 

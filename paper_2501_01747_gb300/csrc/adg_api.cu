@@ -192,11 +192,29 @@ static void at_weights(int order, int k, double *c) {
 
 // ---------------------------------------------------------------------------
 
+// A subdomain instance (adg_config.pe_end > 0): the PEs [pb, pe) of a domain of N
+// elements and P PEs, PE q owning elements [floor(q N / P), floor((q+1) N / P)),
+// plus a buffer element at each cut side (a side that borders another
+// subdomain). Its PE faces, in order, are the whole domain's faces
+// pb - cut_l .. pe - 1 - (1 - cut_r) (mod the whole domain's face count).
+struct PartInfo {
+  bool part = false;
+  int pb = 0, pe = 0;
+  int n_local = 0;    // elements with the buffers
+  int elem0 = 0;      // whole-domain index of local element 0 (may be -1: periodic)
+  int cut_l = 0, cut_r = 0;
+  int npf = 0;        // PE faces of the instance
+  int face_base = 0;  // local face f is whole-domain face (f + face_base) mod npf_draw
+  int npf_draw = 0;   // PE faces of the whole domain
+  double dx = 0.0;    // the whole domain's element size
+};
+
 struct InstHost {
   Inst d;         // device view (a copy lives in the device instance table)
   int64_t n;      // steps done (host mirror of the device counter)
   double *prim;   // staging for projection / temperature
   int n_pe;       // PEs of the instance
+  PartInfo part;  // subdomain layout (part = false: the whole domain)
 };
 
 // Instances of one polynomial degree and precision share the stage and limiter
@@ -370,6 +388,56 @@ int n_pe_faces(const adg_config &c) {
   return c.bc_left == ADG_BC_PERIODIC ? c.n_pe : c.n_pe - 1;
 }
 
+// Layout of a config's (sub)domain; false for a bad PE range.
+bool part_info(const adg_config &c, PartInfo *out) {
+  PartInfo r;
+  const int64_t N = c.n_elem, P = c.n_pe;
+  const bool per = c.bc_left == ADG_BC_PERIODIC;
+  r.n_local = c.n_elem;
+  r.npf = r.npf_draw = n_pe_faces(c);
+  r.dx = c.length / c.n_elem;
+  if (c.pe_end == 0) {
+    if (c.pe_begin != 0) return false;
+  } else {
+    if (c.pe_begin < 0 || c.pe_begin >= c.pe_end || c.pe_end > c.n_pe) return false;
+    if (!(c.pe_begin == 0 && c.pe_end == c.n_pe)) {
+      r.part = true;
+      r.pb = c.pe_begin;
+      r.pe = c.pe_end;
+      r.cut_l = (c.pe_begin > 0 || per) ? 1 : 0;
+      r.cut_r = (c.pe_end < c.n_pe || per) ? 1 : 0;
+      const int64_t e0 = (int64_t)c.pe_begin * N / P, e1 = (int64_t)c.pe_end * N / P;
+      r.elem0 = (int)e0 - r.cut_l;
+      r.n_local = (int)(e1 - e0) + r.cut_l + r.cut_r;
+      r.npf = r.cut_l + (c.pe_end - c.pe_begin - 1) + r.cut_r;
+      r.face_base = c.pe_begin - r.cut_l;
+    }
+  }
+  *out = r;
+  return true;
+}
+
+// The instance each config describes: a subdomain becomes a bounded mesh of its
+// n_local elements whose cut sides end in outflow boundaries beyond the buffer
+// elements, with npf + 1 "PEs" so that n_pe_faces counts its PE faces (the PE
+// table itself comes from part_info, not from the even split).
+int localise(const adg_config *cfgs, int n, std::vector<adg_config> &lc,
+             std::vector<PartInfo> &pi) {
+  lc.assign(cfgs, cfgs + n);
+  pi.resize(n);
+  for (int k = 0; k < n; ++k) {
+    if (!part_info(cfgs[k], &pi[k])) return ADG_ERR_ARG;
+    if (!pi[k].part) continue;
+    if (cfgs[k].viscous) return ADG_ERR_ARG;
+    adg_config &c = lc[k];
+    c.n_elem = pi[k].n_local;
+    c.n_pe = pi[k].npf + 1;
+    if (pi[k].cut_l) c.bc_left = ADG_BC_OUTFLOW;
+    if (pi[k].cut_r) c.bc_right = ADG_BC_OUTFLOW;
+  }
+  return ADG_OK;
+}
+
 // Lay out every buffer; with dry = true only measures.
 size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
   int ns = ctx->ns, nr = ctx->nr, nv = ns + 2;
@@ -512,10 +580,16 @@ static int cuda_fail(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
 
-int adg_workspace_bytes(const adg_mechanism *mech, const adg_config *cfgs, int n, size_t *bytes) {
-  int rc = check_args(mech, cfgs, n);
+int adg_workspace_bytes(const adg_mechanism *mech, const adg_config *cfgs_in, int n,
+                        size_t *bytes) {
+  int rc = check_args(mech, cfgs_in, n);
   if (rc) return rc;
   if (!bytes) return ADG_ERR_ARG;
+  std::vector<adg_config> lc;
+  std::vector<PartInfo> pi;
+  rc = localise(cfgs_in, n, lc, pi);
+  if (rc) return rc;
+  const adg_config *cfgs = lc.data();
   adg_ctx tmp;
   tmp.n_inst = n;
   tmp.ns = mech->n_species;
@@ -540,20 +614,29 @@ int adg_delay_table(const adg_config *c, int64_t step0, int n_steps, uint8_t *ou
     acc += (c->delay_mode == ADG_SAA) ? c->delay_probs[k] : 0.0;
     cum[k] = acc;
   }
-  int npf = n_pe_faces(*c);
+  PartInfo pt;
+  if (!part_info(*c, &pt)) return ADG_ERR_ARG;
+  const int npf = pt.npf;
   for (int s = 0; s < n_steps; ++s)
     for (int f = 0; f < npf; ++f)
       out[(size_t)s * npf + f] =
-          (uint8_t)draw_delay(c->delay_mode, c->max_delay, c->seed, cum, step0 + s, f);
+          (uint8_t)draw_delay(c->delay_mode, c->max_delay, c->seed, cum, step0 + s,
+                              face_number(f, pt.face_base, pt.npf_draw));
   return ADG_OK;
 }
 
-int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *workspace,
+int adg_create(const adg_mechanism *mech, const adg_config *cfgs_in, int n, void *workspace,
                size_t ws_bytes, adg_ctx **out) {
   if (!out) return ADG_ERR_ARG;
   *out = nullptr;
-  int rc = check_args(mech, cfgs, n);
+  int rc = check_args(mech, cfgs_in, n);
   if (rc) return rc;
+  // subdomains become instances of their local elements (buffers included)
+  std::vector<adg_config> lc;
+  std::vector<PartInfo> pinfo;
+  rc = localise(cfgs_in, n, lc, pinfo);
+  if (rc) return rc;
+  const adg_config *cfgs = lc.data();
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return ADG_ERR_NOLIB;
   adg_ctx *ctx = new (std::nothrow) adg_ctx();
@@ -565,6 +648,7 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
   ctx->mech.nr = ctx->nr;
   ctx->mech.nterm = count_terms(mech);
   ctx->inst.resize(n);
+  for (int k = 0; k < n; ++k) ctx->inst[k].part = pinfo[k];
   ctx->last_stream = 0;
   ctx->unsync_polls = 1ll << 22;  // polls of ~0.5 us: a few seconds
   ctx->unsync_withheld = -1;
@@ -668,10 +752,12 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
     I.limiter = c.limiter;
     I.delay_mode = c.delay_mode;
     I.max_delay = c.max_delay;
-    I.dx = c.length / N;
+    I.dx = h.part.part ? h.part.dx : c.length / N;
     I.dt = c.dt;
     I.tvb = c.tvb_M * I.dx * I.dx;
     I.mixed = c.precision;
+    I.face_base = h.part.face_base;
+    I.npf_draw = h.part.part ? h.part.npf_draw : npf;
     I.ind_floor = indicator_guard(c.precision);
     I.ind_floor_p = indicator_guard_p(c.precision);
     I.seed = c.seed;
@@ -690,8 +776,18 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs, int n, void *w
     // PE partition (Sec. 4): PE q owns elements [q N / P, (q+1) N / P)
     std::vector<int> pl(N, -1), pr(N, -1), pe(2 * (npf > 0 ? npf : 1), -1);
     int P = c.n_pe;
+    const PartInfo &pt = h.part;
     for (int f = 0; f < npf; ++f) {
-      int right = (int)(((int64_t)((f + 1) % P) * N) / P);
+      int right;
+      if (!pt.part)
+        right = (int)(((int64_t)((f + 1) % P) * N) / P);
+      else if (pt.cut_l && f == 0)
+        right = 1;  // the left buffer | the first owned element
+      else if (pt.cut_r && f == npf - 1)
+        right = N - 1;  // the last owned element | the right buffer
+      else  // whole-domain face g sits left of the first element of PE g + 1
+        right = (int)(((int64_t)(pt.pb - pt.cut_l + f + 1) * cfgs_in[k].n_elem) /
+                      cfgs_in[k].n_pe) - pt.elem0;
       int left = (right == 0) ? N - 1 : right - 1;
       pr[left] = f;
       pl[right] = f;
@@ -866,25 +962,28 @@ static LimArgs aux_args(const adg_ctx *ctx, const Group &G, int s) {
 }
 
 // The stages of one group's step: per RK stage, the auxiliary kernel (viscous
-// groups), the stage kernel and the limiter.
-static int enqueue_group(adg_ctx *ctx, int gi, int s, cudaStream_t st) {
+// groups), the stage kernel and the limiter; half 0 only the first two, half 1
+// only the limiter, any other value all three.
+static int enqueue_group(adg_ctx *ctx, int gi, int s, cudaStream_t st, int half = -1) {
   const Group &G = ctx->groups[gi];
   if (s >= G.S) return ADG_OK;
-  StageArgs A;
-  A.insts = ctx->d_insts;
-  A.tiles = G.d_tiles;
-  A.s = s;
-  A.TE = G.TE;
-  A.NT = G.NT;
-  A.O = G.O;
-  A.visc = G.visc;
-  CK(timed_begin(ctx, 0, st));
-  // viscous groups: the LDG auxiliary variable of the stage input first
-  // (timed with the stage kernel)
-  if (G.visc) CK(launch_aux(aux_args(ctx, G, s), G.Q, G.n_blocks, st));
-  CK(launch_stage(ctx->mech, A, G.Q, G.prec, G.n_tiles, st));
-  CK(timed_end(ctx, st));
-  if (!G.any_limiter) return ADG_OK;
+  if (half != 1) {
+    StageArgs A;
+    A.insts = ctx->d_insts;
+    A.tiles = G.d_tiles;
+    A.s = s;
+    A.TE = G.TE;
+    A.NT = G.NT;
+    A.O = G.O;
+    A.visc = G.visc;
+    CK(timed_begin(ctx, 0, st));
+    // viscous groups: the LDG auxiliary variable of the stage input first
+    // (timed with the stage kernel)
+    if (G.visc) CK(launch_aux(aux_args(ctx, G, s), G.Q, G.n_blocks, st));
+    CK(launch_stage(ctx->mech, A, G.Q, G.prec, G.n_tiles, st));
+    CK(timed_end(ctx, st));
+  }
+  if (half == 0 || !G.any_limiter) return ADG_OK;
   LimArgs L;
   L.insts = ctx->d_insts;
   L.blocks = G.d_blocks;
@@ -1006,6 +1105,72 @@ int adg_step(adg_ctx *ctx, int n_steps, void *stream) {
   return ADG_OK;
 }
 
+int adg_part_layout(const adg_config *cfg, int *n_local, int *elem0, int *cut_left,
+                    int *cut_right) {
+  if (!cfg || cfg->n_elem < 1 || cfg->n_pe < 1 || cfg->n_pe > cfg->n_elem || !(cfg->length > 0.0))
+    return ADG_ERR_ARG;
+  PartInfo pt;
+  if (!part_info(*cfg, &pt)) return ADG_ERR_ARG;
+  if (n_local) *n_local = pt.n_local;
+  if (elem0) *elem0 = pt.elem0;
+  if (cut_left) *cut_left = pt.cut_l;
+  if (cut_right) *cut_right = pt.cut_r;
+  return ADG_OK;
+}
+
+int adg_step_stage(adg_ctx *ctx, int stage, int half, void *stream) {
+  if (!ctx || stage < 0 || half < 0 || half > 1) return ADG_ERR_ARG;
+  int max_s = 0;
+  for (int gi = 0; gi < ctx->n_groups; ++gi)
+    max_s = ctx->groups[gi].S > max_s ? ctx->groups[gi].S : max_s;
+  if (stage >= max_s) return ADG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  for (int gi = 0; gi < ctx->n_groups; ++gi) {
+    int rc = enqueue_group(ctx, gi, stage, st, half);
+    if (rc != ADG_OK) return rc;
+  }
+  if (half == 1 && stage == max_s - 1) {
+    CK(launch_advance(ctx->d_steps, ctx->n_inst, st));
+    for (InstHost &h : ctx->inst) h.n += 1;
+  }
+  return ADG_OK;
+}
+
+int adg_part_block(adg_ctx *ctx, int k, int what, int side, int stage, double *blk, int import,
+                   void *stream) {
+  if (!inst_ok(ctx, k) || !blk || side < 0 || side > 1 ||
+      (what != ADG_PART_INPUT && what != ADG_PART_PRELIMIT))
+    return ADG_ERR_ARG;
+  InstHost &h = ctx->inst[k];
+  const PartInfo &pt = h.part;
+  const Inst &I = h.d;
+  if (!pt.part || !(side == 0 ? pt.cut_l : pt.cut_r) || stage < 0 || stage >= I.n_stages)
+    return ADG_ERR_ARG;
+  const int N = I.n_elem, Q = I.p + 1, nv = I.nv;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  // [nv][N][Q]: one element's block is nv rows of Q doubles, N Q apart
+  double *arr = (what == ADG_PART_PRELIMIT) ? I.wpre : const_cast<double *>(stage_input(I, stage));
+  const size_t row = sizeof(double) * Q, pitch = sizeof(double) * (size_t)N * Q;
+  if (!import) {
+    const int e = side == 0 ? 1 : N - 2;  // the owned boundary element
+    CK(cudaMemcpy2DAsync(blk, row, arr + (size_t)e * Q, pitch, row, nv, cudaMemcpyDeviceToDevice,
+                         st));
+    return ADG_OK;
+  }
+  const int e = side == 0 ? 0 : N - 1;  // the buffer element
+  CK(cudaMemcpy2DAsync(arr + (size_t)e * Q, pitch, blk, row, row, nv, cudaMemcpyDeviceToDevice,
+                       st));
+  if (what == ADG_PART_PRELIMIT) {
+    // the buffer's side of the cut face in the pre-limit history of this step
+    const int pf = side == 0 ? 0 : I.npf - 1;
+    CK(cudaMemcpyAsync(I.ring_pre + ring_block(I, h.n, stage, pf, side), blk, row * nv,
+                       cudaMemcpyDeviceToDevice, st));
+  }
+  return ADG_OK;
+}
+
 // Drop the captured graphs (after the launch configuration changed).
 static void drop_graphs(adg_ctx *ctx) {
   if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
@@ -1117,6 +1282,7 @@ int adg_step_unsync(adg_ctx *ctx, int instance, int n_steps, void *stream) {
   InstHost &h = ctx->inst[instance];
   const Inst &I = h.d;
   if (I.viscous) return ADG_ERR_ARG;  // the unsynchronised mode runs the Euler terms only
+  if (h.part.part) return ADG_ERR_ARG;  // and whole domains only
   // the unsynchronised mode offers the FP64 and the ADG_MIXED stage arithmetic
   if (I.mixed == ADG_MIXED_F32CHEM) return ADG_ERR_ARG;
   const int Q = I.p + 1;

@@ -98,6 +98,8 @@ struct Inst {
   int instance;
   int mixed;                            // precision (ADG_FP64, ADG_MIXED, ADG_MIXED_F32CHEM):
                                         // nonzero for FP32 flux, DG operator, limiter
+  int face_base, npf_draw;              // PE face f is face (f + face_base) mod npf_draw of
+                                        // the whole domain (a subdomain; else 0 and npf)
   double ind_floor, ind_floor_p;        // rounding guards of the indicator (indicator_guard)
 };
 
@@ -175,13 +177,22 @@ __host__ __device__ inline int draw_delay(int mode, int max_delay, uint64_t seed
   return max_delay;
 }
 
+// The whole domain's number of PE face f of an instance (a subdomain numbers its
+// own faces from its first cut face; the delays are those of the whole domain).
+__host__ __device__ inline int face_number(int f, int face_base, int npf_draw) {
+  if (npf_draw <= 0) return f;
+  const int g = (f + face_base) % npf_draw;
+  return g < 0 ? g + npf_draw : g;
+}
+
 // Delay in force: synchronous until the ring holds levels n-k-(o-1).
 __device__ inline int effective_delay(const Inst &I, int64_t n, int f) {
-  int k = draw_delay(I.delay_mode, I.max_delay, I.seed, I.cum, n, f);
+  int k = draw_delay(I.delay_mode, I.max_delay, I.seed, I.cum, n,
+                     face_number(f, I.face_base, I.npf_draw));
   return (n >= (int64_t)k + I.at_order - 1) ? k : 0;
 }
 
-__device__ inline size_t ring_block(const Inst &I, int64_t level, int s, int pf, int side) {
+__host__ __device__ inline size_t ring_block(const Inst &I, int64_t level, int s, int pf, int side) {
   int slot = (int)(level % I.depth);
   return ((((size_t)slot * I.n_stages + s) * I.npf + pf) * 2 + side) * (size_t)I.nv * (I.p + 1);
 }

@@ -128,7 +128,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
       ((c.bc_left == ADG_BC_PERIODIC) != (c.bc_right == ADG_BC_PERIODIC)) ||
       (c.precision != ADG_FP64 && c.precision != ADG_MIXED && c.precision != ADG_MIXED_F32CHEM) ||
       c.integrator != ADG_RK_SSP3 ||
-      c.viscous != 0)
+      c.viscous != 0 || c.pe_begin != 0 || c.pe_end != 0)
     return ADG_ERR_ARG;
   if (!mech->W || !mech->cp || !mech->h_f || !mech->s0) return ADG_ERR_ARG;
   if (nr > 0 && (!mech->nu_f || !mech->nu_r || !mech->A || !mech->b || !mech->Ea))
@@ -215,6 +215,7 @@ extern "C" int adg_step_noalloc(const adg_mechanism *mech, const adg_config *cfg
   I.p = c.p;
   I.nv = nv;
   I.npf = npf;
+  I.npf_draw = npf;  // the whole domain: face f draws as face f (face_base 0)
   I.depth = depth;
   I.n_stages = 3;  // SSP-RK3 (memset left lserk = 0, wq = null)
   I.at_order = c.at_order;

@@ -246,6 +246,9 @@ class Workload:
     T_mu: float = 300.0
     mu_exp: float = 0.7
     prandtl: float = 0.7
+    # subdomain of PEs [pe_begin, pe_end) of the domain above (pe_end = 0: whole)
+    pe_begin: int = 0
+    pe_end: int = 0
 
     def mechanism(self) -> Mechanism:
         return make_mechanism(self.ns, self.nr, self.mech_seed, self.attempts)
