@@ -475,6 +475,9 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   // Euler kernels keep their register budget), run for viscous instances
   const bool visc = VISC && I.viscous;
   const int tid = threadIdx.x, nth = blockDim.x;
+  // (2i+1)/dx of the assembly in the variant's type, once per CTA (per thread it
+  // cost an FP64 division and Q conversions, as much FP64 work as an item's own)
+  __shared__ DG s_scale[MAXQ];
 
   // 0. mechanism, species fields, incidence, exp table and basis values into
   // shared memory
@@ -518,6 +521,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
           iexp_table_df(c_iexp.t32[k], &stab->tf[2 * k], &stab->tf[2 * k + 1]);
       }
       if (k < Q * Q) sPq[k] = B.P[k / Q][k % Q];
+      if (k < Q) s_scale[k] = conv_r<DG>((2.0 * k + 1.0) * (1.0 / I.dx));
     }
   }
   // 1. tile of modal coefficients with a one-element halo on each side and, for
@@ -755,7 +759,14 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         slnT[t] = log(T);
         sinvT[t] = cv / num;
       }
-      if (!(rho > 0.0) || !(T > 0.0) || !isfinite(T) || !isfinite(m))
+      // rho > 0, 0 < T < inf and m finite, on the bit patterns (integer pipe): a
+      // positive double (+inf included) is 1 .. 0x7FF0000000000000, a positive
+      // finite one 1 .. 0x7FEFFFFFFFFFFFFF; NaNs and negatives lie above
+      const unsigned long long brho = (unsigned long long)__double_as_longlong(rho);
+      const unsigned long long bT = (unsigned long long)__double_as_longlong(T);
+      const unsigned long long bm = (unsigned long long)__double_as_longlong(m);
+      if (!(brho - 1ull < 0x7FF0000000000000ull) || !(bT - 1ull < 0x7FEFFFFFFFFFFFFFull) ||
+          (bm & 0x7FF0000000000000ull) == 0x7FF0000000000000ull)
         report_error(I, ADG_ERR_NONPHYSICAL, e0 + t / Q, A.s, nstep);
       if constexpr (MIX) {
         // FP32 copies for phase 2c, in the storage of su (2 TQ floats)
@@ -975,10 +986,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   // 6. assembly of Eq. (5) (in the variant's arithmetic) and the SSP-RK3
   // combination (FP64); history ring writes
   const int slot_ok = (I.npf > 0);
-  const double inv_dx = 1.0 / I.dx;
-  DG scale[Q];  // (2i+1)/dx in the variant's type, once per thread
-#pragma unroll
-  for (int i = 0; i < Q; ++i) scale[i] = (DG)((2.0 * i + 1.0) * inv_dx);
+  const DG *scale = s_scale;
   Walk w6(tid, nth, te);
   for (int item = tid; item < nv * te; item += nth, w6.next()) {
     const int v = w6.o, e = w6.i, ge = e0 + e, le = e + 1;
@@ -1367,7 +1375,7 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
   DG *tlo = tile + (size_t)nv * vs;                // [nv][EPB + 2] (FP32) mean - (float) mean
   DG *alo = tlo + (size_t)LO * nv * ls;            // [2][EPB][nv] (FP32) the same of atn
   DG *wsp = alo + (size_t)LO * 2 * EPB * nv;       // WENO workspace
-  for (int k = threadIdx.x; k < SP_NFIELDS * ns; k += blockDim.x) spf[k] = (DG)M.sp[k];
+  for (int k = threadIdx.x; k < SP_NFIELDS * ns; k += blockDim.x) spf[k] = conv_r<DG>(M.sp[k]);
   if ((int)threadIdx.x < 2 * te) {
     const int side = threadIdx.x / te, le = threadIdx.x - side * te;
     s_nb[side][le] = neighbour_of<UNSYNC>(I, nstep, e0 + le, side, pd);
@@ -1490,9 +1498,9 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
                       nr = neighbour_of<UNSYNC>(I, nstep, e, 1, pd);
       for (int t = gl; t < NB; t += G) {
         const int v = t / Q, j = t - v * Q;
-        blk[t] = (DG)A_wpre[(size_t)v * VS + (size_t)e * Q + j];
-        blk[NB + t] = (DG)neighbour_mode<UNSYNC>(I, A_wpre, A.s, nstep, nl, v, j, Q);
-        blk[2 * NB + t] = (DG)neighbour_mode<UNSYNC>(I, A_wpre, A.s, nstep, nr, v, j, Q);
+        blk[t] = conv_r<DG>(A_wpre[(size_t)v * VS + (size_t)e * Q + j]);
+        blk[NB + t] = conv_r<DG>(neighbour_mode<UNSYNC>(I, A_wpre, A.s, nstep, nl, v, j, Q));
+        blk[2 * NB + t] = conv_r<DG>(neighbour_mode<UNSYNC>(I, A_wpre, A.s, nstep, nr, v, j, Q));
       }
     }
     __syncwarp();
