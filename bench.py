@@ -284,12 +284,14 @@ def measure(adg, torch, wls, mech, prims, prec, args, dev, pg, steps, autotune=T
     g.check()
     torch.cuda.synchronize(dev)
     if args.tuning:
-        # "TE,NT" for every group, or "TE,NT;TE,NT;..." per group in order
+        # "TE,NT[,EPB]" for every group, or "TE,NT[,EPB];..." per group in order
         parts = [x for x in args.tuning.split(";") if x]
         tuning = None
         for gi in range(len(g.tuning())):
-            te, nt = (int(x) for x in parts[min(gi, len(parts) - 1)].split(","))
-            tuning = g.set_tuning(gi, te, nt)
+            vals = [int(x) for x in parts[min(gi, len(parts) - 1)].split(",")]
+            tuning = g.set_tuning(gi, vals[0], vals[1])
+            if len(vals) > 2:
+                tuning = g.set_limiter_tuning(gi, vals[2])
     else:
         tuning = g.autotune(stream) if autotune and not args.no_autotune else g.tuning()
     torch.cuda.synchronize(dev)
@@ -554,9 +556,10 @@ def main(argv=None):
                     help="the headline variant; the others are timed beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--tuning", default="", help="TE,NT (every group) or TE,NT;TE,NT;... (one "
-                    "pair per group, in the order of config.tuning): set the stage launch "
-                    "configuration of the headline variant instead of autotuning it")
+    ap.add_argument("--tuning", default="", help="TE,NT[,EPB] (every group) or TE,NT[,EPB];... "
+                    "(one per group, in the order of config.tuning): set the stage launch "
+                    "configuration (and the limiter's elements per CTA) of the headline "
+                    "variant instead of autotuning it")
     ap.add_argument("--only", action="store_true",
                     help="time the headline variant of the headline workload only")
     ap.add_argument("--instances", type=int, default=0,

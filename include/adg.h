@@ -311,16 +311,22 @@ int adg_delay_table(const adg_config *cfg, int64_t step0, int n_steps, uint8_t *
 int adg_enable_kernel_timing(adg_ctx *ctx, int on);
 int adg_kernel_times(adg_ctx *ctx, double *ms, int64_t *launches);
 
-/* Autotuner of the launch configuration (elements per stage tile and threads
- * per stage CTA, per group of instances): times the
- * stage kernel for every candidate that fits in shared memory on `stream`,
- * keeps the fastest and drops the captured step graphs. The trajectory is not
- * changed (the trial launches only rewrite buffers the next step rewrites).
- * Synchronous. Instances are grouped by degree, precision and number of RK
- * stages. adg_get_tuning fills tuning[6 * g + {0,1,2,3,4,5}] with the degree,
- * precision, tile elements, threads per CTA, tile count and RK stages of group
- * g (at most ADG_MAX_GROUPS groups). */
+/* Autotuner of the launch configuration, per group of instances: times the
+ * stage kernel for every (elements per stage tile, threads per stage CTA)
+ * candidate that fits in shared memory, then the limiter for every number of
+ * elements per limiter CTA it is built for (8, 16, 32 in the mixed variants;
+ * 16, 32 in FP64), on `stream`; keeps the fastest and drops the captured step
+ * graphs. The trial launches leave the trajectory as it was: they only rewrite
+ * buffers the next step rewrites, and the flags and flag counts the trial
+ * limiter launches write are put back. The configuration chosen may change the
+ * rounding of the limiter's sums (its lanes per element follow the elements per
+ * CTA), not the stage kernel's. Synchronous. Instances are grouped by
+ * degree, precision and number of RK stages. adg_get_tuning fills
+ * tuning[ADG_TUNING_FIELDS * g + {0..6}] with the degree, precision, tile
+ * elements, threads per CTA, tile count, RK stages and limiter elements per CTA
+ * of group g (at most ADG_MAX_GROUPS groups). */
 #define ADG_MAX_GROUPS (6 * ADG_MAX_P)
+#define ADG_TUNING_FIELDS 7
 int adg_autotune(adg_ctx *ctx, void *stream);
 int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning);
 /* Set the launch configuration of group g directly (for instance one that an
@@ -328,6 +334,10 @@ int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning);
  * multiple of 32 in [32, 512]. Synchronous; drops the captured step graphs.
  * ADG_ERR_ARG for a bad group or a tile whose shared memory exceeds 200 KB. */
 int adg_set_tuning(adg_ctx *ctx, int group, int elements_per_tile, int threads_per_cta);
+/* Set the limiter's elements per CTA of group g (8, 16 or 32 in the mixed
+ * variants, 16 or 32 in FP64; ADG_ERR_ARG otherwise). Synchronous; drops the
+ * captured step graphs. */
+int adg_set_limiter_tuning(adg_ctx *ctx, int group, int elements_per_cta);
 
 /* Number of kernel launches one adg_step(ctx, 1, ...) enqueues. */
 int adg_launches_per_step(const adg_ctx *ctx);

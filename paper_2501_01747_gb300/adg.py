@@ -30,6 +30,7 @@ ERRORS = {-1: "ADG_ERR_ARG", -2: "ADG_ERR_CUDA", -3: "ADG_ERR_NOMEM",
           -7: "ADG_ERR_TIMEOUT"}
 MAX_DELAY = 7  # ADG_MAX_DELAY
 MAX_GROUPS = 24  # ADG_MAX_GROUPS
+TUNING_FIELDS = 7  # ADG_TUNING_FIELDS
 
 
 class AdgError(RuntimeError):
@@ -108,7 +109,7 @@ EXPORTS = ["adg_workspace_bytes", "adg_create", "adg_destroy", "adg_set_primitiv
            "adg_kernel_times", "adg_step_noalloc", "adg_autotune", "adg_get_tuning",
            "adg_set_tuning", "adg_step_unsync", "adg_unsync_delays",
            "adg_set_unsync_wait", "adg_set_unsync_imbalance", "adg_get_aux",
-           "adg_part_layout", "adg_step_stage", "adg_part_block"]
+           "adg_part_layout", "adg_step_stage", "adg_part_block", "adg_set_limiter_tuning"]
 
 
 def lib(path: str | None = None):
@@ -149,6 +150,7 @@ def lib(path: str | None = None):
     L.adg_autotune.argtypes = [vp, vp]
     L.adg_get_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.adg_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+    L.adg_set_limiter_tuning.argtypes = [vp, C.c_int, C.c_int]
     L.adg_step_unsync.argtypes = [vp, C.c_int, C.c_int, vp]
     L.adg_unsync_delays.argtypes = [vp, C.POINTER(C.c_uint64)]
     L.adg_set_unsync_wait.argtypes = [vp, C.c_longlong, C.c_int]
@@ -427,11 +429,13 @@ class ADG:
 
     def tuning(self):
         n = C.c_int(0)
-        t = (C.c_int * (6 * MAX_GROUPS))()
+        F = TUNING_FIELDS
+        t = (C.c_int * (F * MAX_GROUPS))()
         _check(self.L.adg_get_tuning(self.h, C.byref(n), t), "adg_get_tuning")
-        return [{"p": t[6 * g], "precision": PRECISION_NAMES[t[6 * g + 1]],
-                 "elements_per_tile": t[6 * g + 2], "threads_per_cta": t[6 * g + 3],
-                 "tiles": t[6 * g + 4], "stages": t[6 * g + 5]} for g in range(n.value)]
+        return [{"p": t[F * g], "precision": PRECISION_NAMES[t[F * g + 1]],
+                 "elements_per_tile": t[F * g + 2], "threads_per_cta": t[F * g + 3],
+                 "tiles": t[F * g + 4], "stages": t[F * g + 5],
+                 "limiter_elements_per_cta": t[F * g + 6]} for g in range(n.value)]
 
     def set_tuning(self, group, elements_per_tile, threads_per_cta):
         """Set the stage launch configuration of a group (e.g. a stored autotune result)."""
@@ -439,6 +443,12 @@ class ADG:
                                      int(threads_per_cta)), "adg_set_tuning")
         return self.tuning()
 
+
+    def set_limiter_tuning(self, group, elements_per_cta):
+        """Set a group's limiter elements per CTA (adg_set_limiter_tuning)."""
+        _check(self.L.adg_set_limiter_tuning(self.h, int(group), int(elements_per_cta)),
+               "adg_set_limiter_tuning")
+        return self.tuning()
     def step_unsync(self, n=1, k=0, stream=None):
         """n steps of instance k in the truly unsynchronised mode (one CTA per PE,
         each PE using the newest level its neighbours have published)."""

@@ -492,20 +492,22 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
     if (target < G.TE) G.TE = target < 4 ? 4 : (int)target;
     G.NT = stage_threads(G.TE, Q, nr);
     G.EPB = limiter_elems_per_block(total, G.mixed);
-    const int epb = G.EPB;
-    int64_t max_tiles = 0;
+    const int epb = G.EPB, epb_min = G.mixed ? 8 : 16;
+    int64_t max_tiles = 0, max_blocks = 0;
     for (int k = 0; k < ctx->n_inst; ++k)
       if (member(k)) {
         tiles += (cfgs[k].n_elem + G.TE - 1) / G.TE;
         max_tiles += (cfgs[k].n_elem + kMinTile - 1) / kMinTile;
         blocks += (cfgs[k].n_elem + epb - 1) / epb;
+        max_blocks += (cfgs[k].n_elem + epb_min - 1) / epb_min;
       }
     G.n_tiles = (int)tiles;
     G.n_blocks = (int)blocks;
     G.any_limiter = lim;
-    // room for the tile table of the smallest tile the autotuner may pick
+    // room for the tile and block tables of the smallest tile and limiter block
+    // the autotuner may pick
     G.d_tiles = (int2 *)cv.take(sizeof(int2) * max_tiles);
-    G.d_blocks = (int2 *)cv.take(sizeof(int2) * blocks);
+    G.d_blocks = (int2 *)cv.take(sizeof(int2) * max_blocks);
   }
   for (int k = 0; k < ctx->n_inst; ++k) {
     const adg_config &c = cfgs[k];
@@ -551,6 +553,24 @@ static cudaError_t upload_tiles(adg_ctx *ctx, Group &G) {
   }
   G.n_tiles = (int)tl.size();
   return cudaMemcpy(G.d_tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
+}
+
+// Limiter block table of a group for its current elements per CTA.
+static cudaError_t upload_blocks(adg_ctx *ctx, Group &G) {
+  std::vector<int2> bl;
+  for (int k = 0; k < ctx->n_inst; ++k) {
+    const Inst &I = ctx->inst[k].d;
+    if (I.p + 1 != G.Q || I.mixed != G.prec || I.n_stages != G.S) continue;
+    for (int e = 0; e < I.n_elem; e += G.EPB) bl.push_back(make_int2(k, e));
+  }
+  G.n_blocks = (int)bl.size();
+  return cudaMemcpy(G.d_blocks, bl.data(), sizeof(int2) * bl.size(), cudaMemcpyHostToDevice);
+}
+
+// Elements per limiter CTA that the limiter is built for: 8, 16 and 32 in the
+// mixed variants, 16 and 32 in FP64.
+static bool limiter_block_ok(const Group &G, int epb) {
+  return epb == 16 || epb == 32 || (G.mixed && epb == 8);
 }
 
 extern "C" {
@@ -813,16 +833,7 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs_in, int n, void
       rc2 = ADG_ERR_CUDA;
     for (int gi = 0; gi < ctx->n_groups && rc2 == ADG_OK; ++gi) {
       Group &G = ctx->groups[gi];
-      const int epb = G.EPB;
-      std::vector<int2> bl;
-      for (int k = 0; k < n; ++k) {
-        if (cfgs[k].p + 1 != G.Q || cfgs[k].precision != G.prec ||
-            rk_stages(cfgs[k].integrator) != G.S)
-          continue;
-        for (int e = 0; e < cfgs[k].n_elem; e += epb) bl.push_back(make_int2(k, e));
-      }
-      if (upload_tiles(ctx, G) != cudaSuccess ||
-          cudaMemcpy(G.d_blocks, bl.data(), sizeof(int2) * bl.size(), cudaMemcpyHostToDevice))
+      if (upload_tiles(ctx, G) != cudaSuccess || upload_blocks(ctx, G) != cudaSuccess)
         rc2 = ADG_ERR_CUDA;
     }
     if (prepare_kernels(nv, ns, nr) != cudaSuccess) rc2 = ADG_ERR_CUDA;
@@ -1182,6 +1193,61 @@ static void drop_graphs(adg_ctx *ctx) {
   ctx->graph_ok = false;
 }
 
+// The limiter's elements per CTA for one group: times a limiter launch of stage
+// 0 (on the pre-limit output the stage kernel's trial launches left) for every
+// block size the limiter is built for, and keeps the fastest. The trial
+// launches also write the group's flags and add to its flag counts, which are
+// saved before and put back after.
+static int tune_limiter(adg_ctx *ctx, Group &G, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  std::vector<int> members;
+  std::vector<std::vector<int32_t>> counts;
+  std::vector<std::vector<uint8_t>> flags;
+  CK(cudaStreamSynchronize(st));
+  for (int k = 0; k < ctx->n_inst; ++k) {
+    const Inst &I = ctx->inst[k].d;
+    if (I.p + 1 != G.Q || I.mixed != G.prec || I.n_stages != G.S) continue;
+    members.push_back(k);
+    counts.emplace_back(I.n_elem);
+    flags.emplace_back((size_t)I.n_stages * I.n_elem);
+    CK(cudaMemcpy(counts.back().data(), I.count, sizeof(int32_t) * I.n_elem,
+                  cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(flags.back().data(), I.flags, flags.back().size(), cudaMemcpyDeviceToHost));
+  }
+  const int cand[3] = {8, 16, 32};
+  int best_epb = G.EPB;
+  float best = 1e30f;
+  for (int epb : cand) {
+    if (!limiter_block_ok(G, epb)) continue;
+    G.EPB = epb;
+    CK(upload_blocks(ctx, G));
+    LimArgs L;
+    L.insts = ctx->d_insts;
+    L.blocks = G.d_blocks;
+    L.s = 0;
+    L.EPB = epb;
+    CK(launch_limiter(ctx->mech, L, G.Q, G.mixed, ctx->ns + 2, G.n_blocks, st));
+    CK(cudaEventRecord(e0, st));
+    for (int w = 0; w < 2; ++w)
+      CK(launch_limiter(ctx->mech, L, G.Q, G.mixed, ctx->ns + 2, G.n_blocks, st));
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_epb = epb;
+    }
+  }
+  G.EPB = best_epb;
+  CK(upload_blocks(ctx, G));
+  for (size_t m = 0; m < members.size(); ++m) {
+    const Inst &I = ctx->inst[members[m]].d;
+    CK(cudaMemcpy(I.count, counts[m].data(), sizeof(int32_t) * I.n_elem, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(I.flags, flags[m].data(), flags[m].size(), cudaMemcpyHostToDevice));
+  }
+  return ADG_OK;
+}
+
 int adg_autotune(adg_ctx *ctx, void *stream) {
   if (!ctx) return ADG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -1239,6 +1305,7 @@ int adg_autotune(adg_ctx *ctx, void *stream) {
     G.TE = bestTE;
     G.NT = bestNT;
     if (upload_tiles(ctx, G) != cudaSuccess) rc = ADG_ERR_CUDA;
+    if (rc == ADG_OK && G.any_limiter) rc = tune_limiter(ctx, G, st, e0, e1);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1261,17 +1328,30 @@ int adg_set_tuning(adg_ctx *ctx, int group, int elements_per_tile, int threads_p
   return ADG_OK;
 }
 
+int adg_set_limiter_tuning(adg_ctx *ctx, int group, int elements_per_cta) {
+  if (!ctx || group < 0 || group >= ctx->n_groups) return ADG_ERR_ARG;
+  Group &G = ctx->groups[group];
+  if (!limiter_block_ok(G, elements_per_cta)) return ADG_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->last_stream));
+  G.EPB = elements_per_cta;
+  CK(upload_blocks(ctx, G));
+  drop_graphs(ctx);
+  return ADG_OK;
+}
+
 int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning) {
   if (!ctx || !n_groups || !tuning) return ADG_ERR_ARG;
   *n_groups = ctx->n_groups;
   for (int gi = 0; gi < ctx->n_groups; ++gi) {
     const Group &G = ctx->groups[gi];
-    tuning[6 * gi + 0] = G.Q - 1;
-    tuning[6 * gi + 1] = G.prec;
-    tuning[6 * gi + 2] = G.TE;
-    tuning[6 * gi + 3] = G.NT;
-    tuning[6 * gi + 4] = G.n_tiles;
-    tuning[6 * gi + 5] = G.S;
+    int *t = tuning + ADG_TUNING_FIELDS * gi;
+    t[0] = G.Q - 1;
+    t[1] = G.prec;
+    t[2] = G.TE;
+    t[3] = G.NT;
+    t[4] = G.n_tiles;
+    t[5] = G.S;
+    t[6] = G.EPB;
   }
   return ADG_OK;
 }

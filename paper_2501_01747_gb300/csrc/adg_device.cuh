@@ -4,12 +4,13 @@
 //
 // Per RK stage two kernels run. The stage kernel comes in three precision
 // variants PREC (include/adg.h): ADG_FP64; ADG_MIXED, FP32 for the flux and the
-// DG operator, FP64 for the Gauss-point temperature, the chemistry (Arrhenius
-// and equilibrium exponentials, mass action, production rates), the AT level
-// sums and the accumulation of the conserved state; ADG_MIXED_F32CHEM, as
-// ADG_MIXED but with the chemistry's exponents as float pairs and its
-// exponentials, products and sums in FP32. The limiter has an FP64 and an FP32
-// variant (MIX), the latter for both mixed variants.
+// DG operator, FP64 for the Gauss-point temperature, the Arrhenius and
+// equilibrium exponents and exponentials, the AT level sums and the
+// accumulation of the conserved state, and float pairs (about 48 bits) for the
+// mass action and production rates from the FP64 rate constants;
+// ADG_MIXED_F32CHEM, as ADG_MIXED but with the chemistry's exponents as float
+// pairs and its exponentials, products and sums in FP32. The limiter has an FP64
+// and an FP32 variant (MIX), the latter for both mixed variants.
 //   stage_kernel<Q,PREC>: one CTA per tile of TE consecutive elements of one
 //                      instance (stage_body).
 //   limiter_kernel<Q,G,MIX,EPB>: the troubled-cell indicator and, on troubled

@@ -1,8 +1,9 @@
 """The mixed-precision CUDA paths against the FP64 oracle: ADG_MIXED (FP32 flux,
-DG operator and limiter; FP64 state, temperature, chemistry -- Arrhenius and
-equilibrium exponentials, mass action, production rates --, AT sums and RK
-accumulation) and ADG_MIXED_F32CHEM (the same with the chemistry's exponents as
-float pairs and its exponentials, products and sums in FP32).
+DG operator and limiter; FP64 state, temperature, Arrhenius and equilibrium
+exponents and exponentials, AT sums and RK accumulation; mass action and
+production rates in float pairs of about 48 bits from the FP64 rate constants)
+and ADG_MIXED_F32CHEM (the same with the chemistry's exponents as float pairs
+and its exponentials, products and sums in FP32).
 
 Bar, in the relative L-infinity norm of the FP64 bar: the temperature within
 1e-4 of the oracle's at every Gauss point (relative to the local value); the mass

@@ -312,14 +312,20 @@ def test_autotune_keeps_the_trajectory():
     g.step(8)
     tun = g.autotune()
     assert tun and tun[0]["elements_per_tile"] >= 2 and tun[0]["threads_per_cta"] >= 64
+    assert tun[0]["limiter_elements_per_cta"] in (16, 32)  # the FP64 limiter's sizes
     g.step(8)
     tun = g.set_tuning(0, 3, 96)
     assert tun[0]["elements_per_tile"] == 3 and tun[0]["threads_per_cta"] == 96
     assert tun[0]["tiles"] == (wl.n_elem + 2) // 3
+    other = 48 - tun[0]["limiter_elements_per_cta"]  # the other FP64 limiter size
+    assert g.set_limiter_tuning(0, other)[0]["limiter_elements_per_cta"] == other
     g.step(8)
     g.check()
     with pytest.raises(adg.AdgError):
         g.set_tuning(0, 3, 100)
+    for bad in (8, 12, 64):
+        with pytest.raises(adg.AdgError):
+            g.set_limiter_tuning(0, bad)
     o = O.Oracle(wl, mech)
     o.set_primitive(prim)
     o.step(24)
