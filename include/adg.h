@@ -193,6 +193,15 @@ int adg_write_state(adg_ctx *ctx, int instance, const double *w_host, void *stre
  * synchronisation; the data is valid once the stream has passed the copy). */
 int adg_read_state(adg_ctx *ctx, int instance, double *w_host, void *stream);
 
+/* adg_write_state and adg_read_state for every instance with one call: w_host
+ * holds the states of instances 0, 1, ... in order, each [nv][n_elem][p+1]
+ * (adg_states_doubles gives the total length); one copy per instance is
+ * enqueued on `stream`. The same rules on pinned memory and validity apply.
+ * Errors: ADG_ERR_ARG (NULL), ADG_ERR_CUDA. */
+int adg_write_states(adg_ctx *ctx, const double *w_host, void *stream);
+int adg_read_states(adg_ctx *ctx, double *w_host, void *stream);
+int64_t adg_states_doubles(const adg_ctx *ctx);
+
 /* Copy the current modal state out: the DOFs w_j^e of Sec. 3.1 (Eq. 4) after the
  * steps done, in the layout of the conventions above. Synchronises the
  * context's last stream first, so the result is the state after every step

@@ -109,7 +109,8 @@ EXPORTS = ["adg_workspace_bytes", "adg_create", "adg_destroy", "adg_set_primitiv
            "adg_kernel_times", "adg_step_noalloc", "adg_autotune", "adg_get_tuning",
            "adg_set_tuning", "adg_step_unsync", "adg_unsync_delays",
            "adg_set_unsync_wait", "adg_set_unsync_imbalance", "adg_get_aux",
-           "adg_part_layout", "adg_step_stage", "adg_part_block", "adg_set_limiter_tuning"]
+           "adg_part_layout", "adg_step_stage", "adg_part_block", "adg_set_limiter_tuning",
+           "adg_write_states", "adg_read_states", "adg_states_doubles"]
 
 
 def lib(path: str | None = None):
@@ -143,6 +144,10 @@ def lib(path: str | None = None):
     L.adg_launches_per_step.argtypes = [vp]
     L.adg_write_state.argtypes = [vp, C.c_int, d, vp]
     L.adg_read_state.argtypes = [vp, C.c_int, d, vp]
+    L.adg_write_states.argtypes = [vp, d, vp]
+    L.adg_read_states.argtypes = [vp, d, vp]
+    L.adg_states_doubles.argtypes = [vp]
+    L.adg_states_doubles.restype = C.c_int64
     L.adg_enable_kernel_timing.argtypes = [vp, C.c_int]
     L.adg_kernel_times.argtypes = [vp, d, C.POINTER(C.c_int64)]
     L.adg_step_noalloc.argtypes = [C.POINTER(Mechanism_), C.POINTER(Config_), vp, vp, C.c_int,
@@ -410,6 +415,21 @@ class ADG:
         """Async D2H read of the state (valid after the stream passes it)."""
         _check(self.L.adg_read_state(self.h, k, _dp(w_host), self._stream(stream)),
                "adg_read_state")
+
+    def states_doubles(self):
+        """Length of the buffer that write_states / read_states use."""
+        return int(self.L.adg_states_doubles(self.h))
+
+    def write_states(self, w_host, stream=None):
+        """adg_write_states: every instance's state from one host buffer (the
+        states in instance order), asynchronously on the stream."""
+        _check(self.L.adg_write_states(self.h, _dp(w_host), self._stream(stream)),
+               "adg_write_states")
+
+    def read_states(self, w_host, stream=None):
+        """adg_read_states: every instance's state into one host buffer."""
+        _check(self.L.adg_read_states(self.h, _dp(w_host), self._stream(stream)),
+               "adg_read_states")
 
     def enable_kernel_timing(self, on=True):
         _check(self.L.adg_enable_kernel_timing(self.h, 1 if on else 0), "timing")

@@ -1460,6 +1460,37 @@ int adg_write_state(adg_ctx *ctx, int k, const double *w, void *stream) {
   return ADG_OK;
 }
 
+int64_t adg_states_doubles(const adg_ctx *ctx) {
+  if (!ctx) return 0;
+  int64_t n = 0;
+  for (const InstHost &h : ctx->inst) n += (int64_t)h.d.nv * h.d.n_elem * (h.d.p + 1);
+  return n;
+}
+
+int adg_write_states(adg_ctx *ctx, const double *w, void *stream) {
+  if (!ctx || !w) return ADG_ERR_ARG;
+  for (const InstHost &h : ctx->inst) {
+    const size_t n = (size_t)h.d.nv * h.d.n_elem * (h.d.p + 1);
+    CK(cudaMemcpyAsync(h.d.wn, w, sizeof(double) * n, cudaMemcpyHostToDevice,
+                       (cudaStream_t)stream));
+    w += n;
+  }
+  ctx->last_stream = (cudaStream_t)stream;
+  return ADG_OK;
+}
+
+int adg_read_states(adg_ctx *ctx, double *w, void *stream) {
+  if (!ctx || !w) return ADG_ERR_ARG;
+  for (const InstHost &h : ctx->inst) {
+    const size_t n = (size_t)h.d.nv * h.d.n_elem * (h.d.p + 1);
+    CK(cudaMemcpyAsync(w, h.d.wn, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                       (cudaStream_t)stream));
+    w += n;
+  }
+  ctx->last_stream = (cudaStream_t)stream;
+  return ADG_OK;
+}
+
 int adg_read_state(adg_ctx *ctx, int k, double *w, void *stream) {
   if (!inst_ok(ctx, k) || !w) return ADG_ERR_ARG;
   InstHost &h = ctx->inst[k];

@@ -253,6 +253,20 @@ __device__ __forceinline__ double trace_of(const double *w, bool right) {
   return a;
 }
 
+// The same trace in float from the modes rounded to float on the integer pipe
+// (ADG_MIXED: the face flux is FP32, so its traces need no FP64 sum). A trace
+// that enters the history ring in that variant is this value, exactly.
+template <int Q>
+__device__ __forceinline__ float trace_f(const double *w, bool right) {
+  float a = 0.0f;
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    const float x = d2f_int(w[j]);
+    a += (right && (j & 1)) ? -x : x;
+  }
+  return a;
+}
+
 // A value of the history ring. Written by another CTA of the same launch in the
 // unsynchronised mode, so read from L2 (the point of coherence), not from a
 // possibly stale L1 line of an earlier level in the same slot.
@@ -591,10 +605,14 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       const int r = item - nv * teq, side = r & 1, vf = r >> 1;
       const int v = vf / (te + 1), f = vf - v * (te + 1);
       const double *wi = sw + ((size_t)v * (TE + 2) + f + side) * Q;
-      double a = 0.0;
+      if constexpr (DFCHEM) {
+        str[(size_t)f * 2 * nv + side * nv + v] = trace_f<Q>(wi, side);
+      } else {
+        double a = 0.0;
 #pragma unroll
-      for (int j = 0; j < Q; ++j) a += (side && (j & 1)) ? -wi[j] : wi[j];
-      str[(size_t)f * 2 * nv + side * nv + v] = conv_r<DG>(a);
+        for (int j = 0; j < Q; ++j) a += (side && (j & 1)) ? -wi[j] : wi[j];
+        str[(size_t)f * 2 * nv + side * nv + v] = conv_r<DG>(a);
+      }
       continue;
     }
     const int v = w2a.o, t = w2a.i;
@@ -1047,14 +1065,16 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
         size_t b = ring_block(I, nstep, A.s, pr, 0) + (size_t)v * Q;
         for (int i = 0; i < Q; ++i) I.ring_pre[b + i] = out[i];
         if constexpr (!UNSYNC)
-          I.ring_in[ring_trace(I, nstep, A.s, pr, 0) + v] = trace_of<Q>(wi, false);
+          I.ring_in[ring_trace(I, nstep, A.s, pr, 0) + v] =
+              (DFCHEM && !visc) ? f2d_exact(trace_f<Q>(wi, false)) : trace_of<Q>(wi, false);
       }
       if (pl >= 0) {
         // right element of the PE face: its trace at xi = -1
         size_t b = ring_block(I, nstep, A.s, pl, 1) + (size_t)v * Q;
         for (int i = 0; i < Q; ++i) I.ring_pre[b + i] = out[i];
         if constexpr (!UNSYNC)
-          I.ring_in[ring_trace(I, nstep, A.s, pl, 1) + v] = trace_of<Q>(wi, true);
+          I.ring_in[ring_trace(I, nstep, A.s, pl, 1) + v] =
+              (DFCHEM && !visc) ? f2d_exact(trace_f<Q>(wi, true)) : trace_of<Q>(wi, true);
       }
     }
   }

@@ -138,10 +138,12 @@ __global__ void __launch_bounds__(LIM_THREADS) unsync_kernel(Mech M, UnsyncArgs 
         const int side = t / nv, v = t - side * nv;
         if (side == 0 && pfl >= 0) {
           const double *w = win + ((size_t)v * N + first) * Q;
-          I.ring_in[ring_trace(I, n, s, pfl, 1) + v] = trace_of<Q>(w, true);
+          I.ring_in[ring_trace(I, n, s, pfl, 1) + v] =
+              MIX ? f2d_exact(trace_f<Q>(w, true)) : trace_of<Q>(w, true);
         } else if (side == 1 && pfr >= 0) {
           const double *w = win + ((size_t)v * N + last) * Q;
-          I.ring_in[ring_trace(I, n, s, pfr, 0) + v] = trace_of<Q>(w, false);
+          I.ring_in[ring_trace(I, n, s, pfr, 0) + v] =
+              MIX ? f2d_exact(trace_f<Q>(w, false)) : trace_of<Q>(w, false);
         }
       }
       __syncthreads();

@@ -246,6 +246,33 @@ def test_state_roundtrip_zero_steps_and_determinism():
     assert np.array_equal(g.get_state(), a)
 
 
+def test_all_states_in_one_buffer():
+    """adg_write_states / adg_read_states move every instance's state with one
+    call, in instance order, and agree with the per-instance calls."""
+    import torch
+    base = W()["ignition-5sp-200x3"]
+    wls = [base, I.scaled(base, 97, 7), I.scaled(base, 64, 4)]
+    wls[1].p, wls[1].at_order = 2, 3
+    mech = base.mechanism()
+    g = adg.ADG(mech, wls)
+    for k, w in enumerate(wls):
+        g.set_primitive(w.primitive(mech), k)
+    g.step(5)
+    n = g.states_doubles()
+    assert n == sum(g.nv * w.n_elem * (w.p + 1) for w in wls)
+    buf = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    g.read_states(buf.numpy())
+    torch.cuda.synchronize()
+    flat = np.concatenate([g.get_state(k).ravel() for k in range(len(wls))])
+    assert np.array_equal(buf.numpy(), flat)
+    new = torch.from_numpy(flat * 1.0001).pin_memory()
+    g.write_states(new.numpy())
+    torch.cuda.synchronize()
+    got = np.concatenate([g.get_state(k).ravel() for k in range(len(wls))])
+    assert np.array_equal(got, new.numpy())
+    g.close()
+
+
 def test_nonphysical_state_is_reported():
     """A state with negative density (made on the host) is reported by
     adg_status as ADG_ERR_NONPHYSICAL; the context stays usable."""
