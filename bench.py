@@ -744,12 +744,12 @@ def main(argv=None):
 # degree groups) from ncu, per (workload, kernel revision, precision); the
 # summaries are under profiles/.
 STAGE_TRAFFIC = {
-    (ENSEMBLE, "v17", "mixed"): 2.656e9,
-    (ENSEMBLE, "v17", "fp64"): 2.660e9,
-    (ENSEMBLE, "v17", "mixed_f32chem"): 2.657e9,
+    (ENSEMBLE, "v20", "mixed"): 2.655e9,
+    (ENSEMBLE, "v20", "fp64"): 2.663e9,
+    (ENSEMBLE, "v20", "mixed_f32chem"): 2.656e9,
 }
 
-KERNEL_REV = "v19"
+KERNEL_REV = "v20"
 
 if __name__ == "__main__":
     sys.exit(main())

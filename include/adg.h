@@ -195,8 +195,11 @@ int adg_read_state(adg_ctx *ctx, int instance, double *w_host, void *stream);
 
 /* adg_write_state and adg_read_state for every instance with one call: w_host
  * holds the states of instances 0, 1, ... in order, each [nv][n_elem][p+1]
- * (adg_states_doubles gives the total length); one copy per instance is
- * enqueued on `stream`. The same rules on pinned memory and validity apply.
+ * (adg_states_doubles gives the total length, which the buffer must hold). A
+ * pinned buffer mapped into the device's address space (cudaHostAlloc or
+ * cudaHostRegister memory under unified addressing) is read or written by one
+ * kernel over the host link; other host memory by one copy per instance. Both
+ * are enqueued on `stream`; the same rules on validity apply.
  * Errors: ADG_ERR_ARG (NULL), ADG_ERR_CUDA. */
 int adg_write_states(adg_ctx *ctx, const double *w_host, void *stream);
 int adg_read_states(adg_ctx *ctx, double *w_host, void *stream);

@@ -253,6 +253,7 @@ struct adg_ctx {
   Group groups[ADG_MAX_GROUPS];
   int n_groups;
   Inst *d_insts;                 // device instance table
+  int64_t *d_offs;               // [n_inst + 1] first double of each state in a flat buffer
   int64_t *d_steps;              // device step counters [n_inst]
   void *mem;
   bool owns_mem;
@@ -451,6 +452,7 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
   ctx->err_all = (int *)cv.take(sizeof(int) * 4 * ctx->n_inst);
   ctx->d_insts = (Inst *)cv.take(sizeof(Inst) * ctx->n_inst);
   ctx->d_steps = (int64_t *)cv.take(sizeof(int64_t) * ctx->n_inst);
+  ctx->d_offs = (int64_t *)cv.take(sizeof(int64_t) * (ctx->n_inst + 1));
   int max_pe = 1;
   for (int k = 0; k < ctx->n_inst; ++k) max_pe = cfgs[k].n_pe > max_pe ? cfgs[k].n_pe : max_pe;
   ctx->pub_in = (int *)cv.take(sizeof(int) * max_pe);
@@ -828,7 +830,11 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs_in, int n, void
   if (rc2 == ADG_OK) {
     std::vector<Inst> hi(n);
     for (int k = 0; k < n; ++k) hi[k] = ctx->inst[k].d;
+    std::vector<int64_t> offs(n + 1, 0);
+    for (int k = 0; k < n; ++k)
+      offs[k + 1] = offs[k] + (int64_t)hi[k].nv * hi[k].n_elem * (hi[k].p + 1);
     if (cudaMemcpy(ctx->d_insts, hi.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(ctx->d_offs, offs.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice) ||
         cudaMemset(ctx->d_steps, 0, sizeof(int64_t) * n))
       rc2 = ADG_ERR_CUDA;
     for (int gi = 0; gi < ctx->n_groups && rc2 == ADG_OK; ++gi) {
@@ -1213,9 +1219,13 @@ static int tune_limiter(adg_ctx *ctx, Group &G, cudaStream_t st, cudaEvent_t e0,
                   cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(flags.back().data(), I.flags, flags.back().size(), cudaMemcpyDeviceToHost));
   }
+  // the best of three rounds of three launches per size (a launch of a small
+  // group takes some 20 us, where one round is noisy); another size replaces
+  // the rule's only when it is 3 % faster
+  const int rule = G.EPB;
   const int cand[3] = {8, 16, 32};
-  int best_epb = G.EPB;
-  float best = 1e30f;
+  int best_epb = rule;
+  float best = 1e30f, at_rule = 1e30f;
   for (int epb : cand) {
     if (!limiter_block_ok(G, epb)) continue;
     G.EPB = epb;
@@ -1226,18 +1236,24 @@ static int tune_limiter(adg_ctx *ctx, Group &G, cudaStream_t st, cudaEvent_t e0,
     L.s = 0;
     L.EPB = epb;
     CK(launch_limiter(ctx->mech, L, G.Q, G.mixed, ctx->ns + 2, G.n_blocks, st));
-    CK(cudaEventRecord(e0, st));
-    for (int w = 0; w < 2; ++w)
-      CK(launch_limiter(ctx->mech, L, G.Q, G.mixed, ctx->ns + 2, G.n_blocks, st));
-    CK(cudaEventRecord(e1, st));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0.0f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) {
-      best = ms;
+    float round_best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      CK(cudaEventRecord(e0, st));
+      for (int w = 0; w < 3; ++w)
+        CK(launch_limiter(ctx->mech, L, G.Q, G.mixed, ctx->ns + 2, G.n_blocks, st));
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < round_best) round_best = ms;
+    }
+    if (epb == rule) at_rule = round_best;
+    if (round_best < best) {
+      best = round_best;
       best_epb = epb;
     }
   }
+  if (best_epb != rule && best > 0.97f * at_rule) best_epb = rule;
   G.EPB = best_epb;
   CK(upload_blocks(ctx, G));
   for (size_t m = 0; m < members.size(); ++m) {
@@ -1467,8 +1483,26 @@ int64_t adg_states_doubles(const adg_ctx *ctx) {
   return n;
 }
 
+// The device address of a host buffer the GPU can read and write directly
+// (pinned and mapped into the device's address space), or null.
+static double *mapped_host(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? (double *)at.devicePointer : nullptr;
+}
+
 int adg_write_states(adg_ctx *ctx, const double *w, void *stream) {
   if (!ctx || !w) return ADG_ERR_ARG;
+  ctx->last_stream = (cudaStream_t)stream;
+  // a mapped pinned buffer: one kernel reads it over the host link
+  if (double *dw = mapped_host(w)) {
+    CK(launch_states_copy(ctx->d_insts, ctx->d_offs, ctx->n_inst, dw, false,
+                          (cudaStream_t)stream));
+    return ADG_OK;
+  }
   for (const InstHost &h : ctx->inst) {
     const size_t n = (size_t)h.d.nv * h.d.n_elem * (h.d.p + 1);
     CK(cudaMemcpyAsync(h.d.wn, w, sizeof(double) * n, cudaMemcpyHostToDevice,
@@ -1481,6 +1515,12 @@ int adg_write_states(adg_ctx *ctx, const double *w, void *stream) {
 
 int adg_read_states(adg_ctx *ctx, double *w, void *stream) {
   if (!ctx || !w) return ADG_ERR_ARG;
+  ctx->last_stream = (cudaStream_t)stream;
+  if (double *dw = mapped_host(w)) {
+    CK(launch_states_copy(ctx->d_insts, ctx->d_offs, ctx->n_inst, dw, true,
+                          (cudaStream_t)stream));
+    return ADG_OK;
+  }
   for (const InstHost &h : ctx->inst) {
     const size_t n = (size_t)h.d.nv * h.d.n_elem * (h.d.p + 1);
     CK(cudaMemcpyAsync(w, h.d.wn, sizeof(double) * n, cudaMemcpyDeviceToHost,

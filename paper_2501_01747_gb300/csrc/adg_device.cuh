@@ -1302,7 +1302,7 @@ __device__ bool troubled_cell(const Mech &M, const Inst &I, int s, int64_t nstep
   sphp = allsum(sphp);
   // 3. the characteristic fields, k = 0 and nv-1 acoustic, k = 1..ns species k-1
   const R sig0 = fma(rho, a, fabs(m0)), sig1 = fabs(E0), sigr = rho;
-  const R tvb = (R)I.tvb, tau = (R)I.ind_floor, taup = (R)I.ind_floor_p;
+  const R tvb = conv_r<R>(I.tvb), tau = conv_r<R>(I.ind_floor), taup = conv_r<R>(I.ind_floor_p);
   bool tr = false;
   for (int k = li; k < nv; k += L) {
     R v[NP], scale, scale_p;  // the field's magnitude, and its momentum and energy part
@@ -1409,16 +1409,18 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
     Walk wk(threadIdx.x, nth, span);  // (variable, position in the span) of each load
     for (int base = threadIdx.x; base < total; base += BATCH * nth) {
       double xs[BATCH];
-      int dst[BATCH];
+      int dst[BATCH], mean[BATCH];  // tile index; index of the mean's low part, or -1
 #pragma unroll
       for (int b = 0; b < BATCH; ++b) {
         const int idx = base + b * nth;
         const int v = wk.o, r = wk.i;
         wk.next();
         dst[b] = -1;
+        mean[b] = -1;
         xs[b] = 0.0;
         if (idx < total) {
           const int le = r / Q, j = r - le * Q;
+          if (j == 0) mean[b] = v * ls + le;
           int src = e0 - 1 + le;
           bool mirror = false;
           if (src < 0 || src >= N) {
@@ -1441,8 +1443,7 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
           const DG hi = conv_r<DG>(xs[b]);
           tile[dst[b]] = hi;
           if constexpr (MIX) {
-            const int v = dst[b] / vs, r = dst[b] - v * vs;
-            if (r % Q == 0) tlo[v * ls + r / Q] = conv_r<DG>(xs[b] - f2d_exact(hi));
+            if (mean[b] >= 0) tlo[mean[b]] = conv_r<DG>(xs[b] - f2d_exact(hi));
           }
         }
     }

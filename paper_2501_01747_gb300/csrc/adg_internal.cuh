@@ -370,6 +370,11 @@ cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, int prec, int
 cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, bool mixed, int nv,
                            int n_blocks, cudaStream_t st);
 cudaError_t launch_advance(int64_t *steps, int n, cudaStream_t st);
+// Every instance's current state to (to_host) or from a flat host buffer the
+// device can address (pinned and mapped): offs[k] is instance k's first double
+// in it, offs[n] the total.
+cudaError_t launch_states_copy(const Inst *insts, const int64_t *offs, int n, double *host,
+                               bool to_host, cudaStream_t st);
 cudaError_t launch_aux(const LimArgs &A, int Q, int n_blocks, cudaStream_t st);
 // per-variant units (adg_k64.cu, adg_k32.cu, adg_k32f.cu)
 cudaError_t launch_stage_fp64(const Mech &M, const StageArgs &A, int Q, int n_tiles,

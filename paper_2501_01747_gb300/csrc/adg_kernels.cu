@@ -272,6 +272,43 @@ cudaError_t launch_advance_by(int64_t *step, int64_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// A flat buffer of all states <-> the instances' w^n, one double per item in
+// grid-stride order (consecutive threads touch consecutive doubles on both
+// sides); the instance of an item comes from a binary search of the offsets,
+// staged in shared memory when they fit.
+__global__ void states_copy_kernel(const Inst *insts, const int64_t *offs, int n, double *host,
+                                   int to_host) {
+  constexpr int MAXS = 2048;
+  __shared__ int64_t so[MAXS + 1];
+  const bool staged = n < MAXS;
+  if (staged)
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) so[k] = offs[k];
+  __syncthreads();
+  const int64_t *o = staged ? so : offs;
+  const int64_t total = o[n];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n - 1;  // the instance k with o[k] <= i < o[k + 1]
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (o[mid] <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    double *w = insts[lo].wn + (i - o[lo]);
+    if (to_host) host[i] = *w;
+    else *w = host[i];
+  }
+}
+
+cudaError_t launch_states_copy(const Inst *insts, const int64_t *offs, int n, double *host,
+                               bool to_host, cudaStream_t st) {
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  states_copy_kernel<<<n_sm * 8, 256, 0, st>>>(insts, offs, n, host, to_host ? 1 : 0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_advance(int64_t *steps, int n, cudaStream_t st) {
   return launch_pdl(advance_kernel, dim3((n + 127) / 128), dim3(128), 0, st, steps, n);
 }

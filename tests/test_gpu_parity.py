@@ -270,6 +270,14 @@ def test_all_states_in_one_buffer():
     torch.cuda.synchronize()
     got = np.concatenate([g.get_state(k).ravel() for k in range(len(wls))])
     assert np.array_equal(got, new.numpy())
+    # pageable host memory takes the per-instance copies
+    page = flat * 0.9999
+    g.write_states(page)
+    torch.cuda.synchronize()
+    back = np.zeros(n)
+    g.read_states(back)
+    torch.cuda.synchronize()
+    assert np.array_equal(back, page)
     g.close()
 
 
