@@ -459,6 +459,62 @@ def unsync_measure(adg, torch, wl, mech, prim, prec, dev, warmup, steps):
             "relative_drift": drift}
 
 
+def decomposed_measure(adg, torch, wl, mech, prim, dev, warmup, steps, n_sub=4):
+    """One problem cut into n_sub subdomains of whole PEs (domain.py), held as the
+    instances of one context on this GPU and stepped half-stage by half-stage,
+    with their boundary blocks moved by adg_part_block between the halves: first
+    as plain launches and device copies on one stream, then the same step
+    captured as one CUDA graph and replayed (the headline of the record). The
+    rate counts the whole domain's DOFs only (not the buffer elements); the
+    state after both runs is compared bit for bit with the whole-domain run of
+    the same steps."""
+    from paper_2501_01747_gb300 import domain as D
+    subs = [D.subdomain(wl, pb, pe) for pb, pe in D.split_pes(wl.n_pe, n_sub)]
+    g = adg.ADG(mech, subs, device=dev, precision="mixed")
+    parts = [D.AdgPart(g, k) for k in range(len(subs))]
+    for k, part in enumerate(parts):
+        g.set_primitive(D.local_slice(prim, wl.n_elem, part.elem0, part.n_local, axis=1), k)
+    ex = D.LocalExchange(parts)
+    S = rk_stages(wl)
+    stream = torch.cuda.current_stream(dev)
+    D.advance(warmup, S, g.step_stage, ex)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # plain launches, then the same step captured as a CUDA graph and replayed
+    e0.record(stream)
+    D.advance(steps, S, g.step_stage, ex)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_plain = e0.elapsed_time(e1)
+    graph = D.capture_step(S, g.step_stage, ex, dev)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    g.check()
+    got = np.concatenate([D.owned(g.get_state(k), *p_.cut, axis=1)
+                          for k, p_ in enumerate(parts)], axis=1)
+    g.close()
+    w = adg.ADG(mech, [wl], device=dev, precision="mixed")
+    w.set_primitive(prim)
+    w.step(warmup + 2 * steps)
+    ref = w.get_state()
+    w.close()
+    rate = dof_stages_per_step([wl]) * steps
+    return {"workload": wl.name, "precision": "mixed", "subdomains": n_sub,
+            "pe_ranges": D.split_pes(wl.n_pe, n_sub),
+            "launch": "one CUDA graph per step: per half-stage the stage or limiter kernels "
+                      "and the block moves (adg_part_block) of every subdomain; buffer "
+                      "elements computed and discarded",
+            "value": rate / (ms / 1e3), "unit": "DOF-stage/s", "steps": steps,
+            "ms_per_step": ms / steps,
+            "plain_launches": {"value": rate / (ms_plain / 1e3), "ms_per_step": ms_plain / steps},
+            "bit_identical_to_whole_domain": bool(np.array_equal(got, ref))}
+
+
 def mixed_error(adg, torch, wls, mech, prims, dev, n_steps, variant="mixed"):
     """Error of a mixed variant against the FP64 path (which matches the FP64
     oracle to 1e-10) after n_steps from the same state: the largest relative
@@ -599,6 +655,9 @@ def main(argv=None):
     ap.add_argument("--lserk-steps", type=int, default=100,
                     help="timed steps of the LSERK4 measurement (the 5-stage 4th-order "
                          "low-storage integrator) on the 9-species ignition; 0 to skip")
+    ap.add_argument("--domain-steps", type=int, default=20,
+                    help="steps of the domain-decomposed run (4 subdomains of the ignition "
+                         "workload in one context); 0 leaves it out")
     ap.add_argument("--viscous", action="store_true",
                     help="run the headline workload with the viscous terms")
     ap.add_argument("--visc-steps", type=int, default=100,
@@ -665,9 +724,12 @@ def main(argv=None):
         subs["detonation_53sp"] = sub_record(l_wls, l_all, l_mech, lres, lerr, args.large_steps,
                                              peaks, src, LARGE, largs, l_mode, ws)
 
-    uns = lsk = vis = None
+    uns = lsk = vis = dec = None
     if single is not None and not args.only:
         swl, smech, sprim = single
+        if args.domain_steps > 0 and swl.n_pe >= 4:
+            dec = decomposed_measure(adg, torch, swl, smech, sprim, dev, args.warmup,
+                                     args.domain_steps)
         if args.unsync_steps > 0:
             uns = unsync_measure(adg, torch, swl, smech, sprim, "mixed", dev, args.warmup,
                                  args.unsync_steps)
@@ -712,6 +774,11 @@ def main(argv=None):
     line.update(subs)
     if uns is not None:
         line["unsync"] = uns
+    if dec is not None:
+        whole = subs.get("ignition", {}).get("mixed", {}).get("value")
+        if whole:
+            dec["vs_whole_domain_graph"] = dec["value"] / whole
+        line["decomposed"] = dec
     if vis is not None:
         vw, vmech, r = vis
         line["viscous"] = {

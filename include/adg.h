@@ -270,9 +270,13 @@ int adg_step_stage(adg_ctx *ctx, int stage, int half, void *stream);
  * import = 0 (export): copies the owned element at that side (the neighbour's
  * buffer) into blk_dev; import = 1: writes blk_dev into the buffer element at
  * that side, and for ADG_PART_PRELIMIT also into the cut face's pre-limit
- * history (the levels the AT-WENO neighbour of Eq. 11 reads). Call the exports
- * of a stage's pre-limit output after its half 0 and the imports before its
- * half 1; the stage inputs' before half 0 of the stage.
+ * history (the levels the AT-WENO neighbour of Eq. 11 reads), at the step the
+ * device's step counter holds when the copy runs. Exports are device copies,
+ * imports a small kernel; both only enqueue work on `stream`, so the halves
+ * and the block moves of a step can be captured in a CUDA graph and replayed
+ * (adg_steps_done then counts only the calls made, not the replays). Call the
+ * exports of a stage's pre-limit output after its half 0 and the imports
+ * before its half 1; the stage inputs' before half 0 of the stage.
  * Errors: ADG_ERR_ARG (NULL, bad instance, side that is not cut, bad what or
  * stage), ADG_ERR_CUDA. */
 #define ADG_PART_INPUT 0

@@ -1176,15 +1176,10 @@ int adg_part_block(adg_ctx *ctx, int k, int what, int side, int stage, double *b
                          st));
     return ADG_OK;
   }
-  const int e = side == 0 ? 0 : N - 1;  // the buffer element
-  CK(cudaMemcpy2DAsync(arr + (size_t)e * Q, pitch, blk, row, row, nv, cudaMemcpyDeviceToDevice,
-                       st));
-  if (what == ADG_PART_PRELIMIT) {
-    // the buffer's side of the cut face in the pre-limit history of this step
-    const int pf = side == 0 ? 0 : I.npf - 1;
-    CK(cudaMemcpyAsync(I.ring_pre + ring_block(I, h.n, stage, pf, side), blk, row * nv,
-                       cudaMemcpyDeviceToDevice, st));
-  }
+  // the buffer element, and for a pre-limit block the buffer's side of the cut
+  // face in the pre-limit history of the current step: by a kernel that reads
+  // the step from the device counter, so that a captured exchange replays
+  CK(launch_part_import(ctx->d_insts + k, what, side, stage, blk, nv, Q, st));
   return ADG_OK;
 }
 

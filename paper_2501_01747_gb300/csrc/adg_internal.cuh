@@ -370,6 +370,12 @@ cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, int prec, int
 cudaError_t launch_limiter(const Mech &M, const LimArgs &A, int Q, bool mixed, int nv,
                            int n_blocks, cudaStream_t st);
 cudaError_t launch_advance(int64_t *steps, int n, cudaStream_t st);
+// A neighbour subdomain's boundary block [nv][Q] into the buffer element at one
+// side of a subdomain instance (the stage input of `stage`, or its pre-limit
+// output, which also goes into the cut face's pre-limit history at the step the
+// device counter holds, so that the copy may be replayed from a graph).
+cudaError_t launch_part_import(const Inst *inst, int what, int side, int stage,
+                               const double *blk, int nv, int Q, cudaStream_t st);
 // Every instance's current state to (to_host) or from a flat host buffer the
 // device can address (pinned and mapped): offs[k] is instance k's first double
 // in it, offs[n] the total.

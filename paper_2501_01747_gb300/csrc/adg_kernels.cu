@@ -272,6 +272,29 @@ cudaError_t launch_advance_by(int64_t *step, int64_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+__global__ void part_import_kernel(const Inst *inst, int what, int side, int stage,
+                                   const double *blk) {
+  const Inst &I = *inst;
+  const int Q = I.p + 1, n = I.nv * Q, N = I.n_elem;
+  const int e = side == 0 ? 0 : N - 1;  // the buffer element
+  double *arr = what == ADG_PART_PRELIMIT ? I.wpre : const_cast<double *>(stage_input(I, stage));
+  const int pf = side == 0 ? 0 : I.npf - 1;
+  const int64_t nstep = *I.step;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int v = t / Q, j = t - v * Q;
+    const double x = blk[t];
+    arr[((size_t)v * N + e) * Q + j] = x;
+    if (what == ADG_PART_PRELIMIT) I.ring_pre[ring_block(I, nstep, stage, pf, side) + t] = x;
+  }
+}
+
+cudaError_t launch_part_import(const Inst *inst, int what, int side, int stage,
+                               const double *blk, int nv, int Q, cudaStream_t st) {
+  const int n = nv * Q, threads = n < 512 ? ((n + 31) / 32) * 32 : 512;
+  part_import_kernel<<<1, threads, 0, st>>>(inst, what, side, stage, blk);
+  return cudaGetLastError();
+}
+
 // A flat buffer of all states <-> the instances' w^n, one double per item in
 // grid-stride order (consecutive threads touch consecutive doubles on both
 // sides); the instance of an item comes from a binary search of the offsets,

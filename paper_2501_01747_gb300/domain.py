@@ -84,6 +84,19 @@ def advance(n_steps, n_stages, stage, exchange):
             stage(s, 1)
 
 
+def capture_step(n_stages, stage, exchange, device=None):
+    """One step of a decomposed run (the sequence of `advance`) captured into a
+    torch CUDA graph on the current device, for runs whose stage and exchange
+    calls only enqueue work on PyTorch's current stream (``adg.ADG.step_stage``
+    and ``AdgPart``): the graph's replay is one step. Capturing enqueues nothing
+    that runs; the blocks the exchange allocates come from the graph's pool."""
+    import torch
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        advance(1, n_stages, stage, exchange)
+    return g
+
+
 class LocalExchange:
     """The exchange between subdomains held by one process, listed in PE order.
 
