@@ -546,43 +546,48 @@ def mixed_error(adg, torch, wls, mech, prims, dev, n_steps, variant="mixed"):
 
 
 def roofline(wls, mech, r, prec, peaks, src, traffic_key=None):
-    """Roofline of the stage kernel (the dominant one): the algorithmic bytes of
-    one RK stage of every instance (stage_kernel_bytes) over the stage kernels'
-    time for one stage (all degree groups), against the measured HBM copy
-    bandwidth; beside it the algorithmic flops against the pipe that carries
-    them (FP32 in the mixed variants, FP64 otherwise)."""
+    """Roofline of the stage kernel (the dominant one) over one RK stage of every
+    instance, all degree groups, against the stage kernels' time for that stage.
+    The kernel does more FP64 work per DRAM byte (about 1.4 flop/byte in
+    ADG_MIXED on the ensemble) than the FP64 ridge point (the measured FP64 FMA
+    peak over the measured HBM copy bandwidth, 0.16 flop/byte), and ncu finds the
+    FP64 pipe its busiest unit, so its roof is the FP64 pipe: the primary figure
+    is the FP64 flops the variant does by design (all algorithmic flops in FP64,
+    stage_kernel_fp64_flops in the mixed variants) against the measured FP64 FMA
+    peak. Beside it: the algorithmic bytes (stage_kernel_bytes) against the
+    measured HBM copy bandwidth, and in the mixed variants all algorithmic flops
+    against the FP32 pipe."""
     n_st = max(rk_stages(w) for w in wls)  # stage launches per step (uniform here)
     stage_s = r["kms"][0] / 1e3 / (n_st * r["steps"])
     nbytes = sum(stage_kernel_bytes(w, mech, prec) for w in wls)
     flops = sum(stage_kernel_flops(w, mech)[0] for w in wls)
     n_exp = sum(stage_kernel_flops(w, mech)[1] for w in wls)
     hbm = peaks.get("hbm_gbs", 6800.0)
-    achieved = nbytes / stage_s / 1e9
     mixed = prec in MIXED_VARIANTS
-    alu_peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
+    f64 = sum(stage_kernel_fp64_flops(w, mech, prec) for w in wls) if mixed else flops
     tr = STAGE_TRAFFIC.get((traffic_key, KERNEL_REV, prec)) if traffic_key else None
-    alu = {"pipe": "fp32" if mixed else "fp64",
-           "achieved": flops / stage_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-           "frac": flops / stage_s / 1e12 / alu_peak, "peak_source": PEAK_NOTE,
-           "exp_per_s": n_exp / stage_s}
+    out = {"bound": "alu", "pipe": "fp64",
+           "achieved": f64 / stage_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+           "frac": f64 / stage_s / 1e12 / FP64_PEAK_TFLOPS, "traffic": tr,
+           "peak_source": PEAK_NOTE,
+           "kernel": "stage_kernel (%s), all degree groups of one RK stage" % prec,
+           "fp64_flops_per_stage": f64,
+           "fp64_flops_per_dram_byte": f64 / (tr or nbytes),
+           "ridge_flops_per_byte": FP64_PEAK_TFLOPS * 1e12 / (hbm * 1e9),
+           "exp_per_s": n_exp / stage_s,
+           "kernel_ms": stage_s * 1e3,
+           "kernel_share": r["kms"][0] / max(1e-9, r["kms"][0] + r["kms"][1]),
+           "limiter_ms": r["kms"][1] / (n_st * r["steps"]),
+           "hbm": {"achieved": nbytes / stage_s / 1e9, "peak": hbm, "unit": "GB/s",
+                   "frac": nbytes / stage_s / 1e9 / hbm,
+                   "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % src,
+                   "algorithmic_bytes_per_stage": nbytes,
+                   "bytes_per_vector_dof": (16 if mixed else 24) * (mech.ns + 2) + 16}}
     if mixed:
-        # the FP64 work the variant keeps by design, against the FP64 pipe that
-        # bounds it (ncu: the busiest unit of the mixed stage kernels)
-        f64 = sum(stage_kernel_fp64_flops(w, mech, prec) for w in wls)
-        alu["fp64_part"] = {"achieved": f64 / stage_s / 1e12, "peak": FP64_PEAK_TFLOPS,
-                            "unit": "TFLOP/s",
-                            "frac": f64 / stage_s / 1e12 / FP64_PEAK_TFLOPS,
-                            "flops_per_stage": f64, "peak_source": PEAK_NOTE}
-    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": tr,
-            "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % src,
-            "kernel": "stage_kernel (%s), all degree groups of one RK stage" % prec,
-            "algorithmic_bytes_per_stage": nbytes,
-            "bytes_per_vector_dof": (16 if mixed else 24) * (mech.ns + 2) + 16,
-            "kernel_ms": stage_s * 1e3,
-            "kernel_share": r["kms"][0] / max(1e-9, r["kms"][0] + r["kms"][1]),
-            "limiter_ms": r["kms"][1] / (n_st * r["steps"]),
-            "alu": alu}
+        out["fp32"] = {"achieved": flops / stage_s / 1e12, "peak": FP32_PEAK_TFLOPS,
+                       "unit": "TFLOP/s", "frac": flops / stage_s / 1e12 / FP32_PEAK_TFLOPS,
+                       "algorithmic_flops_per_stage": flops, "peak_source": PEAK_NOTE}
+    return out
 
 
 def compare(adg, torch, wls, mech, prims, args, dev, pg, steps, autotune=True,
