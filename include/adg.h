@@ -347,7 +347,8 @@ int adg_autotune(adg_ctx *ctx, void *stream);
 int adg_get_tuning(const adg_ctx *ctx, int *n_groups, int *tuning);
 /* Set the launch configuration of group g directly (for instance one that an
  * earlier adg_autotune found): elements per stage tile >= 2, threads per CTA a
- * multiple of 32 in [32, 512]. Synchronous; drops the captured step graphs.
+ * multiple of 32 in [32, 512], or up to 1024 for a group of the mixed variants
+ * without viscous terms. Synchronous; drops the captured step graphs.
  * ADG_ERR_ARG for a bad group or a tile whose shared memory exceeds 200 KB. */
 int adg_set_tuning(adg_ctx *ctx, int group, int elements_per_tile, int threads_per_cta);
 /* Set the limiter's elements per CTA of group g (8, 16 or 32 in the mixed

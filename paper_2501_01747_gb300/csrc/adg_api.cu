@@ -1267,7 +1267,7 @@ int adg_autotune(adg_ctx *ctx, void *stream) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   static const int kTE[] = {2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 32, 40, 48, 64};
-  static const int kNT[] = {64, 128, 192, 256, 384, 512};
+  static const int kNT[] = {64, 128, 192, 256, 384, 512, 768, 1024};
   int rc = ADG_OK;
   for (int gi = 0; gi < ctx->n_groups && rc == ADG_OK; ++gi) {
     Group &G = ctx->groups[gi];
@@ -1282,6 +1282,7 @@ int adg_autotune(adg_ctx *ctx, void *stream) {
         break;
       }
       for (int nt : kNT) {
+        if (nt > stage_max_threads(G.prec, G.visc)) continue;
         StageArgs A;
         A.insts = ctx->d_insts;
         A.tiles = G.d_tiles;
@@ -1329,7 +1330,8 @@ int adg_set_tuning(adg_ctx *ctx, int group, int elements_per_tile, int threads_p
   if (!ctx || group < 0 || group >= ctx->n_groups) return ADG_ERR_ARG;
   Group &G = ctx->groups[group];
   const int te = elements_per_tile, nt = threads_per_cta;
-  if (te < kMinTile || nt < 32 || nt > 512 || nt % 32) return ADG_ERR_ARG;
+  if (te < kMinTile || nt < 32 || nt > stage_max_threads(G.prec, G.visc) || nt % 32)
+    return ADG_ERR_ARG;
   if (stage_smem(ctx->mech, te, G.Q, G.O, G.prec, G.visc) > 200 * 1024) return ADG_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->last_stream));
   G.TE = te;

@@ -1081,7 +1081,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
 }
 
 template <int Q, int PREC, bool VISC>
-__global__ void __launch_bounds__(512) stage_kernel(Mech M, StageArgs A) {
+__global__ void __launch_bounds__(stage_max_threads(PREC, VISC)) stage_kernel(Mech M, StageArgs A) {
   pdl_wait();
   __shared__ Inst sI;
   const int2 tile = A.tiles[blockIdx.x];
@@ -1719,7 +1719,7 @@ static cudaError_t launch_stage_q(const Mech &M, const StageArgs &A, int n_tiles
                                   cudaStream_t st) {
   if ((A.visc != 0) != VISC) return cudaErrorInvalidValue;
   size_t smem = stage_smem_bytes(A.TE, Q, M.ns, M.nr, M.nterm, A.O, PREC, VISC);
-  if (A.NT < 32 || A.NT > 512 || A.NT % 32) return cudaErrorInvalidValue;
+  if (A.NT < 32 || A.NT > stage_max_threads(PREC, VISC) || A.NT % 32) return cudaErrorInvalidValue;
   return launch_pdl(stage_kernel<Q, PREC, VISC>, dim3(n_tiles), dim3(A.NT), smem, st, M, A);
 }
 

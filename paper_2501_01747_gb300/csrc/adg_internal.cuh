@@ -363,6 +363,13 @@ void make_tables(Basis *tables);
 cudaError_t upload_basis(const Basis *tables);
 int stage_tile(const Mech &M, int Q, int O, int prec, bool visc);
 int stage_threads(int TE, int Q, int nr);
+// Largest CTA of the stage kernel: 1024 threads for the inviscid mixed variants
+// (they fit in 64 registers a thread, so that a tile too large for two CTAs per
+// SM can still keep 32 warps resident), 512 otherwise (FP64 and the viscous
+// terms need up to 128 registers).
+__host__ __device__ constexpr int stage_max_threads(int prec, bool visc) {
+  return (prec != ADG_FP64 && !visc) ? 1024 : 512;
+}
 size_t stage_smem(const Mech &M, int TE, int Q, int O, int prec, bool visc);
 cudaError_t prepare_kernels(int nv, int ns, int nr);
 cudaError_t launch_stage(const Mech &M, const StageArgs &A, int Q, int prec, int n_tiles,
