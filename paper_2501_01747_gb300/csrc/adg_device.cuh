@@ -243,8 +243,8 @@ __device__ __forceinline__ R conv_r(C x) {
 // The trace of one variable's modes w[0..Q) at xi = +1 (right = false: sum_j
 // w_j) or at xi = -1 (right = true: sum_j (-1)^j w_j), in FP64 and in the order
 // of the stage kernel's face phase. Every trace that enters the history ring is
-// formed by it, so that a face reads the same value from the ring as it would
-// form itself.
+// formed by it (by trace_f in ADG_MIXED), so that a face reads the same value
+// from the ring as it would form itself.
 template <int Q>
 __device__ __forceinline__ double trace_of(const double *w, bool right) {
   double a = 0.0;
