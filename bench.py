@@ -819,9 +819,12 @@ STAGE_TRAFFIC = {
     (ENSEMBLE, "v20", "mixed"): 2.655e9,
     (ENSEMBLE, "v20", "fp64"): 2.663e9,
     (ENSEMBLE, "v20", "mixed_f32chem"): 2.656e9,
+    (ENSEMBLE, "v21", "mixed"): 2.655e9,
+    (ENSEMBLE, "v21", "fp64"): 2.662e9,
+    (ENSEMBLE, "v21", "mixed_f32chem"): 2.656e9,
 }
 
-KERNEL_REV = "v20"
+KERNEL_REV = "v21"
 
 if __name__ == "__main__":
     sys.exit(main())

@@ -732,25 +732,42 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
   // for constant c_p), ln T, 1/T, velocity and pressure, in FP64; the face items
   {
     const double *sQW = ssp + SP_QW * ns, *sCVW = ssp + SP_CVW * ns, *sRW = ssp + SP_RW * ns;
+    // A large mechanism's species sums run on L lanes per point (lane g takes
+    // species g, g + L, ...; a shuffle tree adds the lanes up), so that a tile
+    // of few points does not leave the CTA waiting at the next barrier on a
+    // long serial chain. L depends on the mechanism only, so the result does
+    // not depend on the launch configuration.
+    const int L = !MIX ? 1 : (ns >= 32 ? 8 : (ns >= 16 ? 4 : 1));
+    const int lsh = L == 8 ? 3 : (L == 4 ? 2 : 0);
+    const int npl = teq << lsh;
     // the face items start on a warp boundary: a warp holding points and faces
     // ran both paths one after the other and was the phase's critical path
-    const int fb = (teq + 31) & ~31;
+    const int fb = (npl + 31) & ~31;
     for (int it = tid; it < fb + n_face; it += nth) {
       if (it >= fb) {
         face_item(it - fb);
         continue;
       }
-      if (it >= teq) continue;
-      const int t = it;
+      // a warp of the point region: all its lanes take part in the shuffles
+      const bool act = it < npl;
+      const int t = act ? (it >> lsh) : 0, g = it & (L - 1);
       const double *wq = snw + t;
       double rho = 0.0, qsum = 0.0, cv = 0.0, Rm = 0.0;
-      for (int i = 0; i < ns; ++i) {
-        const double r = wq[(size_t)(2 + i) * TQ];
-        rho += r;
-        qsum = fma(r, sQW[i], qsum);
-        cv = fma(r, sCVW[i], cv);
-        Rm = fma(r, sRW[i], Rm);
+      if (act)
+        for (int i = g; i < ns; i += L) {
+          const double r = wq[(size_t)(2 + i) * TQ];
+          rho += r;
+          qsum = fma(r, sQW[i], qsum);
+          cv = fma(r, sCVW[i], cv);
+          Rm = fma(r, sRW[i], Rm);
+        }
+      for (int o = L >> 1; o > 0; o >>= 1) {
+        rho += __shfl_xor_sync(0xffffffffu, rho, o, L);
+        qsum += __shfl_xor_sync(0xffffffffu, qsum, o, L);
+        cv += __shfl_xor_sync(0xffffffffu, cv, o, L);
+        Rm += __shfl_xor_sync(0xffffffffu, Rm, o, L);
       }
+      if (!act || g != 0) continue;
       const double m = wq[0];
       double u, num, T;
       if constexpr (FCHEM) {

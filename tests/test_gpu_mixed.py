@@ -18,6 +18,8 @@ Troubled-cell flags are not required to match exactly: the FP32 indicator uses
 the oracle's rounding guard (1e-10 of the field's magnitude) on deviations it
 forms from the FP64 modes, and a deviation near the guard, or a cell at the
 edge of the minmod test, may be decided either way."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -78,6 +80,27 @@ def run_mixed(wl, mech, prim, n_steps, chunks=1, prec="mixed"):
     assert np.all(np.isfinite(g.get_state()))
     return g, o
 
+
+
+@pytest.mark.parametrize("case", ["20sp", "53sp"])
+def test_large_mechanisms_mixed_bar(case):
+    """ADG_MIXED on mechanisms whose temperature inversion sums its species on 4
+    lanes (a 20-species, 12-reaction draw on the ignition shape) and on 8 (the
+    53-species detonation mechanism) per Gauss point, 97 ragged elements and 7
+    PEs, SAA delays, WENO: the mixed bar against the oracle."""
+    if case == "20sp":
+        base = W()["ignition-5sp-200x3"]
+        wl = dataclasses.replace(I.scaled(base, 97, 7), ns=20, nr=12, mech_seed=5, attempts=None)
+        steps = 40
+    else:
+        base = W()["detonation-53sp-65536x3"]
+        wl = I.scaled(base, 97, 7)
+        wl.dt = base.dt * 0.25
+        steps = 20
+    mech = wl.mechanism()
+    g, o = run_mixed(wl, mech, wl.primitive(mech), steps)
+    eT, eY = errors(g, o, wl, pointwise=False)
+    assert eT <= TOL_T and eY <= TOL_Y, (eT, eY)
 
 def W():
     return I.load_workloads()

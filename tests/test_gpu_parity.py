@@ -10,6 +10,8 @@ oracle's own input moves by 1e-15; in these scales the oracle moves by less than
 1e-11 (tests/test_oracle_conditioning.py), ten times below the bar.
 Troubled-cell flags must be identical (per stage of the last step and counted
 over the whole run)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -100,6 +102,28 @@ def test_every_degree_ragged_mesh_shock(p):
     wl.dt = base.dt * 0.05
     mech = wl.mechanism()
     g, o = run_both(wl, mech, wl.primitive(mech), 60)
+    assert_parity(g, o)
+    assert o.flags()[1].sum() > 0
+
+
+@pytest.mark.parametrize("case", ["20sp", "53sp"])
+def test_large_mechanisms_small_mesh(case):
+    """Mechanisms whose temperature inversion sums its species on 4 lanes per
+    Gauss point (16 to 31 species: a 20-species, 12-reaction draw on the
+    ignition shape) and on 8 (32 and more: the 53-species, 325-reaction
+    mechanism on the detonation shape), on 97 ragged elements and 7 PEs with
+    SAA delays and WENO: full comparison with the oracle, flags included."""
+    if case == "20sp":
+        base = W()["ignition-5sp-200x3"]
+        wl = dataclasses.replace(I.scaled(base, 97, 7), ns=20, nr=12, mech_seed=5, attempts=None)
+        steps = 40
+    else:
+        base = W()["detonation-53sp-65536x3"]
+        wl = I.scaled(base, 97, 7)
+        wl.dt = base.dt * 0.25
+        steps = 20
+    mech = wl.mechanism()
+    g, o = run_both(wl, mech, wl.primitive(mech), steps)
     assert_parity(g, o)
     assert o.flags()[1].sum() > 0
 
