@@ -1708,8 +1708,14 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
   (void)gmask;
 }
 
+// The mixed variants are held to 64 registers a thread (eight 128-thread CTAs,
+// 32 warps, per SM instead of five at 96 registers): their limiter waits on
+// instruction latency, and the extra warps hide it (1.12 -> 0.97 ms per RK
+// stage on the 512-instance ensemble, a few bytes of spills). The FP64 limiter
+// is bound by the FP64 pipe and keeps the compiler's choice (a cap of 170
+// registers measured the same).
 template <int Q, int G, bool MIX, int EPB>
-__global__ void __launch_bounds__(LIM_THREADS) limiter_kernel(Mech M, LimArgs A) {
+__global__ void __launch_bounds__(LIM_THREADS, MIX ? 8 : 1) limiter_kernel(Mech M, LimArgs A) {
   pdl_enter();
   __shared__ Inst sI;
   const int2 blkid = A.blocks[blockIdx.x];
