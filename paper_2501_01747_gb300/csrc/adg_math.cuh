@@ -188,12 +188,16 @@ __host__ __device__ __forceinline__ IExpParts iexp_parts(long long bits, const I
   return o;
 }
 
+// The library exp for the rare arguments iexp leaves to it, out of line: inline,
+// its FP64 instructions may be issued, predicated off, on every call.
+static __host__ __device__ __noinline__ double iexp_slow(double x) { return exp(x); }
+
 // exp(x) with the table in shared (or host) memory. Outside |x| <= 700 (and for
 // NaN and infinities) the library exp is returned.
 __host__ __device__ __forceinline__ double iexp(double x, const IExpTable &tab) {
   const long long bits = iexp_bits(x);
   // 0x4085E000 is the high word of 700.0
-  if ((int)((bits >> 32) & 0x7fffffff) > 0x4085E000) return exp(x);
+  if ((int)((bits >> 32) & 0x7fffffff) > 0x4085E000) return iexp_slow(x);
   const IExpParts p = iexp_parts(bits, tab);
   const int s = 11 - iexp_clz(p.V);  // leading bit 59..61 -> s = 7..9
   const unsigned long long mt = (p.V + (1ull << (s - 1))) >> s;  // 2^52 <= mt <= 2^53
@@ -447,6 +451,32 @@ __host__ __device__ __forceinline__ double log_tab(double x, const LogTable &tb)
   q = fma(u, q, 1.0);
   const double L_hi = 0x1.62e42fefa3800p-1, L_lo = 0x1.ef35793c76730p-45;
   return fma(dk, L_hi, tb.ln[j]) + fma(dk, L_lo, u * q);
+}
+
+// Double -> float rounded to nearest even, from the double's high and low words
+// to the float's bits, for the doubles outside the normal float range: zeros,
+// values whose float is subnormal or zero, values beyond the largest float, and
+// infinities and NaN (the canonical NaN 0x7fffffff). Integer operations only, so
+// that the fast conversion of the kernels (the bit-field move of d2f_int) needs
+// no FP64 instruction on any path. A normal double below the float range is
+// F 2^(eb - 1075) with the 53-bit significand F = 2^52 + m; in units of the
+// smallest subnormal float, 2^-149, that is F 2^(eb - 926), and the float's bits
+// are that integer rounded to even (a carry into 2^23 gives the smallest normal
+// float, as it should). A subnormal double is far below half the smallest
+// subnormal float and rounds to a signed zero; so does any value below 2^-150.
+__host__ __device__ inline unsigned d2f_edge_bits(unsigned hi, unsigned lo) {
+  const unsigned s = hi & 0x80000000u;
+  const int eb = (int)((hi >> 20) & 0x7ffu);
+  const unsigned mh = hi & 0xfffffu;
+  if (eb == 0x7ff) return (mh | lo) != 0u ? 0x7fffffffu : (s | 0x7f800000u);
+  if (eb - 1023 + 127 >= 255) return s | 0x7f800000u;
+  const int sh = 926 - eb;  // at least 30 for a double below the float range
+  if (eb == 0 || sh > 54) return s;
+  const unsigned long long F = (1ull << 52) | ((unsigned long long)mh << 32) | lo;
+  const unsigned long long q = F >> sh, rem = F & ((1ull << sh) - 1ull);
+  const unsigned long long half = 1ull << (sh - 1);
+  const unsigned long long up = (rem > half || (rem == half && (q & 1ull) != 0ull)) ? 1ull : 0ull;
+  return s | (unsigned)(q + up);
 }
 
 }  // namespace adg

@@ -4,13 +4,17 @@
 // precision on the host; the mixed variant's table logarithm likewise (against
 // its host build and logl), and its Newton-Raphson reciprocal (csrc/adg_device.cuh)
 // against the exact reciprocal, and its two-step reciprocal and integer-pipe
-// split of a double into a float pair. Prints one JSON line.
+// split of a double into a float pair; its integer-pipe double -> float
+// conversion at the edges of the float range against the host's conversion.
+// Prints one JSON line.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "../../paper_2501_01747_gb300/csrc/adg_device.cuh"
+#include "d2f_edge_values.h"
 
 __global__ void eval(const double *x, double *mine, double *cuda_ref, int n, adg::IExpTable tab) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -33,6 +37,12 @@ __global__ void eval_split(const double *x, float *hi, float *lo, double *rc2, i
   hi[i] = d.hi;
   lo[i] = d.lo;
   rc2[i] = adg::recip_nr2(x[i]);
+}
+
+__global__ void eval_d2f(const double *x, float *f, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  f[i] = adg::d2f_int(x[i]);
 }
 
 static double ulp_err(double got, long double ref) {
@@ -126,10 +136,30 @@ int main() {
     const long double rr = 1.0L / (long double)y[i];
     recip2_max_rel = fmax(recip2_max_rel, (double)fabsl(((long double)c2[i] - rr) / rr));
   }
-  printf("{\"n\": %d, \"host_mismatch\": %lld, \"max_ulp\": %.4f, \"cuda_exp_max_ulp\": %.4f, "
+  // the conversion at the edges of the float range, bit for bit (NaN as NaN)
+  const std::vector<double> ev = d2f_edge_values(1 << 18);
+  const int ne = (int)ev.size();
+  double *dev_e;
+  float *dev_f;
+  if (cudaMalloc(&dev_e, ne * 8) || cudaMalloc(&dev_f, ne * 4)) return 2;
+  cudaMemcpy(dev_e, ev.data(), ne * 8, cudaMemcpyHostToDevice);
+  eval_d2f<<<(ne + 255) / 256, 256>>>(dev_e, dev_f, ne);
+  std::vector<float> ef(ne);
+  cudaMemcpy(ef.data(), dev_f, ne * 4, cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  long long edge_mismatch = 0;
+  for (int i = 0; i < ne; ++i) {
+    const float ref = (float)ev[i];
+    if (std::isnan(ev[i])) {
+      if (!std::isnan(ef[i])) ++edge_mismatch;
+    } else if (std::memcmp(&ef[i], &ref, 4) != 0) {
+      ++edge_mismatch;
+    }
+  }
+  printf("{\"n\": %d, \"edge_n\": %d, \"edge_mismatch\": %lld, \"host_mismatch\": %lld, \"max_ulp\": %.4f, \"cuda_exp_max_ulp\": %.4f, "
          "\"log_host_mismatch\": %lld, \"log_max_ulp\": %.4f, \"recip_max_rel\": %.3g, "
          "\"recip2_max_rel\": %.3g, \"split_hi_mismatch\": %lld, \"split_max_rel\": %.3g, "
-         "\"cuda\": \"%s\"}\n", n, mismatch, max_ulp, cuda_max_ulp, log_mismatch, log_max_ulp,
+         "\"cuda\": \"%s\"}\n", n, ne, edge_mismatch, mismatch, max_ulp, cuda_max_ulp, log_mismatch, log_max_ulp,
          recip_max_rel, recip2_max_rel, split_hi_mismatch, split_max_rel, cudaGetErrorString(err));
   return err == cudaSuccess ? 0 : 1;
 }

@@ -6,7 +6,10 @@ logarithm on the GPU: bit for bit its host build and within 1.5 units in the
 last place of logl; its Newton-Raphson reciprocal within 2^-44 of 1/x, and the
 two-step one within 2^-51. The integer-pipe split of a double into a float
 pair: the high part is the double rounded to float, and the pair is within
-2^-47 of the double, for magnitudes from 2^-97 to the float maximum."""
+2^-47 of the double, for magnitudes from 2^-97 to the float maximum. The
+integer-pipe double -> float conversion at the edges of the float range (zeros,
+subnormal results and their ties, overflow, infinities, NaN) equals the host's
+conversion bit for bit."""
 import json
 import os
 import subprocess
@@ -33,3 +36,4 @@ def test_integer_exp_on_gpu_matches_host_and_exact(tmp_path):
     assert rec["recip2_max_rel"] <= 2.0 ** -51, rec
     assert rec["split_hi_mismatch"] == 0, rec
     assert rec["split_max_rel"] <= 2.0 ** -47, rec
+    assert rec["edge_n"] > 2 ** 18 and rec["edge_mismatch"] == 0, rec

@@ -37,3 +37,21 @@ def test_integer_exp_host_build_against_extended_precision(tmp_path):
     assert rec["df_correctly_rounded"] >= 0.99, rec
     assert rec["log_max_ulp"] <= 1.5, rec
     assert rec["log_max_abs_T"] <= 3e-15, rec
+
+
+def test_integer_float_conversion_at_the_range_edges_host_build(tmp_path):
+    """The integer double -> float conversion of the doubles outside the normal
+    float range (zeros, subnormal results with exact ties, overflow, infinities,
+    NaN; `d2f_edge_bits`), compiled for the host, equals the host's IEEE
+    round-to-nearest-even conversion bit for bit on about a million values."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    exe = str(tmp_path / "d2f_host")
+    subprocess.check_call([nvcc, "-O2", "-std=c++17",
+                           os.path.join(HERE, "cuda", "d2f_host_check.cu"), "-o", exe])
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout + out.stderr
+    rec = json.loads(out.stdout.strip().splitlines()[-1])
+    assert rec["checked"] > 10 ** 6, rec
+    assert rec["mismatch"] == 0 and rec["nan_bad"] == 0, rec
