@@ -450,6 +450,32 @@ __device__ inline void visc_faces(const double *sp, const R *spr, int ns, const 
 }
 
 
+// The rate of progress of reaction Rx at point t in FP64, for an item whose
+// rate constant kf or kr lies beyond the float range (ADG_MIXED), from the
+// float-pair concentrations scc [species][TQ]. Out of line, like the other rare
+// paths: inline, its FP64 products could be issued, predicated off, for every
+// item.
+static __device__ __noinline__ DF rate_fp64(const Rxn &Rx, const DF *scc, int TQ, int t, double f,
+                                            double r) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (Rx.rn[k] == 0) break;
+    const DF c = scc[(size_t)Rx.rs[k] * TQ + t];
+    const double cd = f2d_exact(c.hi) + f2d_exact(c.lo);
+    f *= cd;
+    if (Rx.rn[k] > 1) f *= cd;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (Rx.pn[k] == 0) break;
+    const DF c = scc[(size_t)Rx.ps[k] * TQ + t];
+    const double cd = f2d_exact(c.hi) + f2d_exact(c.lo);
+    r *= cd;
+    if (Rx.pn[k] > 1) r *= cd;
+  }
+  return d2df_int(f - r);
+}
+
 // Stage s of one tile: elements [e0, e0 + te) of instance I at step level nstep.
 // With UNSYNC the PE faces of the tile take the delays pd->k observed by a PE
 // that runs without synchronisation and read both sides from the history ring,
@@ -928,24 +954,7 @@ __device__ __forceinline__ void stage_body(const Mech &M, const StageArgs &A, co
       DF fwd = d2df_int(kf), rev = d2df_int(kr);
       if (!(fabsf(fwd.hi) < 3.0e38f) || !(fabsf(rev.hi) < 3.0e38f)) {
         // a rate constant beyond the float range: this item in FP64
-        double f = kf, r = kr;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if (Rx.rn[k] == 0) break;
-          const DF c = scc[(size_t)Rx.rs[k] * TQ + t];
-          const double cd = f2d_exact(c.hi) + f2d_exact(c.lo);
-          f *= cd;
-          if (Rx.rn[k] > 1) f *= cd;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if (Rx.pn[k] == 0) break;
-          const DF c = scc[(size_t)Rx.ps[k] * TQ + t];
-          const double cd = f2d_exact(c.hi) + f2d_exact(c.lo);
-          r *= cd;
-          if (Rx.pn[k] > 1) r *= cd;
-        }
-        sq[(size_t)j * TQ + t] = d2df_int(f - r);
+        sq[(size_t)j * TQ + t] = rate_fp64(Rx, scc, TQ, t, kf, kr);
         continue;
       }
 #pragma unroll
@@ -1741,10 +1750,12 @@ __device__ __forceinline__ void limiter_body(const Mech &M, const LimArgs &A, co
 // 32 warps, per SM instead of five at 96 registers): their limiter waits on
 // instruction latency, and the extra warps hide it (1.12 -> 0.97 ms per RK
 // stage on the 512-instance ensemble, a few bytes of spills). The FP64 limiter
-// is bound by the FP64 pipe and keeps the compiler's choice (a cap of 170
-// registers measured the same).
+// is bound by the FP64 pipe; with a hint of four CTAs per SM (at most 128
+// registers, a few bytes of spills at p = 4) it took 4.30 ms per RK stage
+// against 4.40 without a hint and 4.87 with a hint of one, which lets its
+// allocation grow by up to 30 registers.
 template <int Q, int G, bool MIX, int EPB>
-__global__ void __launch_bounds__(LIM_THREADS, MIX ? 8 : 1) limiter_kernel(Mech M, LimArgs A) {
+__global__ void __launch_bounds__(LIM_THREADS, MIX ? 8 : 4) limiter_kernel(Mech M, LimArgs A) {
   pdl_enter();
   __shared__ Inst sI;
   const int2 blkid = A.blocks[blockIdx.x];

@@ -430,11 +430,15 @@ struct LogTable {
   double inv[128];
 };
 
+// The library log for the arguments log_tab leaves to it, out of line (as
+// iexp_slow).
+static __host__ __device__ __noinline__ double log_slow(double x) { return log(x); }
+
 __host__ __device__ __forceinline__ double log_tab(double x, const LogTable &tb) {
   unsigned long long b;
   std::memcpy(&b, &x, 8);
   const unsigned ex = (unsigned)(b >> 52);  // sign and biased exponent
-  if (ex == 0u || ex >= 2047u || ex == 1022u || ex == 1023u) return log(x);
+  if (ex == 0u || ex >= 2047u || ex == 1022u || ex == 1023u) return log_slow(x);
   const int k = (int)ex - 1023;
   const int j = (int)((b >> 45) & 127u);
   const unsigned long long mb = (b & 0x000fffffffffffffull) | 0x3ff0000000000000ull;
