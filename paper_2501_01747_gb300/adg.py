@@ -110,7 +110,7 @@ EXPORTS = ["adg_workspace_bytes", "adg_create", "adg_destroy", "adg_set_primitiv
            "adg_set_tuning", "adg_step_unsync", "adg_unsync_delays",
            "adg_set_unsync_wait", "adg_set_unsync_imbalance", "adg_get_aux",
            "adg_part_layout", "adg_step_stage", "adg_part_block", "adg_set_limiter_tuning",
-           "adg_write_states", "adg_read_states", "adg_states_doubles"]
+           "adg_write_states", "adg_read_states", "adg_states_doubles", "adg_step_io"]
 
 
 def lib(path: str | None = None):
@@ -147,6 +147,7 @@ def lib(path: str | None = None):
     L.adg_write_states.argtypes = [vp, d, vp]
     L.adg_read_states.argtypes = [vp, d, vp]
     L.adg_states_doubles.argtypes = [vp]
+    L.adg_step_io.argtypes = [vp, d, d, vp]
     L.adg_states_doubles.restype = C.c_int64
     L.adg_enable_kernel_timing.argtypes = [vp, C.c_int]
     L.adg_kernel_times.argtypes = [vp, d, C.POINTER(C.c_int64)]
@@ -430,6 +431,14 @@ class ADG:
         """adg_read_states: every instance's state into one host buffer."""
         _check(self.L.adg_read_states(self.h, _dp(w_host), self._stream(stream)),
                "adg_read_states")
+
+    def step_io(self, w_in_host, w_out_host, stream=None):
+        """adg_step_io: every instance's state from w_in_host, one step, the
+        results into w_out_host (both in write_states' layout), with each
+        group's copies overlapped with the other groups' stages when the
+        buffers are mapped pinned memory."""
+        _check(self.L.adg_step_io(self.h, _dp(w_in_host), _dp(w_out_host), self._stream(stream)),
+               "adg_step_io")
 
     def enable_kernel_timing(self, on=True):
         _check(self.L.adg_enable_kernel_timing(self.h, 1 if on else 0), "timing")

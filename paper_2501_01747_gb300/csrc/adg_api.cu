@@ -233,6 +233,8 @@ struct Group {
   int2 *d_tiles = nullptr;      // (instance, first element) per stage CTA
   int2 *d_blocks = nullptr;     // (instance, first element) per limiter CTA
   bool any_limiter = false;
+  int mem0 = 0, nmem = 0;       // the group's instances: d_members[mem0 .. mem0 + nmem)
+  int moff0 = 0;                // and their prefix counts: d_moffs[moff0 .. moff0 + nmem]
 };
 
 struct adg_ctx {
@@ -254,6 +256,8 @@ struct adg_ctx {
   int n_groups;
   Inst *d_insts;                 // device instance table
   int64_t *d_offs;               // [n_inst + 1] first double of each state in a flat buffer
+  int *d_members;                // [n_inst] instances of each group, group after group
+  int64_t *d_moffs;              // per group [nmem + 1] doubles of its members before each
   int64_t *d_steps;              // device step counters [n_inst]
   void *mem;
   bool owns_mem;
@@ -274,6 +278,14 @@ struct adg_ctx {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   bool graph_ok;
+  // adg_step_io: the step with every group's state copies, for one pair of
+  // mapped host buffers; the copies in run one group after another on io_stream
+  cudaStream_t io_stream;
+  cudaEvent_t io_ev[ADG_MAX_GROUPS];
+  cudaGraph_t io_graph;
+  cudaGraphExec_t io_exec;
+  const double *io_in;
+  double *io_out;
 };
 
 // The streams and events of the concurrent branches (those created).
@@ -453,6 +465,8 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
   ctx->d_insts = (Inst *)cv.take(sizeof(Inst) * ctx->n_inst);
   ctx->d_steps = (int64_t *)cv.take(sizeof(int64_t) * ctx->n_inst);
   ctx->d_offs = (int64_t *)cv.take(sizeof(int64_t) * (ctx->n_inst + 1));
+  ctx->d_members = (int *)cv.take(sizeof(int) * ctx->n_inst);
+  ctx->d_moffs = (int64_t *)cv.take(sizeof(int64_t) * (ctx->n_inst + ADG_MAX_GROUPS));
   int max_pe = 1;
   for (int k = 0; k < ctx->n_inst; ++k) max_pe = cfgs[k].n_pe > max_pe ? cfgs[k].n_pe : max_pe;
   ctx->pub_in = (int *)cv.take(sizeof(int) * max_pe);
@@ -694,6 +708,12 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs_in, int n, void
   ctx->graph = nullptr;
   ctx->exec = nullptr;
   ctx->graph_ok = false;
+  ctx->io_stream = nullptr;
+  for (int g = 0; g < ADG_MAX_GROUPS; ++g) ctx->io_ev[g] = nullptr;
+  ctx->io_graph = nullptr;
+  ctx->io_exec = nullptr;
+  ctx->io_in = nullptr;
+  ctx->io_out = nullptr;
   Carver dry{nullptr, 0, 0, true};
   size_t need = layout(ctx, cfgs, dry) + 256;
   if (workspace) {
@@ -837,6 +857,28 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs_in, int n, void
         cudaMemcpy(ctx->d_offs, offs.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice) ||
         cudaMemset(ctx->d_steps, 0, sizeof(int64_t) * n))
       rc2 = ADG_ERR_CUDA;
+    // each group's instances and their prefix counts (adg_step_io's copies)
+    std::vector<int> mem;
+    std::vector<int64_t> moff;
+    for (int gi = 0; gi < ctx->n_groups; ++gi) {
+      Group &G = ctx->groups[gi];
+      G.mem0 = (int)mem.size();
+      G.moff0 = (int)moff.size();
+      moff.push_back(0);
+      for (int k = 0; k < n; ++k)
+        if (cfgs[k].p + 1 == G.Q && cfgs[k].precision == G.prec &&
+            rk_stages(cfgs[k].integrator) == G.S) {
+          mem.push_back(k);
+          moff.push_back(moff.back() + (offs[k + 1] - offs[k]));
+        }
+      G.nmem = (int)mem.size() - G.mem0;
+    }
+    if (rc2 == ADG_OK &&
+        ((int)mem.size() != n ||
+         cudaMemcpy(ctx->d_members, mem.data(), sizeof(int) * n, cudaMemcpyHostToDevice) ||
+         cudaMemcpy(ctx->d_moffs, moff.data(), sizeof(int64_t) * moff.size(),
+                    cudaMemcpyHostToDevice)))
+      rc2 = ADG_ERR_CUDA;
     for (int gi = 0; gi < ctx->n_groups && rc2 == ADG_OK; ++gi) {
       Group &G = ctx->groups[gi];
       if (upload_tiles(ctx, G) != cudaSuccess || upload_blocks(ctx, G) != cudaSuccess)
@@ -874,6 +916,11 @@ void adg_destroy(adg_ctx *ctx) {
     if (e) cudaEventDestroy(e);
   if (ctx->tgraph) cudaGraphDestroy(ctx->tgraph);
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  if (ctx->io_exec) cudaGraphExecDestroy(ctx->io_exec);
+  if (ctx->io_graph) cudaGraphDestroy(ctx->io_graph);
+  for (cudaEvent_t e : ctx->io_ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->io_stream) cudaStreamDestroy(ctx->io_stream);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   destroy_branches(ctx);
   if (ctx->owns_mem) cudaFree(ctx->mem);
@@ -1192,6 +1239,10 @@ static void drop_graphs(adg_ctx *ctx) {
   ctx->exec = ctx->texec = nullptr;
   ctx->graph = ctx->tgraph = nullptr;
   ctx->graph_ok = false;
+  if (ctx->io_exec) cudaGraphExecDestroy(ctx->io_exec);
+  if (ctx->io_graph) cudaGraphDestroy(ctx->io_graph);
+  ctx->io_exec = nullptr;
+  ctx->io_graph = nullptr;
 }
 
 // The limiter's elements per CTA for one group: times a limiter launch of stage
@@ -1525,6 +1576,86 @@ int adg_read_states(adg_ctx *ctx, double *w, void *stream) {
     w += n;
   }
   ctx->last_stream = (cudaStream_t)stream;
+  return ADG_OK;
+}
+
+// The step with its state copies as one graph (adg_step_io). The copies in run
+// one group after another on io_stream; each group's stages start as soon as
+// its own states are in (its branch waits on io_ev[g]) and its states go out at
+// the end of its branch, so the copies of one group overlap the stages of the
+// others. Every instance still reads only its own new input and is read only
+// after its own step, as in adg_write_states + adg_step + adg_read_states.
+static int capture_io(adg_ctx *ctx, double *din, double *dout) {
+  if (ctx->io_exec) cudaGraphExecDestroy(ctx->io_exec);
+  if (ctx->io_graph) cudaGraphDestroy(ctx->io_graph);
+  ctx->io_exec = nullptr;
+  ctx->io_graph = nullptr;
+  if (!ctx->io_stream) CK(cudaStreamCreateWithFlags(&ctx->io_stream, cudaStreamNonBlocking));
+  for (int g = 0; g < ctx->n_groups; ++g)
+    if (!ctx->io_ev[g]) CK(cudaEventCreateWithFlags(&ctx->io_ev[g], cudaEventDisableTiming));
+  cudaStream_t st = ctx->cap_stream;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = ADG_OK;
+  cudaError_t e = cudaEventRecord(ctx->fork_ev, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->io_stream, ctx->fork_ev, 0);
+  for (int g = 0; g < ctx->n_groups && e == cudaSuccess; ++g) {
+    const Group &G = ctx->groups[g];
+    e = launch_group_states_copy(ctx->d_insts, ctx->d_offs, ctx->d_members + G.mem0,
+                                 ctx->d_moffs + G.moff0, G.nmem, din, false, ctx->io_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->io_ev[g], ctx->io_stream);
+  }
+  for (int g = 0; g < ctx->n_groups && e == cudaSuccess && rc == ADG_OK; ++g) {
+    const Group &G = ctx->groups[g];
+    cudaStream_t b = ctx->branch[g];
+    e = cudaStreamWaitEvent(b, ctx->io_ev[g], 0);
+    for (int s = 0; s < G.S && e == cudaSuccess && rc == ADG_OK; ++s) rc = enqueue_group(ctx, g, s, b);
+    if (e == cudaSuccess && rc == ADG_OK)
+      e = launch_group_states_copy(ctx->d_insts, ctx->d_offs, ctx->d_members + G.mem0,
+                                   ctx->d_moffs + G.moff0, G.nmem, dout, true, b);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->join_ev[g], b);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[g], 0);
+  }
+  // the copy stream joins the capture through its last event
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->io_ev[ctx->n_groups - 1], 0);
+  if (e == cudaSuccess) e = launch_advance(ctx->d_steps, ctx->n_inst, st);
+  cudaGraph_t gr = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+  if (rc != ADG_OK || e != cudaSuccess || e2 != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    if (rc != ADG_OK) return rc;
+    return cuda_fail(e != cudaSuccess ? e : e2);
+  }
+  e = cudaGraphInstantiate(&ctx->io_exec, gr, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(gr);
+    ctx->io_exec = nullptr;
+    return cuda_fail(e);
+  }
+  ctx->io_graph = gr;
+  ctx->io_in = din;
+  ctx->io_out = dout;
+  return ADG_OK;
+}
+
+int adg_step_io(adg_ctx *ctx, const double *w_in, double *w_out, void *stream) {
+  if (!ctx || !w_in || !w_out) return ADG_ERR_ARG;
+  double *din = mapped_host(w_in), *dout = mapped_host(w_out);
+  if (!din || !dout || ctx->timing || ctx->n_groups < 2 || !ctx->fork_ev) {
+    // one group (nothing to overlap), pageable buffers or kernel timing: the
+    // three calls one after the other
+    int rc = adg_write_states(ctx, w_in, stream);
+    if (rc == ADG_OK) rc = adg_step(ctx, 1, stream);
+    if (rc == ADG_OK) rc = adg_read_states(ctx, w_out, stream);
+    return rc;
+  }
+  if (!ctx->io_exec || ctx->io_in != din || ctx->io_out != dout) {
+    int rc = capture_io(ctx, din, dout);
+    if (rc != ADG_OK) return rc;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  CK(cudaGraphLaunch(ctx->io_exec, st));
+  for (InstHost &h : ctx->inst) h.n += 1;
   return ADG_OK;
 }
 
