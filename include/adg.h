@@ -208,12 +208,13 @@ int64_t adg_states_doubles(const adg_ctx *ctx);
 /* One time step (Sec. 3.1, Eq. 5; the step of adg_step) of every instance
  * from new host states to host results: the same as adg_write_states(w_in),
  * adg_step(1) and adg_read_states(w_out) on `stream`, with the same results to
- * the bit, but with each group's copies overlapped with other groups' stages
- * (the instances of one degree and precision form a group and share the stage
- * and limiter launches). The copies in run group after group; a group's stages
- * start once its own states are in, and its states go out when its own step
- * ends. w_in and w_out: pinned host buffers mapped into the device's address
- * space, in adg_write_states' layout (adg_states_doubles long each), valid
+ * the bit, but with the copies overlapped with the stages (the instances of one
+ * degree and precision form a group and share the stage and limiter
+ * launches). The copies in run group after group, one copy per instance on
+ * the copy engines; the groups step one after another, each once its own
+ * states are in, and a group's states go out while the next group steps.
+ * w_in and w_out: pinned host buffers (cudaHostAlloc or cudaHostRegister
+ * memory) in adg_write_states' layout, adg_states_doubles long each, valid
  * until the stream passes the step; they may be the same buffer only if the
  * caller does not need w_in afterwards. The first call for a pair of buffers
  * captures a CUDA graph for it (later calls with the same pair replay it; a

@@ -233,8 +233,7 @@ struct Group {
   int2 *d_tiles = nullptr;      // (instance, first element) per stage CTA
   int2 *d_blocks = nullptr;     // (instance, first element) per limiter CTA
   bool any_limiter = false;
-  int mem0 = 0, nmem = 0;       // the group's instances: d_members[mem0 .. mem0 + nmem)
-  int moff0 = 0;                // and their prefix counts: d_moffs[moff0 .. moff0 + nmem]
+  std::vector<int> members;     // the group's instances (adg_step_io's copies)
 };
 
 struct adg_ctx {
@@ -256,8 +255,6 @@ struct adg_ctx {
   int n_groups;
   Inst *d_insts;                 // device instance table
   int64_t *d_offs;               // [n_inst + 1] first double of each state in a flat buffer
-  int *d_members;                // [n_inst] instances of each group, group after group
-  int64_t *d_moffs;              // per group [nmem + 1] doubles of its members before each
   int64_t *d_steps;              // device step counters [n_inst]
   void *mem;
   bool owns_mem;
@@ -279,9 +276,11 @@ struct adg_ctx {
   cudaGraphExec_t exec;
   bool graph_ok;
   // adg_step_io: the step with every group's state copies, for one pair of
-  // mapped host buffers; the copies in run one group after another on io_stream
+  // pinned host buffers; the copies in run one group after another on
+  // io_stream (io_ev[g]: group g's states are in), and the groups' stages one
+  // group after another (done_ev[g]: group g's stages are done)
   cudaStream_t io_stream;
-  cudaEvent_t io_ev[ADG_MAX_GROUPS];
+  cudaEvent_t io_ev[ADG_MAX_GROUPS], done_ev[ADG_MAX_GROUPS];
   cudaGraph_t io_graph;
   cudaGraphExec_t io_exec;
   const double *io_in;
@@ -465,8 +464,6 @@ size_t layout(adg_ctx *ctx, const adg_config *cfgs, Carver &cv) {
   ctx->d_insts = (Inst *)cv.take(sizeof(Inst) * ctx->n_inst);
   ctx->d_steps = (int64_t *)cv.take(sizeof(int64_t) * ctx->n_inst);
   ctx->d_offs = (int64_t *)cv.take(sizeof(int64_t) * (ctx->n_inst + 1));
-  ctx->d_members = (int *)cv.take(sizeof(int) * ctx->n_inst);
-  ctx->d_moffs = (int64_t *)cv.take(sizeof(int64_t) * (ctx->n_inst + ADG_MAX_GROUPS));
   int max_pe = 1;
   for (int k = 0; k < ctx->n_inst; ++k) max_pe = cfgs[k].n_pe > max_pe ? cfgs[k].n_pe : max_pe;
   ctx->pub_in = (int *)cv.take(sizeof(int) * max_pe);
@@ -709,7 +706,7 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs_in, int n, void
   ctx->exec = nullptr;
   ctx->graph_ok = false;
   ctx->io_stream = nullptr;
-  for (int g = 0; g < ADG_MAX_GROUPS; ++g) ctx->io_ev[g] = nullptr;
+  for (int g = 0; g < ADG_MAX_GROUPS; ++g) ctx->io_ev[g] = ctx->done_ev[g] = nullptr;
   ctx->io_graph = nullptr;
   ctx->io_exec = nullptr;
   ctx->io_in = nullptr;
@@ -857,28 +854,15 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs_in, int n, void
         cudaMemcpy(ctx->d_offs, offs.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice) ||
         cudaMemset(ctx->d_steps, 0, sizeof(int64_t) * n))
       rc2 = ADG_ERR_CUDA;
-    // each group's instances and their prefix counts (adg_step_io's copies)
-    std::vector<int> mem;
-    std::vector<int64_t> moff;
+    // each group's instances (adg_step_io's copies)
     for (int gi = 0; gi < ctx->n_groups; ++gi) {
       Group &G = ctx->groups[gi];
-      G.mem0 = (int)mem.size();
-      G.moff0 = (int)moff.size();
-      moff.push_back(0);
+      G.members.clear();
       for (int k = 0; k < n; ++k)
         if (cfgs[k].p + 1 == G.Q && cfgs[k].precision == G.prec &&
-            rk_stages(cfgs[k].integrator) == G.S) {
-          mem.push_back(k);
-          moff.push_back(moff.back() + (offs[k + 1] - offs[k]));
-        }
-      G.nmem = (int)mem.size() - G.mem0;
+            rk_stages(cfgs[k].integrator) == G.S)
+          G.members.push_back(k);
     }
-    if (rc2 == ADG_OK &&
-        ((int)mem.size() != n ||
-         cudaMemcpy(ctx->d_members, mem.data(), sizeof(int) * n, cudaMemcpyHostToDevice) ||
-         cudaMemcpy(ctx->d_moffs, moff.data(), sizeof(int64_t) * moff.size(),
-                    cudaMemcpyHostToDevice)))
-      rc2 = ADG_ERR_CUDA;
     for (int gi = 0; gi < ctx->n_groups && rc2 == ADG_OK; ++gi) {
       Group &G = ctx->groups[gi];
       if (upload_tiles(ctx, G) != cudaSuccess || upload_blocks(ctx, G) != cudaSuccess)
@@ -918,8 +902,10 @@ void adg_destroy(adg_ctx *ctx) {
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   if (ctx->io_exec) cudaGraphExecDestroy(ctx->io_exec);
   if (ctx->io_graph) cudaGraphDestroy(ctx->io_graph);
-  for (cudaEvent_t e : ctx->io_ev)
-    if (e) cudaEventDestroy(e);
+  for (int g = 0; g < ADG_MAX_GROUPS; ++g) {
+    if (ctx->io_ev[g]) cudaEventDestroy(ctx->io_ev[g]);
+    if (ctx->done_ev[g]) cudaEventDestroy(ctx->done_ev[g]);
+  }
   if (ctx->io_stream) cudaStreamDestroy(ctx->io_stream);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   destroy_branches(ctx);
@@ -1580,38 +1566,51 @@ int adg_read_states(adg_ctx *ctx, double *w, void *stream) {
 }
 
 // The step with its state copies as one graph (adg_step_io). The copies in run
-// one group after another on io_stream; each group's stages start as soon as
-// its own states are in (its branch waits on io_ev[g]) and its states go out at
-// the end of its branch, so the copies of one group overlap the stages of the
-// others. Every instance still reads only its own new input and is read only
-// after its own step, as in adg_write_states + adg_step + adg_read_states.
-static int capture_io(adg_ctx *ctx, double *din, double *dout) {
+// group after group on io_stream, one copy per instance on the copy engines
+// (kernels over the mapped buffers would take SM slots from the stage kernels);
+// the groups' stages run one group after another, each once its own states are
+// in, and each group's states go out at the end of its branch while the next
+// group computes. Every instance still reads only its own new input and is read
+// only after its own step, as in adg_write_states + adg_step + adg_read_states.
+static int capture_io(adg_ctx *ctx, const double *w_in, double *w_out) {
   if (ctx->io_exec) cudaGraphExecDestroy(ctx->io_exec);
   if (ctx->io_graph) cudaGraphDestroy(ctx->io_graph);
   ctx->io_exec = nullptr;
   ctx->io_graph = nullptr;
   if (!ctx->io_stream) CK(cudaStreamCreateWithFlags(&ctx->io_stream, cudaStreamNonBlocking));
-  for (int g = 0; g < ctx->n_groups; ++g)
+  for (int g = 0; g < ctx->n_groups; ++g) {
     if (!ctx->io_ev[g]) CK(cudaEventCreateWithFlags(&ctx->io_ev[g], cudaEventDisableTiming));
+    if (!ctx->done_ev[g]) CK(cudaEventCreateWithFlags(&ctx->done_ev[g], cudaEventDisableTiming));
+  }
+  // the first double of each instance's state in the host buffers
+  std::vector<int64_t> offs(ctx->n_inst + 1, 0);
+  for (int k = 0; k < ctx->n_inst; ++k) {
+    const Inst &I = ctx->inst[k].d;
+    offs[k + 1] = offs[k] + (int64_t)I.nv * I.n_elem * (I.p + 1);
+  }
+  auto bytes = [&](int k) { return sizeof(double) * (size_t)(offs[k + 1] - offs[k]); };
   cudaStream_t st = ctx->cap_stream;
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   int rc = ADG_OK;
   cudaError_t e = cudaEventRecord(ctx->fork_ev, st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->io_stream, ctx->fork_ev, 0);
   for (int g = 0; g < ctx->n_groups && e == cudaSuccess; ++g) {
-    const Group &G = ctx->groups[g];
-    e = launch_group_states_copy(ctx->d_insts, ctx->d_offs, ctx->d_members + G.mem0,
-                                 ctx->d_moffs + G.moff0, G.nmem, din, false, ctx->io_stream);
+    for (int k : ctx->groups[g].members)
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->inst[k].d.wn, w_in + offs[k], bytes(k), cudaMemcpyHostToDevice,
+                            ctx->io_stream);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->io_ev[g], ctx->io_stream);
   }
   for (int g = 0; g < ctx->n_groups && e == cudaSuccess && rc == ADG_OK; ++g) {
     const Group &G = ctx->groups[g];
     cudaStream_t b = ctx->branch[g];
     e = cudaStreamWaitEvent(b, ctx->io_ev[g], 0);
+    if (e == cudaSuccess && g > 0) e = cudaStreamWaitEvent(b, ctx->done_ev[g - 1], 0);
     for (int s = 0; s < G.S && e == cudaSuccess && rc == ADG_OK; ++s) rc = enqueue_group(ctx, g, s, b);
-    if (e == cudaSuccess && rc == ADG_OK)
-      e = launch_group_states_copy(ctx->d_insts, ctx->d_offs, ctx->d_members + G.mem0,
-                                   ctx->d_moffs + G.moff0, G.nmem, dout, true, b);
+    if (e == cudaSuccess && rc == ADG_OK) e = cudaEventRecord(ctx->done_ev[g], b);
+    for (int k : G.members)
+      if (e == cudaSuccess && rc == ADG_OK)
+        e = cudaMemcpyAsync(w_out + offs[k], ctx->inst[k].d.wn, bytes(k), cudaMemcpyDeviceToHost, b);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->join_ev[g], b);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[g], 0);
   }
@@ -1632,15 +1631,16 @@ static int capture_io(adg_ctx *ctx, double *din, double *dout) {
     return cuda_fail(e);
   }
   ctx->io_graph = gr;
-  ctx->io_in = din;
-  ctx->io_out = dout;
+  ctx->io_in = w_in;
+  ctx->io_out = w_out;
   return ADG_OK;
 }
 
 int adg_step_io(adg_ctx *ctx, const double *w_in, double *w_out, void *stream) {
   if (!ctx || !w_in || !w_out) return ADG_ERR_ARG;
-  double *din = mapped_host(w_in), *dout = mapped_host(w_out);
-  if (!din || !dout || ctx->timing || ctx->n_groups < 2 || !ctx->fork_ev) {
+  // pinned host memory (the graph's copies need it), seen through its mapping
+  const bool pinned = mapped_host(w_in) && mapped_host(w_out);
+  if (!pinned || ctx->timing || ctx->n_groups < 2 || !ctx->fork_ev) {
     // one group (nothing to overlap), pageable buffers or kernel timing: the
     // three calls one after the other
     int rc = adg_write_states(ctx, w_in, stream);
@@ -1648,8 +1648,8 @@ int adg_step_io(adg_ctx *ctx, const double *w_in, double *w_out, void *stream) {
     if (rc == ADG_OK) rc = adg_read_states(ctx, w_out, stream);
     return rc;
   }
-  if (!ctx->io_exec || ctx->io_in != din || ctx->io_out != dout) {
-    int rc = capture_io(ctx, din, dout);
+  if (!ctx->io_exec || ctx->io_in != w_in || ctx->io_out != w_out) {
+    int rc = capture_io(ctx, w_in, w_out);
     if (rc != ADG_OK) return rc;
   }
   cudaStream_t st = (cudaStream_t)stream;

@@ -388,9 +388,6 @@ cudaError_t launch_part_import(const Inst *inst, int what, int side, int stage,
 // in it, offs[n] the total.
 cudaError_t launch_states_copy(const Inst *insts, const int64_t *offs, int n, double *host,
                                bool to_host, cudaStream_t st);
-cudaError_t launch_group_states_copy(const Inst *insts, const int64_t *offs, const int *members,
-                                     const int64_t *moffs, int nm, double *host, bool to_host,
-                                     cudaStream_t st);
 cudaError_t launch_aux(const LimArgs &A, int Q, int n_blocks, cudaStream_t st);
 // per-variant units (adg_k64.cu, adg_k32.cu, adg_k32f.cu)
 cudaError_t launch_stage_fp64(const Mech &M, const StageArgs &A, int Q, int n_tiles,

@@ -332,63 +332,6 @@ cudaError_t launch_states_copy(const Inst *insts, const int64_t *offs, int n, do
   return cudaGetLastError();
 }
 
-// The states of one group's instances, members[0 .. nm), between the device
-// and a flat host buffer laid out like adg_write_states' (offs: the context's
-// offsets of every instance). moffs[m] counts the group's doubles before member
-// m, so item i of the group belongs to the member m with moffs[m] <= i <
-// moffs[m + 1]. adg_step_io runs these copies beside other groups' stage
-// kernels, so the grid is small (two CTAs per SM) with four accesses in flight
-// per thread: the host link, not the SMs, bounds the copy.
-__global__ void group_states_copy_kernel(const Inst *insts, const int64_t *offs,
-                                         const int *members, const int64_t *moffs, int nm,
-                                         double *host, int to_host) {
-  constexpr int U = 4;
-  const int64_t total = moffs[nm];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; base < total;
-       base += U * stride) {
-    double *dev[U], *hp[U], v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t i = base + u * stride;
-      dev[u] = nullptr;
-      hp[u] = nullptr;
-      if (i < total) {
-        int lo = 0, hi = nm - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (moffs[mid] <= i) lo = mid;
-          else hi = mid - 1;
-        }
-        const int k = members[lo];
-        const int64_t r = i - moffs[lo];
-        dev[u] = insts[k].wn + r;
-        hp[u] = host + offs[k] + r;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (dev[u]) v[u] = to_host ? *dev[u] : *hp[u];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (dev[u]) {
-        if (to_host) *hp[u] = v[u];
-        else *dev[u] = v[u];
-      }
-  }
-}
-
-cudaError_t launch_group_states_copy(const Inst *insts, const int64_t *offs, const int *members,
-                                     const int64_t *moffs, int nm, double *host, bool to_host,
-                                     cudaStream_t st) {
-  int dev = 0, n_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  group_states_copy_kernel<<<2 * n_sm, 256, 0, st>>>(insts, offs, members, moffs, nm, host,
-                                                       to_host ? 1 : 0);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_advance(int64_t *steps, int n, cudaStream_t st) {
   return launch_pdl(advance_kernel, dim3((n + 127) / 128), dim3(128), 0, st, steps, n);
 }
