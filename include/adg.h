@@ -210,9 +210,10 @@ int64_t adg_states_doubles(const adg_ctx *ctx);
  * adg_step(1) and adg_read_states(w_out) on `stream`, with the same results to
  * the bit, but with the copies overlapped with the stages (the instances of one
  * degree and precision form a group and share the stage and limiter
- * launches). The copies in run group after group, one copy per instance on
- * the copy engines; the groups step one after another, each once its own
- * states are in, and a group's states go out while the next group steps.
+ * launches; each group without viscous terms is cut into two parts of its
+ * instances). The copies in run part after part, one copy per instance on the
+ * copy engines; the parts step one after another, each once its own states
+ * are in, and a part's states go out while the next part steps.
  * w_in and w_out: pinned host buffers (cudaHostAlloc or cudaHostRegister
  * memory) in adg_write_states' layout, adg_states_doubles long each, valid
  * until the stream passes the step; they may be the same buffer only if the

@@ -275,12 +275,13 @@ struct adg_ctx {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   bool graph_ok;
-  // adg_step_io: the step with every group's state copies, for one pair of
-  // pinned host buffers; the copies in run one group after another on
-  // io_stream (io_ev[g]: group g's states are in), and the groups' stages one
-  // group after another (done_ev[g]: group g's stages are done)
-  cudaStream_t io_stream;
-  cudaEvent_t io_ev[ADG_MAX_GROUPS], done_ev[ADG_MAX_GROUPS];
+  // adg_step_io: the step with every state copy, for one pair of pinned host
+  // buffers, in parts of up to two per group: the copies in run part after part
+  // on io_stream (io_ev[j]: part j's states are in), the parts' stages one after
+  // another on the capture stream (done_ev[j]: part j's step is done), the
+  // copies out on out_stream
+  cudaStream_t io_stream, out_stream;
+  cudaEvent_t io_ev[2 * ADG_MAX_GROUPS], done_ev[2 * ADG_MAX_GROUPS];
   cudaGraph_t io_graph;
   cudaGraphExec_t io_exec;
   const double *io_in;
@@ -705,8 +706,8 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs_in, int n, void
   ctx->graph = nullptr;
   ctx->exec = nullptr;
   ctx->graph_ok = false;
-  ctx->io_stream = nullptr;
-  for (int g = 0; g < ADG_MAX_GROUPS; ++g) ctx->io_ev[g] = ctx->done_ev[g] = nullptr;
+  ctx->io_stream = ctx->out_stream = nullptr;
+  for (int j = 0; j < 2 * ADG_MAX_GROUPS; ++j) ctx->io_ev[j] = ctx->done_ev[j] = nullptr;
   ctx->io_graph = nullptr;
   ctx->io_exec = nullptr;
   ctx->io_in = nullptr;
@@ -902,11 +903,12 @@ void adg_destroy(adg_ctx *ctx) {
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   if (ctx->io_exec) cudaGraphExecDestroy(ctx->io_exec);
   if (ctx->io_graph) cudaGraphDestroy(ctx->io_graph);
-  for (int g = 0; g < ADG_MAX_GROUPS; ++g) {
-    if (ctx->io_ev[g]) cudaEventDestroy(ctx->io_ev[g]);
-    if (ctx->done_ev[g]) cudaEventDestroy(ctx->done_ev[g]);
+  for (int j = 0; j < 2 * ADG_MAX_GROUPS; ++j) {
+    if (ctx->io_ev[j]) cudaEventDestroy(ctx->io_ev[j]);
+    if (ctx->done_ev[j]) cudaEventDestroy(ctx->done_ev[j]);
   }
   if (ctx->io_stream) cudaStreamDestroy(ctx->io_stream);
+  if (ctx->out_stream) cudaStreamDestroy(ctx->out_stream);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   destroy_branches(ctx);
   if (ctx->owns_mem) cudaFree(ctx->mem);
@@ -1011,16 +1013,28 @@ static LimArgs aux_args(const adg_ctx *ctx, const Group &G, int s) {
   return L;
 }
 
+// A part of a group's launches: stage tiles [tile0, tile0 + n_tiles) and
+// limiter blocks [blk0, blk0 + n_blocks) of its tables (n_tiles < 0: all).
+// Tiles and blocks never span instances, so the instances of a part step
+// independently of the rest of the group.
+struct Part {
+  int tile0 = 0, n_tiles = -1, blk0 = 0, n_blocks = -1;
+};
+
 // The stages of one group's step: per RK stage, the auxiliary kernel (viscous
 // groups), the stage kernel and the limiter; half 0 only the first two, half 1
-// only the limiter, any other value all three.
-static int enqueue_group(adg_ctx *ctx, int gi, int s, cudaStream_t st, int half = -1) {
+// only the limiter, any other value all three. `part` limits the launches to a
+// range of the group's instances (inviscid groups only).
+static int enqueue_group(adg_ctx *ctx, int gi, int s, cudaStream_t st, int half = -1,
+                         Part part = Part()) {
   const Group &G = ctx->groups[gi];
   if (s >= G.S) return ADG_OK;
+  const int n_tiles = part.n_tiles < 0 ? G.n_tiles : part.n_tiles;
+  const int n_blocks = part.n_tiles < 0 ? G.n_blocks : part.n_blocks;
   if (half != 1) {
     StageArgs A;
     A.insts = ctx->d_insts;
-    A.tiles = G.d_tiles;
+    A.tiles = G.d_tiles + part.tile0;
     A.s = s;
     A.TE = G.TE;
     A.NT = G.NT;
@@ -1030,17 +1044,17 @@ static int enqueue_group(adg_ctx *ctx, int gi, int s, cudaStream_t st, int half 
     // viscous groups: the LDG auxiliary variable of the stage input first
     // (timed with the stage kernel)
     if (G.visc) CK(launch_aux(aux_args(ctx, G, s), G.Q, G.n_blocks, st));
-    CK(launch_stage(ctx->mech, A, G.Q, G.prec, G.n_tiles, st));
+    CK(launch_stage(ctx->mech, A, G.Q, G.prec, n_tiles, st));
     CK(timed_end(ctx, st));
   }
   if (half == 0 || !G.any_limiter) return ADG_OK;
   LimArgs L;
   L.insts = ctx->d_insts;
-  L.blocks = G.d_blocks;
+  L.blocks = G.d_blocks + part.blk0;
   L.s = s;
   L.EPB = G.EPB;
   CK(timed_begin(ctx, 1, st));
-  CK(launch_limiter(ctx->mech, L, G.Q, G.mixed, ctx->ns + 2, G.n_blocks, st));
+  CK(launch_limiter(ctx->mech, L, G.Q, G.mixed, ctx->ns + 2, n_blocks, st));
   CK(timed_end(ctx, st));
   return ADG_OK;
 }
@@ -1565,23 +1579,24 @@ int adg_read_states(adg_ctx *ctx, double *w, void *stream) {
   return ADG_OK;
 }
 
-// The step with its state copies as one graph (adg_step_io). The copies in run
-// group after group on io_stream, one copy per instance on the copy engines
-// (kernels over the mapped buffers would take SM slots from the stage kernels);
-// the groups' stages run one group after another, each once its own states are
-// in, and each group's states go out at the end of its branch while the next
-// group computes. Every instance still reads only its own new input and is read
-// only after its own step, as in adg_write_states + adg_step + adg_read_states.
+// The step with its state copies as one graph (adg_step_io). Each inviscid
+// group is cut into two parts of about equal bytes (its instances in order;
+// tiles and limiter blocks never span instances), so the first part's copies
+// in and the last part's copies out, the only copies no stage hides, are half a
+// group's. The copies in run part after part on io_stream, one copy per
+// instance on the copy engines (kernels over the mapped buffers would take SM
+// slots from the stage kernels); the parts step one after another on the
+// capture stream, each once its own states are in; each part's states go out
+// on out_stream while the next part steps. Every instance still reads only its
+// own new input and is read only after its own step, as in adg_write_states +
+// adg_step + adg_read_states.
 static int capture_io(adg_ctx *ctx, const double *w_in, double *w_out) {
   if (ctx->io_exec) cudaGraphExecDestroy(ctx->io_exec);
   if (ctx->io_graph) cudaGraphDestroy(ctx->io_graph);
   ctx->io_exec = nullptr;
   ctx->io_graph = nullptr;
   if (!ctx->io_stream) CK(cudaStreamCreateWithFlags(&ctx->io_stream, cudaStreamNonBlocking));
-  for (int g = 0; g < ctx->n_groups; ++g) {
-    if (!ctx->io_ev[g]) CK(cudaEventCreateWithFlags(&ctx->io_ev[g], cudaEventDisableTiming));
-    if (!ctx->done_ev[g]) CK(cudaEventCreateWithFlags(&ctx->done_ev[g], cudaEventDisableTiming));
-  }
+  if (!ctx->out_stream) CK(cudaStreamCreateWithFlags(&ctx->out_stream, cudaStreamNonBlocking));
   // the first double of each instance's state in the host buffers
   std::vector<int64_t> offs(ctx->n_inst + 1, 0);
   for (int k = 0; k < ctx->n_inst; ++k) {
@@ -1589,34 +1604,87 @@ static int capture_io(adg_ctx *ctx, const double *w_in, double *w_out) {
     offs[k + 1] = offs[k] + (int64_t)I.nv * I.n_elem * (I.p + 1);
   }
   auto bytes = [&](int k) { return sizeof(double) * (size_t)(offs[k + 1] - offs[k]); };
+  // the parts: (group, members [m0, m1), tile and block ranges)
+  struct IoPart {
+    int g, m0, m1;
+    Part r;
+  };
+  std::vector<IoPart> parts;
+  for (int g = 0; g < ctx->n_groups; ++g) {
+    const Group &G = ctx->groups[g];
+    const int nm = (int)G.members.size();
+    int cut = nm;
+    if (!G.visc && nm > 1) {
+      int64_t tot = 0, acc = 0;
+      for (int k : G.members) tot += offs[k + 1] - offs[k];
+      cut = 0;
+      while (cut < nm - 1 && 2 * acc < tot) {
+        acc += offs[G.members[cut] + 1] - offs[G.members[cut]];
+        ++cut;
+      }
+    }
+    int t0 = 0, b0 = 0;
+    for (int m0 = 0; m0 < nm; m0 = cut, cut = nm) {
+      IoPart P{g, m0, cut, Part()};
+      if (!(m0 == 0 && cut == nm)) {
+        int nt = 0, nb = 0;
+        for (int m = m0; m < cut; ++m) {
+          const int ne = ctx->inst[G.members[m]].d.n_elem;
+          nt += (ne + G.TE - 1) / G.TE;
+          nb += (ne + G.EPB - 1) / G.EPB;
+        }
+        P.r.tile0 = t0;
+        P.r.n_tiles = nt;
+        P.r.blk0 = b0;
+        P.r.n_blocks = nb;
+        t0 += nt;
+        b0 += nb;
+      }
+      parts.push_back(P);
+    }
+    // the parts must cover the group's tables exactly; otherwise one part
+    if (t0 != 0 && (t0 != G.n_tiles || b0 != G.n_blocks)) {
+      while (!parts.empty() && parts.back().g == g) parts.pop_back();
+      parts.push_back(IoPart{g, 0, nm, Part()});
+    }
+  }
+  const int np = (int)parts.size();
+  for (int j = 0; j < np; ++j) {
+    if (!ctx->io_ev[j]) CK(cudaEventCreateWithFlags(&ctx->io_ev[j], cudaEventDisableTiming));
+    if (!ctx->done_ev[j]) CK(cudaEventCreateWithFlags(&ctx->done_ev[j], cudaEventDisableTiming));
+  }
   cudaStream_t st = ctx->cap_stream;
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   int rc = ADG_OK;
   cudaError_t e = cudaEventRecord(ctx->fork_ev, st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->io_stream, ctx->fork_ev, 0);
-  for (int g = 0; g < ctx->n_groups && e == cudaSuccess; ++g) {
-    for (int k : ctx->groups[g].members)
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->inst[k].d.wn, w_in + offs[k], bytes(k), cudaMemcpyHostToDevice,
-                            ctx->io_stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->io_ev[g], ctx->io_stream);
+  for (int j = 0; j < np && e == cudaSuccess; ++j) {
+    const IoPart &P = parts[j];
+    for (int m = P.m0; m < P.m1 && e == cudaSuccess; ++m) {
+      const int k = ctx->groups[P.g].members[m];
+      e = cudaMemcpyAsync(ctx->inst[k].d.wn, w_in + offs[k], bytes(k), cudaMemcpyHostToDevice,
+                          ctx->io_stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->io_ev[j], ctx->io_stream);
   }
-  for (int g = 0; g < ctx->n_groups && e == cudaSuccess && rc == ADG_OK; ++g) {
-    const Group &G = ctx->groups[g];
-    cudaStream_t b = ctx->branch[g];
-    e = cudaStreamWaitEvent(b, ctx->io_ev[g], 0);
-    if (e == cudaSuccess && g > 0) e = cudaStreamWaitEvent(b, ctx->done_ev[g - 1], 0);
-    for (int s = 0; s < G.S && e == cudaSuccess && rc == ADG_OK; ++s) rc = enqueue_group(ctx, g, s, b);
-    if (e == cudaSuccess && rc == ADG_OK) e = cudaEventRecord(ctx->done_ev[g], b);
-    for (int k : G.members)
-      if (e == cudaSuccess && rc == ADG_OK)
-        e = cudaMemcpyAsync(w_out + offs[k], ctx->inst[k].d.wn, bytes(k), cudaMemcpyDeviceToHost, b);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->join_ev[g], b);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[g], 0);
+  for (int j = 0; j < np && e == cudaSuccess && rc == ADG_OK; ++j) {
+    const IoPart &P = parts[j];
+    e = cudaStreamWaitEvent(st, ctx->io_ev[j], 0);
+    for (int s = 0; s < ctx->groups[P.g].S && e == cudaSuccess && rc == ADG_OK; ++s)
+      rc = enqueue_group(ctx, P.g, s, st, -1, P.r);
+    if (e == cudaSuccess && rc == ADG_OK) e = cudaEventRecord(ctx->done_ev[j], st);
+    if (e == cudaSuccess && rc == ADG_OK) e = cudaStreamWaitEvent(ctx->out_stream, ctx->done_ev[j], 0);
+    for (int m = P.m0; m < P.m1 && e == cudaSuccess && rc == ADG_OK; ++m) {
+      const int k = ctx->groups[P.g].members[m];
+      e = cudaMemcpyAsync(w_out + offs[k], ctx->inst[k].d.wn, bytes(k), cudaMemcpyDeviceToHost,
+                          ctx->out_stream);
+    }
   }
-  // the copy stream joins the capture through its last event
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->io_ev[ctx->n_groups - 1], 0);
-  if (e == cudaSuccess) e = launch_advance(ctx->d_steps, ctx->n_inst, st);
+  if (e == cudaSuccess && rc == ADG_OK) e = launch_advance(ctx->d_steps, ctx->n_inst, st);
+  // the copy streams join the capture through their last events
+  if (e == cudaSuccess && rc == ADG_OK) e = cudaEventRecord(ctx->join_ev[0], ctx->out_stream);
+  if (e == cudaSuccess && rc == ADG_OK) e = cudaStreamWaitEvent(st, ctx->join_ev[0], 0);
+  if (e == cudaSuccess && rc == ADG_OK) e = cudaStreamWaitEvent(st, ctx->io_ev[np - 1], 0);
   cudaGraph_t gr = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(st, &gr);
   if (rc != ADG_OK || e != cudaSuccess || e2 != cudaSuccess) {
