@@ -210,8 +210,8 @@ int64_t adg_states_doubles(const adg_ctx *ctx);
  * adg_step(1) and adg_read_states(w_out) on `stream`, with the same results to
  * the bit, but with the copies overlapped with the stages (the instances of one
  * degree and precision form a group and share the stage and limiter
- * launches; each group without viscous terms is cut into two parts of its
- * instances). The copies in run part after part, one copy per instance on the
+ * launches; each group without viscous terms is cut into up to four parts of
+ * its instances). The copies in run part after part, one copy per instance on the
  * copy engines; the parts step one after another, each once its own states
  * are in, and a part's states go out while the next part steps.
  * w_in and w_out: pinned host buffers (cudaHostAlloc or cudaHostRegister

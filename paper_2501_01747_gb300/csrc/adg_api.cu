@@ -236,6 +236,10 @@ struct Group {
   std::vector<int> members;     // the group's instances (adg_step_io's copies)
 };
 
+// Parts per group of adg_step_io's pipeline (at most; groups without viscous
+// terms and with that many instances).
+constexpr int kIoParts = 4;
+
 struct adg_ctx {
   std::vector<cudaEvent_t> ev;   // timing events: a pair around every kernel of one step
   std::vector<int> ev_kind;      // kernel kind of each pair
@@ -276,12 +280,12 @@ struct adg_ctx {
   cudaGraphExec_t exec;
   bool graph_ok;
   // adg_step_io: the step with every state copy, for one pair of pinned host
-  // buffers, in parts of up to two per group: the copies in run part after part
+  // buffers, in parts of up to kIoParts per group: the copies in run part after part
   // on io_stream (io_ev[j]: part j's states are in), the parts' stages one after
   // another on the capture stream (done_ev[j]: part j's step is done), the
   // copies out on out_stream
   cudaStream_t io_stream, out_stream;
-  cudaEvent_t io_ev[2 * ADG_MAX_GROUPS], done_ev[2 * ADG_MAX_GROUPS];
+  cudaEvent_t io_ev[kIoParts * ADG_MAX_GROUPS], done_ev[kIoParts * ADG_MAX_GROUPS];
   cudaGraph_t io_graph;
   cudaGraphExec_t io_exec;
   const double *io_in;
@@ -707,7 +711,7 @@ int adg_create(const adg_mechanism *mech, const adg_config *cfgs_in, int n, void
   ctx->exec = nullptr;
   ctx->graph_ok = false;
   ctx->io_stream = ctx->out_stream = nullptr;
-  for (int j = 0; j < 2 * ADG_MAX_GROUPS; ++j) ctx->io_ev[j] = ctx->done_ev[j] = nullptr;
+  for (int j = 0; j < kIoParts * ADG_MAX_GROUPS; ++j) ctx->io_ev[j] = ctx->done_ev[j] = nullptr;
   ctx->io_graph = nullptr;
   ctx->io_exec = nullptr;
   ctx->io_in = nullptr;
@@ -903,7 +907,7 @@ void adg_destroy(adg_ctx *ctx) {
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   if (ctx->io_exec) cudaGraphExecDestroy(ctx->io_exec);
   if (ctx->io_graph) cudaGraphDestroy(ctx->io_graph);
-  for (int j = 0; j < 2 * ADG_MAX_GROUPS; ++j) {
+  for (int j = 0; j < kIoParts * ADG_MAX_GROUPS; ++j) {
     if (ctx->io_ev[j]) cudaEventDestroy(ctx->io_ev[j]);
     if (ctx->done_ev[j]) cudaEventDestroy(ctx->done_ev[j]);
   }
@@ -1580,10 +1584,10 @@ int adg_read_states(adg_ctx *ctx, double *w, void *stream) {
 }
 
 // The step with its state copies as one graph (adg_step_io). Each inviscid
-// group is cut into two parts of about equal bytes (its instances in order;
-// tiles and limiter blocks never span instances), so the first part's copies
-// in and the last part's copies out, the only copies no stage hides, are half a
-// group's. The copies in run part after part on io_stream, one copy per
+// group is cut into up to kIoParts parts of about equal bytes (its instances
+// in order; tiles and limiter blocks never span instances), so the first
+// part's copies in and the last part's copies out, the only copies no stage
+// hides, are a fraction of a group's. The copies in run part after part on io_stream, one copy per
 // instance on the copy engines (kernels over the mapped buffers would take SM
 // slots from the stage kernels); the parts step one after another on the
 // capture stream, each once its own states are in; each part's states go out
@@ -1613,18 +1617,24 @@ static int capture_io(adg_ctx *ctx, const double *w_in, double *w_out) {
   for (int g = 0; g < ctx->n_groups; ++g) {
     const Group &G = ctx->groups[g];
     const int nm = (int)G.members.size();
-    int cut = nm;
+    // ends of the parts: about equal bytes each, every part non-empty
+    std::vector<int> ends;
     if (!G.visc && nm > 1) {
+      const int P = nm < kIoParts ? nm : kIoParts;
       int64_t tot = 0, acc = 0;
       for (int k : G.members) tot += offs[k + 1] - offs[k];
-      cut = 0;
-      while (cut < nm - 1 && 2 * acc < tot) {
-        acc += offs[G.members[cut] + 1] - offs[G.members[cut]];
-        ++cut;
+      int j = 1;
+      for (int m = 0; m + 1 < nm && j < P; ++m) {
+        acc += offs[G.members[m] + 1] - offs[G.members[m]];
+        if (acc * P >= tot * j || nm - (m + 1) == P - j) {
+          ends.push_back(m + 1);
+          ++j;
+        }
       }
     }
-    int t0 = 0, b0 = 0;
-    for (int m0 = 0; m0 < nm; m0 = cut, cut = nm) {
+    ends.push_back(nm);
+    int t0 = 0, b0 = 0, m0 = 0;
+    for (int cut : ends) {
       IoPart P{g, m0, cut, Part()};
       if (!(m0 == 0 && cut == nm)) {
         int nt = 0, nb = 0;
@@ -1641,6 +1651,7 @@ static int capture_io(adg_ctx *ctx, const double *w_in, double *w_out) {
         b0 += nb;
       }
       parts.push_back(P);
+      m0 = cut;
     }
     // the parts must cover the group's tables exactly; otherwise one part
     if (t0 != 0 && (t0 != G.n_tiles || b0 != G.n_blocks)) {

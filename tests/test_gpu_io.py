@@ -3,7 +3,7 @@ against adg_write_states + adg_step + adg_read_states on the same inputs: the
 host results, the device states and the troubled-cell counts are the same to
 the bit, step after step, with each step's input taken from the previous
 step's output (a host-side time loop). The instances span three degrees and
-two precisions (six groups; groups of two or more instances are cut into two
+two precisions (six groups; groups of two or more instances are cut into
 parts, stepped one after the other while the other parts' copies run). A
 second pair of buffers makes the call capture its graph again; pageable
 buffers and a one-group context take the sequential path."""
